@@ -1,0 +1,350 @@
+"""Oracle: a plain, slow, fp64 (complex128) CPU state-vector simulator of the QVA hot path.
+
+TEST INFRASTRUCTURE ONLY. Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline /
+reference legs of ``bench.py`` may import this package. It shares no code with the CUDA library
+(``paper_2110_03963_gb300``) and never imports it; the two meet only in the seeded raw inputs of
+``workloads``.
+
+What it computes (paper: Matwiejew & Wang, "QuOp_MPI: a framework for parallel simulation of
+quantum variational algorithms", arXiv 2110.03963):
+
+* Sec. 2.1, generic ansatz: |theta> = prod_k U(theta_k) |psi0>, objective f = <theta|Q|theta>
+  with Q diagonal (the quality vector q).
+* Sec. 2.1 / Sec. 3, phase shift: U_phase(gamma) = exp(-i gamma Q) acts elementwise,
+  c_i <- exp(-i gamma q_i) c_i.
+* Sec. 2.1, mixer: U_mix(t) = exp(-i t W); three forms
+    - Sec. 2.3.1 QAOA: W = sum_j X_j (hypercube adjacency; the printed "X^{tensor N}" is read as
+      the sum of single-qubit X, which is the hypercube coupling of the same section). The oracle
+      applies it as the product of the commuting single-qubit rotations exp(-i t X_j).
+    - Sec. 2.4.2 / Sec. 3 QWOA: W circulant. Eigenvalues from the first row by the DFT relation of
+      Sec. 3 (written out as a direct sum), action F^-1 exp(-i t Lambda) F (Sec. 3 prints
+      exp(+i t Lambda); exp(-i t Lambda) is what equals exp(-i t W) of Sec. 2.1).
+    - Sec. 2.4.1 QAOAz: W = sum over ring edges (a, a+1 mod n) of X_a X_{a+1} + Y_a Y_{a+1},
+      restricted to a Hamming-weight subspace; exp(-i t W) v by a truncated Taylor series with
+      step splitting (the scaling family of Sec. 3's sparse method).
+* Layer order: phase first, then mixer, parameters interleaved (gamma_1, t_1, gamma_2, t_2, ...),
+  as fixed by Example 1 (Sec. 6.1.1).
+* Gradient: the adjoint recurrences of the alternating ansatz, every intermediate state stored
+  (no uncompute), and Richardson-extrapolated central finite differences (Sec. 4 uses finite
+  differences for the gradient).
+
+Conventions: qubit u is bit (n-1-u) of the basis index (most significant first, as
+``np.binary_repr`` in Example 3 and q_90 = 0 for (0,1,0,1,1,0,1,0) in Sec. 6.1.1).
+
+Every function below is pinned by ``tests/test_oracle_pins.py`` against values the paper prints,
+closed forms, dense matrix exponentials, and invariants.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+# ============================================================== quality vectors (Sec. 2.2, Sec. 6)
+
+
+def qubit_bits(n: int, idx: np.ndarray) -> np.ndarray:
+    """x[u, i] = value of qubit u in basis state idx[i] (qubit u = bit n-1-u)."""
+    idx = np.asarray(idx, dtype=np.int64)
+    return np.stack([(idx >> (n - 1 - u)) & 1 for u in range(n)], axis=0)
+
+
+def maxcut_quality(n: int, eu, ev, w=None) -> np.ndarray:
+    """Sec. 6.1, max-cut cost C(s) = sum_{edges} 1/2 (I + Z_u Z_v) = (weighted) number of UNCUT edges.
+
+    Unit weights give integers (Example 3 counts n_edges minus cut edges). With weights, each
+    uncut edge contributes w_e; the terms are summed in edge order in fp64.
+    """
+    N = 1 << n
+    idx = np.arange(N, dtype=np.int64)
+    q = np.zeros(N, dtype=np.float64)
+    for e in range(len(eu)):
+        bu = (idx >> (n - 1 - int(eu[e]))) & 1
+        bv = (idx >> (n - 1 - int(ev[e]))) & 1
+        same = (bu == bv)
+        q += np.where(same, 1.0 if w is None else float(w[e]), 0.0)
+    return q
+
+
+def subset_quality(n: int, weights) -> np.ndarray:
+    """q_i = sum_b w_b x_b(i): item b is selected when qubit b is 1 (summed in item order, fp64)."""
+    N = 1 << n
+    idx = np.arange(N, dtype=np.int64)
+    q = np.zeros(N, dtype=np.float64)
+    for b in range(n):
+        q += np.where(((idx >> (n - 1 - b)) & 1) == 1, float(weights[b]), 0.0)
+    return q
+
+
+def subspace_states(n: int, k: int) -> np.ndarray:
+    """All n-bit basis states with exactly k ones, in increasing integer order."""
+    idx = np.arange(1 << n, dtype=np.int64)
+    pc = np.zeros_like(idx)
+    for b in range(n):
+        pc += (idx >> b) & 1
+    return idx[pc == k]
+
+
+def portfolio_quality(n_qubits: int, states: np.ndarray, returns, cov, omega: float) -> np.ndarray:
+    """Sec. 6.2, discrete mean-variance cost omega * sum_ij sigma_ij z_i z_j - (1-omega) sum_i r_i z_i.
+
+    Two qubits per asset a: qubit 2a is the 'long' qubit, qubit 2a+1 the 'short' one;
+    |10> -> long (z=+1), |01> -> short (z=-1), |00>,|11> -> no position (z=0).
+    """
+    M = n_qubits // 2
+    x = qubit_bits(n_qubits, states)
+    z = np.stack([x[2 * a] - x[2 * a + 1] for a in range(M)], axis=0).astype(np.float64)
+    q = np.zeros(states.shape[0], dtype=np.float64)
+    for i in range(M):
+        for j in range(M):
+            q += omega * float(cov[i][j]) * z[i] * z[j]
+    for i in range(M):
+        q -= (1.0 - omega) * float(returns[i]) * z[i]
+    return q
+
+
+# ============================================================== unitaries (Sec. 2.1, Sec. 3)
+
+
+def phase(psi: np.ndarray, q: np.ndarray, gamma: float) -> np.ndarray:
+    """Sec. 3: U_phase(gamma) psi = sum_i exp(-i gamma q_i) c_i |i>."""
+    return psi * (np.cos(gamma * q) - 1j * np.sin(gamma * q))
+
+
+def mix_hypercube(psi: np.ndarray, n: int, t: float) -> np.ndarray:
+    """Sec. 2.3.1: exp(-i t sum_j X_j) = prod_j (cos t I - i sin t X_j), one qubit at a time."""
+    c, s = math.cos(t), math.sin(t)
+    out = psi.copy()
+    for b in range(n):
+        v = out.reshape(-1, 2, 1 << b)      # axis 1 = bit b
+        a0 = v[:, 0, :].copy()
+        a1 = v[:, 1, :].copy()
+        v[:, 0, :] = c * a0 - 1j * s * a1
+        v[:, 1, :] = c * a1 - 1j * s * a0
+    return out
+
+
+def apply_hypercube_W(psi: np.ndarray, n: int) -> np.ndarray:
+    """W psi with W = sum_j X_j (X_j flips bit j)."""
+    idx = np.arange(psi.shape[0], dtype=np.int64)
+    out = np.zeros_like(psi)
+    for b in range(n):
+        out += psi[idx ^ (1 << b)]
+    return out
+
+
+def circulant_first_row_from_offsets(N: int, offsets, weight: float = 1.0) -> np.ndarray:
+    """Symmetric circulant adjacency: w_s = w_{N-s} = weight for each offset s (0 < s < N)."""
+    row = np.zeros(N, dtype=np.float64)
+    for s in offsets:
+        s = int(s) % N
+        if s == 0:
+            continue
+        row[s] = weight
+        row[(N - s) % N] = weight
+    return row
+
+
+def circulant_eigenvalues(first_row: np.ndarray) -> np.ndarray:
+    """Sec. 3: lambda_j = sum_k w_k omega^{jk}, omega = exp(2 pi i / M), summed directly over the
+    nonzero entries of the first row. Requires a symmetric first row (w_k = w_{M-k}), so the
+    eigenvalues are real; the exponent j*k is reduced mod M in integers before the cosine.
+    """
+    M = first_row.shape[0]
+    ks = np.nonzero(first_row)[0]
+    assert np.allclose(first_row, np.roll(first_row[::-1], 1)), "circulant must be symmetric"
+    j = np.arange(M, dtype=np.int64)
+    lam = np.zeros(M, dtype=np.float64)
+    for k in ks:
+        lam += first_row[k] * np.cos(2.0 * math.pi * ((j * int(k)) % M) / M)
+    return lam
+
+
+def mix_circulant(psi: np.ndarray, lam: np.ndarray, t: float) -> np.ndarray:
+    """Sec. 3: U_mix(t) psi = F^-1 exp(-i t Lambda) F psi (F = unitary DFT; numpy's FFT pair)."""
+    return np.fft.ifft(np.exp(-1j * t * lam) * np.fft.fft(psi))
+
+
+def apply_circulant_W(psi: np.ndarray, lam: np.ndarray) -> np.ndarray:
+    return np.fft.ifft(lam * np.fft.fft(psi))
+
+
+def xy_ring_apply(psi: np.ndarray, n: int, states: np.ndarray) -> np.ndarray:
+    """Sec. 2.4.1 operator family: W = sum_{a=0}^{n-1} (X_a X_{a+1} + Y_a Y_{a+1}), a+1 taken mod n,
+    on the subspace spanned by ``states``. (XX+YY)|01> = 2|10>, (XX+YY)|00> = (XX+YY)|11> = 0.
+    """
+    out = np.zeros_like(psi)
+    for a in range(n):
+        b = (a + 1) % n
+        ba, bb = n - 1 - a, n - 1 - b
+        differ = (((states >> ba) ^ (states >> bb)) & 1) == 1
+        src = np.nonzero(differ)[0]
+        flipped = states[src] ^ ((1 << ba) | (1 << bb))
+        dst = np.searchsorted(states, flipped)
+        assert np.all(states[dst] == flipped)
+        np.add.at(out, dst, 2.0 * psi[src])
+    return out
+
+
+def mix_xy_ring(psi: np.ndarray, n: int, states: np.ndarray, t: float) -> np.ndarray:
+    """exp(-i t W) psi by a Taylor series with step splitting: s substeps of tau = t/s with
+    |tau| * ||W||_1 <= 1 (||W||_1 <= 2n: at most n differing ring pairs, each entry 2); each
+    substep sums terms until one falls below 1e-18 of the vector's max norm.
+    """
+    s = max(1, math.ceil(abs(t) * 2 * n))
+    tau = t / s
+    v = psi.copy()
+    for _ in range(s):
+        term = v.copy()
+        acc = v.copy()
+        m = 1
+        while True:
+            term = (-1j * tau / m) * xy_ring_apply(term, n, states)
+            acc = acc + term
+            if np.max(np.abs(term)) < 1e-18 * max(np.max(np.abs(acc)), 1e-300) or m > 60:
+                break
+            m += 1
+        v = acc
+    return v
+
+
+# ============================================================== problems and the ansatz
+
+
+@dataclass
+class Problem:
+    """One QVA instance: quality vector q (fp64), a mixer, and an initial state (None = uniform)."""
+    q: np.ndarray
+    mixer: str                     # "hypercube" | "circulant" | "xy_ring"
+    n: int = 0                     # qubits (hypercube, xy_ring)
+    lam: np.ndarray | None = None  # circulant eigenvalues
+    states: np.ndarray | None = None   # xy_ring subspace basis
+    psi0: np.ndarray | None = None
+
+    @property
+    def dim(self) -> int:
+        return int(self.q.shape[0])
+
+    def initial_state(self) -> np.ndarray:
+        """Sec. 2.3.1 / Sec. 2.4.2: equal superposition over the simulated space, 1/sqrt(dim)."""
+        if self.psi0 is not None:
+            return np.asarray(self.psi0, dtype=np.complex128).copy()
+        return np.full(self.dim, 1.0 / math.sqrt(self.dim), dtype=np.complex128)
+
+    def mix(self, psi: np.ndarray, t: float) -> np.ndarray:
+        if self.mixer == "hypercube":
+            return mix_hypercube(psi, self.n, t)
+        if self.mixer == "circulant":
+            return mix_circulant(psi, self.lam, t)
+        if self.mixer == "xy_ring":
+            return mix_xy_ring(psi, self.n, self.states, t)
+        raise ValueError(self.mixer)
+
+    def apply_W(self, psi: np.ndarray) -> np.ndarray:
+        if self.mixer == "hypercube":
+            return apply_hypercube_W(psi, self.n)
+        if self.mixer == "circulant":
+            return apply_circulant_W(psi, self.lam)
+        if self.mixer == "xy_ring":
+            return xy_ring_apply(psi, self.n, self.states)
+        raise ValueError(self.mixer)
+
+
+def evolve(prob: Problem, gammas, ts) -> np.ndarray:
+    """Sec. 2.1 / Eqs. of Sec. 2.3-2.4: psi_p = prod_{k=1..p} U_mix(t_k) U_phase(gamma_k) psi0."""
+    psi = prob.initial_state()
+    for g, t in zip(gammas, ts):
+        psi = phase(psi, prob.q, float(g))
+        psi = prob.mix(psi, float(t))
+    return psi
+
+
+def expectation(psi: np.ndarray, q: np.ndarray) -> float:
+    """Sec. 2.1: f = <psi|Q|psi> = sum_i q_i |c_i|^2."""
+    return float(np.sum(q * (psi.real ** 2 + psi.imag ** 2)))
+
+
+def objective(prob: Problem, gammas, ts) -> float:
+    return expectation(evolve(prob, gammas, ts), prob.q)
+
+
+def gradient(prob: Problem, gammas, ts):
+    """Adjoint gradient of f = <psi_p|Q|psi_p> with every state stored.
+
+    Forward: phi_k = P_k psi_{k-1}, psi_k = M_k phi_k.
+    With lambda_p = Q psi_p and lambda_{k-1} = P_k^dag M_k^dag lambda_k:
+      df/dt_k     = 2 Im <lambda_k | W psi_k>
+      df/dgamma_k = 2 Im <M_k^dag lambda_k | Q phi_k>
+    Returns (f, dgamma[p], dt[p]).
+    """
+    p = len(gammas)
+    psi = prob.initial_state()
+    phis, psis = [], []
+    for k in range(p):
+        phi = phase(psi, prob.q, float(gammas[k]))
+        psi = prob.mix(phi, float(ts[k]))
+        phis.append(phi)
+        psis.append(psi)
+    f = expectation(psi, prob.q)
+    lam = prob.q * psi
+    dg = np.zeros(p)
+    dt = np.zeros(p)
+    for k in range(p - 1, -1, -1):
+        dt[k] = 2.0 * np.vdot(lam, prob.apply_W(psis[k])).imag
+        lam = prob.mix(lam, -float(ts[k]))                # M_k^dag
+        dg[k] = 2.0 * np.vdot(lam, prob.q * phis[k]).imag
+        lam = phase(lam, prob.q, -float(gammas[k]))       # P_k^dag
+    return f, dg, dt
+
+
+def central_fd(prob: Problem, gammas, ts, h: float = 1e-3):
+    """Richardson-extrapolated central differences: D(h) = (f(x+h)-f(x-h))/2h,
+    estimate = (4 D(h/2) - D(h)) / 3 (error O(h^4))."""
+    gammas = np.asarray(gammas, dtype=np.float64)
+    ts = np.asarray(ts, dtype=np.float64)
+    p = len(gammas)
+
+    def d(vec_is_gamma, k, hh):
+        g1, t1 = gammas.copy(), ts.copy()
+        g2, t2 = gammas.copy(), ts.copy()
+        if vec_is_gamma:
+            g1[k] += hh
+            g2[k] -= hh
+        else:
+            t1[k] += hh
+            t2[k] -= hh
+        return (objective(prob, g1, t1) - objective(prob, g2, t2)) / (2 * hh)
+
+    dg = np.array([(4 * d(True, k, h / 2) - d(True, k, h)) / 3 for k in range(p)])
+    dt = np.array([(4 * d(False, k, h / 2) - d(False, k, h)) / 3 for k in range(p)])
+    return dg, dt
+
+
+# ============================================================== convenience builders
+
+
+def maxcut_problem(n: int, eu, ev, w=None, q_dtype=None) -> Problem:
+    """QAOA max-cut: hypercube mixer; q rounded to ``q_dtype`` (e.g. float32) and promoted back
+    to fp64 when the simulated device path consumes that precision."""
+    q = maxcut_quality(n, eu, ev, w)
+    if q_dtype is not None:
+        q = q.astype(q_dtype).astype(np.float64)
+    return Problem(q=q, mixer="hypercube", n=n)
+
+
+def qwoa_problem(log2n: int, weights, offsets, q_dtype=None) -> Problem:
+    N = 1 << log2n
+    q = subset_quality(log2n, weights)
+    if q_dtype is not None:
+        q = q.astype(q_dtype).astype(np.float64)
+    lam = circulant_eigenvalues(circulant_first_row_from_offsets(N, offsets))
+    return Problem(q=q, mixer="circulant", lam=lam)
+
+
+def qaoaz_problem(n: int, k: int, returns, cov, omega: float, q_dtype=None) -> Problem:
+    states = subspace_states(n, k)
+    q = portfolio_quality(n, states, returns, cov, omega)
+    if q_dtype is not None:
+        q = q.astype(q_dtype).astype(np.float64)
+    return Problem(q=q, mixer="xy_ring", n=n, states=states)

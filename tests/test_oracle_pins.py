@@ -1,0 +1,289 @@
+"""Pins of the fp64 oracle against things other than itself (CPU only).
+
+Each test is chosen so that a plausible mistake in the oracle (a dropped term, a wrong sign, a
+wrong bit order, a transposed operand, a swapped parameter order) makes at least one fail.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+import oracle as orc
+import workloads as wl
+from tests import closed_forms as cf
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _dense_pauli(n, ops):
+    """Dense 2^n matrix of a Pauli string {qubit: 'X'|'Y'|'Z'} (qubit u = bit n-1-u, so qubit 0 is
+    the leftmost Kronecker factor)."""
+    P = {"I": np.eye(2), "X": np.array([[0, 1], [1, 0]]), "Y": np.array([[0, -1j], [1j, 0]]),
+         "Z": np.diag([1.0, -1.0])}
+    m = np.array([[1.0 + 0j]])
+    for u in range(n):
+        m = np.kron(m, P[ops.get(u, "I")])
+    return m
+
+
+# ------------------------------------------------------------------ P1/P2: the paper's Example 1
+
+def _ex1():
+    with open(os.path.join(GOLDEN, "ex1_maxcut_cl4.json")) as f:
+        return json.load(f)
+
+
+def test_p1_example1_objective_matches_printed_value():
+    g = _ex1()
+    e = np.array(g["edges"])
+    prob = orc.maxcut_problem(g["n"], e[:, 0], e[:, 1])
+    th = g["theta_interleaved"]
+    f = orc.objective(prob, th[0::2], th[1::2])
+    assert abs(f - g["f_printed"]) <= g["f_tolerance"], f
+
+
+def test_p1_example1_rejects_other_conventions():
+    """Blocked parameter order or the literal X^{tensor n} mixer do not reproduce 2.30."""
+    g = _ex1()
+    e = np.array(g["edges"])
+    prob = orc.maxcut_problem(g["n"], e[:, 0], e[:, 1])
+    th = g["theta_interleaved"]
+    f_blocked = orc.objective(prob, th[:2], th[2:])
+    assert abs(f_blocked - g["f_printed"]) > 0.5
+    # phase with the opposite sign moves f as well
+    f_neg = orc.objective(prob, [-x for x in th[0::2]], th[1::2])
+    assert abs(f_neg - g["f_printed"]) > 0.5
+
+
+def test_p2_example1_optimal_quality_and_bit_order():
+    g = _ex1()
+    e = np.array(g["edges"])
+    q = orc.maxcut_quality(g["n"], e[:, 0], e[:, 1])
+    assert q[g["optimal_index"]] == g["optimal_quality"]
+    bits = [int(b) for b in np.binary_repr(g["optimal_index"], width=g["n"])]
+    assert bits == g["optimal_bits"]
+    # the optimum and its complement are the only zero-quality states
+    assert set(np.nonzero(q == 0)[0].tolist()) == {g["optimal_index"], (1 << g["n"]) - 1 - g["optimal_index"]}
+    assert q.max() == len(g["edges"])
+
+
+# ------------------------------------------------------------------ P3: p=1 closed form
+
+@pytest.mark.parametrize("n,weighted,seed", [(8, False, 0), (10, False, 1), (9, True, 2), (11, True, 3)])
+def test_p3_p1_closed_form(n, weighted, seed):
+    rng = wl.rng_for(99, seed)
+    if weighted:
+        G = wl.gnp_graph(n, 0.5, rng, weighted=True)
+    else:
+        G = wl.regular3_graph(n, rng)
+    prob = orc.maxcut_problem(n, G.eu, G.ev, G.w)
+    for gamma, t in [(0.37, 0.81), (2.9, 1.3), (1.1, 2.7)]:
+        f = orc.objective(prob, [gamma], [t])
+        ref = cf.p1_maxcut_expectation(n, G.eu, G.ev, G.w, gamma, t)
+        assert abs(f - ref) < 1e-12 * max(1.0, abs(ref)), (f, ref)
+
+
+def test_p3_p1_amplitudes_explicit_sum():
+    n = 9
+    G = wl.gnp_graph(n, 0.5, wl.rng_for(98, 0), weighted=True)
+    prob = orc.maxcut_problem(n, G.eu, G.ev, G.w)
+    psi = orc.evolve(prob, [0.7], [0.4])
+    for i in [0, 5, 77, 300, 511]:
+        a = cf.p1_hypercube_amplitude(n, prob.q, 0.7, 0.4, i)
+        assert abs(psi[i] - a) < 1e-13
+
+
+# ------------------------------------------------------------------ P4: dense matrix exponentials
+
+def test_p4_hypercube_vs_expm():
+    n = 6
+    W = sum(_dense_pauli(n, {u: "X"}) for u in range(n))
+    rng = np.random.default_rng(4)
+    psi = rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)
+    for t in [0.3, 1.7, -2.2]:
+        ref = scipy.linalg.expm(-1j * t * W) @ psi
+        assert np.max(np.abs(orc.mix_hypercube(psi, n, t) - ref)) < 1e-12
+        assert np.max(np.abs(orc.apply_hypercube_W(psi, n) - W @ psi)) < 1e-12
+
+
+def test_p4_circulant_vs_expm():
+    N = 64
+    row = orc.circulant_first_row_from_offsets(N, [1, 2, 4, 8, 16, 32])
+    C = np.array([[row[(k - j) % N] for k in range(N)] for j in range(N)])
+    lam = orc.circulant_eigenvalues(row)
+    rng = np.random.default_rng(5)
+    psi = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    for t in [0.25, 1.9]:
+        ref = scipy.linalg.expm(-1j * t * C) @ psi
+        assert np.max(np.abs(orc.mix_circulant(psi, lam, t) - ref)) < 1e-11
+    assert np.max(np.abs(orc.apply_circulant_W(psi, lam) - C @ psi)) < 1e-11
+
+
+@pytest.mark.parametrize("n,k", [(6, 3), (8, 4), (7, 2)])
+def test_p4_xy_ring_vs_expm(n, k):
+    H = np.zeros((1 << n, 1 << n), dtype=complex)
+    for a in range(n):
+        b = (a + 1) % n
+        H += _dense_pauli(n, {a: "X", b: "X"}) + _dense_pauli(n, {a: "Y", b: "Y"})
+    states = orc.subspace_states(n, k)
+    Hs = H[np.ix_(states, states)]
+    # the Hamming-weight subspace is invariant: nothing leaks out of it
+    other = np.setdiff1d(np.arange(1 << n), states)
+    assert np.max(np.abs(H[np.ix_(other, states)])) == 0
+    rng = np.random.default_rng(6)
+    psi = rng.standard_normal(states.shape[0]) + 1j * rng.standard_normal(states.shape[0])
+    assert np.max(np.abs(orc.xy_ring_apply(psi, n, states) - Hs @ psi)) < 1e-12
+    for t in [0.2, 1.3]:
+        ref = scipy.linalg.expm(-1j * t * Hs) @ psi
+        assert np.max(np.abs(orc.mix_xy_ring(psi, n, states, t) - ref)) < 1e-11
+
+
+def test_p4_full_ansatz_vs_dense_qaoa():
+    """Whole p=3 ansatz against dense exponentials of W and diag(q) (n=7)."""
+    n = 7
+    G = wl.gnp_graph(n, 0.5, wl.rng_for(97, 0), weighted=True)
+    prob = orc.maxcut_problem(n, G.eu, G.ev, G.w)
+    W = sum(_dense_pauli(n, {u: "X"}) for u in range(n))
+    Q = np.diag(prob.q)
+    psi = np.full(1 << n, 1 / math.sqrt(1 << n), dtype=complex)
+    gs, ts = [0.3, 1.2, 2.2], [0.9, 0.4, 2.8]
+    for g, t in zip(gs, ts):
+        psi = scipy.linalg.expm(-1j * t * W) @ (scipy.linalg.expm(-1j * g * Q) @ psi)
+    assert np.max(np.abs(orc.evolve(prob, gs, ts) - psi)) < 1e-12
+
+
+# ------------------------------------------------------------------ P5/P7: circulant closed forms
+
+def test_p5_complete_graph_mixer():
+    N = 256
+    row = np.ones(N)
+    row[0] = 0.0
+    lam = orc.circulant_eigenvalues(row)
+    assert lam[0] == pytest.approx(N - 1)
+    assert np.max(np.abs(lam[1:] + 1.0)) < 1e-9
+    rng = np.random.default_rng(7)
+    psi = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    for t in [0.1, 0.77, 3.0]:
+        assert np.max(np.abs(orc.mix_circulant(psi, lam, t) - cf.complete_graph_mix(psi, t))) < 1e-11
+
+
+@pytest.mark.parametrize("log2n", [4, 9, 12])
+def test_p7_circulant_eigenvalues(log2n):
+    N = 1 << log2n
+    row = orc.circulant_first_row_from_offsets(N, wl.circulant_offsets_pow2(log2n))
+    lam = orc.circulant_eigenvalues(row)
+    assert np.max(np.abs(lam - cf.pow2_circulant_eigs(log2n))) < 1e-10
+    # library FFT of the first row gives the same spectrum
+    assert np.max(np.abs(lam - np.fft.fft(row).real)) < 1e-9
+    # degree: every vertex has 2*(log2n-1) + 1 neighbours
+    assert lam[0] == pytest.approx(2 * (log2n - 1) + 1)
+
+
+# ------------------------------------------------------------------ P8: XY pair rotation
+
+def test_p8_xy_pair_is_givens():
+    """On n=2 the 'ring' has the pair (0,1) twice, so W = 2 (XX + YY); check exp on |01>,|10>."""
+    n = 2
+    states = orc.subspace_states(n, 1)       # [1, 2] = |01>, |10>
+    psi = np.array([0.6, 0.8j])
+    for t in [0.3, 1.1]:
+        ref = cf.givens_xy(2 * t) @ psi
+        assert np.max(np.abs(orc.mix_xy_ring(psi, n, states, t) - ref)) < 1e-12
+
+
+# ------------------------------------------------------------------ P9: invariants
+
+def _qaoa_small(n=8, seed=0):
+    G = wl.gnp_graph(n, 0.5, wl.rng_for(96, seed), weighted=True)
+    return orc.maxcut_problem(n, G.eu, G.ev, G.w)
+
+
+def test_p9_norm_and_reversibility():
+    for prob in [_qaoa_small(),
+                 orc.qwoa_problem(8, wl.item_weights(8, wl.rng_for(95, 0)), wl.circulant_offsets_pow2(8)),
+                 orc.qaoaz_problem(8, 4, *(lambda P: (P.returns, P.cov, P.omega))(wl.portfolio(4, wl.rng_for(94, 0))))]:
+        gs, ts = [0.4, 2.1, 1.3], [0.7, 0.2, 2.9]
+        psi = orc.evolve(prob, gs, ts)
+        assert abs(np.vdot(psi, psi).real - 1.0) < 1e-13
+        # un-evolve: apply the inverse layers in reverse order
+        back = psi
+        for g, t in zip(gs[::-1], ts[::-1]):
+            back = prob.mix(back, -t)
+            back = orc.phase(back, prob.q, -g)
+        assert np.max(np.abs(back - prob.initial_state())) < 1e-12
+        f = orc.expectation(psi, prob.q)
+        assert prob.q.min() - 1e-12 <= f <= prob.q.max() + 1e-12
+
+
+def test_p9_periodicities_and_symmetry():
+    n = 8
+    G = wl.regular3_graph(n, wl.rng_for(93, 0))
+    prob = orc.maxcut_problem(n, G.eu, G.ev)       # integer q
+    gs, ts = [0.4, 2.1], [0.7, 1.9]
+    f = orc.objective(prob, gs, ts)
+    assert orc.objective(prob, [gs[0] + 2 * math.pi, gs[1]], ts) == pytest.approx(f, abs=1e-12)
+    assert orc.objective(prob, gs, [ts[0] + math.pi, ts[1]]) == pytest.approx(f, abs=1e-12)
+    # real initial state and real q: E(-gamma, -t) = E(gamma, t)
+    assert orc.objective(prob, [-x for x in gs], [-x for x in ts]) == pytest.approx(f, abs=1e-12)
+    # relabelling the vertices does not change E
+    perm = wl.rng_for(93, 1).permutation(n)
+    prob2 = orc.maxcut_problem(n, perm[G.eu], perm[G.ev])
+    assert orc.objective(prob2, gs, ts) == pytest.approx(f, abs=1e-12)
+    # complete graph: E is periodic in t with period 2 pi / N
+    N = 64
+    row = np.ones(N)
+    row[0] = 0
+    pc = orc.Problem(q=prob.q[:N], mixer="circulant", lam=orc.circulant_eigenvalues(row))
+    fc = orc.objective(pc, [0.5], [0.3])
+    assert orc.objective(pc, [0.5], [0.3 + 2 * math.pi / N]) == pytest.approx(fc, abs=1e-11)
+
+
+# ------------------------------------------------------------------ P10: gradients
+
+@pytest.mark.parametrize("kind", ["hypercube", "circulant", "xy_ring"])
+def test_p10_adjoint_vs_richardson_fd(kind):
+    if kind == "hypercube":
+        prob = _qaoa_small(7, 1)
+    elif kind == "circulant":
+        prob = orc.qwoa_problem(7, wl.item_weights(7, wl.rng_for(92, 0)), wl.circulant_offsets_pow2(7))
+    else:
+        P = wl.portfolio(4, wl.rng_for(91, 0))
+        prob = orc.qaoaz_problem(8, 4, P.returns, P.cov, P.omega)
+    gs, ts = [0.4, 2.1, 1.3], [0.7, 0.2, 2.9]
+    f, dg, dt = orc.gradient(prob, gs, ts)
+    assert f == pytest.approx(orc.objective(prob, gs, ts), abs=1e-13)
+    fdg, fdt = orc.central_fd(prob, gs, ts, h=1e-3)
+    scale = max(np.max(np.abs(dg)), np.max(np.abs(dt)))
+    assert np.max(np.abs(dg - fdg)) < 1e-8 * scale
+    assert np.max(np.abs(dt - fdt)) < 1e-8 * scale
+
+
+def test_p10_adjoint_vs_closed_form_derivative():
+    n = 9
+    G = wl.gnp_graph(n, 0.5, wl.rng_for(90, 0), weighted=True)
+    prob = orc.maxcut_problem(n, G.eu, G.ev, G.w)
+    f, dg, dt = orc.gradient(prob, [1.3], [0.6])
+    cg, ct = cf.p1_maxcut_gradient(n, G.eu, G.ev, G.w, 1.3, 0.6)
+    assert dg[0] == pytest.approx(cg, rel=1e-7, abs=1e-9)
+    assert dt[0] == pytest.approx(ct, rel=1e-7, abs=1e-9)
+
+
+# ------------------------------------------------------------------ qualities
+
+def test_quality_subset_and_portfolio_small_cases():
+    # subset: qubit b selects item b (qubit 0 = most significant bit)
+    q = orc.subset_quality(3, [1.0, 10.0, 100.0])
+    assert q.tolist() == [0, 100, 10, 110, 1, 101, 11, 111]
+    # portfolio: one asset: |10> long (z=+1), |01> short (z=-1)
+    states = np.array([0, 1, 2, 3])
+    q = orc.portfolio_quality(2, states, [2.0], [[3.0]], 0.25)
+    # z = [0, -1, +1, 0]: omega*3*z^2 - 0.75*2*z
+    assert np.allclose(q, [0.0, 0.75 + 1.5, 0.75 - 1.5, 0.0])
+
+
+def test_subspace_count():
+    assert orc.subspace_states(10, 5).shape[0] == math.comb(10, 5)
+    assert orc.subspace_states(24, 12).shape[0] == 2704156

@@ -1,0 +1,316 @@
+"""Throughput of the QVA hot path on GB300: amplitude-layer updates per second for one
+objective + adjoint-gradient solve of QAOA weighted max-cut, n = 28 qubits (2^28 complex64
+amplitudes), G(28, 1/2) with U[0,1] weights, p = 8 layers.
+
+One step = qvs_gradient on that instance: forward evolution through 8 layers (phase + hypercube
+mixer), the objective <psi|Q|psi> and the adjoint sweep giving all 16 gradient entries.
+Units: 2^28 * 8 amplitude-layer updates per step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the fp64 CPU oracle (the only reference: the paper ships no code) on a
+bounded sample of the same workload family. Under torchrun (N > 1) every rank runs an independent
+replica (the path does not shard across ranks); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as wl  # noqa: E402
+
+N_QUBITS = 28
+P_LAYERS = 8
+METRIC = "amplitude-layer updates/s (fwd+adjoint grad) n=28 QAOA; % of HBM peak"
+UNIT = "amp-layer/s"
+WORKLOAD = "QAOA weighted max-cut, n=28 (2^28 complex64 amplitudes), G(28,1/2) U[0,1] weights, p=8, objective + adjoint gradient"
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = "clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown," \
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown," \
+             "clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ------------------------------------------------------------------ CPU oracle sample
+
+def oracle_sample(seconds_target: float = 15.0):
+    """Time the fp64 numpy oracle (as it stands) on the same workload family: weighted max-cut on
+    G(n, 1/2), p = 8, objective + adjoint gradient, at the largest n (starting from 16) whose
+    solve stays near the time target. Returns (amp-layer/s, description)."""
+    import oracle as orc
+    best = None
+    for n in range(16, N_QUBITS + 1):
+        inst = wl.wmaxcut(n, P_LAYERS)
+        G = inst.graph
+        prob = orc.maxcut_problem(n, G.eu, G.ev, G.w, q_dtype=np.float32)
+        t0 = time.perf_counter()
+        orc.gradient(prob, inst.gammas, inst.ts)
+        dt = time.perf_counter() - t0
+        best = (n, dt)
+        if dt * 2.2 > seconds_target:
+            break
+    n, dt = best
+    rate = (1 << n) * P_LAYERS / dt
+    desc = (f"oracle (numpy fp64, single thread) objective + adjoint gradient of weighted max-cut on G({n},1/2), "
+            f"p={P_LAYERS}: {dt:.2f} s per solve of 2^{n} amplitudes")
+    return rate, desc, n
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    vals = []
+    n_used = None
+    desc = ""
+    t_all = time.perf_counter()
+    for i in range(args.warmup + args.steps):
+        rate, desc, n_used = oracle_sample(seconds_target=max(2.0, 60.0 / max(1, args.warmup + args.steps)))
+        if i >= args.warmup:
+            vals.append(rate)
+    value = float(np.median(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": (1 << n_used) * P_LAYERS / value * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample_n_qubits": n_used},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": time.perf_counter() - t_all,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_ours(args):
+    import torch
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    from paper_2110_03963_gb300 import _build
+    if rank == 0 or world == 1:
+        _build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    import paper_2110_03963_gb300 as qvs
+
+    n, p = N_QUBITS, P_LAYERS
+    dim = 1 << n
+    inst = wl.wmaxcut(n, p, instance=rank)
+    G = inst.graph
+    stream = torch.cuda.current_stream()
+    q = torch.empty(dim, dtype=torch.float32, device="cuda")
+    qvs.qvs_quality_maxcut(n, G.eu, G.ev, G.w, q, qvs.QVS_F32, stream)
+    sim = qvs.Simulator(dim, qvs.QVS_C64, stream)
+    sim.set_quality(q)
+    sim.set_mixer(qvs.QVS_MIX_HYPERCUBE, qvs.hypercube_desc(n))
+    if args.ckpt is not None:
+        sim.set_option(qvs.QVS_OPT_CKPT_LAYERS, args.ckpt)
+    gs, ts = np.asarray(inst.gammas), np.asarray(inst.ts)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-resident timing
+    for _ in range(args.warmup):
+        sim.gradient(gs, ts)
+    launches_per_step = sim.launches()
+    sampler = ClockSampler(dev)
+    barrier()
+    sampler.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    results = []
+    for _ in range(args.steps):
+        results.append(sim.gradient(gs, ts))
+    ev1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    units = float(dim) * p
+    value = units * world / (ms * 1e-3)
+
+    # ---- per-kernel event timing (separate, profiled steps)
+    sim.set_option(qvs.QVS_OPT_PROFILE, 1)
+    for _ in range(max(2, min(args.steps, 5))):
+        sim.gradient(gs, ts)
+    stats = qvs.qvs_kernel_stats(sim.h)
+    sim.set_option(qvs.QVS_OPT_PROFILE, 0)
+    total_ms = sum(s["ms"] for s in stats) or 1.0
+    top = max(stats, key=lambda s: s["ms"])
+    peak, peak_kind = _peaks()
+    achieved = top["bytes"] / (top["ms"] * 1e-3) / 1e9
+    kernels = {s["name"]: {"launches": s["launches"], "avg_ms": s["ms"] / s["launches"],
+                           "share": s["ms"] / total_ms,
+                           "GBps": s["bytes"] / (s["ms"] * 1e-3) / 1e9 if s["ms"] > 0 else None}
+               for s in stats}
+    step_bytes = sum(s["bytes"] for s in stats) / max(2, min(args.steps, 5))
+
+    # ---- end to end through the C ABI with host buffers
+    q_host = torch.empty(dim, dtype=torch.float32, pin_memory=True)
+    q_host.copy_(q.cpu())
+    del q
+    torch.cuda.empty_cache()
+    for _ in range(2):
+        sim.set_quality(q_host.numpy())
+        sim.gradient(gs, ts)
+    barrier()
+    t0 = time.perf_counter()
+    e2e_steps = max(3, args.steps // 2)
+    for _ in range(e2e_steps):
+        sim.set_quality(q_host.numpy())      # H2D of the step's quality vector (pinned host)
+        E, dg, dt = sim.gradient(gs, ts)      # returns E and 2p gradient entries to the host
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = units * world / e2e_s
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, desc, _ = oracle_sample(seconds_target=15.0)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        E0 = results[-1][0]
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64 (fp32 complex; fp64 phase turns, reductions)",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_qubits": n, "p": p, "amplitudes": dim,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (2 GiB state, 1 GiB q)",
+                       "ckpt_layers": args.ckpt if args.ckpt is not None else "ceil(sqrt(p))"},
+            "roofline": {"bound": "hbm", "kernel": top["name"], "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
+                         "traffic": None},
+            "step_roofline": {"algorithmic_bytes_per_step": step_bytes,
+                              "GBps": step_bytes / (ms * 1e-3) / 1e9,
+                              "frac": step_bytes / (ms * 1e-3) / 1e9 / peak},
+            "kernels": kernels,
+            "gpu_launches": launches_per_step * args.steps,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": dim * 4 + 16 * p,
+                    "d2h_bytes_per_step": 8 * (1 + 2 * p)},
+            "clocks": clocks,
+            "objective": E0,
+        }
+        if cpu:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ckpt", type=int, default=None, help="checkpoint interval in layers (0 = ceil(sqrt(p)))")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,178 @@
+/*
+ * qvs.h - C ABI of libqvs, a single-GPU (sm_103a) state-vector engine for quantum variational
+ * algorithms (QAOA, QWOA, QAOAz) following Matwiejew & Wang, "QuOp_MPI: a framework for parallel
+ * simulation of quantum variational algorithms" (arXiv 2110.03963).
+ *
+ * What the library computes (paper Sec. 2.1): for a quality vector q (the diagonal of Q), a mixing
+ * operator W and parameters gamma_k, t_k (k = 1..p), the state
+ *     |theta> = prod_{k=1..p} exp(-i t_k W) exp(-i gamma_k Q) |psi0>
+ * (phase first, then mixer, within each layer - the interleaved order of Sec. 6.1.1), the
+ * objective f = <theta|Q|theta> and its gradient with respect to every gamma_k and t_k.
+ *
+ * Conventions shared by every entry point:
+ *   - All functions return an int status (QVS_OK = 0 or a negative QVS_E* code); none aborts,
+ *     traps or prints. qvs_strerror() names a code. A CUDA failure is QVS_ECUDA and leaves the
+ *     handle usable unless the CUDA context itself is lost.
+ *   - A qvs_t handle owns every device buffer it allocates (state, adjoint vector, checkpoints,
+ *     copies of q and of the mixer, reduction scratch); qvs_destroy frees them. Inputs are always
+ *     copied: the caller may free or reuse its buffers as soon as a call returns.
+ *   - "on_device" arguments: 0 = the pointer is host memory, 1 = device memory of the handle's
+ *     device. Host inputs may be pageable or pinned.
+ *   - Every kernel is launched on the handle's stream (the one given to qvs_create, or the legacy
+ *     default stream when NULL). Scalar outputs (E, gradients) are complete when the call returns;
+ *     the call synchronises the stream for them.
+ *   - Basis index i holds qubit u in bit (n-1-u) (most significant first).
+ *   - Parameters arrive as two host arrays gammas[p], ts[p] (layer k uses gammas[k], ts[k]).
+ *   - Calls on one handle are not thread-safe; distinct handles are independent.
+ */
+#ifndef QVS_H
+#define QVS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qvs_ctx* qvs_t;
+
+/* status codes */
+enum {
+  QVS_OK = 0,
+  QVS_EINVAL = -1,       /* bad argument: NULL pointer, size, dtype, non-finite parameter   */
+  QVS_ENOMEM = -2,       /* device allocation failed                                         */
+  QVS_ECUDA = -3,        /* a CUDA runtime call or kernel launch failed                      */
+  QVS_ESTATE = -4,       /* call out of order (e.g. evolve before quality and mixer are set) */
+  QVS_ENUMERIC = -5,     /* numerical check failed (e.g. Chebyshev series did not converge)  */
+  QVS_ETIMEOUT = -6,     /* a bounded device-side wait gave up                               */
+  QVS_EUNSUPPORTED = -7  /* valid request outside what this build implements                  */
+};
+
+/* state precision */
+enum { QVS_C64 = 1, QVS_C128 = 2 };
+/* element type of quality vectors */
+enum { QVS_I32 = 1, QVS_F32 = 2, QVS_F64 = 3 };
+/* mixer kinds (paper Sec. 3: sparse, circulant, and the QAOA hypercube) */
+enum { QVS_MIX_HYPERCUBE = 1, QVS_MIX_CIRCULANT = 2, QVS_MIX_CSR = 3 };
+/* options for qvs_set_option */
+enum {
+  QVS_OPT_CKPT_LAYERS = 1,  /* adjoint: store the forward state every this many layers and
+                               uncompute in between; 0 = ceil(sqrt(p)) (default); 1 = store
+                               every pass boundary (no uncompute)                             */
+  QVS_OPT_PROFILE = 2       /* 1: bracket every kernel launch with CUDA events on the handle's
+                               stream and accumulate per-kernel statistics (qvs_kernel_stats);
+                               0: off (default). Setting it resets the statistics.           */
+};
+
+/*
+ * Mixer description (qvs_set_mixer). Only the fields of the chosen kind are read.
+ *
+ * QVS_MIX_HYPERCUBE (Sec. 2.3.1): W = sum_j X_j on n_qubits qubits; dim must equal 2^n_qubits.
+ * QVS_MIX_CIRCULANT (Sec. 2.4.2, Sec. 3): W symmetric circulant of size dim (a power of two),
+ *     given by n_offsets connection offsets s (0 < s < dim) with weights w_s (NULL = all 1):
+ *     W[j][(j+s) mod dim] = W[j][(j-s) mod dim] = w_s (the offset dim/2 couples each j once).
+ * QVS_MIX_CSR (Sec. 2.4.1, Sec. 3): W real symmetric sparse (rowptr int64[dim+1], colind
+ *     int32[nnz]), values float[nnz] or NULL for a constant implicit_value; host or device arrays
+ *     per csr_on_device. spec_lo/spec_hi bound the spectrum (both 0: a Gershgorin bound is
+ *     computed); cheb_tol is the Chebyshev truncation tolerance (0: 1e-7).
+ */
+typedef struct {
+  int n_qubits;
+  int n_offsets;
+  const int64_t* offsets;
+  const double* offset_weights;
+  const int64_t* rowptr;
+  const int32_t* colind;
+  const float* values;
+  float implicit_value;
+  int64_t nnz;
+  int csr_on_device;
+  double spec_lo, spec_hi;
+  double cheb_tol;
+} qvs_mixer_desc;
+
+/* Sec. 4 ("plan"): create a handle for states of dimension dim at the given precision on the
+ * current CUDA device. stream: a cudaStream_t or NULL. On success *out is set. */
+int qvs_create(qvs_t* out, int64_t dim, int precision, void* stream);
+
+/* Release every device buffer of the handle (NULL is accepted). */
+int qvs_destroy(qvs_t h);
+
+/* Sec. 2.1: set the quality vector q (dim entries). I32 and F32 values are used as given
+ * (the complex64 path computes phases from the fp32 value); F64 is kept in fp64 by the
+ * complex128 path and rounded once to fp32 by the complex64 path. */
+int qvs_set_quality(qvs_t h, const void* q, int dtype, int on_device);
+
+/* Sec. 3: set the mixing operator (copied). */
+int qvs_set_mixer(qvs_t h, int kind, const qvs_mixer_desc* desc);
+
+/* Sec. 2.1 / Sec. 5: set |psi0> (dim complex values, interleaved re/im, in the handle's
+ * precision). psi0 = NULL restores the default equal superposition 1/sqrt(dim). */
+int qvs_set_initial_state(qvs_t h, const void* psi0, int on_device);
+
+/* Set an option (QVS_OPT_*). */
+int qvs_set_option(qvs_t h, int option, int64_t value);
+
+/* Sec. 2.1: evolve |psi0> through p layers; the final state stays on the device and its
+ * objective is available from qvs_expectation. gammas, ts: host arrays of length p. */
+int qvs_evolve(qvs_t h, int p, const double* gammas, const double* ts);
+
+/* Sec. 2.1: f = <theta|Q|theta> of the last qvs_evolve (fp64 reduction). */
+int qvs_expectation(qvs_t h, double* E);
+
+/* Sec. 2.1 / Sec. 4: objective and its gradient in one forward sweep and one adjoint sweep.
+ * Writes E, dgamma[p], dt[p] (host arrays). Afterwards the handle's state is undefined
+ * (qvs_get_state needs a fresh qvs_evolve). */
+int qvs_gradient(qvs_t h, int p, const double* gammas, const double* ts,
+                 double* E, double* dgamma, double* dt);
+
+/* Copy the current state (dim interleaved complex values in the handle's precision) to dst. */
+int qvs_get_state(qvs_t h, void* dst, int on_device);
+
+/* Number of kernels the last qvs_evolve / qvs_gradient launched. */
+int qvs_last_launch_count(qvs_t h, int64_t* count);
+
+/* Per-kernel statistics gathered while QVS_OPT_PROFILE is on: for slot = 0, 1, ... returns the
+ * kernel's name (NUL-terminated, truncated to name_len), its launch count, the summed
+ * event-timed duration in milliseconds, and the summed algorithmic bytes it must move (compulsory
+ * reads + writes of state, adjoint vector, quality and tables). QVS_EINVAL past the last slot. */
+int qvs_kernel_stats(qvs_t h, int slot, char* name, int name_len, int64_t* launches, double* ms,
+                     double* bytes);
+
+/* ----------------------------------------------------------------- quality generators
+ * Write a quality vector into the device buffer q_out (caller-owned, dim entries of out_dtype)
+ * on the given stream, computed on the GPU.
+ *
+ * Sec. 6.1, max-cut: q_i = sum over edges e=(u,v) with x_u(i) == x_v(i) of w_e (w = NULL: 1),
+ *   dim = 2^n; edge endpoints are qubit indices (host arrays). The sum runs over the edges in
+ *   the given order in fp64 and is rounded once to out_dtype (QVS_I32 needs w == NULL).
+ */
+int qvs_quality_maxcut(int n, int n_edges, const int32_t* eu, const int32_t* ev, const double* w,
+                       int out_dtype, void* q_out, void* stream);
+
+/* QWOA subset sums: q_i = sum_b w_b x_b(i) over items b = 0..n-1 (qubit b selects item b),
+ * fp64 in item order, rounded once to out_dtype (F32 or F64). w: host array of n weights. */
+int qvs_quality_subset(int n, const double* w, int out_dtype, void* q_out, void* stream);
+
+/* Sec. 6.2, portfolio cost on a list of basis states (device array states[dim], n_qubits
+ * qubits, asset a = qubits (2a long, 2a+1 short)): q = omega sum_ij sigma_ij z_i z_j
+ * - (1-omega) sum_i r_i z_i, z_a = x_{2a} - x_{2a+1}; fp64, rounded once to out_dtype.
+ * returns[M], cov[M*M] (row-major): host arrays, M = n_qubits/2 <= 32. */
+int qvs_quality_portfolio(int n_qubits, int64_t dim, const int64_t* states, const double* returns,
+                          const double* cov, double omega, int out_dtype, void* q_out, void* stream);
+
+/* Sec. 2.4.1: the XY-ring mixer sum_{a} (X_a X_{a+1} + Y_a Y_{a+1}) (a+1 mod n) restricted to
+ * the n-qubit basis states of Hamming weight k, as CSR over those states in increasing integer
+ * order. Host arrays; pass NULL outputs to query the sizes (*dim_out, *nnz_out). Values are all 2
+ * (use implicit_value = 2). */
+int qvs_xy_ring_csr(int n, int k, int64_t* states, int64_t* rowptr, int32_t* colind,
+                    int64_t* dim_out, int64_t* nnz_out);
+
+const char* qvs_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QVS_H */

@@ -1,0 +1,397 @@
+"""Python binding of libqvs: a single-GPU (sm_103a) state-vector engine for quantum variational
+algorithms (QAOA, QWOA, QAOAz; Matwiejew & Wang, arXiv 2110.03963).
+
+The binding only marshals arguments: every step of the evolution, objective and gradient runs in
+the CUDA kernels of ``libqvs.so`` (built in-tree by ``_build.py``). PyTorch supplies device memory
+for inputs/outputs given as tensors and the CUDA stream. Loading fails loudly if the library is
+missing; there is no CPU fallback.
+
+Function names match the C ABI in ``include/qvs.h``.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from typing import Optional
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libqvs.so")
+
+QVS_OK, QVS_EINVAL, QVS_ENOMEM, QVS_ECUDA, QVS_ESTATE, QVS_ENUMERIC, QVS_ETIMEOUT, QVS_EUNSUPPORTED = \
+    0, -1, -2, -3, -4, -5, -6, -7
+QVS_C64, QVS_C128 = 1, 2
+QVS_I32, QVS_F32, QVS_F64 = 1, 2, 3
+QVS_MIX_HYPERCUBE, QVS_MIX_CIRCULANT, QVS_MIX_CSR = 1, 2, 3
+QVS_OPT_CKPT_LAYERS = 1
+QVS_OPT_PROFILE = 2
+
+EXPORTED = [
+    "qvs_create", "qvs_destroy", "qvs_set_quality", "qvs_set_mixer", "qvs_set_initial_state",
+    "qvs_set_option", "qvs_evolve", "qvs_expectation", "qvs_gradient", "qvs_get_state",
+    "qvs_last_launch_count", "qvs_kernel_stats", "qvs_quality_maxcut", "qvs_quality_subset", "qvs_quality_portfolio",
+    "qvs_xy_ring_csr", "qvs_strerror",
+]
+
+
+class QvsError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {strerror(status)} ({status})")
+
+
+class MixerDesc(ctypes.Structure):
+    _fields_ = [
+        ("n_qubits", ctypes.c_int),
+        ("n_offsets", ctypes.c_int),
+        ("offsets", ctypes.POINTER(ctypes.c_int64)),
+        ("offset_weights", ctypes.POINTER(ctypes.c_double)),
+        ("rowptr", ctypes.c_void_p),
+        ("colind", ctypes.c_void_p),
+        ("values", ctypes.c_void_p),
+        ("implicit_value", ctypes.c_float),
+        ("nnz", ctypes.c_int64),
+        ("csr_on_device", ctypes.c_int),
+        ("spec_lo", ctypes.c_double),
+        ("spec_hi", ctypes.c_double),
+        ("cheb_tol", ctypes.c_double),
+    ]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libqvs.so (raises if it is missing: build it with ``_build.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libqvs.so not built at {path}; run paper_2110_03963_gb300._build.build()")
+    lib = ctypes.CDLL(path)
+    P, I, I64, D, V = ctypes.POINTER, ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+    sig = {
+        "qvs_create": (I, [P(V), I64, I, V]),
+        "qvs_destroy": (I, [V]),
+        "qvs_set_quality": (I, [V, V, I, I]),
+        "qvs_set_mixer": (I, [V, I, P(MixerDesc)]),
+        "qvs_set_initial_state": (I, [V, V, I]),
+        "qvs_set_option": (I, [V, I, I64]),
+        "qvs_evolve": (I, [V, I, P(D), P(D)]),
+        "qvs_expectation": (I, [V, P(D)]),
+        "qvs_gradient": (I, [V, I, P(D), P(D), P(D), P(D), P(D)]),
+        "qvs_get_state": (I, [V, V, I]),
+        "qvs_last_launch_count": (I, [V, P(I64)]),
+        "qvs_kernel_stats": (I, [V, I, ctypes.c_char_p, I, P(I64), P(D), P(D)]),
+        "qvs_quality_maxcut": (I, [I, I, P(ctypes.c_int32), P(ctypes.c_int32), P(D), I, V, V]),
+        "qvs_quality_subset": (I, [I, P(D), I, V, V]),
+        "qvs_quality_portfolio": (I, [I, I64, V, P(D), P(D), D, I, V, V]),
+        "qvs_xy_ring_csr": (I, [I, I, V, V, V, P(I64), P(I64)]),
+        "qvs_strerror": (ctypes.c_char_p, [I]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def strerror(status: int) -> str:
+    return load().qvs_strerror(status).decode()
+
+
+def _check(status: int, what: str):
+    if status != QVS_OK:
+        raise QvsError(status, what)
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _ptr_of(x):
+    """(pointer, on_device) of a numpy array or a torch tensor."""
+    if isinstance(x, np.ndarray):
+        return ctypes.c_void_p(x.ctypes.data), 0
+    import torch
+    if isinstance(x, torch.Tensor):
+        return ctypes.c_void_p(x.data_ptr()), 1 if x.is_cuda else 0
+    raise TypeError(type(x))
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return ctypes.c_void_p(0)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+# ---------------------------------------------------------------- thin wrappers, same names
+
+
+def qvs_create(dim: int, precision: int = QVS_C64, stream=None) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(load().qvs_create(ctypes.byref(h), int(dim), int(precision), _stream_ptr(stream)), "qvs_create")
+    return h
+
+
+def qvs_destroy(h):
+    _check(load().qvs_destroy(h), "qvs_destroy")
+
+
+def qvs_set_quality(h, q, dtype: Optional[int] = None):
+    if dtype is None:
+        dt = str(q.dtype)
+        dtype = {"int32": QVS_I32, "float32": QVS_F32, "float64": QVS_F64,
+                 "torch.int32": QVS_I32, "torch.float32": QVS_F32, "torch.float64": QVS_F64}[dt]
+    p, dev = _ptr_of(q)
+    _check(load().qvs_set_quality(h, p, int(dtype), dev), "qvs_set_quality")
+
+
+def qvs_set_mixer(h, kind: int, desc: MixerDesc):
+    _check(load().qvs_set_mixer(h, int(kind), ctypes.byref(desc)), "qvs_set_mixer")
+
+
+def qvs_set_initial_state(h, psi0=None):
+    if psi0 is None:
+        _check(load().qvs_set_initial_state(h, None, 0), "qvs_set_initial_state")
+        return
+    p, dev = _ptr_of(psi0)
+    _check(load().qvs_set_initial_state(h, p, dev), "qvs_set_initial_state")
+
+
+def qvs_set_option(h, option: int, value: int):
+    _check(load().qvs_set_option(h, int(option), int(value)), "qvs_set_option")
+
+
+def qvs_evolve(h, gammas, ts):
+    g = np.ascontiguousarray(gammas, dtype=np.float64)
+    t = np.ascontiguousarray(ts, dtype=np.float64)
+    _check(load().qvs_evolve(h, len(g), _dptr(g), _dptr(t)), "qvs_evolve")
+
+
+def qvs_expectation(h) -> float:
+    e = ctypes.c_double()
+    _check(load().qvs_expectation(h, ctypes.byref(e)), "qvs_expectation")
+    return e.value
+
+
+def qvs_gradient(h, gammas, ts):
+    """Returns (E, dgamma[p], dt[p])."""
+    g = np.ascontiguousarray(gammas, dtype=np.float64)
+    t = np.ascontiguousarray(ts, dtype=np.float64)
+    p = len(g)
+    e = ctypes.c_double()
+    dg = np.zeros(p)
+    dt = np.zeros(p)
+    _check(load().qvs_gradient(h, p, _dptr(g), _dptr(t), ctypes.byref(e), _dptr(dg), _dptr(dt)),
+           "qvs_gradient")
+    return e.value, dg, dt
+
+
+def qvs_get_state(h, out):
+    p, dev = _ptr_of(out)
+    _check(load().qvs_get_state(h, p, dev), "qvs_get_state")
+    return out
+
+
+def qvs_last_launch_count(h) -> int:
+    c = ctypes.c_int64()
+    _check(load().qvs_last_launch_count(h, ctypes.byref(c)), "qvs_last_launch_count")
+    return c.value
+
+
+def qvs_kernel_stats(h):
+    """List of dicts {name, launches, ms, bytes} gathered while QVS_OPT_PROFILE is on."""
+    out = []
+    lib = load()
+    slot = 0
+    while True:
+        name = ctypes.create_string_buffer(128)
+        n = ctypes.c_int64()
+        ms = ctypes.c_double()
+        by = ctypes.c_double()
+        if lib.qvs_kernel_stats(h, slot, name, 128, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)) != QVS_OK:
+            break
+        out.append({"name": name.value.decode(), "launches": n.value, "ms": ms.value, "bytes": by.value})
+        slot += 1
+    return out
+
+
+def qvs_quality_maxcut(n: int, eu, ev, w, out, dtype: int, stream=None):
+    eu = np.ascontiguousarray(eu, dtype=np.int32)
+    ev = np.ascontiguousarray(ev, dtype=np.int32)
+    wp = None
+    if w is not None:
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        wp = _dptr(w)
+    p, dev = _ptr_of(out)
+    assert dev == 1, "quality output must be a device tensor"
+    _check(load().qvs_quality_maxcut(n, len(eu), eu.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                     ev.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), wp, int(dtype), p,
+                                     _stream_ptr(stream)), "qvs_quality_maxcut")
+    return out
+
+
+def qvs_quality_subset(n: int, w, out, dtype: int, stream=None):
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    p, dev = _ptr_of(out)
+    assert dev == 1
+    _check(load().qvs_quality_subset(n, _dptr(w), int(dtype), p, _stream_ptr(stream)), "qvs_quality_subset")
+    return out
+
+
+def qvs_quality_portfolio(n_qubits: int, states_dev, returns, cov, omega: float, out, dtype: int, stream=None):
+    r = np.ascontiguousarray(returns, dtype=np.float64)
+    c = np.ascontiguousarray(cov, dtype=np.float64)
+    sp, sdev = _ptr_of(states_dev)
+    op, odev = _ptr_of(out)
+    assert sdev == 1 and odev == 1
+    dim = int(states_dev.shape[0])
+    _check(load().qvs_quality_portfolio(n_qubits, dim, sp, _dptr(r), _dptr(c), float(omega), int(dtype), op,
+                                        _stream_ptr(stream)), "qvs_quality_portfolio")
+    return out
+
+
+def qvs_xy_ring_csr(n: int, k: int):
+    """Returns (states int64[dim], rowptr int64[dim+1], colind int32[nnz]) as numpy arrays."""
+    lib = load()
+    dim = ctypes.c_int64()
+    nnz = ctypes.c_int64()
+    _check(lib.qvs_xy_ring_csr(n, k, None, None, None, ctypes.byref(dim), ctypes.byref(nnz)), "qvs_xy_ring_csr")
+    states = np.zeros(dim.value, dtype=np.int64)
+    rowptr = np.zeros(dim.value + 1, dtype=np.int64)
+    colind = np.zeros(nnz.value, dtype=np.int32)
+    _check(lib.qvs_xy_ring_csr(n, k, ctypes.c_void_p(states.ctypes.data), ctypes.c_void_p(rowptr.ctypes.data),
+                               ctypes.c_void_p(colind.ctypes.data), ctypes.byref(dim), ctypes.byref(nnz)),
+           "qvs_xy_ring_csr")
+    return states, rowptr, colind
+
+
+def qvs_strerror(status: int) -> str:
+    return strerror(status)
+
+
+# ---------------------------------------------------------------- convenience layer
+
+
+def hypercube_desc(n: int) -> MixerDesc:
+    d = MixerDesc()
+    d.n_qubits = n
+    return d
+
+
+def circulant_desc(offsets, weights=None) -> MixerDesc:
+    d = MixerDesc()
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    d.n_offsets = len(off)
+    d._off = off   # keep alive
+    d.offsets = off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    if weights is not None:
+        w = np.ascontiguousarray(weights, dtype=np.float64)
+        d._w = w
+        d.offset_weights = w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    return d
+
+
+def csr_desc(rowptr, colind, values=None, implicit_value: float = 1.0, spec=(0.0, 0.0), tol: float = 0.0) -> MixerDesc:
+    d = MixerDesc()
+    rp, dev1 = _ptr_of(rowptr)
+    ci, dev2 = _ptr_of(colind)
+    assert dev1 == dev2
+    d._keep = (rowptr, colind, values)
+    d.rowptr = rp.value
+    d.colind = ci.value
+    if values is not None:
+        vp, _ = _ptr_of(values)
+        d.values = vp.value
+    d.implicit_value = implicit_value
+    d.nnz = int(colind.shape[0])
+    d.csr_on_device = dev1
+    d.spec_lo, d.spec_hi = spec
+    d.cheb_tol = tol
+    return d
+
+
+class Simulator:
+    """Owns one qvs handle: quality vector + mixer + optional initial state."""
+
+    def __init__(self, dim: int, precision: int = QVS_C64, stream=None):
+        self.dim = int(dim)
+        self.precision = precision
+        self.h = qvs_create(dim, precision, stream)
+
+    def close(self):
+        if self.h is not None:
+            qvs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_quality(self, q, dtype=None):
+        qvs_set_quality(self.h, q, dtype)
+        return self
+
+    def set_mixer(self, kind: int, desc: MixerDesc):
+        qvs_set_mixer(self.h, kind, desc)
+        return self
+
+    def set_initial_state(self, psi0=None):
+        qvs_set_initial_state(self.h, psi0)
+        return self
+
+    def set_option(self, option, value):
+        qvs_set_option(self.h, option, value)
+        return self
+
+    def evolve(self, gammas, ts) -> float:
+        qvs_evolve(self.h, gammas, ts)
+        return qvs_expectation(self.h)
+
+    def gradient(self, gammas, ts):
+        return qvs_gradient(self.h, gammas, ts)
+
+    def state(self) -> np.ndarray:
+        out = np.zeros(self.dim, dtype=np.complex64 if self.precision == QVS_C64 else np.complex128)
+        qvs_get_state(self.h, out)
+        return out
+
+    def launches(self) -> int:
+        return qvs_last_launch_count(self.h)
+
+
+class QAOAObjective:
+    """torch.autograd.Function-style objective: E(gammas, ts) with the adjoint gradient."""
+
+    @staticmethod
+    def function(sim: Simulator):
+        import torch
+
+        class _Evolve(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, gammas, ts):
+                E, dg, dt = sim.gradient(gammas.detach().cpu().double().numpy(),
+                                         ts.detach().cpu().double().numpy())
+                ctx.save_for_backward(torch.from_numpy(dg), torch.from_numpy(dt))
+                return torch.tensor(E, dtype=torch.float64)
+
+            @staticmethod
+            def backward(ctx, grad_out):
+                dg, dt = ctx.saved_tensors
+                return grad_out * dg, grad_out * dt
+
+        return _Evolve.apply

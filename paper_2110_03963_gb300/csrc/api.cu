@@ -1,0 +1,337 @@
+// C ABI of libqvs: handle life cycle, argument checks and dispatch to the mixer paths.
+// The call sequence mirrors the paper's Ansatz workflow (Sec. 5, Table of Ansatz methods):
+// set the quality vector (observables), the unitaries (mixer), optionally the initial state,
+// then evolve / evaluate the objective / its gradient.
+#include <math.h>
+#include <string.h>
+
+#include <new>
+
+#include "qvs_internal.h"
+
+namespace qvs {
+
+int ensure_host_res(qvs_ctx* h, int p) {
+  if (h->host_res && h->host_res_cap >= p) return QVS_OK;
+  if (h->host_res) cudaFreeHost(h->host_res);
+  h->host_res = nullptr;
+  h->host_res_cap = 0;
+  const int cap = p < 64 ? 64 : p;
+  QVS_CUDA_TRY(cudaMallocHost((void**)&h->host_res, sizeof(double) * (1 + 2 * (size_t)cap)));
+  h->host_res_cap = cap;
+  return QVS_OK;
+}
+
+static cudaEvent_t pool_get(qvs_ctx* h) {
+  if (!h->evpool.empty()) {
+    cudaEvent_t e = h->evpool.back();
+    h->evpool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+int prof_begin(qvs_ctx* h, cudaEvent_t* start) {
+  *start = nullptr;
+  if (!h->profile) return QVS_OK;
+  *start = pool_get(h);
+  if (!*start) return QVS_ECUDA;
+  QVS_CUDA_TRY(cudaEventRecord(*start, h->stream));
+  return QVS_OK;
+}
+
+int prof_end(qvs_ctx* h, const char* name, double bytes, cudaEvent_t start) {
+  if (!h->profile || !start) return QVS_OK;
+  cudaEvent_t end = pool_get(h);
+  if (!end) return QVS_ECUDA;
+  QVS_CUDA_TRY(cudaEventRecord(end, h->stream));
+  int id = -1;
+  for (size_t i = 0; i < h->kstats.size(); ++i)
+    if (h->kstats[i].name == name) id = (int)i;
+  if (id < 0) {
+    h->kstats.push_back(qvs_ctx::KStat{});
+    h->kstats.back().name = name;
+    id = (int)h->kstats.size() - 1;
+  }
+  h->pending.push_back(qvs_ctx::Pending{id, bytes, start, end});
+  return QVS_OK;
+}
+
+int prof_flush(qvs_ctx* h) {
+  for (auto& p : h->pending) {
+    float ms = 0.f;
+    QVS_CUDA_TRY(cudaEventSynchronize(p.b));
+    QVS_CUDA_TRY(cudaEventElapsedTime(&ms, p.a, p.b));
+    auto& k = h->kstats[p.id];
+    k.launches += 1;
+    k.ms += ms;
+    k.bytes += p.bytes;
+    h->evpool.push_back(p.a);
+    h->evpool.push_back(p.b);
+  }
+  h->pending.clear();
+  return QVS_OK;
+}
+
+void prof_release(qvs_ctx* h) {
+  for (auto& p : h->pending) {
+    h->evpool.push_back(p.a);
+    h->evpool.push_back(p.b);
+  }
+  h->pending.clear();
+  for (auto e : h->evpool) cudaEventDestroy(e);
+  h->evpool.clear();
+}
+
+static int log2_exact(int64_t d) {
+  if (d < 1 || (d & (d - 1))) return -1;
+  int n = 0;
+  while ((int64_t(1) << n) < d) ++n;
+  return n;
+}
+
+static bool params_ok(int p, const double* g, const double* t) {
+  if (p < 1 || p > 4096 || !g || !t) return false;
+  for (int k = 0; k < p; ++k)
+    if (!isfinite(g[k]) || !isfinite(t[k])) return false;
+  return true;
+}
+
+}  // namespace qvs
+
+using namespace qvs;
+
+extern "C" int qvs_create(qvs_t* out, int64_t dim, int precision, void* stream) {
+  if (!out) return QVS_EINVAL;
+  *out = nullptr;
+  if (dim < 2 || dim > (int64_t(1) << 34)) return QVS_EINVAL;
+  if (precision != QVS_C64 && precision != QVS_C128) return QVS_EINVAL;
+  qvs_ctx* h = new (std::nothrow) qvs_ctx();
+  if (!h) return QVS_ENOMEM;
+  h->dim = dim;
+  h->n = log2_exact(dim);
+  h->precision = precision;
+  h->stream = (cudaStream_t)stream;
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    (void)cudaGetLastError();
+    delete h;
+    return QVS_ECUDA;
+  }
+  *out = h;
+  return QVS_OK;
+}
+
+extern "C" int qvs_destroy(qvs_t h) {
+  if (!h) return QVS_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  h->q.release();
+  h->psi0.release();
+  h->psi.release();
+  h->lam.release();
+  h->ckpt.release();
+  h->part.release();
+  h->res.release();
+  h->rowmap.release();
+  h->work.release();
+  h->circ.lam.release();
+  h->csr.rowptr.release();
+  h->csr.colind.release();
+  h->csr.values.release();
+  if (h->host_res) cudaFreeHost(h->host_res);
+  prof_release(h);
+  delete h;
+  (void)cudaGetLastError();
+  return QVS_OK;
+}
+
+template <class Dst, class Src>
+__global__ void convert_kernel(Dst* __restrict__ d, const Src* __restrict__ s, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    d[i] = (Dst)s[i];
+}
+
+template <class Dst, class Src>
+static int convert_on_device(qvs_ctx* h, Dst* d, const Src* s, int64_t n) {
+  int64_t g = (n + 255) / 256;
+  if (g > 152 * 16) g = 152 * 16;
+  convert_kernel<Dst, Src><<<(int)g, 256, 0, h->stream>>>(d, s, n);
+  QVS_CUDA_TRY(cudaGetLastError());
+  return QVS_OK;
+}
+
+extern "C" int qvs_set_quality(qvs_t h, const void* q, int dtype, int on_device) {
+  if (!h || !q) return QVS_EINVAL;
+  if (dtype != QVS_I32 && dtype != QVS_F32 && dtype != QVS_F64) return QVS_EINVAL;
+  const int64_t n = h->dim;
+  const size_t in_elem = dtype == QVS_F64 ? 8 : 4;
+  const bool want_f32 = h->precision == QVS_C64;
+  const size_t out_elem = want_f32 ? 4 : 8;
+  QVS_TRY(h->q.ensure(out_elem * (size_t)n));
+  h->have_q = false;
+  const bool same = (want_f32 && dtype == QVS_F32) || (!want_f32 && dtype == QVS_F64);
+  if (same) {
+    QVS_CUDA_TRY(cudaMemcpyAsync(h->q.ptr, q, out_elem * n,
+                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                 h->stream));
+  } else {
+    // stage the raw input on the device, then convert there
+    const void* src = q;
+    if (!on_device) {
+      QVS_TRY(h->work.ensure(in_elem * (size_t)n));
+      QVS_CUDA_TRY(cudaMemcpyAsync(h->work.ptr, q, in_elem * n, cudaMemcpyHostToDevice, h->stream));
+      src = h->work.ptr;
+    }
+    if (want_f32) {
+      if (dtype == QVS_I32) QVS_TRY(convert_on_device(h, h->q.as<float>(), (const int32_t*)src, n));
+      else QVS_TRY(convert_on_device(h, h->q.as<float>(), (const double*)src, n));
+    } else {
+      if (dtype == QVS_I32) QVS_TRY(convert_on_device(h, h->q.as<double>(), (const int32_t*)src, n));
+      else QVS_TRY(convert_on_device(h, h->q.as<double>(), (const float*)src, n));
+    }
+  }
+  h->have_q = true;
+  h->have_E = false;
+  return QVS_OK;
+}
+
+extern "C" int qvs_set_mixer(qvs_t h, int kind, const qvs_mixer_desc* d) {
+  if (!h || !d) return QVS_EINVAL;
+  h->have_mixer = false;
+  h->have_E = false;
+  if (kind == QVS_MIX_HYPERCUBE) {
+    if (d->n_qubits < 1 || h->n != d->n_qubits) return QVS_EINVAL;
+    if (h->n > 32) return QVS_EUNSUPPORTED;
+  } else if (kind == QVS_MIX_CIRCULANT) {
+    if (h->n < 1) return QVS_EINVAL;
+    QVS_TRY(circ_set_mixer(h, d));
+  } else if (kind == QVS_MIX_CSR) {
+    QVS_TRY(csr_set_mixer(h, d));
+  } else {
+    return QVS_EINVAL;
+  }
+  h->mixer = kind;
+  h->have_mixer = true;
+  return QVS_OK;
+}
+
+extern "C" int qvs_set_initial_state(qvs_t h, const void* psi0, int on_device) {
+  if (!h) return QVS_EINVAL;
+  h->have_E = false;
+  if (!psi0) {
+    h->have_psi0 = false;
+    return QVS_OK;
+  }
+  const size_t bytes = elem_bytes(h) * (size_t)h->dim;
+  QVS_TRY(h->psi0.ensure(bytes));
+  QVS_CUDA_TRY(cudaMemcpyAsync(h->psi0.ptr, psi0, bytes,
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                               h->stream));
+  h->have_psi0 = true;
+  return QVS_OK;
+}
+
+extern "C" int qvs_set_option(qvs_t h, int option, int64_t value) {
+  if (!h) return QVS_EINVAL;
+  if (option == QVS_OPT_CKPT_LAYERS) {
+    if (value < 0 || value > 4096) return QVS_EINVAL;
+    h->ckpt_layers = (int)value;
+    return QVS_OK;
+  }
+  if (option == QVS_OPT_PROFILE) {
+    if (value != 0 && value != 1) return QVS_EINVAL;
+    h->profile = value == 1;
+    h->kstats.clear();
+    return QVS_OK;
+  }
+  return QVS_EINVAL;
+}
+
+static int ready(qvs_t h) {
+  if (!h) return QVS_EINVAL;
+  if (!h->have_q || !h->have_mixer) return QVS_ESTATE;
+  return QVS_OK;
+}
+
+extern "C" int qvs_evolve(qvs_t h, int p, const double* gammas, const double* ts) {
+  QVS_TRY(ready(h));
+  if (!params_ok(p, gammas, ts)) return QVS_EINVAL;
+  h->have_E = false;
+  switch (h->mixer) {
+    case QVS_MIX_HYPERCUBE: return hc_evolve(h, p, gammas, ts);
+    case QVS_MIX_CIRCULANT: return circ_evolve(h, p, gammas, ts);
+    case QVS_MIX_CSR: return csr_evolve(h, p, gammas, ts);
+  }
+  return QVS_ESTATE;
+}
+
+extern "C" int qvs_expectation(qvs_t h, double* E) {
+  if (!h || !E) return QVS_EINVAL;
+  if (!h->have_E) return QVS_ESTATE;
+  *E = h->E;
+  return QVS_OK;
+}
+
+extern "C" int qvs_gradient(qvs_t h, int p, const double* gammas, const double* ts, double* E,
+                            double* dgamma, double* dt) {
+  QVS_TRY(ready(h));
+  if (!params_ok(p, gammas, ts) || !E || !dgamma || !dt) return QVS_EINVAL;
+  h->have_E = false;
+  switch (h->mixer) {
+    case QVS_MIX_HYPERCUBE: return hc_gradient(h, p, gammas, ts, E, dgamma, dt);
+    case QVS_MIX_CIRCULANT: return circ_gradient(h, p, gammas, ts, E, dgamma, dt);
+    case QVS_MIX_CSR: return csr_gradient(h, p, gammas, ts, E, dgamma, dt);
+  }
+  return QVS_ESTATE;
+}
+
+extern "C" int qvs_get_state(qvs_t h, void* dst, int on_device) {
+  if (!h || !dst) return QVS_EINVAL;
+  if (!h->have_E || !h->psi.ptr) return QVS_ESTATE;
+  const size_t bytes = elem_bytes(h) * (size_t)h->dim;
+  QVS_CUDA_TRY(cudaMemcpyAsync(dst, h->psi.ptr, bytes,
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                               h->stream));
+  QVS_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return QVS_OK;
+}
+
+extern "C" int qvs_last_launch_count(qvs_t h, int64_t* count) {
+  if (!h || !count) return QVS_EINVAL;
+  *count = h->launches;
+  return QVS_OK;
+}
+
+extern "C" int qvs_kernel_stats(qvs_t h, int slot, char* name, int name_len, int64_t* launches,
+                                double* ms, double* bytes) {
+  if (!h || slot < 0 || slot >= (int)h->kstats.size()) return QVS_EINVAL;
+  const auto& k = h->kstats[slot];
+  if (name && name_len > 0) {
+    strncpy(name, k.name.c_str(), (size_t)name_len - 1);
+    name[name_len - 1] = 0;
+  }
+  if (launches) *launches = k.launches;
+  if (ms) *ms = k.ms;
+  if (bytes) *bytes = k.bytes;
+  return QVS_OK;
+}
+
+extern "C" const char* qvs_strerror(int s) {
+  switch (s) {
+    case QVS_OK: return "ok";
+    case QVS_EINVAL: return "invalid argument";
+    case QVS_ENOMEM: return "device allocation failed";
+    case QVS_ECUDA: return "CUDA error";
+    case QVS_ESTATE: return "call out of order (quality, mixer or evolve missing)";
+    case QVS_ENUMERIC: return "numerical check failed";
+    case QVS_ETIMEOUT: return "device wait timed out";
+    case QVS_EUNSUPPORTED: return "unsupported configuration";
+  }
+  return "unknown status";
+}

@@ -1,0 +1,715 @@
+// QAOA hypercube-mixer path (Sec. 2.3.1): forward evolution, objective and adjoint gradient.
+//
+// Schedule. The n index bits are split into g groups (g = 2 for n <= 20, g = 3 up to n = 32):
+// group A = bits 0..11 (contiguous tile), groups B and C = higher bits, each tile padded with
+// low "chunk" bits so every tile row is >= 128 contiguous bytes (s >= 4 for the default sizes).
+// Because the rotations of different bits commute, one pass over a tile can finish the mixer of
+// layer k on its group, apply the phase of layer k+1, and start the mixer of layer k+1 on the same
+// group. With g groups a layer therefore costs g-1 passes instead of g: p+1 passes in total for
+// g = 2 and 2p+1 for g = 3, each one read and one write of the state (plus q where a phase is
+// applied). The last forward pass is fused with the first adjoint pass.
+//
+// Adjoint (gradient of f = <psi|Q|psi>, Sec. 2.1): with lambda = Q psi at the end, the reverse
+// sweep undoes each pass on psi and lambda together and accumulates
+//   df/dt_k     = 2 Im <lambda|X_b psi> summed over the bits b of layer k's mixer,
+//   df/dgamma_k = 2 Im <lambda|Q phi_k> at the point just before phase k is undone.
+// psi is either re-read from a stored checkpoint of the forward sweep or uncomputed by the
+// inverse pass; checkpoints are kept every ckpt_layers layers (default ceil(sqrt(p))).
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "hc_kernels.cuh"
+#include "qvs_internal.h"
+
+namespace qvs {
+namespace hc {
+
+enum Shape : int {
+  F0 = 0,   // first pass: psi0 (generated or loaded), phase, rotations ("after")
+  F1 = 1,   // rotations (before), phase, rotations (after)
+  F2 = 2,   // rotations only
+  FE = 3,   // last forward pass fused with its adjoint: rotations, E and lambda = Q psi, undo
+  FV = 4,   // last forward pass for qvs_evolve: rotations, E, store psi
+  R1 = 5,   // adjoint of F1
+  R2 = 6,   // adjoint of F2
+  R0 = 7    // adjoint of F0 (gradient contributions only)
+};
+
+template <class T>
+struct PassArgs {
+  Tile tile;
+  const typename Cx<T>::t* psi_in;
+  typename Cx<T>::t* psi_out;
+  const typename Cx<T>::t* lam_in;
+  typename Cx<T>::t* lam_out;
+  const T* q;
+  uint32_t mask_bef, mask_aft;
+  T cb, sb, ca, sa;     // cos / sin of the "before" and "after" mixer angles
+  T ph0, ph1;           // phase: complex64: gamma/2pi as hi, lo; complex128: gamma, 0
+  double* part;         // partial-sum rows: part[row * gridDim.x + blockIdx.x]
+  int row_bef, row_aft, row_gam, row_E;
+  T init_amp;           // amplitude of the uniform initial state
+  int gen_init;         // F0: 1 = generate psi0 = init_amp, 0 = load psi_in
+};
+
+// Block sum of up to three values, written to their partial rows (rows < 0 skipped).
+__device__ __forceinline__ void block_store3(double a, double b, double c, double* part, int ra,
+                                             int rb, int rc, int tid) {
+  __shared__ double red[3][NT / 32];
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+  }
+  if ((tid & 31) == 0) {
+    red[0][tid >> 5] = a;
+    red[1][tid >> 5] = b;
+    red[2][tid >> 5] = c;
+  }
+  __syncthreads();
+  if (tid < 3) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < NT / 32; ++w) s += red[tid][w];
+    const int row = tid == 0 ? ra : (tid == 1 ? rb : rc);
+    if (row >= 0) part[(size_t)row * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+template <class T, int SHAPE>
+__global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassArgs<T> a) {
+  using C = typename Cx<T>::t;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* sm = reinterpret_cast<C*>(smem_raw);
+  const int tid = threadIdx.x;
+  const uint32_t base = tile_base(a.tile, blockIdx.x);
+  const uint32_t off0 = base + scatter(a.tile, tj<0>(0, tid));
+  const uint32_t off2 = base + scatter(a.tile, tj<2>(0, tid));
+  uint32_t ro0[R], ro2[R];
+  reg_offsets<0>(a.tile, ro0);
+  reg_offsets<2>(a.tile, ro2);
+
+  constexpr bool NEEDS_Q = SHAPE == F0 || SHAPE == F1 || SHAPE == FE || SHAPE == FV ||
+                           SHAPE == R1 || SHAPE == R0;
+  T qv[R];
+  if constexpr (NEEDS_Q) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) qv[r] = __ldcs(a.q + off2 + ro2[r]);
+  }
+
+  C v[R];
+  if constexpr (SHAPE == F0) {
+    if (a.gen_init) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) { v[r].x = a.init_amp; v[r].y = T(0); }
+    } else {
+      gload<2>(v, a.psi_in, off2, ro2);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      T c, s;
+      phase_cs(qv[r], a.ph0, a.ph1, c, s);
+      v[r] = cmul_conj(v[r], c, s);
+    }
+    rot_layout<2>(v, a.mask_aft, a.ca, a.sa);
+    xchg<2, 1>(v, sm, tid);
+    rot_layout<1>(v, a.mask_aft, a.ca, a.sa);
+    xchg<1, 0>(v, sm, tid);
+    rot_layout<0>(v, a.mask_aft, a.ca, a.sa);
+    gstore<0>(v, a.psi_out, off0, ro0);
+  } else if constexpr (SHAPE == F1) {
+    gload<0>(v, a.psi_in, off0, ro0);
+    rot_layout<0>(v, a.mask_bef, a.cb, a.sb);
+    xchg<0, 1>(v, sm, tid);
+    rot_layout<1>(v, a.mask_bef, a.cb, a.sb);
+    xchg<1, 2>(v, sm, tid);
+    rot_layout<2>(v, a.mask_bef, a.cb, a.sb);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      T c, s;
+      phase_cs(qv[r], a.ph0, a.ph1, c, s);
+      v[r] = cmul_conj(v[r], c, s);
+    }
+    rot_layout<2>(v, a.mask_aft, a.ca, a.sa);
+    xchg<2, 1>(v, sm, tid);
+    rot_layout<1>(v, a.mask_aft, a.ca, a.sa);
+    xchg<1, 0>(v, sm, tid);
+    rot_layout<0>(v, a.mask_aft, a.ca, a.sa);
+    gstore<0>(v, a.psi_out, off0, ro0);
+  } else if constexpr (SHAPE == F2) {
+    gload<0>(v, a.psi_in, off0, ro0);
+    rot_layout<0>(v, a.mask_bef, a.cb, a.sb);
+    xchg<0, 1>(v, sm, tid);
+    rot_layout<1>(v, a.mask_bef, a.cb, a.sb);
+    xchg<1, 2>(v, sm, tid);
+    rot_layout<2>(v, a.mask_bef, a.cb, a.sb);
+    gstore<2>(v, a.psi_out, off2, ro2);
+  } else if constexpr (SHAPE == FE || SHAPE == FV) {
+    gload<0>(v, a.psi_in, off0, ro0);
+    rot_layout<0>(v, a.mask_bef, a.cb, a.sb);
+    xchg<0, 1>(v, sm, tid);
+    rot_layout<1>(v, a.mask_bef, a.cb, a.sb);
+    xchg<1, 2>(v, sm, tid);
+    rot_layout<2>(v, a.mask_bef, a.cb, a.sb);
+    T e = T(0);
+#pragma unroll
+    for (int r = 0; r < R; ++r) e += qv[r] * (v[r].x * v[r].x + v[r].y * v[r].y);
+    if constexpr (SHAPE == FV) {
+      gstore<2>(v, a.psi_out, off2, ro2);
+      block_store3((double)e, 0.0, 0.0, a.part, a.row_E, -1, -1, tid);
+    } else {
+      C l[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) { l[r].x = qv[r] * v[r].x; l[r].y = qv[r] * v[r].y; }
+      T acc = T(0);
+      unrot_layout_acc<2>(v, l, a.mask_bef, a.cb, a.sb, acc);
+      xchg2<2, 1>(v, l, sm, tid);
+      unrot_layout_acc<1>(v, l, a.mask_bef, a.cb, a.sb, acc);
+      xchg2<1, 0>(v, l, sm, tid);
+      unrot_layout_acc<0>(v, l, a.mask_bef, a.cb, a.sb, acc);
+      gstore<0>(l, a.lam_out, off0, ro0);
+      block_store3((double)e, 2.0 * (double)acc, 0.0, a.part, a.row_E, a.row_bef, -1, tid);
+    }
+  } else if constexpr (SHAPE == R1 || SHAPE == R0) {
+    C l[R];
+    gload<0>(v, a.psi_in, off0, ro0);
+    gload<0>(l, a.lam_in, off0, ro0);
+    T acc_a = T(0), acc_b = T(0), acc_g = T(0);
+    unrot_layout_acc<0>(v, l, a.mask_aft, a.ca, a.sa, acc_a);
+    xchg2<0, 1>(v, l, sm, tid);
+    unrot_layout_acc<1>(v, l, a.mask_aft, a.ca, a.sa, acc_a);
+    xchg2<1, 2>(v, l, sm, tid);
+    unrot_layout_acc<2>(v, l, a.mask_aft, a.ca, a.sa, acc_a);
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc_g += qv[r] * imdot(l[r], v[r]);
+    if constexpr (SHAPE == R1) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        T c, s;
+        phase_cs(qv[r], a.ph0, a.ph1, c, s);
+        v[r] = cmul_conj(v[r], c, -s);
+        l[r] = cmul_conj(l[r], c, -s);
+      }
+      unrot_layout_acc<2>(v, l, a.mask_bef, a.cb, a.sb, acc_b);
+      xchg2<2, 1>(v, l, sm, tid);
+      unrot_layout_acc<1>(v, l, a.mask_bef, a.cb, a.sb, acc_b);
+      xchg2<1, 0>(v, l, sm, tid);
+      unrot_layout_acc<0>(v, l, a.mask_bef, a.cb, a.sb, acc_b);
+      gstore<0>(l, a.lam_out, off0, ro0);
+      if (a.psi_out) gstore<0>(v, a.psi_out, off0, ro0);
+    }
+    block_store3(2.0 * (double)acc_b, 2.0 * (double)acc_a, 2.0 * (double)acc_g, a.part, a.row_bef,
+                 a.row_aft, a.row_gam, tid);
+  } else if constexpr (SHAPE == R2) {
+    C l[R];
+    gload<2>(v, a.psi_in, off2, ro2);
+    gload<2>(l, a.lam_in, off2, ro2);
+    T acc_b = T(0);
+    unrot_layout_acc<2>(v, l, a.mask_bef, a.cb, a.sb, acc_b);
+    xchg2<2, 1>(v, l, sm, tid);
+    unrot_layout_acc<1>(v, l, a.mask_bef, a.cb, a.sb, acc_b);
+    xchg2<1, 0>(v, l, sm, tid);
+    unrot_layout_acc<0>(v, l, a.mask_bef, a.cb, a.sb, acc_b);
+    gstore<0>(l, a.lam_out, off0, ro0);
+    if (a.psi_out) gstore<0>(v, a.psi_out, off0, ro0);
+    block_store3(2.0 * (double)acc_b, 0.0, 0.0, a.part, a.row_bef, -1, -1, tid);
+  }
+}
+
+// ---------------------------------------------------------------- small states (n <= TB)
+//
+// One CTA holds the whole state in shared memory and runs every layer, the objective and the
+// adjoint sweep; the forward states psi_k are kept in global scratch for the adjoint.
+
+template <class T>
+struct SmallArgs {
+  int n, p;
+  const T* q;
+  const typename Cx<T>::t* psi0;    // NULL = uniform
+  typename Cx<T>::t* states;        // [p][dim] forward states psi_k (gradient) or NULL
+  typename Cx<T>::t* psi_out;       // final state (evolve) or NULL
+  const double* ang;                // [4p]: cos t_k, sin t_k, gamma_k, (unused)
+  double* res;                      // [1 + 2p]: E, dgamma, dt
+  int grad;
+};
+
+__device__ __forceinline__ double block_sum_all(double v, double* red) {
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((tid & 31) == 0) red[tid >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+  return s;
+}
+
+template <class T>
+__device__ void small_rotate(typename Cx<T>::t* s, int n, T c, T sn) {
+  const int dim = 1 << n;
+  for (int b = 0; b < n; ++b) {
+    const int h = 1 << b;
+    for (int k = threadIdx.x; k < dim / 2; k += blockDim.x) {
+      const int i = ((k >> b) << (b + 1)) | (k & (h - 1));
+      rot(s[i], s[i | h], c, sn);
+    }
+    __syncthreads();
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) small_kernel(const __grid_constant__ SmallArgs<T> a) {
+  using C = typename Cx<T>::t;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[8];
+  const int dim = 1 << a.n;
+  C* ps = reinterpret_cast<C*>(smem_raw);
+  C* ls = ps + dim;
+  const T amp = (T)rsqrt((double)dim);
+  for (int i = threadIdx.x; i < dim; i += blockDim.x) {
+    if (a.psi0) ps[i] = a.psi0[i];
+    else { ps[i].x = amp; ps[i].y = T(0); }
+  }
+  __syncthreads();
+  for (int k = 0; k < a.p; ++k) {
+    const double g = a.ang[4 * k + 2];
+    for (int i = threadIdx.x; i < dim; i += blockDim.x) {
+      double sd, cd;
+      sincos(g * (double)a.q[i], &sd, &cd);
+      ps[i] = cmul_conj(ps[i], (T)cd, (T)sd);
+    }
+    __syncthreads();
+    small_rotate<T>(ps, a.n, (T)a.ang[4 * k], (T)a.ang[4 * k + 1]);
+    if (a.grad)
+      for (int i = threadIdx.x; i < dim; i += blockDim.x) a.states[(size_t)k * dim + i] = ps[i];
+  }
+  double e = 0.0;
+  for (int i = threadIdx.x; i < dim; i += blockDim.x)
+    e += (double)a.q[i] * ((double)ps[i].x * ps[i].x + (double)ps[i].y * ps[i].y);
+  e = block_sum_all(e, red);
+  if (threadIdx.x == 0) a.res[0] = e;
+  if (!a.grad) {
+    for (int i = threadIdx.x; i < dim; i += blockDim.x) a.psi_out[i] = ps[i];
+    return;
+  }
+  for (int i = threadIdx.x; i < dim; i += blockDim.x) {
+    ls[i].x = a.q[i] * ps[i].x;
+    ls[i].y = a.q[i] * ps[i].y;
+  }
+  __syncthreads();
+  for (int k = a.p - 1; k >= 0; --k) {
+    // psi_k from the forward sweep
+    for (int i = threadIdx.x; i < dim; i += blockDim.x) ps[i] = a.states[(size_t)k * dim + i];
+    __syncthreads();
+    // dt_k = 2 Im <lam | W psi>, W = sum_b X_b
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < dim; i += blockDim.x) {
+      C w;
+      w.x = T(0);
+      w.y = T(0);
+      for (int b = 0; b < a.n; ++b) {
+        w.x += ps[i ^ (1 << b)].x;
+        w.y += ps[i ^ (1 << b)].y;
+      }
+      acc += (double)imdot(ls[i], w);
+    }
+    acc = block_sum_all(acc, red);
+    if (threadIdx.x == 0) a.res[1 + a.p + k] = 2.0 * acc;
+    const T c = (T)a.ang[4 * k], s = (T)a.ang[4 * k + 1];
+    small_rotate<T>(ps, a.n, c, -s);
+    small_rotate<T>(ls, a.n, c, -s);
+    double ag = 0.0;
+    for (int i = threadIdx.x; i < dim; i += blockDim.x) ag += (double)a.q[i] * (double)imdot(ls[i], ps[i]);
+    ag = block_sum_all(ag, red);
+    if (threadIdx.x == 0) a.res[1 + k] = 2.0 * ag;
+    const double g = a.ang[4 * k + 2];
+    for (int i = threadIdx.x; i < dim; i += blockDim.x) {
+      double sd, cd;
+      sincos(g * (double)a.q[i], &sd, &cd);
+      ls[i] = cmul_conj(ls[i], (T)cd, -(T)sd);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- host-side plan
+
+struct PassInfo {
+  int type, shape;
+  int lb, la, lg;   // layer of the before rotations, after rotations, phase (-1 = none)
+};
+
+struct Plan {
+  int n = 0, g = 0, F = 0;
+  Tile tile[3];
+  uint32_t gmask[3];
+  std::vector<PassInfo> pass;   // index 1..F (0 unused)
+};
+
+static Tile make_tile(int n, int s, int hfirst, int nh) {
+  Tile t{};
+  for (int b = 0; b < s; ++b) t.bitoff[b] = 1u << b;
+  for (int i = 0; i < nh; ++i) t.bitoff[s + i] = 1u << (hfirst + i);
+  int k = 0;
+  for (int b = 0; b < n; ++b) {
+    const bool in_tile = (b < s) || (b >= hfirst && b < hfirst + nh);
+    if (!in_tile) t.ntbit[k++] = (uint8_t)b;
+  }
+  t.n_nt = k;
+  return t;
+}
+
+static int make_plan(int n, int p, Plan& pl) {
+  pl = Plan{};
+  pl.n = n;
+  const int rest = n - TB;
+  if (rest <= 0) return QVS_EUNSUPPORTED;
+  pl.tile[0] = make_tile(n, TB, TB, 0);
+  pl.gmask[0] = (1u << TB) - 1;
+  if (rest <= TB - 4) {
+    pl.g = 2;
+    const int s = TB - rest;
+    pl.tile[1] = make_tile(n, s, TB, rest);
+    pl.gmask[1] = ((1u << TB) - 1) & ~((1u << s) - 1);
+  } else {
+    const int r1 = (rest + 1) / 2, r2 = rest - r1;
+    if (TB - r1 < 2) return QVS_EUNSUPPORTED;
+    pl.g = 3;
+    const int s1 = TB - r1, s2 = TB - r2;
+    pl.tile[1] = make_tile(n, s1, TB, r1);
+    pl.gmask[1] = ((1u << TB) - 1) & ~((1u << s1) - 1);
+    pl.tile[2] = make_tile(n, s2, TB + r1, r2);
+    pl.gmask[2] = ((1u << TB) - 1) & ~((1u << s2) - 1);
+  }
+  if (pl.g == 2) {
+    pl.F = p + 1;
+    pl.pass.assign(pl.F + 1, PassInfo{});
+    for (int j = 1; j <= pl.F; ++j) {
+      PassInfo& q = pl.pass[j];
+      q.type = (j - 1) % 2;
+      if (j == 1) q = {q.type, F0, -1, 0, 0};
+      else if (j <= p) q = {q.type, F1, j - 2, j - 1, j - 1};
+      else q = {q.type, FE, p - 1, -1, -1};
+    }
+  } else {
+    pl.F = 2 * p + 1;
+    pl.pass.assign(pl.F + 1, PassInfo{});
+    for (int j = 1; j <= pl.F; ++j) {
+      PassInfo& q = pl.pass[j];
+      q.type = (j - 1) % 3;
+      if (j == 1) q = {q.type, F0, -1, 0, 0};
+      else if (j == pl.F) q = {q.type, FE, p - 1, -1, -1};
+      else if (j % 2 == 0) q = {q.type, F2, (j - 2) / 2, -1, -1};
+      else q = {q.type, F1, (j - 3) / 2, (j - 1) / 2, (j - 1) / 2};
+    }
+  }
+  return QVS_OK;
+}
+
+template <class T>
+static void fill_angles(PassArgs<T>& a, const PassInfo& pi, const double* gammas, const double* ts) {
+  a.cb = a.sb = a.ca = a.sa = T(0);
+  if (pi.lb >= 0) { a.cb = (T)cos(ts[pi.lb]); a.sb = (T)sin(ts[pi.lb]); }
+  if (pi.la >= 0) { a.ca = (T)cos(ts[pi.la]); a.sa = (T)sin(ts[pi.la]); }
+  a.ph0 = a.ph1 = T(0);
+  if (pi.lg >= 0) {
+    if constexpr (sizeof(T) == 4) {
+      float hi, lo;
+      turns_split(gammas[pi.lg], &hi, &lo);
+      a.ph0 = hi;
+      a.ph1 = lo;
+    } else {
+      a.ph0 = gammas[pi.lg];
+    }
+  }
+}
+
+template <class T>
+static size_t smem_bytes(int shape) {
+  const bool two = shape == FE || shape == R1 || shape == R2 || shape == R0;
+  (void)two;
+  return (size_t)TILE * sizeof(typename Cx<T>::t);
+}
+
+template <class T, int S>
+static int launch_one(const PassArgs<T>& a, uint32_t grid, cudaStream_t st) {
+  const size_t sm = (size_t)TILE * sizeof(typename Cx<T>::t);
+  static bool configured = false;   // per instantiation
+  if (!configured) {
+    QVS_CUDA_TRY(cudaFuncSetAttribute(pass_kernel<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)sm));
+    configured = true;
+  }
+  pass_kernel<T, S><<<grid, NT, sm, st>>>(a);
+  QVS_CUDA_TRY(cudaGetLastError());
+  return QVS_OK;
+}
+
+static const char* shape_name(int shape, bool dbl) {
+  static const char* f[] = {"hc_pass_F0_c64", "hc_pass_F1_c64", "hc_pass_F2_c64", "hc_pass_FE_c64",
+                            "hc_pass_FV_c64", "hc_pass_R1_c64", "hc_pass_R2_c64", "hc_pass_R0_c64"};
+  static const char* d[] = {"hc_pass_F0_c128", "hc_pass_F1_c128", "hc_pass_F2_c128", "hc_pass_FE_c128",
+                            "hc_pass_FV_c128", "hc_pass_R1_c128", "hc_pass_R2_c128", "hc_pass_R0_c128"};
+  return dbl ? d[shape] : f[shape];
+}
+
+// compulsory bytes per amplitude of one pass (complex element size c, quality element size qb)
+static double shape_bytes(int shape, const void* psi_in, const void* psi_out, double c, double qb) {
+  switch (shape) {
+    case F0: return qb + c + (psi_in ? c : 0.0);
+    case F1: return 2 * c + qb;
+    case F2: return 2 * c;
+    case FE: return 2 * c + qb;
+    case FV: return 2 * c + qb;
+    case R1: return 3 * c + qb + (psi_out ? c : 0.0);
+    case R2: return 3 * c + (psi_out ? c : 0.0);
+    case R0: return 2 * c + qb;
+  }
+  return 0.0;
+}
+
+template <class T>
+static int launch_shape_raw(int shape, const PassArgs<T>& a, uint32_t grid, cudaStream_t st);
+
+template <class T>
+static int launch_shape(qvs_ctx* h, int shape, const PassArgs<T>& a, uint32_t grid) {
+  cudaEvent_t ev;
+  QVS_TRY(prof_begin(h, &ev));
+  QVS_TRY(launch_shape_raw<T>(shape, a, grid, h->stream));
+  const double c = sizeof(typename Cx<T>::t), qb = sizeof(T);
+  return prof_end(h, shape_name(shape, sizeof(T) == 8),
+                  shape_bytes(shape, a.psi_in, a.psi_out, c, qb) * (double)grid * TILE, ev);
+}
+
+template <class T>
+static int launch_shape_raw(int shape, const PassArgs<T>& a, uint32_t grid, cudaStream_t st) {
+  switch (shape) {
+    case F0: return launch_one<T, F0>(a, grid, st);
+    case F1: return launch_one<T, F1>(a, grid, st);
+    case F2: return launch_one<T, F2>(a, grid, st);
+    case FE: return launch_one<T, FE>(a, grid, st);
+    case FV: return launch_one<T, FV>(a, grid, st);
+    case R1: return launch_one<T, R1>(a, grid, st);
+    case R2: return launch_one<T, R2>(a, grid, st);
+    case R0: return launch_one<T, R0>(a, grid, st);
+  }
+  return QVS_EINVAL;
+}
+
+// ---------------------------------------------------------------- small-state driver
+
+template <class T>
+static int run_small(qvs_ctx* h, int p, const double* gammas, const double* ts, bool grad,
+                     double* E, double* dg, double* dt) {
+  using C = typename Cx<T>::t;
+  const int64_t dim = h->dim;
+  QVS_TRY(h->res.ensure(sizeof(double) * (size_t)(1 + 2 * p) + sizeof(double) * 4 * (size_t)p));
+  double* res = h->res.as<double>();
+  double* ang = res + 1 + 2 * p;
+  std::vector<double> hang(4 * (size_t)p);
+  for (int k = 0; k < p; ++k) {
+    hang[4 * k] = cos(ts[k]);
+    hang[4 * k + 1] = sin(ts[k]);
+    hang[4 * k + 2] = gammas[k];
+    hang[4 * k + 3] = 0.0;
+  }
+  QVS_CUDA_TRY(cudaMemcpyAsync(ang, hang.data(), sizeof(double) * 4 * p, cudaMemcpyHostToDevice,
+                               h->stream));
+  QVS_TRY(h->psi.ensure(dim * sizeof(C)));
+  if (grad) QVS_TRY(h->ckpt.ensure((size_t)p * dim * sizeof(C)));
+  SmallArgs<T> a{};
+  a.n = h->n;
+  a.p = p;
+  a.q = h->q.as<T>();
+  a.psi0 = h->have_psi0 ? h->psi0.as<C>() : nullptr;
+  a.states = grad ? h->ckpt.as<C>() : nullptr;
+  a.psi_out = h->psi.as<C>();
+  a.ang = ang;
+  a.res = res;
+  a.grad = grad ? 1 : 0;
+  const size_t sm = 2 * (size_t)dim * sizeof(C);
+  QVS_CUDA_TRY(cudaFuncSetAttribute(small_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)sm));
+  small_kernel<T><<<1, 256, sm, h->stream>>>(a);
+  QVS_CUDA_TRY(cudaGetLastError());
+  h->launches = 1;
+  QVS_TRY(ensure_host_res(h, p));
+  const int nres = grad ? 1 + 2 * p : 1;
+  QVS_CUDA_TRY(cudaMemcpyAsync(h->host_res, res, sizeof(double) * nres, cudaMemcpyDeviceToHost,
+                               h->stream));
+  QVS_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  *E = h->host_res[0];
+  if (grad) {
+    for (int k = 0; k < p; ++k) {
+      dg[k] = h->host_res[1 + k];
+      dt[k] = h->host_res[1 + p + k];
+    }
+  }
+  return QVS_OK;
+}
+
+// ---------------------------------------------------------------- tiled driver
+
+template <class T>
+static int run_tiled(qvs_ctx* h, int p, const double* gammas, const double* ts, bool grad,
+                     double* E, double* dg, double* dt) {
+  using C = typename Cx<T>::t;
+  Plan pl;
+  QVS_TRY(make_plan(h->n, p, pl));
+  const int F = pl.F;
+  const uint32_t grid = 1u << (h->n - TB);
+  const size_t sbytes = (size_t)h->dim * sizeof(C);
+
+  // checkpoint placement: stored pass boundaries j = c, 2c, ... <= F-1
+  int ckl = h->ckpt_layers > 0 ? h->ckpt_layers : (int)ceil(sqrt((double)p) - 1e-9);
+  if (ckl < 1) ckl = 1;
+  const int c = grad ? ckl * (pl.g - 1) : (F + 1);
+  const int nck = grad ? (F - 1) / c : 0;
+  QVS_TRY(h->psi.ensure(sbytes));
+  if (grad) {
+    QVS_TRY(h->lam.ensure(sbytes));
+    if (nck > 0) QVS_TRY(h->ckpt.ensure((size_t)nck * sbytes));
+  }
+  const int nrows = 3 * F + 1;
+  QVS_TRY(h->part.ensure(sizeof(double) * (size_t)nrows * grid));
+  const int nslots = 1 + 2 * p;
+  QVS_TRY(h->res.ensure(sizeof(double) * nslots));
+  QVS_TRY(h->rowmap.ensure(sizeof(int) * 3 * nslots));
+  C* W = h->psi.as<C>();
+  C* K = h->ckpt.as<C>();
+  auto loc = [&](int j) -> C* {
+    if (j >= 1 && j <= F - 1 && j % c == 0 && (j / c) <= nck) return K + (size_t)(j / c - 1) * h->dim;
+    return W;
+  };
+  const bool stored_ck = true;
+  (void)stored_ck;
+  auto is_stored = [&](int j) { return j >= 1 && j <= F - 1 && j % c == 0 && (j / c) <= nck; };
+
+  // reduction row map: slot 0 = E; 1..p = dgamma_k; p+1..2p = dt_k
+  std::vector<int> rowmap(3 * (size_t)nslots, -1);
+  rowmap[0] = 3 * F;
+  if (grad) {
+    std::vector<int> fill(nslots, 0);
+    auto add = [&](int slot, int row) { rowmap[3 * slot + fill[slot]++] = row; };
+    for (int j = 1; j <= F; ++j) {
+      const PassInfo& pi = pl.pass[j];
+      if (pi.lg >= 0) add(1 + pi.lg, 3 * (j - 1) + 2);
+      if (pi.lb >= 0) add(1 + p + pi.lb, 3 * (j - 1) + 0);
+      if (pi.la >= 0) add(1 + p + pi.la, 3 * (j - 1) + 1);
+    }
+  }
+  QVS_CUDA_TRY(cudaMemcpyAsync(h->rowmap.ptr, rowmap.data(), sizeof(int) * rowmap.size(),
+                               cudaMemcpyHostToDevice, h->stream));
+
+  const T amp = (T)(1.0 / sqrt((double)h->dim));
+  int64_t launches = 0;
+  // forward
+  for (int j = 1; j <= F; ++j) {
+    const PassInfo& pi = pl.pass[j];
+    PassArgs<T> a{};
+    a.tile = pl.tile[pi.type];
+    a.q = h->q.as<T>();
+    a.part = h->part.as<double>();
+    a.row_bef = a.row_aft = a.row_gam = -1;
+    a.row_E = 3 * F;
+    a.init_amp = amp;
+    a.gen_init = h->have_psi0 ? 0 : 1;
+    a.mask_bef = pi.lb >= 0 ? pl.gmask[pi.type] : 0u;
+    a.mask_aft = pi.la >= 0 ? pl.gmask[pi.type] : 0u;
+    fill_angles(a, pi, gammas, ts);
+    a.psi_in = (j == 1) ? (h->have_psi0 ? h->psi0.as<C>() : nullptr) : loc(j - 1);
+    int shape = pi.shape;
+    if (j == F) {
+      if (grad) {
+        a.lam_out = h->lam.as<C>();
+        a.row_bef = 3 * (j - 1) + 0;
+      } else {
+        shape = FV;
+        a.psi_out = W;
+      }
+    } else {
+      a.psi_out = grad ? loc(j) : W;
+    }
+    QVS_TRY(launch_shape<T>(h, shape, a, grid));
+    ++launches;
+  }
+  // adjoint
+  if (grad) {
+    for (int j = F - 1; j >= 1; --j) {
+      const PassInfo& pi = pl.pass[j];
+      PassArgs<T> a{};
+      a.tile = pl.tile[pi.type];
+      a.q = h->q.as<T>();
+      a.part = h->part.as<double>();
+      a.mask_bef = pi.lb >= 0 ? pl.gmask[pi.type] : 0u;
+      a.mask_aft = pi.la >= 0 ? pl.gmask[pi.type] : 0u;
+      fill_angles(a, pi, gammas, ts);
+      a.psi_in = loc(j);
+      a.lam_in = h->lam.as<C>();
+      a.lam_out = h->lam.as<C>();
+      a.psi_out = (j - 1 >= 1 && !is_stored(j - 1)) ? W : nullptr;
+      a.row_bef = pi.lb >= 0 ? 3 * (j - 1) + 0 : -1;
+      a.row_aft = pi.la >= 0 ? 3 * (j - 1) + 1 : -1;
+      a.row_gam = pi.lg >= 0 ? 3 * (j - 1) + 2 : -1;
+      a.row_E = -1;
+      const int shape = pi.shape == F0 ? R0 : (pi.shape == F1 ? R1 : R2);
+      QVS_TRY(launch_shape<T>(h, shape, a, grid));
+      ++launches;
+    }
+  }
+  const int nout = grad ? nslots : 1;
+  {
+    cudaEvent_t ev;
+    QVS_TRY(prof_begin(h, &ev));
+    QVS_TRY(reduce_rows(h, h->part.as<double>(), grid, h->rowmap.as<int>(), nout, h->res.as<double>()));
+    QVS_TRY(prof_end(h, "reduce_rows", 8.0 * grid * (nout == 1 ? 1 : 3 * F), ev));
+  }
+  ++launches;
+  h->launches = launches;
+  QVS_TRY(ensure_host_res(h, p));
+  QVS_CUDA_TRY(cudaMemcpyAsync(h->host_res, h->res.ptr, sizeof(double) * nout,
+                               cudaMemcpyDeviceToHost, h->stream));
+  QVS_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  QVS_TRY(prof_flush(h));
+  *E = h->host_res[0];
+  if (grad) {
+    for (int k = 0; k < p; ++k) {
+      dg[k] = h->host_res[1 + k];
+      dt[k] = h->host_res[1 + p + k];
+    }
+  }
+  return QVS_OK;
+}
+
+}  // namespace hc
+
+static int hc_run(qvs_ctx* h, int p, const double* gammas, const double* ts, bool grad, double* E,
+                  double* dg, double* dt) {
+  if (h->n < 1) return QVS_EINVAL;
+  const bool small = h->n <= hc::TB;
+  if (h->precision == QVS_C64)
+    return small ? hc::run_small<float>(h, p, gammas, ts, grad, E, dg, dt)
+                 : hc::run_tiled<float>(h, p, gammas, ts, grad, E, dg, dt);
+  return small ? hc::run_small<double>(h, p, gammas, ts, grad, E, dg, dt)
+               : hc::run_tiled<double>(h, p, gammas, ts, grad, E, dg, dt);
+}
+
+int hc_evolve(qvs_ctx* h, int p, const double* gammas, const double* ts) {
+  double E = 0.0;
+  QVS_TRY(hc_run(h, p, gammas, ts, false, &E, nullptr, nullptr));
+  h->E = E;
+  h->have_E = true;
+  return QVS_OK;
+}
+
+int hc_gradient(qvs_ctx* h, int p, const double* gammas, const double* ts, double* E, double* dg,
+                double* dt) {
+  h->have_E = false;
+  return hc_run(h, p, gammas, ts, true, E, dg, dt);
+}
+
+}  // namespace qvs

@@ -1,0 +1,165 @@
+// Internal declarations shared by the libqvs translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/qvs.h"
+
+#define QVS_CUDA_TRY(expr)                         \
+  do {                                             \
+    cudaError_t _e = (expr);                       \
+    if (_e != cudaSuccess) {                       \
+      (void)cudaGetLastError();                    \
+      return _e == cudaErrorMemoryAllocation ? QVS_ENOMEM : QVS_ECUDA; \
+    }                                              \
+  } while (0)
+
+#define QVS_TRY(expr)                 \
+  do {                                \
+    int _s = (expr);                  \
+    if (_s != QVS_OK) return _s;      \
+  } while (0)
+
+namespace qvs {
+
+// Device buffer owned by a handle.
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  int ensure(size_t b) {
+    if (b <= bytes && ptr) return QVS_OK;
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    bytes = 0;
+    if (b == 0) return QVS_OK;
+    cudaError_t e = cudaMalloc(&ptr, b);
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      ptr = nullptr;
+      return QVS_ENOMEM;
+    }
+    bytes = b;
+    return QVS_OK;
+  }
+  void release() {
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    bytes = 0;
+  }
+  template <class T> T* as() const { return static_cast<T*>(ptr); }
+};
+
+// Circulant mixer data: eigenvalues in the order the FFT passes produce them.
+struct CircData {
+  int log2n = 0;
+  DevBuf lam;     // double[dim]
+};
+
+// CSR mixer data.
+struct CsrData {
+  DevBuf rowptr, colind, values;
+  int64_t nnz = 0;
+  bool has_values = false;
+  float implicit_value = 0.f;
+  double spec_lo = 0, spec_hi = 0, tol = 1e-7;
+};
+
+}  // namespace qvs
+
+struct qvs_ctx {
+  int64_t dim = 0;
+  int n = 0;                // log2(dim) when dim is a power of two, else -1
+  int precision = QVS_C64;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+
+  bool have_q = false, have_mixer = false, have_psi0 = false;
+  int mixer = 0;
+  qvs::DevBuf q;            // float[dim] (C64) or double[dim] (C128)
+  qvs::DevBuf psi0;         // explicit initial state
+  qvs::DevBuf psi;          // working state / final state of qvs_evolve
+  qvs::DevBuf lam;          // adjoint vector
+  qvs::DevBuf ckpt;         // checkpoint states (contiguous slots)
+  qvs::DevBuf part;         // per-CTA fp64 partial sums (reduction scratch)
+  qvs::DevBuf res;          // double[1 + 2p] final reductions
+  qvs::DevBuf rowmap;       // int[...] reduction row map
+  qvs::DevBuf work;         // mixer-specific scratch
+  double* host_res = nullptr;   // pinned, 1 + 2 * host_res_cap doubles
+  int host_res_cap = 0;
+
+  int ckpt_layers = 0;
+  bool have_E = false;
+  double E = 0.0;
+  int64_t launches = 0;
+
+  qvs::CircData circ;
+  qvs::CsrData csr;
+
+  // QVS_OPT_PROFILE: per-kernel event timing
+  struct KStat {
+    std::string name;
+    int64_t launches = 0;
+    double ms = 0.0, bytes = 0.0;
+  };
+  struct Pending {
+    int id;
+    double bytes;
+    cudaEvent_t a, b;
+  };
+  bool profile = false;
+  std::vector<KStat> kstats;
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> evpool;
+};
+
+namespace qvs {
+
+// complex element size in bytes for the handle precision
+inline size_t elem_bytes(const qvs_ctx* h) { return h->precision == QVS_C128 ? 16 : 8; }
+
+int ensure_host_res(qvs_ctx* h, int p);
+
+// Profiling: prof_begin records a start event (when QVS_OPT_PROFILE is on) and returns a token;
+// prof_end records the end event for kernel `name` moving `bytes` algorithmic bytes; prof_flush
+// (after the stream has been synchronised) folds the elapsed times into the statistics.
+int prof_begin(qvs_ctx* h, cudaEvent_t* start);
+int prof_end(qvs_ctx* h, const char* name, double bytes, cudaEvent_t start);
+int prof_flush(qvs_ctx* h);
+void prof_release(qvs_ctx* h);
+
+// hypercube (QAOA) path: hypercube.cu
+int hc_evolve(qvs_ctx* h, int p, const double* gammas, const double* ts);
+int hc_gradient(qvs_ctx* h, int p, const double* gammas, const double* ts, double* E, double* dg,
+                double* dt);
+
+// circulant (QWOA) path: circulant.cu
+int circ_set_mixer(qvs_ctx* h, const qvs_mixer_desc* d);
+int circ_evolve(qvs_ctx* h, int p, const double* gammas, const double* ts);
+int circ_gradient(qvs_ctx* h, int p, const double* gammas, const double* ts, double* E, double* dg,
+                  double* dt);
+
+// CSR Chebyshev (QAOAz) path: csr_cheb.cu
+int csr_set_mixer(qvs_ctx* h, const qvs_mixer_desc* d);
+int csr_evolve(qvs_ctx* h, int p, const double* gammas, const double* ts);
+int csr_gradient(qvs_ctx* h, int p, const double* gammas, const double* ts, double* E, double* dg,
+                 double* dt);
+
+// Final deterministic reduction of per-CTA partial rows into result slots (reduce.cu).
+// slot s = sum over rows rowmap[s*3 + 0..2] (-1 = unused) of part[row * nblk + b], b < nblk.
+int reduce_rows(qvs_ctx* h, const double* part, int64_t nblk, const int* rowmap_dev, int nslots,
+                double* out_dev);
+
+// float-float turns of an angle gamma: gamma / (2 pi) split into hi + lo floats.
+inline void turns_split(double gamma, float* hi, float* lo) {
+  const double two_pi = 6.283185307179586476925286766559;
+  double g = gamma / two_pi;
+  float h = (float)g;
+  *hi = h;
+  *lo = (float)(g - (double)h);
+}
+
+}  // namespace qvs

@@ -1,0 +1,87 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds, loads and exports every
+function that include/qvs.h declares; host-only entry points are compared with the oracle."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as orc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for f in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"\b(qvs_\w+)\s*\(", src)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def qvs():
+    from paper_2110_03963_gb300 import _build
+    _build.build()
+    import paper_2110_03963_gb300 as q
+    q.load()
+    return q
+
+
+def test_exports_every_declared_symbol(qvs):
+    import ctypes
+    lib = ctypes.CDLL(qvs.LIB_PATH)
+    declared = _declared()
+    assert len(declared) >= 16
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def test_binding_names_match_header(qvs):
+    declared = set(_declared())
+    assert declared == set(qvs.EXPORTED)
+    for name in declared:
+        assert callable(getattr(qvs, name)), name
+
+
+def test_strerror(qvs):
+    assert qvs.strerror(0) == "ok"
+    assert "invalid" in qvs.strerror(-1)
+    assert qvs.strerror(12345) == "unknown status"
+
+
+def test_create_rejects_bad_arguments_without_gpu(qvs):
+    import ctypes
+    lib = qvs.load()
+    h = ctypes.c_void_p()
+    assert lib.qvs_create(ctypes.byref(h), 1, qvs.QVS_C64, None) == qvs.QVS_EINVAL
+    assert lib.qvs_create(ctypes.byref(h), 1024, 7, None) == qvs.QVS_EINVAL
+    assert lib.qvs_create(None, 1024, qvs.QVS_C64, None) == qvs.QVS_EINVAL
+    assert lib.qvs_destroy(None) == qvs.QVS_OK
+    assert lib.qvs_evolve(None, 1, None, None) == qvs.QVS_EINVAL
+
+
+@pytest.mark.parametrize("n,k", [(6, 3), (8, 4), (9, 2), (12, 6)])
+def test_xy_ring_csr_matches_oracle_operator(qvs, n, k):
+    states, rowptr, colind = qvs.qvs_xy_ring_csr(n, k)
+    ref_states = orc.subspace_states(n, k)
+    assert np.array_equal(states, ref_states)
+    rng = np.random.default_rng(n * 100 + k)
+    v = rng.standard_normal(states.shape[0]) + 1j * rng.standard_normal(states.shape[0])
+    rows = np.repeat(np.arange(states.shape[0]), np.diff(rowptr))
+    y = np.zeros_like(v)
+    np.add.at(y, rows, 2.0 * v[colind])
+    assert np.max(np.abs(y - orc.xy_ring_apply(v, n, states))) < 1e-12
+
+
+def test_xy_ring_csr_full_size_counts(qvs):
+    import math
+    import ctypes
+    lib = qvs.load()
+    dim = ctypes.c_int64()
+    nnz = ctypes.c_int64()
+    assert lib.qvs_xy_ring_csr(24, 12, None, None, None, ctypes.byref(dim), ctypes.byref(nnz)) == 0
+    assert dim.value == math.comb(24, 12)
+    assert nnz.value == 2 * 24 * math.comb(22, 11)

@@ -179,7 +179,7 @@ def run_ours(args):
         torch.distributed.barrier()
     import paper_2110_03963_gb300 as qvs
 
-    n, p = N_QUBITS, P_LAYERS
+    n, p = args.qubits, args.layers
     dim = 1 << n
     inst = wl.wmaxcut(n, p, instance=rank)
     G = inst.graph
@@ -272,7 +272,9 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c64 (fp32 complex; fp64 phase turns, reductions)",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_qubits": n, "p": p, "amplitudes": dim,
+            "config": {"workload": WORKLOAD if (n, p) == (N_QUBITS, P_LAYERS) else
+                       f"QAOA weighted max-cut, n={n}, G({n},1/2) U[0,1] weights, p={p}, objective + adjoint gradient",
+                       "n_qubits": n, "p": p, "amplitudes": dim,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (2 GiB state, 1 GiB q)",
                        "ckpt_layers": args.ckpt if args.ckpt is not None else "ceil(sqrt(p))"},
@@ -306,6 +308,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ckpt", type=int, default=None, help="checkpoint interval in layers (0 = ceil(sqrt(p)))")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--qubits", type=int, default=N_QUBITS, help="state size 2^qubits (28 is the benchmark)")
+    ap.add_argument("--layers", type=int, default=P_LAYERS, help="depth p (8 is the benchmark)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -140,6 +140,8 @@ extern "C" int qvs_destroy(qvs_t h) {
   h->rowmap.release();
   h->work.release();
   h->circ.lam.release();
+  h->circ.tab.release();
+  h->circ.qT.release();
   h->csr.rowptr.release();
   h->csr.colind.release();
   h->csr.values.release();
@@ -198,6 +200,7 @@ extern "C" int qvs_set_quality(qvs_t h, const void* q, int dtype, int on_device)
   }
   h->have_q = true;
   h->have_E = false;
+  h->circ.qT_valid = false;
   return QVS_OK;
 }
 

@@ -38,11 +38,13 @@ __host__ __device__ __forceinline__ constexpr int regbit(int L, int i) {
 // phases of 8-byte accesses conflict-free in all three layouts and keeps pairs (j, j^1) adjacent.
 __device__ __forceinline__ int spos(int j) { return j ^ ((j >> 4) & 0xE); }
 
-// Tile geometry: global element offset of each tile bit, and the non-tile bit positions that
-// the CTA index scatters into.
+// Tile geometry. Tile bits 0..s-1 are the low index bits 0..s-1 (a contiguous chunk of 2^s
+// amplitudes); tile bits s..TB-1 are the consecutive index bits hfirst..hfirst+TB-s-1. The CTA
+// index scatters into the remaining (non-tile) index bits.
 struct Tile {
-  uint32_t bitoff[TB];
-  uint8_t ntbit[32];
+  uint32_t smask;     // (1 << s) - 1
+  int hshift;         // hfirst - s
+  uint8_t ntbit[32];  // non-tile index bit positions (ascending)
   int n_nt;
 };
 
@@ -53,50 +55,47 @@ __device__ __forceinline__ uint32_t tile_base(const Tile& t, uint32_t bid) {
   return base;
 }
 
-// global offset of tile index j (bit scatter through bitoff)
-__device__ __forceinline__ uint32_t scatter(const Tile& t, int j) {
-  uint32_t o = 0;
-#pragma unroll
-  for (int b = 0; b < TB; ++b)
-    if ((j >> b) & 1) o += t.bitoff[b];
-  return o;
+// global offset of tile index j (bits below s stay, bits from s up move by hshift); the map is
+// bitwise, so offset(j1 | j2) = offset(j1) + offset(j2) for disjoint j1, j2
+__device__ __forceinline__ uint32_t toff(const Tile& t, uint32_t j) {
+  return (j & t.smask) + ((j & ~t.smask) << t.hshift);
 }
 
 template <class T> struct Cx;
 template <> struct Cx<float> { using t = float2; };
 template <> struct Cx<double> { using t = double2; };
 
-// ---------------------------------------------------------------- complex helpers
+// ---------------------------------------------------------------- storage form
+//
+// Amplitudes in the tiled path are kept in a "parity form": amplitude g is stored as (re, im)
+// when popcount(g) is even and as (im, re) when it is odd. Every rotation pairs two indices that
+// differ in one bit, so one partner of each pair is always in each form, and
+//     a' = c a - i s b   becomes   A' = c A + (s, -s) * B   (A normal, B swapped)
+//                                  B' = c B + (-s, s) * A
+// (componentwise products): two paired-float operations per amplitude and bit, with no operand
+// shuffles. The private buffers of the tiled path (working state, adjoint vector, checkpoints)
+// hold this form; inputs and outputs visible to callers are converted at the edge.
 
-// exp(-i t X) on the pair (a, b) with c = cos t, s = sin t:
-//   a' = c a - i s b,  b' = c b - i s a   (the adjoint passes -s)
-__device__ __forceinline__ void rot(float2& a, float2& b, float c, float s) {
-  const float2 cc = make_float2(c, c);
-  const float2 sp = make_float2(s, -s);
-  const float2 na = __ffma2_rn(cc, a, __fmul2_rn(sp, make_float2(b.y, b.x)));
-  const float2 nb = __ffma2_rn(cc, b, __fmul2_rn(sp, make_float2(a.y, a.x)));
-  a = na;
-  b = nb;
-}
-__device__ __forceinline__ void rot(double2& a, double2& b, double c, double s) {
-  const double2 a0 = a;
-  a.x = c * a.x + s * b.y;
-  a.y = c * a.y - s * b.x;
-  b.x = c * b.x + s * a0.y;
-  b.y = c * b.y - s * a0.x;
+__host__ __device__ __forceinline__ constexpr int cpar(int x) {
+  x ^= x >> 8;
+  x ^= x >> 4;
+  x ^= x >> 2;
+  x ^= x >> 1;
+  return x & 1;
 }
 
-// Im(conj(a) * b)
-__device__ __forceinline__ float imdot(float2 a, float2 b) { return a.x * b.y - a.y * b.x; }
-__device__ __forceinline__ double imdot(double2 a, double2 b) { return a.x * b.y - a.y * b.x; }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ double2 fma2(double2 a, double2 b, double2 c) {
+  return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+__device__ __forceinline__ double2 mul2(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+template <class C, class T> __device__ __forceinline__ C mk2(T x, T y);
+template <> __device__ __forceinline__ float2 mk2<float2, float>(float x, float y) { return make_float2(x, y); }
+template <> __device__ __forceinline__ double2 mk2<double2, double>(double x, double y) { return make_double2(x, y); }
 
-// multiply v by (c - i s) (forward phase exp(-i theta) with c = cos theta, s = sin theta)
-__device__ __forceinline__ float2 cmul_conj(float2 v, float c, float s) {
-  return make_float2(c * v.x + s * v.y, c * v.y - s * v.x);
-}
-__device__ __forceinline__ double2 cmul_conj(double2 v, double c, double s) {
-  return make_double2(c * v.x + s * v.y, c * v.y - s * v.x);
-}
+// swap re/im: converts between the two storage forms
+template <class C> __device__ __forceinline__ C swp(C v) { C w; w.x = v.y; w.y = v.x; return w; }
 
 // Phase angle of exp(-i gamma q): the complex64 path carries gamma / 2pi as a float-float pair
 // (hi, lo). The exact product error of hi*q (FMA two-product, Ogita-Rump-Oishi 2005) and the lo
@@ -113,26 +112,52 @@ __device__ __forceinline__ void phase_cs(double q, double gamma, double, double&
   sincos(gamma * q, &s, &c);
 }
 
-// ---------------------------------------------------------------- register-layout operations
-
-template <int L, class C, class T>
-__device__ __forceinline__ void rot_layout(C (&v)[R], uint32_t mask, T c, T s) {
-#pragma unroll
-  for (int i = 0; i < RB; ++i) {
-    if (mask & (1u << regbit(L, i))) {
-#pragma unroll
-      for (int r = 0; r < R; ++r)
-        if (!(r & (1 << i))) rot(v[r], v[r | (1 << i)], c, s);
-    }
-  }
+// multiply a stored amplitude by exp(-i theta) (c = cos, s = sin); a swapped amplitude uses -s
+template <class C, class T>
+__device__ __forceinline__ C phase_mul(C v, T c, T s) {
+  C w;
+  w.x = c * v.x + s * v.y;
+  w.y = c * v.y - s * v.x;
+  return w;
 }
 
-// Adjoint rotations exp(+i t X_b) on psi and lam, accumulating Im<lam|X_b psi> for every bit b
-// undone (X_b commutes with all rotations of the same layer, so the value is the one at the
-// layer's output).
-template <int L, class C, class T, class A>
-__device__ __forceinline__ void unrot_layout_acc(C (&p)[R], C (&l)[R], uint32_t mask, T c, T s,
-                                                 A& acc) {
+// Im(conj(lam) * psi) for two amplitudes stored in the same form (negate for the swapped form)
+template <class C> __device__ __forceinline__ auto imdot_st(C l, C p) { return l.x * p.y - l.y * p.x; }
+template <class C> __device__ __forceinline__ auto dif(C z) { return z.x - z.y; }
+
+// normal-form helpers (the single-CTA small-state kernel keeps amplitudes as (re, im))
+__device__ __forceinline__ void rot_normal(float2& a, float2& b, float c, float s) {
+  const float2 a0 = a;
+  a.x = c * a.x + s * b.y;
+  a.y = c * a.y - s * b.x;
+  b.x = c * b.x + s * a0.y;
+  b.y = c * b.y - s * a0.x;
+}
+__device__ __forceinline__ void rot_normal(double2& a, double2& b, double c, double s) {
+  const double2 a0 = a;
+  a.x = c * a.x + s * b.y;
+  a.y = c * a.y - s * b.x;
+  b.x = c * b.x + s * a0.y;
+  b.y = c * b.y - s * a0.x;
+}
+__device__ __forceinline__ float imdot(float2 a, float2 b) { return a.x * b.y - a.y * b.x; }
+__device__ __forceinline__ double imdot(double2 a, double2 b) { return a.x * b.y - a.y * b.x; }
+__device__ __forceinline__ float2 cmul_conj(float2 v, float c, float s) {
+  return make_float2(c * v.x + s * v.y, c * v.y - s * v.x);
+}
+__device__ __forceinline__ double2 cmul_conj(double2 v, double c, double s) {
+  return make_double2(c * v.x + s * v.y, c * v.y - s * v.x);
+}
+
+// ---------------------------------------------------------------- register-layout operations
+// tpar = parity of the thread's own index bits (plus the tile base) in layout L; the parity of
+// register r adds cpar(tj<L>(r, 0)), known at compile time.
+
+template <int L, class C, class T>
+__device__ __forceinline__ void rot_layout(C (&v)[R], uint32_t mask, T c, T s, uint32_t tpar) {
+  const C cc = mk2<C, T>(c, c);
+  const T sp = tpar ? -s : s;
+  const C svp = mk2<C, T>(sp, -sp), svn = mk2<C, T>(-sp, sp);
 #pragma unroll
   for (int i = 0; i < RB; ++i) {
     if (mask & (1u << regbit(L, i))) {
@@ -140,13 +165,53 @@ __device__ __forceinline__ void unrot_layout_acc(C (&p)[R], C (&l)[R], uint32_t 
       for (int r = 0; r < R; ++r) {
         if (!(r & (1 << i))) {
           const int r1 = r | (1 << i);
-          acc += imdot(l[r], p[r1]) + imdot(l[r1], p[r]);
-          rot(p[r], p[r1], c, -s);
-          rot(l[r], l[r1], c, -s);
+          const bool pr = cpar(tj<L>(r, 0));
+          const C a = v[r], b = v[r1];
+          v[r] = fma2(cc, a, mul2(pr ? svn : svp, b));
+          v[r1] = fma2(cc, b, mul2(pr ? svp : svn, a));
         }
       }
     }
   }
+}
+
+// Adjoint rotations exp(+i t X_b) on psi and lam, accumulating Im<lam|X_b psi> for every bit b
+// undone (X_b commutes with all rotations of the same layer, so the value is the one at the
+// layer's output). For a pair (r, r1) whose first member is in normal form the term is
+// dif(l_r * p_r1) - dif(l_r1 * p_r) (componentwise products), and its negative otherwise.
+template <int L, class C, class T, class A>
+__device__ __forceinline__ void unrot_layout_acc(C (&p)[R], C (&l)[R], uint32_t mask, T c, T s,
+                                                 uint32_t tpar, A& acc) {
+  const C cc = mk2<C, T>(c, c);
+  const T sp = tpar ? s : -s;   // adjoint: angle -t
+  const C svp = mk2<C, T>(sp, -sp), svn = mk2<C, T>(-sp, sp);
+  C e1 = mk2<C, T>(0, 0), e2 = e1, o1 = e1, o2 = e1;
+#pragma unroll
+  for (int i = 0; i < RB; ++i) {
+    if (mask & (1u << regbit(L, i))) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        if (!(r & (1 << i))) {
+          const int r1 = r | (1 << i);
+          const bool pr = cpar(tj<L>(r, 0));
+          const C pa = p[r], pb = p[r1], la = l[r], lb = l[r1];
+          if (pr) {
+            o1 = fma2(la, pb, o1);
+            o2 = fma2(lb, pa, o2);
+          } else {
+            e1 = fma2(la, pb, e1);
+            e2 = fma2(lb, pa, e2);
+          }
+          p[r] = fma2(cc, pa, mul2(pr ? svn : svp, pb));
+          p[r1] = fma2(cc, pb, mul2(pr ? svp : svn, pa));
+          l[r] = fma2(cc, la, mul2(pr ? svn : svp, lb));
+          l[r1] = fma2(cc, lb, mul2(pr ? svp : svn, la));
+        }
+      }
+    }
+  }
+  const A t = (A)((dif(e1) - dif(e2)) - (dif(o1) - dif(o2)));
+  acc += tpar ? -t : t;
 }
 
 // shared-memory transpose from layout LF to layout LT
@@ -180,51 +245,106 @@ __device__ __forceinline__ void xchg(C (&v)[R], C* sm, int tid) {
   __syncthreads();
 }
 
-template <int LF, int LT, class C>
-__device__ __forceinline__ void xchg2(C (&a)[R], C (&b)[R], C* sm, int tid) {
-  xchg<LF, LT>(a, sm, tid);
-  xchg<LF, LT>(b, sm, tid);
-}
-
-// ---------------------------------------------------------------- global loads and stores
-
-// offsets of the 16 registers of layout L relative to the thread's own offset
-template <int L>
-__device__ __forceinline__ void reg_offsets(const Tile& t, uint32_t (&ro)[R]) {
+template <int L, class C>
+__device__ __forceinline__ void sput(const C (&v)[R], C* sm, int tid) {
+  if constexpr (L == 0 && sizeof(C) == 8) {
+    float4* s4 = reinterpret_cast<float4*>(sm);
 #pragma unroll
-  for (int r = 0; r < R; ++r) ro[r] = scatter(t, tj<L>(r, 0));
+    for (int r = 0; r < R; r += 2) {
+      const float2 a = *reinterpret_cast<const float2*>(&v[r]);
+      const float2 b = *reinterpret_cast<const float2*>(&v[r + 1]);
+      s4[spos(tj<0>(r, tid)) >> 1] = make_float4(a.x, a.y, b.x, b.y);
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < R; ++r) sm[spos(tj<L>(r, tid))] = v[r];
+  }
 }
 
 template <int L, class C>
-__device__ __forceinline__ void gload(C (&v)[R], const C* __restrict__ g, uint32_t off,
-                                      const uint32_t (&ro)[R]) {
+__device__ __forceinline__ void sget(C (&v)[R], const C* sm, int tid) {
   if constexpr (L == 0 && sizeof(C) == 8) {
+    const float4* s4 = reinterpret_cast<const float4*>(sm);
 #pragma unroll
     for (int r = 0; r < R; r += 2) {
-      const float4 w = __ldcs(reinterpret_cast<const float4*>(g + off + ro[r]));
+      const float4 w = s4[spos(tj<0>(r, tid)) >> 1];
       *reinterpret_cast<float2*>(&v[r]) = make_float2(w.x, w.y);
       *reinterpret_cast<float2*>(&v[r + 1]) = make_float2(w.z, w.w);
     }
   } else {
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = __ldcs(g + off + ro[r]);
+    for (int r = 0; r < R; ++r) v[r] = sm[spos(tj<L>(r, tid))];
+  }
+}
+
+// two vectors through two shared buffers (sm and sm + TILE) with one barrier pair
+template <int LF, int LT, class C>
+__device__ __forceinline__ void xchg2(C (&a)[R], C (&b)[R], C* sm, int tid) {
+  sput<LF>(a, sm, tid);
+  sput<LF>(b, sm + TILE, tid);
+  __syncthreads();
+  sget<LT>(a, sm, tid);
+  sget<LT>(b, sm + TILE, tid);
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------- global loads and stores
+// off = tile base + offset of the thread's own index bits in layout L; each register's offset is
+// formed at the access (two logic ops and a shift) rather than held in registers.
+
+template <int L, class C>
+__device__ __forceinline__ void gload(C (&v)[R], const C* __restrict__ g, uint32_t off, const Tile& t) {
+  if constexpr (L == 0 && sizeof(C) == 8) {
+#pragma unroll
+    for (int r = 0; r < R; r += 2) {
+      const float4 w = __ldcs(reinterpret_cast<const float4*>(g + off + toff(t, tj<L>(r, 0))));
+      *reinterpret_cast<float2*>(&v[r]) = make_float2(w.x, w.y);
+      *reinterpret_cast<float2*>(&v[r + 1]) = make_float2(w.z, w.w);
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = __ldcs(g + off + toff(t, tj<L>(r, 0)));
   }
 }
 
 template <int L, class C>
-__device__ __forceinline__ void gstore(const C (&v)[R], C* __restrict__ g, uint32_t off,
-                                       const uint32_t (&ro)[R]) {
+__device__ __forceinline__ void gstore(const C (&v)[R], C* __restrict__ g, uint32_t off, const Tile& t) {
   if constexpr (L == 0 && sizeof(C) == 8) {
 #pragma unroll
     for (int r = 0; r < R; r += 2) {
       const float2 a = *reinterpret_cast<const float2*>(&v[r]);
       const float2 b = *reinterpret_cast<const float2*>(&v[r + 1]);
-      __stcs(reinterpret_cast<float4*>(g + off + ro[r]), make_float4(a.x, a.y, b.x, b.y));
+      __stcs(reinterpret_cast<float4*>(g + off + toff(t, tj<L>(r, 0))), make_float4(a.x, a.y, b.x, b.y));
     }
   } else {
 #pragma unroll
-    for (int r = 0; r < R; ++r) __stcs(g + off + ro[r], v[r]);
+    for (int r = 0; r < R; ++r) __stcs(g + off + toff(t, tj<L>(r, 0)), v[r]);
   }
+}
+
+// normal-form loads/stores: convert to/from the parity form (caller-visible buffers)
+template <int L, class C>
+__device__ __forceinline__ void gload_normal(C (&v)[R], const C* __restrict__ g, uint32_t off,
+                                             const Tile& t, uint32_t tpar) {
+  gload<L>(v, g, off, t);
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+    if (tpar ^ (uint32_t)cpar(tj<L>(r, 0))) v[r] = swp(v[r]);
+}
+
+template <int L, class C>
+__device__ __forceinline__ void gstore_normal(C (&v)[R], C* __restrict__ g, uint32_t off,
+                                              const Tile& t, uint32_t tpar) {
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+    if (tpar ^ (uint32_t)cpar(tj<L>(r, 0))) v[r] = swp(v[r]);
+  gstore<L>(v, g, off, t);
+}
+
+template <int L, class T>
+__device__ __forceinline__ void qload(T (&qv)[R], const T* __restrict__ q, uint32_t off, const Tile& t) {
+#pragma unroll
+  for (int r = 0; r < R; ++r) qv[r] = __ldcs(q + off + toff(t, tj<L>(r, 0)));
 }
 
 }  // namespace hc

@@ -80,141 +80,148 @@ __device__ __forceinline__ void block_store3(double a, double b, double c, doubl
 }
 
 template <class T, int SHAPE>
-__global__ void __launch_bounds__(NT) pass_kernel(const __grid_constant__ PassArgs<T> a) {
+__global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 1 : ((SHAPE == FE || SHAPE == R1 || SHAPE == R2 || SHAPE == R0) ? 2 : 3))
+pass_kernel(const __grid_constant__ PassArgs<T> a) {
   using C = typename Cx<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* sm = reinterpret_cast<C*>(smem_raw);
   const int tid = threadIdx.x;
   const uint32_t base = tile_base(a.tile, blockIdx.x);
-  const uint32_t off0 = base + scatter(a.tile, tj<0>(0, tid));
-  const uint32_t off2 = base + scatter(a.tile, tj<2>(0, tid));
-  uint32_t ro0[R], ro2[R];
-  reg_offsets<0>(a.tile, ro0);
-  reg_offsets<2>(a.tile, ro2);
-
-  constexpr bool NEEDS_Q = SHAPE == F0 || SHAPE == F1 || SHAPE == FE || SHAPE == FV ||
-                           SHAPE == R1 || SHAPE == R0;
+  const uint32_t off0 = base + toff(a.tile, tj<0>(0, tid));
+  const uint32_t off2 = base + toff(a.tile, tj<2>(0, tid));
+  // storage-form parity of the thread's own index bits in each layout
+  const uint32_t bpar = __popc(base) & 1u;
+  const uint32_t tp0 = bpar ^ (__popc(tj<0>(0, tid)) & 1u);
+  const uint32_t tp1 = bpar ^ (__popc(tj<1>(0, tid)) & 1u);
+  const uint32_t tp2 = bpar ^ (__popc(tj<2>(0, tid)) & 1u);
   T qv[R];
-  if constexpr (NEEDS_Q) {
+
+  // phase exp(-+i gamma q) on the amplitudes of layout 2 (dir = +1 forward, -1 adjoint)
+  auto phase2 = [&](C (&v)[R], T dir) {
 #pragma unroll
-    for (int r = 0; r < R; ++r) qv[r] = __ldcs(a.q + off2 + ro2[r]);
-  }
+    for (int r = 0; r < R; ++r) {
+      T c, s;
+      phase_cs(qv[r], a.ph0, a.ph1, c, s);
+      s = (tp2 ^ (uint32_t)cpar(tj<2>(r, 0))) ? -dir * s : dir * s;
+      v[r] = phase_mul(v[r], c, s);
+    }
+  };
 
   C v[R];
   if constexpr (SHAPE == F0) {
     if (a.gen_init) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) { v[r].x = a.init_amp; v[r].y = T(0); }
+      for (int r = 0; r < R; ++r) {
+        const bool sw = tp2 ^ (uint32_t)cpar(tj<2>(r, 0));
+        v[r].x = sw ? T(0) : a.init_amp;
+        v[r].y = sw ? a.init_amp : T(0);
+      }
     } else {
-      gload<2>(v, a.psi_in, off2, ro2);
+      gload_normal<2>(v, a.psi_in, off2, a.tile, tp2);
     }
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      T c, s;
-      phase_cs(qv[r], a.ph0, a.ph1, c, s);
-      v[r] = cmul_conj(v[r], c, s);
-    }
-    rot_layout<2>(v, a.mask_aft, a.ca, a.sa);
+    qload<2>(qv, a.q, off2, a.tile);
+    phase2(v, T(1));
+    rot_layout<2>(v, a.mask_aft, a.ca, a.sa, tp2);
     xchg<2, 1>(v, sm, tid);
-    rot_layout<1>(v, a.mask_aft, a.ca, a.sa);
+    rot_layout<1>(v, a.mask_aft, a.ca, a.sa, tp1);
     xchg<1, 0>(v, sm, tid);
-    rot_layout<0>(v, a.mask_aft, a.ca, a.sa);
-    gstore<0>(v, a.psi_out, off0, ro0);
+    rot_layout<0>(v, a.mask_aft, a.ca, a.sa, tp0);
+    gstore<0>(v, a.psi_out, off0, a.tile);
   } else if constexpr (SHAPE == F1) {
-    gload<0>(v, a.psi_in, off0, ro0);
-    rot_layout<0>(v, a.mask_bef, a.cb, a.sb);
+    gload<0>(v, a.psi_in, off0, a.tile);
+    rot_layout<0>(v, a.mask_bef, a.cb, a.sb, tp0);
     xchg<0, 1>(v, sm, tid);
-    rot_layout<1>(v, a.mask_bef, a.cb, a.sb);
+    rot_layout<1>(v, a.mask_bef, a.cb, a.sb, tp1);
+    qload<2>(qv, a.q, off2, a.tile);
     xchg<1, 2>(v, sm, tid);
-    rot_layout<2>(v, a.mask_bef, a.cb, a.sb);
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      T c, s;
-      phase_cs(qv[r], a.ph0, a.ph1, c, s);
-      v[r] = cmul_conj(v[r], c, s);
-    }
-    rot_layout<2>(v, a.mask_aft, a.ca, a.sa);
+    rot_layout<2>(v, a.mask_bef, a.cb, a.sb, tp2);
+    phase2(v, T(1));
+    rot_layout<2>(v, a.mask_aft, a.ca, a.sa, tp2);
     xchg<2, 1>(v, sm, tid);
-    rot_layout<1>(v, a.mask_aft, a.ca, a.sa);
+    rot_layout<1>(v, a.mask_aft, a.ca, a.sa, tp1);
     xchg<1, 0>(v, sm, tid);
-    rot_layout<0>(v, a.mask_aft, a.ca, a.sa);
-    gstore<0>(v, a.psi_out, off0, ro0);
+    rot_layout<0>(v, a.mask_aft, a.ca, a.sa, tp0);
+    gstore<0>(v, a.psi_out, off0, a.tile);
   } else if constexpr (SHAPE == F2) {
-    gload<0>(v, a.psi_in, off0, ro0);
-    rot_layout<0>(v, a.mask_bef, a.cb, a.sb);
+    gload<0>(v, a.psi_in, off0, a.tile);
+    rot_layout<0>(v, a.mask_bef, a.cb, a.sb, tp0);
     xchg<0, 1>(v, sm, tid);
-    rot_layout<1>(v, a.mask_bef, a.cb, a.sb);
+    rot_layout<1>(v, a.mask_bef, a.cb, a.sb, tp1);
     xchg<1, 2>(v, sm, tid);
-    rot_layout<2>(v, a.mask_bef, a.cb, a.sb);
-    gstore<2>(v, a.psi_out, off2, ro2);
+    rot_layout<2>(v, a.mask_bef, a.cb, a.sb, tp2);
+    gstore<2>(v, a.psi_out, off2, a.tile);
   } else if constexpr (SHAPE == FE || SHAPE == FV) {
-    gload<0>(v, a.psi_in, off0, ro0);
-    rot_layout<0>(v, a.mask_bef, a.cb, a.sb);
+    gload<0>(v, a.psi_in, off0, a.tile);
+    rot_layout<0>(v, a.mask_bef, a.cb, a.sb, tp0);
     xchg<0, 1>(v, sm, tid);
-    rot_layout<1>(v, a.mask_bef, a.cb, a.sb);
+    rot_layout<1>(v, a.mask_bef, a.cb, a.sb, tp1);
+    qload<2>(qv, a.q, off2, a.tile);
     xchg<1, 2>(v, sm, tid);
-    rot_layout<2>(v, a.mask_bef, a.cb, a.sb);
+    rot_layout<2>(v, a.mask_bef, a.cb, a.sb, tp2);
     T e = T(0);
 #pragma unroll
     for (int r = 0; r < R; ++r) e += qv[r] * (v[r].x * v[r].x + v[r].y * v[r].y);
     if constexpr (SHAPE == FV) {
-      gstore<2>(v, a.psi_out, off2, ro2);
+      gstore_normal<2>(v, a.psi_out, off2, a.tile, tp2);
       block_store3((double)e, 0.0, 0.0, a.part, a.row_E, -1, -1, tid);
     } else {
       C l[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) { l[r].x = qv[r] * v[r].x; l[r].y = qv[r] * v[r].y; }
       T acc = T(0);
-      unrot_layout_acc<2>(v, l, a.mask_bef, a.cb, a.sb, acc);
+      unrot_layout_acc<2>(v, l, a.mask_bef, a.cb, a.sb, tp2, acc);
       xchg2<2, 1>(v, l, sm, tid);
-      unrot_layout_acc<1>(v, l, a.mask_bef, a.cb, a.sb, acc);
+      unrot_layout_acc<1>(v, l, a.mask_bef, a.cb, a.sb, tp1, acc);
       xchg2<1, 0>(v, l, sm, tid);
-      unrot_layout_acc<0>(v, l, a.mask_bef, a.cb, a.sb, acc);
-      gstore<0>(l, a.lam_out, off0, ro0);
+      unrot_layout_acc<0>(v, l, a.mask_bef, a.cb, a.sb, tp0, acc);
+      gstore<0>(l, a.lam_out, off0, a.tile);
       block_store3((double)e, 2.0 * (double)acc, 0.0, a.part, a.row_E, a.row_bef, -1, tid);
     }
   } else if constexpr (SHAPE == R1 || SHAPE == R0) {
     C l[R];
-    gload<0>(v, a.psi_in, off0, ro0);
-    gload<0>(l, a.lam_in, off0, ro0);
+    gload<0>(v, a.psi_in, off0, a.tile);
+    gload<0>(l, a.lam_in, off0, a.tile);
     T acc_a = T(0), acc_b = T(0), acc_g = T(0);
-    unrot_layout_acc<0>(v, l, a.mask_aft, a.ca, a.sa, acc_a);
+    unrot_layout_acc<0>(v, l, a.mask_aft, a.ca, a.sa, tp0, acc_a);
     xchg2<0, 1>(v, l, sm, tid);
-    unrot_layout_acc<1>(v, l, a.mask_aft, a.ca, a.sa, acc_a);
+    unrot_layout_acc<1>(v, l, a.mask_aft, a.ca, a.sa, tp1, acc_a);
+    qload<2>(qv, a.q, off2, a.tile);
     xchg2<1, 2>(v, l, sm, tid);
-    unrot_layout_acc<2>(v, l, a.mask_aft, a.ca, a.sa, acc_a);
-#pragma unroll
-    for (int r = 0; r < R; ++r) acc_g += qv[r] * imdot(l[r], v[r]);
-    if constexpr (SHAPE == R1) {
+    unrot_layout_acc<2>(v, l, a.mask_aft, a.ca, a.sa, tp2, acc_a);
+    {
+      T ge = T(0), go = T(0);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        T c, s;
-        phase_cs(qv[r], a.ph0, a.ph1, c, s);
-        v[r] = cmul_conj(v[r], c, -s);
-        l[r] = cmul_conj(l[r], c, -s);
+        if (cpar(tj<2>(r, 0))) go += qv[r] * imdot_st(l[r], v[r]);
+        else ge += qv[r] * imdot_st(l[r], v[r]);
       }
-      unrot_layout_acc<2>(v, l, a.mask_bef, a.cb, a.sb, acc_b);
+      acc_g = tp2 ? (go - ge) : (ge - go);
+    }
+    if constexpr (SHAPE == R1) {
+      phase2(v, T(-1));
+      phase2(l, T(-1));
+      unrot_layout_acc<2>(v, l, a.mask_bef, a.cb, a.sb, tp2, acc_b);
       xchg2<2, 1>(v, l, sm, tid);
-      unrot_layout_acc<1>(v, l, a.mask_bef, a.cb, a.sb, acc_b);
+      unrot_layout_acc<1>(v, l, a.mask_bef, a.cb, a.sb, tp1, acc_b);
       xchg2<1, 0>(v, l, sm, tid);
-      unrot_layout_acc<0>(v, l, a.mask_bef, a.cb, a.sb, acc_b);
-      gstore<0>(l, a.lam_out, off0, ro0);
-      if (a.psi_out) gstore<0>(v, a.psi_out, off0, ro0);
+      unrot_layout_acc<0>(v, l, a.mask_bef, a.cb, a.sb, tp0, acc_b);
+      gstore<0>(l, a.lam_out, off0, a.tile);
+      if (a.psi_out) gstore<0>(v, a.psi_out, off0, a.tile);
     }
     block_store3(2.0 * (double)acc_b, 2.0 * (double)acc_a, 2.0 * (double)acc_g, a.part, a.row_bef,
                  a.row_aft, a.row_gam, tid);
   } else if constexpr (SHAPE == R2) {
     C l[R];
-    gload<2>(v, a.psi_in, off2, ro2);
-    gload<2>(l, a.lam_in, off2, ro2);
+    gload<2>(v, a.psi_in, off2, a.tile);
+    gload<2>(l, a.lam_in, off2, a.tile);
     T acc_b = T(0);
-    unrot_layout_acc<2>(v, l, a.mask_bef, a.cb, a.sb, acc_b);
+    unrot_layout_acc<2>(v, l, a.mask_bef, a.cb, a.sb, tp2, acc_b);
     xchg2<2, 1>(v, l, sm, tid);
-    unrot_layout_acc<1>(v, l, a.mask_bef, a.cb, a.sb, acc_b);
+    unrot_layout_acc<1>(v, l, a.mask_bef, a.cb, a.sb, tp1, acc_b);
     xchg2<1, 0>(v, l, sm, tid);
-    unrot_layout_acc<0>(v, l, a.mask_bef, a.cb, a.sb, acc_b);
-    gstore<0>(l, a.lam_out, off0, ro0);
-    if (a.psi_out) gstore<0>(v, a.psi_out, off0, ro0);
+    unrot_layout_acc<0>(v, l, a.mask_bef, a.cb, a.sb, tp0, acc_b);
+    gstore<0>(l, a.lam_out, off0, a.tile);
+    if (a.psi_out) gstore<0>(v, a.psi_out, off0, a.tile);
     block_store3(2.0 * (double)acc_b, 0.0, 0.0, a.part, a.row_bef, -1, -1, tid);
   }
 }
@@ -255,7 +262,7 @@ __device__ void small_rotate(typename Cx<T>::t* s, int n, T c, T sn) {
     const int h = 1 << b;
     for (int k = threadIdx.x; k < dim / 2; k += blockDim.x) {
       const int i = ((k >> b) << (b + 1)) | (k & (h - 1));
-      rot(s[i], s[i | h], c, sn);
+      rot_normal(s[i], s[i | h], c, sn);
     }
     __syncthreads();
   }
@@ -352,8 +359,8 @@ struct Plan {
 
 static Tile make_tile(int n, int s, int hfirst, int nh) {
   Tile t{};
-  for (int b = 0; b < s; ++b) t.bitoff[b] = 1u << b;
-  for (int i = 0; i < nh; ++i) t.bitoff[s + i] = 1u << (hfirst + i);
+  t.smask = (1u << s) - 1u;
+  t.hshift = hfirst - s;
   int k = 0;
   for (int b = 0; b < n; ++b) {
     const bool in_tile = (b < s) || (b >= hfirst && b < hfirst + nh);
@@ -428,16 +435,10 @@ static void fill_angles(PassArgs<T>& a, const PassInfo& pi, const double* gammas
   }
 }
 
-template <class T>
-static size_t smem_bytes(int shape) {
-  const bool two = shape == FE || shape == R1 || shape == R2 || shape == R0;
-  (void)two;
-  return (size_t)TILE * sizeof(typename Cx<T>::t);
-}
-
 template <class T, int S>
 static int launch_one(const PassArgs<T>& a, uint32_t grid, cudaStream_t st) {
-  const size_t sm = (size_t)TILE * sizeof(typename Cx<T>::t);
+  constexpr bool two = S == FE || S == R1 || S == R2 || S == R0;
+  const size_t sm = (two ? 2 : 1) * (size_t)TILE * sizeof(typename Cx<T>::t);
   static bool configured = false;   // per instantiation
   if (!configured) {
     QVS_CUDA_TRY(cudaFuncSetAttribute(pass_kernel<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -1,10 +1,494 @@
-// QAOAz sparse-mixer path (Sec. 2.4.1, Sec. 3) - placeholder until the Chebyshev kernels land.
+// QAOAz sparse-mixer path (Sec. 2.4.1, Sec. 3): exp(-i t W) v for a real symmetric CSR matrix W
+// by a Chebyshev expansion,
+//     exp(-i t W) v = e^{-i t a} sum_m (2 - delta_m0) (-i)^m J_m(b t) T_m(W~) v,  W~ = (W - a) / b,
+// with [a - b, a + b] enclosing the spectrum (Gershgorin when no bounds are given). The series is
+// cut at the first K whose tail bound sum_{m > K} 2 |J_m(b t)| falls below the tolerance (the
+// truncation error in the 2-norm is at most that bound since |T_m| <= 1 on [-1, 1]). Coefficients
+// are computed in fp64 on the host; each term is one fused kernel: a CSR SpMV of T_m (four lanes per
+// row, gathers served from L2), the three-term recurrence and the accumulation into y.
+//
+// Gradient: the subspace vectors are small (C(24,12) complex64 amplitudes = 21.6 MB), so every
+// phi_k and psi_k of the forward sweep is stored and the adjoint sweep moves only lambda:
+//   df/dt_k     = 2 Im <lambda_k | W psi_k>      (one SpMV fused with the inner product)
+//   df/dgamma_k = 2 Im <M_k^dag lambda_k | Q phi_k>.
+#include <math.h>
+
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <functional>
+#include <vector>
+
 #include "qvs_internal.h"
 
 namespace qvs {
-int csr_set_mixer(qvs_ctx*, const qvs_mixer_desc*) { return QVS_EUNSUPPORTED; }
-int csr_evolve(qvs_ctx*, int, const double*, const double*) { return QVS_EUNSUPPORTED; }
-int csr_gradient(qvs_ctx*, int, const double*, const double*, double*, double*, double*) {
-  return QVS_EUNSUPPORTED;
+namespace cs {
+
+constexpr int NT = 256;
+constexpr int LPR = 4;                 // lanes per row
+constexpr int ROWS_PER_CTA = NT / LPR;
+constexpr int RED_GRID = 152 * 8;      // CTAs of the elementwise/reduction kernels
+
+struct StepArgs {
+  int64_t dim;
+  const uint32_t* rowptr;
+  const int32_t* colind;
+  const float* values;        // NULL = implicit value
+  float implicit_value;
+  float inv_b, a_over_b;      // W~ = W / b - a / b
+  float alpha, beta;          // T_next = alpha W~ T_cur - beta T_prev
+  float2 c;                   // coefficient of T_next added to y
+  const float2* tcur;
+  const float2* tprev;        // may be NULL when beta == 0
+  float2* tnext;
+  float2* y;                  // y += c * T_next
+  int y_init;                 // 1: y = c0 * tcur + c * tnext (first term folded in)
+  float2 c0;
+};
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
+
+// sum over the row's nonzeros of value * x[col], by LPR lanes. Every lane of the warp must call
+// it (the lane sum uses full-warp shuffles); lanes past the last row pass valid = false.
+__device__ __forceinline__ float2 row_spmv(const uint32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+                                           const float* __restrict__ values, float iv,
+                                           const float2* __restrict__ x, int64_t row, int lane, bool valid) {
+  float2 acc = make_float2(0.f, 0.f);
+  uint32_t b = 0, e = 0;
+  if (valid) {
+    b = __ldg(rowptr + row);
+    e = __ldg(rowptr + row + 1);
+  }
+  for (uint32_t j = b + lane; j < e; j += LPR) {
+    const int32_t c = __ldcs(colind + j);
+    const float v = values ? __ldcs(values + j) : iv;
+    const float2 t = __ldg(x + c);
+    acc.x = fmaf(v, t.x, acc.x);
+    acc.y = fmaf(v, t.y, acc.y);
+  }
+#pragma unroll
+  for (int o = LPR / 2; o; o >>= 1) {
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+  }
+  return acc;
+}
+
+__global__ void __launch_bounds__(NT) cheb_step_kernel(const __grid_constant__ StepArgs a) {
+  const int lane = threadIdx.x & (LPR - 1);
+  const int64_t row = (int64_t)blockIdx.x * ROWS_PER_CTA + (threadIdx.x / LPR);
+  const bool valid = row < a.dim;
+  const float2 wx = row_spmv(a.rowptr, a.colind, a.values, a.implicit_value, a.tcur, row, lane, valid);
+  if (lane != 0 || !valid) return;
+  const float2 tc = a.tcur[row];
+  // W~ x = (W x) / b - (a / b) x
+  float2 t = make_float2(a.alpha * (wx.x * a.inv_b - a.a_over_b * tc.x),
+                         a.alpha * (wx.y * a.inv_b - a.a_over_b * tc.y));
+  if (a.tprev) {
+    const float2 tp = a.tprev[row];
+    t.x -= a.beta * tp.x;
+    t.y -= a.beta * tp.y;
+  }
+  a.tnext[row] = t;
+  const float2 ct = cmulf(a.c, t);
+  if (a.y_init) {
+    const float2 c0 = cmulf(a.c0, tc);
+    a.y[row] = make_float2(c0.x + ct.x, c0.y + ct.y);
+  } else {
+    const float2 yo = a.y[row];
+    a.y[row] = make_float2(yo.x + ct.x, yo.y + ct.y);
+  }
+}
+
+// y = c0 * x (a single-term series, bt == 0)
+__global__ void scale_kernel(int64_t dim, float2 c0, const float2* __restrict__ x, float2* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < dim; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = cmulf(c0, x[i]);
+}
+
+// fractional turns of gamma q (gamma / 2pi as float-float, q exact in fp32)
+__device__ __forceinline__ void phase_cs(float q, float gh, float gl, float& c, float& s) {
+  const float p = gh * q;
+  const float e = fmaf(gh, q, -p) + gl * q;
+  __sincosf(6.28318530717958647692f * ((p - rintf(p)) + e), &s, &c);
+}
+
+__device__ __forceinline__ void block_store(float v, double scale, double* part, int row) {
+  __shared__ double red[NT / 32];
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < NT / 32; ++w) s += red[w];
+    part[(size_t)row * gridDim.x + blockIdx.x] = scale * s;
+  }
+}
+
+enum EwMode : int { PH_FWD = 0, PH_REV = 1, E_LAM = 2, E_ONLY = 3 };
+
+struct EwArgs {
+  int64_t dim;
+  const float* q;
+  const float2* in;       // PH_FWD: psi; PH_REV: phi (stored); E_*: psi
+  float2* out;            // PH_FWD: phi; PH_REV: lambda (in place); E_LAM: lambda
+  float gh, gl;
+  float init_amp;         // PH_FWD with in == NULL: uniform psi0
+  double* part;
+  int row;
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(NT) ew_kernel(const __grid_constant__ EwArgs a) {
+  float acc = 0.f;
+  for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < a.dim; i += (int64_t)gridDim.x * NT) {
+    const float q = a.q[i];
+    if constexpr (MODE == PH_FWD) {
+      const float2 v = a.in ? a.in[i] : make_float2(a.init_amp, 0.f);
+      float c, s;
+      phase_cs(q, a.gh, a.gl, c, s);
+      a.out[i] = make_float2(c * v.x + s * v.y, c * v.y - s * v.x);
+    } else if constexpr (MODE == PH_REV) {
+      const float2 ph = a.in[i];
+      const float2 l = a.out[i];
+      acc += q * (l.x * ph.y - l.y * ph.x);
+      float c, s;
+      phase_cs(q, a.gh, a.gl, c, s);
+      a.out[i] = make_float2(c * l.x - s * l.y, c * l.y + s * l.x);
+    } else {
+      const float2 v = a.in[i];
+      acc += q * (v.x * v.x + v.y * v.y);
+      if constexpr (MODE == E_LAM) a.out[i] = make_float2(q * v.x, q * v.y);
+    }
+  }
+  if constexpr (MODE != PH_FWD) block_store(acc, MODE == PH_REV ? 2.0 : 1.0, a.part, a.row);
+}
+
+// df/dt partial: 2 Im sum_row conj(lambda_row) (W psi)_row
+__global__ void __launch_bounds__(NT) dt_kernel(int64_t dim, const uint32_t* __restrict__ rowptr,
+                                                const int32_t* __restrict__ colind, const float* __restrict__ values,
+                                                float iv, const float2* __restrict__ psi,
+                                                const float2* __restrict__ lam, double* part, int prow,
+                                                int nchunks) {
+  const int lane = threadIdx.x & (LPR - 1);
+  float acc = 0.f;
+  // CTA b handles row blocks b, b + gridDim.x, ...
+  for (int chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
+    const int64_t row = (int64_t)chunk * ROWS_PER_CTA + (threadIdx.x / LPR);
+    const bool valid = row < dim;
+    const float2 wx = row_spmv(rowptr, colind, values, iv, psi, row, lane, valid);
+    if (lane == 0 && valid) {
+      const float2 l = lam[row];
+      acc += l.x * wx.y - l.y * wx.x;
+    }
+  }
+  block_store(acc, 2.0, part, prow);
+}
+
+__global__ void gershgorin_kernel(int64_t dim, const uint32_t* rowptr, const float* values, float iv,
+                                  unsigned int* out_bits) {
+  float m = 0.f;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < dim; r += (int64_t)gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (uint32_t j = rowptr[r]; j < rowptr[r + 1]; ++j) s += fabsf(values ? values[j] : iv);
+    m = fmaxf(m, s);
+  }
+  atomicMax(out_bits, __float_as_uint(m));   // non-negative floats order like their bit patterns
+}
+
+__global__ void rowptr32_kernel(int64_t n1, const int64_t* __restrict__ in, uint32_t* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n1; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (uint32_t)in[i];
+}
+
+// ---------------------------------------------------------------- host side
+
+// Chebyshev coefficients c_m = (2 - delta_m0) (-i)^m J_m(b t) e^{-i t a}, cut where the tail bound
+// sum_{m > K} 2 |J_m(b t)| < tol. Returns K + 1 coefficients, or an empty vector if none fits.
+static std::vector<double> cheb_coeffs(double a, double b, double t, double tol, int kmax, double* tail_out) {
+  const double x = b * t;
+  const double ax = fabs(x);
+  const int mmax = (int)std::min<double>(kmax + 64.0, ax + 60.0 + 8.0 * std::cbrt(ax + 1.0));
+  std::vector<double> J(mmax + 1);
+  for (int m = 0; m <= mmax; ++m) J[m] = std::cyl_bessel_j((double)m, ax) * ((x < 0 && (m & 1)) ? -1.0 : 1.0);
+  // tail sums
+  std::vector<double> tail(mmax + 2, 0.0);
+  for (int m = mmax; m >= 0; --m) tail[m] = tail[m + 1] + 2.0 * fabs(J[m]);
+  int K = -1;
+  for (int m = 0; m < mmax; ++m)
+    if (tail[m + 1] < tol) { K = m; break; }
+  if (K < 0 || K > kmax) return {};
+  if (tail_out) *tail_out = tail[K + 1];
+  std::vector<double> c(2 * (size_t)(K + 1));
+  const double ca = cos(t * a), sa = -sin(t * a);   // e^{-i t a}
+  for (int m = 0; m <= K; ++m) {
+    const double w = (m == 0 ? 1.0 : 2.0) * J[m];
+    // (-i)^m
+    double re, im;
+    switch (m & 3) {
+      case 0: re = w; im = 0; break;
+      case 1: re = 0; im = -w; break;
+      case 2: re = -w; im = 0; break;
+      default: re = 0; im = w; break;
+    }
+    c[2 * m] = re * ca - im * sa;
+    c[2 * m + 1] = re * sa + im * ca;
+  }
+  return c;
+}
+
+static int launch_prof(qvs_ctx* h, const char* name, double bytes, int64_t& launches,
+                       const std::function<void()>& fn) {
+  cudaEvent_t e0;
+  QVS_TRY(prof_begin(h, &e0));
+  fn();
+  QVS_CUDA_TRY(cudaGetLastError());
+  ++launches;
+  return prof_end(h, name, bytes, e0);
+}
+
+// y = exp(-i t W) x (sign = +1) or exp(+i t W) x (sign = -1); uses three scratch vectors.
+static int expmv(qvs_ctx* h, double t, const float2* x, float2* y, float2* s0, float2* s1, float2* s2,
+                 int64_t& launches) {
+  const int64_t dim = h->dim;
+  const CsrData& C = h->csr;
+  const double a = 0.5 * (C.spec_hi + C.spec_lo), b = 0.5 * (C.spec_hi - C.spec_lo);
+  double tail = 0.0;
+  const std::vector<double> c = cheb_coeffs(a, b, t, C.tol, 20000, &tail);
+  if (c.empty()) return QVS_ENUMERIC;
+  const int K = (int)(c.size() / 2) - 1;
+  const uint32_t grid = (uint32_t)((dim + ROWS_PER_CTA - 1) / ROWS_PER_CTA);
+  const double nnz = (double)C.nnz;
+  const double step_bytes = nnz * 4.0 + (C.has_values ? nnz * 4.0 : 0.0) + (double)dim * (4.0 + 8 + 8 + 8 + 16);
+  if (K == 0) {
+    return launch_prof(h, "csr_scale", 16.0 * dim, launches, [&] {
+      scale_kernel<<<RED_GRID, NT, 0, h->stream>>>(dim, make_float2((float)c[0], (float)c[1]), x, y);
+    });
+  }
+  StepArgs s{};
+  s.dim = dim;
+  s.rowptr = C.rowptr.as<uint32_t>();
+  s.colind = C.colind.as<int32_t>();
+  s.values = C.has_values ? C.values.as<float>() : nullptr;
+  s.implicit_value = C.implicit_value;
+  s.inv_b = (float)(1.0 / b);
+  s.a_over_b = (float)(a / b);
+  // T_0 = x, T_1 = W~ x, y = c0 T_0 + c1 T_1
+  float2* bufs[3] = {s0, s1, s2};
+  const float2* tprev = nullptr;
+  const float2* tcur = x;
+  for (int m = 1; m <= K; ++m) {
+    float2* tnext = bufs[m % 3];
+    if (tnext == tcur || tnext == tprev) tnext = bufs[(m + 1) % 3];
+    s.alpha = m == 1 ? 1.f : 2.f;
+    s.beta = m == 1 ? 0.f : 1.f;
+    s.tcur = tcur;
+    s.tprev = m == 1 ? nullptr : tprev;
+    s.tnext = tnext;
+    s.y = y;
+    s.c = make_float2((float)c[2 * m], (float)c[2 * m + 1]);
+    s.y_init = m == 1 ? 1 : 0;
+    s.c0 = make_float2((float)c[0], (float)c[1]);
+    QVS_TRY(launch_prof(h, "csr_cheb_step", step_bytes, launches, [&] {
+      cheb_step_kernel<<<grid, NT, 0, h->stream>>>(s);
+    }));
+    tprev = tcur;
+    tcur = tnext;
+  }
+  return QVS_OK;
+}
+
+static int run(qvs_ctx* h, int p, const double* gammas, const double* ts, bool grad, double* E, double* dg,
+               double* dt) {
+  const int64_t dim = h->dim;
+  const size_t vb = sizeof(float2) * (size_t)dim;
+  // vectors: work (psi / y), 3 recurrence buffers, lambda, and for the gradient phi_k, psi_k
+  QVS_TRY(h->psi.ensure(vb));
+  QVS_TRY(h->work.ensure(vb * 3));
+  if (grad) {
+    QVS_TRY(h->lam.ensure(vb * 2));
+    QVS_TRY(h->ckpt.ensure(vb * (size_t)(2 * p)));
+  }
+  const int nslots = 1 + 2 * p;
+  QVS_TRY(h->part.ensure(sizeof(double) * (size_t)nslots * RED_GRID));
+  QVS_TRY(h->res.ensure(sizeof(double) * nslots));
+  QVS_TRY(h->rowmap.ensure(sizeof(int) * 3 * nslots));
+  std::vector<int> rowmap(3 * (size_t)nslots, -1);
+  for (int s = 0; s < nslots; ++s) rowmap[3 * s] = s;
+  QVS_CUDA_TRY(cudaMemcpyAsync(h->rowmap.ptr, rowmap.data(), sizeof(int) * rowmap.size(), cudaMemcpyHostToDevice,
+                               h->stream));
+  float2* W = h->psi.as<float2>();
+  float2* S = h->work.as<float2>();
+  float2* s0 = S;
+  float2* s1 = S + dim;
+  float2* s2 = S + 2 * dim;
+  float2* phiK = grad ? h->ckpt.as<float2>() : nullptr;        // phi_k, k = 1..p
+  float2* psiK = grad ? phiK + (size_t)p * dim : nullptr;      // psi_k, k = 1..p
+  int64_t launches = 0;
+  const float amp = (float)(1.0 / sqrt((double)dim));
+  const float* q = h->q.as<float>();
+  const float2* psi0 = h->have_psi0 ? h->psi0.as<float2>() : nullptr;
+  auto ew = [&](int mode, EwArgs e, double bytes) -> int {
+    static const char* names[] = {"csr_phase", "csr_phase_adjoint", "csr_expect_lambda", "csr_expect"};
+    return launch_prof(h, names[mode], bytes * (double)dim, launches, [&] {
+      switch (mode) {
+        case PH_FWD: ew_kernel<PH_FWD><<<RED_GRID, NT, 0, h->stream>>>(e); break;
+        case PH_REV: ew_kernel<PH_REV><<<RED_GRID, NT, 0, h->stream>>>(e); break;
+        case E_LAM: ew_kernel<E_LAM><<<RED_GRID, NT, 0, h->stream>>>(e); break;
+        case E_ONLY: ew_kernel<E_ONLY><<<RED_GRID, NT, 0, h->stream>>>(e); break;
+      }
+    });
+  };
+  // forward (evolve mode: phi in lam[0..dim), the state in W)
+  if (!grad) QVS_TRY(h->lam.ensure(vb * 2));
+  const float2* cur = psi0;   // NULL = uniform
+  for (int k = 0; k < p; ++k) {
+    float2* phi = grad ? phiK + (size_t)k * dim : h->lam.as<float2>();
+    float2* out = grad ? psiK + (size_t)k * dim : W;
+    EwArgs e{};
+    e.dim = dim;
+    e.q = q;
+    e.in = cur;
+    e.out = phi;
+    turns_split(gammas[k], &e.gh, &e.gl);
+    e.init_amp = amp;
+    QVS_TRY(ew(PH_FWD, e, 4.0 + 8.0 + (cur ? 8.0 : 0.0)));
+    QVS_TRY(expmv(h, ts[k], phi, out, s0, s1, s2, launches));
+    cur = out;
+  }
+  {
+    EwArgs e{};
+    e.dim = dim;
+    e.q = q;
+    e.in = cur;
+    e.part = h->part.as<double>();
+    e.row = 0;
+    if (grad) {
+      e.out = h->lam.as<float2>();
+      QVS_TRY(ew(E_LAM, e, 4.0 + 16.0));
+    } else {
+      QVS_TRY(ew(E_ONLY, e, 4.0 + 8.0));
+    }
+  }
+  if (grad) {
+    float2* lam = h->lam.as<float2>();
+    float2* lam2 = lam + dim;
+    const CsrData& C = h->csr;
+    const int nchunks = (int)((dim + ROWS_PER_CTA - 1) / ROWS_PER_CTA);
+    for (int k = p - 1; k >= 0; --k) {
+      const float2* psik = psiK + (size_t)k * dim;
+      QVS_TRY(launch_prof(h, "csr_dt", (double)C.nnz * 4.0 + (double)dim * 20.0, launches, [&] {
+        dt_kernel<<<RED_GRID, NT, 0, h->stream>>>(dim, C.rowptr.as<uint32_t>(), C.colind.as<int32_t>(),
+                                                  C.has_values ? C.values.as<float>() : nullptr, C.implicit_value,
+                                                  psik, lam, h->part.as<double>(), 1 + p + k, nchunks);
+      }));
+      QVS_TRY(expmv(h, -ts[k], lam, lam2, s0, s1, s2, launches));
+      std::swap(lam, lam2);
+      EwArgs e{};
+      e.dim = dim;
+      e.q = q;
+      e.in = phiK + (size_t)k * dim;
+      e.out = lam;
+      turns_split(gammas[k], &e.gh, &e.gl);
+      e.part = h->part.as<double>();
+      e.row = 1 + k;
+      QVS_TRY(ew(PH_REV, e, 4.0 + 8.0 + 16.0));
+    }
+  }
+  const int nout = grad ? nslots : 1;
+  QVS_TRY(launch_prof(h, "reduce_rows", 8.0 * RED_GRID * nout, launches, [&] {
+    reduce_rows(h, h->part.as<double>(), RED_GRID, h->rowmap.as<int>(), nout, h->res.as<double>());
+  }));
+  h->launches = launches;
+  QVS_TRY(ensure_host_res(h, p));
+  QVS_CUDA_TRY(cudaMemcpyAsync(h->host_res, h->res.ptr, sizeof(double) * nout, cudaMemcpyDeviceToHost, h->stream));
+  QVS_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  QVS_TRY(prof_flush(h));
+  *E = h->host_res[0];
+  if (grad)
+    for (int k = 0; k < p; ++k) {
+      dg[k] = h->host_res[1 + k];
+      dt[k] = h->host_res[1 + p + k];
+    }
+  return QVS_OK;
+}
+
+}  // namespace cs
+
+int csr_set_mixer(qvs_ctx* h, const qvs_mixer_desc* d) {
+  using namespace cs;
+  if (h->precision != QVS_C64) return QVS_EUNSUPPORTED;
+  const int64_t dim = h->dim;
+  if (!d->rowptr || !d->colind || d->nnz < 0 || d->nnz >= (int64_t(1) << 32)) return QVS_EINVAL;
+  if (!(d->cheb_tol >= 0.0) || !isfinite(d->spec_lo) || !isfinite(d->spec_hi)) return QVS_EINVAL;
+  CsrData& C = h->csr;
+  const int64_t nnz = d->nnz;
+  const auto kind = d->csr_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (!d->csr_on_device) {
+    if (d->rowptr[0] != 0 || d->rowptr[dim] != nnz) return QVS_EINVAL;
+    for (int64_t r = 0; r < dim; ++r)
+      if (d->rowptr[r + 1] < d->rowptr[r]) return QVS_EINVAL;
+    for (int64_t j = 0; j < nnz; ++j)
+      if (d->colind[j] < 0 || d->colind[j] >= dim) return QVS_EINVAL;
+  }
+  // rowptr: staged as int64 in work, narrowed to uint32 on the device
+  QVS_TRY(h->work.ensure(sizeof(int64_t) * (size_t)(dim + 1)));
+  QVS_CUDA_TRY(cudaMemcpyAsync(h->work.ptr, d->rowptr, sizeof(int64_t) * (dim + 1), kind, h->stream));
+  QVS_TRY(C.rowptr.ensure(sizeof(uint32_t) * (size_t)(dim + 1)));
+  rowptr32_kernel<<<RED_GRID, NT, 0, h->stream>>>(dim + 1, h->work.as<int64_t>(), C.rowptr.as<uint32_t>());
+  QVS_CUDA_TRY(cudaGetLastError());
+  QVS_TRY(C.colind.ensure(sizeof(int32_t) * (size_t)std::max<int64_t>(nnz, 1)));
+  if (nnz) QVS_CUDA_TRY(cudaMemcpyAsync(C.colind.ptr, d->colind, sizeof(int32_t) * nnz, kind, h->stream));
+  C.has_values = d->values != nullptr;
+  if (C.has_values) {
+    QVS_TRY(C.values.ensure(sizeof(float) * (size_t)std::max<int64_t>(nnz, 1)));
+    if (nnz) QVS_CUDA_TRY(cudaMemcpyAsync(C.values.ptr, d->values, sizeof(float) * nnz, kind, h->stream));
+  }
+  C.implicit_value = d->implicit_value;
+  C.nnz = nnz;
+  C.tol = d->cheb_tol > 0 ? d->cheb_tol : 1e-7;
+  if (d->spec_lo == 0.0 && d->spec_hi == 0.0) {
+    // Gershgorin: every eigenvalue of a matrix with zero diagonal lies within the largest
+    // absolute row sum of zero
+    unsigned int* bits = nullptr;
+    QVS_TRY(h->res.ensure(sizeof(double) * 8));
+    bits = reinterpret_cast<unsigned int*>(h->res.ptr);
+    QVS_CUDA_TRY(cudaMemsetAsync(bits, 0, sizeof(unsigned int), h->stream));
+    gershgorin_kernel<<<RED_GRID, NT, 0, h->stream>>>(dim, C.rowptr.as<uint32_t>(),
+                                                      C.has_values ? C.values.as<float>() : nullptr,
+                                                      C.implicit_value, bits);
+    QVS_CUDA_TRY(cudaGetLastError());
+    unsigned int hb = 0;
+    QVS_CUDA_TRY(cudaMemcpyAsync(&hb, bits, sizeof(hb), cudaMemcpyDeviceToHost, h->stream));
+    QVS_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    float g;
+    memcpy(&g, &hb, sizeof(g));
+    const double G = (double)g * (1.0 + 1e-6) + 1e-30;
+    C.spec_lo = -G;
+    C.spec_hi = G;
+  } else {
+    if (!(d->spec_hi > d->spec_lo)) return QVS_EINVAL;
+    C.spec_lo = d->spec_lo;
+    C.spec_hi = d->spec_hi;
+  }
+  QVS_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return QVS_OK;
+}
+
+int csr_evolve(qvs_ctx* h, int p, const double* gammas, const double* ts) {
+  double E = 0.0;
+  QVS_TRY(cs::run(h, p, gammas, ts, false, &E, nullptr, nullptr));
+  h->E = E;
+  h->have_E = true;
+  return QVS_OK;
+}
+
+int csr_gradient(qvs_ctx* h, int p, const double* gammas, const double* ts, double* E, double* dg, double* dt) {
+  return cs::run(h, p, gammas, ts, true, E, dg, dt);
+}
+
 }  // namespace qvs

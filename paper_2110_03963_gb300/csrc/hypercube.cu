@@ -54,9 +54,12 @@ struct PassArgs {
   int gen_init;         // F0: 1 = generate psi0 = init_amp, 0 = load psi_in
 };
 
-// Block sum of up to three values, written to their partial rows (rows < 0 skipped).
-__device__ __forceinline__ void block_store3(double a, double b, double c, double* part, int ra,
-                                             int rb, int rc, int tid) {
+// Block sum of up to three values, written to their partial rows (rows < 0 skipped). Lanes are
+// summed in the thread's precision (a warp holds 512 amplitude contributions), warps and CTAs in
+// fp64; the order is fixed, so results are reproducible run to run.
+template <class T>
+__device__ __forceinline__ void block_store3(T a, T b, T c, double* part, int ra, int rb, int rc,
+                                             int tid) {
   __shared__ double red[3][NT / 32];
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
@@ -65,9 +68,9 @@ __device__ __forceinline__ void block_store3(double a, double b, double c, doubl
     c += __shfl_xor_sync(0xffffffffu, c, o);
   }
   if ((tid & 31) == 0) {
-    red[0][tid >> 5] = a;
-    red[1][tid >> 5] = b;
-    red[2][tid >> 5] = c;
+    red[0][tid >> 5] = (double)a;
+    red[1][tid >> 5] = (double)b;
+    red[2][tid >> 5] = (double)c;
   }
   __syncthreads();
   if (tid < 3) {
@@ -163,7 +166,7 @@ pass_kernel(const __grid_constant__ PassArgs<T> a) {
     for (int r = 0; r < R; ++r) e += qv[r] * (v[r].x * v[r].x + v[r].y * v[r].y);
     if constexpr (SHAPE == FV) {
       gstore_normal<2>(v, a.psi_out, off2, a.tile, tp2);
-      block_store3((double)e, 0.0, 0.0, a.part, a.row_E, -1, -1, tid);
+      block_store3(e, T(0), T(0), a.part, a.row_E, -1, -1, tid);
     } else {
       C l[R];
 #pragma unroll
@@ -175,7 +178,7 @@ pass_kernel(const __grid_constant__ PassArgs<T> a) {
       xchg2<1, 0>(v, l, sm, tid);
       unrot_layout_acc<0>(v, l, a.mask_bef, a.cb, a.sb, tp0, acc);
       gstore<0>(l, a.lam_out, off0, a.tile);
-      block_store3((double)e, 2.0 * (double)acc, 0.0, a.part, a.row_E, a.row_bef, -1, tid);
+      block_store3(e, T(2) * acc, T(0), a.part, a.row_E, a.row_bef, -1, tid);
     }
   } else if constexpr (SHAPE == R1 || SHAPE == R0) {
     C l[R];
@@ -208,8 +211,7 @@ pass_kernel(const __grid_constant__ PassArgs<T> a) {
       gstore<0>(l, a.lam_out, off0, a.tile);
       if (a.psi_out) gstore<0>(v, a.psi_out, off0, a.tile);
     }
-    block_store3(2.0 * (double)acc_b, 2.0 * (double)acc_a, 2.0 * (double)acc_g, a.part, a.row_bef,
-                 a.row_aft, a.row_gam, tid);
+    block_store3(T(2) * acc_b, T(2) * acc_a, T(2) * acc_g, a.part, a.row_bef, a.row_aft, a.row_gam, tid);
   } else if constexpr (SHAPE == R2) {
     C l[R];
     gload<2>(v, a.psi_in, off2, a.tile);
@@ -222,7 +224,7 @@ pass_kernel(const __grid_constant__ PassArgs<T> a) {
     unrot_layout_acc<0>(v, l, a.mask_bef, a.cb, a.sb, tp0, acc_b);
     gstore<0>(l, a.lam_out, off0, a.tile);
     if (a.psi_out) gstore<0>(v, a.psi_out, off0, a.tile);
-    block_store3(2.0 * (double)acc_b, 0.0, 0.0, a.part, a.row_bef, -1, -1, tid);
+    block_store3(T(2) * acc_b, T(0), T(0), a.part, a.row_bef, -1, -1, tid);
   }
 }
 

@@ -1,0 +1,143 @@
+"""GPU parity of the QAOAz CSR/Chebyshev path, through the C ABI, against the fp64 oracle."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as orc
+import workloads as wl
+from tests import closed_forms as cf
+from tests.gpu_util import TOL_E, TOL_G, infidelity, lib, rel_err_E, rel_err_grad
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qvs():
+    return lib()
+
+
+def _torch():
+    import torch
+    assert torch.cuda.is_available()
+    return torch
+
+
+def _setup(qvs, n, k, port, tol=0.0):
+    torch = _torch()
+    states, rowptr, colind = qvs.qvs_xy_ring_csr(n, k)
+    dim = states.shape[0]
+    st_dev = torch.from_numpy(states).cuda()
+    q = torch.empty(dim, dtype=torch.float32, device="cuda")
+    qvs.qvs_quality_portfolio(n, st_dev, port.returns, port.cov, port.omega, q, qvs.QVS_F32)
+    sim = qvs.Simulator(dim, qvs.QVS_C64)
+    sim.set_quality(q)
+    sim.set_mixer(qvs.QVS_MIX_CSR, qvs.csr_desc(rowptr, colind, None, 2.0, tol=tol))
+    return sim, q, states
+
+
+def _oracle(n, k, port):
+    return orc.qaoaz_problem(n, k, port.returns, port.cov, port.omega, q_dtype=np.float32)
+
+
+@pytest.mark.parametrize("n", [8, 12, 24])
+def test_portfolio_quality_bit_exact(qvs, n):
+    torch = _torch()
+    k = n // 2
+    port = wl.portfolio(n // 2, wl.rng_for(80, n))
+    states, _, _ = qvs.qvs_xy_ring_csr(n, k)
+    q = torch.empty(states.shape[0], dtype=torch.float32, device="cuda")
+    qvs.qvs_quality_portfolio(n, torch.from_numpy(states).cuda(), port.returns, port.cov, port.omega, q,
+                              qvs.QVS_F32)
+    got = q.cpu().numpy()
+    if n <= 12:
+        ref = orc.portfolio_quality(n, states, port.returns, port.cov, port.omega)
+    else:   # sampled rows, evaluated one by one from the definition
+        idx = wl.rng_for(81, 0).integers(0, states.shape[0], 2000)
+        ref = orc.portfolio_quality(n, states[idx], port.returns, port.cov, port.omega)
+        got = got[idx]
+    assert np.array_equal(got, ref.astype(np.float32))
+
+
+@pytest.mark.parametrize("n,p", [(10, 2), (12, 3), (16, 2)])
+def test_qaoaz_vs_oracle(qvs, n, p):
+    port = wl.portfolio(n // 2, wl.rng_for(82, n))
+    sim, _, _ = _setup(qvs, n, n // 2, port)
+    prob = _oracle(n, n // 2, port)
+    gs, ts = wl.thetas(p, wl.rng_for(83, n))
+    E = sim.evolve(gs, ts)
+    ref_psi = orc.evolve(prob, gs, ts)
+    assert rel_err_E(E, orc.expectation(ref_psi, prob.q)) < TOL_E
+    assert infidelity(sim.state(), ref_psi) < 1e-6
+    E2, dg, dt = sim.gradient(gs, ts)
+    f, rdg, rdt = orc.gradient(prob, gs, ts)
+    assert rel_err_E(E2, f) < TOL_E
+    assert rel_err_grad(dg, dt, rdg, rdt) < TOL_G
+
+
+def test_chebyshev_truncation_bound(qvs):
+    """A loose tolerance must still land within its own error bound (tail of 2|J_m|)."""
+    n, p = 10, 1
+    port = wl.portfolio(5, wl.rng_for(84, 0))
+    for tol in [1e-3, 1e-5]:
+        sim, _, _ = _setup(qvs, n, 5, port, tol=tol)
+        prob = _oracle(n, 5, port)
+        gs, ts = [0.0], [2.5]
+        sim.evolve(gs, ts)
+        err = np.linalg.norm(sim.state().astype(np.complex128) - orc.evolve(prob, gs, ts))
+        assert err <= tol + 1e-5
+
+
+def test_givens_pair_exact(qvs):
+    """A single XY pair term on span{|01>,|10>} is the rotation [[c2t, -i s2t], [-i s2t, c2t]]."""
+    torch = _torch()
+    sim = qvs.Simulator(2, qvs.QVS_C64)
+    sim.set_quality(np.zeros(2, dtype=np.float32))
+    rowptr = np.array([0, 1, 2], dtype=np.int64)
+    colind = np.array([1, 0], dtype=np.int32)
+    sim.set_mixer(qvs.QVS_MIX_CSR, qvs.csr_desc(rowptr, colind, None, 2.0, spec=(-2.0, 2.0)))
+    psi0 = np.array([0.6, 0.8j], dtype=np.complex64)
+    sim.set_initial_state(psi0)
+    for t in [0.3, 1.1, 2.9]:
+        sim.evolve([0.0], [t])
+        # W = [[0, 2], [2, 0]] = (XX + YY) on the pair: exp(-itW) = Givens(t)
+        ref = cf.givens_xy(t) @ psi0.astype(np.complex128)
+        assert np.max(np.abs(sim.state() - ref)) < 2e-6
+
+
+# ------------------------------------------------------------------ full size: n=24, weight 12, p=4
+
+@pytest.fixture(scope="module")
+def full24(qvs):
+    inst = wl.qaoaz(24, 12, 4)
+    sim, q, states = _setup(qvs, 24, 12, inst.port)
+    return inst, sim, q
+
+
+def test_full24_identities_and_norm(full24):
+    inst, sim, q = full24
+    qh = q.cpu().numpy().astype(np.float64)
+    assert rel_err_E(sim.evolve(inst.gammas, np.zeros(4)), qh.mean()) < TOL_E
+    E = sim.evolve(inst.gammas, inst.ts)
+    psi = sim.state()
+    assert abs(np.sum(np.abs(psi.astype(np.complex128)) ** 2) - 1.0) < 1e-4
+    assert qh.min() <= E <= qh.max()
+
+
+def test_full24_gradient_consistency(full24):
+    inst, sim, q = full24
+    gs, ts = np.asarray(inst.gammas, float), np.asarray(inst.ts, float)
+    E, dg, dt = sim.gradient(gs, ts)
+    assert rel_err_E(E, sim.evolve(gs, ts)) < TOL_E
+    h = 1e-3
+    fd = []
+    for which in range(2):
+        for k in range(4):
+            g2, t2 = gs.copy(), ts.copy()
+            (g2 if which == 0 else t2)[k] += h
+            ep = sim.evolve(g2, t2)
+            (g2 if which == 0 else t2)[k] -= 2 * h
+            em = sim.evolve(g2, t2)
+            fd.append((ep - em) / (2 * h))
+    fd = np.array(fd)
+    assert rel_err_grad(dg, dt, fd[:4], fd[4:]) < 2e-3

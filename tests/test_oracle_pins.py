@@ -284,6 +284,20 @@ def test_quality_subset_and_portfolio_small_cases():
     assert np.allclose(q, [0.0, 0.75 + 1.5, 0.75 - 1.5, 0.0])
 
 
+def test_portfolio_two_assets_hand_computed():
+    """Two assets, every position pair written out by hand (cross-covariance terms included)."""
+    cov = [[2.0, 0.5], [0.5, 3.0]]
+    r = [1.0, -2.0]
+    om = 0.25
+    # qubits (0 long, 1 short) for asset 0 and (2 long, 3 short) for asset 1, qubit 0 = MSB
+    cases = {(1, 0, 1, 0): (1, 1), (1, 0, 0, 1): (1, -1), (0, 1, 0, 0): (-1, 0), (1, 1, 0, 1): (0, -1)}
+    for bits, (z0, z1) in cases.items():
+        idx = int("".join(map(str, bits)), 2)
+        q = orc.portfolio_quality(4, np.array([idx]), r, cov, om)[0]
+        expect = om * (2.0 * z0 * z0 + 0.5 * z0 * z1 + 0.5 * z1 * z0 + 3.0 * z1 * z1) - (1 - om) * (1.0 * z0 - 2.0 * z1)
+        assert q == pytest.approx(expect, abs=1e-15)
+
+
 def test_subspace_count():
     assert orc.subspace_states(10, 5).shape[0] == math.comb(10, 5)
     assert orc.subspace_states(24, 12).shape[0] == 2704156

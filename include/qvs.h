@@ -169,6 +169,40 @@ int qvs_quality_portfolio(int n_qubits, int64_t dim, const int64_t* states, cons
 int qvs_xy_ring_csr(int n, int k, int64_t* states, int64_t* rowptr, int32_t* colind,
                     int64_t* dim_out, int64_t* nnz_out);
 
+/* ----------------------------------------------------------------- allocation-free small solve
+ * The paper has no counterpart to this entry point. It is for callers that cannot allocate device
+ * memory at the moment they need a solve: code running while a stream is being captured into a
+ * CUDA graph (cudaMalloc cannot be captured), code inside an allocator or memory-pool callback, a
+ * real-time loop whose device memory is fixed up front, or a host runtime that owns all device
+ * memory and forbids libraries from taking more.
+ *
+ * It computes what qvs_gradient computes for a handle with the hypercube (QAOA) mixer, the
+ * equal-superposition initial state and dim = 2^n with n <= 12, but takes every input and output
+ * from the caller and keeps its only scratch (the p forward states that the adjoint sweep reads
+ * back) in one file-scope device array of QVS_NOALLOC_SCRATCH_BYTES bytes, which every GPU that
+ * loads the library holds until the process exits. It never calls cudaMalloc, cudaFree or any
+ * allocating routine.
+ *
+ *   n          qubits, 1 <= n <= 12 (dim = 2^n);
+ *   precision  QVS_C64 or QVS_C128;
+ *   p          layers, 1 <= p <= QVS_NOALLOC_MAX_LAYERS, and p * 2^n * (8 for C64, 16 for C128)
+ *              must not exceed QVS_NOALLOC_SCRATCH_BYTES (QVS_EINVAL otherwise);
+ *   q          device array of 2^n qualities: float for QVS_C64, double for QVS_C128;
+ *   gammas, ts host arrays of length p (read before the call returns);
+ *   out        device array of 1 + 2p doubles, written with E, dgamma[0..p), dt[0..p);
+ *   stream     cudaStream_t or NULL.
+ * The call only enqueues one kernel on `stream` and returns; `out` is valid once the stream has
+ * reached that point. The first call on a device (with that device current) resolves the scratch
+ * address with cudaGetSymbolAddress and sets the kernel's shared-memory limit; make that first call
+ * before any stream capture. Every call on a device shares the one scratch array and overwrites
+ * it (it keeps the last call's contents; nothing in it needs to start at zero), so calls whose
+ * kernels may overlap on the GPU - on different streams without ordering between them - race.
+ */
+#define QVS_NOALLOC_SCRATCH_BYTES (4u << 20)
+#define QVS_NOALLOC_MAX_LAYERS 128
+int qvs_gradient_small_noalloc(int n, int precision, int p, const void* q, const double* gammas,
+                               const double* ts, double* out, void* stream);
+
 const char* qvs_strerror(int status);
 
 #ifdef __cplusplus

@@ -32,7 +32,7 @@ EXPORTED = [
     "qvs_create", "qvs_destroy", "qvs_set_quality", "qvs_set_mixer", "qvs_set_initial_state",
     "qvs_set_option", "qvs_evolve", "qvs_expectation", "qvs_gradient", "qvs_get_state",
     "qvs_last_launch_count", "qvs_kernel_stats", "qvs_quality_maxcut", "qvs_quality_subset", "qvs_quality_portfolio",
-    "qvs_xy_ring_csr", "qvs_strerror",
+    "qvs_xy_ring_csr", "qvs_gradient_small_noalloc", "qvs_strerror",
 ]
 
 
@@ -89,6 +89,7 @@ def load(path: str = LIB_PATH):
         "qvs_quality_subset": (I, [I, P(D), I, V, V]),
         "qvs_quality_portfolio": (I, [I, I64, V, P(D), P(D), D, I, V, V]),
         "qvs_xy_ring_csr": (I, [I, I, V, V, V, P(I64), P(I64)]),
+        "qvs_gradient_small_noalloc": (I, [I, I, I, V, P(D), P(D), V, V]),
         "qvs_strerror": (ctypes.c_char_p, [I]),
     }
     for name, (res, args) in sig.items():
@@ -276,6 +277,19 @@ def qvs_xy_ring_csr(n: int, k: int):
                                ctypes.c_void_p(colind.ctypes.data), ctypes.byref(dim), ctypes.byref(nnz)),
            "qvs_xy_ring_csr")
     return states, rowptr, colind
+
+
+def qvs_gradient_small_noalloc(n: int, precision: int, q_dev, gammas, ts, out_dev, stream=None):
+    """Allocation-free small-state solve (n <= 12): writes E, dgamma[p], dt[p] into the device
+    tensor out_dev (1 + 2p float64) on the stream; see include/qvs.h for the limits."""
+    g = np.ascontiguousarray(gammas, dtype=np.float64)
+    t = np.ascontiguousarray(ts, dtype=np.float64)
+    qp, qdev = _ptr_of(q_dev)
+    op, odev = _ptr_of(out_dev)
+    assert qdev == 1 and odev == 1, "q and out must be device tensors"
+    _check(load().qvs_gradient_small_noalloc(int(n), int(precision), len(g), qp, _dptr(g), _dptr(t), op,
+                                             _stream_ptr(stream)), "qvs_gradient_small_noalloc")
+    return out_dev
 
 
 def qvs_strerror(status: int) -> str:

@@ -160,6 +160,113 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------------ the other hot-path configurations
+
+def _time_steps(torch, stream, fn, steps, warmup):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def _kernel_summary(qvs, h, peak, nsteps):
+    stats = qvs.qvs_kernel_stats(h)
+    if not stats:
+        return None, {}
+    total = sum(s["ms"] for s in stats) or 1.0
+    top = max(stats, key=lambda s: s["ms"])
+    gbps = top["bytes"] / (top["ms"] * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": top["name"], "achieved": gbps, "peak": peak, "unit": "GB/s",
+            "frac": gbps / peak, "peak_source": "measured" if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else "fallback"}
+    ker = {s["name"]: {"launches_per_step": s["launches"] / nsteps, "avg_ms": s["ms"] / s["launches"],
+                       "share": s["ms"] / total} for s in stats}
+    return roof, ker
+
+
+def run_extras(qvs, torch, stream, peak, steps, warmup):
+    """Objective + adjoint-gradient throughput of the QWOA circulant (N=2^26, p=6), QAOAz CSR
+    (n=24, weight 12, p=4) and batched QAOA (4096 instances) workloads."""
+    out = {}
+    # QWOA circulant, N = 2^26, p = 6
+    inst = wl.qwoa(26, 6)
+    q = torch.empty(1 << 26, dtype=torch.float32, device="cuda")
+    qvs.qvs_quality_subset(26, inst.weights, q, qvs.QVS_F32, stream)
+    sim = qvs.Simulator(1 << 26, qvs.QVS_C64, stream)
+    sim.set_quality(q).set_mixer(qvs.QVS_MIX_CIRCULANT, qvs.circulant_desc(inst.offsets))
+    ms = _time_steps(torch, stream, lambda: sim.gradient(inst.gammas, inst.ts), steps, warmup)
+    sim.set_option(qvs.QVS_OPT_PROFILE, 1)
+    for _ in range(2):
+        sim.gradient(inst.gammas, inst.ts)
+    roof, ker = _kernel_summary(qvs, sim.h, peak, 2)
+    units = float(1 << 26) * 6
+    out["qwoa_circulant_n26_p6"] = {"value": units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                                    "launches_per_step": sim.launches(), "roofline": roof, "kernels": ker}
+    sim.close()
+    del q
+    # QAOAz XY ring on the Hamming-weight-12 subspace of 24 qubits, p = 4
+    inst = wl.qaoaz(24, 12, 4)
+    states, rowptr, colind = qvs.qvs_xy_ring_csr(24, 12)
+    dim = states.shape[0]
+    st = torch.from_numpy(states).cuda()
+    q = torch.empty(dim, dtype=torch.float32, device="cuda")
+    qvs.qvs_quality_portfolio(24, st, inst.port.returns, inst.port.cov, inst.port.omega, q, qvs.QVS_F32, stream)
+    sim = qvs.Simulator(dim, qvs.QVS_C64, stream)
+    sim.set_quality(q).set_mixer(qvs.QVS_MIX_CSR, qvs.csr_desc(rowptr, colind, None, 2.0))
+    ms = _time_steps(torch, stream, lambda: sim.gradient(inst.gammas, inst.ts), max(2, steps // 2), 2)
+    sim.set_option(qvs.QVS_OPT_PROFILE, 1)
+    sim.gradient(inst.gammas, inst.ts)
+    roof, ker = _kernel_summary(qvs, sim.h, peak, 1)
+    units = float(dim) * 4
+    out["qaoaz_csr_n24_k12_p4"] = {"value": units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                                   "launches_per_step": sim.launches(), "roofline": roof, "kernels": ker,
+                                   "nnz": int(colind.shape[0])}
+    sim.close()
+    # batched QAOA: 4096 instances, n in 12..20, p in 2..8, 3-regular graphs
+    spec = wl.batch_spec()
+    insts = [wl.maxcut3(int(n), int(p), instance=2 * 100000 + i) for i, (n, p) in enumerate(zip(spec.ns, spec.ps))]
+    sizes = [1 << int(n) for n in spec.ns]
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    q = torch.empty(int(offs[-1]), dtype=torch.float32, device="cuda")
+    for k, inst in enumerate(insts):
+        qvs.qvs_quality_maxcut(inst.graph.n, inst.graph.eu, inst.graph.ev, None, q[int(offs[k]):int(offs[k + 1])],
+                               qvs.QVS_F32, stream)
+    b = qvs.Batch(spec.ns, spec.ps, stream).set_quality(q)
+    gl, tl = [i.gammas for i in insts], [i.ts for i in insts]
+    ms = _time_steps(torch, stream, lambda: b.gradient(gl, tl), max(3, steps // 2), 2)
+    units = float(sum(s * int(p) for s, p in zip(sizes, spec.ps)))
+    # the plain per-instance path over the same instances, timed once
+    sims = []
+    t0 = time.perf_counter()
+    for k, inst in enumerate(insts):
+        sim = qvs.Simulator(sizes[k], qvs.QVS_C64, stream)
+        sim.set_quality(q[int(offs[k]):int(offs[k + 1])]).set_mixer(qvs.QVS_MIX_HYPERCUBE, qvs.hypercube_desc(inst.graph.n))
+        sims.append(sim)
+    setup_s = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k, inst in enumerate(insts):
+        sims[k].gradient(inst.gammas, inst.ts)
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - t0
+    for sim in sims:
+        sim.close()
+    out["batched_qaoa_4096"] = {"value": units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                                "instances_per_s": len(insts) / (ms * 1e-3), "launches_per_step": 1,
+                                "autotune": b.info(),
+                                "plain_per_instance": {"value": units / plain_s, "unit": UNIT, "s_per_batch": plain_s,
+                                                       "note": "looped single-instance qvs_gradient calls, complex64"},
+                                "speedup_vs_plain": plain_s / (ms * 1e-3)}
+    b.close()
+    return out
+
+
 # ------------------------------------------------------------------ GPU arm
 
 def run_ours(args):
@@ -260,6 +367,12 @@ def run_ours(args):
         e2e_s = float(t.item())
     e2e_value = units * world / e2e_s
 
+    extras = None
+    if rank == 0 and world == 1 and not args.no_extras and (n, p) == (N_QUBITS, P_LAYERS):
+        sim.close()
+        torch.cuda.empty_cache()
+        extras = run_extras(qvs, torch, stream, peak, args.steps, args.warmup)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, desc, _ = oracle_sample(seconds_target=15.0)
@@ -293,8 +406,11 @@ def run_ours(args):
         }
         if cpu:
             line["cpu_baseline"] = cpu
+        if extras:
+            line["extras"] = extras
         print(json.dumps(line), flush=True)
-    sim.close()
+    if extras is None:
+        sim.close()
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
@@ -308,6 +424,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ckpt", type=int, default=None, help="checkpoint interval in layers (0 = ceil(sqrt(p)))")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the QWOA, QAOAz and batched lines")
     ap.add_argument("--qubits", type=int, default=N_QUBITS, help="state size 2^qubits (28 is the benchmark)")
     ap.add_argument("--layers", type=int, default=P_LAYERS, help="depth p (8 is the benchmark)")
     args = ap.parse_args()

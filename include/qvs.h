@@ -169,6 +169,33 @@ int qvs_quality_portfolio(int n_qubits, int64_t dim, const int64_t* states, cons
 int qvs_xy_ring_csr(int n, int k, int64_t* states, int64_t* rowptr, int32_t* colind,
                     int64_t* dim_out, int64_t* nnz_out);
 
+/* ----------------------------------------------------------------- batched solves
+ * Sec. 4 parallelises over gradient components with MPI sub-communicators; the GPU analogue here
+ * is many independent instances solved by one persistent kernel. A batch holds `count` QAOA
+ * max-cut-style instances with the hypercube mixer and the equal-superposition initial state:
+ * instance i has n_qubits[i] qubits (12 <= n <= 28) and layers[i] layers (1 <= p <= 64), complex64
+ * state, fp32 qualities. The kernel's CTAs pull instances (longest first) from a device counter and
+ * run each one's forward sweep, objective and adjoint gradient to completion; the first solve
+ * times one and two CTAs per SM and keeps the faster, then captures parameters-in, the kernel and
+ * results-out as a CUDA graph that later solves replay.
+ *
+ * Layouts: qualities are concatenated in instance order (instance i at offset
+ * sum_{j<i} 2^n_j); parameters and gradient entries are concatenated per instance (instance i at
+ * offset sum_{j<i} p_j). The handle owns its device workspace (one slot per resident CTA).
+ */
+typedef struct qvs_batch* qvs_batch_t;
+
+int qvs_batch_create(qvs_batch_t* out, int count, const int32_t* n_qubits, const int32_t* layers,
+                     void* stream);
+/* q: the concatenated fp32 qualities (host or device per on_device); copied. */
+int qvs_batch_set_quality(qvs_batch_t b, const float* q, int on_device);
+/* gammas, ts: concatenated host arrays; E[count], dgamma and dt concatenated host outputs. */
+int qvs_batch_gradient(qvs_batch_t b, const double* gammas, const double* ts, double* E,
+                       double* dgamma, double* dt);
+/* The autotuner's choice (CTAs per SM) and its two trial times in milliseconds. */
+int qvs_batch_info(qvs_batch_t b, int* ctas_per_sm, double* tuned_ms_1, double* tuned_ms_2);
+int qvs_batch_destroy(qvs_batch_t b);
+
 /* ----------------------------------------------------------------- allocation-free small solve
  * The paper has no counterpart to this entry point. It is for callers that cannot allocate device
  * memory at the moment they need a solve: code running while a stream is being captured into a

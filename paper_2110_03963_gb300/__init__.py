@@ -32,7 +32,8 @@ EXPORTED = [
     "qvs_create", "qvs_destroy", "qvs_set_quality", "qvs_set_mixer", "qvs_set_initial_state",
     "qvs_set_option", "qvs_evolve", "qvs_expectation", "qvs_gradient", "qvs_get_state",
     "qvs_last_launch_count", "qvs_kernel_stats", "qvs_quality_maxcut", "qvs_quality_subset", "qvs_quality_portfolio",
-    "qvs_xy_ring_csr", "qvs_gradient_small_noalloc", "qvs_strerror",
+    "qvs_xy_ring_csr", "qvs_batch_create", "qvs_batch_set_quality", "qvs_batch_gradient",
+    "qvs_batch_info", "qvs_batch_destroy", "qvs_gradient_small_noalloc", "qvs_strerror",
 ]
 
 
@@ -90,6 +91,11 @@ def load(path: str = LIB_PATH):
         "qvs_quality_portfolio": (I, [I, I64, V, P(D), P(D), D, I, V, V]),
         "qvs_xy_ring_csr": (I, [I, I, V, V, V, P(I64), P(I64)]),
         "qvs_gradient_small_noalloc": (I, [I, I, I, V, P(D), P(D), V, V]),
+        "qvs_batch_create": (I, [P(V), I, P(ctypes.c_int32), P(ctypes.c_int32), V]),
+        "qvs_batch_set_quality": (I, [V, V, I]),
+        "qvs_batch_gradient": (I, [V, P(D), P(D), P(D), P(D), P(D)]),
+        "qvs_batch_info": (I, [V, P(I), P(D), P(D)]),
+        "qvs_batch_destroy": (I, [V]),
         "qvs_strerror": (ctypes.c_char_p, [I]),
     }
     for name, (res, args) in sig.items():
@@ -290,6 +296,79 @@ def qvs_gradient_small_noalloc(n: int, precision: int, q_dev, gammas, ts, out_de
     _check(load().qvs_gradient_small_noalloc(int(n), int(precision), len(g), qp, _dptr(g), _dptr(t), op,
                                              _stream_ptr(stream)), "qvs_gradient_small_noalloc")
     return out_dev
+
+
+def qvs_batch_create(n_qubits, layers, stream=None):
+    ns = np.ascontiguousarray(n_qubits, dtype=np.int32)
+    ps = np.ascontiguousarray(layers, dtype=np.int32)
+    h = ctypes.c_void_p()
+    _check(load().qvs_batch_create(ctypes.byref(h), len(ns), ns.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                   ps.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _stream_ptr(stream)),
+           "qvs_batch_create")
+    return h
+
+
+def qvs_batch_set_quality(b, q):
+    p, dev = _ptr_of(q)
+    _check(load().qvs_batch_set_quality(b, p, dev), "qvs_batch_set_quality")
+
+
+def qvs_batch_gradient(b, gammas, ts, count: int):
+    """gammas, ts: concatenated per-instance parameters. Returns (E[count], dgamma, dt) concatenated."""
+    g = np.ascontiguousarray(gammas, dtype=np.float64)
+    t = np.ascontiguousarray(ts, dtype=np.float64)
+    E = np.zeros(count)
+    dg = np.zeros(len(g))
+    dt = np.zeros(len(g))
+    _check(load().qvs_batch_gradient(b, _dptr(g), _dptr(t), _dptr(E), _dptr(dg), _dptr(dt)), "qvs_batch_gradient")
+    return E, dg, dt
+
+
+def qvs_batch_info(b):
+    c = ctypes.c_int()
+    t1 = ctypes.c_double()
+    t2 = ctypes.c_double()
+    _check(load().qvs_batch_info(b, ctypes.byref(c), ctypes.byref(t1), ctypes.byref(t2)), "qvs_batch_info")
+    return {"ctas_per_sm": c.value, "trial_ms": [t1.value, t2.value]}
+
+
+def qvs_batch_destroy(b):
+    _check(load().qvs_batch_destroy(b), "qvs_batch_destroy")
+
+
+class Batch:
+    """Many QAOA hypercube instances (n >= 12) solved by one persistent launch."""
+
+    def __init__(self, n_qubits, layers, stream=None):
+        self.ns = np.asarray(n_qubits, dtype=np.int64)
+        self.ps = np.asarray(layers, dtype=np.int64)
+        self.qoff = np.concatenate([[0], np.cumsum(1 << self.ns)])
+        self.poff = np.concatenate([[0], np.cumsum(self.ps)])
+        self.h = qvs_batch_create(self.ns, self.ps, stream)
+
+    def close(self):
+        if self.h is not None:
+            qvs_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_quality(self, q_concat):
+        qvs_batch_set_quality(self.h, q_concat)
+        return self
+
+    def gradient(self, gammas_list, ts_list):
+        """Lists of per-instance parameter arrays -> (E array, list of dgamma, list of dt)."""
+        E, dg, dt = qvs_batch_gradient(self.h, np.concatenate(gammas_list), np.concatenate(ts_list), len(self.ns))
+        cut = lambda v: [v[self.poff[i]:self.poff[i + 1]] for i in range(len(self.ns))]
+        return E, cut(dg), cut(dt)
+
+    def info(self):
+        return qvs_batch_info(self.h)
 
 
 def qvs_strerror(status: int) -> str:

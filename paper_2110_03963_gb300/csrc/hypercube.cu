@@ -17,7 +17,10 @@
 // inverse pass; checkpoints are kept every ckpt_layers layers (default ceil(sqrt(p))).
 #include <math.h>
 
+#include <string.h>
+
 #include <algorithm>
+#include <new>
 #include <vector>
 
 #include "hc_kernels.cuh"
@@ -59,7 +62,7 @@ struct PassArgs {
 // fp64; the order is fixed, so results are reproducible run to run.
 template <class T>
 __device__ __forceinline__ void block_store3(T a, T b, T c, double* part, int ra, int rb, int rc,
-                                             int tid) {
+                                             int tid, uint32_t bid, uint32_t nblk) {
   __shared__ double red[3][NT / 32];
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
@@ -78,18 +81,19 @@ __device__ __forceinline__ void block_store3(T a, T b, T c, double* part, int ra
 #pragma unroll
     for (int w = 0; w < NT / 32; ++w) s += red[tid][w];
     const int row = tid == 0 ? ra : (tid == 1 ? rb : rc);
-    if (row >= 0) part[(size_t)row * gridDim.x + blockIdx.x] = s;
+    if (row >= 0) part[(size_t)row * nblk + bid] = s;
   }
 }
 
+// One tile (index bid of nblk) of one pass; the CTA's shared memory is smem_raw. Used by the
+// per-pass kernels (one CTA per tile) and by the batched persistent kernel (a CTA walks the tiles).
 template <class T, int SHAPE>
-__global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 1 : ((SHAPE == FE || SHAPE == R1 || SHAPE == R2 || SHAPE == R0) ? 2 : 3))
-pass_kernel(const __grid_constant__ PassArgs<T> a) {
+__device__ __forceinline__ void run_pass(const PassArgs<T>& a, uint32_t bid, uint32_t nblk,
+                                         unsigned char* smem_raw) {
   using C = typename Cx<T>::t;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   C* sm = reinterpret_cast<C*>(smem_raw);
   const int tid = threadIdx.x;
-  const uint32_t base = tile_base(a.tile, blockIdx.x);
+  const uint32_t base = tile_base(a.tile, bid);
   const uint32_t off0 = base + toff(a.tile, tj<0>(0, tid));
   const uint32_t off2 = base + toff(a.tile, tj<2>(0, tid));
   // storage-form parity of the thread's own index bits in each layout
@@ -166,7 +170,7 @@ pass_kernel(const __grid_constant__ PassArgs<T> a) {
     for (int r = 0; r < R; ++r) e += qv[r] * (v[r].x * v[r].x + v[r].y * v[r].y);
     if constexpr (SHAPE == FV) {
       gstore_normal<2>(v, a.psi_out, off2, a.tile, tp2);
-      block_store3(e, T(0), T(0), a.part, a.row_E, -1, -1, tid);
+      block_store3(e, T(0), T(0), a.part, a.row_E, -1, -1, tid, bid, nblk);
     } else {
       C l[R];
 #pragma unroll
@@ -178,7 +182,7 @@ pass_kernel(const __grid_constant__ PassArgs<T> a) {
       xchg2<1, 0>(v, l, sm, tid);
       unrot_layout_acc<0>(v, l, a.mask_bef, a.cb, a.sb, tp0, acc);
       gstore<0>(l, a.lam_out, off0, a.tile);
-      block_store3(e, T(2) * acc, T(0), a.part, a.row_E, a.row_bef, -1, tid);
+      block_store3(e, T(2) * acc, T(0), a.part, a.row_E, a.row_bef, -1, tid, bid, nblk);
     }
   } else if constexpr (SHAPE == R1 || SHAPE == R0) {
     C l[R];
@@ -211,7 +215,7 @@ pass_kernel(const __grid_constant__ PassArgs<T> a) {
       gstore<0>(l, a.lam_out, off0, a.tile);
       if (a.psi_out) gstore<0>(v, a.psi_out, off0, a.tile);
     }
-    block_store3(T(2) * acc_b, T(2) * acc_a, T(2) * acc_g, a.part, a.row_bef, a.row_aft, a.row_gam, tid);
+    block_store3(T(2) * acc_b, T(2) * acc_a, T(2) * acc_g, a.part, a.row_bef, a.row_aft, a.row_gam, tid, bid, nblk);
   } else if constexpr (SHAPE == R2) {
     C l[R];
     gload<2>(v, a.psi_in, off2, a.tile);
@@ -224,8 +228,15 @@ pass_kernel(const __grid_constant__ PassArgs<T> a) {
     unrot_layout_acc<0>(v, l, a.mask_bef, a.cb, a.sb, tp0, acc_b);
     gstore<0>(l, a.lam_out, off0, a.tile);
     if (a.psi_out) gstore<0>(v, a.psi_out, off0, a.tile);
-    block_store3(T(2) * acc_b, T(0), T(0), a.part, a.row_bef, -1, -1, tid);
+    block_store3(T(2) * acc_b, T(0), T(0), a.part, a.row_bef, -1, -1, tid, bid, nblk);
   }
+}
+
+template <class T, int SHAPE>
+__global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 1 : ((SHAPE == FE || SHAPE == R1 || SHAPE == R2 || SHAPE == R0) ? 2 : 3))
+pass_kernel(const __grid_constant__ PassArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  run_pass<T, SHAPE>(a, blockIdx.x, gridDim.x, smem_raw);
 }
 
 // ---------------------------------------------------------------- small states (n <= TB)
@@ -376,9 +387,22 @@ static int make_plan(int n, int p, Plan& pl) {
   pl = Plan{};
   pl.n = n;
   const int rest = n - TB;
-  if (rest <= 0) return QVS_EUNSUPPORTED;
+  if (rest < 0) return QVS_EUNSUPPORTED;
   pl.tile[0] = make_tile(n, TB, TB, 0);
   pl.gmask[0] = (1u << TB) - 1;
+  if (rest == 0) {
+    // one tile holds the whole state: pass j applies phase j-1 and all of mixer j-1
+    pl.g = 1;
+    pl.F = p + 1;
+    pl.pass.assign(pl.F + 1, PassInfo{});
+    for (int j = 1; j <= pl.F; ++j) {
+      PassInfo& q = pl.pass[j];
+      if (j == 1) q = {0, F0, -1, 0, 0};
+      else if (j <= p) q = {0, F1, -1, j - 1, j - 1};
+      else q = {0, FE, -1, -1, -1};
+    }
+    return QVS_OK;
+  }
   if (rest <= TB - 4) {
     pl.g = 2;
     const int s = TB - rest;
@@ -716,3 +740,436 @@ int hc_gradient(qvs_ctx* h, int p, const double* gammas, const double* ts, doubl
 }
 
 }  // namespace qvs
+
+// ================================================================ batched persistent solve
+//
+// Many independent QAOA instances (each with its own n >= 12, p and quality vector) are solved
+// by one persistent kernel: every CTA owns a workspace slot and repeatedly takes the next
+// instance from a device-side counter (instances pre-sorted by decreasing cost, so the longest
+// start first), then runs that instance's whole pass schedule - forward sweep, fused adjoint,
+// reductions - walking its tiles itself, with a block barrier between passes. Small instances stay
+// in L2 for their whole solve.
+
+namespace qvs {
+namespace hc {
+
+struct BInst {
+  int n, p, F, g;
+  uint32_t ntiles;
+  int th0;            // offset of the instance's p parameters / gradient entries
+  int ck_c, nck;      // checkpoint interval (passes) and count
+  int64_t qoff;       // offset of the instance's q in the concatenated quality buffer
+  Tile tile[3];
+  uint32_t gmask[3];
+};
+
+struct BatchArgs {
+  int count;
+  const BInst* inst;
+  const int* order;          // processing order (by decreasing cost)
+  const float* q;            // concatenated qualities
+  const double* gammas;      // concatenated parameters
+  const double* ts;
+  double* out_E;             // [count]
+  double* out_dg;            // concatenated like gammas
+  double* out_dt;
+  int* counter;
+  unsigned char* ws;         // workspace slots
+  size_t slot_bytes;
+  int64_t dim_max;
+  int nck_max;
+};
+
+// pass j (1-based) of an instance's forward schedule (same rules as make_plan)
+__device__ __forceinline__ void bpass_info(const BInst& I, int j, int& type, int& shape, int& lb, int& la,
+                                           int& lg) {
+  const int p = I.p;
+  if (I.g == 1) {
+    type = 0;
+    if (j == 1) { shape = F0; lb = -1; la = 0; lg = 0; }
+    else if (j <= p) { shape = F1; lb = -1; la = j - 1; lg = j - 1; }
+    else { shape = FE; lb = -1; la = -1; lg = -1; }
+  } else if (I.g == 2) {
+    type = (j - 1) % 2;
+    if (j == 1) { shape = F0; lb = -1; la = 0; lg = 0; }
+    else if (j <= p) { shape = F1; lb = j - 2; la = j - 1; lg = j - 1; }
+    else { shape = FE; lb = p - 1; la = -1; lg = -1; }
+  } else {
+    type = (j - 1) % 3;
+    if (j == 1) { shape = F0; lb = -1; la = 0; lg = 0; }
+    else if (j == I.F) { shape = FE; lb = p - 1; la = -1; lg = -1; }
+    else if (j % 2 == 0) { shape = F2; lb = (j - 2) / 2; la = -1; lg = -1; }
+    else { shape = F1; lb = (j - 3) / 2; la = (j - 1) / 2; lg = (j - 1) / 2; }
+  }
+}
+
+__device__ __forceinline__ void run_shape(int shape, const PassArgs<float>& a, uint32_t t, uint32_t nt,
+                                          unsigned char* sm) {
+  switch (shape) {
+    case F0: run_pass<float, F0>(a, t, nt, sm); break;
+    case F1: run_pass<float, F1>(a, t, nt, sm); break;
+    case F2: run_pass<float, F2>(a, t, nt, sm); break;
+    case FE: run_pass<float, FE>(a, t, nt, sm); break;
+    case R1: run_pass<float, R1>(a, t, nt, sm); break;
+    case R2: run_pass<float, R2>(a, t, nt, sm); break;
+    case R0: run_pass<float, R0>(a, t, nt, sm); break;
+  }
+}
+
+__global__ void __launch_bounds__(NT, 2) batch_kernel(const __grid_constant__ BatchArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_inst;
+  __shared__ float s_ang[6];
+  const int tid = threadIdx.x;
+  unsigned char* slot = a.ws + (size_t)blockIdx.x * a.slot_bytes;
+  float2* W = reinterpret_cast<float2*>(slot);
+  float2* Lm = W + a.dim_max;
+  float2* K = Lm + a.dim_max;
+  double* part = reinterpret_cast<double*>(K + (size_t)a.nck_max * a.dim_max);
+  for (;;) {
+    if (tid == 0) s_inst = atomicAdd(a.counter, 1);
+    __syncthreads();
+    const int idx = s_inst;
+    __syncthreads();
+    if (idx >= a.count) return;
+    const int i = a.order[idx];
+    const BInst& I = a.inst[i];
+    const int F = I.F;
+    const int64_t dim = (int64_t)1 << I.n;
+    auto is_stored = [&](int j) { return j >= 1 && j <= F - 1 && j % I.ck_c == 0 && (j / I.ck_c) <= I.nck; };
+    auto loc = [&](int j) -> float2* {
+      return is_stored(j) ? K + (size_t)(j / I.ck_c - 1) * dim : W;
+    };
+    for (int step = 0; step < 2 * F - 1; ++step) {
+      const bool fwd = step < F;
+      const int j = fwd ? step + 1 : 2 * F - 1 - step;   // forward 1..F, then F-1..1
+      int type, shape, lb, la, lg;
+      bpass_info(I, j, type, shape, lb, la, lg);
+      if (tid == 0) {
+        s_ang[0] = lb >= 0 ? (float)cos(a.ts[I.th0 + lb]) : 0.f;
+        s_ang[1] = lb >= 0 ? (float)sin(a.ts[I.th0 + lb]) : 0.f;
+        s_ang[2] = la >= 0 ? (float)cos(a.ts[I.th0 + la]) : 0.f;
+        s_ang[3] = la >= 0 ? (float)sin(a.ts[I.th0 + la]) : 0.f;
+        if (lg >= 0) {
+          const double g = a.gammas[I.th0 + lg] / 6.283185307179586476925286766559;
+          const float hi = (float)g;
+          s_ang[4] = hi;
+          s_ang[5] = (float)(g - (double)hi);
+        } else {
+          s_ang[4] = s_ang[5] = 0.f;
+        }
+      }
+      __syncthreads();
+      PassArgs<float> pa{};
+      pa.tile = I.tile[type];
+      pa.q = a.q + I.qoff;
+      pa.mask_bef = lb >= 0 ? I.gmask[type] : 0u;
+      pa.mask_aft = la >= 0 ? I.gmask[type] : 0u;
+      pa.cb = s_ang[0];
+      pa.sb = s_ang[1];
+      pa.ca = s_ang[2];
+      pa.sa = s_ang[3];
+      pa.ph0 = s_ang[4];
+      pa.ph1 = s_ang[5];
+      pa.part = part;
+      pa.init_amp = (float)rsqrt((double)dim);
+      pa.gen_init = 1;
+      pa.row_bef = pa.row_aft = pa.row_gam = pa.row_E = -1;
+      if (fwd) {
+        pa.psi_in = j == 1 ? nullptr : loc(j - 1);
+        if (j == F) {
+          pa.lam_out = Lm;
+          pa.row_bef = lb >= 0 ? 3 * (j - 1) : -1;
+          pa.row_E = 3 * F;
+        } else {
+          pa.psi_out = loc(j);
+        }
+      } else {
+        shape = shape == F0 ? R0 : (shape == F1 ? R1 : R2);
+        pa.psi_in = loc(j);
+        pa.lam_in = Lm;
+        pa.lam_out = Lm;
+        pa.psi_out = (j - 1 >= 1 && !is_stored(j - 1)) ? W : nullptr;
+        pa.row_bef = lb >= 0 ? 3 * (j - 1) + 0 : -1;
+        pa.row_aft = la >= 0 ? 3 * (j - 1) + 1 : -1;
+        pa.row_gam = lg >= 0 ? 3 * (j - 1) + 2 : -1;
+      }
+      for (uint32_t t = 0; t < I.ntiles; ++t) run_shape(shape, pa, t, I.ntiles, smem_raw);
+      __syncthreads();   // every tile of this pass is written before the next pass reads it
+    }
+    // deterministic reduction of the partial rows into the outputs
+    const int p = I.p;
+    if (tid < 1 + 2 * p) {
+      double sum = 0.0;
+      for (int j = 1; j <= F; ++j) {
+        int type, shape, lb, la, lg;
+        bpass_info(I, j, type, shape, lb, la, lg);
+        int rows[2] = {-1, -1};
+        if (tid == 0) rows[0] = j == F ? 3 * F : -1;
+        else if (tid <= p) rows[0] = (lg == tid - 1) ? 3 * (j - 1) + 2 : -1;
+        else {
+          rows[0] = (lb == tid - 1 - p) ? 3 * (j - 1) + 0 : -1;
+          rows[1] = (la == tid - 1 - p) ? 3 * (j - 1) + 1 : -1;
+        }
+        for (int r = 0; r < 2; ++r)
+          if (rows[r] >= 0)
+            for (uint32_t t = 0; t < I.ntiles; ++t) sum += part[(size_t)rows[r] * I.ntiles + t];
+      }
+      if (tid == 0) a.out_E[i] = sum;
+      else if (tid <= p) a.out_dg[I.th0 + tid - 1] = sum;
+      else a.out_dt[I.th0 + tid - 1 - p] = sum;
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace hc
+}  // namespace qvs
+
+struct qvs_batch {
+  int count = 0;
+  int total_p = 0;
+  int64_t total_q = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<int> n, p, th0;
+  std::vector<int64_t> qoff;
+  qvs::DevBuf inst, order, q, theta, out, counter, ws;
+  size_t slot_bytes = 0;
+  int64_t dim_max = 0;
+  int nck_max = 0;
+  int nslots = 0;
+  int sms = 0;
+  int ctas_per_sm = 0;       // chosen by the autotuner on the first solve (0 = not yet tuned)
+  double tuned_ms[3] = {0, 0, 0};
+  double* host_theta = nullptr;   // pinned: gammas then ts
+  double* host_out = nullptr;     // pinned: E, dg, dt
+  cudaGraphExec_t graph = nullptr;
+  bool have_q = false;
+};
+
+namespace qvs {
+namespace hc {
+
+static int batch_launch(qvs_batch_t b, int ctas_per_sm) {
+  BatchArgs a{};
+  a.count = b->count;
+  a.inst = b->inst.as<BInst>();
+  a.order = b->order.as<int>();
+  a.q = b->q.as<float>();
+  a.gammas = b->theta.as<double>();
+  a.ts = a.gammas + b->total_p;
+  a.out_E = b->out.as<double>();
+  a.out_dg = a.out_E + b->count;
+  a.out_dt = a.out_dg + b->total_p;
+  a.counter = b->counter.as<int>();
+  a.ws = b->ws.as<unsigned char>();
+  a.slot_bytes = b->slot_bytes;
+  a.dim_max = b->dim_max;
+  a.nck_max = b->nck_max;
+  const int grid = std::min(b->nslots, b->sms * ctas_per_sm);
+  QVS_CUDA_TRY(cudaMemsetAsync(b->counter.ptr, 0, sizeof(int), b->stream));
+  batch_kernel<<<grid, NT, 2 * TILE * sizeof(float2), b->stream>>>(a);
+  QVS_CUDA_TRY(cudaGetLastError());
+  return QVS_OK;
+}
+
+}  // namespace hc
+}  // namespace qvs
+
+extern "C" int qvs_batch_create(qvs_batch_t* out, int count, const int32_t* n_qubits, const int32_t* layers,
+                                void* stream) {
+  using namespace qvs;
+  using namespace qvs::hc;
+  if (!out || count < 1 || count > (1 << 20) || !n_qubits || !layers) return QVS_EINVAL;
+  *out = nullptr;
+  qvs_batch* b = new (std::nothrow) qvs_batch();
+  if (!b) return QVS_ENOMEM;
+  b->count = count;
+  b->stream = (cudaStream_t)stream;
+  std::vector<BInst> inst(count);
+  std::vector<double> cost(count);
+  int64_t qtot = 0;
+  int ptot = 0;
+  size_t max_rows_tiles = 0;
+  for (int i = 0; i < count; ++i) {
+    const int n = n_qubits[i], p = layers[i];
+    if (n < TB || n > 28 || p < 1 || p > 64) {
+      delete b;
+      return n < TB ? QVS_EUNSUPPORTED : QVS_EINVAL;
+    }
+    Plan pl;
+    const int st = make_plan(n, p, pl);
+    if (st != QVS_OK) {
+      delete b;
+      return st;
+    }
+    BInst& I = inst[i];
+    I.n = n;
+    I.p = p;
+    I.F = pl.F;
+    I.g = pl.g;
+    I.ntiles = 1u << (n - TB);
+    I.th0 = ptot;
+    const int ckl = (int)ceil(sqrt((double)p) - 1e-9);
+    I.ck_c = std::max(1, ckl * std::max(1, pl.g - 1));
+    I.nck = (pl.F - 1) / I.ck_c;
+    I.qoff = qtot;
+    for (int t = 0; t < 3; ++t) {
+      I.tile[t] = pl.tile[t];
+      I.gmask[t] = pl.gmask[t];
+    }
+    b->n.push_back(n);
+    b->p.push_back(p);
+    b->th0.push_back(ptot);
+    b->qoff.push_back(qtot);
+    b->dim_max = std::max<int64_t>(b->dim_max, (int64_t)1 << n);
+    b->nck_max = std::max(b->nck_max, I.nck);
+    max_rows_tiles = std::max(max_rows_tiles, (size_t)(3 * pl.F + 1) * I.ntiles);
+    cost[i] = (double)((int64_t)1 << n) * (2 * pl.F - 1);
+    qtot += (int64_t)1 << n;
+    ptot += p;
+  }
+  b->total_q = qtot;
+  b->total_p = ptot;
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+  int dev = 0;
+  cudaDeviceProp prop;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    delete b;
+    return QVS_ECUDA;
+  }
+  b->sms = prop.multiProcessorCount;
+  b->nslots = 2 * b->sms;
+  b->slot_bytes = (sizeof(float2) * (size_t)b->dim_max * (2 + b->nck_max) + sizeof(double) * max_rows_tiles + 255) &
+                  ~(size_t)255;
+  int st = QVS_OK;
+  if ((st = b->inst.ensure(sizeof(BInst) * count)) != QVS_OK || (st = b->order.ensure(sizeof(int) * count)) != QVS_OK ||
+      (st = b->q.ensure(sizeof(float) * (size_t)qtot)) != QVS_OK ||
+      (st = b->theta.ensure(sizeof(double) * 2 * (size_t)ptot)) != QVS_OK ||
+      (st = b->out.ensure(sizeof(double) * ((size_t)count + 2 * (size_t)ptot))) != QVS_OK ||
+      (st = b->counter.ensure(sizeof(int))) != QVS_OK ||
+      (st = b->ws.ensure(b->slot_bytes * (size_t)b->nslots)) != QVS_OK) {
+    qvs_batch_destroy(b);
+    return st;
+  }
+  if (cudaMallocHost((void**)&b->host_theta, sizeof(double) * 2 * (size_t)ptot) != cudaSuccess ||
+      cudaMallocHost((void**)&b->host_out, sizeof(double) * ((size_t)count + 2 * (size_t)ptot)) != cudaSuccess) {
+    (void)cudaGetLastError();
+    qvs_batch_destroy(b);
+    return QVS_ENOMEM;
+  }
+  if (cudaMemcpyAsync(b->inst.ptr, inst.data(), sizeof(BInst) * count, cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+      cudaMemcpyAsync(b->order.ptr, order.data(), sizeof(int) * count, cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+      cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(2 * TILE * sizeof(float2))) != cudaSuccess ||
+      cudaStreamSynchronize(b->stream) != cudaSuccess) {
+    (void)cudaGetLastError();
+    qvs_batch_destroy(b);
+    return QVS_ECUDA;
+  }
+  *out = b;
+  return QVS_OK;
+}
+
+extern "C" int qvs_batch_set_quality(qvs_batch_t b, const float* q, int on_device) {
+  if (!b || !q) return QVS_EINVAL;
+  QVS_CUDA_TRY(cudaMemcpyAsync(b->q.ptr, q, sizeof(float) * (size_t)b->total_q,
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, b->stream));
+  b->have_q = true;
+  return QVS_OK;
+}
+
+extern "C" int qvs_batch_gradient(qvs_batch_t b, const double* gammas, const double* ts, double* E, double* dgamma,
+                                  double* dt) {
+  using namespace qvs;
+  if (!b || !gammas || !ts || !E || !dgamma || !dt) return QVS_EINVAL;
+  if (!b->have_q) return QVS_ESTATE;
+  const size_t P = (size_t)b->total_p;
+  for (size_t k = 0; k < P; ++k)
+    if (!isfinite(gammas[k]) || !isfinite(ts[k])) return QVS_EINVAL;
+  memcpy(b->host_theta, gammas, sizeof(double) * P);
+  memcpy(b->host_theta + P, ts, sizeof(double) * P);
+  if (b->ctas_per_sm == 0) {
+    // autotune: one timed run per candidate occupancy, keep the fastest
+    cudaEvent_t e0, e1;
+    QVS_CUDA_TRY(cudaEventCreate(&e0));
+    QVS_CUDA_TRY(cudaEventCreate(&e1));
+    double best = 1e30;
+    for (int c = 1; c <= 2; ++c) {
+      QVS_CUDA_TRY(cudaMemcpyAsync(b->theta.ptr, b->host_theta, sizeof(double) * 2 * P, cudaMemcpyHostToDevice,
+                                   b->stream));
+      QVS_CUDA_TRY(cudaEventRecord(e0, b->stream));
+      QVS_TRY(hc::batch_launch(b, c));
+      QVS_CUDA_TRY(cudaEventRecord(e1, b->stream));
+      QVS_CUDA_TRY(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      QVS_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+      b->tuned_ms[c] = ms;
+      if (ms < best) {
+        best = ms;
+        b->ctas_per_sm = c;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // capture the whole solve (parameters in, kernel, results out) as a CUDA graph
+    cudaStream_t cs;
+    QVS_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t g;
+    const cudaStream_t keep = b->stream;
+    b->stream = cs;
+    QVS_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    int st = QVS_OK;
+    if (cudaMemcpyAsync(b->theta.ptr, b->host_theta, sizeof(double) * 2 * P, cudaMemcpyHostToDevice, cs) != cudaSuccess)
+      st = QVS_ECUDA;
+    if (st == QVS_OK) st = hc::batch_launch(b, b->ctas_per_sm);
+    if (st == QVS_OK &&
+        cudaMemcpyAsync(b->host_out, b->out.ptr, sizeof(double) * ((size_t)b->count + 2 * P), cudaMemcpyDeviceToHost,
+                        cs) != cudaSuccess)
+      st = QVS_ECUDA;
+    const cudaError_t ce = cudaStreamEndCapture(cs, &g);
+    b->stream = keep;
+    cudaStreamDestroy(cs);
+    if (st != QVS_OK) return st;
+    QVS_CUDA_TRY(ce);
+    const cudaError_t ie = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    QVS_CUDA_TRY(ie);
+  }
+  QVS_CUDA_TRY(cudaGraphLaunch(b->graph, b->stream));
+  QVS_CUDA_TRY(cudaStreamSynchronize(b->stream));
+  memcpy(E, b->host_out, sizeof(double) * b->count);
+  memcpy(dgamma, b->host_out + b->count, sizeof(double) * P);
+  memcpy(dt, b->host_out + b->count + P, sizeof(double) * P);
+  return QVS_OK;
+}
+
+extern "C" int qvs_batch_info(qvs_batch_t b, int* ctas_per_sm, double* tuned_ms_1, double* tuned_ms_2) {
+  if (!b) return QVS_EINVAL;
+  if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm;
+  if (tuned_ms_1) *tuned_ms_1 = b->tuned_ms[1];
+  if (tuned_ms_2) *tuned_ms_2 = b->tuned_ms[2];
+  return QVS_OK;
+}
+
+extern "C" int qvs_batch_destroy(qvs_batch_t b) {
+  if (!b) return QVS_OK;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  else cudaDeviceSynchronize();
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  b->inst.release();
+  b->order.release();
+  b->q.release();
+  b->theta.release();
+  b->out.release();
+  b->counter.release();
+  b->ws.release();
+  if (b->host_theta) cudaFreeHost(b->host_theta);
+  if (b->host_out) cudaFreeHost(b->host_out);
+  delete b;
+  (void)cudaGetLastError();
+  return QVS_OK;
+}

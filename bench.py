@@ -190,46 +190,66 @@ def _kernel_summary(qvs, h, peak, nsteps):
     return roof, ker
 
 
-def run_extras(qvs, torch, stream, peak, steps, warmup):
+def run_extras(qvs, torch, stream, peak, steps, warmup, only=None, qwoa_n=26, qwoa_p=6, qaoaz_n=24, qaoaz_p=4,
+               batch_count=4096):
     """Objective + adjoint-gradient throughput of the QWOA circulant (N=2^26, p=6), QAOAz CSR
     (n=24, weight 12, p=4) and batched QAOA (4096 instances) workloads."""
     out = {}
-    # QWOA circulant, N = 2^26, p = 6
-    inst = wl.qwoa(26, 6)
-    q = torch.empty(1 << 26, dtype=torch.float32, device="cuda")
-    qvs.qvs_quality_subset(26, inst.weights, q, qvs.QVS_F32, stream)
-    sim = qvs.Simulator(1 << 26, qvs.QVS_C64, stream)
+    if only in (None, "qwoa"):
+        out.update(_extra_qwoa(qvs, torch, stream, peak, steps, warmup, qwoa_n, qwoa_p))
+    if only in (None, "qaoaz"):
+        out.update(_extra_qaoaz(qvs, torch, stream, peak, steps, warmup, qaoaz_n, qaoaz_p))
+    if only in (None, "batch"):
+        out.update(_extra_batch(qvs, torch, stream, peak, steps, warmup, batch_count, plain=only is None))
+    return out
+
+
+def _extra_qwoa(qvs, torch, stream, peak, steps, warmup, n, p):
+    out = {}
+    inst = wl.qwoa(n, p)
+    q = torch.empty(1 << n, dtype=torch.float32, device="cuda")
+    qvs.qvs_quality_subset(n, inst.weights, q, qvs.QVS_F32, stream)
+    sim = qvs.Simulator(1 << n, qvs.QVS_C64, stream)
     sim.set_quality(q).set_mixer(qvs.QVS_MIX_CIRCULANT, qvs.circulant_desc(inst.offsets))
     ms = _time_steps(torch, stream, lambda: sim.gradient(inst.gammas, inst.ts), steps, warmup)
     sim.set_option(qvs.QVS_OPT_PROFILE, 1)
     for _ in range(2):
         sim.gradient(inst.gammas, inst.ts)
     roof, ker = _kernel_summary(qvs, sim.h, peak, 2)
-    units = float(1 << 26) * 6
-    out["qwoa_circulant_n26_p6"] = {"value": units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
-                                    "launches_per_step": sim.launches(), "roofline": roof, "kernels": ker}
+    units = float(1 << n) * p
+    out[f"qwoa_circulant_n{n}_p{p}"] = {"value": units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                                        "launches_per_step": sim.launches(), "roofline": roof, "kernels": ker}
     sim.close()
-    del q
-    # QAOAz XY ring on the Hamming-weight-12 subspace of 24 qubits, p = 4
-    inst = wl.qaoaz(24, 12, 4)
-    states, rowptr, colind = qvs.qvs_xy_ring_csr(24, 12)
+    return out
+
+
+def _extra_qaoaz(qvs, torch, stream, peak, steps, warmup, n, p):
+    out = {}
+    # QAOAz XY ring on the Hamming-weight-n/2 subspace of n qubits
+    inst = wl.qaoaz(n, n // 2, p)
+    states, rowptr, colind = qvs.qvs_xy_ring_csr(n, n // 2)
     dim = states.shape[0]
     st = torch.from_numpy(states).cuda()
     q = torch.empty(dim, dtype=torch.float32, device="cuda")
-    qvs.qvs_quality_portfolio(24, st, inst.port.returns, inst.port.cov, inst.port.omega, q, qvs.QVS_F32, stream)
+    qvs.qvs_quality_portfolio(n, st, inst.port.returns, inst.port.cov, inst.port.omega, q, qvs.QVS_F32, stream)
     sim = qvs.Simulator(dim, qvs.QVS_C64, stream)
     sim.set_quality(q).set_mixer(qvs.QVS_MIX_CSR, qvs.csr_desc(rowptr, colind, None, 2.0))
     ms = _time_steps(torch, stream, lambda: sim.gradient(inst.gammas, inst.ts), max(2, steps // 2), 2)
     sim.set_option(qvs.QVS_OPT_PROFILE, 1)
     sim.gradient(inst.gammas, inst.ts)
     roof, ker = _kernel_summary(qvs, sim.h, peak, 1)
-    units = float(dim) * 4
-    out["qaoaz_csr_n24_k12_p4"] = {"value": units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
-                                   "launches_per_step": sim.launches(), "roofline": roof, "kernels": ker,
-                                   "nnz": int(colind.shape[0])}
+    units = float(dim) * p
+    out[f"qaoaz_csr_n{n}_k{n // 2}_p{p}"] = {"value": units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                                             "launches_per_step": sim.launches(), "roofline": roof, "kernels": ker,
+                                             "nnz": int(colind.shape[0])}
     sim.close()
-    # batched QAOA: 4096 instances, n in 12..20, p in 2..8, 3-regular graphs
-    spec = wl.batch_spec()
+    return out
+
+
+def _extra_batch(qvs, torch, stream, peak, steps, warmup, count, plain=True):
+    out = {}
+    # batched QAOA: n in 12..20, p in 2..8, 3-regular graphs
+    spec = wl.batch_spec(count=count)
     insts = [wl.maxcut3(int(n), int(p), instance=2 * 100000 + i) for i, (n, p) in enumerate(zip(spec.ns, spec.ps))]
     sizes = [1 << int(n) for n in spec.ns]
     offs = np.concatenate([[0], np.cumsum(sizes)])
@@ -241,6 +261,12 @@ def run_extras(qvs, torch, stream, peak, steps, warmup):
     gl, tl = [i.gammas for i in insts], [i.ts for i in insts]
     ms = _time_steps(torch, stream, lambda: b.gradient(gl, tl), max(3, steps // 2), 2)
     units = float(sum(s * int(p) for s, p in zip(sizes, spec.ps)))
+    entry = {"value": units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+             "instances_per_s": len(insts) / (ms * 1e-3), "launches_per_step": 1, "autotune": b.info()}
+    b.close()
+    out[f"batched_qaoa_{count}"] = entry
+    if not plain:
+        return out
     # the plain per-instance path over the same instances, timed once
     sims = []
     t0 = time.perf_counter()
@@ -257,13 +283,9 @@ def run_extras(qvs, torch, stream, peak, steps, warmup):
     plain_s = time.perf_counter() - t0
     for sim in sims:
         sim.close()
-    out["batched_qaoa_4096"] = {"value": units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
-                                "instances_per_s": len(insts) / (ms * 1e-3), "launches_per_step": 1,
-                                "autotune": b.info(),
-                                "plain_per_instance": {"value": units / plain_s, "unit": UNIT, "s_per_batch": plain_s,
-                                                       "note": "looped single-instance qvs_gradient calls, complex64"},
-                                "speedup_vs_plain": plain_s / (ms * 1e-3)}
-    b.close()
+    entry["plain_per_instance"] = {"value": units / plain_s, "unit": UNIT, "s_per_batch": plain_s,
+                                   "note": "looped single-instance qvs_gradient calls, complex64"}
+    entry["speedup_vs_plain"] = plain_s / (ms * 1e-3)
     return out
 
 
@@ -416,6 +438,24 @@ def run_ours(args):
     return 0
 
 
+def run_workload(args):
+    """One diagnostic line for a non-benchmark workload (QWOA, QAOAz or batched)."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2110_03963_gb300 import _build
+    _build.build()
+    import paper_2110_03963_gb300 as qvs
+    stream = torch.cuda.current_stream()
+    peak, _ = _peaks()
+    n = args.qubits if args.qubits != N_QUBITS else {"qwoa": 26, "qaoaz": 24, "batch": 0}[args.workload]
+    p = args.layers if args.layers != P_LAYERS else {"qwoa": 6, "qaoaz": 4, "batch": 0}[args.workload]
+    res = run_extras(qvs, torch, stream, peak, args.steps, args.warmup, only=args.workload, qwoa_n=n, qwoa_p=p,
+                     qaoaz_n=n, qaoaz_p=p, batch_count=args.count)
+    (name, entry), = res.items()
+    print(json.dumps({"workload": name, **entry}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -425,11 +465,17 @@ def main():
     ap.add_argument("--ckpt", type=int, default=None, help="checkpoint interval in layers (0 = ceil(sqrt(p)))")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the QWOA, QAOAz and batched lines")
+    ap.add_argument("--workload", default="qaoa", choices=["qaoa", "qwoa", "qaoaz", "batch"],
+                    help="qaoa = the benchmark line; the others print one diagnostic line for that workload "
+                         "(sizes from --qubits/--layers/--count)")
+    ap.add_argument("--count", type=int, default=4096, help="instances for --workload batch")
     ap.add_argument("--qubits", type=int, default=N_QUBITS, help="state size 2^qubits (28 is the benchmark)")
     ap.add_argument("--layers", type=int, default=P_LAYERS, help="depth p (8 is the benchmark)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "qaoa":
+        return run_workload(args)
     return run_ours(args)
 
 

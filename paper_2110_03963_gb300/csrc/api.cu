@@ -117,11 +117,13 @@ extern "C" int qvs_create(qvs_t* out, int64_t dim, int precision, void* stream) 
   h->n = log2_exact(dim);
   h->precision = precision;
   h->stream = (cudaStream_t)stream;
-  if (cudaGetDevice(&h->device) != cudaSuccess) {
+  if (cudaGetDevice(&h->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
     (void)cudaGetLastError();
     delete h;
     return QVS_ECUDA;
   }
+
   *out = h;
   return QVS_OK;
 }
@@ -245,6 +247,11 @@ extern "C" int qvs_set_option(qvs_t h, int option, int64_t value) {
   if (option == QVS_OPT_CKPT_LAYERS) {
     if (value < 0 || value > 4096) return QVS_EINVAL;
     h->ckpt_layers = (int)value;
+    return QVS_OK;
+  }
+  if (option == QVS_OPT_PIPELINE) {
+    if (value != 0 && value != 1) return QVS_EINVAL;
+    h->pipeline = (int)value;
     return QVS_OK;
   }
   if (option == QVS_OPT_PROFILE) {

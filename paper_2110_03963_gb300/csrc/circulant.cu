@@ -24,468 +24,36 @@
 namespace qvs {
 namespace cf {
 
-using GRow = Geo<0, 4, 5, 5>;
+int set_mixer_n20(qvs_ctx* h, const int64_t* ofs, const double* w, int nofs);
+int run_n20(qvs_ctx* h, int p, const double* gammas, const double* ts, bool grad, double* E, double* dg,
+            double* dt);
+int set_mixer_n22(qvs_ctx* h, const int64_t* ofs, const double* w, int nofs);
+int run_n22(qvs_ctx* h, int p, const double* gammas, const double* ts, bool grad, double* E, double* dg,
+            double* dt);
+int set_mixer_n24(qvs_ctx* h, const int64_t* ofs, const double* w, int nofs);
+int run_n24(qvs_ctx* h, int p, const double* gammas, const double* ts, bool grad, double* E, double* dg,
+            double* dt);
+int set_mixer_n26(qvs_ctx* h, const int64_t* ofs, const double* w, int nofs);
+int run_n26(qvs_ctx* h, int p, const double* gammas, const double* ts, bool grad, double* E, double* dg,
+            double* dt);
 
-enum ColMode : int { CF = 0, CM = 1, CL = 2, CV = 3, RCM = 4, RCF = 5 };
-enum RowMode : int { RF = 0, RR = 1 };
-
-struct CircArgs {
-  int n;                       // log2 N
-  const float2* in;            // pass input (natural positions)
-  float2* out;                 // pass output
-  const float2* psi0;          // explicit initial state (natural, normal form) or NULL
-  float2* priv_out;            // stored vector for the adjoint (thread-major), or NULL
-  const float2* priv_in;       // stored vector read by the adjoint (thread-major)
-  const float* qT;             // q in column-pass thread-major order
-  const float2* lamT;          // eigenvalues (hi, lo) in row-spectral thread-major order
-  const float2* tw14;          // e^{-2 pi i e / 2^14}
-  const float2* tlo;           // e^{-2 pi i e / N}, e < 2^13
-  const float2* thi;           // e^{-2 pi i e 2^13 / N}
-  float ph_hi, ph_lo;          // phase: gamma / 2pi (float-float)
-  float ph2_hi, ph2_lo;        // reverse passes: the phase to re-apply to the stored psi
-  float ev_hi, ev_lo;          // eigenphase: t / 2pi (float-float)
-  float init_amp;
-  double* part;                // partial rows [row * gridDim.x + blockIdx.x]
-  int row_a, row_b;
-};
-
-// thread-major private index of register r of thread tid in tile blk
-__device__ __forceinline__ size_t priv_idx(uint32_t blk, int r, int tid) {
-  return ((size_t)blk * R + r) * NT + tid;
+static int dispatch_set_mixer(qvs_ctx* h, const int64_t* ofs, const double* w, int nofs) {
+  switch (h->n) {
+    case 20: return set_mixer_n20(h, ofs, w, nofs);
+    case 22: return set_mixer_n22(h, ofs, w, nofs);
+    case 24: return set_mixer_n24(h, ofs, w, nofs);
+    case 26: return set_mixer_n26(h, ofs, w, nofs);
+  }
+  return QVS_EUNSUPPORTED;
 }
 
-// fractional turns of x * y for float-float x and y (|x y| well below 2^24)
-__device__ __forceinline__ float ff_turns(float xh, float xl, float yh, float yl) {
-  const float p = xh * yh;
-  const float e = fmaf(xh, yh, -p) + fmaf(xh, yl, xl * yh);
-  return (p - rintf(p)) + e;
-}
-
-// block sum (lanes in fp32, warps and CTAs in fp64, fixed order)
-__device__ __forceinline__ void block_store2(float a, float b, double scale, double* part, int ra, int rb) {
-  __shared__ double red[2][NT / 32];
-  const int tid = threadIdx.x;
-#pragma unroll
-  for (int o = 16; o; o >>= 1) {
-    a += __shfl_xor_sync(0xffffffffu, a, o);
-    b += __shfl_xor_sync(0xffffffffu, b, o);
-  }
-  if ((tid & 31) == 0) {
-    red[0][tid >> 5] = scale * (double)a;
-    red[1][tid >> 5] = scale * (double)b;
-  }
-  __syncthreads();
-  if (tid < 2) {
-    double s = 0.0;
-    for (int w = 0; w < NT / 32; ++w) s += red[tid][w];
-    const int row = tid == 0 ? ra : rb;
-    if (row >= 0) part[(size_t)row * gridDim.x + blockIdx.x] = s;
-  }
-}
-
-// ---------------------------------------------------------------- column pass
-
-template <class G, int MODE>
-__global__ void __launch_bounds__(NT, 1) col_kernel(const __grid_constant__ CircArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* sm = reinterpret_cast<float2*>(smem_raw);
-  constexpr int CB = G::dstart(0);
-  const int tid = threadIdx.x;
-  const uint32_t blk = blockIdx.x;
-  const uint32_t N = 1u << a.n;
-  // global index of tile index j
-  auto gidx = [&](int j) -> uint32_t {
-    return (uint32_t)(j & ((1 << CB) - 1)) | (blk << CB) | ((uint32_t)(j >> CB) << TB);
-  };
-  // four-step twiddle omega_N^(+-j_low * k_col) on layout 0 (column-spectral positions). The
-  // position-to-frequency map is a bit permutation, so it splits into a per-thread part and a
-  // compile-time per-register part.
-  auto gtw = [&](float2(&v)[R], bool conj) {
-    const int jt = G::template jthr<0>(tid_fresh());
-    const uint32_t jlt = (uint32_t)(jt & ((1 << CB) - 1)) | (blk << CB);
-    const uint32_t kt = (uint32_t)G::freq(jt >> CB);
-    static_for<R>([&](auto ri) {
-      constexpr int r = decltype(ri)::value;
-      constexpr int jr = G::jreg(0, r);
-      constexpr uint32_t jlr = (uint32_t)(jr & ((1 << CB) - 1));
-      constexpr uint32_t kr = (uint32_t)G::freq(jr >> CB);
-      const uint32_t e = ((jlt | jlr) * (kt | kr)) & (N - 1);
-      const float2 w = cmul(__ldg(a.tlo + (e & 8191u)), __ldg(a.thi + (e >> 13)));
-      v[r] = conj ? cmulc(v[r], w) : cmul(v[r], w);
-      // keep the table loads in groups of eight (bounds the registers they occupy)
-      if constexpr ((r & 7) == 7) asm volatile("" ::: "memory");
-    });
-  };
-  auto gload0 = [&](float2(&v)[R], const float2* src) {
-    const int jt = G::template jthr<0>(tid_fresh());
-    static_for<R>([&](auto ri) {
-      constexpr int r = decltype(ri)::value;
-      v[r] = __ldcs(src + gidx(jt | G::jreg(0, r)));
-    });
-  };
-  auto gstore0 = [&](const float2(&v)[R], float2* dst) {
-    const int jt = G::template jthr<0>(tid_fresh());
-    static_for<R>([&](auto ri) {
-      constexpr int r = decltype(ri)::value;
-      __stcs(dst + gidx(jt | G::jreg(0, r)), v[r]);
-    });
-  };
-  // exp(-i 2pi turns(q * g)) for the amplitude in register r of layout 2 (natural positions)
-  auto phase_cs = [&](int r, float q, float gh, float gl, float& c, float& s) {
-    __sincosf(6.28318530717958647692f * ff_turns(gh, gl, q, 0.0f), &s, &c);
-  };
-  auto qat = [&](int r) { return __ldcs(a.qT + priv_idx(blk, r, tid_fresh())); };
-  const float invL = 1.0f / (float)G::L;
-
-  float2 v[R];
-  if constexpr (MODE == CF) {
-    const int jt = G::template jthr<2>(tid);
-    static_for<R>([&](auto ri) {
-      constexpr int r = decltype(ri)::value;
-      float2 x = a.psi0 ? __ldg(a.psi0 + gidx(jt | G::jreg(2, r))) : make_float2(a.init_amp, 0.0f);
-      float c, s;
-      phase_cs(r, qat(r), a.ph_hi, a.ph_lo, c, s);
-      v[r] = make_float2(c * x.x + s * x.y, c * x.y - s * x.x);
-    });
-    tile_fwd<G>(v, sm, a.tw14, tid);
-    gtw(v, false);
-    gstore0(v, a.out);
-  } else {
-    gload0(v, a.in);
-    gtw(v, true);
-    tile_inv<G>(v, sm, a.tw14, tid);
-    if constexpr (MODE == CM) {
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const float2 x = make_float2(v[r].x * invL, v[r].y * invL);
-        if (a.priv_out) __stcs(a.priv_out + priv_idx(blk, r, tid), x);   // stored for the adjoint
-        float c, s;
-        phase_cs(r, qat(r), a.ph_hi, a.ph_lo, c, s);
-        v[r] = make_float2(c * x.x + s * x.y, c * x.y - s * x.x);
-      }
-      tile_fwd<G>(v, sm, a.tw14, tid);
-      gtw(v, false);
-      gstore0(v, a.out);
-    } else if constexpr (MODE == CL || MODE == CV) {
-      float e = 0.0f;
-      if constexpr (MODE == CV) {
-        const int jt = G::template jthr<2>(tid);
-        static_for<R>([&](auto ri) {
-          constexpr int r = decltype(ri)::value;
-          const float2 x = make_float2(v[r].x * invL, v[r].y * invL);
-          e += qat(r) * (x.x * x.x + x.y * x.y);
-          __stcs(a.out + gidx(jt | G::jreg(2, r)), x);
-        });
-      } else {
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          const float q = qat(r);
-          const float2 x = make_float2(v[r].x * invL, v[r].y * invL);
-          e += q * (x.x * x.x + x.y * x.y);
-          v[r] = make_float2(q * x.x, q * x.y);
-        }
-        tile_fwd<G>(v, sm, a.tw14, tid);
-        gtw(v, false);
-        gstore0(v, a.out);
-      }
-      block_store2(e, 0.0f, 1.0, a.part, a.row_a, -1);
-    } else {   // RCM, RCF: v = lambda' after the adjoint mixer; gamma gradient, then phase^dagger
-      float g = 0.0f;
-      const int jt = G::template jthr<2>(tid);
-      static_for<R>([&](auto ri) {
-        constexpr int r = decltype(ri)::value;
-        float2 ps;
-        if constexpr (MODE == RCM) ps = __ldcs(a.priv_in + priv_idx(blk, r, tid));
-        else ps = a.psi0 ? __ldg(a.psi0 + gidx(jt | G::jreg(2, r))) : make_float2(a.init_amp, 0.0f);
-        const float q = qat(r);
-        float c, s;
-        phase_cs(r, q, a.ph2_hi, a.ph2_lo, c, s);
-        const float2 phi = make_float2(c * ps.x + s * ps.y, c * ps.y - s * ps.x);   // P psi
-        const float2 l = make_float2(v[r].x * invL, v[r].y * invL);
-        g += q * (l.x * phi.y - l.y * phi.x);
-        v[r] = make_float2(c * l.x - s * l.y, c * l.y + s * l.x);                   // P^dagger lambda'
-      });
-      if constexpr (MODE == RCM) {
-        tile_fwd<G>(v, sm, a.tw14, tid);
-        gtw(v, false);
-        gstore0(v, a.out);
-      }
-      block_store2(g, 0.0f, 2.0, a.part, a.row_a, -1);
-    }
-  }
-}
-
-// ---------------------------------------------------------------- row pass
-
-template <int MODE>
-__global__ void __launch_bounds__(NT, 1) row_kernel(const __grid_constant__ CircArgs a) {
-  using G = GRow;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* sm = reinterpret_cast<float2*>(smem_raw);
-  const int tid = threadIdx.x;
-  const uint32_t blk = blockIdx.x;
-  const float2* src = a.in + ((size_t)blk << TB);
-  float2* dst = a.out + ((size_t)blk << TB);
-  float2 v[R];
-  {
-    const int jt = G::template jthr<2>(tid);
-    static_for<R>([&](auto ri) {
-      constexpr int r = decltype(ri)::value;
-      v[r] = __ldcs(src + (jt | G::jreg(2, r)));
-    });
-  }
-  tile_fwd<G>(v, sm, a.tw14, tid);
-  float acc = 0.0f;
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const float2 lam = __ldcs(a.lamT + priv_idx(blk, r, tid));
-    float s, c;
-    __sincosf(6.28318530717958647692f * ff_turns(lam.x, lam.y, a.ev_hi, a.ev_lo), &s, &c);
-    if constexpr (MODE == RF) {
-      v[r] = make_float2(c * v[r].x + s * v[r].y, c * v[r].y - s * v[r].x);   // exp(-i t lambda)
-      if (a.priv_out) __stcs(a.priv_out + priv_idx(blk, r, tid), v[r]);
-    } else {
-      const float2 x = __ldcs(a.priv_in + priv_idx(blk, r, tid));
-      acc += lam.x * (v[r].x * x.y - v[r].y * x.x);
-      v[r] = make_float2(c * v[r].x - s * v[r].y, c * v[r].y + s * v[r].x);   // exp(+i t lambda)
-    }
-  }
-  tile_inv<G>(v, sm, a.tw14, tid);
-  const float invL = 1.0f / (float)TILE;
-  {
-    const int jt = G::template jthr<2>(tid);
-    static_for<R>([&](auto ri) {
-      constexpr int r = decltype(ri)::value;
-      __stcs(dst + (jt | G::jreg(2, r)), make_float2(v[r].x * invL, v[r].y * invL));
-    });
-  }
-  if constexpr (MODE == RR) {
-    block_store2(acc, 0.0f, 2.0 / (double)(1ull << a.n), a.part, a.row_a, -1);
-  }
-}
-
-// ---------------------------------------------------------------- tables
-
-// eigenvalues lambda_k = sum_s w_s (2 cos(2 pi s k / N), or (-1)^k for s = N/2), fp64, stored as
-// float-float in the row-spectral thread-major order
-template <class GC>
-__global__ void __launch_bounds__(NT) lam_kernel(int n, int nofs, const int64_t* __restrict__ ofs,
-                                                 const double* __restrict__ w, float2* lamT) {
-  using G = GRow;
-  const int tid = threadIdx.x;
-  const uint32_t blk = blockIdx.x;
-  const uint64_t N = 1ull << n;
-  const int B = n - TB;
-  const uint64_t kcol = (uint64_t)GC::freq((int)blk);
-  const int jt = G::template jthr<0>(tid);
-  for (int r = 0; r < R; ++r) {
-    const int j = jt | G::jreg(0, r);
-    const uint64_t k = kcol + ((uint64_t)G::freq(j) << B);
-    double lam = 0.0;
-    for (int i = 0; i < nofs; ++i) {
-      const uint64_t s = (uint64_t)ofs[i];
-      if (2 * s == N) lam += w[i] * ((k & 1) ? -1.0 : 1.0);
-      else lam += 2.0 * w[i] * cospi(2.0 * (double)((s * k) & (N - 1)) / (double)N);
-    }
-    const float hi = (float)lam;
-    lamT[priv_idx(blk, r, tid)] = make_float2(hi, (float)(lam - (double)hi));
-  }
-}
-
-template <class GC>
-__global__ void __launch_bounds__(NT) qperm_kernel(const float* __restrict__ q, float* __restrict__ qT) {
-  constexpr int CB = GC::dstart(0);
-  const int tid = threadIdx.x;
-  const uint32_t blk = blockIdx.x;
-  const int jt = GC::template jthr<2>(tid);
-  static_for<R>([&](auto ri) {
-    constexpr int r = decltype(ri)::value;
-    const int j = jt | GC::jreg(2, r);
-    const uint32_t g = (uint32_t)(j & ((1 << CB) - 1)) | (blk << CB) | ((uint32_t)(j >> CB) << TB);
-    qT[priv_idx(blk, r, tid)] = q[g];
-  });
-}
-
-// ---------------------------------------------------------------- host driver
-
-template <class GC>
-struct Driver {
-  static int set_mixer(qvs_ctx* h, const int64_t* ofs_dev, const double* w_dev, int nofs) {
-    const uint32_t grid = (uint32_t)(h->dim >> TB);
-    QVS_TRY(h->circ.lam.ensure(sizeof(float2) * (size_t)h->dim));
-    lam_kernel<GC><<<grid, NT, 0, h->stream>>>(h->n, nofs, ofs_dev, w_dev, h->circ.lam.as<float2>());
-    QVS_CUDA_TRY(cudaGetLastError());
-    return QVS_OK;
-  }
-
-  static int run(qvs_ctx* h, int p, const double* gammas, const double* ts, bool grad, double* E,
-                 double* dg, double* dt) {
-    const int64_t dim = h->dim;
-    const uint32_t grid = (uint32_t)(dim >> TB);
-    const size_t vb = sizeof(float2) * (size_t)dim;
-    const size_t smem = sizeof(float2) * TILE;
-    // q in column-pass order (rebuilt when q or the mixer changed)
-    if (!h->circ.qT_valid) {
-      QVS_TRY(h->circ.qT.ensure(sizeof(float) * (size_t)dim));
-      qperm_kernel<GC><<<grid, NT, 0, h->stream>>>(h->q.as<float>(), h->circ.qT.as<float>());
-      QVS_CUDA_TRY(cudaGetLastError());
-      h->circ.qT_valid = true;
-    }
-    QVS_TRY(h->psi.ensure(vb));
-    if (grad) {
-      QVS_TRY(h->lam.ensure(vb));
-      QVS_TRY(h->ckpt.ensure(vb * (size_t)(2 * p)));   // psi_1..psi_{p-1}, X_1..X_p
-    }
-    const int nslots = 1 + 2 * p;
-    const int nrows = 2 * p + 1;   // 0: E; 1..p: dgamma_k; p+1..2p: dt_k
-    QVS_TRY(h->part.ensure(sizeof(double) * (size_t)nrows * grid));
-    QVS_TRY(h->res.ensure(sizeof(double) * nslots));
-    QVS_TRY(h->rowmap.ensure(sizeof(int) * 3 * nslots));
-    std::vector<int> rowmap(3 * (size_t)nslots, -1);
-    for (int s = 0; s < (grad ? nslots : 1); ++s) rowmap[3 * s] = s;
-    QVS_CUDA_TRY(cudaMemcpyAsync(h->rowmap.ptr, rowmap.data(), sizeof(int) * rowmap.size(),
-                                 cudaMemcpyHostToDevice, h->stream));
-    for (auto f : {col_kernel<GC, CF>, col_kernel<GC, CM>, col_kernel<GC, CL>, col_kernel<GC, CV>,
-                   col_kernel<GC, RCM>, col_kernel<GC, RCF>})
-      QVS_CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    for (auto f : {row_kernel<RF>, row_kernel<RR>})
-      QVS_CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-
-    float2* W = h->psi.as<float2>();
-    float2* Lb = grad ? h->lam.as<float2>() : nullptr;
-    float2* S = grad ? h->ckpt.as<float2>() : nullptr;             // psi_k, k = 1..p-1
-    float2* X = grad ? S + (size_t)p * dim : nullptr;             // X_k, k = 1..p
-    auto Sk = [&](int k) { return S + (size_t)(k - 1) * dim; };
-    auto Xk = [&](int k) { return X + (size_t)(k - 1) * dim; };
-
-    CircArgs base{};
-    base.n = h->n;
-    base.psi0 = h->have_psi0 ? h->psi0.as<float2>() : nullptr;
-    base.qT = h->circ.qT.as<float>();
-    base.lamT = h->circ.lam.as<float2>();
-    base.tw14 = h->circ.tab.as<float2>();
-    base.tlo = base.tw14 + TILE;
-    base.thi = base.tlo + 8192;
-    base.init_amp = (float)(1.0 / sqrt((double)dim));
-    base.part = h->part.as<double>();
-    base.row_a = base.row_b = -1;
-    auto ph = [&](CircArgs& a, int k) { turns_split(gammas[k], &a.ph_hi, &a.ph_lo); };
-    auto ev = [&](CircArgs& a, int k) { turns_split(ts[k], &a.ev_hi, &a.ev_lo); };
-    const double colb = 16.0 + 4.0, rowb = 16.0 + 8.0;   // bytes per amplitude (state r+w, q / lambda)
-    int64_t launches = 0;
-    auto launch_col = [&](int mode, const CircArgs& a, double bytes) -> int {
-      cudaEvent_t e0;
-      QVS_TRY(prof_begin(h, &e0));
-      switch (mode) {
-        case CF: col_kernel<GC, CF><<<grid, NT, smem, h->stream>>>(a); break;
-        case CM: col_kernel<GC, CM><<<grid, NT, smem, h->stream>>>(a); break;
-        case CL: col_kernel<GC, CL><<<grid, NT, smem, h->stream>>>(a); break;
-        case CV: col_kernel<GC, CV><<<grid, NT, smem, h->stream>>>(a); break;
-        case RCM: col_kernel<GC, RCM><<<grid, NT, smem, h->stream>>>(a); break;
-        case RCF: col_kernel<GC, RCF><<<grid, NT, smem, h->stream>>>(a); break;
-      }
-      QVS_CUDA_TRY(cudaGetLastError());
-      ++launches;
-      static const char* names[] = {"circ_col_first", "circ_col_mid", "circ_col_last", "circ_col_last_evolve",
-                                    "circ_col_adjoint", "circ_col_adjoint_first"};
-      return prof_end(h, names[mode], bytes * (double)dim, e0);
-    };
-    auto launch_row = [&](int mode, const CircArgs& a, double bytes) -> int {
-      cudaEvent_t e0;
-      QVS_TRY(prof_begin(h, &e0));
-      if (mode == RF) row_kernel<RF><<<grid, NT, smem, h->stream>>>(a);
-      else row_kernel<RR><<<grid, NT, smem, h->stream>>>(a);
-      QVS_CUDA_TRY(cudaGetLastError());
-      ++launches;
-      return prof_end(h, mode == RF ? "circ_row" : "circ_row_adjoint", bytes * (double)dim, e0);
-    };
-
-    // forward: C_0, R_1, C_1, ..., R_p, C_p
-    {
-      CircArgs a = base;
-      ph(a, 0);
-      a.out = W;
-      QVS_TRY(launch_col(CF, a, 12.0 + (base.psi0 ? 8.0 : 0.0)));
-    }
-    for (int k = 1; k <= p; ++k) {
-      CircArgs r = base;
-      ev(r, k - 1);
-      r.in = W;
-      r.out = W;
-      r.priv_out = grad ? Xk(k) : nullptr;
-      QVS_TRY(launch_row(RF, r, rowb + (grad ? 8.0 : 0.0)));
-      CircArgs c = base;
-      c.in = W;
-      if (k < p) {
-        ph(c, k);
-        c.out = W;
-        c.priv_out = grad ? Sk(k) : nullptr;
-        QVS_TRY(launch_col(CM, c, colb + (grad ? 8.0 : 0.0)));
-      } else if (grad) {
-        c.out = Lb;
-        c.row_a = 0;
-        QVS_TRY(launch_col(CL, c, colb));
-      } else {
-        c.out = W;
-        c.row_a = 0;
-        QVS_TRY(launch_col(CV, c, colb));
-      }
-    }
-    // adjoint: R_p^dag, C_{p-1}^dag, ..., R_1^dag, C_0^dag
-    if (grad) {
-      for (int k = p; k >= 1; --k) {
-        CircArgs r = base;
-        ev(r, k - 1);
-        r.in = Lb;
-        r.out = Lb;
-        r.priv_in = Xk(k);
-        r.row_a = 1 + p + (k - 1);
-        QVS_TRY(launch_row(RR, r, rowb + 8.0));
-        CircArgs c = base;
-        c.in = Lb;
-        c.out = Lb;
-        turns_split(gammas[k - 1], &c.ph2_hi, &c.ph2_lo);
-        c.row_a = 1 + (k - 1);
-        if (k >= 2) {
-          c.priv_in = Sk(k - 1);
-          QVS_TRY(launch_col(RCM, c, colb + 8.0));
-        } else {
-          QVS_TRY(launch_col(RCF, c, 12.0 + (base.psi0 ? 8.0 : 0.0)));
-        }
-      }
-    }
-    const int nout = grad ? nslots : 1;
-    {
-      cudaEvent_t e0;
-      QVS_TRY(prof_begin(h, &e0));
-      QVS_TRY(reduce_rows(h, h->part.as<double>(), grid, h->rowmap.as<int>(), nout, h->res.as<double>()));
-      QVS_TRY(prof_end(h, "reduce_rows", 8.0 * grid * nout, e0));
-      ++launches;
-    }
-    h->launches = launches;
-    QVS_TRY(ensure_host_res(h, p));
-    QVS_CUDA_TRY(cudaMemcpyAsync(h->host_res, h->res.ptr, sizeof(double) * nout, cudaMemcpyDeviceToHost,
-                                 h->stream));
-    QVS_CUDA_TRY(cudaStreamSynchronize(h->stream));
-    QVS_TRY(prof_flush(h));
-    *E = h->host_res[0];
-    if (grad)
-      for (int k = 0; k < p; ++k) {
-        dg[k] = h->host_res[1 + k];
-        dt[k] = h->host_res[1 + p + k];
-      }
-    return QVS_OK;
-  }
-};
-
-template <class F>
-static int dispatch(int n, F&& f) {
-  switch (n) {
-    case 20: return f(Driver<Geo<8, 2, 2, 2>>{});
-    case 22: return f(Driver<Geo<6, 2, 3, 3>>{});
-    case 24: return f(Driver<Geo<4, 3, 3, 4>>{});
-    case 26: return f(Driver<Geo<2, 4, 4, 4>>{});
-    case 28: return f(Driver<Geo<0, 4, 5, 5>>{});
+static int dispatch_run(qvs_ctx* h, int p, const double* g, const double* t, bool grad, double* E, double* dg,
+                        double* dt) {
+  switch (h->n) {
+    case 20: return run_n20(h, p, g, t, grad, E, dg, dt);
+    case 22: return run_n22(h, p, g, t, grad, E, dg, dt);
+    case 24: return run_n24(h, p, g, t, grad, E, dg, dt);
+    case 26: return run_n26(h, p, g, t, grad, E, dg, dt);
   }
   return QVS_EUNSUPPORTED;
 }
@@ -502,36 +70,36 @@ int circ_set_mixer(qvs_ctx* h, const qvs_mixer_desc* d) {
     if (d->offsets[i] <= 0 || d->offsets[i] >= N) return QVS_EINVAL;
     if (d->offset_weights && !isfinite(d->offset_weights[i])) return QVS_EINVAL;
   }
-  // twiddle tables: tw14 (2^14), tlo (2^13), thi (N / 2^13), in fp64 then rounded once
-  const int64_t nhi = N >> 13;
-  std::vector<float2> tab((size_t)(TILE + 8192 + nhi));
+  // twiddle sub-tables (fp64, rounded once): A14[k] = w14^(128k), B14[k] = w14^k,
+  // C0[k] = wN^k, C1[k] = wN^(128k), C2[k] = wN^(2^14 k), C3[k] = wN^(2^21 k), w_M = e^{-2 pi i / M}
+  std::vector<float2> tab(TW_SLOTS);
   const double two_pi = 6.283185307179586476925286766559;
-  for (int e = 0; e < TILE; ++e) {
-    const double ang = two_pi * (double)e / (double)TILE;
-    tab[e] = make_float2((float)cos(ang), (float)-sin(ang));
-  }
-  for (int e = 0; e < 8192; ++e) {
-    const double ang = two_pi * (double)e / (double)N;
-    tab[TILE + e] = make_float2((float)cos(ang), (float)-sin(ang));
-  }
-  for (int64_t e = 0; e < nhi; ++e) {
-    const double ang = two_pi * (double)((e << 13) % N) / (double)N;
-    tab[TILE + 8192 + e] = make_float2((float)cos(ang), (float)-sin(ang));
+  auto w = [&](int64_t e, int64_t M) {
+    const double ang = two_pi * (double)(e % M) / (double)M;
+    return make_float2((float)cos(ang), (float)-sin(ang));
+  };
+  for (int k = 0; k < 128; ++k) {
+    tab[TW_A14 + k] = w(128 * (int64_t)k, TILE);
+    tab[TW_B14 + k] = w(k, TILE);
+    tab[TW_C0 + k] = w(k, N);
+    tab[TW_C1 + k] = w((int64_t)k << 7, N);
+    tab[TW_C2 + k] = w((int64_t)k << 14, N);
+    tab[TW_C3 + k] = w((int64_t)k << 21, N);
   }
   QVS_TRY(h->circ.tab.ensure(sizeof(float2) * tab.size()));
   QVS_CUDA_TRY(cudaMemcpyAsync(h->circ.tab.ptr, tab.data(), sizeof(float2) * tab.size(),
                                cudaMemcpyHostToDevice, h->stream));
-  std::vector<double> w(d->n_offsets, 1.0);
+  std::vector<double> wt(d->n_offsets, 1.0);
   if (d->offset_weights)
-    for (int i = 0; i < d->n_offsets; ++i) w[i] = d->offset_weights[i];
+    for (int i = 0; i < d->n_offsets; ++i) wt[i] = d->offset_weights[i];
   QVS_TRY(h->work.ensure(sizeof(int64_t) * d->n_offsets + sizeof(double) * d->n_offsets));
   int64_t* ofs_dev = h->work.as<int64_t>();
   double* w_dev = reinterpret_cast<double*>(ofs_dev + d->n_offsets);
   QVS_CUDA_TRY(cudaMemcpyAsync(ofs_dev, d->offsets, sizeof(int64_t) * d->n_offsets, cudaMemcpyHostToDevice,
                                h->stream));
-  QVS_CUDA_TRY(cudaMemcpyAsync(w_dev, w.data(), sizeof(double) * d->n_offsets, cudaMemcpyHostToDevice,
+  QVS_CUDA_TRY(cudaMemcpyAsync(w_dev, wt.data(), sizeof(double) * d->n_offsets, cudaMemcpyHostToDevice,
                                h->stream));
-  const int st = dispatch(h->n, [&](auto drv) { return decltype(drv)::set_mixer(h, ofs_dev, w_dev, d->n_offsets); });
+  const int st = dispatch_set_mixer(h, ofs_dev, w_dev, d->n_offsets);
   if (st != QVS_OK) return st;
   QVS_CUDA_TRY(cudaStreamSynchronize(h->stream));   // host staging buffers go out of scope
   h->circ.qT_valid = false;
@@ -540,9 +108,7 @@ int circ_set_mixer(qvs_ctx* h, const qvs_mixer_desc* d) {
 
 int circ_evolve(qvs_ctx* h, int p, const double* gammas, const double* ts) {
   double E = 0.0;
-  const int st = cf::dispatch(h->n, [&](auto drv) {
-    return decltype(drv)::run(h, p, gammas, ts, false, &E, nullptr, nullptr);
-  });
+  const int st = cf::dispatch_run(h, p, gammas, ts, false, &E, nullptr, nullptr);
   if (st != QVS_OK) return st;
   h->E = E;
   h->have_E = true;
@@ -551,7 +117,7 @@ int circ_evolve(qvs_ctx* h, int p, const double* gammas, const double* ts) {
 
 int circ_gradient(qvs_ctx* h, int p, const double* gammas, const double* ts, double* E, double* dg,
                   double* dt) {
-  return cf::dispatch(h->n, [&](auto drv) { return decltype(drv)::run(h, p, gammas, ts, true, E, dg, dt); });
+  return cf::dispatch_run(h, p, gammas, ts, true, E, dg, dt);
 }
 
 }  // namespace qvs

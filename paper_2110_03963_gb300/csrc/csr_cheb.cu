@@ -52,7 +52,11 @@ __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
 }
 
 // sum over the row's nonzeros of value * x[col], by LPR lanes. Every lane of the warp must call
-// it (the lane sum uses full-warp shuffles); lanes past the last row pass valid = false.
+// it (the lane sum uses full-warp shuffles); lanes past the last row pass valid = false. Each
+// lane issues the index loads of up to UNR nonzeros before their gathers, so the
+// row pointer -> column index -> vector chain is paid once per UNR*LPR nonzeros.
+constexpr int UNR = 4;
+
 __device__ __forceinline__ float2 row_spmv(const uint32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
                                            const float* __restrict__ values, float iv,
                                            const float2* __restrict__ x, int64_t row, int lane, bool valid) {
@@ -62,12 +66,24 @@ __device__ __forceinline__ float2 row_spmv(const uint32_t* __restrict__ rowptr, 
     b = __ldg(rowptr + row);
     e = __ldg(rowptr + row + 1);
   }
-  for (uint32_t j = b + lane; j < e; j += LPR) {
-    const int32_t c = __ldcs(colind + j);
-    const float v = values ? __ldcs(values + j) : iv;
-    const float2 t = __ldg(x + c);
-    acc.x = fmaf(v, t.x, acc.x);
-    acc.y = fmaf(v, t.y, acc.y);
+  for (uint32_t j0 = b + lane; j0 < e; j0 += UNR * LPR) {
+    int32_t c[UNR];
+    float v[UNR];
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+      const uint32_t j = j0 + u * LPR;
+      const bool in = j < e;
+      c[u] = in ? __ldcs(colind + j) : -1;
+      v[u] = in ? (values ? __ldcs(values + j) : iv) : 0.f;
+    }
+    float2 t[UNR];
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) t[u] = c[u] >= 0 ? __ldg(x + c[u]) : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+      acc.x = fmaf(v[u], t[u].x, acc.x);
+      acc.y = fmaf(v[u], t[u].y, acc.y);
+    }
   }
 #pragma unroll
   for (int o = LPR / 2; o; o >>= 1) {

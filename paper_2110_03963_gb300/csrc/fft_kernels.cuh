@@ -119,9 +119,12 @@ __device__ __forceinline__ int tid_fresh() {
   return t;
 }
 
-// shared-memory slot of tile index j (XOR swizzle; conflict-free 16-lane phases for the step
-// layouts of the 14-bit row transform and the 12-bit column transform)
-__device__ __forceinline__ int spos(int j) { return j ^ ((j >> 4) & 15) ^ ((j >> 8) & 15); }
+// shared-memory slot of tile index j: one padding slot after every 16 amplitudes and one more
+// after every 256. The map is additive over disjoint index bits (a register's slot is the
+// thread's base slot plus a compile-time constant) and keeps the 16-lane phases of the step layouts
+// of the 14-bit row transform and the 12-bit column transform conflict-free.
+__host__ __device__ __forceinline__ constexpr int spos(int j) { return j + (j >> 4) + (j >> 8); }
+constexpr int SM_SLOTS = TILE + (TILE >> 4) + (TILE >> 8);
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
@@ -191,27 +194,41 @@ __device__ __forceinline__ void small_idft(float2 (&v)[R]) {
 // shared-memory transpose from step layout KF to step layout KT
 template <class G, int KF, int KT>
 __device__ __forceinline__ void xchg(float2 (&v)[R], float2* sm, int tid) {
-  const int jf = G::template jthr<KF>(tid);
+  float2* bf = sm + spos(G::template jthr<KF>(tid));
   static_for<R>([&](auto ri) {
     constexpr int r = decltype(ri)::value;
-    constexpr int jr = G::jreg(KF, r);
-    sm[spos(jf | jr)] = v[r];
+    constexpr int o = spos(G::jreg(KF, r));
+    bf[o] = v[r];
   });
   __syncthreads();
-  const int jt = G::template jthr<KT>(tid);
+  const float2* bt = sm + spos(G::template jthr<KT>(tid));
   static_for<R>([&](auto ri) {
     constexpr int r = decltype(ri)::value;
-    constexpr int jr = G::jreg(KT, r);
-    v[r] = sm[spos(jt | jr)];
+    constexpr int o = spos(G::jreg(KT, r));
+    v[r] = bt[o];
   });
   __syncthreads();
 }
 
+// Shared-memory twiddle sub-tables (built once per CTA from a 768-entry global table computed in
+// fp64 and rounded once): e^{-2 pi i e / 2^14} = A14[e >> 7] * B14[e & 127], and for the
+// four-step twiddle of an N-point transform, e^{-2 pi i e / N} = C0[e & 127] * C1[(e >> 7) & 127]
+// * C2[(e >> 14) & 127] * C3[e >> 21] (N <= 2^28).
+constexpr int TW_A14 = 0, TW_B14 = 128, TW_C0 = 256, TW_C1 = 384, TW_C2 = 512, TW_C3 = 640, TW_SLOTS = 768;
+
+__device__ __forceinline__ float2 tw14(const float2* __restrict__ ts, int e) {
+  return cmul(ts[TW_A14 + (e >> 7)], ts[TW_B14 + (e & 127)]);
+}
+__device__ __forceinline__ float2 twN(const float2* __restrict__ ts, uint32_t e) {
+  return cmul(cmul(ts[TW_C0 + (e & 127)], ts[TW_C1 + ((e >> 7) & 127)]),
+              cmul(ts[TW_C2 + ((e >> 14) & 127)], ts[TW_C3 + (e >> 21)]));
+}
+
 // Twiddle between digit 3 and digit 2 (in step layout 2): omega_L^((j1 + 2^D1 j2) * k3), and
-// between digit 2 and digit 1 (in step layout 1): omega_L^(2^D3 * j1 * k2). tw14 holds
-// e^{-2 pi i e / 2^14}; conj = true applies the conjugate (inverse transform).
+// between digit 2 and digit 1 (in step layout 1): omega_L^(2^D3 * j1 * k2). conj = true applies
+// the conjugate (inverse transform).
 template <class G, bool CONJ>
-__device__ __forceinline__ void twiddle32(float2 (&v)[R], const float2* __restrict__ tw14, int tid) {
+__device__ __forceinline__ void twiddle32(float2 (&v)[R], const float2* ts, int tid) {
   constexpr int D1 = G::dsize(0), D2 = G::dsize(1), D3 = G::dsize(2);
   const int jt = G::template jthr<2>(tid_fresh());
   static_for<R>([&](auto ri) {
@@ -220,13 +237,13 @@ __device__ __forceinline__ void twiddle32(float2 (&v)[R], const float2* __restri
     if constexpr (k3 != 0) {
       const int jlow = ((jt | G::jreg(2, r)) >> G::dstart(0)) & ((1 << (D1 + D2)) - 1);
       const int e = (jlow * k3) & (G::L - 1);
-      const float2 w = __ldg(tw14 + (e << (TB - G::B)));
+      const float2 w = tw14(ts, e << (TB - G::B));
       v[r] = CONJ ? cmulc(v[r], w) : cmul(v[r], w);
     }
   });
 }
 template <class G, bool CONJ>
-__device__ __forceinline__ void twiddle21(float2 (&v)[R], const float2* __restrict__ tw14, int tid) {
+__device__ __forceinline__ void twiddle21(float2 (&v)[R], const float2* ts, int tid) {
   constexpr int D1 = G::dsize(0), D2 = G::dsize(1), D3 = G::dsize(2);
   const int jt = G::template jthr<1>(tid_fresh());
   static_for<R>([&](auto ri) {
@@ -235,7 +252,7 @@ __device__ __forceinline__ void twiddle21(float2 (&v)[R], const float2* __restri
     if constexpr (k2 != 0) {
       const int j1 = ((jt | G::jreg(1, r)) >> G::dstart(0)) & ((1 << D1) - 1);
       const int e = ((j1 * k2) << D3) & (G::L - 1);
-      const float2 w = __ldg(tw14 + (e << (TB - G::B)));
+      const float2 w = tw14(ts, e << (TB - G::B));
       v[r] = CONJ ? cmulc(v[r], w) : cmul(v[r], w);
     }
   });
@@ -243,25 +260,25 @@ __device__ __forceinline__ void twiddle21(float2 (&v)[R], const float2* __restri
 
 // forward tile DFT: from step layout 2 (natural order in the transform bits) to step layout 0
 template <class G>
-__device__ __forceinline__ void tile_fwd(float2 (&v)[R], float2* sm, const float2* tw14, int tid) {
+__device__ __forceinline__ void tile_fwd(float2 (&v)[R], float2* sm, const float2* ts, int tid) {
   small_dft<G, 2>(v);
-  twiddle32<G, false>(v, tw14, tid);
+  twiddle32<G, false>(v, ts, tid);
   xchg<G, 2, 1>(v, sm, tid);
   small_dft<G, 1>(v);
-  twiddle21<G, false>(v, tw14, tid);
+  twiddle21<G, false>(v, ts, tid);
   xchg<G, 1, 0>(v, sm, tid);
   small_dft<G, 0>(v);
 }
 
 // inverse tile DFT (unscaled): from step layout 0 back to step layout 2
 template <class G>
-__device__ __forceinline__ void tile_inv(float2 (&v)[R], float2* sm, const float2* tw14, int tid) {
+__device__ __forceinline__ void tile_inv(float2 (&v)[R], float2* sm, const float2* ts, int tid) {
   small_idft<G, 0>(v);
   xchg<G, 0, 1>(v, sm, tid);
-  twiddle21<G, true>(v, tw14, tid);
+  twiddle21<G, true>(v, ts, tid);
   small_idft<G, 1>(v);
   xchg<G, 1, 2>(v, sm, tid);
-  twiddle32<G, true>(v, tw14, tid);
+  twiddle32<G, true>(v, ts, tid);
   small_idft<G, 2>(v);
 }
 

@@ -34,9 +34,13 @@ __host__ __device__ __forceinline__ constexpr int tj(int r, int tid) {
 __host__ __device__ __forceinline__ constexpr int regbit(int L, int i) {
   return L == 0 ? (i == 0 ? 0 : 8 + i) : (L == 1 ? 1 + i : 5 + i);
 }
-// shared-memory slot of tile index j: XOR swizzle of bits 1..3 by bits 5..7 keeps the 16-lane
-// phases of 8-byte accesses conflict-free in all three layouts and keeps pairs (j, j^1) adjacent.
-__device__ __forceinline__ int spos(int j) { return j ^ ((j >> 4) & 0xE); }
+// shared-memory slot of tile index j: two padding slots after every 32 amplitudes. The map is
+// additive over disjoint index bits, so a register's slot is the thread's base slot plus a
+// compile-time constant (no per-access index arithmetic); the 16-lane phases of 8-byte accesses
+// (L1, L2) and the 8-lane phases of 16-byte accesses (L0) hit distinct banks, and pairs (j, j^1)
+// stay adjacent and 16-byte aligned.
+__host__ __device__ __forceinline__ constexpr int spos(int j) { return j + 2 * (j >> 5); }
+constexpr int SM_SLOTS = TILE + 2 * (TILE >> 5);   // slots per shared buffer
 
 // Tile geometry. Tile bits 0..s-1 are the low index bits 0..s-1 (a contiguous chunk of 2^s
 // amplitudes); tile bits s..TB-1 are the consecutive index bits hfirst..hfirst+TB-s-1. The CTA
@@ -215,110 +219,134 @@ __device__ __forceinline__ void unrot_layout_acc(C (&p)[R], C (&l)[R], uint32_t 
 }
 
 // shared-memory transpose from layout LF to layout LT
+template <int L, class C>
+__device__ __forceinline__ void sput(const C (&v)[R], C* sm, int tid);
+template <int L, class C>
+__device__ __forceinline__ void sget(C (&v)[R], const C* sm, int tid);
+
 template <int LF, int LT, class C>
 __device__ __forceinline__ void xchg(C (&v)[R], C* sm, int tid) {
-  if constexpr (LF == 0 && sizeof(C) == 8) {
-    float4* s4 = reinterpret_cast<float4*>(sm);
-#pragma unroll
-    for (int r = 0; r < R; r += 2) {
-      const float2 a = *reinterpret_cast<float2*>(&v[r]);
-      const float2 b = *reinterpret_cast<float2*>(&v[r + 1]);
-      s4[spos(tj<0>(r, tid)) >> 1] = make_float4(a.x, a.y, b.x, b.y);
-    }
-  } else {
-#pragma unroll
-    for (int r = 0; r < R; ++r) sm[spos(tj<LF>(r, tid))] = v[r];
-  }
+  sput<LF>(v, sm, tid);
   __syncthreads();
-  if constexpr (LT == 0 && sizeof(C) == 8) {
-    const float4* s4 = reinterpret_cast<const float4*>(sm);
-#pragma unroll
-    for (int r = 0; r < R; r += 2) {
-      const float4 w = s4[spos(tj<0>(r, tid)) >> 1];
-      *reinterpret_cast<float2*>(&v[r]) = make_float2(w.x, w.y);
-      *reinterpret_cast<float2*>(&v[r + 1]) = make_float2(w.z, w.w);
-    }
-  } else {
-#pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = sm[spos(tj<LT>(r, tid))];
-  }
+  sget<LT>(v, sm, tid);
   __syncthreads();
 }
 
 template <int L, class C>
 __device__ __forceinline__ void sput(const C (&v)[R], C* sm, int tid) {
+  C* b = sm + spos(tj<L>(0, tid));
   if constexpr (L == 0 && sizeof(C) == 8) {
-    float4* s4 = reinterpret_cast<float4*>(sm);
 #pragma unroll
     for (int r = 0; r < R; r += 2) {
-      const float2 a = *reinterpret_cast<const float2*>(&v[r]);
-      const float2 b = *reinterpret_cast<const float2*>(&v[r + 1]);
-      s4[spos(tj<0>(r, tid)) >> 1] = make_float4(a.x, a.y, b.x, b.y);
+      const float2 x = *reinterpret_cast<const float2*>(&v[r]);
+      const float2 y = *reinterpret_cast<const float2*>(&v[r + 1]);
+      *reinterpret_cast<float4*>(b + spos(tj<0>(r, 0))) = make_float4(x.x, x.y, y.x, y.y);
     }
   } else {
 #pragma unroll
-    for (int r = 0; r < R; ++r) sm[spos(tj<L>(r, tid))] = v[r];
+    for (int r = 0; r < R; ++r) b[spos(tj<L>(r, 0))] = v[r];
   }
 }
 
 template <int L, class C>
 __device__ __forceinline__ void sget(C (&v)[R], const C* sm, int tid) {
+  const C* b = sm + spos(tj<L>(0, tid));
   if constexpr (L == 0 && sizeof(C) == 8) {
-    const float4* s4 = reinterpret_cast<const float4*>(sm);
 #pragma unroll
     for (int r = 0; r < R; r += 2) {
-      const float4 w = s4[spos(tj<0>(r, tid)) >> 1];
+      const float4 w = *reinterpret_cast<const float4*>(b + spos(tj<0>(r, 0)));
       *reinterpret_cast<float2*>(&v[r]) = make_float2(w.x, w.y);
       *reinterpret_cast<float2*>(&v[r + 1]) = make_float2(w.z, w.w);
     }
   } else {
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = sm[spos(tj<L>(r, tid))];
+    for (int r = 0; r < R; ++r) v[r] = b[spos(tj<L>(r, 0))];
   }
 }
 
-// two vectors through two shared buffers (sm and sm + TILE) with one barrier pair
-template <int LF, int LT, class C>
-__device__ __forceinline__ void xchg2(C (&a)[R], C (&b)[R], C* sm, int tid) {
-  sput<LF>(a, sm, tid);
-  sput<LF>(b, sm + TILE, tid);
-  __syncthreads();
-  sget<LT>(a, sm, tid);
-  sget<LT>(b, sm + TILE, tid);
-  __syncthreads();
-}
-
-// ---------------------------------------------------------------- global loads and stores
-// off = tile base + offset of the thread's own index bits in layout L; each register's offset is
-// formed at the access (two logic ops and a shift) rather than held in registers.
-
+// read layout L from a tile staged in shared memory in plain tile-index order (as the bulk copies
+// leave it); conflict-free for L0 (16-byte, consecutive pairs) and L2 (8-byte, consecutive lanes)
 template <int L, class C>
-__device__ __forceinline__ void gload(C (&v)[R], const C* __restrict__ g, uint32_t off, const Tile& t) {
+__device__ __forceinline__ void sget_lin(C (&v)[R], const C* st, int tid) {
+  const C* b = st + tj<L>(0, tid);
   if constexpr (L == 0 && sizeof(C) == 8) {
 #pragma unroll
     for (int r = 0; r < R; r += 2) {
-      const float4 w = __ldcs(reinterpret_cast<const float4*>(g + off + toff(t, tj<L>(r, 0))));
+      const float4 w = *reinterpret_cast<const float4*>(b + tj<0>(r, 0));
       *reinterpret_cast<float2*>(&v[r]) = make_float2(w.x, w.y);
       *reinterpret_cast<float2*>(&v[r + 1]) = make_float2(w.z, w.w);
     }
   } else {
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = __ldcs(g + off + toff(t, tj<L>(r, 0)));
+    for (int r = 0; r < R; ++r) v[r] = b[tj<L>(r, 0)];
+  }
+}
+
+// two vectors through two shared buffers (sm and sm + SM_SLOTS) with one barrier pair
+template <int LF, int LT, class C>
+__device__ __forceinline__ void xchg2(C (&a)[R], C (&b)[R], C* sm, int tid) {
+  sput<LF>(a, sm, tid);
+  sput<LF>(b, sm + SM_SLOTS, tid);
+  __syncthreads();
+  sget<LT>(a, sm, tid);
+  sget<LT>(b, sm + SM_SLOTS, tid);
+  __syncthreads();
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// ---------------------------------------------------------------- global loads and stores
+// off = tile base + offset of the thread's own index bits in layout L. The tile map is additive
+// over disjoint index bits, so the offset of register r is the sum of the offsets of its set
+// register bits: four per-layout values, combined with at most three additions per access.
+
+template <int L>
+__device__ __forceinline__ void reg_bit_offsets(const Tile& t, uint32_t (&o)[RB]) {
+#pragma unroll
+  for (int i = 0; i < RB; ++i) o[i] = toff(t, 1u << regbit(L, i));
+}
+
+__device__ __forceinline__ uint32_t reg_off(const uint32_t (&o)[RB], int r) {
+  uint32_t x = 0;
+#pragma unroll
+  for (int i = 0; i < RB; ++i)
+    if ((r >> i) & 1) x += o[i];
+  return x;
+}
+
+template <int L, class C>
+__device__ __forceinline__ void gload(C (&v)[R], const C* __restrict__ g, uint32_t off, const Tile& t) {
+  uint32_t o[RB];
+  reg_bit_offsets<L>(t, o);
+  if constexpr (L == 0 && sizeof(C) == 8) {
+#pragma unroll
+    for (int r = 0; r < R; r += 2) {
+      const float4 w = __ldcs(reinterpret_cast<const float4*>(g + off + reg_off(o, r)));
+      *reinterpret_cast<float2*>(&v[r]) = make_float2(w.x, w.y);
+      *reinterpret_cast<float2*>(&v[r + 1]) = make_float2(w.z, w.w);
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = __ldcs(g + off + reg_off(o, r));
   }
 }
 
 template <int L, class C>
 __device__ __forceinline__ void gstore(const C (&v)[R], C* __restrict__ g, uint32_t off, const Tile& t) {
+  uint32_t o[RB];
+  reg_bit_offsets<L>(t, o);
   if constexpr (L == 0 && sizeof(C) == 8) {
 #pragma unroll
     for (int r = 0; r < R; r += 2) {
       const float2 a = *reinterpret_cast<const float2*>(&v[r]);
       const float2 b = *reinterpret_cast<const float2*>(&v[r + 1]);
-      __stcs(reinterpret_cast<float4*>(g + off + toff(t, tj<L>(r, 0))), make_float4(a.x, a.y, b.x, b.y));
+      __stcs(reinterpret_cast<float4*>(g + off + reg_off(o, r)), make_float4(a.x, a.y, b.x, b.y));
     }
   } else {
 #pragma unroll
-    for (int r = 0; r < R; ++r) __stcs(g + off + toff(t, tj<L>(r, 0)), v[r]);
+    for (int r = 0; r < R; ++r) __stcs(g + off + reg_off(o, r), v[r]);
   }
 }
 
@@ -343,8 +371,10 @@ __device__ __forceinline__ void gstore_normal(C (&v)[R], C* __restrict__ g, uint
 
 template <int L, class T>
 __device__ __forceinline__ void qload(T (&qv)[R], const T* __restrict__ q, uint32_t off, const Tile& t) {
+  uint32_t o[RB];
+  reg_bit_offsets<L>(t, o);
 #pragma unroll
-  for (int r = 0; r < R; ++r) qv[r] = __ldcs(q + off + toff(t, tj<L>(r, 0)));
+  for (int r = 0; r < R; ++r) qv[r] = __ldcs(q + off + reg_off(o, r));
 }
 
 }  // namespace hc

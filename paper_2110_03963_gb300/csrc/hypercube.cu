@@ -21,6 +21,7 @@
 
 #include <algorithm>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "hc_kernels.cuh"
@@ -87,11 +88,42 @@ __device__ __forceinline__ void block_store3(T a, T b, T c, double* part, int ra
 
 // One tile (index bid of nblk) of one pass; the CTA's shared memory is smem_raw. Used by the
 // per-pass kernels (one CTA per tile) and by the batched persistent kernel (a CTA walks the tiles).
-template <class T, int SHAPE>
+// stp / stl: the tile's psi / lambda already staged in shared memory in tile-index order (NULL:
+// load from global memory). ONEBUF: exchange two vectors one after the other through a single
+// shared buffer (leaves room for the staging area).
+struct NoHook {
+  __device__ void operator()() const {}
+};
+
+// hook() runs once, right after the pass's first shared-memory exchange: by then every thread has
+// finished reading the staged tile, so a pipelined caller can start refilling the stage.
+template <class T, int SHAPE, bool ONEBUF = false, class Hook = NoHook>
 __device__ __forceinline__ void run_pass(const PassArgs<T>& a, uint32_t bid, uint32_t nblk,
-                                         unsigned char* smem_raw) {
+                                         unsigned char* smem_raw,
+                                         const typename Cx<T>::t* stp = nullptr,
+                                         const typename Cx<T>::t* stl = nullptr,
+                                         const Hook& hook = Hook{}) {
   using C = typename Cx<T>::t;
   C* sm = reinterpret_cast<C*>(smem_raw);
+  // two-vector transpose through one or two shared buffers
+  auto x2 = [&](auto lf, auto lt, C(&p)[R], C(&l)[R]) {
+    constexpr int LF = decltype(lf)::value, LT = decltype(lt)::value;
+    if constexpr (ONEBUF) {
+      xchg<LF, LT>(p, sm, threadIdx.x);
+      xchg<LF, LT>(l, sm, threadIdx.x);
+    } else {
+      xchg2<LF, LT>(p, l, sm, threadIdx.x);
+    }
+  };
+  using I0 = std::integral_constant<int, 0>;
+  using I1 = std::integral_constant<int, 1>;
+  using I2 = std::integral_constant<int, 2>;
+  // load psi (or lambda) of this tile in layout L, from the stage when there is one
+  auto ld = [&](auto li, C(&v)[R], const C* g, const C* st, uint32_t off) {
+    constexpr int L = decltype(li)::value;
+    if (st) sget_lin<L>(v, st, threadIdx.x);
+    else gload<L>(v, g, off, a.tile);
+  };
   const int tid = threadIdx.x;
   const uint32_t base = tile_base(a.tile, bid);
   const uint32_t off0 = base + toff(a.tile, tj<0>(0, tid));
@@ -124,20 +156,26 @@ __device__ __forceinline__ void run_pass(const PassArgs<T>& a, uint32_t bid, uin
         v[r].y = sw ? a.init_amp : T(0);
       }
     } else {
-      gload_normal<2>(v, a.psi_in, off2, a.tile, tp2);
+      if (stp) sget_lin<2>(v, stp, tid);
+      else gload<2>(v, a.psi_in, off2, a.tile);
+#pragma unroll
+      for (int r = 0; r < R; ++r)   // caller-visible psi0 is in normal form
+        if (tp2 ^ (uint32_t)cpar(tj<2>(r, 0))) v[r] = swp(v[r]);
     }
     qload<2>(qv, a.q, off2, a.tile);
     phase2(v, T(1));
     rot_layout<2>(v, a.mask_aft, a.ca, a.sa, tp2);
     xchg<2, 1>(v, sm, tid);
+    hook();
     rot_layout<1>(v, a.mask_aft, a.ca, a.sa, tp1);
     xchg<1, 0>(v, sm, tid);
     rot_layout<0>(v, a.mask_aft, a.ca, a.sa, tp0);
     gstore<0>(v, a.psi_out, off0, a.tile);
   } else if constexpr (SHAPE == F1) {
-    gload<0>(v, a.psi_in, off0, a.tile);
+    ld(I0{}, v, a.psi_in, stp, off0);
     rot_layout<0>(v, a.mask_bef, a.cb, a.sb, tp0);
     xchg<0, 1>(v, sm, tid);
+    hook();
     rot_layout<1>(v, a.mask_bef, a.cb, a.sb, tp1);
     qload<2>(qv, a.q, off2, a.tile);
     xchg<1, 2>(v, sm, tid);
@@ -150,17 +188,19 @@ __device__ __forceinline__ void run_pass(const PassArgs<T>& a, uint32_t bid, uin
     rot_layout<0>(v, a.mask_aft, a.ca, a.sa, tp0);
     gstore<0>(v, a.psi_out, off0, a.tile);
   } else if constexpr (SHAPE == F2) {
-    gload<0>(v, a.psi_in, off0, a.tile);
+    ld(I0{}, v, a.psi_in, stp, off0);
     rot_layout<0>(v, a.mask_bef, a.cb, a.sb, tp0);
     xchg<0, 1>(v, sm, tid);
+    hook();
     rot_layout<1>(v, a.mask_bef, a.cb, a.sb, tp1);
     xchg<1, 2>(v, sm, tid);
     rot_layout<2>(v, a.mask_bef, a.cb, a.sb, tp2);
     gstore<2>(v, a.psi_out, off2, a.tile);
   } else if constexpr (SHAPE == FE || SHAPE == FV) {
-    gload<0>(v, a.psi_in, off0, a.tile);
+    ld(I0{}, v, a.psi_in, stp, off0);
     rot_layout<0>(v, a.mask_bef, a.cb, a.sb, tp0);
     xchg<0, 1>(v, sm, tid);
+    hook();
     rot_layout<1>(v, a.mask_bef, a.cb, a.sb, tp1);
     qload<2>(qv, a.q, off2, a.tile);
     xchg<1, 2>(v, sm, tid);
@@ -177,23 +217,24 @@ __device__ __forceinline__ void run_pass(const PassArgs<T>& a, uint32_t bid, uin
       for (int r = 0; r < R; ++r) { l[r].x = qv[r] * v[r].x; l[r].y = qv[r] * v[r].y; }
       T acc = T(0);
       unrot_layout_acc<2>(v, l, a.mask_bef, a.cb, a.sb, tp2, acc);
-      xchg2<2, 1>(v, l, sm, tid);
+      x2(I2{}, I1{}, v, l);
       unrot_layout_acc<1>(v, l, a.mask_bef, a.cb, a.sb, tp1, acc);
-      xchg2<1, 0>(v, l, sm, tid);
+      x2(I1{}, I0{}, v, l);
       unrot_layout_acc<0>(v, l, a.mask_bef, a.cb, a.sb, tp0, acc);
       gstore<0>(l, a.lam_out, off0, a.tile);
       block_store3(e, T(2) * acc, T(0), a.part, a.row_E, a.row_bef, -1, tid, bid, nblk);
     }
   } else if constexpr (SHAPE == R1 || SHAPE == R0) {
     C l[R];
-    gload<0>(v, a.psi_in, off0, a.tile);
-    gload<0>(l, a.lam_in, off0, a.tile);
+    ld(I0{}, v, a.psi_in, stp, off0);
+    ld(I0{}, l, a.lam_in, stl, off0);
     T acc_a = T(0), acc_b = T(0), acc_g = T(0);
     unrot_layout_acc<0>(v, l, a.mask_aft, a.ca, a.sa, tp0, acc_a);
-    xchg2<0, 1>(v, l, sm, tid);
+    x2(I0{}, I1{}, v, l);
+    hook();
     unrot_layout_acc<1>(v, l, a.mask_aft, a.ca, a.sa, tp1, acc_a);
     qload<2>(qv, a.q, off2, a.tile);
-    xchg2<1, 2>(v, l, sm, tid);
+    x2(I1{}, I2{}, v, l);
     unrot_layout_acc<2>(v, l, a.mask_aft, a.ca, a.sa, tp2, acc_a);
     {
       T ge = T(0), go = T(0);
@@ -208,9 +249,9 @@ __device__ __forceinline__ void run_pass(const PassArgs<T>& a, uint32_t bid, uin
       phase2(v, T(-1));
       phase2(l, T(-1));
       unrot_layout_acc<2>(v, l, a.mask_bef, a.cb, a.sb, tp2, acc_b);
-      xchg2<2, 1>(v, l, sm, tid);
+      x2(I2{}, I1{}, v, l);
       unrot_layout_acc<1>(v, l, a.mask_bef, a.cb, a.sb, tp1, acc_b);
-      xchg2<1, 0>(v, l, sm, tid);
+      x2(I1{}, I0{}, v, l);
       unrot_layout_acc<0>(v, l, a.mask_bef, a.cb, a.sb, tp0, acc_b);
       gstore<0>(l, a.lam_out, off0, a.tile);
       if (a.psi_out) gstore<0>(v, a.psi_out, off0, a.tile);
@@ -218,13 +259,14 @@ __device__ __forceinline__ void run_pass(const PassArgs<T>& a, uint32_t bid, uin
     block_store3(T(2) * acc_b, T(2) * acc_a, T(2) * acc_g, a.part, a.row_bef, a.row_aft, a.row_gam, tid, bid, nblk);
   } else if constexpr (SHAPE == R2) {
     C l[R];
-    gload<2>(v, a.psi_in, off2, a.tile);
-    gload<2>(l, a.lam_in, off2, a.tile);
+    ld(I2{}, v, a.psi_in, stp, off2);
+    ld(I2{}, l, a.lam_in, stl, off2);
     T acc_b = T(0);
     unrot_layout_acc<2>(v, l, a.mask_bef, a.cb, a.sb, tp2, acc_b);
-    xchg2<2, 1>(v, l, sm, tid);
+    x2(I2{}, I1{}, v, l);
+    hook();
     unrot_layout_acc<1>(v, l, a.mask_bef, a.cb, a.sb, tp1, acc_b);
-    xchg2<1, 0>(v, l, sm, tid);
+    x2(I1{}, I0{}, v, l);
     unrot_layout_acc<0>(v, l, a.mask_bef, a.cb, a.sb, tp0, acc_b);
     gstore<0>(l, a.lam_out, off0, a.tile);
     if (a.psi_out) gstore<0>(v, a.psi_out, off0, a.tile);
@@ -237,6 +279,62 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 1 : ((SHAPE == FE || SHAP
 pass_kernel(const __grid_constant__ PassArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   run_pass<T, SHAPE>(a, blockIdx.x, gridDim.x, smem_raw);
+}
+
+// Persistent, software-pipelined form of the complex64 passes: each CTA walks tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ...; the next tile's psi (and lambda) are fetched into a
+// shared-memory stage by asynchronous 16-byte copies (cp.async, no registers held) while the current
+// tile is computed, so HBM reads overlap the rotations and exchanges.
+template <int SHAPE>
+struct PipeTraits {
+  static constexpr int NV = (SHAPE == R1 || SHAPE == R2 || SHAPE == R0) ? 2 : 1;   // staged vectors
+  // CTAs per SM: FE stages one vector but holds two in registers in its second half
+  static constexpr int MINB = (NV == 2 || SHAPE == FE) ? 2 : 3;
+  static constexpr size_t smem_bytes() {
+    return (size_t)SM_SLOTS * sizeof(float2) + (size_t)NV * TILE * sizeof(float2);
+  }
+};
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+template <int SHAPE>
+__global__ void __launch_bounds__(NT, PipeTraits<SHAPE>::MINB)
+pipe_kernel(const __grid_constant__ PassArgs<float> a, uint32_t ntiles) {
+  constexpr int NV = PipeTraits<SHAPE>::NV;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float2* stage = reinterpret_cast<float2*>(smem_raw + (size_t)SM_SLOTS * sizeof(float2));
+  const int tid = threadIdx.x;
+  const bool staged = !(SHAPE == F0 && a.gen_init);
+  // thread tid copies the amplitude pairs (2c, 2c + 1), c = tid + k * NT, of tile t
+  auto issue = [&](uint32_t t) {
+    const uint32_t base = tile_base(a.tile, t);
+#pragma unroll
+    for (int k = 0; k < TILE / 2 / NT; ++k) {
+      const uint32_t j = 2u * (uint32_t)(tid + k * NT);
+      const uint32_t g = base + toff(a.tile, j);
+      cp_async16(stage + j, a.psi_in + g);
+      if constexpr (NV == 2) cp_async16(stage + TILE + j, a.lam_in + g);
+    }
+    cp_async_commit();
+  };
+  uint32_t t = blockIdx.x;
+  if (staged && t < ntiles) issue(t);
+  for (; t < ntiles; t += gridDim.x) {
+    if (staged) {
+      cp_async_wait_all();
+      __syncthreads();
+    }
+    const uint32_t next = t + gridDim.x;
+    auto refill = [&]() {
+      if (staged && next < ntiles) issue(next);
+    };
+    run_pass<float, SHAPE, true>(a, t, ntiles, smem_raw, staged ? stage : nullptr,
+                                 (staged && NV == 2) ? stage + TILE : nullptr, refill);
+  }
 }
 
 // ---------------------------------------------------------------- small states (n <= TB)
@@ -464,7 +562,7 @@ static void fill_angles(PassArgs<T>& a, const PassInfo& pi, const double* gammas
 template <class T, int S>
 static int launch_one(const PassArgs<T>& a, uint32_t grid, cudaStream_t st) {
   constexpr bool two = S == FE || S == R1 || S == R2 || S == R0;
-  const size_t sm = (two ? 2 : 1) * (size_t)TILE * sizeof(typename Cx<T>::t);
+  const size_t sm = (two ? 2 : 1) * (size_t)SM_SLOTS * sizeof(typename Cx<T>::t);
   static bool configured = false;   // per instantiation
   if (!configured) {
     QVS_CUDA_TRY(cudaFuncSetAttribute(pass_kernel<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -502,11 +600,44 @@ static double shape_bytes(int shape, const void* psi_in, const void* psi_out, do
 template <class T>
 static int launch_shape_raw(int shape, const PassArgs<T>& a, uint32_t grid, cudaStream_t st);
 
+template <int S>
+static int launch_pipe(const PassArgs<float>& a, uint32_t ntiles, int sms, cudaStream_t st) {
+  const size_t sm = PipeTraits<S>::smem_bytes();
+  static bool configured = false;
+  if (!configured) {
+    QVS_CUDA_TRY(cudaFuncSetAttribute(pipe_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    configured = true;
+  }
+  const uint32_t grid = std::min<uint32_t>(ntiles, (uint32_t)(sms * PipeTraits<S>::MINB));
+  pipe_kernel<S><<<grid, NT, sm, st>>>(a, ntiles);
+  QVS_CUDA_TRY(cudaGetLastError());
+  return QVS_OK;
+}
+
+static int launch_pipe_shape(int shape, const PassArgs<float>& a, uint32_t ntiles, int sms, cudaStream_t st) {
+  switch (shape) {
+    case F0: return launch_pipe<F0>(a, ntiles, sms, st);
+    case F1: return launch_pipe<F1>(a, ntiles, sms, st);
+    case F2: return launch_pipe<F2>(a, ntiles, sms, st);
+    case FE: return launch_pipe<FE>(a, ntiles, sms, st);
+    case FV: return launch_pipe<FV>(a, ntiles, sms, st);
+    case R1: return launch_pipe<R1>(a, ntiles, sms, st);
+    case R2: return launch_pipe<R2>(a, ntiles, sms, st);
+    case R0: return launch_pipe<R0>(a, ntiles, sms, st);
+  }
+  return QVS_EINVAL;
+}
+
 template <class T>
 static int launch_shape(qvs_ctx* h, int shape, const PassArgs<T>& a, uint32_t grid) {
   cudaEvent_t ev;
   QVS_TRY(prof_begin(h, &ev));
-  QVS_TRY(launch_shape_raw<T>(shape, a, grid, h->stream));
+  if constexpr (sizeof(T) == 4) {
+    if (h->pipeline) QVS_TRY(launch_pipe_shape(shape, a, grid, h->sms, h->stream));
+    else QVS_TRY(launch_shape_raw<T>(shape, a, grid, h->stream));
+  } else {
+    QVS_TRY(launch_shape_raw<T>(shape, a, grid, h->stream));
+  }
   const double c = sizeof(typename Cx<T>::t), qb = sizeof(T);
   return prof_end(h, shape_name(shape, sizeof(T) == 8),
                   shape_bytes(shape, a.psi_in, a.psi_out, c, qb) * (double)grid * TILE, ev);
@@ -968,7 +1099,7 @@ static int batch_launch(qvs_batch_t b, int ctas_per_sm) {
   a.nck_max = b->nck_max;
   const int grid = std::min(b->nslots, b->sms * ctas_per_sm);
   QVS_CUDA_TRY(cudaMemsetAsync(b->counter.ptr, 0, sizeof(int), b->stream));
-  batch_kernel<<<grid, NT, 2 * TILE * sizeof(float2), b->stream>>>(a);
+  batch_kernel<<<grid, NT, 2 * SM_SLOTS * sizeof(float2), b->stream>>>(a);
   QVS_CUDA_TRY(cudaGetLastError());
   return QVS_OK;
 }
@@ -1064,7 +1195,7 @@ extern "C" int qvs_batch_create(qvs_batch_t* out, int count, const int32_t* n_qu
   if (cudaMemcpyAsync(b->inst.ptr, inst.data(), sizeof(BInst) * count, cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
       cudaMemcpyAsync(b->order.ptr, order.data(), sizeof(int) * count, cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
       cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(2 * TILE * sizeof(float2))) != cudaSuccess ||
+                           (int)(2 * SM_SLOTS * sizeof(float2))) != cudaSuccess ||
       cudaStreamSynchronize(b->stream) != cudaSuccess) {
     (void)cudaGetLastError();
     qvs_batch_destroy(b);

@@ -93,7 +93,9 @@ struct qvs_ctx {
   double* host_res = nullptr;   // pinned, 1 + 2 * host_res_cap doubles
   int host_res_cap = 0;
 
+  int sms = 0;               // multiprocessors of the device (grid sizing of persistent kernels)
   int ckpt_layers = 0;
+  int pipeline = 0;          // QVS_OPT_PIPELINE
   bool have_E = false;
   double E = 0.0;
   int64_t launches = 0;

@@ -320,8 +320,6 @@ def run_ours(args):
     sim.set_mixer(qvs.QVS_MIX_HYPERCUBE, qvs.hypercube_desc(n))
     if args.ckpt is not None:
         sim.set_option(qvs.QVS_OPT_CKPT_LAYERS, args.ckpt)
-    if args.pipeline is not None:
-        sim.set_option(qvs.QVS_OPT_PIPELINE, args.pipeline)
     gs, ts = np.asarray(inst.gammas), np.asarray(inst.ts)
 
     def barrier():
@@ -471,8 +469,6 @@ def main():
                     help="qaoa = the benchmark line; the others print one diagnostic line for that workload "
                          "(sizes from --qubits/--layers/--count)")
     ap.add_argument("--count", type=int, default=4096, help="instances for --workload batch")
-    ap.add_argument("--pipeline", type=int, default=None, choices=[0, 1],
-                    help="hypercube passes: 1 persistent prefetching CTAs, 0 one CTA per tile")
     ap.add_argument("--qubits", type=int, default=N_QUBITS, help="state size 2^qubits (28 is the benchmark)")
     ap.add_argument("--layers", type=int, default=P_LAYERS, help="depth p (8 is the benchmark)")
     args = ap.parse_args()

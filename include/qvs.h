@@ -60,12 +60,9 @@ enum {
   QVS_OPT_CKPT_LAYERS = 1,  /* adjoint: store the forward state every this many layers and
                                uncompute in between; 0 = ceil(sqrt(p)) (default); 1 = store
                                every pass boundary (no uncompute)                             */
-  QVS_OPT_PROFILE = 2,      /* 1: bracket every kernel launch with CUDA events on the handle's
+  QVS_OPT_PROFILE = 2       /* 1: bracket every kernel launch with CUDA events on the handle's
                                stream and accumulate per-kernel statistics (qvs_kernel_stats);
                                0: off (default). Setting it resets the statistics.           */
-  QVS_OPT_PIPELINE = 3      /* complex64 hypercube passes: 1 = persistent CTAs that prefetch the
-                               next tile with asynchronous copies while computing the current
-                               one (default); 0 = one CTA per tile                           */
 };
 
 /*

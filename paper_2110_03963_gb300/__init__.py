@@ -27,7 +27,6 @@ QVS_I32, QVS_F32, QVS_F64 = 1, 2, 3
 QVS_MIX_HYPERCUBE, QVS_MIX_CIRCULANT, QVS_MIX_CSR = 1, 2, 3
 QVS_OPT_CKPT_LAYERS = 1
 QVS_OPT_PROFILE = 2
-QVS_OPT_PIPELINE = 3
 
 EXPORTED = [
     "qvs_create", "qvs_destroy", "qvs_set_quality", "qvs_set_mixer", "qvs_set_initial_state",

@@ -249,11 +249,6 @@ extern "C" int qvs_set_option(qvs_t h, int option, int64_t value) {
     h->ckpt_layers = (int)value;
     return QVS_OK;
   }
-  if (option == QVS_OPT_PIPELINE) {
-    if (value != 0 && value != 1) return QVS_EINVAL;
-    h->pipeline = (int)value;
-    return QVS_OK;
-  }
   if (option == QVS_OPT_PROFILE) {
     if (value != 0 && value != 1) return QVS_EINVAL;
     h->profile = value == 1;

@@ -71,21 +71,28 @@ template <> struct Cx<double> { using t = double2; };
 
 // ---------------------------------------------------------------- storage form
 //
-// Amplitudes in the tiled path are kept in a "parity form": amplitude g is stored as (re, im)
-// when popcount(g) is even and as (im, re) when it is odd. Every rotation pairs two indices that
-// differ in one bit, so one partner of each pair is always in each form, and
-//     a' = c a - i s b   becomes   A' = c A + (s, -s) * B   (A normal, B swapped)
-//                                  B' = c B + (-s, s) * A
-// (componentwise products): two paired-float operations per amplitude and bit, with no operand
-// shuffles. The private buffers of the tiled path (working state, adjoint vector, checkpoints)
-// hold this form; inputs and outputs visible to callers are converted at the edge.
+// The private buffers of the tiled path (working state, adjoint vector, checkpoints) hold
+// W_j = (-i)^popcount(j) psi_j (up to the frame below). In this gauge the single-qubit term -i X_b
+// is the real map (W_a, W_b) -> (W_b, -W_a) on every pair a, b = a | 2^b, so
+//     exp(-i t X_b) = cos t (I - i tan t X_b)   acts as   W_a += T W_b,  W_b -= T W_a   (T = tan t)
+// up to the common real factor cos t: one paired-float FMA per amplitude and bit, with the same
+// two constants (T, T) and (-T, -T) for every pair. Diagonal operators (phase, Q) are unchanged.
+//
+// |T| <= 1 is kept by a per-layer angle shift t = t' + pi/2 where |tan t| > 1:
+// exp(-i t X)^{(x)n} = exp(-i t' X)^{(x)n} (-i)^n X_all, and (-i)^n X_all (X_all = all bits
+// flipped) commutes with every mixer rotation, so the schedule carries it as a frame: the buffer
+// holds W with state = k P^F W, P the gauge image of (-i)^n X_all, F in {0, 1} and k real. Under
+// F = 1 the diagonal operators read q at the complemented index (q index XOR qx, qx = 2^n - 1).
+// The host tracks k and F pass by pass (the cos t' factors, the frame toggles and the
+// renormalisation folded into each phase) and hands every kernel its real scale factors.
 
-__host__ __device__ __forceinline__ constexpr int cpar(int x) {
-  x ^= x >> 8;
-  x ^= x >> 4;
-  x ^= x >> 2;
-  x ^= x >> 1;
-  return x & 1;
+__host__ __device__ __forceinline__ constexpr int cpop(int x) {
+  int c = 0;
+  while (x) {
+    c += x & 1;
+    x >>= 1;
+  }
+  return c;
 }
 
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
@@ -98,8 +105,20 @@ template <class C, class T> __device__ __forceinline__ C mk2(T x, T y);
 template <> __device__ __forceinline__ float2 mk2<float2, float>(float x, float y) { return make_float2(x, y); }
 template <> __device__ __forceinline__ double2 mk2<double2, double>(double x, double y) { return make_double2(x, y); }
 
-// swap re/im: converts between the two storage forms
-template <class C> __device__ __forceinline__ C swp(C v) { C w; w.x = v.y; w.y = v.x; return w; }
+// multiply by i^m (m mod 4): edge conversions between the gauge and the plain amplitudes
+template <class C>
+__device__ __forceinline__ C mul_ipow(C v, uint32_t m) {
+  C w = v;
+  if (m & 1u) {
+    w.x = -v.y;
+    w.y = v.x;
+  }
+  if (m & 2u) {
+    w.x = -w.x;
+    w.y = -w.y;
+  }
+  return w;
+}
 
 // Phase angle of exp(-i gamma q): the complex64 path carries gamma / 2pi as a float-float pair
 // (hi, lo). The exact product error of hi*q (FMA two-product, Ogita-Rump-Oishi 2005) and the lo
@@ -116,7 +135,8 @@ __device__ __forceinline__ void phase_cs(double q, double gamma, double, double&
   sincos(gamma * q, &s, &c);
 }
 
-// multiply a stored amplitude by exp(-i theta) (c = cos, s = sin); a swapped amplitude uses -s
+// multiply an amplitude by (c - i s) (c = rho cos theta, s = rho sin theta: exp(-i theta) and a real
+// scale rho)
 template <class C, class T>
 __device__ __forceinline__ C phase_mul(C v, T c, T s) {
   C w;
@@ -125,9 +145,9 @@ __device__ __forceinline__ C phase_mul(C v, T c, T s) {
   return w;
 }
 
-// Im(conj(lam) * psi) for two amplitudes stored in the same form (negate for the swapped form)
+// Im(conj(l) * p)
 template <class C> __device__ __forceinline__ auto imdot_st(C l, C p) { return l.x * p.y - l.y * p.x; }
-template <class C> __device__ __forceinline__ auto dif(C z) { return z.x - z.y; }
+template <class C> __device__ __forceinline__ auto hsum(C z) { return z.x + z.y; }
 
 // normal-form helpers (the single-CTA small-state kernel keeps amplitudes as (re, im))
 __device__ __forceinline__ void rot_normal(float2& a, float2& b, float c, float s) {
@@ -154,68 +174,66 @@ __device__ __forceinline__ double2 cmul_conj(double2 v, double c, double s) {
 }
 
 // ---------------------------------------------------------------- register-layout operations
-// tpar = parity of the thread's own index bits (plus the tile base) in layout L; the parity of
-// register r adds cpar(tj<L>(r, 0)), known at compile time.
+//
+// The tile bits a pass rotates are "every tile bit >= TH" for a threshold TH fixed by the tile type
+// (TH = 0: all twelve; TH = s: the group above the s low chunk bits). With TH a template argument
+// the per-bit choice folds away after unrolling and each layout step is straight-line code.
+// TH < 0 reads the bits from the runtime mask instead (batched kernel).
+template <int L, int TH>
+__device__ __forceinline__ bool bit_on(int i, uint32_t mask) {
+  if constexpr (TH >= 0) return regbit(L, i) >= TH;
+  else return (mask >> regbit(L, i)) & 1u;
+}
 
-template <int L, class C, class T>
-__device__ __forceinline__ void rot_layout(C (&v)[R], uint32_t mask, T c, T s, uint32_t tpar) {
-  const C cc = mk2<C, T>(c, c);
-  const T sp = tpar ? -s : s;
-  const C svp = mk2<C, T>(sp, -sp), svn = mk2<C, T>(-sp, sp);
+// W_a += T W_b, W_b -= T W_a on the register pairs of the rotated bits (T < 0: the inverse map up
+// to the real factor 1 + T^2)
+template <int L, int TH, class C, class T>
+__device__ __forceinline__ void rot_layout(C (&v)[R], uint32_t mask, T tn) {
+  const C tp = mk2<C, T>(tn, tn), tm = mk2<C, T>(-tn, -tn);
 #pragma unroll
   for (int i = 0; i < RB; ++i) {
-    if (mask & (1u << regbit(L, i))) {
+    if (bit_on<L, TH>(i, mask)) {
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         if (!(r & (1 << i))) {
           const int r1 = r | (1 << i);
-          const bool pr = cpar(tj<L>(r, 0));
           const C a = v[r], b = v[r1];
-          v[r] = fma2(cc, a, mul2(pr ? svn : svp, b));
-          v[r1] = fma2(cc, b, mul2(pr ? svp : svn, a));
+          v[r] = fma2(tp, b, a);
+          v[r1] = fma2(tm, a, b);
         }
       }
     }
   }
 }
 
-// Adjoint rotations exp(+i t X_b) on psi and lam, accumulating Im<lam|X_b psi> for every bit b
-// undone (X_b commutes with all rotations of the same layer, so the value is the one at the
-// layer's output). For a pair (r, r1) whose first member is in normal form the term is
-// dif(l_r * p_r1) - dif(l_r1 * p_r) (componentwise products), and its negative otherwise.
-template <int L, class C, class T, class A>
-__device__ __forceinline__ void unrot_layout_acc(C (&p)[R], C (&l)[R], uint32_t mask, T c, T s,
-                                                 uint32_t tpar, A& acc) {
-  const C cc = mk2<C, T>(c, c);
-  const T sp = tpar ? s : -s;   // adjoint: angle -t
-  const C svp = mk2<C, T>(sp, -sp), svn = mk2<C, T>(-sp, sp);
-  C e1 = mk2<C, T>(0, 0), e2 = e1, o1 = e1, o2 = e1;
+// Adjoint step on psi (p) and lambda (l): accumulate Re<l|Y_b|p> = Im<lam|X_b psi> for every
+// rotated bit b of the layout at the step's entry point (X_b commutes with all rotations of the
+// same layer, so any common point of the two vectors gives the layer's value), then undo the
+// rotations (tangent -tn). acc += sc * sum; the step moves both vectors by the real factor
+// cos t' per bit, so sc advances by c2 = cos^2 t' per rotated bit.
+template <int L, int TH, class C, class T, class A>
+__device__ __forceinline__ void unrot_layout_acc(C (&p)[R], C (&l)[R], uint32_t mask, T tn, T c2, T& sc,
+                                                 A& acc) {
+  C e1 = mk2<C, T>(0, 0), e2 = e1;
+  T step = T(1);
 #pragma unroll
   for (int i = 0; i < RB; ++i) {
-    if (mask & (1u << regbit(L, i))) {
+    if (bit_on<L, TH>(i, mask)) {
+      step *= c2;
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         if (!(r & (1 << i))) {
           const int r1 = r | (1 << i);
-          const bool pr = cpar(tj<L>(r, 0));
-          const C pa = p[r], pb = p[r1], la = l[r], lb = l[r1];
-          if (pr) {
-            o1 = fma2(la, pb, o1);
-            o2 = fma2(lb, pa, o2);
-          } else {
-            e1 = fma2(la, pb, e1);
-            e2 = fma2(lb, pa, e2);
-          }
-          p[r] = fma2(cc, pa, mul2(pr ? svn : svp, pb));
-          p[r1] = fma2(cc, pb, mul2(pr ? svp : svn, pa));
-          l[r] = fma2(cc, la, mul2(pr ? svn : svp, lb));
-          l[r1] = fma2(cc, lb, mul2(pr ? svp : svn, la));
+          e1 = fma2(l[r], p[r1], e1);
+          e2 = fma2(l[r1], p[r], e2);
         }
       }
     }
   }
-  const A t = (A)((dif(e1) - dif(e2)) - (dif(o1) - dif(o2)));
-  acc += tpar ? -t : t;
+  rot_layout<L, TH>(p, mask, -tn);
+  rot_layout<L, TH>(l, mask, -tn);
+  acc += (A)(sc * (hsum(e1) - hsum(e2)));
+  sc *= step;
 }
 
 // shared-memory transpose from layout LF to layout LT
@@ -261,24 +279,6 @@ __device__ __forceinline__ void sget(C (&v)[R], const C* sm, int tid) {
   } else {
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = b[spos(tj<L>(r, 0))];
-  }
-}
-
-// read layout L from a tile staged in shared memory in plain tile-index order (as the bulk copies
-// leave it); conflict-free for L0 (16-byte, consecutive pairs) and L2 (8-byte, consecutive lanes)
-template <int L, class C>
-__device__ __forceinline__ void sget_lin(C (&v)[R], const C* st, int tid) {
-  const C* b = st + tj<L>(0, tid);
-  if constexpr (L == 0 && sizeof(C) == 8) {
-#pragma unroll
-    for (int r = 0; r < R; r += 2) {
-      const float4 w = *reinterpret_cast<const float4*>(b + tj<0>(r, 0));
-      *reinterpret_cast<float2*>(&v[r]) = make_float2(w.x, w.y);
-      *reinterpret_cast<float2*>(&v[r + 1]) = make_float2(w.z, w.w);
-    }
-  } else {
-#pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = b[tj<L>(r, 0)];
   }
 }
 
@@ -350,31 +350,41 @@ __device__ __forceinline__ void gstore(const C (&v)[R], C* __restrict__ g, uint3
   }
 }
 
-// normal-form loads/stores: convert to/from the parity form (caller-visible buffers)
+// Caller-visible (plain) amplitudes to the gauge on load: W_j = (-i)^|j| psi_j. tpop = popcount
+// of the tile base and the thread's own index bits in layout L.
 template <int L, class C>
-__device__ __forceinline__ void gload_normal(C (&v)[R], const C* __restrict__ g, uint32_t off,
-                                             const Tile& t, uint32_t tpar) {
+__device__ __forceinline__ void gload_plain(C (&v)[R], const C* __restrict__ g, uint32_t off,
+                                            const Tile& t, uint32_t tpop) {
   gload<L>(v, g, off, t);
 #pragma unroll
-  for (int r = 0; r < R; ++r)
-    if (tpar ^ (uint32_t)cpar(tj<L>(r, 0))) v[r] = swp(v[r]);
+  for (int r = 0; r < R; ++r) v[r] = mul_ipow(v[r], (0u - (tpop + (uint32_t)cpop(tj<L>(r, 0)))) & 3u);
 }
 
-template <int L, class C>
-__device__ __forceinline__ void gstore_normal(C (&v)[R], C* __restrict__ g, uint32_t off,
-                                              const Tile& t, uint32_t tpar) {
-#pragma unroll
-  for (int r = 0; r < R; ++r)
-    if (tpar ^ (uint32_t)cpar(tj<L>(r, 0))) v[r] = swp(v[r]);
-  gstore<L>(v, g, off, t);
-}
-
-template <int L, class T>
-__device__ __forceinline__ void qload(T (&qv)[R], const T* __restrict__ q, uint32_t off, const Tile& t) {
+// Gauge to plain amplitudes on store, with the frame: slot j holds the amplitude of index j ^ ox,
+// psi_{j ^ ox} = k i^(|j| - F n) W_j (fm = F n mod 4); scalar stores at the XORed index.
+template <int L, class C, class T>
+__device__ __forceinline__ void gstore_plain(const C (&v)[R], C* __restrict__ g, uint32_t off,
+                                             const Tile& t, uint32_t tpop, uint32_t ox, uint32_t fm, T k) {
   uint32_t o[RB];
   reg_bit_offsets<L>(t, o);
 #pragma unroll
-  for (int r = 0; r < R; ++r) qv[r] = __ldcs(q + off + reg_off(o, r));
+  for (int r = 0; r < R; ++r) {
+    C w = mul_ipow(v[r], (tpop + (uint32_t)cpop(tj<L>(r, 0)) - fm) & 3u);
+    w.x *= k;
+    w.y *= k;
+    __stcs(g + ((off + reg_off(o, r)) ^ ox), w);
+  }
+}
+
+// q at the element indices XOR qx (qx = 0, or 2^n - 1 under the flipped frame: the warp then reads
+// the same segments in reverse lane order)
+template <int L, class T>
+__device__ __forceinline__ void qload(T (&qv)[R], const T* __restrict__ q, uint32_t off, const Tile& t,
+                                      uint32_t qx) {
+  uint32_t o[RB];
+  reg_bit_offsets<L>(t, o);
+#pragma unroll
+  for (int r = 0; r < R; ++r) qv[r] = __ldcs(q + ((off + reg_off(o, r)) ^ qx));
 }
 
 }  // namespace hc

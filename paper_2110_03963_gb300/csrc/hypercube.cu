@@ -24,318 +24,10 @@
 #include <type_traits>
 #include <vector>
 
-#include "hc_kernels.cuh"
-#include "qvs_internal.h"
+#include "hc_pass.cuh"
 
 namespace qvs {
 namespace hc {
-
-enum Shape : int {
-  F0 = 0,   // first pass: psi0 (generated or loaded), phase, rotations ("after")
-  F1 = 1,   // rotations (before), phase, rotations (after)
-  F2 = 2,   // rotations only
-  FE = 3,   // last forward pass fused with its adjoint: rotations, E and lambda = Q psi, undo
-  FV = 4,   // last forward pass for qvs_evolve: rotations, E, store psi
-  R1 = 5,   // adjoint of F1
-  R2 = 6,   // adjoint of F2
-  R0 = 7    // adjoint of F0 (gradient contributions only)
-};
-
-template <class T>
-struct PassArgs {
-  Tile tile;
-  const typename Cx<T>::t* psi_in;
-  typename Cx<T>::t* psi_out;
-  const typename Cx<T>::t* lam_in;
-  typename Cx<T>::t* lam_out;
-  const T* q;
-  uint32_t mask_bef, mask_aft;
-  T cb, sb, ca, sa;     // cos / sin of the "before" and "after" mixer angles
-  T ph0, ph1;           // phase: complex64: gamma/2pi as hi, lo; complex128: gamma, 0
-  double* part;         // partial-sum rows: part[row * gridDim.x + blockIdx.x]
-  int row_bef, row_aft, row_gam, row_E;
-  T init_amp;           // amplitude of the uniform initial state
-  int gen_init;         // F0: 1 = generate psi0 = init_amp, 0 = load psi_in
-};
-
-// Block sum of up to three values, written to their partial rows (rows < 0 skipped). Lanes are
-// summed in the thread's precision (a warp holds 512 amplitude contributions), warps and CTAs in
-// fp64; the order is fixed, so results are reproducible run to run.
-template <class T>
-__device__ __forceinline__ void block_store3(T a, T b, T c, double* part, int ra, int rb, int rc,
-                                             int tid, uint32_t bid, uint32_t nblk) {
-  __shared__ double red[3][NT / 32];
-#pragma unroll
-  for (int o = 16; o; o >>= 1) {
-    a += __shfl_xor_sync(0xffffffffu, a, o);
-    b += __shfl_xor_sync(0xffffffffu, b, o);
-    c += __shfl_xor_sync(0xffffffffu, c, o);
-  }
-  if ((tid & 31) == 0) {
-    red[0][tid >> 5] = (double)a;
-    red[1][tid >> 5] = (double)b;
-    red[2][tid >> 5] = (double)c;
-  }
-  __syncthreads();
-  if (tid < 3) {
-    double s = 0.0;
-#pragma unroll
-    for (int w = 0; w < NT / 32; ++w) s += red[tid][w];
-    const int row = tid == 0 ? ra : (tid == 1 ? rb : rc);
-    if (row >= 0) part[(size_t)row * nblk + bid] = s;
-  }
-}
-
-// One tile (index bid of nblk) of one pass; the CTA's shared memory is smem_raw. Used by the
-// per-pass kernels (one CTA per tile) and by the batched persistent kernel (a CTA walks the tiles).
-// stp / stl: the tile's psi / lambda already staged in shared memory in tile-index order (NULL:
-// load from global memory). ONEBUF: exchange two vectors one after the other through a single
-// shared buffer (leaves room for the staging area).
-struct NoHook {
-  __device__ void operator()() const {}
-};
-
-// hook() runs once, right after the pass's first shared-memory exchange: by then every thread has
-// finished reading the staged tile, so a pipelined caller can start refilling the stage.
-template <class T, int SHAPE, bool ONEBUF = false, class Hook = NoHook>
-__device__ __forceinline__ void run_pass(const PassArgs<T>& a, uint32_t bid, uint32_t nblk,
-                                         unsigned char* smem_raw,
-                                         const typename Cx<T>::t* stp = nullptr,
-                                         const typename Cx<T>::t* stl = nullptr,
-                                         const Hook& hook = Hook{}) {
-  using C = typename Cx<T>::t;
-  C* sm = reinterpret_cast<C*>(smem_raw);
-  // two-vector transpose through one or two shared buffers
-  auto x2 = [&](auto lf, auto lt, C(&p)[R], C(&l)[R]) {
-    constexpr int LF = decltype(lf)::value, LT = decltype(lt)::value;
-    if constexpr (ONEBUF) {
-      xchg<LF, LT>(p, sm, threadIdx.x);
-      xchg<LF, LT>(l, sm, threadIdx.x);
-    } else {
-      xchg2<LF, LT>(p, l, sm, threadIdx.x);
-    }
-  };
-  using I0 = std::integral_constant<int, 0>;
-  using I1 = std::integral_constant<int, 1>;
-  using I2 = std::integral_constant<int, 2>;
-  // load psi (or lambda) of this tile in layout L, from the stage when there is one
-  auto ld = [&](auto li, C(&v)[R], const C* g, const C* st, uint32_t off) {
-    constexpr int L = decltype(li)::value;
-    if (st) sget_lin<L>(v, st, threadIdx.x);
-    else gload<L>(v, g, off, a.tile);
-  };
-  const int tid = threadIdx.x;
-  const uint32_t base = tile_base(a.tile, bid);
-  const uint32_t off0 = base + toff(a.tile, tj<0>(0, tid));
-  const uint32_t off2 = base + toff(a.tile, tj<2>(0, tid));
-  // storage-form parity of the thread's own index bits in each layout
-  const uint32_t bpar = __popc(base) & 1u;
-  const uint32_t tp0 = bpar ^ (__popc(tj<0>(0, tid)) & 1u);
-  const uint32_t tp1 = bpar ^ (__popc(tj<1>(0, tid)) & 1u);
-  const uint32_t tp2 = bpar ^ (__popc(tj<2>(0, tid)) & 1u);
-  T qv[R];
-
-  // phase exp(-+i gamma q) on the amplitudes of layout 2 (dir = +1 forward, -1 adjoint)
-  auto phase2 = [&](C (&v)[R], T dir) {
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      T c, s;
-      phase_cs(qv[r], a.ph0, a.ph1, c, s);
-      s = (tp2 ^ (uint32_t)cpar(tj<2>(r, 0))) ? -dir * s : dir * s;
-      v[r] = phase_mul(v[r], c, s);
-    }
-  };
-
-  C v[R];
-  if constexpr (SHAPE == F0) {
-    if (a.gen_init) {
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const bool sw = tp2 ^ (uint32_t)cpar(tj<2>(r, 0));
-        v[r].x = sw ? T(0) : a.init_amp;
-        v[r].y = sw ? a.init_amp : T(0);
-      }
-    } else {
-      if (stp) sget_lin<2>(v, stp, tid);
-      else gload<2>(v, a.psi_in, off2, a.tile);
-#pragma unroll
-      for (int r = 0; r < R; ++r)   // caller-visible psi0 is in normal form
-        if (tp2 ^ (uint32_t)cpar(tj<2>(r, 0))) v[r] = swp(v[r]);
-    }
-    qload<2>(qv, a.q, off2, a.tile);
-    phase2(v, T(1));
-    rot_layout<2>(v, a.mask_aft, a.ca, a.sa, tp2);
-    xchg<2, 1>(v, sm, tid);
-    hook();
-    rot_layout<1>(v, a.mask_aft, a.ca, a.sa, tp1);
-    xchg<1, 0>(v, sm, tid);
-    rot_layout<0>(v, a.mask_aft, a.ca, a.sa, tp0);
-    gstore<0>(v, a.psi_out, off0, a.tile);
-  } else if constexpr (SHAPE == F1) {
-    ld(I0{}, v, a.psi_in, stp, off0);
-    rot_layout<0>(v, a.mask_bef, a.cb, a.sb, tp0);
-    xchg<0, 1>(v, sm, tid);
-    hook();
-    rot_layout<1>(v, a.mask_bef, a.cb, a.sb, tp1);
-    qload<2>(qv, a.q, off2, a.tile);
-    xchg<1, 2>(v, sm, tid);
-    rot_layout<2>(v, a.mask_bef, a.cb, a.sb, tp2);
-    phase2(v, T(1));
-    rot_layout<2>(v, a.mask_aft, a.ca, a.sa, tp2);
-    xchg<2, 1>(v, sm, tid);
-    rot_layout<1>(v, a.mask_aft, a.ca, a.sa, tp1);
-    xchg<1, 0>(v, sm, tid);
-    rot_layout<0>(v, a.mask_aft, a.ca, a.sa, tp0);
-    gstore<0>(v, a.psi_out, off0, a.tile);
-  } else if constexpr (SHAPE == F2) {
-    ld(I0{}, v, a.psi_in, stp, off0);
-    rot_layout<0>(v, a.mask_bef, a.cb, a.sb, tp0);
-    xchg<0, 1>(v, sm, tid);
-    hook();
-    rot_layout<1>(v, a.mask_bef, a.cb, a.sb, tp1);
-    xchg<1, 2>(v, sm, tid);
-    rot_layout<2>(v, a.mask_bef, a.cb, a.sb, tp2);
-    gstore<2>(v, a.psi_out, off2, a.tile);
-  } else if constexpr (SHAPE == FE || SHAPE == FV) {
-    ld(I0{}, v, a.psi_in, stp, off0);
-    rot_layout<0>(v, a.mask_bef, a.cb, a.sb, tp0);
-    xchg<0, 1>(v, sm, tid);
-    hook();
-    rot_layout<1>(v, a.mask_bef, a.cb, a.sb, tp1);
-    qload<2>(qv, a.q, off2, a.tile);
-    xchg<1, 2>(v, sm, tid);
-    rot_layout<2>(v, a.mask_bef, a.cb, a.sb, tp2);
-    T e = T(0);
-#pragma unroll
-    for (int r = 0; r < R; ++r) e += qv[r] * (v[r].x * v[r].x + v[r].y * v[r].y);
-    if constexpr (SHAPE == FV) {
-      gstore_normal<2>(v, a.psi_out, off2, a.tile, tp2);
-      block_store3(e, T(0), T(0), a.part, a.row_E, -1, -1, tid, bid, nblk);
-    } else {
-      C l[R];
-#pragma unroll
-      for (int r = 0; r < R; ++r) { l[r].x = qv[r] * v[r].x; l[r].y = qv[r] * v[r].y; }
-      T acc = T(0);
-      unrot_layout_acc<2>(v, l, a.mask_bef, a.cb, a.sb, tp2, acc);
-      x2(I2{}, I1{}, v, l);
-      unrot_layout_acc<1>(v, l, a.mask_bef, a.cb, a.sb, tp1, acc);
-      x2(I1{}, I0{}, v, l);
-      unrot_layout_acc<0>(v, l, a.mask_bef, a.cb, a.sb, tp0, acc);
-      gstore<0>(l, a.lam_out, off0, a.tile);
-      block_store3(e, T(2) * acc, T(0), a.part, a.row_E, a.row_bef, -1, tid, bid, nblk);
-    }
-  } else if constexpr (SHAPE == R1 || SHAPE == R0) {
-    C l[R];
-    ld(I0{}, v, a.psi_in, stp, off0);
-    ld(I0{}, l, a.lam_in, stl, off0);
-    T acc_a = T(0), acc_b = T(0), acc_g = T(0);
-    unrot_layout_acc<0>(v, l, a.mask_aft, a.ca, a.sa, tp0, acc_a);
-    x2(I0{}, I1{}, v, l);
-    hook();
-    unrot_layout_acc<1>(v, l, a.mask_aft, a.ca, a.sa, tp1, acc_a);
-    qload<2>(qv, a.q, off2, a.tile);
-    x2(I1{}, I2{}, v, l);
-    unrot_layout_acc<2>(v, l, a.mask_aft, a.ca, a.sa, tp2, acc_a);
-    {
-      T ge = T(0), go = T(0);
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        if (cpar(tj<2>(r, 0))) go += qv[r] * imdot_st(l[r], v[r]);
-        else ge += qv[r] * imdot_st(l[r], v[r]);
-      }
-      acc_g = tp2 ? (go - ge) : (ge - go);
-    }
-    if constexpr (SHAPE == R1) {
-      phase2(v, T(-1));
-      phase2(l, T(-1));
-      unrot_layout_acc<2>(v, l, a.mask_bef, a.cb, a.sb, tp2, acc_b);
-      x2(I2{}, I1{}, v, l);
-      unrot_layout_acc<1>(v, l, a.mask_bef, a.cb, a.sb, tp1, acc_b);
-      x2(I1{}, I0{}, v, l);
-      unrot_layout_acc<0>(v, l, a.mask_bef, a.cb, a.sb, tp0, acc_b);
-      gstore<0>(l, a.lam_out, off0, a.tile);
-      if (a.psi_out) gstore<0>(v, a.psi_out, off0, a.tile);
-    }
-    block_store3(T(2) * acc_b, T(2) * acc_a, T(2) * acc_g, a.part, a.row_bef, a.row_aft, a.row_gam, tid, bid, nblk);
-  } else if constexpr (SHAPE == R2) {
-    C l[R];
-    ld(I2{}, v, a.psi_in, stp, off2);
-    ld(I2{}, l, a.lam_in, stl, off2);
-    T acc_b = T(0);
-    unrot_layout_acc<2>(v, l, a.mask_bef, a.cb, a.sb, tp2, acc_b);
-    x2(I2{}, I1{}, v, l);
-    hook();
-    unrot_layout_acc<1>(v, l, a.mask_bef, a.cb, a.sb, tp1, acc_b);
-    x2(I1{}, I0{}, v, l);
-    unrot_layout_acc<0>(v, l, a.mask_bef, a.cb, a.sb, tp0, acc_b);
-    gstore<0>(l, a.lam_out, off0, a.tile);
-    if (a.psi_out) gstore<0>(v, a.psi_out, off0, a.tile);
-    block_store3(T(2) * acc_b, T(0), T(0), a.part, a.row_bef, -1, -1, tid, bid, nblk);
-  }
-}
-
-template <class T, int SHAPE>
-__global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 1 : ((SHAPE == FE || SHAPE == R1 || SHAPE == R2 || SHAPE == R0) ? 2 : 3))
-pass_kernel(const __grid_constant__ PassArgs<T> a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  run_pass<T, SHAPE>(a, blockIdx.x, gridDim.x, smem_raw);
-}
-
-// Persistent, software-pipelined form of the complex64 passes: each CTA walks tiles
-// blockIdx.x, blockIdx.x + gridDim.x, ...; the next tile's psi (and lambda) are fetched into a
-// shared-memory stage by asynchronous 16-byte copies (cp.async, no registers held) while the current
-// tile is computed, so HBM reads overlap the rotations and exchanges.
-template <int SHAPE>
-struct PipeTraits {
-  static constexpr int NV = (SHAPE == R1 || SHAPE == R2 || SHAPE == R0) ? 2 : 1;   // staged vectors
-  // CTAs per SM: FE stages one vector but holds two in registers in its second half
-  static constexpr int MINB = (NV == 2 || SHAPE == FE) ? 2 : 3;
-  static constexpr size_t smem_bytes() {
-    return (size_t)SM_SLOTS * sizeof(float2) + (size_t)NV * TILE * sizeof(float2);
-  }
-};
-
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-
-template <int SHAPE>
-__global__ void __launch_bounds__(NT, PipeTraits<SHAPE>::MINB)
-pipe_kernel(const __grid_constant__ PassArgs<float> a, uint32_t ntiles) {
-  constexpr int NV = PipeTraits<SHAPE>::NV;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  float2* stage = reinterpret_cast<float2*>(smem_raw + (size_t)SM_SLOTS * sizeof(float2));
-  const int tid = threadIdx.x;
-  const bool staged = !(SHAPE == F0 && a.gen_init);
-  // thread tid copies the amplitude pairs (2c, 2c + 1), c = tid + k * NT, of tile t
-  auto issue = [&](uint32_t t) {
-    const uint32_t base = tile_base(a.tile, t);
-#pragma unroll
-    for (int k = 0; k < TILE / 2 / NT; ++k) {
-      const uint32_t j = 2u * (uint32_t)(tid + k * NT);
-      const uint32_t g = base + toff(a.tile, j);
-      cp_async16(stage + j, a.psi_in + g);
-      if constexpr (NV == 2) cp_async16(stage + TILE + j, a.lam_in + g);
-    }
-    cp_async_commit();
-  };
-  uint32_t t = blockIdx.x;
-  if (staged && t < ntiles) issue(t);
-  for (; t < ntiles; t += gridDim.x) {
-    if (staged) {
-      cp_async_wait_all();
-      __syncthreads();
-    }
-    const uint32_t next = t + gridDim.x;
-    auto refill = [&]() {
-      if (staged && next < ntiles) issue(next);
-    };
-    run_pass<float, SHAPE, true>(a, t, ntiles, smem_raw, staged ? stage : nullptr,
-                                 (staged && NV == 2) ? stage + TILE : nullptr, refill);
-  }
-}
 
 // ---------------------------------------------------------------- small states (n <= TB)
 //
@@ -541,38 +233,6 @@ static int make_plan(int n, int p, Plan& pl) {
   return QVS_OK;
 }
 
-template <class T>
-static void fill_angles(PassArgs<T>& a, const PassInfo& pi, const double* gammas, const double* ts) {
-  a.cb = a.sb = a.ca = a.sa = T(0);
-  if (pi.lb >= 0) { a.cb = (T)cos(ts[pi.lb]); a.sb = (T)sin(ts[pi.lb]); }
-  if (pi.la >= 0) { a.ca = (T)cos(ts[pi.la]); a.sa = (T)sin(ts[pi.la]); }
-  a.ph0 = a.ph1 = T(0);
-  if (pi.lg >= 0) {
-    if constexpr (sizeof(T) == 4) {
-      float hi, lo;
-      turns_split(gammas[pi.lg], &hi, &lo);
-      a.ph0 = hi;
-      a.ph1 = lo;
-    } else {
-      a.ph0 = gammas[pi.lg];
-    }
-  }
-}
-
-template <class T, int S>
-static int launch_one(const PassArgs<T>& a, uint32_t grid, cudaStream_t st) {
-  constexpr bool two = S == FE || S == R1 || S == R2 || S == R0;
-  const size_t sm = (two ? 2 : 1) * (size_t)SM_SLOTS * sizeof(typename Cx<T>::t);
-  static bool configured = false;   // per instantiation
-  if (!configured) {
-    QVS_CUDA_TRY(cudaFuncSetAttribute(pass_kernel<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)sm));
-    configured = true;
-  }
-  pass_kernel<T, S><<<grid, NT, sm, st>>>(a);
-  QVS_CUDA_TRY(cudaGetLastError());
-  return QVS_OK;
-}
 
 static const char* shape_name(int shape, bool dbl) {
   static const char* f[] = {"hc_pass_F0_c64", "hc_pass_F1_c64", "hc_pass_F2_c64", "hc_pass_FE_c64",
@@ -597,35 +257,39 @@ static double shape_bytes(int shape, const void* psi_in, const void* psi_out, do
   return 0.0;
 }
 
-template <class T>
-static int launch_shape_raw(int shape, const PassArgs<T>& a, uint32_t grid, cudaStream_t st);
-
-template <int S>
-static int launch_pipe(const PassArgs<float>& a, uint32_t ntiles, int sms, cudaStream_t st) {
-  const size_t sm = PipeTraits<S>::smem_bytes();
-  static bool configured = false;
-  if (!configured) {
-    QVS_CUDA_TRY(cudaFuncSetAttribute(pipe_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    configured = true;
+// Rotation threshold of a pass from its masks: every used mask must be "tile bits >= TH" for one
+// TH that has a compiled complex64 kernel (TH_NONE: no "before" bits, all "after" bits), else the
+// runtime-mask kernel runs.
+static int pass_threshold(int shape, uint32_t mask_bef, uint32_t mask_aft) {
+  const bool ub = shape == F1 || shape == F2 || shape == FE || shape == FV || shape == R1 || shape == R2;
+  const bool ua = shape == F0 || shape == F1 || shape == R1 || shape == R0;
+  auto th = [](uint32_t m) -> int {
+    if (m == 0) return -2;
+    int t = 0;
+    while (!((m >> t) & 1u)) ++t;
+    return m == (((1u << TB) - 1u) & ~((1u << t) - 1u)) ? t : -3;
+  };
+  const int tb = ub ? th(mask_bef) : -4, ta = ua ? th(mask_aft) : -4;
+  int t = TH_RUNTIME;
+  if (ub && ua) {
+    if (tb >= 0 && tb == ta) t = tb;
+    else if (tb == -2 && ta == 0) t = TH_NONE;
+  } else if (ub) {
+    t = tb >= 0 ? tb : TH_RUNTIME;
+  } else if (ua) {
+    t = ta >= 0 ? ta : TH_RUNTIME;
   }
-  const uint32_t grid = std::min<uint32_t>(ntiles, (uint32_t)(sms * PipeTraits<S>::MINB));
-  pipe_kernel<S><<<grid, NT, sm, st>>>(a, ntiles);
-  QVS_CUDA_TRY(cudaGetLastError());
-  return QVS_OK;
+  return t;
 }
 
-static int launch_pipe_shape(int shape, const PassArgs<float>& a, uint32_t ntiles, int sms, cudaStream_t st) {
-  switch (shape) {
-    case F0: return launch_pipe<F0>(a, ntiles, sms, st);
-    case F1: return launch_pipe<F1>(a, ntiles, sms, st);
-    case F2: return launch_pipe<F2>(a, ntiles, sms, st);
-    case FE: return launch_pipe<FE>(a, ntiles, sms, st);
-    case FV: return launch_pipe<FV>(a, ntiles, sms, st);
-    case R1: return launch_pipe<R1>(a, ntiles, sms, st);
-    case R2: return launch_pipe<R2>(a, ntiles, sms, st);
-    case R0: return launch_pipe<R0>(a, ntiles, sms, st);
+static int launch_c64(int th, int shape, const PassArgs<float>& a, uint32_t grid, cudaStream_t st) {
+  switch (th) {
+#define QVS_HC_CASE(K) \
+    case K: return launch_pass<float, K>(shape, a, grid, st);
+    QVS_HC_C64_THRESHOLDS(QVS_HC_CASE)
+#undef QVS_HC_CASE
+    default: return launch_pass<float, TH_RUNTIME>(shape, a, grid, st);
   }
-  return QVS_EINVAL;
 }
 
 template <class T>
@@ -633,29 +297,13 @@ static int launch_shape(qvs_ctx* h, int shape, const PassArgs<T>& a, uint32_t gr
   cudaEvent_t ev;
   QVS_TRY(prof_begin(h, &ev));
   if constexpr (sizeof(T) == 4) {
-    if (h->pipeline) QVS_TRY(launch_pipe_shape(shape, a, grid, h->sms, h->stream));
-    else QVS_TRY(launch_shape_raw<T>(shape, a, grid, h->stream));
+    QVS_TRY(launch_c64(pass_threshold(shape, a.mask_bef, a.mask_aft), shape, a, grid, h->stream));
   } else {
-    QVS_TRY(launch_shape_raw<T>(shape, a, grid, h->stream));
+    QVS_TRY((launch_pass<T, TH_RUNTIME>(shape, a, grid, h->stream)));
   }
   const double c = sizeof(typename Cx<T>::t), qb = sizeof(T);
   return prof_end(h, shape_name(shape, sizeof(T) == 8),
                   shape_bytes(shape, a.psi_in, a.psi_out, c, qb) * (double)grid * TILE, ev);
-}
-
-template <class T>
-static int launch_shape_raw(int shape, const PassArgs<T>& a, uint32_t grid, cudaStream_t st) {
-  switch (shape) {
-    case F0: return launch_one<T, F0>(a, grid, st);
-    case F1: return launch_one<T, F1>(a, grid, st);
-    case F2: return launch_one<T, F2>(a, grid, st);
-    case FE: return launch_one<T, FE>(a, grid, st);
-    case FV: return launch_one<T, FV>(a, grid, st);
-    case R1: return launch_one<T, R1>(a, grid, st);
-    case R2: return launch_one<T, R2>(a, grid, st);
-    case R0: return launch_one<T, R0>(a, grid, st);
-  }
-  return QVS_EINVAL;
 }
 
 // ---------------------------------------------------------------- small-state driver
@@ -764,10 +412,19 @@ static int run_tiled(qvs_ctx* h, int p, const double* gammas, const double* ts, 
                                cudaMemcpyHostToDevice, h->stream));
 
   const T amp = (T)(1.0 / sqrt((double)h->dim));
+  const int n = h->n;
   int64_t launches = 0;
+  // Frames (scale k and flip F of the stored vector) at the pass boundaries, tracked on the host:
+  // fw[j] = psi after forward pass j.
+  std::vector<Frame> fw(F + 1, Frame{1.0, 0});
+  Frame fr{1.0, 0}, lf{1.0, 0};
+  // qvs_evolve under a flipped final frame writes the output at complemented indices: another
+  // tile's input, so it goes to a second buffer
+  C* out_buf = W;
   // forward
   for (int j = 1; j <= F; ++j) {
     const PassInfo& pi = pl.pass[j];
+    const int G = __builtin_popcount(pl.gmask[pi.type]);
     PassArgs<T> a{};
     a.tile = pl.tile[pi.type];
     a.q = h->q.as<T>();
@@ -778,34 +435,41 @@ static int run_tiled(qvs_ctx* h, int p, const double* gammas, const double* ts, 
     a.gen_init = h->have_psi0 ? 0 : 1;
     a.mask_bef = pi.lb >= 0 ? pl.gmask[pi.type] : 0u;
     a.mask_aft = pi.la >= 0 ? pl.gmask[pi.type] : 0u;
-    fill_angles(a, pi, gammas, ts);
     a.psi_in = (j == 1) ? (h->have_psi0 ? h->psi0.as<C>() : nullptr) : loc(j - 1);
     int shape = pi.shape;
+    if (j == F) shape = grad ? FE : FV;
+    fwd_scalars<T>(a, shape, pi.lb, pi.la, pi.lg, G, n, p, gammas, ts, fr, lf);
     if (j == F) {
       if (grad) {
         a.lam_out = h->lam.as<C>();
         a.row_bef = 3 * (j - 1) + 0;
       } else {
-        shape = FV;
-        a.psi_out = W;
+        if (a.ox) {
+          QVS_TRY(h->lam.ensure(sbytes));
+          out_buf = h->lam.as<C>();
+        }
+        a.psi_out = out_buf;
       }
     } else {
       a.psi_out = grad ? loc(j) : W;
+      fw[j] = fr;
     }
     QVS_TRY(launch_shape<T>(h, shape, a, grid));
     ++launches;
   }
+  if (out_buf != W) std::swap(h->psi, h->lam);
   // adjoint
   if (grad) {
+    Frame pout{1.0, 0};
     for (int j = F - 1; j >= 1; --j) {
       const PassInfo& pi = pl.pass[j];
+      const int G = __builtin_popcount(pl.gmask[pi.type]);
       PassArgs<T> a{};
       a.tile = pl.tile[pi.type];
       a.q = h->q.as<T>();
       a.part = h->part.as<double>();
       a.mask_bef = pi.lb >= 0 ? pl.gmask[pi.type] : 0u;
       a.mask_aft = pi.la >= 0 ? pl.gmask[pi.type] : 0u;
-      fill_angles(a, pi, gammas, ts);
       a.psi_in = loc(j);
       a.lam_in = h->lam.as<C>();
       a.lam_out = h->lam.as<C>();
@@ -815,6 +479,11 @@ static int run_tiled(qvs_ctx* h, int p, const double* gammas, const double* ts, 
       a.row_gam = pi.lg >= 0 ? 3 * (j - 1) + 2 : -1;
       a.row_E = -1;
       const int shape = pi.shape == F0 ? R0 : (pi.shape == F1 ? R1 : R2);
+      // psi at boundary j: a checkpoint or the forward sweep's last write (frame fw[j]), else the
+      // previous adjoint pass's uncompute
+      Frame pf = (is_stored(j) || j == F - 1) ? fw[j] : pout;
+      bwd_scalars<T>(a, shape, pi.lb, pi.la, pi.lg, G, n, gammas, ts, pf, lf);
+      pout = pf;
       QVS_TRY(launch_shape<T>(h, shape, a, grid));
       ++launches;
     }
@@ -884,6 +553,8 @@ int hc_gradient(qvs_ctx* h, int p, const double* gammas, const double* ts, doubl
 namespace qvs {
 namespace hc {
 
+constexpr int BATCH_MAX_LAYERS = 64;
+
 struct BInst {
   int n, p, F, g;
   uint32_t ntiles;
@@ -937,20 +608,21 @@ __device__ __forceinline__ void bpass_info(const BInst& I, int j, int& type, int
 __device__ __forceinline__ void run_shape(int shape, const PassArgs<float>& a, uint32_t t, uint32_t nt,
                                           unsigned char* sm) {
   switch (shape) {
-    case F0: run_pass<float, F0>(a, t, nt, sm); break;
-    case F1: run_pass<float, F1>(a, t, nt, sm); break;
-    case F2: run_pass<float, F2>(a, t, nt, sm); break;
-    case FE: run_pass<float, FE>(a, t, nt, sm); break;
-    case R1: run_pass<float, R1>(a, t, nt, sm); break;
-    case R2: run_pass<float, R2>(a, t, nt, sm); break;
-    case R0: run_pass<float, R0>(a, t, nt, sm); break;
+    case F0: run_pass<float, F0, TH_RUNTIME>(a, t, nt, sm); break;
+    case F1: run_pass<float, F1, TH_RUNTIME>(a, t, nt, sm); break;
+    case F2: run_pass<float, F2, TH_RUNTIME>(a, t, nt, sm); break;
+    case FE: run_pass<float, FE, TH_RUNTIME>(a, t, nt, sm); break;
+    case R1: run_pass<float, R1, TH_RUNTIME>(a, t, nt, sm); break;
+    case R2: run_pass<float, R2, TH_RUNTIME>(a, t, nt, sm); break;
+    case R0: run_pass<float, R0, TH_RUNTIME>(a, t, nt, sm); break;
   }
 }
 
 __global__ void __launch_bounds__(NT, 2) batch_kernel(const __grid_constant__ BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_inst;
-  __shared__ float s_ang[6];
+  __shared__ PassArgs<float> s_pa;
+  __shared__ Frame s_fw[2 * BATCH_MAX_LAYERS + 2];   // psi frame after forward pass j
   const int tid = threadIdx.x;
   unsigned char* slot = a.ws + (size_t)blockIdx.x * a.slot_bytes;
   float2* W = reinterpret_cast<float2*>(slot);
@@ -971,60 +643,55 @@ __global__ void __launch_bounds__(NT, 2) batch_kernel(const __grid_constant__ Ba
     auto loc = [&](int j) -> float2* {
       return is_stored(j) ? K + (size_t)(j / I.ck_c - 1) * dim : W;
     };
+    // frames of psi / lambda (thread 0 only; see the host driver)
+    Frame fr{1.0, 0}, lf{1.0, 0}, pout{1.0, 0};
     for (int step = 0; step < 2 * F - 1; ++step) {
       const bool fwd = step < F;
       const int j = fwd ? step + 1 : 2 * F - 1 - step;   // forward 1..F, then F-1..1
       int type, shape, lb, la, lg;
       bpass_info(I, j, type, shape, lb, la, lg);
       if (tid == 0) {
-        s_ang[0] = lb >= 0 ? (float)cos(a.ts[I.th0 + lb]) : 0.f;
-        s_ang[1] = lb >= 0 ? (float)sin(a.ts[I.th0 + lb]) : 0.f;
-        s_ang[2] = la >= 0 ? (float)cos(a.ts[I.th0 + la]) : 0.f;
-        s_ang[3] = la >= 0 ? (float)sin(a.ts[I.th0 + la]) : 0.f;
-        if (lg >= 0) {
-          const double g = a.gammas[I.th0 + lg] / 6.283185307179586476925286766559;
-          const float hi = (float)g;
-          s_ang[4] = hi;
-          s_ang[5] = (float)(g - (double)hi);
+        PassArgs<float> pa{};
+        pa.tile = I.tile[type];
+        pa.q = a.q + I.qoff;
+        pa.mask_bef = lb >= 0 ? I.gmask[type] : 0u;
+        pa.mask_aft = la >= 0 ? I.gmask[type] : 0u;
+        pa.part = part;
+        pa.init_amp = (float)rsqrt((double)dim);
+        pa.gen_init = 1;
+        pa.row_bef = pa.row_aft = pa.row_gam = pa.row_E = -1;
+        const int G = __popc(I.gmask[type]);
+        const double* gs = a.gammas + I.th0;
+        const double* ts = a.ts + I.th0;
+        if (fwd) {
+          fwd_scalars<float>(pa, shape, lb, la, lg, G, I.n, I.p, gs, ts, fr, lf);
+          pa.psi_in = j == 1 ? nullptr : loc(j - 1);
+          if (j == F) {
+            pa.lam_out = Lm;
+            pa.row_bef = lb >= 0 ? 3 * (j - 1) : -1;
+            pa.row_E = 3 * F;
+          } else {
+            pa.psi_out = loc(j);
+            s_fw[j] = fr;
+          }
         } else {
-          s_ang[4] = s_ang[5] = 0.f;
+          const int rshape = shape == F0 ? R0 : (shape == F1 ? R1 : R2);
+          Frame pf = (is_stored(j) || j == F - 1) ? s_fw[j] : pout;
+          bwd_scalars<float>(pa, rshape, lb, la, lg, G, I.n, gs, ts, pf, lf);
+          pout = pf;
+          pa.psi_in = loc(j);
+          pa.lam_in = Lm;
+          pa.lam_out = Lm;
+          pa.psi_out = (j - 1 >= 1 && !is_stored(j - 1)) ? W : nullptr;
+          pa.row_bef = lb >= 0 ? 3 * (j - 1) + 0 : -1;
+          pa.row_aft = la >= 0 ? 3 * (j - 1) + 1 : -1;
+          pa.row_gam = lg >= 0 ? 3 * (j - 1) + 2 : -1;
         }
+        s_pa = pa;
       }
       __syncthreads();
-      PassArgs<float> pa{};
-      pa.tile = I.tile[type];
-      pa.q = a.q + I.qoff;
-      pa.mask_bef = lb >= 0 ? I.gmask[type] : 0u;
-      pa.mask_aft = la >= 0 ? I.gmask[type] : 0u;
-      pa.cb = s_ang[0];
-      pa.sb = s_ang[1];
-      pa.ca = s_ang[2];
-      pa.sa = s_ang[3];
-      pa.ph0 = s_ang[4];
-      pa.ph1 = s_ang[5];
-      pa.part = part;
-      pa.init_amp = (float)rsqrt((double)dim);
-      pa.gen_init = 1;
-      pa.row_bef = pa.row_aft = pa.row_gam = pa.row_E = -1;
-      if (fwd) {
-        pa.psi_in = j == 1 ? nullptr : loc(j - 1);
-        if (j == F) {
-          pa.lam_out = Lm;
-          pa.row_bef = lb >= 0 ? 3 * (j - 1) : -1;
-          pa.row_E = 3 * F;
-        } else {
-          pa.psi_out = loc(j);
-        }
-      } else {
-        shape = shape == F0 ? R0 : (shape == F1 ? R1 : R2);
-        pa.psi_in = loc(j);
-        pa.lam_in = Lm;
-        pa.lam_out = Lm;
-        pa.psi_out = (j - 1 >= 1 && !is_stored(j - 1)) ? W : nullptr;
-        pa.row_bef = lb >= 0 ? 3 * (j - 1) + 0 : -1;
-        pa.row_aft = la >= 0 ? 3 * (j - 1) + 1 : -1;
-        pa.row_gam = lg >= 0 ? 3 * (j - 1) + 2 : -1;
-      }
+      const PassArgs<float> pa = s_pa;
+      if (!fwd) shape = shape == F0 ? R0 : (shape == F1 ? R1 : R2);
       for (uint32_t t = 0; t < I.ntiles; ++t) run_shape(shape, pa, t, I.ntiles, smem_raw);
       __syncthreads();   // every tile of this pass is written before the next pass reads it
     }
@@ -1124,7 +791,7 @@ extern "C" int qvs_batch_create(qvs_batch_t* out, int count, const int32_t* n_qu
   size_t max_rows_tiles = 0;
   for (int i = 0; i < count; ++i) {
     const int n = n_qubits[i], p = layers[i];
-    if (n < TB || n > 28 || p < 1 || p > 64) {
+    if (n < TB || n > 28 || p < 1 || p > BATCH_MAX_LAYERS) {
       delete b;
       return n < TB ? QVS_EUNSUPPORTED : QVS_EINVAL;
     }

@@ -95,7 +95,6 @@ struct qvs_ctx {
 
   int sms = 0;               // multiprocessors of the device (grid sizing of persistent kernels)
   int ckpt_layers = 0;
-  int pipeline = 0;          // QVS_OPT_PIPELINE
   bool have_E = false;
   double E = 0.0;
   int64_t launches = 0;
@@ -158,7 +157,7 @@ int reduce_rows(qvs_ctx* h, const double* part, int64_t nblk, const int* rowmap_
                 double* out_dev);
 
 // float-float turns of an angle gamma: gamma / (2 pi) split into hi + lo floats.
-inline void turns_split(double gamma, float* hi, float* lo) {
+__host__ __device__ inline void turns_split(double gamma, float* hi, float* lo) {
   const double two_pi = 6.283185307179586476925286766559;
   double g = gamma / two_pi;
   float h = (float)g;

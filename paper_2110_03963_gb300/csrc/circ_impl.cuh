@@ -128,7 +128,10 @@ __global__ void __launch_bounds__(NT, 1) col_kernel(const __grid_constant__ Circ
   auto phase_cs = [&](int r, float q, float gh, float gl, float& c, float& s) {
     __sincosf(6.28318530717958647692f * ff_turns(gh, gl, q, 0.0f), &s, &c);
   };
-  auto qat = [&](int r) { return __ldcs(a.qT + priv_idx(blk, r, tid_fresh())); };
+  // The side vectors never alias the stored-vector outputs: restrict-qualified copies let their
+  // loads be issued ahead of the stores instead of one latency at a time.
+  const float* __restrict__ qT = a.qT;
+  auto qat = [&](int r) { return __ldcs(qT + priv_idx(blk, r, tid_fresh())); };
   const float invL = 1.0f / (float)G::L;
 
   float2 v[R];
@@ -150,9 +153,15 @@ __global__ void __launch_bounds__(NT, 1) col_kernel(const __grid_constant__ Circ
     tile_inv<G>(v, sm, ts, tid);
     if constexpr (MODE == CM) {
 #pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = make_float2(v[r].x * invL, v[r].y * invL);
+      float2* __restrict__ po = a.priv_out;
+      if (po) {   // stored for the adjoint
+#pragma unroll
+        for (int r = 0; r < R; ++r) __stcs(po + priv_idx(blk, r, tid), v[r]);
+      }
+#pragma unroll
       for (int r = 0; r < R; ++r) {
-        const float2 x = make_float2(v[r].x * invL, v[r].y * invL);
-        if (a.priv_out) __stcs(a.priv_out + priv_idx(blk, r, tid), x);   // stored for the adjoint
+        const float2 x = v[r];
         float c, s;
         phase_cs(r, qat(r), a.ph_hi, a.ph_lo, c, s);
         v[r] = make_float2(c * x.x + s * x.y, c * x.y - s * x.x);
@@ -184,12 +193,13 @@ __global__ void __launch_bounds__(NT, 1) col_kernel(const __grid_constant__ Circ
       }
       block_store2(e, 0.0f, 1.0, a.part, a.row_a, -1);
     } else {   // RCM, RCF: v = lambda' after the adjoint mixer; gamma gradient, then phase^dagger
+      const float2* __restrict__ pin = a.priv_in;
       float g = 0.0f;
       const int jt = G::template jthr<2>(tid);
       static_for<R>([&](auto ri) {
         constexpr int r = decltype(ri)::value;
         float2 ps;
-        if constexpr (MODE == RCM) ps = __ldcs(a.priv_in + priv_idx(blk, r, tid));
+        if constexpr (MODE == RCM) ps = __ldcs(pin + priv_idx(blk, r, tid));
         else ps = a.psi0 ? __ldg(a.psi0 + gidx(jt | G::jreg(2, r))) : make_float2(a.init_amp, 0.0f);
         const float q = qat(r);
         float c, s;
@@ -230,19 +240,28 @@ __global__ void __launch_bounds__(NT, 1) row_kernel(const __grid_constant__ Circ
     });
   }
   tile_fwd<G>(v, sm, ts, tid);
+  // restrict-qualified: the table and stored-vector loads are issued ahead of the stores
+  const float2* __restrict__ lamT = a.lamT;
+  const float2* __restrict__ pin = a.priv_in;
+  float2* __restrict__ po = a.priv_out;
   float acc = 0.0f;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
-    const float2 lam = __ldcs(a.lamT + priv_idx(blk, r, tid));
+    const float2 lam = __ldcs(lamT + priv_idx(blk, r, tid));
     float s, c;
     __sincosf(6.28318530717958647692f * ff_turns(lam.x, lam.y, a.ev_hi, a.ev_lo), &s, &c);
     if constexpr (MODE == RF) {
       v[r] = make_float2(c * v[r].x + s * v[r].y, c * v[r].y - s * v[r].x);   // exp(-i t lambda)
-      if (a.priv_out) __stcs(a.priv_out + priv_idx(blk, r, tid), v[r]);
     } else {
-      const float2 x = __ldcs(a.priv_in + priv_idx(blk, r, tid));
+      const float2 x = __ldcs(pin + priv_idx(blk, r, tid));
       acc += lam.x * (v[r].x * x.y - v[r].y * x.x);
       v[r] = make_float2(c * v[r].x - s * v[r].y, c * v[r].y + s * v[r].x);   // exp(+i t lambda)
+    }
+  }
+  if constexpr (MODE == RF) {
+    if (po) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) __stcs(po + priv_idx(blk, r, tid), v[r]);
     }
   }
   tile_inv<G>(v, sm, ts, tid);

@@ -74,8 +74,10 @@ enum {
  *     W[j][(j+s) mod dim] = W[j][(j-s) mod dim] = w_s (the offset dim/2 couples each j once).
  * QVS_MIX_CSR (Sec. 2.4.1, Sec. 3): W real symmetric sparse (rowptr int64[dim+1], colind
  *     int32[nnz]), values float[nnz] or NULL for a constant implicit_value; host or device arrays
- *     per csr_on_device. spec_lo/spec_hi bound the spectrum (both 0: a Gershgorin bound is
- *     computed); cheb_tol is the Chebyshev truncation tolerance (0: 1e-7).
+ *     per csr_on_device. spec_lo/spec_hi bound the spectrum (both 0: the library estimates the
+ *     interval once, here: 64 fp64 Lanczos steps, extreme Ritz values widened by their residuals
+ *     and by 1 % of the width, capped by the Gershgorin bound); cheb_tol is the Chebyshev
+ *     truncation tolerance (0: 1e-7).
  */
 typedef struct {
   int n_qubits;

@@ -221,6 +221,195 @@ __global__ void rowptr32_kernel(int64_t n1, const int64_t* __restrict__ in, uint
     out[i] = (uint32_t)in[i];
 }
 
+// ---------------------------------------------------------------- spectral interval (Lanczos)
+//
+// A few dozen Lanczos steps in fp64 on the device give Ritz values inside the spectrum whose
+// extremes converge to the extreme eigenvalues first; their residuals bound how far an eigenvalue
+// lies from them. The interval used is the extreme Ritz values widened by those residuals and by 1 %
+// of the width, capped by the Gershgorin interval (which always encloses the spectrum).
+
+__global__ void lz_spmv_kernel(int64_t dim, const uint32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+                               const float* __restrict__ values, float iv, const double* __restrict__ x,
+                               double* __restrict__ y) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < dim; r += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (uint32_t j = rowptr[r]; j < rowptr[r + 1]; ++j) acc += (double)(values ? values[j] : iv) * x[colind[j]];
+    y[r] = acc;
+  }
+}
+
+__device__ __forceinline__ void lz_block_add(double v, double* out) {
+  __shared__ double red[NT / 32];
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sum = 0.0;
+    for (int w = 0; w < NT / 32; ++w) sum += red[w];
+    atomicAdd(out, sum);
+  }
+}
+
+// out += a . b
+__global__ void __launch_bounds__(NT) lz_dot_kernel(int64_t dim, const double* __restrict__ a,
+                                                    const double* __restrict__ b, double* out) {
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < dim; i += (int64_t)gridDim.x * blockDim.x)
+    acc += a[i] * b[i];
+  lz_block_add(acc, out);
+}
+
+// w -= alpha v + beta vprev; out += |w|^2
+__global__ void __launch_bounds__(NT) lz_update_kernel(int64_t dim, double alpha, double beta,
+                                                       const double* __restrict__ v, const double* __restrict__ vprev,
+                                                       double* __restrict__ w, double* out) {
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < dim; i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = w[i] - alpha * v[i] - beta * vprev[i];
+    w[i] = x;
+    acc += x * x;
+  }
+  lz_block_add(acc, out);
+}
+
+__global__ void lz_scale_kernel(int64_t dim, double s, const double* __restrict__ x, double* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < dim; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = s * x[i];
+}
+
+// deterministic start vector: entries from a 64-bit mix of the index, in [-1, 1)
+__global__ void lz_start_kernel(int64_t dim, double* __restrict__ v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < dim; i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t z = (uint64_t)i * 0x9E3779B97F4A7C15ull + 0x2110039630ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    v[i] = (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+  }
+}
+
+// number of eigenvalues of the symmetric tridiagonal (alpha, beta) below x (Sturm sequence)
+static int sturm_below(const std::vector<double>& al, const std::vector<double>& be, double x) {
+  int c = 0;
+  double d = 1.0;
+  for (size_t i = 0; i < al.size(); ++i) {
+    const double b2 = i ? be[i - 1] * be[i - 1] : 0.0;
+    d = al[i] - x - (i ? b2 / d : 0.0);
+    if (d == 0.0) d = -1e-300;
+    if (d < 0) ++c;
+  }
+  return c;
+}
+
+// k-th smallest eigenvalue (0-based) of the tridiagonal, by bisection
+static double tri_eig(const std::vector<double>& al, const std::vector<double>& be, int k) {
+  double lo = 1e300, hi = -1e300;
+  for (size_t i = 0; i < al.size(); ++i) {
+    const double r = (i ? fabs(be[i - 1]) : 0.0) + (i + 1 < al.size() ? fabs(be[i]) : 0.0);
+    lo = std::min(lo, al[i] - r);
+    hi = std::max(hi, al[i] + r);
+  }
+  for (int it = 0; it < 200 && hi - lo > 1e-15 * std::max(1.0, fabs(hi) + fabs(lo)); ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (sturm_below(al, be, mid) > k) hi = mid;
+    else lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+// |last component| of the unit eigenvector of the tridiagonal for eigenvalue th (inverse iteration)
+static double tri_last_component(const std::vector<double>& al, const std::vector<double>& be, double th) {
+  const size_t k = al.size();
+  std::vector<double> x(k, 1.0), c(k), d(k), y(k);
+  const double shift = th + 1e-10 * std::max(1.0, fabs(th));
+  for (int it = 0; it < 3; ++it) {
+    // solve (T - shift) y = x by the Thomas algorithm
+    for (size_t i = 0; i < k; ++i) {
+      const double a = i ? be[i - 1] : 0.0;
+      double m = al[i] - shift - (i ? a * c[i - 1] : 0.0);
+      if (fabs(m) < 1e-300) m = 1e-300;
+      c[i] = (i + 1 < k ? be[i] : 0.0) / m;
+      d[i] = (x[i] - (i ? a * d[i - 1] : 0.0)) / m;
+    }
+    for (size_t i = k; i-- > 0;) y[i] = d[i] - (i + 1 < k ? c[i] * y[i + 1] : 0.0);
+    double nrm = 0.0;
+    for (double v : y) nrm += v * v;
+    nrm = sqrt(nrm);
+    for (size_t i = 0; i < k; ++i) x[i] = y[i] / nrm;
+  }
+  return fabs(x[k - 1]);
+}
+
+static int lanczos_interval(qvs_ctx* h, int iters, double gersh, double* lo, double* hi) {
+  const int64_t dim = h->dim;
+  CsrData& C = h->csr;
+  DevBuf buf;   // freed on every return (cudaFree waits for the kernels that use it)
+  struct Release {
+    DevBuf& b;
+    ~Release() { b.release(); }
+  } release{buf};
+  QVS_TRY(buf.ensure(sizeof(double) * (3 * (size_t)dim + 2)));
+  double* v = buf.as<double>();
+  double* vp = v + dim;
+  double* w = vp + dim;
+  double* sc = w + dim;   // two accumulators
+  const float* vals = C.has_values ? C.values.as<float>() : nullptr;
+  cudaStream_t st = h->stream;
+  auto scalar = [&](double* out) -> int {
+    QVS_CUDA_TRY(cudaMemcpyAsync(out, sc, sizeof(double), cudaMemcpyDeviceToHost, st));
+    QVS_CUDA_TRY(cudaStreamSynchronize(st));
+    return QVS_OK;
+  };
+  lz_start_kernel<<<RED_GRID, NT, 0, st>>>(dim, v);
+  QVS_CUDA_TRY(cudaMemsetAsync(vp, 0, sizeof(double) * dim, st));
+  QVS_CUDA_TRY(cudaMemsetAsync(sc, 0, sizeof(double), st));
+  lz_dot_kernel<<<RED_GRID, NT, 0, st>>>(dim, v, v, sc);
+  QVS_CUDA_TRY(cudaGetLastError());
+  double n2 = 0.0;
+  QVS_TRY(scalar(&n2));
+  if (!(n2 > 0.0)) return QVS_ENUMERIC;
+  lz_scale_kernel<<<RED_GRID, NT, 0, st>>>(dim, 1.0 / sqrt(n2), v, v);
+  std::vector<double> al, be;
+  double beta = 0.0;
+  const int kmax = (int)std::min<int64_t>(iters, dim);
+  for (int j = 0; j < kmax; ++j) {
+    lz_spmv_kernel<<<RED_GRID, NT, 0, st>>>(dim, C.rowptr.as<uint32_t>(), C.colind.as<int32_t>(), vals,
+                                            C.implicit_value, v, w);
+    QVS_CUDA_TRY(cudaMemsetAsync(sc, 0, sizeof(double), st));
+    lz_dot_kernel<<<RED_GRID, NT, 0, st>>>(dim, v, w, sc);
+    QVS_CUDA_TRY(cudaGetLastError());
+    double alpha = 0.0;
+    QVS_TRY(scalar(&alpha));
+    al.push_back(alpha);
+    QVS_CUDA_TRY(cudaMemsetAsync(sc, 0, sizeof(double), st));
+    lz_update_kernel<<<RED_GRID, NT, 0, st>>>(dim, alpha, beta, v, vp, w, sc);
+    QVS_CUDA_TRY(cudaGetLastError());
+    double b2 = 0.0;
+    QVS_TRY(scalar(&b2));
+    beta = sqrt(std::max(b2, 0.0));
+    if (beta <= 1e-12 * (fabs(alpha) + gersh + 1e-300)) break;   // invariant subspace: T is exact
+    be.push_back(beta);
+    std::swap(vp, v);                                             // vprev <- v
+    lz_scale_kernel<<<RED_GRID, NT, 0, st>>>(dim, 1.0 / beta, w, v);   // v <- w / beta
+    QVS_CUDA_TRY(cudaGetLastError());
+  }
+  const int k = (int)al.size();
+  be.resize(k - 1 > 0 ? k - 1 : 0);
+  const double tlo = tri_eig(al, be, 0), thi = tri_eig(al, be, k - 1);
+  const double rlast = (int)be.size() < k ? beta : 0.0;   // beta_k: residual factor of every Ritz pair
+  const double rlo = rlast * tri_last_component(al, be, tlo);
+  const double rhi = rlast * tri_last_component(al, be, thi);
+  const double width = thi - tlo;
+  *lo = std::max(-gersh, tlo - rlo - 0.01 * width);
+  *hi = std::min(gersh, thi + rhi + 0.01 * width);
+  if (!(*hi > *lo)) {
+    *lo = -gersh;
+    *hi = gersh;
+  }
+  return QVS_OK;
+}
+
 // ---------------------------------------------------------------- host side
 
 // Chebyshev coefficients c_m = (2 - delta_m0) (-i)^m J_m(b t) e^{-i t a}, cut where the tail bound
@@ -484,8 +673,8 @@ int csr_set_mixer(qvs_ctx* h, const qvs_mixer_desc* d) {
     float g;
     memcpy(&g, &hb, sizeof(g));
     const double G = (double)g * (1.0 + 1e-6) + 1e-30;
-    C.spec_lo = -G;
-    C.spec_hi = G;
+    C.gersh = G;
+    QVS_TRY(lanczos_interval(h, 64, G, &C.spec_lo, &C.spec_hi));
   } else {
     if (!(d->spec_hi > d->spec_lo)) return QVS_EINVAL;
     C.spec_lo = d->spec_lo;

@@ -68,6 +68,7 @@ struct CsrData {
   bool has_values = false;
   float implicit_value = 0.f;
   double spec_lo = 0, spec_hi = 0, tol = 1e-7;
+  double gersh = 0;         // Gershgorin radius (0 when the caller gave the interval)
 };
 
 }  // namespace qvs

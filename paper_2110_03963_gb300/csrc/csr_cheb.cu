@@ -4,8 +4,9 @@
 // with [a - b, a + b] enclosing the spectrum (Gershgorin when no bounds are given). The series is
 // cut at the first K whose tail bound sum_{m > K} 2 |J_m(b t)| falls below the tolerance (the
 // truncation error in the 2-norm is at most that bound since |T_m| <= 1 on [-1, 1]). Coefficients
-// are computed in fp64 on the host; each term is one fused kernel: a CSR SpMV of T_m (four lanes per
-// row, gathers served from L2), the three-term recurrence and the accumulation into y.
+// are computed in fp64 on the host; each term is one fused kernel: a CSR SpMV of T_m (one lane per
+// row, up to 16 index loads in flight before their gathers, which L1/L2 serve), the three-term
+// recurrence and the accumulation into y.
 //
 // Gradient: the subspace vectors are small (C(24,12) complex64 amplitudes = 21.6 MB), so every
 // phi_k and psi_k of the forward sweep is stored and the adjoint sweep moves only lambda:
@@ -26,7 +27,7 @@ namespace qvs {
 namespace cs {
 
 constexpr int NT = 256;
-constexpr int LPR = 4;                 // lanes per row
+constexpr int LPR = 1;                 // lanes per row
 constexpr int ROWS_PER_CTA = NT / LPR;
 constexpr int RED_GRID = 152 * 8;      // CTAs of the elementwise/reduction kernels
 
@@ -54,8 +55,11 @@ __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
 // sum over the row's nonzeros of value * x[col], by LPR lanes. Every lane of the warp must call
 // it (the lane sum uses full-warp shuffles); lanes past the last row pass valid = false. Each
 // lane issues the index loads of up to UNR nonzeros before their gathers, so the
-// row pointer -> column index -> vector chain is paid once per UNR*LPR nonzeros.
-constexpr int UNR = 4;
+// row pointer -> column index -> vector chain is paid once per UNR*LPR nonzeros. The step is bound
+// by that chain's latency, so the number of rows in flight is what matters: one lane per row with
+// 16 loads in flight ran the C(24,12) step in 75 us, against 82 us at 2 lanes x 8 and 104 us at
+// 4 lanes x 4.
+constexpr int UNR = 16;
 
 __device__ __forceinline__ float2 row_spmv(const uint32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
                                            const float* __restrict__ values, float iv,

@@ -38,6 +38,37 @@ UNIT = "amp-layer/s"
 WORKLOAD = "QAOA weighted max-cut, n=28 (2^28 complex64 amplitudes), G(28,1/2) U[0,1] weights, p=8, objective + adjoint gradient"
 
 
+# DRAM traffic of the dominant kernel per amplitude, from one ncu capture of the same kernels
+# (profiles/hc_passes_qaoa25_dram.md: measured at n=25, averaged over the launch mix of the n=28,
+# p=8 solve). Reported only while the kernel sources hash to the value recorded in that file.
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "hc_passes_qaoa25_dram.md")
+TRAFFIC_BYTES_PER_AMP = {"hc_pass_R1_c64": 32.0}
+TRAFFIC_SOURCES = ["hc_kernels.cuh", "hc_pass.cuh", "hypercube.cu", "hc_pass_th_a.cu", "hc_pass_th_b.cu",
+                   "hc_pass_th_c.cu", "hc_pass_th_d.cu"]
+
+
+def kernel_sources_sha256() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_2110_03963_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def _traffic_per_launch(kernel: str, amplitudes: int):
+    """ncu DRAM bytes per launch of `kernel` at the benchmark size, or None when the capture no
+    longer describes the built kernels."""
+    try:
+        with open(TRAFFIC_PROFILE) as f:
+            text = f.read()
+    except OSError:
+        return None
+    if kernel not in TRAFFIC_BYTES_PER_AMP or ("sha256: " + kernel_sources_sha256()) not in text:
+        return None
+    return TRAFFIC_BYTES_PER_AMP[kernel] * amplitudes
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -415,7 +446,10 @@ def run_ours(args):
                        "ckpt_layers": args.ckpt if args.ckpt is not None else "ceil(sqrt(p))"},
             "roofline": {"bound": "hbm", "kernel": top["name"], "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
-                         "traffic": None},
+                         "traffic": _traffic_per_launch(top["name"], dim) if (n, p) == (N_QUBITS, P_LAYERS)
+                         else None,
+                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum at n=25, "
+                                           "scaled by amplitudes (profiles/hc_passes_qaoa25_dram.md)"},
             "step_roofline": {"algorithmic_bytes_per_step": step_bytes,
                               "GBps": step_bytes / (ms * 1e-3) / 1e9,
                               "frac": step_bytes / (ms * 1e-3) / 1e9 / peak},

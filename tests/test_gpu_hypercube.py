@@ -135,6 +135,54 @@ def test_tiled_forward_and_gradient_c64(qvs, n, p):
     assert rel_err_grad(dg, dt, rdg, rdt) < TOL_G
 
 
+# Mixer angles where the kernels shift t by pi/2 (|tan t| > 1) and carry the remaining all-bit flip
+# as a frame: every layer flipped, alternating, on the |tan t| = 1 boundary, exactly pi/2 (tangent
+# 0 after the shift), 0 and pi; odd and even n, two- and three-group schedules.
+FRAME_TS = {
+    "all_flip": [1.3, 1.9, 1.6, 1.45],
+    "alternate": [0.4, 1.7, 2.9, 1.2],
+    "boundary": [math.pi / 4, 3 * math.pi / 4, math.pi / 4 + 1e-9, 3 * math.pi / 4 - 1e-9],
+    "exact": [math.pi / 2, 0.0, math.pi, math.pi / 2],
+}
+
+
+@pytest.mark.parametrize("n", [13, 14, 21, 22])
+@pytest.mark.parametrize("pattern", sorted(FRAME_TS))
+def test_tiled_angle_frames_c64(qvs, n, pattern):
+    G = wl.gnp_graph(n, 0.5, wl.rng_for(67, n))
+    sim, _ = _sim_maxcut(qvs, n, G, qvs.QVS_C64, "f32")
+    ts = np.array(FRAME_TS[pattern])
+    gs = np.array([0.7, 2.3, 1.1, 0.2])
+    prob = orc.maxcut_problem(n, G.eu, G.ev, G.w, q_dtype=np.float32)
+    E = sim.evolve(gs, ts)
+    ref_psi = orc.evolve(prob, gs, ts)
+    assert rel_err_E(E, orc.expectation(ref_psi, prob.q)) < TOL_E
+    assert infidelity(sim.state(), ref_psi) < 1e-6
+    # the returned state carries the right global phase too (not only up to a phase)
+    assert np.max(np.abs(sim.state() - ref_psi)) < 5e-6 / math.sqrt(1 << n) * 64
+    E2, dg, dt = sim.gradient(gs, ts)
+    f, rdg, rdt = orc.gradient(prob, gs, ts)
+    assert rel_err_E(E2, f) < TOL_E
+    assert rel_err_grad(dg, dt, rdg, rdt) < TOL_G
+
+
+@pytest.mark.parametrize("pattern", ["all_flip", "alternate"])
+def test_tiled_angle_frames_c128_tight(qvs, pattern):
+    n = 15
+    G = wl.gnp_graph(n, 0.5, wl.rng_for(68, n))
+    sim, _ = _sim_maxcut(qvs, n, G, qvs.QVS_C128, "f64")
+    ts = np.array(FRAME_TS[pattern])
+    gs = np.array([0.7, 2.3, 1.1, 0.2])
+    prob = orc.maxcut_problem(n, G.eu, G.ev, G.w)
+    E = sim.evolve(gs, ts)
+    ref_psi = orc.evolve(prob, gs, ts)
+    assert np.max(np.abs(sim.state() - ref_psi)) < 1e-12
+    E2, dg, dt = sim.gradient(gs, ts)
+    f, rdg, rdt = orc.gradient(prob, gs, ts)
+    assert rel_err_E(E2, f) < 1e-11
+    assert rel_err_grad(dg, dt, rdg, rdt) < 1e-10
+
+
 @pytest.mark.parametrize("n", [14, 22])
 def test_tiled_c128_matches_oracle_tightly(qvs, n):
     G = wl.gnp_graph(n, 0.5, wl.rng_for(57, n))

@@ -186,13 +186,15 @@ __device__ __forceinline__ bool bit_on(int i, uint32_t mask) {
 }
 
 // W_a += T W_b, W_b -= T W_a on the register pairs of the rotated bits (T < 0: the inverse map up
-// to the real factor 1 + T^2)
+// to the real factor 1 + T^2). With a runtime mask every bit is rotated, the masked-out ones with
+// tangent 0 (the identity): a per-bit branch would cost register moves at every join.
 template <int L, int TH, class C, class T>
 __device__ __forceinline__ void rot_layout(C (&v)[R], uint32_t mask, T tn) {
-  const C tp = mk2<C, T>(tn, tn), tm = mk2<C, T>(-tn, -tn);
 #pragma unroll
   for (int i = 0; i < RB; ++i) {
-    if (bit_on<L, TH>(i, mask)) {
+    if (TH < 0 || bit_on<L, TH>(i, mask)) {
+      const T ti = (TH >= 0 || bit_on<L, TH>(i, mask)) ? tn : T(0);
+      const C tp = mk2<C, T>(ti, ti), tm = mk2<C, T>(-ti, -ti);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         if (!(r & (1 << i))) {
@@ -248,6 +250,23 @@ __device__ __forceinline__ void xchg(C (&v)[R], C* sm, int tid) {
   __syncthreads();
   sget<LT>(v, sm, tid);
   __syncthreads();
+}
+
+// ALT: transpose through buffer BUF of two (sm, sm + SM_SLOTS) with one barrier: a pass alternates
+// the buffers, so the barrier of the next transpose already orders this one's reads before the
+// transpose after it writes the same buffer again. Used where the CTA already holds two buffers
+// (the batched kernel); the per-pass kernels keep one buffer, since a second one costs them L1
+// capacity that their streaming loads need (F2 0.67 -> 0.86 ms at n=28 with two).
+template <int LF, int LT, int BUF, bool ALT, class C>
+__device__ __forceinline__ void xchg_alt(C (&v)[R], C* sm, int tid) {
+  if constexpr (ALT) {
+    C* b = sm + BUF * SM_SLOTS;
+    sput<LF>(v, b, tid);
+    __syncthreads();
+    sget<LT>(v, b, tid);
+  } else {
+    xchg<LF, LT>(v, sm, tid);
+  }
 }
 
 template <int L, class C>

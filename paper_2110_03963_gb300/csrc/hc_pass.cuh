@@ -217,7 +217,9 @@ __device__ __forceinline__ void block_store3(T a, T b, T c, double* part, int ra
 // TH: rotated tile bits are those >= TH (TH_RUNTIME: the runtime masks a.mask_bef / a.mask_aft).
 // TBF / TAF are the thresholds of the "before" / "after" rotations: both TH, except for TH_NONE
 // (single-tile schedules, whose passes have no "before" rotations and rotate every tile bit after).
-template <class T, int SHAPE, int TH>
+// ALT: the single-vector passes alternate two shared buffers (one barrier per transpose); the CTA
+// must hold 2 * SM_SLOTS elements.
+template <class T, int SHAPE, int TH, bool ALT = false>
 __device__ __forceinline__ void run_pass(const PassArgs<T>& a, uint32_t bid, uint32_t nblk,
                                          unsigned char* smem_raw) {
   using C = typename Cx<T>::t;
@@ -279,41 +281,43 @@ __device__ __forceinline__ void run_pass(const PassArgs<T>& a, uint32_t bid, uin
     qload<2>(qv, a.q, off2, a.tile, a.qx);
     phase2(v, T(1), a.rho_p);
     rot_layout<2, TAF>(v, a.mask_aft, a.ta);
-    xchg<2, 1>(v, sm, tid);
+    xchg_alt<2, 1, 0, ALT>(v, sm, tid);
     rot_layout<1, TAF>(v, a.mask_aft, a.ta);
-    xchg<1, 0>(v, sm, tid);
+    xchg_alt<1, 0, 1, ALT>(v, sm, tid);
     rot_layout<0, TAF>(v, a.mask_aft, a.ta);
     gstore<0>(v, a.psi_out, off0, a.tile);
   } else if constexpr (SHAPE == F1) {
     ld(I0{}, v, a.psi_in, off0);
     rot_layout<0, TBF>(v, a.mask_bef, a.tb);
-    xchg<0, 1>(v, sm, tid);
+    xchg_alt<0, 1, 0, ALT>(v, sm, tid);
     rot_layout<1, TBF>(v, a.mask_bef, a.tb);
     qload<2>(qv, a.q, off2, a.tile, a.qx);
-    xchg<1, 2>(v, sm, tid);
+    xchg_alt<1, 2, 1, ALT>(v, sm, tid);
     rot_layout<2, TBF>(v, a.mask_bef, a.tb);
     phase2(v, T(1), a.rho_p);
     rot_layout<2, TAF>(v, a.mask_aft, a.ta);
-    xchg<2, 1>(v, sm, tid);
+    xchg_alt<2, 1, 0, ALT>(v, sm, tid);
     rot_layout<1, TAF>(v, a.mask_aft, a.ta);
-    xchg<1, 0>(v, sm, tid);
+    xchg_alt<1, 0, 1, ALT>(v, sm, tid);
     rot_layout<0, TAF>(v, a.mask_aft, a.ta);
     gstore<0>(v, a.psi_out, off0, a.tile);
   } else if constexpr (SHAPE == F2) {
     ld(I0{}, v, a.psi_in, off0);
     rot_layout<0, TBF>(v, a.mask_bef, a.tb);
-    xchg<0, 1>(v, sm, tid);
+    xchg_alt<0, 1, 0, ALT>(v, sm, tid);
     rot_layout<1, TBF>(v, a.mask_bef, a.tb);
-    xchg<1, 2>(v, sm, tid);
+    xchg_alt<1, 2, 1, ALT>(v, sm, tid);
     rot_layout<2, TBF>(v, a.mask_bef, a.tb);
     gstore<2>(v, a.psi_out, off2, a.tile);
   } else if constexpr (SHAPE == FE || SHAPE == FV) {
     ld(I0{}, v, a.psi_in, off0);
     rot_layout<0, TBF>(v, a.mask_bef, a.tb);
-    xchg<0, 1>(v, sm, tid);
+    if constexpr (SHAPE == FV) xchg_alt<0, 1, 0, ALT>(v, sm, tid);
+    else xchg<0, 1>(v, sm, tid);   // FE's second half writes both buffers: keep the trailing barrier
     rot_layout<1, TBF>(v, a.mask_bef, a.tb);
     qload<2>(qv, a.q, off2, a.tile, a.qx);
-    xchg<1, 2>(v, sm, tid);
+    if constexpr (SHAPE == FV) xchg_alt<1, 2, 1, ALT>(v, sm, tid);
+    else xchg<1, 2>(v, sm, tid);
     rot_layout<2, TBF>(v, a.mask_bef, a.tb);
     T e = T(0);
 #pragma unroll

@@ -608,13 +608,13 @@ __device__ __forceinline__ void bpass_info(const BInst& I, int j, int& type, int
 __device__ __forceinline__ void run_shape(int shape, const PassArgs<float>& a, uint32_t t, uint32_t nt,
                                           unsigned char* sm) {
   switch (shape) {
-    case F0: run_pass<float, F0, TH_RUNTIME>(a, t, nt, sm); break;
-    case F1: run_pass<float, F1, TH_RUNTIME>(a, t, nt, sm); break;
-    case F2: run_pass<float, F2, TH_RUNTIME>(a, t, nt, sm); break;
-    case FE: run_pass<float, FE, TH_RUNTIME>(a, t, nt, sm); break;
-    case R1: run_pass<float, R1, TH_RUNTIME>(a, t, nt, sm); break;
-    case R2: run_pass<float, R2, TH_RUNTIME>(a, t, nt, sm); break;
-    case R0: run_pass<float, R0, TH_RUNTIME>(a, t, nt, sm); break;
+    case F0: run_pass<float, F0, TH_RUNTIME, true>(a, t, nt, sm); break;
+    case F1: run_pass<float, F1, TH_RUNTIME, true>(a, t, nt, sm); break;
+    case F2: run_pass<float, F2, TH_RUNTIME, true>(a, t, nt, sm); break;
+    case FE: run_pass<float, FE, TH_RUNTIME, true>(a, t, nt, sm); break;
+    case R1: run_pass<float, R1, TH_RUNTIME, true>(a, t, nt, sm); break;
+    case R2: run_pass<float, R2, TH_RUNTIME, true>(a, t, nt, sm); break;
+    case R0: run_pass<float, R0, TH_RUNTIME, true>(a, t, nt, sm); break;
   }
 }
 

@@ -383,7 +383,7 @@ __device__ __forceinline__ void run_pass(const PassArgs<T>& a, uint32_t bid, uin
 }
 
 template <class T, int SHAPE, int TH>
-__global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 1 : ((SHAPE == FE || SHAPE == R1 || SHAPE == R2 || SHAPE == R0) ? 2 : 3))
+__global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 1 : ((SHAPE == FE || SHAPE == R1 || SHAPE == R2 || SHAPE == R0) ? 2 : 4))
 pass_kernel(const __grid_constant__ PassArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   run_pass<T, SHAPE, TH>(a, blockIdx.x, gridDim.x, smem_raw);

@@ -88,14 +88,16 @@ __global__ void __launch_bounds__(NT, 1) col_kernel(const __grid_constant__ Circ
   constexpr int CB = G::dstart(0);
   const int tid = threadIdx.x;
   const uint32_t blk = blockIdx.x;
-  const uint32_t N = 1u << a.n;
   // global index of tile index j
   auto gidx = [&](int j) -> uint32_t {
     return (uint32_t)(j & ((1 << CB) - 1)) | (blk << CB) | ((uint32_t)(j >> CB) << TB);
   };
   // four-step twiddle omega_N^(+-j_low * k_col) on layout 0 (column-spectral positions). The
   // position-to-frequency map is a bit permutation, so it splits into a per-thread part and a
-  // compile-time per-register part.
+  // compile-time per-register part. The exponent is exact in 32-bit integers; shifted to the top of
+  // a 32-bit word it is the turn e / N as a fixed-point fraction whose signed value is already
+  // reduced to [-1/2, 1/2), so one hardware sine/cosine of its float conversion (relative error
+  // 2^-24 of an angle of at most pi) replaces four table reads and three complex products.
   auto gtw = [&](float2(&v)[R], bool conj) {
     const int jt = G::template jthr<0>(tid_fresh());
     const uint32_t jlt = (uint32_t)(jt & ((1 << CB) - 1)) | (blk << CB);
@@ -105,8 +107,11 @@ __global__ void __launch_bounds__(NT, 1) col_kernel(const __grid_constant__ Circ
       constexpr int jr = G::jreg(0, r);
       constexpr uint32_t jlr = (uint32_t)(jr & ((1 << CB) - 1));
       constexpr uint32_t kr = (uint32_t)G::freq(jr >> CB);
-      const uint32_t e = ((jlt | jlr) * (kt | kr)) & (N - 1);
-      const float2 w = twN(ts, e);
+      // e / N as a 32-bit fixed-point fraction; its signed value is the reduced turn in [-1/2, 1/2)
+      const int32_t es = (int32_t)(((jlt | jlr) * (kt | kr)) << (32 - a.n));
+      float sn, cs;
+      __sincosf((float)es * 1.46291807926715968e-09f, &sn, &cs);   // 2 pi / 2^32
+      const float2 w = make_float2(cs, -sn);
       v[r] = conj ? cmulc(v[r], w) : cmul(v[r], w);
     });
   };

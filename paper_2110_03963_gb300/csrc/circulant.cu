@@ -70,8 +70,7 @@ int circ_set_mixer(qvs_ctx* h, const qvs_mixer_desc* d) {
     if (d->offsets[i] <= 0 || d->offsets[i] >= N) return QVS_EINVAL;
     if (d->offset_weights && !isfinite(d->offset_weights[i])) return QVS_EINVAL;
   }
-  // twiddle sub-tables (fp64, rounded once): A14[k] = w14^(128k), B14[k] = w14^k,
-  // C0[k] = wN^k, C1[k] = wN^(128k), C2[k] = wN^(2^14 k), C3[k] = wN^(2^21 k), w_M = e^{-2 pi i / M}
+  // twiddle sub-tables (fp64, rounded once): A14[k] = w14^(128k), B14[k] = w14^k, w_M = e^{-2 pi i / M}
   std::vector<float2> tab(TW_SLOTS);
   const double two_pi = 6.283185307179586476925286766559;
   auto w = [&](int64_t e, int64_t M) {
@@ -81,10 +80,6 @@ int circ_set_mixer(qvs_ctx* h, const qvs_mixer_desc* d) {
   for (int k = 0; k < 128; ++k) {
     tab[TW_A14 + k] = w(128 * (int64_t)k, TILE);
     tab[TW_B14 + k] = w(k, TILE);
-    tab[TW_C0 + k] = w(k, N);
-    tab[TW_C1 + k] = w((int64_t)k << 7, N);
-    tab[TW_C2 + k] = w((int64_t)k << 14, N);
-    tab[TW_C3 + k] = w((int64_t)k << 21, N);
   }
   QVS_TRY(h->circ.tab.ensure(sizeof(float2) * tab.size()));
   QVS_CUDA_TRY(cudaMemcpyAsync(h->circ.tab.ptr, tab.data(), sizeof(float2) * tab.size(),

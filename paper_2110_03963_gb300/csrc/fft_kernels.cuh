@@ -210,18 +210,14 @@ __device__ __forceinline__ void xchg(float2 (&v)[R], float2* sm, int tid) {
   __syncthreads();
 }
 
-// Shared-memory twiddle sub-tables (built once per CTA from a 768-entry global table computed in
-// fp64 and rounded once): e^{-2 pi i e / 2^14} = A14[e >> 7] * B14[e & 127], and for the
-// four-step twiddle of an N-point transform, e^{-2 pi i e / N} = C0[e & 127] * C1[(e >> 7) & 127]
-// * C2[(e >> 14) & 127] * C3[e >> 21] (N <= 2^28).
-constexpr int TW_A14 = 0, TW_B14 = 128, TW_C0 = 256, TW_C1 = 384, TW_C2 = 512, TW_C3 = 640, TW_SLOTS = 768;
+// Shared-memory twiddle sub-tables (built once per CTA from a 256-entry global table computed in
+// fp64 and rounded once): e^{-2 pi i e / 2^14} = A14[e >> 7] * B14[e & 127]. The four-step twiddle
+// of the N-point transform is computed directly (one hardware sine/cosine of the exactly reduced
+// turn, in the column pass).
+constexpr int TW_A14 = 0, TW_B14 = 128, TW_SLOTS = 256;
 
 __device__ __forceinline__ float2 tw14(const float2* __restrict__ ts, int e) {
   return cmul(ts[TW_A14 + (e >> 7)], ts[TW_B14 + (e & 127)]);
-}
-__device__ __forceinline__ float2 twN(const float2* __restrict__ ts, uint32_t e) {
-  return cmul(cmul(ts[TW_C0 + (e & 127)], ts[TW_C1 + ((e >> 7) & 127)]),
-              cmul(ts[TW_C2 + ((e >> 14) & 127)], ts[TW_C3 + (e >> 21)]));
 }
 
 // Twiddle between digit 3 and digit 2 (in step layout 2): omega_L^((j1 + 2^D1 j2) * k3), and

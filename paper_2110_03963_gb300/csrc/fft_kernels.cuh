@@ -126,6 +126,10 @@ __device__ __forceinline__ int tid_fresh() {
 __host__ __device__ __forceinline__ constexpr int spos(int j) { return j + (j >> 4) + (j >> 8); }
 constexpr int SM_SLOTS = TILE + (TILE >> 4) + (TILE >> 8);
 
+// complex add / subtract as one paired-float instruction each (same rounding as two scalar adds)
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
@@ -147,8 +151,8 @@ __device__ __forceinline__ void small_dft(float2 (&v)[R]) {
       if constexpr (!(u & h)) {
         constexpr int m = (u & (h - 1)) << (4 - s);
         const float2 a = v[r], b = v[r | h];
-        v[r] = make_float2(a.x + b.x, a.y + b.y);
-        const float2 t = make_float2(a.x - b.x, a.y - b.y);
+        v[r] = cadd(a, b);
+        const float2 t = csub(a, b);
         if constexpr (m == 0) {
           v[r | h] = t;
         } else if constexpr (m == 8) {
@@ -184,8 +188,8 @@ __device__ __forceinline__ void small_idft(float2 (&v)[R]) {
           constexpr float wc = kCos32[m], ws = kSin32[m];
           t = cmul(b, make_float2(wc, ws));
         }
-        v[r] = make_float2(a.x + t.x, a.y + t.y);
-        v[r | h] = make_float2(a.x - t.x, a.y - t.y);
+        v[r] = cadd(a, t);
+        v[r | h] = csub(a, t);
       }
     });
   });

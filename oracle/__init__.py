@@ -209,6 +209,14 @@ def mix_xy_ring(psi: np.ndarray, n: int, states: np.ndarray, t: float) -> np.nda
     return v
 
 
+def mix_dense(psi: np.ndarray, W: np.ndarray, t: float) -> np.ndarray:
+    """Sec. 2.1 / Sec. 3: exp(-i t W) psi for a real symmetric W given densely, from the definition
+    of the matrix exponential of a symmetric matrix: W = V diag(w) V^T, exp(-i t W) = V diag(exp(-i t w)) V^T
+    (numpy eigh as the library step)."""
+    w, V = np.linalg.eigh(np.asarray(W, dtype=np.float64))
+    return V @ (np.exp(-1j * t * w) * (V.T @ np.asarray(psi, dtype=np.complex128)))
+
+
 # ============================================================== problems and the ansatz
 
 
@@ -216,11 +224,12 @@ def mix_xy_ring(psi: np.ndarray, n: int, states: np.ndarray, t: float) -> np.nda
 class Problem:
     """One QVA instance: quality vector q (fp64), a mixer, and an initial state (None = uniform)."""
     q: np.ndarray
-    mixer: str                     # "hypercube" | "circulant" | "xy_ring"
+    mixer: str                     # "hypercube" | "circulant" | "xy_ring" | "dense"
     n: int = 0                     # qubits (hypercube, xy_ring)
     lam: np.ndarray | None = None  # circulant eigenvalues
     states: np.ndarray | None = None   # xy_ring subspace basis
     psi0: np.ndarray | None = None
+    W: np.ndarray | None = None        # dense real symmetric mixer matrix
 
     @property
     def dim(self) -> int:
@@ -239,6 +248,8 @@ class Problem:
             return mix_circulant(psi, self.lam, t)
         if self.mixer == "xy_ring":
             return mix_xy_ring(psi, self.n, self.states, t)
+        if self.mixer == "dense":
+            return mix_dense(psi, self.W, t)
         raise ValueError(self.mixer)
 
     def apply_W(self, psi: np.ndarray) -> np.ndarray:
@@ -248,6 +259,8 @@ class Problem:
             return apply_circulant_W(psi, self.lam)
         if self.mixer == "xy_ring":
             return xy_ring_apply(psi, self.n, self.states)
+        if self.mixer == "dense":
+            return np.asarray(self.W, dtype=np.float64) @ psi
         raise ValueError(self.mixer)
 
 

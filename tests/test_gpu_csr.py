@@ -105,6 +105,36 @@ def test_givens_pair_exact(qvs):
         assert np.max(np.abs(sim.state() - ref)) < 2e-6
 
 
+@pytest.mark.parametrize("dim,density,shift", [(600, 0.02, 0.0), (1500, 0.008, 2.5)])
+def test_general_csr_with_values_vs_oracle(qvs, dim, density, shift):
+    """A random real symmetric CSR matrix with explicit fp32 values (and a shifted diagonal, so
+    the spectrum is off-centre): the library's Lanczos interval, the Chebyshev series and the
+    adjoint against the oracle's dense mixer."""
+    sp = pytest.importorskip("scipy.sparse")
+    rng = wl.rng_for(85, dim)
+    M = sp.random(dim, dim, density=density, random_state=np.random.RandomState(dim), format="csr")
+    A = (M + M.T).tocsr()
+    if shift:
+        A = (A + sp.diags(shift + rng.standard_normal(dim))).tocsr()
+    A.sort_indices()
+    vals = A.data.astype(np.float32)
+    W = sp.csr_matrix((vals.astype(np.float64), A.indices, A.indptr), shape=(dim, dim)).toarray()
+    q = rng.uniform(0.0, 3.0, dim).astype(np.float32)
+    sim = qvs.Simulator(dim, qvs.QVS_C64)
+    sim.set_quality(q)
+    sim.set_mixer(qvs.QVS_MIX_CSR, qvs.csr_desc(A.indptr.astype(np.int64), A.indices.astype(np.int32), vals, 0.0))
+    prob = orc.Problem(q=q.astype(np.float64), mixer="dense", W=W)
+    gs, ts = [0.5, 1.3, 0.2], [0.7, 0.4, 1.1]
+    E = sim.evolve(gs, ts)
+    ref_psi = orc.evolve(prob, gs, ts)
+    assert rel_err_E(E, orc.expectation(ref_psi, prob.q)) < TOL_E
+    assert infidelity(sim.state(), ref_psi) < 1e-6
+    E2, dg, dt = sim.gradient(gs, ts)
+    f, rdg, rdt = orc.gradient(prob, gs, ts)
+    assert rel_err_E(E2, f) < TOL_E
+    assert rel_err_grad(dg, dt, rdg, rdt) < TOL_G
+
+
 # ------------------------------------------------------------------ full size: n=24, weight 12, p=4
 
 @pytest.fixture(scope="module")

@@ -141,6 +141,34 @@ def test_p4_xy_ring_vs_expm(n, k):
         assert np.max(np.abs(orc.mix_xy_ring(psi, n, states, t) - ref)) < 1e-11
 
 
+def test_dense_mixer_vs_independent_forms():
+    """The dense symmetric mixer (eigendecomposition) against methods it shares nothing with: the
+    XY-ring Taylor series on a Hamming-weight subspace, the 2x2 Givens closed form, and unitarity
+    plus exact reversal on a random matrix with a nonzero diagonal."""
+    n, k = 6, 3
+    states = orc.subspace_states(n, k)
+    dim = states.shape[0]
+    W = np.zeros((dim, dim))
+    for c in range(dim):
+        e = np.zeros(dim)
+        e[c] = 1.0
+        W[:, c] = orc.xy_ring_apply(e, n, states).real
+    rng = np.random.default_rng(14)
+    psi = rng.standard_normal(dim) + 1j * rng.standard_normal(dim)
+    for t in [0.3, 1.7]:
+        assert np.max(np.abs(orc.mix_dense(psi, W, t) - orc.mix_xy_ring(psi, n, states, t))) < 1e-11
+    G = np.array([[0.0, 2.0], [2.0, 0.0]])
+    v = np.array([0.6, 0.8j])
+    for t in [0.4, 2.2]:
+        assert np.max(np.abs(orc.mix_dense(v, G, t) - cf.givens_xy(t) @ v)) < 1e-14
+    A = rng.standard_normal((40, 40))
+    A = A + A.T + np.diag(rng.standard_normal(40) * 3)
+    x = rng.standard_normal(40) + 1j * rng.standard_normal(40)
+    y = orc.mix_dense(x, A, 0.9)
+    assert abs(np.linalg.norm(y) - np.linalg.norm(x)) < 1e-12
+    assert np.max(np.abs(orc.mix_dense(y, A, -0.9) - x)) < 1e-12
+
+
 def test_p4_full_ansatz_vs_dense_qaoa():
     """Whole p=3 ansatz against dense exponentials of W and diag(q) (n=7)."""
     n = 7
@@ -243,10 +271,15 @@ def test_p9_periodicities_and_symmetry():
 
 # ------------------------------------------------------------------ P10: gradients
 
-@pytest.mark.parametrize("kind", ["hypercube", "circulant", "xy_ring"])
+@pytest.mark.parametrize("kind", ["hypercube", "circulant", "xy_ring", "dense"])
 def test_p10_adjoint_vs_richardson_fd(kind):
     if kind == "hypercube":
         prob = _qaoa_small(7, 1)
+    elif kind == "dense":
+        rng = np.random.default_rng(93)
+        A = rng.standard_normal((30, 30))
+        A = 0.5 * (A + A.T) + np.diag(rng.standard_normal(30))
+        prob = orc.Problem(q=rng.uniform(0, 3, 30), mixer="dense", W=A)
     elif kind == "circulant":
         prob = orc.qwoa_problem(7, wl.item_weights(7, wl.rng_for(92, 0)), wl.circulant_offsets_pow2(7))
     else:

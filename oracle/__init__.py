@@ -209,6 +209,82 @@ def mix_xy_ring(psi: np.ndarray, n: int, states: np.ndarray, t: float) -> np.nda
     return v
 
 
+# ============================================================== QAOAz parity-ring mixer (Sec. 2.4.1)
+
+
+def parity_ring_rounds(n: int):
+    """Sec. 2.4.1, Eqs. for B_odd, B_even, B_last and U_parity: the qubit pairs of the three
+    factors, for the two rings of an n-qubit register (one ring on the even qubits 0, 2, ..., one on
+    the odd qubits 1, 3, ...). On a ring of N qubits with 1-indexed positions k:
+      B_odd  couples (k, k+1) for odd k < N,
+      B_even couples (k, k+1) for even k < N, and the closing pair (N, 1) when N is even,
+      B_last couples (N, 1) when N is odd (identity when N is even).
+    Returns [pairs of B_odd, pairs of B_even, pairs of B_last] as global qubit pairs; the pairs of
+    one factor are disjoint, and the two rings share no qubit."""
+    rounds = [[], [], []]
+    for ring in ([q for q in range(0, n, 2)], [q for q in range(1, n, 2)]):
+        N = len(ring)
+        pos = lambda k: ring[k - 1]   # 1-indexed position on the ring -> qubit
+        for k in range(1, N):
+            rounds[0 if k % 2 == 1 else 1].append((pos(k), pos(k + 1)))
+        if N >= 2:
+            rounds[1 if N % 2 == 0 else 2].append((pos(N), pos(1)))
+    return rounds
+
+
+def xy_pairs_apply(psi: np.ndarray, n: int, pairs) -> np.ndarray:
+    """B psi for B = sum over the pairs (u, v) of X_u X_v + Y_u Y_v: (XX+YY)|01> = 2|10>,
+    (XX+YY)|10> = 2|01>, zero on |00> and |11> (qubit u = bit n-1-u)."""
+    N = psi.shape[0]
+    idx = np.arange(N, dtype=np.int64)
+    out = np.zeros_like(psi, dtype=np.complex128)
+    for u, v in pairs:
+        bu, bv = n - 1 - u, n - 1 - v
+        differ = (((idx >> bu) ^ (idx >> bv)) & 1) == 1
+        out[differ] += 2.0 * psi[idx[differ] ^ ((1 << bu) | (1 << bv))]
+    return out
+
+
+def xy_pairs_exp(psi: np.ndarray, n: int, pairs, t: float) -> np.ndarray:
+    """exp(-i t B) psi for disjoint pairs: one Givens rotation per pair on its |01>, |10>
+    amplitudes, [[cos 2t, -i sin 2t], [-i sin 2t, cos 2t]] (exp(-i t (XX+YY)) on that plane)."""
+    N = psi.shape[0]
+    idx = np.arange(N, dtype=np.int64)
+    out = np.asarray(psi, dtype=np.complex128).copy()
+    c, s = math.cos(2.0 * t), math.sin(2.0 * t)
+    for u, v in pairs:
+        bu, bv = n - 1 - u, n - 1 - v
+        lo = idx[(((idx >> bu) & 1) == 0) & (((idx >> bv) & 1) == 1)]
+        hi = lo ^ ((1 << bu) | (1 << bv))
+        a, b = out[lo].copy(), out[hi].copy()
+        out[lo] = c * a - 1j * s * b
+        out[hi] = c * b - 1j * s * a
+    return out
+
+
+def mix_parity(psi: np.ndarray, n: int, t: float) -> np.ndarray:
+    """U_parity(t) = exp(-i t B_last) exp(-i t B_even) exp(-i t B_odd) on both rings (the rings act
+    on disjoint qubits and commute); one t for every factor."""
+    for pairs in parity_ring_rounds(n):
+        psi = xy_pairs_exp(psi, n, pairs, t)
+    return psi
+
+
+def parity_state(n: int, A: int) -> np.ndarray:
+    """Sec. 6.2 QAOAz initial state: |01>^{(x)A} ((|00> + |11>)/sqrt 2)^{(x)(M-A)}, M = n/2 assets,
+    one pair of qubits (2a, 2a+1) per asset in qubit order (qubit u = bit n-1-u)."""
+    M = n // 2
+    state = np.array([1.0 + 0j])
+    for a in range(M):
+        pair = np.zeros(4, dtype=np.complex128)   # index = 2 * x_{2a} + x_{2a+1}
+        if a < A:
+            pair[0b01] = 1.0
+        else:
+            pair[0b00] = pair[0b11] = 1.0 / math.sqrt(2.0)
+        state = np.kron(state, pair)
+    return state
+
+
 def mix_dense(psi: np.ndarray, W: np.ndarray, t: float) -> np.ndarray:
     """Sec. 2.1 / Sec. 3: exp(-i t W) psi for a real symmetric W given densely, from the definition
     of the matrix exponential of a symmetric matrix: W = V diag(w) V^T, exp(-i t W) = V diag(exp(-i t w)) V^T
@@ -224,7 +300,7 @@ def mix_dense(psi: np.ndarray, W: np.ndarray, t: float) -> np.ndarray:
 class Problem:
     """One QVA instance: quality vector q (fp64), a mixer, and an initial state (None = uniform)."""
     q: np.ndarray
-    mixer: str                     # "hypercube" | "circulant" | "xy_ring" | "dense"
+    mixer: str                     # "hypercube" | "circulant" | "xy_ring" | "dense" | "parity"
     n: int = 0                     # qubits (hypercube, xy_ring)
     lam: np.ndarray | None = None  # circulant eigenvalues
     states: np.ndarray | None = None   # xy_ring subspace basis
@@ -250,6 +326,8 @@ class Problem:
             return mix_xy_ring(psi, self.n, self.states, t)
         if self.mixer == "dense":
             return mix_dense(psi, self.W, t)
+        if self.mixer == "parity":
+            return mix_parity(psi, self.n, t)
         raise ValueError(self.mixer)
 
     def apply_W(self, psi: np.ndarray) -> np.ndarray:
@@ -291,6 +369,8 @@ def gradient(prob: Problem, gammas, ts):
       df/dgamma_k = 2 Im <M_k^dag lambda_k | Q phi_k>
     Returns (f, dgamma[p], dt[p]).
     """
+    if prob.mixer == "parity":
+        return _gradient_factored(prob, gammas, ts)
     p = len(gammas)
     psi = prob.initial_state()
     phis, psis = [], []
@@ -308,6 +388,38 @@ def gradient(prob: Problem, gammas, ts):
         lam = prob.mix(lam, -float(ts[k]))                # M_k^dag
         dg[k] = 2.0 * np.vdot(lam, prob.q * phis[k]).imag
         lam = phase(lam, prob.q, -float(gammas[k]))       # P_k^dag
+    return f, dg, dt
+
+
+def _gradient_factored(prob: Problem, gammas, ts):
+    """Adjoint gradient for a mixer that is a product of exponentials sharing one t,
+    M(t) = exp(-i t B_F) ... exp(-i t B_1) (the parity mixer). Every factor's input state is stored;
+    with lambda moved back through the factors,
+      df/dt_k     = sum_f 2 Im <lambda_{k,f} | B_f psi_{k,f}>   (both at factor f's output)
+      df/dgamma_k = 2 Im <M_k^dag lambda_k | Q phi_k>."""
+    p = len(gammas)
+    rounds = parity_ring_rounds(prob.n)
+    psi = prob.initial_state()
+    phis, outs = [], []   # outs[k][f] = state after factor f of layer k
+    for k in range(p):
+        phi = phase(psi, prob.q, float(gammas[k]))
+        phis.append(phi)
+        cur, lst = phi, []
+        for pairs in rounds:
+            cur = xy_pairs_exp(cur, prob.n, pairs, float(ts[k]))
+            lst.append(cur)
+        outs.append(lst)
+        psi = cur
+    f = expectation(psi, prob.q)
+    lam = prob.q * psi
+    dg = np.zeros(p)
+    dt = np.zeros(p)
+    for k in range(p - 1, -1, -1):
+        for fi in range(len(rounds) - 1, -1, -1):
+            dt[k] += 2.0 * np.vdot(lam, xy_pairs_apply(outs[k][fi], prob.n, rounds[fi])).imag
+            lam = xy_pairs_exp(lam, prob.n, rounds[fi], -float(ts[k]))
+        dg[k] = 2.0 * np.vdot(lam, prob.q * phis[k]).imag
+        lam = phase(lam, prob.q, -float(gammas[k]))
     return f, dg, dt
 
 
@@ -353,6 +465,15 @@ def qwoa_problem(log2n: int, weights, offsets, q_dtype=None) -> Problem:
         q = q.astype(q_dtype).astype(np.float64)
     lam = circulant_eigenvalues(circulant_first_row_from_offsets(N, offsets))
     return Problem(q=q, mixer="circulant", lam=lam)
+
+
+def qaoaz_parity_problem(n: int, A: int, returns, cov, omega: float, q_dtype=None) -> Problem:
+    """QAOAz with the paper's parity-ring mixer on the full 2^n register, portfolio qualities of
+    every basis state, and the parity initial state with constraint value A."""
+    q = portfolio_quality(n, np.arange(1 << n, dtype=np.int64), returns, cov, omega)
+    if q_dtype is not None:
+        q = q.astype(q_dtype).astype(np.float64)
+    return Problem(q=q, mixer="parity", n=n, psi0=parity_state(n, A))
 
 
 def qaoaz_problem(n: int, k: int, returns, cov, omega: float, q_dtype=None) -> Problem:

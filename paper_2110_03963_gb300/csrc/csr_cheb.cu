@@ -1,7 +1,7 @@
 // QAOAz sparse-mixer path (Sec. 2.4.1, Sec. 3): exp(-i t W) v for a real symmetric CSR matrix W
 // by a Chebyshev expansion,
 //     exp(-i t W) v = e^{-i t a} sum_m (2 - delta_m0) (-i)^m J_m(b t) T_m(W~) v,  W~ = (W - a) / b,
-// with [a - b, a + b] enclosing the spectrum (Gershgorin when no bounds are given). The series is
+// with [a - b, a + b] enclosing the spectrum (estimated by Lanczos when no bounds are given). The series is
 // cut at the first K whose tail bound sum_{m > K} 2 |J_m(b t)| falls below the tolerance (the
 // truncation error in the 2-norm is at most that bound since |T_m| <= 1 on [-1, 1]). Coefficients
 // are computed in fp64 on the host; each term is one fused kernel: a CSR SpMV of T_m (one lane per
@@ -661,8 +661,8 @@ int csr_set_mixer(qvs_ctx* h, const qvs_mixer_desc* d) {
   C.nnz = nnz;
   C.tol = d->cheb_tol > 0 ? d->cheb_tol : 1e-7;
   if (d->spec_lo == 0.0 && d->spec_hi == 0.0) {
-    // Gershgorin: every eigenvalue of a matrix with zero diagonal lies within the largest
-    // absolute row sum of zero
+    // Gershgorin: every eigenvalue lies within the largest absolute row sum of zero (diagonal
+    // included); the Lanczos estimate below is capped by it
     unsigned int* bits = nullptr;
     QVS_TRY(h->res.ensure(sizeof(double) * 8));
     bits = reinterpret_cast<unsigned int*>(h->res.ptr);

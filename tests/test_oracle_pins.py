@@ -269,12 +269,94 @@ def test_p9_periodicities_and_symmetry():
     assert orc.objective(pc, [0.5], [0.3 + 2 * math.pi / N]) == pytest.approx(fc, abs=1e-11)
 
 
+# ------------------------------------------------------------------ QAOAz parity-ring mixer (Sec. 2.4.1)
+
+def _xy_dense(n, pairs):
+    B = np.zeros((1 << n, 1 << n), dtype=complex)
+    for u, v in pairs:
+        B += _dense_pauli(n, {u: "X", v: "X"}) + _dense_pauli(n, {u: "Y", v: "Y"})
+    return B
+
+
+@pytest.mark.parametrize("n", [6, 8])
+def test_parity_mixer_vs_dense_factors(n):
+    """Each factor against the dense exponential of its Pauli sum, the whole U_parity against the
+    product in the printed order, and the order itself (the factors do not commute)."""
+    rounds = orc.parity_ring_rounds(n)
+    for pairs in rounds:   # pairs of one factor are disjoint; the two rings share no qubit
+        qs = [q for pr in pairs for q in pr]
+        assert len(qs) == len(set(qs))
+    rng = np.random.default_rng(15)
+    psi = rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)
+    Bs = [_xy_dense(n, pairs) for pairs in rounds]
+    for t in [0.35, 1.9]:
+        U = np.eye(1 << n)
+        for B, pairs in zip(Bs, rounds):
+            assert np.max(np.abs(orc.xy_pairs_apply(psi, n, pairs) - B @ psi)) < 1e-12
+            E = scipy.linalg.expm(-1j * t * B)
+            assert np.max(np.abs(orc.xy_pairs_exp(psi, n, pairs, t) - E @ psi)) < 1e-12
+            U = E @ U
+        assert np.max(np.abs(orc.mix_parity(psi, n, t) - U @ psi)) < 1e-12
+        Urev = np.eye(1 << n)
+        for B in reversed(Bs):
+            Urev = scipy.linalg.expm(-1j * t * B) @ Urev
+        assert np.max(np.abs(Urev @ psi - U @ psi)) > 1e-3
+
+
+def test_parity_mixer_ring_geometry_and_two_site_ring():
+    """Rings of 3 close through B_last, rings of 4 through B_even (n=6, 8); a ring of 2 gets its
+    one edge twice (B_odd and the closing pair of B_even), i.e. a Givens rotation by 2t twice."""
+    r6 = orc.parity_ring_rounds(6)
+    assert r6 == [[(0, 2), (1, 3)], [(2, 4), (3, 5)], [(4, 0), (5, 1)]]
+    r8 = orc.parity_ring_rounds(8)
+    assert sorted(r8[1]) == sorted([(2, 4), (6, 0), (3, 5), (7, 1)]) and r8[2] == []
+    psi = np.zeros(16, dtype=complex)
+    psi[0b0001] = 0.6            # qubit 3 set (ring of qubits 1, 3)
+    psi[0b1000] = 0.8j           # qubit 0 set (ring of qubits 0, 2)
+    for t in [0.2, 0.9]:
+        out = orc.mix_parity(psi, 4, t)
+        G = cf.givens_xy(2 * t)  # exp(-it(XX+YY)) applied twice = rotation by 4t on |01>,|10>
+        ref = np.zeros(16, dtype=complex)
+        ref[[0b0100, 0b0001]] = G @ np.array([0.0, 0.6])      # qubits (1, 3): |10> <-> |01>
+        ref[[0b1000, 0b0010]] = G @ np.array([0.8j, 0.0])     # qubits (0, 2)
+        assert np.max(np.abs(out - ref)) < 1e-14
+
+
+def test_parity_state_and_conservation():
+    """The parity state is normalised and supported on weight(odd qubits) - weight(even qubits) = A;
+    the mixer conserves each ring's Hamming weight (Sec. 2.4.1: amplitude stays in the subspace)."""
+    n = 8
+    odd_mask = sum(1 << (n - 1 - q) for q in range(1, n, 2))
+    even_mask = sum(1 << (n - 1 - q) for q in range(0, n, 2))
+    idx = np.arange(1 << n)
+    w_odd = np.array([bin(i & odd_mask).count("1") for i in idx])
+    w_even = np.array([bin(i & even_mask).count("1") for i in idx])
+    for A in [0, 1, 2, 4]:
+        s = orc.parity_state(n, A)
+        assert abs(np.vdot(s, s) - 1.0) < 1e-14
+        assert np.all(np.abs(s[(w_odd - w_even) != A]) == 0)
+        # the first A assets are |01>: qubit 2a = 0, qubit 2a+1 = 1
+        for a in range(A):
+            sup = idx[np.abs(s) > 0]
+            assert np.all(((sup >> (n - 1 - 2 * a)) & 1) == 0) and np.all(((sup >> (n - 2 - 2 * a)) & 1) == 1)
+    rng = np.random.default_rng(16)
+    psi = rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)
+    out = orc.mix_parity(psi, n, 1.1)
+    for wo in range(5):
+        for we in range(5):
+            sel = (w_odd == wo) & (w_even == we)
+            assert abs(np.sum(np.abs(out[sel]) ** 2) - np.sum(np.abs(psi[sel]) ** 2)) < 1e-10
+
+
 # ------------------------------------------------------------------ P10: gradients
 
-@pytest.mark.parametrize("kind", ["hypercube", "circulant", "xy_ring", "dense"])
+@pytest.mark.parametrize("kind", ["hypercube", "circulant", "xy_ring", "dense", "parity"])
 def test_p10_adjoint_vs_richardson_fd(kind):
     if kind == "hypercube":
         prob = _qaoa_small(7, 1)
+    elif kind == "parity":
+        P = wl.portfolio(4, wl.rng_for(94, 0))
+        prob = orc.qaoaz_parity_problem(8, 2, P.returns, P.cov, P.omega)
     elif kind == "dense":
         rng = np.random.default_rng(93)
         A = rng.standard_normal((30, 30))

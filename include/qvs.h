@@ -54,7 +54,7 @@ enum { QVS_C64 = 1, QVS_C128 = 2 };
 /* element type of quality vectors */
 enum { QVS_I32 = 1, QVS_F32 = 2, QVS_F64 = 3 };
 /* mixer kinds (paper Sec. 3: sparse, circulant, and the QAOA hypercube) */
-enum { QVS_MIX_HYPERCUBE = 1, QVS_MIX_CIRCULANT = 2, QVS_MIX_CSR = 3 };
+enum { QVS_MIX_HYPERCUBE = 1, QVS_MIX_CIRCULANT = 2, QVS_MIX_CSR = 3, QVS_MIX_PARITY = 4 };
 /* options for qvs_set_option */
 enum {
   QVS_OPT_CKPT_LAYERS = 1,  /* adjoint: store the forward state every this many layers and
@@ -78,6 +78,12 @@ enum {
  *     interval once, here: 64 fp64 Lanczos steps, extreme Ritz values widened by their residuals
  *     and by 1 % of the width, capped by the Gershgorin bound); cheb_tol is the Chebyshev
  *     truncation tolerance (0: 1e-7).
+ * QVS_MIX_PARITY (Sec. 2.4.1, QAOAz): U(t) = exp(-i t B_last) exp(-i t B_even) exp(-i t B_odd) on
+ *     two rings of qubits, the even qubits (0, 2, ...) and the odd qubits (1, 3, ...), over the
+ *     full register (dim = 2^n_qubits, 12 <= n_qubits <= 30, complex64). On a ring of N qubits
+ *     (1-indexed positions k) B_odd couples (k, k+1) for odd k, B_even (k, k+1) for even k plus
+ *     the closing pair (N, 1) when N is even, B_last the closing pair when N is odd; each coupling
+ *     is X X + Y Y; one t per layer. Reads n_qubits only.
  */
 typedef struct {
   int n_qubits;
@@ -115,6 +121,13 @@ int qvs_set_initial_state(qvs_t h, const void* psi0, int on_device);
 
 /* Set an option (QVS_OPT_*). */
 int qvs_set_option(qvs_t h, int option, int64_t value);
+
+/* Sec. 6.2 (QAOAz initial state): write |01>^{(x)A} ((|00> + |11>)/sqrt 2)^{(x)(n/2 - A)} into the
+ * complex64 device buffer dst (2^n_qubits amplitudes, normal form): asset a occupies qubits
+ * (2a, 2a+1) (qubit u = index bit n-1-u), the first A assets are |01>. Stream-ordered on stream
+ * (NULL: default stream). QVS_EINVAL for odd or out-of-range n_qubits, A outside [0, n/2], NULL dst.
+ * Pass the buffer to qvs_set_initial_state. */
+int qvs_state_parity(int n_qubits, int A, void* dst, void* stream);
 
 /* Sec. 2.1: evolve |psi0> through p layers; the final state stays on the device and its
  * objective is available from qvs_expectation. gammas, ts: host arrays of length p. */

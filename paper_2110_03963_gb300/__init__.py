@@ -24,7 +24,7 @@ QVS_OK, QVS_EINVAL, QVS_ENOMEM, QVS_ECUDA, QVS_ESTATE, QVS_ENUMERIC, QVS_ETIMEOU
     0, -1, -2, -3, -4, -5, -6, -7
 QVS_C64, QVS_C128 = 1, 2
 QVS_I32, QVS_F32, QVS_F64 = 1, 2, 3
-QVS_MIX_HYPERCUBE, QVS_MIX_CIRCULANT, QVS_MIX_CSR = 1, 2, 3
+QVS_MIX_HYPERCUBE, QVS_MIX_CIRCULANT, QVS_MIX_CSR, QVS_MIX_PARITY = 1, 2, 3, 4
 QVS_OPT_CKPT_LAYERS = 1
 QVS_OPT_PROFILE = 2
 
@@ -32,7 +32,7 @@ EXPORTED = [
     "qvs_create", "qvs_destroy", "qvs_set_quality", "qvs_set_mixer", "qvs_set_initial_state",
     "qvs_set_option", "qvs_evolve", "qvs_expectation", "qvs_gradient", "qvs_get_state",
     "qvs_last_launch_count", "qvs_kernel_stats", "qvs_quality_maxcut", "qvs_quality_subset", "qvs_quality_portfolio",
-    "qvs_xy_ring_csr", "qvs_batch_create", "qvs_batch_set_quality", "qvs_batch_gradient",
+    "qvs_xy_ring_csr", "qvs_state_parity", "qvs_batch_create", "qvs_batch_set_quality", "qvs_batch_gradient",
     "qvs_batch_info", "qvs_batch_destroy", "qvs_gradient_small_noalloc", "qvs_strerror",
 ]
 
@@ -90,6 +90,7 @@ def load(path: str = LIB_PATH):
         "qvs_quality_subset": (I, [I, P(D), I, V, V]),
         "qvs_quality_portfolio": (I, [I, I64, V, P(D), P(D), D, I, V, V]),
         "qvs_xy_ring_csr": (I, [I, I, V, V, V, P(I64), P(I64)]),
+        "qvs_state_parity": (I, [I, I, V, V]),
         "qvs_gradient_small_noalloc": (I, [I, I, I, V, P(D), P(D), V, V]),
         "qvs_batch_create": (I, [P(V), I, P(ctypes.c_int32), P(ctypes.c_int32), V]),
         "qvs_batch_set_quality": (I, [V, V, I]),
@@ -270,6 +271,14 @@ def qvs_quality_portfolio(n_qubits: int, states_dev, returns, cov, omega: float,
     return out
 
 
+def qvs_state_parity(n_qubits: int, A: int, out, stream=None):
+    """The QAOAz parity initial state written into the complex64 device tensor ``out``."""
+    op, odev = _ptr_of(out)
+    assert odev == 1
+    _check(load().qvs_state_parity(int(n_qubits), int(A), op, _stream_ptr(stream)), "qvs_state_parity")
+    return out
+
+
 def qvs_xy_ring_csr(n: int, k: int):
     """Returns (states int64[dim], rowptr int64[dim+1], colind int32[nnz]) as numpy arrays."""
     lib = load()
@@ -376,6 +385,12 @@ def qvs_strerror(status: int) -> str:
 
 
 # ---------------------------------------------------------------- convenience layer
+
+
+def parity_desc(n: int) -> MixerDesc:
+    d = MixerDesc()
+    d.n_qubits = n
+    return d
 
 
 def hypercube_desc(n: int) -> MixerDesc:

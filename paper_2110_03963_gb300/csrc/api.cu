@@ -218,6 +218,8 @@ extern "C" int qvs_set_mixer(qvs_t h, int kind, const qvs_mixer_desc* d) {
     QVS_TRY(circ_set_mixer(h, d));
   } else if (kind == QVS_MIX_CSR) {
     QVS_TRY(csr_set_mixer(h, d));
+  } else if (kind == QVS_MIX_PARITY) {
+    QVS_TRY(parity_set_mixer(h, d));
   } else {
     return QVS_EINVAL;
   }
@@ -272,6 +274,7 @@ extern "C" int qvs_evolve(qvs_t h, int p, const double* gammas, const double* ts
     case QVS_MIX_HYPERCUBE: return hc_evolve(h, p, gammas, ts);
     case QVS_MIX_CIRCULANT: return circ_evolve(h, p, gammas, ts);
     case QVS_MIX_CSR: return csr_evolve(h, p, gammas, ts);
+    case QVS_MIX_PARITY: return parity_evolve(h, p, gammas, ts);
   }
   return QVS_ESTATE;
 }
@@ -292,6 +295,7 @@ extern "C" int qvs_gradient(qvs_t h, int p, const double* gammas, const double* 
     case QVS_MIX_HYPERCUBE: return hc_gradient(h, p, gammas, ts, E, dgamma, dt);
     case QVS_MIX_CIRCULANT: return circ_gradient(h, p, gammas, ts, E, dgamma, dt);
     case QVS_MIX_CSR: return csr_gradient(h, p, gammas, ts, E, dgamma, dt);
+    case QVS_MIX_PARITY: return parity_gradient(h, p, gammas, ts, E, dgamma, dt);
   }
   return QVS_ESTATE;
 }

@@ -1,0 +1,469 @@
+// QAOAz parity-ring mixer path (Sec. 2.4.1): U_parity(t) = exp(-i t B_last) exp(-i t B_even)
+// exp(-i t B_odd) on two rings of qubits (the even qubits and the odd qubits), over the full 2^n
+// register. Each factor is a sum of XY terms on disjoint qubit pairs, so its exponential is one
+// layer of Givens rotations: on the |01>, |10> amplitudes of a pair,
+//     (a, b) -> (cos 2t a - i sin 2t b, cos 2t b - i sin 2t a),
+// and the identity on |00>, |11>. No series is needed.
+//
+// Schedule. The gates of a layer (pairs of index bits, in the printed factor order) are packed on
+// the host into passes: a pass is a tile of 12 index bits (the 4 lowest bits, so each tile row is
+// 128 contiguous bytes, plus up to 8 others) and the gates whose two bits lie in the tile, taken in
+// an order that respects every dependency (a gate follows every earlier gate sharing a bit with
+// it; gates on disjoint bits commute). A CTA stages its 2^12-amplitude tile in shared memory,
+// applies the pass's gates one after another (1024 pairs each) and writes the tile back. The
+// phase of layer k is applied as the tile is loaded in the first pass of the layer. n = 24 needs
+// three passes per layer.
+//
+// Gradient. Every pass output of the forward sweep is stored. The reverse sweep runs the passes
+// backwards on (psi, lambda): psi is re-read from the pass's stored output and both vectors are
+// staged in shared memory; each gate is undone on both after its term
+//     df/dt_k += 2 Im <lambda| (XX+YY)_g |psi>   (at the gate's output)
+// is accumulated (one t per layer is shared by every gate, so the layer's derivative is the sum
+// over its gates, in any order consistent with the dependencies); the first pass of a layer then
+// adds df/dgamma_k = 2 Im <lambda|Q phi_k> and undoes the phase on lambda.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "qvs_internal.h"
+
+namespace qvs {
+namespace pr {
+
+constexpr int TB = 12;
+constexpr int TILE = 1 << TB;
+constexpr int NT = 256;
+constexpr int EPT = TILE / NT;   // 16 amplitudes per thread when staging
+constexpr int CHUNK = 4;         // lowest index bits, always in the tile
+constexpr int MAXG = 40;         // gates per pass
+constexpr int MAXNT = 32;        // non-tile bits
+
+// padded shared slot: one spare slot after every 32 (gate pairs stride by powers of two)
+__host__ __device__ __forceinline__ constexpr int spos(int j) { return j + (j >> 5); }
+constexpr int SLOTS = spos(TILE - 1) + 1;
+
+struct PassDesc {
+  uint8_t pos[TB];       // index bit of tile bit i (pos[i] = i for i < CHUNK)
+  uint8_t ga[MAXG];      // gate g couples tile bits ga[g] and gb[g]
+  uint8_t gb[MAXG];
+  uint8_t ntbit[MAXNT];  // non-tile index bits (the CTA index scatters into them)
+  int ngates, nnt;
+};
+
+struct Args {
+  PassDesc d;
+  const float2* in;      // forward: pass input (NULL: uniform state); reverse: psi at the output
+  float2* out;           // forward: pass output
+  const float2* lam_in;  // reverse only
+  float2* lam_out;
+  const float* q;
+  float c, s;            // cos 2t, sin 2t of the layer
+  float ph0, ph1;        // phase gamma / 2pi as a float-float pair (first pass of a layer)
+  int has_phase;
+  float init_amp;
+  double* part;          // partial rows part[row * gridDim.x + blockIdx.x]
+  int row_t, row_g;
+};
+
+__device__ __forceinline__ uint32_t tile_base(const PassDesc& d, uint32_t bid) {
+  uint32_t base = 0;
+  for (int i = 0; i < d.nnt; ++i)
+    if ((bid >> i) & 1u) base |= 1u << d.ntbit[i];
+  return base;
+}
+
+// index offsets of the amplitudes thread t stages: element m (0..15) is tile index t + 256 m
+__device__ __forceinline__ uint32_t thr_off(const PassDesc& d, uint32_t t) {
+  uint32_t o = t & 15u;
+#pragma unroll
+  for (int i = 4; i < 8; ++i)
+    if ((t >> i) & 1u) o |= 1u << d.pos[i];
+  return o;
+}
+__device__ __forceinline__ uint32_t elem_off(const PassDesc& d, int m) {
+  uint32_t o = 0;
+#pragma unroll
+  for (int i = 8; i < 12; ++i)
+    if ((m >> (i - 8)) & 1) o |= 1u << d.pos[i];
+  return o;
+}
+
+// pair k (0..1023) of a gate on tile bits (a, b): the index with bit a = 0, bit b = 1
+__device__ __forceinline__ uint32_t pair_lo(uint32_t k, int a, int b) {
+  const int p1 = a < b ? a : b, p2 = a < b ? b : a;
+  uint32_t x = ((k >> p1) << (p1 + 1)) | (k & ((1u << p1) - 1u));
+  x = ((x >> p2) << (p2 + 1)) | (x & ((1u << p2) - 1u));
+  return x | (1u << b);
+}
+
+// exp(-i 2 pi f) with f = gamma / 2pi * q reduced exactly (float-float turns, FMA two-product)
+__device__ __forceinline__ void phase_cs(float q, float ghi, float glo, float& c, float& s) {
+  const float p = ghi * q;
+  const float e = fmaf(ghi, q, -p);
+  const float r = p - rintf(p);
+  const float f = r + fmaf(glo, q, e);
+  __sincosf(6.28318530717958647692f * f, &s, &c);
+}
+
+__device__ __forceinline__ void block_store2(float a, float b, double* part, int ra, int rb) {
+  __shared__ double red[2][NT / 32];
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if ((tid & 31) == 0) {
+    red[0][tid >> 5] = (double)a;
+    red[1][tid >> 5] = (double)b;
+  }
+  __syncthreads();
+  if (tid < 2) {
+    double s = 0.0;
+    for (int w = 0; w < NT / 32; ++w) s += red[tid][w];
+    const int row = tid == 0 ? ra : rb;
+    if (row >= 0) part[(size_t)row * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+// forward pass: stage (phase), gates, write back
+__global__ void __launch_bounds__(NT) fwd_kernel(const __grid_constant__ Args a) {
+  __shared__ __align__(16) float2 sm[SLOTS];
+  const uint32_t t = threadIdx.x;
+  const uint32_t base = tile_base(a.d, blockIdx.x) | thr_off(a.d, t);
+#pragma unroll
+  for (int m = 0; m < EPT; ++m) {
+    const uint32_t g = base | elem_off(a.d, m);
+    float2 x = a.in ? __ldcs(a.in + g) : make_float2(a.init_amp, 0.f);
+    if (a.has_phase) {
+      float c, s;
+      phase_cs(__ldcs(a.q + g), a.ph0, a.ph1, c, s);
+      x = make_float2(c * x.x + s * x.y, c * x.y - s * x.x);   // exp(-i gamma q) x
+    }
+    sm[spos((int)t + NT * m)] = x;
+  }
+  __syncthreads();
+  for (int gi = 0; gi < a.d.ngates; ++gi) {
+    const int ba = a.d.ga[gi], bb = a.d.gb[gi];
+    const uint32_t mab = (1u << ba) | (1u << bb);
+#pragma unroll
+    for (int k = 0; k < TILE / 4 / NT; ++k) {
+      const uint32_t lo = pair_lo(t + NT * k, ba, bb), hi = lo ^ mab;
+      const float2 x = sm[spos(lo)], y = sm[spos(hi)];
+      sm[spos(lo)] = make_float2(a.c * x.x + a.s * y.y, a.c * x.y - a.s * y.x);   // c x - i s y
+      sm[spos(hi)] = make_float2(a.c * y.x + a.s * x.y, a.c * y.y - a.s * x.x);   // c y - i s x
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int m = 0; m < EPT; ++m) __stcs(a.out + (base | elem_off(a.d, m)), sm[spos((int)t + NT * m)]);
+}
+
+// reverse pass on (psi, lambda)
+__global__ void __launch_bounds__(NT) rev_kernel(const __grid_constant__ Args a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];   // 2 * SLOTS float2 (dynamic)
+  float2* sp = reinterpret_cast<float2*>(smem_raw);
+  float2* sl = sp + SLOTS;
+  const uint32_t t = threadIdx.x;
+  const uint32_t base = tile_base(a.d, blockIdx.x) | thr_off(a.d, t);
+#pragma unroll
+  for (int m = 0; m < EPT; ++m) {
+    const uint32_t g = base | elem_off(a.d, m);
+    sp[spos((int)t + NT * m)] = __ldcs(a.in + g);
+    sl[spos((int)t + NT * m)] = __ldcs(a.lam_in + g);
+  }
+  __syncthreads();
+  float acc_t = 0.f, acc_g = 0.f;
+  for (int gi = a.d.ngates - 1; gi >= 0; --gi) {
+    const int ba = a.d.ga[gi], bb = a.d.gb[gi];
+    const uint32_t mab = (1u << ba) | (1u << bb);
+#pragma unroll
+    for (int k = 0; k < TILE / 4 / NT; ++k) {
+      const uint32_t lo = pair_lo(t + NT * k, ba, bb), hi = lo ^ mab;
+      const float2 x = sp[spos(lo)], y = sp[spos(hi)];
+      const float2 u = sl[spos(lo)], v = sl[spos(hi)];
+      // Im(conj(l_lo) p_hi) + Im(conj(l_hi) p_lo): <lambda|(XX+YY)|psi> / 2 on this pair
+      acc_t += (u.x * y.y - u.y * y.x) + (v.x * x.y - v.y * x.x);
+      // undo: (a, b) -> (c a + i s b, c b + i s a)
+      sp[spos(lo)] = make_float2(a.c * x.x - a.s * y.y, a.c * x.y + a.s * y.x);
+      sp[spos(hi)] = make_float2(a.c * y.x - a.s * x.y, a.c * y.y + a.s * x.x);
+      sl[spos(lo)] = make_float2(a.c * u.x - a.s * v.y, a.c * u.y + a.s * v.x);
+      sl[spos(hi)] = make_float2(a.c * v.x - a.s * u.y, a.c * v.y + a.s * u.x);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int m = 0; m < EPT; ++m) {
+    const uint32_t g = base | elem_off(a.d, m);
+    float2 l = sl[spos((int)t + NT * m)];
+    if (a.has_phase) {
+      const float2 p = sp[spos((int)t + NT * m)];
+      const float qq = __ldcs(a.q + g);
+      acc_g += qq * (l.x * p.y - l.y * p.x);
+      float c, s;
+      phase_cs(qq, a.ph0, a.ph1, c, s);
+      l = make_float2(c * l.x - s * l.y, c * l.y + s * l.x);   // exp(+i gamma q) lambda
+    }
+    __stcs(a.lam_out + g, l);
+  }
+  // 2 Im<lambda|(XX+YY)|psi> = 4 * (accumulated half-sums); df/dgamma = 2 Im<lambda|Q phi>
+  block_store2(4.f * acc_t, 2.f * acc_g, a.part, a.row_t, a.has_phase ? a.row_g : -1);
+}
+
+// E = sum q |psi|^2 and lambda = Q psi (elementwise over the register)
+__global__ void __launch_bounds__(NT) elam_kernel(int64_t dim, const float2* __restrict__ psi,
+                                                  const float* __restrict__ q, float2* __restrict__ lam,
+                                                  double* part, int row) {
+  float e = 0.f;
+  for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < dim; i += (int64_t)gridDim.x * NT) {
+    const float2 x = __ldcs(psi + i);
+    const float qq = __ldcs(q + i);
+    e += qq * (x.x * x.x + x.y * x.y);
+    if (lam) __stcs(lam + i, make_float2(qq * x.x, qq * x.y));
+  }
+  block_store2(e, 0.f, part, row, -1);
+}
+
+// the paper's parity initial state (Sec. 6.2): asset a on qubits (2a, 2a+1); |01> for a < A,
+// (|00> + |11>)/sqrt 2 otherwise (qubit u = index bit n-1-u)
+__global__ void parity_state_kernel(int n, int A, double amp, float2* __restrict__ out) {
+  const int64_t dim = (int64_t)1 << n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < dim; i += (int64_t)gridDim.x * blockDim.x) {
+    bool ok = true;
+    for (int a = 0; a < n / 2; ++a) {
+      const int hi = (int)((i >> (n - 1 - 2 * a)) & 1), lo = (int)((i >> (n - 2 - 2 * a)) & 1);
+      ok = ok && (a < A ? (hi == 0 && lo == 1) : (hi == lo));
+    }
+    out[i] = make_float2(ok ? (float)amp : 0.f, 0.f);
+  }
+}
+
+// ---------------------------------------------------------------- host side
+
+// qubit pairs of B_odd, B_even, B_last on the even-qubit ring and the odd-qubit ring (1-indexed
+// ring positions k: B_odd (k, k+1) for odd k < N; B_even (k, k+1) for even k < N plus (N, 1) when
+// N is even; B_last (N, 1) when N is odd), as index-bit pairs, in the printed factor order
+static std::vector<std::pair<int, int>> layer_gates(int n) {
+  std::vector<std::pair<int, int>> rounds[3];
+  for (int start = 0; start < 2; ++start) {
+    std::vector<int> ring;
+    for (int qb = start; qb < n; qb += 2) ring.push_back(qb);
+    const int N = (int)ring.size();
+    for (int k = 1; k < N; ++k) rounds[(k % 2 == 1) ? 0 : 1].push_back({ring[k - 1], ring[k]});
+    if (N >= 2) rounds[(N % 2 == 0) ? 1 : 2].push_back({ring[N - 1], ring[0]});
+  }
+  std::vector<std::pair<int, int>> gates;
+  for (auto& r : rounds)
+    for (auto& pq : r) gates.push_back({n - 1 - pq.first, n - 1 - pq.second});
+  return gates;
+}
+
+struct Pass {
+  PassDesc d;
+};
+
+// greedy packing of one layer's gates into passes (see the file comment)
+static int plan_layer(int n, std::vector<Pass>& out) {
+  const auto gates = layer_gates(n);
+  const int G = (int)gates.size();
+  std::vector<char> done(G, 0);
+  int left = G;
+  while (left > 0) {
+    std::vector<int> tile;
+    for (int b = 0; b < CHUNK; ++b) tile.push_back(b);
+    auto in_tile = [&](int b) { return std::find(tile.begin(), tile.end(), b) != tile.end(); };
+    std::vector<int> sel;
+    for (int g = 0; g < G; ++g) {
+      if (done[g]) continue;
+      bool ok = true;
+      for (int h = 0; h < g && ok; ++h) {
+        const bool shares = gates[h].first == gates[g].first || gates[h].first == gates[g].second ||
+                            gates[h].second == gates[g].first || gates[h].second == gates[g].second;
+        if (shares && !done[h] && std::find(sel.begin(), sel.end(), h) == sel.end()) ok = false;
+      }
+      if (!ok) continue;
+      const int need = (in_tile(gates[g].first) ? 0 : 1) + (in_tile(gates[g].second) ? 0 : 1);
+      if ((int)tile.size() + need > TB || (int)sel.size() >= MAXG) continue;
+      if (!in_tile(gates[g].first)) tile.push_back(gates[g].first);
+      if (!in_tile(gates[g].second)) tile.push_back(gates[g].second);
+      sel.push_back(g);
+    }
+    if (sel.empty()) return QVS_EUNSUPPORTED;
+    // pad the tile to 12 bits with the lowest free index bits
+    for (int b = CHUNK; (int)tile.size() < TB && b < n; ++b)
+      if (!in_tile(b)) tile.push_back(b);
+    if ((int)tile.size() != TB) return QVS_EUNSUPPORTED;
+    std::sort(tile.begin() + CHUNK, tile.end());
+    Pass P{};
+    for (int i = 0; i < TB; ++i) P.d.pos[i] = (uint8_t)tile[i];
+    auto tbit = [&](int b) { return (int)(std::find(tile.begin(), tile.end(), b) - tile.begin()); };
+    P.d.ngates = (int)sel.size();
+    for (int i = 0; i < P.d.ngates; ++i) {
+      P.d.ga[i] = (uint8_t)tbit(gates[sel[i]].first);
+      P.d.gb[i] = (uint8_t)tbit(gates[sel[i]].second);
+      done[sel[i]] = 1;
+    }
+    left -= (int)sel.size();
+    P.d.nnt = 0;
+    for (int b = 0; b < n; ++b)
+      if (!in_tile(b)) P.d.ntbit[P.d.nnt++] = (uint8_t)b;
+    out.push_back(P);
+  }
+  return QVS_OK;
+}
+
+static int run(qvs_ctx* h, int p, const double* gammas, const double* ts, bool grad, double* E, double* dg,
+               double* dt) {
+  const int n = h->n;
+  if (h->precision != QVS_C64) return QVS_EUNSUPPORTED;
+  std::vector<Pass> layer;
+  QVS_TRY(plan_layer(n, layer));
+  const int L = (int)layer.size();
+  const int F = L * p;                       // forward passes
+  const int64_t dim = h->dim;
+  const uint32_t grid = (uint32_t)(dim >> TB);
+  const size_t vb = sizeof(float2) * (size_t)dim;
+  // stored pass outputs (every pass), lambda
+  QVS_TRY(h->ckpt.ensure(vb * (size_t)(grad ? F : 1)));
+  if (grad) QVS_TRY(h->lam.ensure(vb));
+  // rows: 0 = E; per layer k: 1 + k = dgamma_k, 1 + p + k = dt_k; one row per reverse pass for dt
+  const int nslots = 1 + 2 * p;
+  const int nrows = 1 + p + F;
+  QVS_TRY(h->part.ensure(sizeof(double) * (size_t)nrows * grid));
+  QVS_TRY(h->res.ensure(sizeof(double) * nslots));
+  std::vector<int> rowmap;   // each slot sums its rows (reduce_rows takes up to 3 rows per slot)
+  // dt_k collects L rows: chain them through extra slots when L > 3 (summed on the host below)
+  const int dt_groups = (L + 2) / 3;
+  const int nout = grad ? (1 + p + p * dt_groups) : 1;
+  rowmap.assign(3 * (size_t)nout, -1);
+  rowmap[0] = 0;
+  if (grad) {
+    for (int k = 0; k < p; ++k) rowmap[3 * (1 + k)] = 1 + k;
+    for (int k = 0; k < p; ++k)
+      for (int j = 0; j < L; ++j) rowmap[3 * (1 + p + k * dt_groups + j / 3) + (j % 3)] = 1 + p + k * L + j;
+  }
+  QVS_TRY(h->rowmap.ensure(sizeof(int) * rowmap.size()));
+  QVS_TRY(h->res.ensure(sizeof(double) * (size_t)nout));
+  QVS_CUDA_TRY(cudaMemcpyAsync(h->rowmap.ptr, rowmap.data(), sizeof(int) * rowmap.size(), cudaMemcpyHostToDevice,
+                               h->stream));
+  float2* S = h->ckpt.as<float2>();
+  auto stored = [&](int j) { return S + (size_t)(grad ? j : 0) * dim; };   // output of forward pass j
+  int64_t launches = 0;
+  const double c = 8.0, qb = 4.0;
+  for (int k = 0; k < p; ++k) {
+    for (int j = 0; j < L; ++j) {
+      const int f = k * L + j;
+      Args a{};
+      a.d = layer[j].d;
+      a.in = f == 0 ? (h->have_psi0 ? h->psi0.as<float2>() : nullptr) : stored(f - 1);
+      a.out = stored(f);
+      a.q = h->q.as<float>();
+      a.c = (float)cos(2.0 * ts[k]);
+      a.s = (float)sin(2.0 * ts[k]);
+      a.has_phase = j == 0;
+      if (j == 0) turns_split(gammas[k], &a.ph0, &a.ph1);
+      a.init_amp = (float)(1.0 / sqrt((double)dim));
+      cudaEvent_t e0;
+      QVS_TRY(prof_begin(h, &e0));
+      fwd_kernel<<<grid, NT, 0, h->stream>>>(a);
+      QVS_CUDA_TRY(cudaGetLastError());
+      QVS_TRY(prof_end(h, "parity_pass", (double)dim * ((a.in ? c : 0.0) + c + (j == 0 ? qb : 0.0)), e0));
+      ++launches;
+    }
+  }
+  float2* psiF = stored(F - 1);
+  {
+    cudaEvent_t e0;
+    QVS_TRY(prof_begin(h, &e0));
+    elam_kernel<<<grid, NT, 0, h->stream>>>(dim, psiF, h->q.as<float>(), grad ? h->lam.as<float2>() : nullptr,
+                                            h->part.as<double>(), 0);
+    QVS_CUDA_TRY(cudaGetLastError());
+    QVS_TRY(prof_end(h, "parity_elam", (double)dim * (c + qb + (grad ? c : 0.0)), e0));
+    ++launches;
+  }
+  if (grad) {
+    const size_t rsm = 2 * (size_t)SLOTS * sizeof(float2);
+    QVS_CUDA_TRY(cudaFuncSetAttribute(rev_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
+    for (int f = F - 1; f >= 0; --f) {
+      const int k = f / L, j = f % L;
+      Args a{};
+      a.d = layer[j].d;
+      a.in = stored(f);
+      a.lam_in = h->lam.as<float2>();
+      a.lam_out = h->lam.as<float2>();
+      a.q = h->q.as<float>();
+      a.c = (float)cos(2.0 * ts[k]);
+      a.s = (float)sin(2.0 * ts[k]);
+      a.has_phase = j == 0;
+      if (j == 0) turns_split(gammas[k], &a.ph0, &a.ph1);
+      a.part = h->part.as<double>();
+      a.row_t = 1 + p + f;
+      a.row_g = 1 + k;
+      cudaEvent_t e0;
+      QVS_TRY(prof_begin(h, &e0));
+      rev_kernel<<<grid, NT, rsm, h->stream>>>(a);
+      QVS_CUDA_TRY(cudaGetLastError());
+      QVS_TRY(prof_end(h, "parity_pass_adjoint", (double)dim * (3 * c + (j == 0 ? qb : 0.0)), e0));
+      ++launches;
+    }
+  }
+  {
+    cudaEvent_t e0;
+    QVS_TRY(prof_begin(h, &e0));
+    QVS_TRY(reduce_rows(h, h->part.as<double>(), grid, h->rowmap.as<int>(), nout, h->res.as<double>()));
+    QVS_TRY(prof_end(h, "reduce_rows", 8.0 * grid * nrows, e0));
+    ++launches;
+  }
+  h->launches = launches;
+  QVS_TRY(ensure_host_res(h, (nout + 1) / 2 + 1));
+  QVS_CUDA_TRY(cudaMemcpyAsync(h->host_res, h->res.ptr, sizeof(double) * nout, cudaMemcpyDeviceToHost, h->stream));
+  QVS_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  QVS_TRY(prof_flush(h));
+  *E = h->host_res[0];
+  if (grad) {
+    for (int k = 0; k < p; ++k) {
+      dg[k] = h->host_res[1 + k];
+      double s = 0.0;
+      for (int gi = 0; gi < dt_groups; ++gi) s += h->host_res[1 + p + k * dt_groups + gi];
+      dt[k] = s;
+    }
+  } else {
+    // evolve: the final state is the last pass output
+    QVS_TRY(h->psi.ensure(vb));
+    QVS_CUDA_TRY(cudaMemcpyAsync(h->psi.ptr, psiF, vb, cudaMemcpyDeviceToDevice, h->stream));
+    QVS_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  }
+  return QVS_OK;
+}
+
+}  // namespace pr
+
+int parity_set_mixer(qvs_ctx* h, const qvs_mixer_desc* d) {
+  if (h->precision != QVS_C64) return QVS_EUNSUPPORTED;
+  if (d->n_qubits < pr::TB || d->n_qubits > 30 || h->n != d->n_qubits) return QVS_EINVAL;
+  std::vector<pr::Pass> layer;
+  return pr::plan_layer(h->n, layer);
+}
+
+int parity_evolve(qvs_ctx* h, int p, const double* gammas, const double* ts) {
+  double E = 0.0;
+  QVS_TRY(pr::run(h, p, gammas, ts, false, &E, nullptr, nullptr));
+  h->E = E;
+  h->have_E = true;
+  return QVS_OK;
+}
+
+int parity_gradient(qvs_ctx* h, int p, const double* gammas, const double* ts, double* E, double* dg, double* dt) {
+  return pr::run(h, p, gammas, ts, true, E, dg, dt);
+}
+
+}  // namespace qvs
+
+extern "C" int qvs_state_parity(int n_qubits, int A, void* dst, void* stream) {
+  if (n_qubits < 2 || n_qubits > 30 || (n_qubits & 1) || A < 0 || A > n_qubits / 2 || !dst) return QVS_EINVAL;
+  const double amp = pow(sqrt(0.5), (double)(n_qubits / 2 - A));
+  qvs::pr::parity_state_kernel<<<1024, 256, 0, (cudaStream_t)stream>>>(n_qubits, A, amp, static_cast<float2*>(dst));
+  QVS_CUDA_TRY(cudaGetLastError());
+  return QVS_OK;
+}

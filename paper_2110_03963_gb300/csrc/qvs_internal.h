@@ -147,6 +147,11 @@ int circ_gradient(qvs_ctx* h, int p, const double* gammas, const double* ts, dou
                   double* dt);
 
 // CSR Chebyshev (QAOAz) path: csr_cheb.cu
+int parity_set_mixer(qvs_ctx* h, const qvs_mixer_desc* d);
+int parity_evolve(qvs_ctx* h, int p, const double* gammas, const double* ts);
+int parity_gradient(qvs_ctx* h, int p, const double* gammas, const double* ts, double* E, double* dg,
+                    double* dt);
+
 int csr_set_mixer(qvs_ctx* h, const qvs_mixer_desc* d);
 int csr_evolve(qvs_ctx* h, int p, const double* gammas, const double* ts);
 int csr_gradient(qvs_ctx* h, int p, const double* gammas, const double* ts, double* E, double* dg,

@@ -228,6 +228,9 @@ def run_extras(qvs, torch, stream, peak, steps, warmup, only=None, qwoa_n=26, qw
     out = {}
     if only in (None, "qwoa"):
         out.update(_extra_qwoa(qvs, torch, stream, peak, steps, warmup, qwoa_n, qwoa_p))
+    if only in (None, "parity"):
+        out.update(_extra_parity(qvs, torch, stream, peak, steps, warmup, qaoaz_n if only == "parity" else 24,
+                                 qaoaz_p if only == "parity" else 4))
     if only in (None, "qaoaz"):
         out.update(_extra_qaoaz(qvs, torch, stream, peak, steps, warmup, qaoaz_n, qaoaz_p))
     if only in (None, "batch"):
@@ -250,6 +253,33 @@ def _extra_qwoa(qvs, torch, stream, peak, steps, warmup, n, p):
     units = float(1 << n) * p
     out[f"qwoa_circulant_n{n}_p{p}"] = {"value": units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
                                         "launches_per_step": sim.launches(), "roofline": roof, "kernels": ker}
+    sim.close()
+    return out
+
+
+def _extra_parity(qvs, torch, stream, peak, steps, warmup, n, p, A=2):
+    """QAOAz with the paper's parity-ring mixer (Sec. 2.4.1) on the full 2^n register: portfolio
+    qualities of every basis state, parity initial state with constraint value A."""
+    out = {}
+    dim = 1 << n
+    port = wl.portfolio(n // 2, wl.rng_for(99, n))
+    states = torch.arange(dim, dtype=torch.int64, device="cuda")
+    q = torch.empty(dim, dtype=torch.float32, device="cuda")
+    qvs.qvs_quality_portfolio(n, states, port.returns, port.cov, port.omega, q, qvs.QVS_F32, stream)
+    del states
+    psi0 = torch.empty(dim, dtype=torch.complex64, device="cuda")
+    qvs.qvs_state_parity(n, A, psi0, stream)
+    sim = qvs.Simulator(dim, qvs.QVS_C64, stream)
+    sim.set_quality(q).set_mixer(qvs.QVS_MIX_PARITY, qvs.parity_desc(n)).set_initial_state(psi0)
+    gs, ts = wl.thetas(p, wl.rng_for(100, 0))
+    ms = _time_steps(torch, stream, lambda: sim.gradient(gs, ts), steps, warmup)
+    sim.set_option(qvs.QVS_OPT_PROFILE, 1)
+    for _ in range(2):
+        sim.gradient(gs, ts)
+    roof, ker = _kernel_summary(qvs, sim.h, peak, 2)
+    units = float(dim) * p
+    out[f"qaoaz_parity_n{n}_A{A}_p{p}"] = {"value": units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                                          "launches_per_step": sim.launches(), "roofline": roof, "kernels": ker}
     sim.close()
     return out
 
@@ -481,8 +511,8 @@ def run_workload(args):
     import paper_2110_03963_gb300 as qvs
     stream = torch.cuda.current_stream()
     peak, _ = _peaks()
-    n = args.qubits if args.qubits != N_QUBITS else {"qwoa": 26, "qaoaz": 24, "batch": 0}[args.workload]
-    p = args.layers if args.layers != P_LAYERS else {"qwoa": 6, "qaoaz": 4, "batch": 0}[args.workload]
+    n = args.qubits if args.qubits != N_QUBITS else {"qwoa": 26, "qaoaz": 24, "parity": 24, "batch": 0}[args.workload]
+    p = args.layers if args.layers != P_LAYERS else {"qwoa": 6, "qaoaz": 4, "parity": 4, "batch": 0}[args.workload]
     res = run_extras(qvs, torch, stream, peak, args.steps, args.warmup, only=args.workload, qwoa_n=n, qwoa_p=p,
                      qaoaz_n=n, qaoaz_p=p, batch_count=args.count)
     (name, entry), = res.items()
@@ -499,7 +529,7 @@ def main():
     ap.add_argument("--ckpt", type=int, default=None, help="checkpoint interval in layers (0 = ceil(sqrt(p)))")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the QWOA, QAOAz and batched lines")
-    ap.add_argument("--workload", default="qaoa", choices=["qaoa", "qwoa", "qaoaz", "batch"],
+    ap.add_argument("--workload", default="qaoa", choices=["qaoa", "qwoa", "qaoaz", "parity", "batch"],
                     help="qaoa = the benchmark line; the others print one diagnostic line for that workload "
                          "(sizes from --qubits/--layers/--count)")
     ap.add_argument("--count", type=int, default=4096, help="instances for --workload batch")

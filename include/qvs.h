@@ -69,9 +69,10 @@ enum {
  * Mixer description (qvs_set_mixer). Only the fields of the chosen kind are read.
  *
  * QVS_MIX_HYPERCUBE (Sec. 2.3.1): W = sum_j X_j on n_qubits qubits; dim must equal 2^n_qubits.
- * QVS_MIX_CIRCULANT (Sec. 2.4.2, Sec. 3): W symmetric circulant of size dim (a power of two),
- *     given by n_offsets connection offsets s (0 < s < dim) with weights w_s (NULL = all 1):
- *     W[j][(j+s) mod dim] = W[j][(j-s) mod dim] = w_s (the offset dim/2 couples each j once).
+ * QVS_MIX_CIRCULANT (Sec. 2.4.2, Sec. 3): W symmetric circulant of size dim = 2^n, 17 <= n <= 27,
+ *     complex64 (other sizes: QVS_EUNSUPPORTED), given by n_offsets connection offsets s
+ *     (0 < s < dim) with weights w_s (NULL = all 1): W[j][(j+s) mod dim] = W[j][(j-s) mod dim] = w_s
+ *     (the offset dim/2 couples each j once).
  * QVS_MIX_CSR (Sec. 2.4.1, Sec. 3): W real symmetric sparse (rowptr int64[dim+1], colind
  *     int32[nnz]), values float[nnz] or NULL for a constant implicit_value; host or device arrays
  *     per csr_on_device. spec_lo/spec_hi bound the spectrum (both 0: the library estimates the

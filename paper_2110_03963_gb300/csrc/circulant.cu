@@ -24,25 +24,53 @@
 namespace qvs {
 namespace cf {
 
+int set_mixer_n17(qvs_ctx* h, const int64_t* ofs, const double* w, int nofs);
+int run_n17(qvs_ctx* h, int p, const double* gammas, const double* ts, bool grad, double* E, double* dg,
+            double* dt);
+int set_mixer_n18(qvs_ctx* h, const int64_t* ofs, const double* w, int nofs);
+int run_n18(qvs_ctx* h, int p, const double* gammas, const double* ts, bool grad, double* E, double* dg,
+            double* dt);
+int set_mixer_n19(qvs_ctx* h, const int64_t* ofs, const double* w, int nofs);
+int run_n19(qvs_ctx* h, int p, const double* gammas, const double* ts, bool grad, double* E, double* dg,
+            double* dt);
 int set_mixer_n20(qvs_ctx* h, const int64_t* ofs, const double* w, int nofs);
 int run_n20(qvs_ctx* h, int p, const double* gammas, const double* ts, bool grad, double* E, double* dg,
+            double* dt);
+int set_mixer_n21(qvs_ctx* h, const int64_t* ofs, const double* w, int nofs);
+int run_n21(qvs_ctx* h, int p, const double* gammas, const double* ts, bool grad, double* E, double* dg,
             double* dt);
 int set_mixer_n22(qvs_ctx* h, const int64_t* ofs, const double* w, int nofs);
 int run_n22(qvs_ctx* h, int p, const double* gammas, const double* ts, bool grad, double* E, double* dg,
             double* dt);
+int set_mixer_n23(qvs_ctx* h, const int64_t* ofs, const double* w, int nofs);
+int run_n23(qvs_ctx* h, int p, const double* gammas, const double* ts, bool grad, double* E, double* dg,
+            double* dt);
 int set_mixer_n24(qvs_ctx* h, const int64_t* ofs, const double* w, int nofs);
 int run_n24(qvs_ctx* h, int p, const double* gammas, const double* ts, bool grad, double* E, double* dg,
+            double* dt);
+int set_mixer_n25(qvs_ctx* h, const int64_t* ofs, const double* w, int nofs);
+int run_n25(qvs_ctx* h, int p, const double* gammas, const double* ts, bool grad, double* E, double* dg,
             double* dt);
 int set_mixer_n26(qvs_ctx* h, const int64_t* ofs, const double* w, int nofs);
 int run_n26(qvs_ctx* h, int p, const double* gammas, const double* ts, bool grad, double* E, double* dg,
             double* dt);
+int set_mixer_n27(qvs_ctx* h, const int64_t* ofs, const double* w, int nofs);
+int run_n27(qvs_ctx* h, int p, const double* gammas, const double* ts, bool grad, double* E, double* dg,
+            double* dt);
 
 static int dispatch_set_mixer(qvs_ctx* h, const int64_t* ofs, const double* w, int nofs) {
   switch (h->n) {
+    case 17: return set_mixer_n17(h, ofs, w, nofs);
+    case 18: return set_mixer_n18(h, ofs, w, nofs);
+    case 19: return set_mixer_n19(h, ofs, w, nofs);
     case 20: return set_mixer_n20(h, ofs, w, nofs);
+    case 21: return set_mixer_n21(h, ofs, w, nofs);
     case 22: return set_mixer_n22(h, ofs, w, nofs);
+    case 23: return set_mixer_n23(h, ofs, w, nofs);
     case 24: return set_mixer_n24(h, ofs, w, nofs);
+    case 25: return set_mixer_n25(h, ofs, w, nofs);
     case 26: return set_mixer_n26(h, ofs, w, nofs);
+    case 27: return set_mixer_n27(h, ofs, w, nofs);
   }
   return QVS_EUNSUPPORTED;
 }
@@ -50,10 +78,17 @@ static int dispatch_set_mixer(qvs_ctx* h, const int64_t* ofs, const double* w, i
 static int dispatch_run(qvs_ctx* h, int p, const double* g, const double* t, bool grad, double* E, double* dg,
                         double* dt) {
   switch (h->n) {
+    case 17: return run_n17(h, p, g, t, grad, E, dg, dt);
+    case 18: return run_n18(h, p, g, t, grad, E, dg, dt);
+    case 19: return run_n19(h, p, g, t, grad, E, dg, dt);
     case 20: return run_n20(h, p, g, t, grad, E, dg, dt);
+    case 21: return run_n21(h, p, g, t, grad, E, dg, dt);
     case 22: return run_n22(h, p, g, t, grad, E, dg, dt);
+    case 23: return run_n23(h, p, g, t, grad, E, dg, dt);
     case 24: return run_n24(h, p, g, t, grad, E, dg, dt);
+    case 25: return run_n25(h, p, g, t, grad, E, dg, dt);
     case 26: return run_n26(h, p, g, t, grad, E, dg, dt);
+    case 27: return run_n27(h, p, g, t, grad, E, dg, dt);
   }
   return QVS_EUNSUPPORTED;
 }

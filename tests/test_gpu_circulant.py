@@ -54,7 +54,8 @@ def test_subset_quality_bit_exact(qvs, n):
     assert np.array_equal(q.cpu().numpy(), orc.subset_quality(n, w).astype(np.float32))
 
 
-@pytest.mark.parametrize("n,p", [(20, 1), (20, 3), (22, 2)])
+# every column-transform geometry below 2^24: one, two and three-bit digits, odd and even n
+@pytest.mark.parametrize("n,p", [(17, 2), (18, 1), (19, 2), (20, 1), (20, 3), (21, 2), (22, 2), (23, 1)])
 def test_qwoa_pow2_offsets_vs_oracle(qvs, n, p):
     inst = wl.qwoa(n, p)
     sim, _ = _sim(qvs, n, inst.weights, inst.offsets)
@@ -139,3 +140,32 @@ def test_full26_norm_bounds_and_gradient_consistency(full26):
             fd.append((ep - em) / (2 * h))
     fd = np.array(fd)
     assert rel_err_grad(dg, dt, fd[:6], fd[6:]) < 2e-3
+
+
+@pytest.mark.parametrize("n", [25, 27])
+def test_large_sizes_norm_bounds_and_gradient_fd(qvs, n):
+    """The largest geometries (three-bit and one-bit spectator rows): norm, E within the quality
+    range, and the adjoint gradient against central differences of the same path."""
+    p = 2
+    inst = wl.qwoa(n, p)
+    sim, q = _sim(qvs, n, inst.weights, inst.offsets)
+    qh = q.cpu().numpy().astype(np.float64)
+    gs, ts = np.asarray(inst.gammas, float), np.asarray(inst.ts, float)
+    E = sim.evolve(gs, ts)
+    psi = sim.state().astype(np.complex128)
+    assert abs(np.sum(np.abs(psi) ** 2) - 1.0) < 1e-4
+    assert qh.min() <= E <= qh.max()
+    E2, dg, dt = sim.gradient(gs, ts)
+    assert rel_err_E(E2, E) < TOL_E
+    h = 1e-3
+    fd = []
+    for which in range(2):
+        for k in range(p):
+            g2, t2 = gs.copy(), ts.copy()
+            (g2 if which == 0 else t2)[k] += h
+            ep = sim.evolve(g2, t2)
+            (g2 if which == 0 else t2)[k] -= 2 * h
+            em = sim.evolve(g2, t2)
+            fd.append((ep - em) / (2 * h))
+    fd = np.array(fd)
+    assert rel_err_grad(dg, dt, fd[:p], fd[p:]) < 2e-3

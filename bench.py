@@ -140,6 +140,14 @@ def _dist():
     return world, rank, local
 
 
+def replica_aggregate(local_ms: float, units_per_rank: float, world: int, allreduce_max=None):
+    """Whole-job figures of `world` independent replicas (the path does not shard): the step time
+    is the maximum over ranks (allreduce_max reduces one float across ranks), and the throughput
+    counts every rank's units. Returns (ms, units per second)."""
+    ms = float(allreduce_max(local_ms)) if world > 1 else float(local_ms)
+    return ms, units_per_rank * world / (ms * 1e-3)
+
+
 # ------------------------------------------------------------------ CPU oracle sample
 
 def oracle_sample(seconds_target: float = 15.0):
@@ -404,13 +412,13 @@ def run_ours(args):
     ev1.record(stream)
     barrier()
     clocks = sampler.stop()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+    def allreduce_max(x):
+        t = torch.tensor([x], device="cuda", dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+        return float(t.item())
+
     units = float(dim) * p
-    value = units * world / (ms * 1e-3)
+    ms, value = replica_aggregate(ev0.elapsed_time(ev1) / args.steps, units, world, allreduce_max)
 
     # ---- per-kernel event timing (separate, profiled steps)
     sim.set_option(qvs.QVS_OPT_PROFILE, 1)
@@ -443,12 +451,7 @@ def run_ours(args):
         sim.set_quality(q_host.numpy())      # H2D of the step's quality vector (pinned host)
         E, dg, dt = sim.gradient(gs, ts)      # returns E and 2p gradient entries to the host
     barrier()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = units * world / e2e_s
+    e2e_ms, e2e_value = replica_aggregate((time.perf_counter() - t0) / e2e_steps * 1e3, units, world, allreduce_max)
 
     extras = None
     if rank == 0 and world == 1 and not args.no_extras and (n, p) == (N_QUBITS, P_LAYERS):

@@ -146,12 +146,13 @@ int circ_evolve(qvs_ctx* h, int p, const double* gammas, const double* ts);
 int circ_gradient(qvs_ctx* h, int p, const double* gammas, const double* ts, double* E, double* dg,
                   double* dt);
 
-// CSR Chebyshev (QAOAz) path: csr_cheb.cu
+// QAOAz parity-ring mixer path: parity.cu
 int parity_set_mixer(qvs_ctx* h, const qvs_mixer_desc* d);
 int parity_evolve(qvs_ctx* h, int p, const double* gammas, const double* ts);
 int parity_gradient(qvs_ctx* h, int p, const double* gammas, const double* ts, double* E, double* dg,
                     double* dt);
 
+// CSR Chebyshev path: csr_cheb.cu
 int csr_set_mixer(qvs_ctx* h, const qvs_mixer_desc* d);
 int csr_evolve(qvs_ctx* h, int p, const double* gammas, const double* ts);
 int csr_gradient(qvs_ctx* h, int p, const double* gammas, const double* ts, double* E, double* dg,

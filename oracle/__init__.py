@@ -104,6 +104,71 @@ def portfolio_quality(n_qubits: int, states: np.ndarray, returns, cov, omega: fl
     return q
 
 
+def qubo_quality(n: int, c: float, h, J) -> np.ndarray:
+    """Qualities written as a quadratic form of the qubit values (Sec. 2.2: q is any function of the
+    basis state; the max-cut, subset-sum and portfolio costs of Sec. 6 are all of this form):
+
+        q(x) = c + sum_u h_u x_u + sum_{u<v} J_uv x_u x_v     (x_u = value of qubit u)
+
+    J is read above its diagonal only. fp64, terms in the order c, h_0..h_{n-1}, then J by rows.
+    """
+    N = 1 << n
+    x = qubit_bits(n, np.arange(N, dtype=np.int64)).astype(np.float64)
+    q = np.full(N, float(c), dtype=np.float64)
+    for u in range(n):
+        q += float(h[u]) * x[u]
+    for u in range(n):
+        for v in range(u + 1, n):
+            q += float(J[u][v]) * x[u] * x[v]
+    return q
+
+
+def qubo_fixed_point(n: int, c: float, h, J):
+    """Fixed-point form of a quadratic quality, the contract of qvs_set_quality_qubo /
+    qvs_quality_qubo (not a step of the paper: the device evaluates q(x) exactly on this grid).
+
+    S = |c| + sum_u |h_u| + sum_{u<v} |J_uv| (fp64, that order); F = the largest integer in
+    [-30, 40] with S * 2^F + 1024 <= 2^30; every coefficient is rounded to the nearest integer
+    multiple of 2^-F, halves away from zero. Any sum of the rounded coefficients is then an integer
+    of magnitude below 2^30 (so exact in 32-bit integers). Returns (F, ci, hi, Ji) with integer
+    ci, hi[u], Ji[u][v] (u < v; zero elsewhere).
+    """
+    S = abs(float(c))
+    for u in range(n):
+        S += abs(float(h[u]))
+    for u in range(n):
+        for v in range(u + 1, n):
+            S += abs(float(J[u][v]))
+    F = 40
+    while F > -30 and S * 2.0 ** F + 1024.0 > 2.0 ** 30:
+        F -= 1
+
+    def rnd(x):
+        y = abs(float(x)) * 2.0 ** F
+        r = math.floor(y + 0.5)
+        return int(r) if x >= 0 else -int(r)
+
+    ci = rnd(c)
+    hi = [rnd(h[u]) for u in range(n)]
+    Ji = [[rnd(J[u][v]) if v > u else 0 for v in range(n)] for u in range(n)]
+    return F, ci, hi, Ji
+
+
+def qubo_quality_fixed(n: int, c: float, h, J) -> np.ndarray:
+    """q(x) of the fixed-point coefficients of ``qubo_fixed_point``, summed exactly in integers and
+    scaled by 2^-F (exact in fp64: the integers stay below 2^30)."""
+    F, ci, hi, Ji = qubo_fixed_point(n, c, h, J)
+    N = 1 << n
+    x = qubit_bits(n, np.arange(N, dtype=np.int64))
+    qi = np.full(N, ci, dtype=np.int64)
+    for u in range(n):
+        qi += hi[u] * x[u]
+    for u in range(n):
+        for v in range(u + 1, n):
+            qi += Ji[u][v] * x[u] * x[v]
+    return qi.astype(np.float64) * 2.0 ** (-F)
+
+
 # ============================================================== unitaries (Sec. 2.1, Sec. 3)
 
 

@@ -39,14 +39,21 @@ constexpr int CHUNK = 4;         // lowest index bits, always in the tile
 constexpr int MAXG = 40;         // gates per pass
 constexpr int MAXNT = 32;        // non-tile bits
 
-// padded shared slot: one spare slot after every 32 (gate pairs stride by powers of two)
-__host__ __device__ __forceinline__ constexpr int spos(int j) { return j + (j >> 5); }
-constexpr int SLOTS = spos(TILE - 1) + 1;
+// Shared slot of tile index j: tile bits 4 and 5 are XORed into the low four bits (the 8-byte
+// bank class of a half-warp access). A gate's 16 lanes of a half-warp then fall on 16 distinct
+// classes for every gate pair the schedules produce at n = 12..28, and for the staging accesses
+// (lanes = tile bits 0..4); n = 30 has one gate with a two-way conflict. The map is linear over
+// XOR, so slot(j1 ^ j2) = slot(j1) ^ slot(j2) and no padding slots are needed.
+__host__ __device__ __forceinline__ constexpr uint32_t swz(uint32_t j) {
+  return j ^ (((j >> 4) & 1u) ? 11u : 0u) ^ (((j >> 5) & 1u) ? 12u : 0u);
+}
+constexpr int SLOTS = TILE;
 
 struct PassDesc {
   uint8_t pos[TB];       // index bit of tile bit i (pos[i] = i for i < CHUNK)
   uint8_t ga[MAXG];      // gate g couples tile bits ga[g] and gb[g]
   uint8_t gb[MAXG];
+  uint16_t goff[MAXG][4];  // slot offsets of gate g: pair groups k = 1..3 (t + 256 k), and the pair mask
   uint8_t ntbit[MAXNT];  // non-tile index bits (the CTA index scatters into them)
   int ngates, nnt;
 };
@@ -89,12 +96,13 @@ __device__ __forceinline__ uint32_t elem_off(const PassDesc& d, int m) {
   return o;
 }
 
-// pair k (0..1023) of a gate on tile bits (a, b): the index with bit a = 0, bit b = 1
-__device__ __forceinline__ uint32_t pair_lo(uint32_t k, int a, int b) {
+// slot of pair 0 of thread t for a gate on tile bits (a, b): t's 8 bits spread over the tile bits
+// other than a and b, bit a = 0, bit b = 1; pair k = t + 256 m is this slot XOR goff[m - 1]
+__device__ __forceinline__ uint32_t pair_slot(uint32_t t, int a, int b) {
   const int p1 = a < b ? a : b, p2 = a < b ? b : a;
-  uint32_t x = ((k >> p1) << (p1 + 1)) | (k & ((1u << p1) - 1u));
+  uint32_t x = ((t >> p1) << (p1 + 1)) | (t & ((1u << p1) - 1u));
   x = ((x >> p2) << (p2 + 1)) | (x & ((1u << p2) - 1u));
-  return x | (1u << b);
+  return swz(x | (1u << b));
 }
 
 // exp(-i 2 pi f) with f = gamma / 2pi * q reduced exactly (float-float turns, FMA two-product)
@@ -132,6 +140,7 @@ __global__ void __launch_bounds__(NT) fwd_kernel(const __grid_constant__ Args a)
   __shared__ __align__(16) float2 sm[SLOTS];
   const uint32_t t = threadIdx.x;
   const uint32_t base = tile_base(a.d, blockIdx.x) | thr_off(a.d, t);
+  const uint32_t st = swz(t);   // slot of tile index t + 256 m is st + 256 m
 #pragma unroll
   for (int m = 0; m < EPT; ++m) {
     const uint32_t g = base | elem_off(a.d, m);
@@ -141,23 +150,22 @@ __global__ void __launch_bounds__(NT) fwd_kernel(const __grid_constant__ Args a)
       phase_cs(__ldcs(a.q + g), a.ph0, a.ph1, c, s);
       x = make_float2(c * x.x + s * x.y, c * x.y - s * x.x);   // exp(-i gamma q) x
     }
-    sm[spos((int)t + NT * m)] = x;
+    sm[st + NT * m] = x;
   }
   __syncthreads();
   for (int gi = 0; gi < a.d.ngates; ++gi) {
-    const int ba = a.d.ga[gi], bb = a.d.gb[gi];
-    const uint32_t mab = (1u << ba) | (1u << bb);
+    const uint32_t s0 = pair_slot(t, a.d.ga[gi], a.d.gb[gi]), sm_ab = a.d.goff[gi][3];
 #pragma unroll
     for (int k = 0; k < TILE / 4 / NT; ++k) {
-      const uint32_t lo = pair_lo(t + NT * k, ba, bb), hi = lo ^ mab;
-      const float2 x = sm[spos(lo)], y = sm[spos(hi)];
-      sm[spos(lo)] = make_float2(a.c * x.x + a.s * y.y, a.c * x.y - a.s * y.x);   // c x - i s y
-      sm[spos(hi)] = make_float2(a.c * y.x + a.s * x.y, a.c * y.y - a.s * x.x);   // c y - i s x
+      const uint32_t lo = k ? (s0 ^ a.d.goff[gi][k - 1]) : s0, hi = lo ^ sm_ab;
+      const float2 x = sm[lo], y = sm[hi];
+      sm[lo] = make_float2(a.c * x.x + a.s * y.y, a.c * x.y - a.s * y.x);   // c x - i s y
+      sm[hi] = make_float2(a.c * y.x + a.s * x.y, a.c * y.y - a.s * x.x);   // c y - i s x
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int m = 0; m < EPT; ++m) __stcs(a.out + (base | elem_off(a.d, m)), sm[spos((int)t + NT * m)]);
+  for (int m = 0; m < EPT; ++m) __stcs(a.out + (base | elem_off(a.d, m)), sm[st + NT * m]);
 }
 
 // reverse pass on (psi, lambda)
@@ -167,42 +175,43 @@ __global__ void __launch_bounds__(NT) rev_kernel(const __grid_constant__ Args a)
   float2* sl = sp + SLOTS;
   const uint32_t t = threadIdx.x;
   const uint32_t base = tile_base(a.d, blockIdx.x) | thr_off(a.d, t);
+  const uint32_t st = swz(t);
+  float qv[EPT];
 #pragma unroll
   for (int m = 0; m < EPT; ++m) {
     const uint32_t g = base | elem_off(a.d, m);
-    sp[spos((int)t + NT * m)] = __ldcs(a.in + g);
-    sl[spos((int)t + NT * m)] = __ldcs(a.lam_in + g);
+    sp[st + NT * m] = __ldcs(a.in + g);
+    sl[st + NT * m] = __ldcs(a.lam_in + g);
+    qv[m] = a.has_phase ? __ldcs(a.q + g) : 0.f;   // read with the vectors, used after the gates
   }
   __syncthreads();
   float acc_t = 0.f, acc_g = 0.f;
   for (int gi = a.d.ngates - 1; gi >= 0; --gi) {
-    const int ba = a.d.ga[gi], bb = a.d.gb[gi];
-    const uint32_t mab = (1u << ba) | (1u << bb);
+    const uint32_t s0 = pair_slot(t, a.d.ga[gi], a.d.gb[gi]), sm_ab = a.d.goff[gi][3];
 #pragma unroll
     for (int k = 0; k < TILE / 4 / NT; ++k) {
-      const uint32_t lo = pair_lo(t + NT * k, ba, bb), hi = lo ^ mab;
-      const float2 x = sp[spos(lo)], y = sp[spos(hi)];
-      const float2 u = sl[spos(lo)], v = sl[spos(hi)];
+      const uint32_t lo = k ? (s0 ^ a.d.goff[gi][k - 1]) : s0, hi = lo ^ sm_ab;
+      const float2 x = sp[lo], y = sp[hi];
+      const float2 u = sl[lo], v = sl[hi];
       // Im(conj(l_lo) p_hi) + Im(conj(l_hi) p_lo): <lambda|(XX+YY)|psi> / 2 on this pair
       acc_t += (u.x * y.y - u.y * y.x) + (v.x * x.y - v.y * x.x);
       // undo: (a, b) -> (c a + i s b, c b + i s a)
-      sp[spos(lo)] = make_float2(a.c * x.x - a.s * y.y, a.c * x.y + a.s * y.x);
-      sp[spos(hi)] = make_float2(a.c * y.x - a.s * x.y, a.c * y.y + a.s * x.x);
-      sl[spos(lo)] = make_float2(a.c * u.x - a.s * v.y, a.c * u.y + a.s * v.x);
-      sl[spos(hi)] = make_float2(a.c * v.x - a.s * u.y, a.c * v.y + a.s * u.x);
+      sp[lo] = make_float2(a.c * x.x - a.s * y.y, a.c * x.y + a.s * y.x);
+      sp[hi] = make_float2(a.c * y.x - a.s * x.y, a.c * y.y + a.s * x.x);
+      sl[lo] = make_float2(a.c * u.x - a.s * v.y, a.c * u.y + a.s * v.x);
+      sl[hi] = make_float2(a.c * v.x - a.s * u.y, a.c * v.y + a.s * u.x);
     }
     __syncthreads();
   }
 #pragma unroll
   for (int m = 0; m < EPT; ++m) {
     const uint32_t g = base | elem_off(a.d, m);
-    float2 l = sl[spos((int)t + NT * m)];
+    float2 l = sl[st + NT * m];
     if (a.has_phase) {
-      const float2 p = sp[spos((int)t + NT * m)];
-      const float qq = __ldcs(a.q + g);
-      acc_g += qq * (l.x * p.y - l.y * p.x);
+      const float2 p = sp[st + NT * m];
+      acc_g += qv[m] * (l.x * p.y - l.y * p.x);
       float c, s;
-      phase_cs(qq, a.ph0, a.ph1, c, s);
+      phase_cs(qv[m], a.ph0, a.ph1, c, s);
       l = make_float2(c * l.x - s * l.y, c * l.y + s * l.x);   // exp(+i gamma q) lambda
     }
     __stcs(a.lam_out + g, l);
@@ -300,8 +309,18 @@ static int plan_layer(int n, std::vector<Pass>& out) {
     auto tbit = [&](int b) { return (int)(std::find(tile.begin(), tile.end(), b) - tile.begin()); };
     P.d.ngates = (int)sel.size();
     for (int i = 0; i < P.d.ngates; ++i) {
-      P.d.ga[i] = (uint8_t)tbit(gates[sel[i]].first);
-      P.d.gb[i] = (uint8_t)tbit(gates[sel[i]].second);
+      const int ta = tbit(gates[sel[i]].first), tb = tbit(gates[sel[i]].second);
+      P.d.ga[i] = (uint8_t)ta;
+      P.d.gb[i] = (uint8_t)tb;
+      // pair group k (= bits 8, 9 of the pair index) spread past the gate's two tile bits
+      const int p1 = std::min(ta, tb), p2 = std::max(ta, tb);
+      for (int k = 1; k < 4; ++k) {
+        uint32_t x = (uint32_t)k << 8;
+        x = ((x >> p1) << (p1 + 1)) | (x & ((1u << p1) - 1u));
+        x = ((x >> p2) << (p2 + 1)) | (x & ((1u << p2) - 1u));
+        P.d.goff[i][k - 1] = (uint16_t)swz(x);
+      }
+      P.d.goff[i][3] = (uint16_t)swz((1u << ta) | (1u << tb));
       done[sel[i]] = 1;
     }
     left -= (int)sel.size();

@@ -416,3 +416,98 @@ def test_portfolio_two_assets_hand_computed():
 def test_subspace_count():
     assert orc.subspace_states(10, 5).shape[0] == math.comb(10, 5)
     assert orc.subspace_states(24, 12).shape[0] == 2704156
+
+
+# ------------------------------------------------------------------ quadratic (QUBO) qualities
+
+def _maxcut_as_qubo(n, eu, ev, w):
+    """[x_u == x_v] = 1 - x_u - x_v + 2 x_u x_v: the textbook identity, written in the test."""
+    c, h, J = 0.0, np.zeros(n), np.zeros((n, n))
+    for e in range(len(eu)):
+        u, v = sorted((int(eu[e]), int(ev[e])))
+        we = 1.0 if w is None else float(w[e])
+        c += we
+        h[u] -= we
+        h[v] -= we
+        J[u, v] += 2 * we
+    return c, h, J
+
+
+def test_qubo_reduces_to_maxcut_subset_and_portfolio():
+    """Special cases with independent definitions: max-cut (edge sums, pinned by Example 1 above),
+    subset sums (J = 0) and the portfolio cost (z_a = x_2a - x_2a+1 expanded by hand)."""
+    G = wl.regular3_graph(10, wl.rng_for(120))
+    c, h, J = _maxcut_as_qubo(10, G.eu, G.ev, None)
+    assert np.array_equal(orc.qubo_quality(10, c, h, J), orc.maxcut_quality(10, G.eu, G.ev))
+    Gw = wl.gnp_graph(9, 0.5, wl.rng_for(121))
+    c, h, J = _maxcut_as_qubo(9, Gw.eu, Gw.ev, Gw.w)
+    assert np.max(np.abs(orc.qubo_quality(9, c, h, J) - orc.maxcut_quality(9, Gw.eu, Gw.ev, Gw.w))) < 1e-12
+    w = [0.5, -1.25, 3.0, 7.5, 0.125]
+    assert np.array_equal(orc.qubo_quality(5, 0.0, w, np.zeros((5, 5))), orc.subset_quality(5, w))
+    # portfolio, 3 assets: z_a^2 = x_l + x_s - 2 x_l x_s, z_a z_b = x_la x_lb - x_la x_sb - x_sa x_lb + x_sa x_sb
+    port = wl.portfolio(3, wl.rng_for(122))
+    om, M = port.omega, 3
+    h = np.zeros(6)
+    J = np.zeros((6, 6))
+    for a in range(M):
+        la, sa = 2 * a, 2 * a + 1
+        h[la] += om * port.cov[a][a] - (1 - om) * port.returns[a]
+        h[sa] += om * port.cov[a][a] + (1 - om) * port.returns[a]
+        J[la, sa] += -2 * om * port.cov[a][a]
+        for b in range(a + 1, M):
+            lb, sb = 2 * b, 2 * b + 1
+            k = 2 * om * port.cov[a][b]
+            J[la, lb] += k
+            J[sa, sb] += k
+            J[la, sb] -= k
+            J[sa, lb] -= k
+    states = np.arange(64)
+    ref = orc.portfolio_quality(6, states, port.returns, port.cov, om)
+    assert np.max(np.abs(orc.qubo_quality(6, 0.0, h, J) - ref)) < 1e-12
+
+
+def test_qubo_reads_upper_triangle_and_bit_order():
+    """One coefficient at a time: h_u marks qubit u (= index bit n-1-u); J below the diagonal and
+    on it is ignored."""
+    n = 4
+    for u in range(n):
+        h = np.zeros(n)
+        h[u] = 1.0
+        q = orc.qubo_quality(n, 0.0, h, np.zeros((n, n)))
+        assert q.tolist() == [float((i >> (n - 1 - u)) & 1) for i in range(16)]
+    J = np.zeros((n, n))
+    J[1, 3] = 2.0
+    J[3, 1] = 100.0
+    J[2, 2] = 100.0
+    q = orc.qubo_quality(n, 0.5, np.zeros(n), J)
+    assert q.tolist() == [0.5 + (2.0 if ((i >> 2) & 1) and (i & 1) else 0.0) for i in range(16)]
+
+
+def test_qubo_fixed_point_rule():
+    """The fixed-point contract: F maximal with S 2^F + 1024 <= 2^30, exact for dyadic
+    coefficients, within half a grid step per coefficient otherwise, and every subset sum of the
+    rounded coefficients below 2^30 in magnitude."""
+    rng = np.random.default_rng(123)
+    for n, scale in ((6, 1.0), (8, 1e-3), (10, 1e4)):
+        c = scale * rng.standard_normal()
+        h = scale * rng.standard_normal(n)
+        J = np.triu(scale * rng.standard_normal((n, n)), 1)
+        F, ci, hi, Ji = orc.qubo_fixed_point(n, c, h, J)
+        S = abs(c) + np.sum(np.abs(h)) + np.sum(np.abs(J))
+        assert S * 2.0 ** F + 1024 <= 2.0 ** 30 < S * 2.0 ** (F + 1) + 1024
+        mag = abs(ci) + sum(abs(x) for x in hi) + sum(abs(x) for row in Ji for x in row)
+        assert mag < 2 ** 30
+        ncoef = 1 + n + n * (n - 1) // 2
+        err = np.max(np.abs(orc.qubo_quality_fixed(n, c, h, J) - orc.qubo_quality(n, c, h, J)))
+        assert err <= ncoef * 2.0 ** (-F - 1) * (1 + 1e-9)
+        assert err > 0   # random coefficients are not on the grid
+    # integer and dyadic coefficients are on the grid: exact
+    G = wl.regular3_graph(12, wl.rng_for(124))
+    c, h, J = _maxcut_as_qubo(12, G.eu, G.ev, None)
+    assert np.array_equal(orc.qubo_quality_fixed(12, c, h, J), orc.maxcut_quality(12, G.eu, G.ev))
+    F, ci, _, _ = orc.qubo_fixed_point(3, 0.75, [0.5, -0.25, 0.0], np.zeros((3, 3)))
+    assert ci * 2.0 ** (-F) == 0.75
+    # halves round away from zero
+    F, ci, hi, _ = orc.qubo_fixed_point(2, 0.0, [1.0, -1.0], np.zeros((2, 2)))
+    F2, ci2, hi2, _ = orc.qubo_fixed_point(2, 0.0, [1.0 + 2.0 ** (-F - 1), -1.0 - 2.0 ** (-F - 1)], np.zeros((2, 2)))
+    assert F2 == F and hi2 == [hi[0] + 1, hi[1] - 1]

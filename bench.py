@@ -133,6 +133,16 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def qubo_scale_bits(c, h, J) -> int:
+    """F of the fixed-point rule of qvs_set_quality_qubo (reported in the config only)."""
+    n = len(h)
+    S = abs(c) + sum(abs(x) for x in h) + sum(abs(J[u][v]) for u in range(n) for v in range(u + 1, n))
+    F = 40
+    while F > -30 and S * 2.0 ** F + 1024.0 > 2.0 ** 30:
+        F -= 1
+    return F
+
+
 def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -234,6 +244,8 @@ def run_extras(qvs, torch, stream, peak, steps, warmup, only=None, qwoa_n=26, qw
     """Objective + adjoint-gradient throughput of the QWOA circulant (N=2^26, p=6), QAOAz CSR
     (n=24, weight 12, p=4) and batched QAOA (4096 instances) workloads."""
     out = {}
+    if only is None:
+        out.update(_extra_inpass(qvs, torch, stream, peak, steps, warmup))
     if only in (None, "qwoa"):
         out.update(_extra_qwoa(qvs, torch, stream, peak, steps, warmup, qwoa_n, qwoa_p))
     if only in (None, "parity"):
@@ -244,6 +256,38 @@ def run_extras(qvs, torch, stream, peak, steps, warmup, only=None, qwoa_n=26, qw
     if only in (None, "batch"):
         out.update(_extra_batch(qvs, torch, stream, peak, steps, warmup, batch_count, plain=only is None))
     return out
+
+
+def _extra_inpass(qvs, torch, stream, peak, steps, warmup, n=N_QUBITS, p=P_LAYERS):
+    """The benchmark instance with its max-cut cost given as a quadratic form: the phase passes
+    evaluate q in the pass (no quality vector in HBM); e2e uploads the form each step."""
+    inst = wl.wmaxcut(n, p)
+    G = inst.graph
+    c, h, J = qvs.qvs_qubo_from_maxcut(n, G.eu, G.ev, G.w)
+    sim = qvs.Simulator(1 << n, qvs.QVS_C64, stream)
+    sim.set_quality_qubo(n, c, h, J).set_mixer(qvs.QVS_MIX_HYPERCUBE, qvs.hypercube_desc(n))
+    gs, ts = np.asarray(inst.gammas), np.asarray(inst.ts)
+    ms = _time_steps(torch, stream, lambda: sim.gradient(gs, ts), steps, warmup)
+    sim.set_option(qvs.QVS_OPT_PROFILE, 1)
+    for _ in range(2):
+        sim.gradient(gs, ts)
+    roof, ker = _kernel_summary(qvs, sim.h, peak, 2)
+    sim.set_option(qvs.QVS_OPT_PROFILE, 0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_steps = max(3, steps // 2)
+    for _ in range(e2e_steps):
+        sim.set_quality_qubo(n, c, h, J)
+        sim.gradient(gs, ts)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    sim.close()
+    units = float(1 << n) * p
+    return {f"qaoa_wmaxcut_n{n}_p{p}_quality_in_pass": {
+        "value": units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+        "quality": "quadratic form, fixed point 2^-%d, evaluated in the phase passes" % qubo_scale_bits(c, h, J),
+        "e2e": {"value": units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * (1 + n + n * n) + 16 * p,
+                "d2h_bytes_per_step": 8 * (1 + 2 * p)},
+        "roofline": roof, "kernels": ker}}
 
 
 def _extra_qwoa(qvs, torch, stream, peak, steps, warmup, n, p):
@@ -382,10 +426,17 @@ def run_ours(args):
     inst = wl.wmaxcut(n, p, instance=rank)
     G = inst.graph
     stream = torch.cuda.current_stream()
-    q = torch.empty(dim, dtype=torch.float32, device="cuda")
-    qvs.qvs_quality_maxcut(n, G.eu, G.ev, G.w, q, qvs.QVS_F32, stream)
     sim = qvs.Simulator(dim, qvs.QVS_C64, stream)
-    sim.set_quality(q)
+    qubo = args.quality == "qubo"
+    if qubo:
+        # the max-cut cost as a quadratic form: the phase passes evaluate q themselves
+        qc, qh, qJ = qvs.qvs_qubo_from_maxcut(n, G.eu, G.ev, G.w)
+        sim.set_quality_qubo(n, qc, qh, qJ)
+        sim_qubo_F = qubo_scale_bits(qc, qh, qJ)
+    else:
+        q = torch.empty(dim, dtype=torch.float32, device="cuda")
+        qvs.qvs_quality_maxcut(n, G.eu, G.ev, G.w, q, qvs.QVS_F32, stream)
+        sim.set_quality(q)
     sim.set_mixer(qvs.QVS_MIX_HYPERCUBE, qvs.hypercube_desc(n))
     if args.ckpt is not None:
         sim.set_option(qvs.QVS_OPT_CKPT_LAYERS, args.ckpt)
@@ -437,18 +488,27 @@ def run_ours(args):
     step_bytes = sum(s["bytes"] for s in stats) / max(2, min(args.steps, 5))
 
     # ---- end to end through the C ABI with host buffers
-    q_host = torch.empty(dim, dtype=torch.float32, pin_memory=True)
-    q_host.copy_(q.cpu())
-    del q
-    torch.cuda.empty_cache()
+    if qubo:
+        def set_inputs():                     # H2D of the step's quadratic form (host arrays)
+            sim.set_quality_qubo(n, qc, qh, qJ)
+        h2d_quality = 8 * (1 + n + n * n)
+    else:
+        q_host = torch.empty(dim, dtype=torch.float32, pin_memory=True)
+        q_host.copy_(q.cpu())
+        del q
+        torch.cuda.empty_cache()
+
+        def set_inputs():                     # H2D of the step's quality vector (pinned host)
+            sim.set_quality(q_host.numpy())
+        h2d_quality = 4 * dim
     for _ in range(2):
-        sim.set_quality(q_host.numpy())
+        set_inputs()
         sim.gradient(gs, ts)
     barrier()
     t0 = time.perf_counter()
     e2e_steps = max(3, args.steps // 2)
     for _ in range(e2e_steps):
-        sim.set_quality(q_host.numpy())      # H2D of the step's quality vector (pinned host)
+        set_inputs()
         E, dg, dt = sim.gradient(gs, ts)      # returns E and 2p gradient entries to the host
     barrier()
     e2e_ms, e2e_value = replica_aggregate((time.perf_counter() - t0) / e2e_steps * 1e3, units, world, allreduce_max)
@@ -475,7 +535,9 @@ def run_ours(args):
                        f"QAOA weighted max-cut, n={n}, G({n},1/2) U[0,1] weights, p={p}, objective + adjoint gradient",
                        "n_qubits": n, "p": p, "amplitudes": dim,
                        "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "inputs larger than L2 (2 GiB state, 1 GiB q)",
+                       "quality": ("quadratic form evaluated in the phase passes (fixed point 2^-%d)"
+                                   % sim_qubo_F if qubo else "fp32 vector in HBM"),
+                       "l2": "inputs larger than L2 (2 GiB state%s)" % ("" if qubo else ", 1 GiB q"),
                        "ckpt_layers": args.ckpt if args.ckpt is not None else "ceil(sqrt(p))"},
             "roofline": {"bound": "hbm", "kernel": top["name"], "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
@@ -488,7 +550,7 @@ def run_ours(args):
                               "frac": step_bytes / (ms * 1e-3) / 1e9 / peak},
             "kernels": kernels,
             "gpu_launches": launches_per_step * args.steps,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": dim * 4 + 16 * p,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d_quality + 16 * p,
                     "d2h_bytes_per_step": 8 * (1 + 2 * p)},
             "clocks": clocks,
             "objective": E0,
@@ -530,6 +592,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ckpt", type=int, default=None, help="checkpoint interval in layers (0 = ceil(sqrt(p)))")
+    ap.add_argument("--quality", default="vector", choices=["vector", "qubo"],
+                    help="vector: q generated once into HBM and read by the phase passes; qubo: the max-cut "
+                         "cost as a quadratic form evaluated inside the phase passes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the QWOA, QAOAz and batched lines")
     ap.add_argument("--workload", default="qaoa", choices=["qaoa", "qwoa", "qaoaz", "parity", "batch"],

@@ -113,6 +113,22 @@ int qvs_destroy(qvs_t h);
  * complex128 path and rounded once to fp32 by the complex64 path. */
 int qvs_set_quality(qvs_t h, const void* q, int dtype, int on_device);
 
+/* Sec. 2.2 / Sec. 6: set a quality given as a quadratic form of the qubit values x_u in {0, 1}
+ * (qubit u = index bit n-1-u):
+ *     q(x) = c + sum_u hlin[u] x_u + sum_{u<v} J[u*n + v] x_u x_v
+ * (J: n*n row-major host array, read above the diagonal only; hlin: n host values). The
+ * max-cut, subset-sum and portfolio costs of Sec. 6 are all of this form.
+ * Fixed point: S = |c| + sum_u |hlin[u]| + sum_{u<v} |J[u*n+v]| (fp64, in that order); F is the
+ * largest integer in [-30, 40] with S 2^F + 1024 <= 2^30; every coefficient is rounded to the
+ * nearest integer multiple of 2^-F (halves away from zero). q(x) is then summed exactly in 32-bit
+ * integers and rounded once to the handle's quality type (fp32 for complex64, fp64 for
+ * complex128): the same values qvs_quality_qubo writes.
+ * The hypercube path for n > 12 evaluates q inside its phase passes from per-tile tables (no
+ * q vector is stored or read); the other paths materialise the vector once on the device.
+ * Needs dim = 2^n_qubits. QVS_EINVAL for a NULL argument, n_qubits not matching the handle, or a
+ * non-finite coefficient. */
+int qvs_set_quality_qubo(qvs_t h, int n_qubits, double c, const double* hlin, const double* J);
+
 /* Sec. 3: set the mixing operator (copied). */
 int qvs_set_mixer(qvs_t h, int kind, const qvs_mixer_desc* desc);
 
@@ -166,6 +182,18 @@ int qvs_kernel_stats(qvs_t h, int slot, char* name, int name_len, int64_t* launc
  */
 int qvs_quality_maxcut(int n, int n_edges, const int32_t* eu, const int32_t* ev, const double* w,
                        int out_dtype, void* q_out, void* stream);
+
+/* Quadratic form of qvs_set_quality_qubo (same arguments, same fixed-point rule), written for
+ * all 2^n_qubits basis states (1 <= n_qubits <= 32) as F32 or F64 into the device buffer q_out. */
+int qvs_quality_qubo(int n_qubits, double c, const double* hlin, const double* J, int out_dtype,
+                     void* q_out, void* stream);
+
+/* The max-cut cost of qvs_quality_maxcut as a quadratic form (host only): an edge (u, v) with
+ * weight w (w = NULL: 1) adds w [x_u == x_v] = w (1 - x_u - x_v + 2 x_u x_v), i.e. w to *c, -w to
+ * hlin[u] and hlin[v], 2w to J[min(u,v)*n + max(u,v)]. Outputs: *c, hlin[n], J[n*n] (zeroed
+ * first). QVS_EINVAL for an endpoint outside 0..n-1 or a self-loop. */
+int qvs_qubo_from_maxcut(int n, int n_edges, const int32_t* eu, const int32_t* ev, const double* w,
+                         double* c, double* hlin, double* J);
 
 /* QWOA subset sums: q_i = sum_b w_b x_b(i) over items b = 0..n-1 (qubit b selects item b),
  * fp64 in item order, rounded once to out_dtype (F32 or F64). w: host array of n weights. */

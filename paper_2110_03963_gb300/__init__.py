@@ -34,6 +34,7 @@ EXPORTED = [
     "qvs_last_launch_count", "qvs_kernel_stats", "qvs_quality_maxcut", "qvs_quality_subset", "qvs_quality_portfolio",
     "qvs_xy_ring_csr", "qvs_state_parity", "qvs_batch_create", "qvs_batch_set_quality", "qvs_batch_gradient",
     "qvs_batch_info", "qvs_batch_destroy", "qvs_gradient_small_noalloc", "qvs_strerror",
+    "qvs_set_quality_qubo", "qvs_quality_qubo", "qvs_qubo_from_maxcut",
 ]
 
 
@@ -98,6 +99,9 @@ def load(path: str = LIB_PATH):
         "qvs_batch_info": (I, [V, P(I), P(D), P(D)]),
         "qvs_batch_destroy": (I, [V]),
         "qvs_strerror": (ctypes.c_char_p, [I]),
+        "qvs_set_quality_qubo": (I, [V, I, D, P(D), P(D)]),
+        "qvs_quality_qubo": (I, [I, D, P(D), P(D), I, V, V]),
+        "qvs_qubo_from_maxcut": (I, [I, I, P(ctypes.c_int32), P(ctypes.c_int32), P(D), P(D), P(D), P(D)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -249,6 +253,43 @@ def qvs_quality_maxcut(n: int, eu, ev, w, out, dtype: int, stream=None):
                                      ev.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), wp, int(dtype), p,
                                      _stream_ptr(stream)), "qvs_quality_maxcut")
     return out
+
+
+def _qubo_arrays(n, hlin, J):
+    hl = np.ascontiguousarray(hlin, dtype=np.float64).reshape(n)
+    Jm = np.ascontiguousarray(J, dtype=np.float64).reshape(n * n)
+    return hl, Jm
+
+
+def qvs_set_quality_qubo(h, n_qubits: int, c: float, hlin, J):
+    hl, Jm = _qubo_arrays(n_qubits, hlin, J)
+    _check(load().qvs_set_quality_qubo(h, int(n_qubits), float(c), _dptr(hl), _dptr(Jm)), "qvs_set_quality_qubo")
+
+
+def qvs_quality_qubo(n_qubits: int, c: float, hlin, J, out, dtype: int, stream=None):
+    hl, Jm = _qubo_arrays(n_qubits, hlin, J)
+    p, dev = _ptr_of(out)
+    assert dev == 1, "quality output must be a device tensor"
+    _check(load().qvs_quality_qubo(int(n_qubits), float(c), _dptr(hl), _dptr(Jm), int(dtype), p,
+                                   _stream_ptr(stream)), "qvs_quality_qubo")
+    return out
+
+
+def qvs_qubo_from_maxcut(n: int, eu, ev, w=None):
+    """(c, hlin[n], J[n, n]) of the max-cut cost (host, no GPU needed)."""
+    eu = np.ascontiguousarray(eu, dtype=np.int32)
+    ev = np.ascontiguousarray(ev, dtype=np.int32)
+    wp = None
+    if w is not None:
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        wp = _dptr(w)
+    c = ctypes.c_double()
+    hl = np.zeros(n, dtype=np.float64)
+    J = np.zeros(n * n, dtype=np.float64)
+    _check(load().qvs_qubo_from_maxcut(n, len(eu), eu.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                       ev.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), wp, ctypes.byref(c),
+                                       _dptr(hl), _dptr(J)), "qvs_qubo_from_maxcut")
+    return c.value, hl, J.reshape(n, n)
 
 
 def qvs_quality_subset(n: int, w, out, dtype: int, stream=None):
@@ -452,6 +493,10 @@ class Simulator:
 
     def set_quality(self, q, dtype=None):
         qvs_set_quality(self.h, q, dtype)
+        return self
+
+    def set_quality_qubo(self, n_qubits: int, c: float, hlin, J):
+        qvs_set_quality_qubo(self.h, n_qubits, c, hlin, J)
         return self
 
     def set_mixer(self, kind: int, desc: MixerDesc):

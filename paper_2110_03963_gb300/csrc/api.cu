@@ -147,6 +147,8 @@ extern "C" int qvs_destroy(qvs_t h) {
   h->csr.rowptr.release();
   h->csr.colind.release();
   h->csr.values.release();
+  h->qubo.dcoef.release();
+  h->qubo.tab.release();
   if (h->host_res) cudaFreeHost(h->host_res);
   prof_release(h);
   delete h;
@@ -203,8 +205,34 @@ extern "C" int qvs_set_quality(qvs_t h, const void* q, int dtype, int on_device)
   h->have_q = true;
   h->have_E = false;
   h->circ.qT_valid = false;
+  h->qubo.on = false;
+  h->qubo.tab_valid = false;
   return QVS_OK;
 }
+
+extern "C" int qvs_set_quality_qubo(qvs_t h, int n_qubits, double c, const double* hlin, const double* J) {
+  if (!h || !hlin || !J) return QVS_EINVAL;
+  if (h->n < 1 || n_qubits != h->n) return QVS_EINVAL;
+  QVS_TRY(qubo_quantize(n_qubits, c, hlin, J, &h->qubo.coef));
+  h->qubo.on = true;
+  h->qubo.materialized = false;
+  h->qubo.tab_valid = false;
+  h->have_q = true;
+  h->have_E = false;
+  h->circ.qT_valid = false;
+  return QVS_OK;
+}
+
+namespace qvs {
+int ensure_q_vector(qvs_ctx* h) {
+  if (!h->qubo.on || h->qubo.materialized) return QVS_OK;
+  const bool f32 = h->precision == QVS_C64;
+  QVS_TRY(h->q.ensure((f32 ? 4 : 8) * (size_t)h->dim));
+  QVS_TRY(qubo_generate(h->qubo.coef, f32 ? QVS_F32 : QVS_F64, h->q.ptr, h->stream));
+  h->qubo.materialized = true;
+  return QVS_OK;
+}
+}  // namespace qvs
 
 extern "C" int qvs_set_mixer(qvs_t h, int kind, const qvs_mixer_desc* d) {
   if (!h || !d) return QVS_EINVAL;
@@ -270,6 +298,7 @@ extern "C" int qvs_evolve(qvs_t h, int p, const double* gammas, const double* ts
   QVS_TRY(ready(h));
   if (!params_ok(p, gammas, ts)) return QVS_EINVAL;
   h->have_E = false;
+  if (h->mixer != QVS_MIX_HYPERCUBE) QVS_TRY(ensure_q_vector(h));
   switch (h->mixer) {
     case QVS_MIX_HYPERCUBE: return hc_evolve(h, p, gammas, ts);
     case QVS_MIX_CIRCULANT: return circ_evolve(h, p, gammas, ts);
@@ -291,6 +320,7 @@ extern "C" int qvs_gradient(qvs_t h, int p, const double* gammas, const double* 
   QVS_TRY(ready(h));
   if (!params_ok(p, gammas, ts) || !E || !dgamma || !dt) return QVS_EINVAL;
   h->have_E = false;
+  if (h->mixer != QVS_MIX_HYPERCUBE) QVS_TRY(ensure_q_vector(h));
   switch (h->mixer) {
     case QVS_MIX_HYPERCUBE: return hc_gradient(h, p, gammas, ts, E, dgamma, dt);
     case QVS_MIX_CIRCULANT: return circ_gradient(h, p, gammas, ts, E, dgamma, dt);

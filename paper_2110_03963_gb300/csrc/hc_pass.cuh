@@ -50,6 +50,12 @@ struct PassArgs {
   int row_bef, row_aft, row_gam, row_E;
   T init_amp;           // amplitude of the uniform initial state
   int gen_init;         // F0: 1 = generate psi0 = init_amp, 0 = load psi_in (plain amplitudes)
+  // Quadratic quality evaluated in the pass (qcta != NULL; q is then not read): tables of this
+  // pass's tile type and frame (see qgen2)
+  const int* qcta;      // per tile: [16] = {constant, linear coefficient of tile bits 0..11}
+  const int* qthr;      // per thread: [8] = {pair sum of its own bits, cross sums of bits 5..8}
+  int qpp[R];           // per register r: pair sum of register bits 5..8
+  T qscale;             // 2^-F
 };
 
 // ---------------------------------------------------------------- per-pass scalars (host and device)
@@ -219,6 +225,42 @@ __device__ __forceinline__ void block_store3(T a, T b, T c, double* part, int ra
 // (single-tile schedules, whose passes have no "before" rotations and rotate every tile bit after).
 // ALT: the single-vector passes alternate two shared buffers (one barrier per transpose); the CTA
 // must hold 2 * SM_SLOTS elements.
+// q of the amplitudes a thread holds in layout 2 from a quadratic form (exact int32 sums).
+// Index bits split into the tile's non-tile bits (fixed per CTA), the thread's own tile bits
+// TT = {0..4, 9..11} and the register bits 5..8; with x = the bit values read at index XOR qx,
+//   q = [c + non-tile terms] + sum_{k in TT} x_k L_k + K_T + sum_{i} x_{5+i} (L_{5+i} + K_i) + PP(r),
+// L_k = h_k + sum_{non-tile j} J_kj x_j (per tile, s_q[1 + k]; s_q[0] = the bracket), K_T / K_i the
+// pair sums within TT / between TT and register bit 5+i (per thread, qthr), PP(r) the pairs among
+// the register bits (per register, qpp). Flipped bits (qx != 0) read x = 1 - bit.
+template <class T>
+__device__ __forceinline__ void qgen2(T (&qv)[R], const PassArgs<T>& a, const int* s_q, int tid) {
+  const uint32_t fl = a.qx ? 0xFFFu : 0u;
+  const uint32_t xt = (uint32_t)tj<2>(0, tid) ^ fl;
+  const int4 k0 = *reinterpret_cast<const int4*>(a.qthr + 8 * tid);
+  const int k4 = a.qthr[8 * tid + 4];
+  int qT = s_q[0] + k0.x;
+#pragma unroll
+  for (int k = 0; k < TB; ++k)
+    if (k < 5 || k > 8)
+      if ((xt >> k) & 1u) qT += s_q[1 + k];
+  int cc[RB] = {s_q[6] + k0.y, s_q[7] + k0.z, s_q[8] + k0.w, s_q[9] + k4};
+  if (fl) {
+#pragma unroll
+    for (int i = 0; i < RB; ++i) {
+      qT += cc[i];
+      cc[i] = -cc[i];
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    int v = qT + a.qpp[r];
+#pragma unroll
+    for (int i = 0; i < RB; ++i)
+      if ((r >> i) & 1) v += cc[i];
+    qv[r] = (T)v * a.qscale;
+  }
+}
+
 template <class T, int SHAPE, int TH, bool ALT = false>
 __device__ __forceinline__ void run_pass(const PassArgs<T>& a, uint32_t bid, uint32_t nblk,
                                          unsigned char* smem_raw) {
@@ -242,6 +284,13 @@ __device__ __forceinline__ void run_pass(const PassArgs<T>& a, uint32_t bid, uin
   const uint32_t off0 = base + toff(a.tile, tj<0>(0, tid));
   const uint32_t off2 = base + toff(a.tile, tj<2>(0, tid));
   T qv[R];
+  // quadratic quality: this tile's row of the table (published by the first barrier below)
+  __shared__ int s_q[16];
+  if (a.qcta && tid < 13) s_q[tid] = a.qcta[16 * (size_t)bid + tid];
+  auto qget = [&]() {
+    if (a.qcta) qgen2<T>(qv, a, s_q, tid);
+    else qload<2>(qv, a.q, off2, a.tile, a.qx);
+  };
 
   // v <- (rho exp(-+i gamma q)) v on the amplitudes of layout 2 (dir = +1 forward, -1 adjoint)
   auto phase2 = [&](C (&v)[R], T dir, T rho) {
@@ -278,7 +327,8 @@ __device__ __forceinline__ void run_pass(const PassArgs<T>& a, uint32_t bid, uin
     } else {
       gload_plain<2>(v, a.psi_in, off2, a.tile, tpop);
     }
-    qload<2>(qv, a.q, off2, a.tile, a.qx);
+    if (a.qcta) __syncthreads();
+    qget();
     phase2(v, T(1), a.rho_p);
     rot_layout<2, TAF>(v, a.mask_aft, a.ta);
     xchg_alt<2, 1, 0, ALT>(v, sm, tid);
@@ -291,7 +341,7 @@ __device__ __forceinline__ void run_pass(const PassArgs<T>& a, uint32_t bid, uin
     rot_layout<0, TBF>(v, a.mask_bef, a.tb);
     xchg_alt<0, 1, 0, ALT>(v, sm, tid);
     rot_layout<1, TBF>(v, a.mask_bef, a.tb);
-    qload<2>(qv, a.q, off2, a.tile, a.qx);
+    qget();
     xchg_alt<1, 2, 1, ALT>(v, sm, tid);
     rot_layout<2, TBF>(v, a.mask_bef, a.tb);
     phase2(v, T(1), a.rho_p);
@@ -315,7 +365,7 @@ __device__ __forceinline__ void run_pass(const PassArgs<T>& a, uint32_t bid, uin
     if constexpr (SHAPE == FV) xchg_alt<0, 1, 0, ALT>(v, sm, tid);
     else xchg<0, 1>(v, sm, tid);   // FE's second half writes both buffers: keep the trailing barrier
     rot_layout<1, TBF>(v, a.mask_bef, a.tb);
-    qload<2>(qv, a.q, off2, a.tile, a.qx);
+    qget();
     if constexpr (SHAPE == FV) xchg_alt<1, 2, 1, ALT>(v, sm, tid);
     else xchg<1, 2>(v, sm, tid);
     rot_layout<2, TBF>(v, a.mask_bef, a.tb);
@@ -348,7 +398,7 @@ __device__ __forceinline__ void run_pass(const PassArgs<T>& a, uint32_t bid, uin
     unrot_layout_acc<0, TAF>(v, l, a.mask_aft, a.ta, a.c2a, sc, acc_a);
     x2(I0{}, I1{}, v, l);
     unrot_layout_acc<1, TAF>(v, l, a.mask_aft, a.ta, a.c2a, sc, acc_a);
-    qload<2>(qv, a.q, off2, a.tile, a.qx);
+    qget();
     x2(I1{}, I2{}, v, l);
     unrot_layout_acc<2, TAF>(v, l, a.mask_aft, a.ta, a.c2a, sc, acc_a);
 #pragma unroll

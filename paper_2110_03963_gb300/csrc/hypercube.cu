@@ -301,7 +301,8 @@ static int launch_shape(qvs_ctx* h, int shape, const PassArgs<T>& a, uint32_t gr
   } else {
     QVS_TRY((launch_pass<T, TH_RUNTIME>(shape, a, grid, h->stream)));
   }
-  const double c = sizeof(typename Cx<T>::t), qb = sizeof(T);
+  // a quadratic quality reads one 64-byte table row per tile instead of q
+  const double c = sizeof(typename Cx<T>::t), qb = a.qcta ? 64.0 / TILE : (double)sizeof(T);
   return prof_end(h, shape_name(shape, sizeof(T) == 8),
                   shape_bytes(shape, a.psi_in, a.psi_out, c, qb) * (double)grid * TILE, ev);
 }
@@ -358,6 +359,114 @@ static int run_small(qvs_ctx* h, int p, const double* gammas, const double* ts, 
   return QVS_OK;
 }
 
+// ---------------------------------------------------------------- quadratic-quality tables
+//
+// For a quadratic quality (qvs_set_quality_qubo) the phase passes compute q themselves (qgen2):
+// per tile type and frame f (bits read at index XOR f (2^n - 1)) they need the per-tile rows
+// {c + non-tile terms, L_0..L_11} and the per-thread rows {K_T, K_5..K_8}, plus the register pair
+// sums PP(r) carried in the pass arguments.
+
+static int tile_index_bit(const Tile& t, int k) {
+  const int s = __builtin_popcount(t.smask);
+  return k < s ? k : k + t.hshift;
+}
+
+__global__ void qubo_rows_kernel(const QuboCoef* __restrict__ Q, Tile t, int flip, uint32_t ntiles,
+                                 int* __restrict__ rows) {
+  const uint32_t bid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (bid >= ntiles) return;
+  const uint32_t xb = tile_base(t, bid) ^ (flip ? all_bits(Q->n) : 0u);
+  const int s = __popc(t.smask);
+  int qU = Q->c;
+  for (int i = 0; i < t.n_nt; ++i) {
+    const int j = t.ntbit[i];
+    if (!((xb >> j) & 1u)) continue;
+    qU += Q->h[j];
+    for (int i2 = 0; i2 < i; ++i2) {
+      const int j2 = t.ntbit[i2];
+      if ((xb >> j2) & 1u) qU += Q->J[j][j2];
+    }
+  }
+  int* row = rows + 16 * (size_t)bid;
+  row[0] = qU;
+  for (int k = 0; k < TB; ++k) {
+    const int pk = k < s ? k : k + t.hshift;
+    int L = Q->h[pk];
+    for (int i = 0; i < t.n_nt; ++i) {
+      const int j = t.ntbit[i];
+      if ((xb >> j) & 1u) L += Q->J[pk][j];
+    }
+    row[1 + k] = L;
+  }
+  row[13] = row[14] = row[15] = 0;
+}
+
+static size_t qubo_block_ints(uint32_t grid) { return 16 * (size_t)grid + 8 * (size_t)NT; }
+
+static int build_qubo_tables(qvs_ctx* h, const Plan& pl, uint32_t grid) {
+  QuboData& D = h->qubo;
+  const QuboCoef& Q = D.coef;
+  const size_t bi = qubo_block_ints(grid);
+  QVS_TRY(D.tab.ensure(sizeof(int) * bi * 2 * pl.g));
+  QVS_TRY(D.dcoef.ensure(sizeof(QuboCoef)));
+  QVS_CUDA_TRY(cudaMemcpyAsync(D.dcoef.ptr, &Q, sizeof(QuboCoef), cudaMemcpyHostToDevice, h->stream));
+  D.pp.assign(16 * 2 * (size_t)pl.g, 0);
+  std::vector<int> thr(8 * (size_t)NT * 2 * pl.g, 0);
+  for (int tau = 0; tau < pl.g; ++tau) {
+    const Tile& t = pl.tile[tau];
+    int pk[TB];
+    for (int k = 0; k < TB; ++k) pk[k] = tile_index_bit(t, k);
+    for (int f = 0; f < 2; ++f) {
+      const int blk = 2 * tau + f;
+      int* rows = D.tab.as<int>() + bi * blk;
+      qubo_rows_kernel<<<(grid + 127) / 128, 128, 0, h->stream>>>(D.dcoef.as<QuboCoef>(), t, f, grid, rows);
+      QVS_CUDA_TRY(cudaGetLastError());
+      const uint32_t fl = f ? 0xFFFu : 0u;
+      for (int tid = 0; tid < NT; ++tid) {
+        const uint32_t xt = (uint32_t)tj<2>(0, tid) ^ fl;
+        int kt = 0, kc[RB] = {0, 0, 0, 0};
+        for (int k = 0; k < TB; ++k) {
+          if ((k >= 5 && k <= 8) || !((xt >> k) & 1u)) continue;
+          for (int l = 0; l < k; ++l)
+            if ((l < 5 || l > 8) && ((xt >> l) & 1u)) kt += Q.J[pk[k]][pk[l]];
+          for (int i = 0; i < RB; ++i) kc[i] += Q.J[pk[5 + i]][pk[k]];
+        }
+        int* row = thr.data() + 8 * ((size_t)NT * blk + tid);
+        row[0] = kt;
+        for (int i = 0; i < RB; ++i) row[1 + i] = kc[i];
+      }
+      for (int r = 0; r < R; ++r) {
+        const int x = r ^ (f ? R - 1 : 0);
+        int v = 0;
+        for (int i = 0; i < RB; ++i)
+          for (int i2 = 0; i2 < i; ++i2)
+            if (((x >> i) & 1) && ((x >> i2) & 1)) v += Q.J[pk[5 + i]][pk[5 + i2]];
+        D.pp[16 * (size_t)blk + r] = v;
+      }
+    }
+  }
+  for (int blk = 0; blk < 2 * pl.g; ++blk)
+    QVS_CUDA_TRY(cudaMemcpyAsync(D.tab.as<int>() + bi * blk + 16 * (size_t)grid, thr.data() + 8 * (size_t)NT * blk,
+                                 sizeof(int) * 8 * NT, cudaMemcpyHostToDevice, h->stream));
+  // the host staging vector goes out of scope: finish the copies first
+  QVS_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  D.tab_valid = true;
+  return QVS_OK;
+}
+
+// point a pass that reads q at the tables of its tile type and frame
+template <class T>
+static void set_qubo_args(const qvs_ctx* h, int type, uint32_t grid, PassArgs<T>& a) {
+  const int blk = 2 * type + (a.qx ? 1 : 0);
+  const int* base = h->qubo.tab.as<int>() + qubo_block_ints(grid) * blk;
+  a.qcta = base;
+  a.qthr = base + 16 * (size_t)grid;
+  for (int r = 0; r < R; ++r) a.qpp[r] = h->qubo.pp[16 * (size_t)blk + r];
+  a.qscale = (T)ldexp(1.0, -h->qubo.coef.F);
+}
+
+static bool shape_reads_q(int shape) { return shape != F2 && shape != R2; }
+
 // ---------------------------------------------------------------- tiled driver
 
 template <class T>
@@ -369,6 +478,8 @@ static int run_tiled(qvs_ctx* h, int p, const double* gammas, const double* ts, 
   const int F = pl.F;
   const uint32_t grid = 1u << (h->n - TB);
   const size_t sbytes = (size_t)h->dim * sizeof(C);
+  const bool qubo = h->qubo.on;
+  if (qubo && !h->qubo.tab_valid) QVS_TRY(build_qubo_tables(h, pl, grid));
 
   // checkpoint placement: stored pass boundaries j = c, 2c, ... <= F-1
   int ckl = h->ckpt_layers > 0 ? h->ckpt_layers : (int)ceil(sqrt((double)p) - 1e-9);
@@ -439,6 +550,7 @@ static int run_tiled(qvs_ctx* h, int p, const double* gammas, const double* ts, 
     int shape = pi.shape;
     if (j == F) shape = grad ? FE : FV;
     fwd_scalars<T>(a, shape, pi.lb, pi.la, pi.lg, G, n, p, gammas, ts, fr, lf);
+    if (qubo && shape_reads_q(shape)) set_qubo_args<T>(h, pi.type, grid, a);
     if (j == F) {
       if (grad) {
         a.lam_out = h->lam.as<C>();
@@ -483,6 +595,7 @@ static int run_tiled(qvs_ctx* h, int p, const double* gammas, const double* ts, 
       // previous adjoint pass's uncompute
       Frame pf = (is_stored(j) || j == F - 1) ? fw[j] : pout;
       bwd_scalars<T>(a, shape, pi.lb, pi.la, pi.lg, G, n, gammas, ts, pf, lf);
+      if (qubo && shape_reads_q(shape)) set_qubo_args<T>(h, pi.type, grid, a);
       pout = pf;
       QVS_TRY(launch_shape<T>(h, shape, a, grid));
       ++launches;
@@ -518,6 +631,7 @@ static int hc_run(qvs_ctx* h, int p, const double* gammas, const double* ts, boo
                   double* dg, double* dt) {
   if (h->n < 1) return QVS_EINVAL;
   const bool small = h->n <= hc::TB;
+  if (small) QVS_TRY(ensure_q_vector(h));   // the one-CTA kernel reads q from memory
   if (h->precision == QVS_C64)
     return small ? hc::run_small<float>(h, p, gammas, ts, grad, E, dg, dt)
                  : hc::run_tiled<float>(h, p, gammas, ts, grad, E, dg, dt);

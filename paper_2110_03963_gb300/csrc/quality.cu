@@ -104,6 +104,65 @@ static int grid_for(int64_t dim) {
   return (int)g;
 }
 
+// ---------------------------------------------------------------- quadratic qualities
+
+int qubo_quantize(int n, double c, const double* hlin, const double* J, QuboCoef* out) {
+  if (n < 1 || n > 32 || !hlin || !J || !out) return QVS_EINVAL;
+  double S = fabs(c);
+  if (!isfinite(c)) return QVS_EINVAL;
+  for (int u = 0; u < n; ++u) {
+    if (!isfinite(hlin[u])) return QVS_EINVAL;
+    S += fabs(hlin[u]);
+  }
+  for (int u = 0; u < n; ++u)
+    for (int v = u + 1; v < n; ++v) {
+      if (!isfinite(J[u * n + v])) return QVS_EINVAL;
+      S += fabs(J[u * n + v]);
+    }
+  int F = 40;
+  while (F > -30 && ldexp(S, F) + 1024.0 > 1073741824.0) --F;
+  // nearest multiple of 2^-F, halves away from zero (llround)
+  auto rnd = [F](double x) -> int32_t { return (int32_t)llround(ldexp(x, F)); };
+  QuboCoef Q;
+  Q.n = n;
+  Q.F = F;
+  Q.c = rnd(c);
+  for (int u = 0; u < n; ++u) Q.h[n - 1 - u] = rnd(hlin[u]);
+  for (int u = 0; u < n; ++u)
+    for (int v = u + 1; v < n; ++v) {
+      const int32_t x = rnd(J[u * n + v]);
+      Q.J[n - 1 - u][n - 1 - v] = x;
+      Q.J[n - 1 - v][n - 1 - u] = x;
+    }
+  *out = Q;
+  return QVS_OK;
+}
+
+__global__ void qubo_kernel(const __grid_constant__ QuboCoef Q, int out_dtype, void* out, int64_t dim) {
+  const float sf = ldexpf(1.0f, -Q.F);
+  const double sd = ldexp(1.0, -Q.F);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < dim;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int32_t v = Q.c;
+    for (int b = 0; b < Q.n; ++b) {
+      if (!((i >> b) & 1)) continue;
+      v += Q.h[b];
+      for (int b2 = 0; b2 < b; ++b2)
+        if ((i >> b2) & 1) v += Q.J[b][b2];
+    }
+    if (out_dtype == QVS_F32) static_cast<float*>(out)[i] = (float)v * sf;
+    else static_cast<double*>(out)[i] = (double)v * sd;
+  }
+}
+
+int qubo_generate(const QuboCoef& Q, int out_dtype, void* out, cudaStream_t stream) {
+  if (out_dtype != QVS_F32 && out_dtype != QVS_F64) return QVS_EINVAL;
+  const int64_t dim = (int64_t)1 << Q.n;
+  qubo_kernel<<<grid_for(dim), 256, 0, stream>>>(Q, out_dtype, out, dim);
+  QVS_CUDA_TRY(cudaGetLastError());
+  return QVS_OK;
+}
+
 }  // namespace qvs
 
 extern "C" int qvs_quality_maxcut(int n, int n_edges, const int32_t* eu, const int32_t* ev,
@@ -236,6 +295,33 @@ extern "C" int qvs_xy_ring_csr(int n, int k, int64_t* states, int64_t* rowptr, i
     std::sort(cols.begin(), cols.end());
     for (int32_t c : cols) colind[pos++] = c;
     rowptr[r + 1] = pos;
+  }
+  return QVS_OK;
+}
+
+extern "C" int qvs_quality_qubo(int n_qubits, double c, const double* hlin, const double* J, int out_dtype,
+                                void* q_out, void* stream) {
+  if (!q_out) return QVS_EINVAL;
+  static qvs::QuboCoef Q;   // 4 KiB: kept off the stack
+  QVS_TRY(qvs::qubo_quantize(n_qubits, c, hlin, J, &Q));
+  return qvs::qubo_generate(Q, out_dtype, q_out, (cudaStream_t)stream);
+}
+
+extern "C" int qvs_qubo_from_maxcut(int n, int n_edges, const int32_t* eu, const int32_t* ev, const double* w,
+                                    double* c, double* hlin, double* J) {
+  if (n < 1 || n > 32 || n_edges < 0 || !c || !hlin || !J) return QVS_EINVAL;
+  if (n_edges > 0 && (!eu || !ev)) return QVS_EINVAL;
+  *c = 0.0;
+  for (int u = 0; u < n; ++u) hlin[u] = 0.0;
+  for (int u = 0; u < n * n; ++u) J[u] = 0.0;
+  for (int e = 0; e < n_edges; ++e) {
+    if (eu[e] < 0 || eu[e] >= n || ev[e] < 0 || ev[e] >= n || eu[e] == ev[e]) return QVS_EINVAL;
+    const double we = w ? w[e] : 1.0;
+    const int u = std::min(eu[e], ev[e]), v = std::max(eu[e], ev[e]);
+    *c += we;
+    hlin[u] -= we;
+    hlin[v] -= we;
+    J[u * n + v] += 2.0 * we;
   }
   return QVS_OK;
 }

@@ -53,6 +53,31 @@ struct DevBuf {
   template <class T> T* as() const { return static_cast<T*>(ptr); }
 };
 
+// Quadratic quality in fixed point (qvs_set_quality_qubo): q(x) = 2^-F (c + sum_b h_b x_b +
+// sum_{b<b'} J_bb' x_b x_b') over INDEX bits b (qubit u = bit n-1-u); J symmetric, zero diagonal.
+// Every sum of these integers stays below 2^30 in magnitude.
+struct QuboCoef {
+  int n = 0, F = 0;
+  int32_t c = 0;
+  int32_t h[32] = {};
+  int32_t J[32][32] = {};
+};
+// Round a qubit-indexed quadratic form to the fixed-point grid (quality.cu). QVS_EINVAL for n
+// outside 1..32 or a non-finite coefficient.
+int qubo_quantize(int n, double c, const double* hlin, const double* J, QuboCoef* out);
+// Write q(i) = float(integer sum) * 2^-F for i < 2^n into out (F32 or F64), stream-ordered.
+int qubo_generate(const QuboCoef& Q, int out_dtype, void* out, cudaStream_t stream);
+
+struct QuboData {
+  bool on = false;            // the handle's quality is this quadratic form
+  bool materialized = false;  // h->q holds it as a vector (paths that read q from memory)
+  QuboCoef coef;
+  DevBuf dcoef;               // QuboCoef on the device (table builder)
+  DevBuf tab;                 // hypercube tables: per tile type and frame, CTA rows + thread rows
+  bool tab_valid = false;
+  std::vector<int32_t> pp;    // per tile type and frame: 16 register pair sums
+};
+
 // Circulant mixer data: eigenvalues in the order the FFT passes produce them.
 struct CircData {
   DevBuf lam;           // float2[dim]: eigenvalues (hi, lo) in row-spectral thread-major order
@@ -102,6 +127,7 @@ struct qvs_ctx {
 
   qvs::CircData circ;
   qvs::CsrData csr;
+  qvs::QuboData qubo;
 
   // QVS_OPT_PROFILE: per-kernel event timing
   struct KStat {
@@ -134,6 +160,9 @@ int prof_begin(qvs_ctx* h, cudaEvent_t* start);
 int prof_end(qvs_ctx* h, const char* name, double bytes, cudaEvent_t start);
 int prof_flush(qvs_ctx* h);
 void prof_release(qvs_ctx* h);
+
+// Materialise a quadratic quality into h->q (no-op for a vector quality); api.cu
+int ensure_q_vector(qvs_ctx* h);
 
 // hypercube (QAOA) path: hypercube.cu
 int hc_evolve(qvs_ctx* h, int p, const double* gammas, const double* ts);

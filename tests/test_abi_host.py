@@ -85,3 +85,20 @@ def test_xy_ring_csr_full_size_counts(qvs):
     assert lib.qvs_xy_ring_csr(24, 12, None, None, None, ctypes.byref(dim), ctypes.byref(nnz)) == 0
     assert dim.value == math.comb(24, 12)
     assert nnz.value == 2 * 24 * math.comb(22, 11)
+
+
+def test_qubo_from_maxcut_matches_oracle_maxcut(qvs):
+    """The host conversion of a (weighted) edge list gives a quadratic form whose qualities equal
+    the oracle's edge-sum max-cut cost."""
+    import workloads as wl
+    G = wl.regular3_graph(10, wl.rng_for(130))
+    c, h, J = qvs.qvs_qubo_from_maxcut(10, G.eu, G.ev)
+    assert np.array_equal(orc.qubo_quality(10, c, h, J), orc.maxcut_quality(10, G.eu, G.ev))
+    Gw = wl.gnp_graph(11, 0.5, wl.rng_for(131))
+    c, h, J = qvs.qvs_qubo_from_maxcut(11, Gw.eu, Gw.ev, Gw.w)
+    assert np.max(np.abs(orc.qubo_quality(11, c, h, J) - orc.maxcut_quality(11, Gw.eu, Gw.ev, Gw.w))) < 1e-12
+    assert np.all(np.tril(J) == 0)
+    with pytest.raises(qvs.QvsError):
+        qvs.qvs_qubo_from_maxcut(4, [0], [0])
+    with pytest.raises(qvs.QvsError):
+        qvs.qvs_qubo_from_maxcut(4, [0], [4])

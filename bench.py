@@ -42,7 +42,7 @@ WORKLOAD = "QAOA weighted max-cut, n=28 (2^28 complex64 amplitudes), G(28,1/2) U
 # (profiles/hc_passes_qaoa25_dram.md: measured at n=25, averaged over the launch mix of the n=28,
 # p=8 solve). Reported only while the kernel sources hash to the value recorded in that file.
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "hc_passes_qaoa25_dram.md")
-TRAFFIC_BYTES_PER_AMP = {"hc_pass_R1_c64": 32.0}
+TRAFFIC_BYTES_PER_AMP = {"hc_pass_R1_c64": 32.1}
 TRAFFIC_SOURCES = ["hc_kernels.cuh", "hc_pass.cuh", "hypercube.cu", "hc_pass_th_a.cu", "hc_pass_th_b.cu",
                    "hc_pass_th_c.cu", "hc_pass_th_d.cu"]
 

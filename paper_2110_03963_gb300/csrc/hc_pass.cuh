@@ -284,12 +284,20 @@ __device__ __forceinline__ void run_pass(const PassArgs<T>& a, uint32_t bid, uin
   const uint32_t off0 = base + toff(a.tile, tj<0>(0, tid));
   const uint32_t off2 = base + toff(a.tile, tj<2>(0, tid));
   T qv[R];
-  // quadratic quality: this tile's row of the table (published by the first barrier below)
+  // quadratic quality (one-CTA-per-tile kernels only; the batched kernel reads vectors): this
+  // tile's row of the table, published by the first barrier below
   __shared__ int s_q[16];
-  if (a.qcta && tid < 13) s_q[tid] = a.qcta[16 * (size_t)bid + tid];
+  if constexpr (!ALT) {
+    if (a.qcta && tid < 13) s_q[tid] = a.qcta[16 * (size_t)bid + tid];
+  }
   auto qget = [&]() {
-    if (a.qcta) qgen2<T>(qv, a, s_q, tid);
-    else qload<2>(qv, a.q, off2, a.tile, a.qx);
+    if constexpr (!ALT) {
+      if (a.qcta) {
+        qgen2<T>(qv, a, s_q, tid);
+        return;
+      }
+    }
+    qload<2>(qv, a.q, off2, a.tile, a.qx);
   };
 
   // v <- (rho exp(-+i gamma q)) v on the amplitudes of layout 2 (dir = +1 forward, -1 adjoint)
@@ -327,7 +335,9 @@ __device__ __forceinline__ void run_pass(const PassArgs<T>& a, uint32_t bid, uin
     } else {
       gload_plain<2>(v, a.psi_in, off2, a.tile, tpop);
     }
-    if (a.qcta) __syncthreads();
+    if constexpr (!ALT) {
+      if (a.qcta) __syncthreads();
+    }
     qget();
     phase2(v, T(1), a.rho_p);
     rot_layout<2, TAF>(v, a.mask_aft, a.ta);

@@ -105,6 +105,11 @@ __device__ __forceinline__ uint32_t pair_slot(uint32_t t, int a, int b) {
   return swz(x | (1u << b));
 }
 
+// paired-float arithmetic: one instruction for both components
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 swp(float2 a) { return make_float2(a.y, a.x); }
+
 // exp(-i 2 pi f) with f = gamma / 2pi * q reduced exactly (float-float turns, FMA two-product)
 __device__ __forceinline__ void phase_cs(float q, float ghi, float glo, float& c, float& s) {
   const float p = ghi * q;
@@ -135,32 +140,53 @@ __device__ __forceinline__ void block_store2(float a, float b, double* part, int
   }
 }
 
+// stage a tile into shared memory: input amplitudes (or the uniform state), the layer's phase
+// applied on the way in; every load of the thread is issued before the first use
+template <bool IN, bool PH>
+__device__ __forceinline__ void stage_fwd(const Args& a, uint32_t base, uint32_t st, float2* sm) {
+  float2 xv[EPT];
+  float qv[EPT];
+#pragma unroll
+  for (int m = 0; m < EPT; ++m) {
+    const uint32_t g = base | elem_off(a.d, m);
+    xv[m] = IN ? __ldcs(a.in + g) : make_float2(a.init_amp, 0.f);
+    if (PH) qv[m] = __ldcs(a.q + g);
+  }
+#pragma unroll
+  for (int m = 0; m < EPT; ++m) {
+    float2 x = xv[m];
+    if (PH) {
+      float c, s;
+      phase_cs(qv[m], a.ph0, a.ph1, c, s);
+      x = make_float2(c * x.x + s * x.y, c * x.y - s * x.x);   // exp(-i gamma q) x
+    }
+    sm[st + NT * m] = x;
+  }
+}
+
 // forward pass: stage (phase), gates, write back
 __global__ void __launch_bounds__(NT) fwd_kernel(const __grid_constant__ Args a) {
   __shared__ __align__(16) float2 sm[SLOTS];
   const uint32_t t = threadIdx.x;
   const uint32_t base = tile_base(a.d, blockIdx.x) | thr_off(a.d, t);
   const uint32_t st = swz(t);   // slot of tile index t + 256 m is st + 256 m
-#pragma unroll
-  for (int m = 0; m < EPT; ++m) {
-    const uint32_t g = base | elem_off(a.d, m);
-    float2 x = a.in ? __ldcs(a.in + g) : make_float2(a.init_amp, 0.f);
-    if (a.has_phase) {
-      float c, s;
-      phase_cs(__ldcs(a.q + g), a.ph0, a.ph1, c, s);
-      x = make_float2(c * x.x + s * x.y, c * x.y - s * x.x);   // exp(-i gamma q) x
-    }
-    sm[st + NT * m] = x;
+  if (a.in) {
+    if (a.has_phase) stage_fwd<true, true>(a, base, st, sm);
+    else stage_fwd<true, false>(a, base, st, sm);
+  } else {
+    if (a.has_phase) stage_fwd<false, true>(a, base, st, sm);
+    else stage_fwd<false, false>(a, base, st, sm);
   }
   __syncthreads();
+  const float2 cc = make_float2(a.c, a.c), sn = make_float2(a.s, -a.s);
   for (int gi = 0; gi < a.d.ngates; ++gi) {
     const uint32_t s0 = pair_slot(t, a.d.ga[gi], a.d.gb[gi]), sm_ab = a.d.goff[gi][3];
 #pragma unroll
     for (int k = 0; k < TILE / 4 / NT; ++k) {
       const uint32_t lo = k ? (s0 ^ a.d.goff[gi][k - 1]) : s0, hi = lo ^ sm_ab;
       const float2 x = sm[lo], y = sm[hi];
-      sm[lo] = make_float2(a.c * x.x + a.s * y.y, a.c * x.y - a.s * y.x);   // c x - i s y
-      sm[hi] = make_float2(a.c * y.x + a.s * x.y, a.c * y.y - a.s * x.x);   // c y - i s x
+      sm[lo] = fma2(cc, x, mul2(sn, swp(y)));   // c x - i s y = (c x.re + s y.im, c x.im - s y.re)
+      sm[hi] = fma2(cc, y, mul2(sn, swp(x)));   // c y - i s x
     }
     __syncthreads();
   }
@@ -185,7 +211,11 @@ __global__ void __launch_bounds__(NT) rev_kernel(const __grid_constant__ Args a)
     qv[m] = a.has_phase ? __ldcs(a.q + g) : 0.f;   // read with the vectors, used after the gates
   }
   __syncthreads();
-  float acc_t = 0.f, acc_g = 0.f;
+  float acc_g = 0.f;
+  // Im(conj(l_lo) p_hi) + Im(conj(l_hi) p_lo) = <lambda|(XX+YY)|psi> / 2 on a pair, accumulated as
+  // componentwise products (re*im, im*re) whose difference is taken once at the end
+  float2 at = make_float2(0.f, 0.f);
+  const float2 cc = make_float2(a.c, a.c), sn = make_float2(-a.s, a.s);
   for (int gi = a.d.ngates - 1; gi >= 0; --gi) {
     const uint32_t s0 = pair_slot(t, a.d.ga[gi], a.d.gb[gi]), sm_ab = a.d.goff[gi][3];
 #pragma unroll
@@ -193,16 +223,17 @@ __global__ void __launch_bounds__(NT) rev_kernel(const __grid_constant__ Args a)
       const uint32_t lo = k ? (s0 ^ a.d.goff[gi][k - 1]) : s0, hi = lo ^ sm_ab;
       const float2 x = sp[lo], y = sp[hi];
       const float2 u = sl[lo], v = sl[hi];
-      // Im(conj(l_lo) p_hi) + Im(conj(l_hi) p_lo): <lambda|(XX+YY)|psi> / 2 on this pair
-      acc_t += (u.x * y.y - u.y * y.x) + (v.x * x.y - v.y * x.x);
-      // undo: (a, b) -> (c a + i s b, c b + i s a)
-      sp[lo] = make_float2(a.c * x.x - a.s * y.y, a.c * x.y + a.s * y.x);
-      sp[hi] = make_float2(a.c * y.x - a.s * x.y, a.c * y.y + a.s * x.x);
-      sl[lo] = make_float2(a.c * u.x - a.s * v.y, a.c * u.y + a.s * v.x);
-      sl[hi] = make_float2(a.c * v.x - a.s * u.y, a.c * v.y + a.s * u.x);
+      at = fma2(u, swp(y), at);
+      at = fma2(v, swp(x), at);
+      // undo: (a, b) -> (c a + i s b, c b + i s a) = (c a.re - s b.im, c a.im + s b.re)
+      sp[lo] = fma2(cc, x, mul2(sn, swp(y)));
+      sp[hi] = fma2(cc, y, mul2(sn, swp(x)));
+      sl[lo] = fma2(cc, u, mul2(sn, swp(v)));
+      sl[hi] = fma2(cc, v, mul2(sn, swp(u)));
     }
     __syncthreads();
   }
+  const float acc_t = at.x - at.y;
 #pragma unroll
   for (int m = 0; m < EPT; ++m) {
     const uint32_t g = base | elem_off(a.d, m);

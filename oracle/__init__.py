@@ -488,6 +488,67 @@ def _gradient_factored(prob: Problem, gammas, ts):
     return f, dg, dt
 
 
+# ============================================================== ex-QAOA (Sec. 2.3.2)
+
+
+def pauli_z_diag(n: int, u: int, v: int = -1) -> np.ndarray:
+    """Diagonal of Z_u (v < 0) or Z_u Z_v on n qubits: Z has eigenvalue +1 on |0>, -1 on |1>."""
+    x = qubit_bits(n, np.arange(1 << n, dtype=np.int64))
+    z = 1.0 - 2.0 * x[u].astype(np.float64)
+    if v >= 0:
+        z = z * (1.0 - 2.0 * x[v].astype(np.float64))
+    return z
+
+
+def exqaoa_term_diags(n: int, tu, tv, coef):
+    """Sec. 2.3.2: the terms Sigma_j = coef_j Z_u Z_v (tv[j] < 0: coef_j Z_u) as diagonals."""
+    return [float(coef[j]) * pauli_z_diag(n, int(tu[j]), int(tv[j])) for j in range(len(coef))]
+
+
+def exqaoa_phase(psi: np.ndarray, terms, gam) -> np.ndarray:
+    """Eq. of U_Qext: prod_j exp(-i gamma_j Sigma_j), each diagonal factor applied in turn."""
+    for j, S in enumerate(terms):
+        psi = psi * np.exp(-1j * float(gam[j]) * S)
+    return psi
+
+
+def exqaoa_evolve(prob: Problem, terms, G, ts) -> np.ndarray:
+    """Sec. 2.3.2: psi = prod_k U_X(t_k) U_Qext(gamma_{k,:}) |+>; G[k][j] = gamma_{k,j}."""
+    psi = prob.initial_state()
+    for k in range(len(ts)):
+        psi = exqaoa_phase(psi, terms, G[k])
+        psi = prob.mix(psi, float(ts[k]))
+    return psi
+
+
+def exqaoa_gradient(prob: Problem, terms, G, ts):
+    """Adjoint gradient of f = <psi_p|Q|psi_p> for ex-QAOA, every state stored. With
+    phi_k = U_Qext,k psi_{k-1}, psi_k = M_k phi_k, lambda_p = Q psi_p:
+      df/dt_k         = 2 Im <lambda_k | W psi_k>
+      df/dgamma_{k,j} = 2 Im <M_k^dag lambda_k | Sigma_j phi_k>
+    Returns (f, dG[p][J], dt[p])."""
+    p = len(ts)
+    J = len(terms)
+    psi = prob.initial_state()
+    phis, psis = [], []
+    for k in range(p):
+        phi = exqaoa_phase(psi, terms, G[k])
+        psi = prob.mix(phi, float(ts[k]))
+        phis.append(phi)
+        psis.append(psi)
+    f = expectation(psi, prob.q)
+    lam = prob.q * psi
+    dG = np.zeros((p, J))
+    dt = np.zeros(p)
+    for k in range(p - 1, -1, -1):
+        dt[k] = 2.0 * np.vdot(lam, prob.apply_W(psis[k])).imag
+        lam = prob.mix(lam, -float(ts[k]))
+        for j in range(J):
+            dG[k, j] = 2.0 * np.vdot(lam, terms[j] * phis[k]).imag
+        lam = exqaoa_phase(lam, terms, -np.asarray(G[k], dtype=np.float64))
+    return f, dG, dt
+
+
 def central_fd(prob: Problem, gammas, ts, h: float = 1e-3):
     """Richardson-extrapolated central differences: D(h) = (f(x+h)-f(x-h))/2h,
     estimate = (4 D(h/2) - D(h)) / 3 (error O(h^4))."""

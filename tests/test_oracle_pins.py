@@ -511,3 +511,98 @@ def test_qubo_fixed_point_rule():
     F, ci, hi, _ = orc.qubo_fixed_point(2, 0.0, [1.0, -1.0], np.zeros((2, 2)))
     F2, ci2, hi2, _ = orc.qubo_fixed_point(2, 0.0, [1.0 + 2.0 ** (-F - 1), -1.0 - 2.0 ** (-F - 1)], np.zeros((2, 2)))
     assert F2 == F and hi2 == [hi[0] + 1, hi[1] - 1]
+
+
+# ------------------------------------------------------------------ ex-QAOA (Sec. 2.3.2)
+
+def _qubo_to_pauli(n, c, h, J):
+    """x_u = (1 - z_u)/2 written out: q = const + sum_u a_u Z_u + sum_{u<v} b_uv Z_u Z_v."""
+    const = c + 0.5 * sum(h) + 0.25 * sum(J[u][v] for u in range(n) for v in range(u + 1, n))
+    tu, tv, coef = [], [], []
+    for u in range(n):
+        a = -0.5 * h[u] - 0.25 * sum(J[min(u, v)][max(u, v)] for v in range(n) if v != u)
+        tu.append(u), tv.append(-1), coef.append(a)
+    for u in range(n):
+        for v in range(u + 1, n):
+            if J[u][v] != 0:
+                tu.append(u), tv.append(v), coef.append(0.25 * J[u][v])
+    return const, tu, tv, coef
+
+
+def test_pauli_z_diag_bit_order():
+    # qubit 0 is the most significant bit; Z = +1 on |0>
+    assert orc.pauli_z_diag(3, 0).tolist() == [1, 1, 1, 1, -1, -1, -1, -1]
+    assert orc.pauli_z_diag(3, 2).tolist() == [1, -1, 1, -1, 1, -1, 1, -1]
+    assert orc.pauli_z_diag(3, 0, 2).tolist() == [1, -1, 1, -1, -1, 1, -1, 1]
+
+
+def test_exqaoa_equal_gammas_is_qaoa():
+    """With gamma_{k,j} = gamma_k for every term of Q's Pauli decomposition, U_Qext differs from
+    exp(-i gamma_k Q) by the global phase of the identity part: same state up to a phase, same
+    objective, and the per-term gradients of a layer sum to the QAOA gamma gradient."""
+    n, p = 7, 3
+    rng = wl.rng_for(160)
+    c, h, J = rng.standard_normal(), rng.standard_normal(n), np.triu(rng.standard_normal((n, n)), 1)
+    const, tu, tv, coef = _qubo_to_pauli(n, c, h, J)
+    terms = orc.exqaoa_term_diags(n, tu, tv, coef)
+    q = orc.qubo_quality(n, c, h, J)
+    assert np.max(np.abs(const + sum(terms) - q)) < 1e-12     # the decomposition itself
+    prob = orc.Problem(q=q, mixer="hypercube", n=n)
+    gs, ts = wl.thetas(p, wl.rng_for(161))
+    G = np.repeat(np.asarray(gs)[:, None], len(terms), axis=1)
+    a = orc.exqaoa_evolve(prob, terms, G, ts)
+    b = orc.evolve(prob, gs, ts)
+    assert abs(abs(np.vdot(a, b)) - 1.0) < 1e-12
+    f, dG, dt = orc.exqaoa_gradient(prob, terms, G, ts)
+    f0, dg0, dt0 = orc.gradient(prob, gs, ts)
+    assert abs(f - f0) < 1e-12
+    assert np.max(np.abs(dG.sum(axis=1) - dg0)) < 1e-10
+    assert np.max(np.abs(dt - dt0)) < 1e-10
+
+
+def test_exqaoa_vs_dense_expm():
+    """n=4, p=2, distinct gamma per term: the ansatz as dense matrix exponentials of the summed
+    diagonal and of W = sum_j X_j."""
+    n, p = 4, 2
+    tu, tv, coef = [0, 1, 0, 2, 1], [1, 3, -1, 3, -1], [0.5, -1.25, 0.75, 2.0, 0.3]
+    terms = orc.exqaoa_term_diags(n, tu, tv, coef)
+    G = wl.rng_for(162).uniform(0, math.pi, size=(p, len(tu)))
+    ts = [0.4, 1.9]
+    W = sum(_dense_pauli(n, {u: "X"}) for u in range(n))
+    psi = np.full(1 << n, 0.25, dtype=np.complex128)
+    for k in range(p):
+        D = np.diag(sum(G[k][j] * terms[j] for j in range(len(tu))))
+        psi = scipy.linalg.expm(-1j * ts[k] * W) @ (scipy.linalg.expm(-1j * D) @ psi)
+    prob = orc.Problem(q=np.arange(16.0), mixer="hypercube", n=n)
+    assert np.max(np.abs(orc.exqaoa_evolve(prob, terms, G, ts) - psi)) < 1e-12
+
+
+def test_exqaoa_gradient_vs_richardson_fd():
+    n, p = 6, 2
+    G6 = wl.gnp_graph(n, 0.6, wl.rng_for(163))
+    tu, tv, coef = list(G6.eu), list(G6.ev), [0.5 * w for w in G6.w]     # Example 2: 1/2 Z_u Z_v per edge
+    terms = orc.exqaoa_term_diags(n, tu, tv, coef)
+    prob = orc.maxcut_problem(n, G6.eu, G6.ev, G6.w)
+    G = wl.rng_for(164).uniform(0, math.pi, size=(p, len(tu)))
+    ts = np.array([0.7, 2.1])
+    f, dG, dt = orc.exqaoa_gradient(prob, terms, G, ts)
+
+    def obj(Gx, tx):
+        return orc.expectation(orc.exqaoa_evolve(prob, terms, Gx, tx), prob.q)
+
+    def rich(fun, h=1e-3):
+        d = lambda hh: (fun(hh) - fun(-hh)) / (2 * hh)
+        return (4 * d(h / 2) - d(h)) / 3
+
+    for k in range(p):
+        for j in range(len(tu)):
+            def fg(hh, k=k, j=j):
+                Gx = G.copy()
+                Gx[k, j] += hh
+                return obj(Gx, ts)
+            assert abs(rich(fg) - dG[k, j]) < 1e-8
+        def ft(hh, k=k):
+            tx = ts.copy()
+            tx[k] += hh
+            return obj(G, tx)
+        assert abs(rich(ft) - dt[k]) < 1e-8

@@ -246,6 +246,7 @@ def run_extras(qvs, torch, stream, peak, steps, warmup, only=None, qwoa_n=26, qw
     out = {}
     if only is None:
         out.update(_extra_inpass(qvs, torch, stream, peak, steps, warmup))
+        out.update(_extra_exqaoa(qvs, torch, stream, peak, steps, warmup))
     if only in (None, "qwoa"):
         out.update(_extra_qwoa(qvs, torch, stream, peak, steps, warmup, qwoa_n, qwoa_p))
     if only in (None, "parity"):
@@ -288,6 +289,32 @@ def _extra_inpass(qvs, torch, stream, peak, steps, warmup, n=N_QUBITS, p=P_LAYER
         "e2e": {"value": units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * (1 + n + n * n) + 16 * p,
                 "d2h_bytes_per_step": 8 * (1 + 2 * p)},
         "roofline": roof, "kernels": ker}}
+
+
+def _extra_exqaoa(qvs, torch, stream, peak, steps, warmup, n=N_QUBITS, p=P_LAYERS):
+    """ex-QAOA (Sec. 2.3.2) on the benchmark graph: one gamma per edge term 1/2 w_e Z_u Z_v (Example 2's
+    form), gammas uniform on [0, pi]; objective + gradient of all p * (1 + |E|) parameters."""
+    inst = wl.wmaxcut(n, p)
+    G = inst.graph
+    q = torch.empty(1 << n, dtype=torch.float32, device="cuda")
+    qvs.qvs_quality_maxcut(n, G.eu, G.ev, G.w, q, qvs.QVS_F32, stream)
+    sim = qvs.Simulator(1 << n, qvs.QVS_C64, stream)
+    sim.set_quality(q).set_mixer(qvs.QVS_MIX_HYPERCUBE, qvs.hypercube_desc(n))
+    sim.set_phase_terms(G.eu, G.ev, [0.5 * w for w in G.w])
+    Gm = wl.rng_for(190).uniform(0.0, math.pi, size=(p, len(G.eu)))
+    ts = np.asarray(inst.ts)
+    ms = _time_steps(torch, stream, lambda: sim.gradient_ex(Gm, ts), steps, warmup)
+    sim.set_option(qvs.QVS_OPT_PROFILE, 1)
+    for _ in range(2):
+        sim.gradient_ex(Gm, ts)
+    roof, ker = _kernel_summary(qvs, sim.h, peak, 2)
+    sim.close()
+    del q
+    torch.cuda.empty_cache()
+    units = float(1 << n) * p
+    return {f"exqaoa_wmaxcut_n{n}_p{p}_{len(G.eu)}terms": {
+        "value": units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+        "parameters": p * (1 + len(G.eu)), "roofline": roof, "kernels": ker}}
 
 
 def _extra_qwoa(qvs, torch, stream, peak, steps, warmup, n, p):

@@ -150,6 +150,28 @@ int qvs_state_parity(int n_qubits, int A, void* dst, void* stream);
  * objective is available from qvs_expectation. gammas, ts: host arrays of length p. */
 int qvs_evolve(qvs_t h, int p, const double* gammas, const double* ts);
 
+/* Sec. 2.3.2 (ex-QAOA): the phase of layer k becomes prod_j exp(-i gamma_{k,j} Sigma_j) with one
+ * parameter per term Sigma_j = coef[j] Z_{u[j]} Z_{v[j]} (v[j] = -1: coef[j] Z_{u[j]}), the non-identity
+ * Pauli terms of the quality operator (Z = +1 on |0>; qubit u = index bit n-1-u). Host arrays of
+ * n_terms entries (copied), 0 <= n_terms <= 1024; u in 0..n-1, v = -1 or in 0..n-1 with v != u.
+ * Used by qvs_evolve_ex / qvs_gradient_ex only; the objective stays <psi|Q|psi> with the handle's
+ * quality. QVS_EINVAL for an out-of-range index, a repeated qubit or a non-finite coefficient. */
+int qvs_set_phase_terms(qvs_t h, int n_terms, const int32_t* u, const int32_t* v, const double* coef);
+
+/* ex-QAOA forward evolution (Sec. 2.3.2): gammas[k * n_terms + j] = gamma_{k,j} (host, p * n_terms
+ * values), ts[k]. Each layer's phase angle sum_j gamma_{k,j} Sigma_j(x) is evaluated in the phase
+ * passes in 32-bit fixed-point turns (exact modulo one turn for the coefficients reduced to 2^-32
+ * turn). Hypercube mixer, complex64, n_qubits > 12 (QVS_EUNSUPPORTED otherwise); QVS_ESTATE
+ * without terms. */
+int qvs_evolve_ex(qvs_t h, int p, const double* gammas, const double* ts);
+
+/* ex-QAOA objective and gradient: E, dgamma[k * n_terms + j] = df/dgamma_{k,j}, dt[k] (host arrays).
+ * The adjoint phase passes store g(x) = 2 Im(conj(lambda) phi)(x); a Walsh-Hadamard transform per
+ * 4096-amplitude tile turns it into every term's derivative sum_x coef_j Z..(x) g(x). Same
+ * conditions as qvs_evolve_ex. */
+int qvs_gradient_ex(qvs_t h, int p, const double* gammas, const double* ts, double* E, double* dgamma,
+                    double* dt);
+
 /* Sec. 2.1: f = <theta|Q|theta> of the last qvs_evolve (fp64 reduction). */
 int qvs_expectation(qvs_t h, double* E);
 

@@ -35,6 +35,7 @@ EXPORTED = [
     "qvs_xy_ring_csr", "qvs_state_parity", "qvs_batch_create", "qvs_batch_set_quality", "qvs_batch_gradient",
     "qvs_batch_info", "qvs_batch_destroy", "qvs_gradient_small_noalloc", "qvs_strerror",
     "qvs_set_quality_qubo", "qvs_quality_qubo", "qvs_qubo_from_maxcut",
+    "qvs_set_phase_terms", "qvs_evolve_ex", "qvs_gradient_ex",
 ]
 
 
@@ -102,6 +103,9 @@ def load(path: str = LIB_PATH):
         "qvs_set_quality_qubo": (I, [V, I, D, P(D), P(D)]),
         "qvs_quality_qubo": (I, [I, D, P(D), P(D), I, V, V]),
         "qvs_qubo_from_maxcut": (I, [I, I, P(ctypes.c_int32), P(ctypes.c_int32), P(D), P(D), P(D), P(D)]),
+        "qvs_set_phase_terms": (I, [V, I, P(ctypes.c_int32), P(ctypes.c_int32), P(D)]),
+        "qvs_evolve_ex": (I, [V, I, P(D), P(D)]),
+        "qvs_gradient_ex": (I, [V, I, P(D), P(D), P(D), P(D), P(D)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -290,6 +294,39 @@ def qvs_qubo_from_maxcut(n: int, eu, ev, w=None):
                                        ev.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), wp, ctypes.byref(c),
                                        _dptr(hl), _dptr(J)), "qvs_qubo_from_maxcut")
     return c.value, hl, J.reshape(n, n)
+
+
+def qvs_set_phase_terms(h, u, v, coef):
+    """ex-QAOA terms coef[j] Z_u[j] Z_v[j] (v[j] = -1: a single Z)."""
+    u = np.ascontiguousarray(u, dtype=np.int32)
+    v = np.ascontiguousarray(v, dtype=np.int32)
+    c = np.ascontiguousarray(coef, dtype=np.float64)
+    assert u.shape == v.shape == c.shape
+    _check(load().qvs_set_phase_terms(h, len(c), u.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                      v.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dptr(c)),
+           "qvs_set_phase_terms")
+
+
+def qvs_evolve_ex(h, gammas, ts) -> float:
+    """gammas: (p, n_terms) array; returns the objective."""
+    G = np.ascontiguousarray(gammas, dtype=np.float64)
+    t = np.ascontiguousarray(ts, dtype=np.float64)
+    _check(load().qvs_evolve_ex(h, len(t), _dptr(G), _dptr(t)), "qvs_evolve_ex")
+    E = ctypes.c_double()
+    _check(load().qvs_expectation(h, ctypes.byref(E)), "qvs_expectation")
+    return E.value
+
+
+def qvs_gradient_ex(h, gammas, ts):
+    """gammas: (p, n_terms) array; returns (E, dgamma (p, n_terms), dt (p,))."""
+    G = np.ascontiguousarray(gammas, dtype=np.float64)
+    t = np.ascontiguousarray(ts, dtype=np.float64)
+    p = len(t)
+    E = ctypes.c_double()
+    dG = np.zeros(G.shape, dtype=np.float64)
+    dt = np.zeros(p, dtype=np.float64)
+    _check(load().qvs_gradient_ex(h, p, _dptr(G), _dptr(t), ctypes.byref(E), _dptr(dG), _dptr(dt)), "qvs_gradient_ex")
+    return E.value, dG, dt
 
 
 def qvs_quality_subset(n: int, w, out, dtype: int, stream=None):
@@ -498,6 +535,16 @@ class Simulator:
     def set_quality_qubo(self, n_qubits: int, c: float, hlin, J):
         qvs_set_quality_qubo(self.h, n_qubits, c, hlin, J)
         return self
+
+    def set_phase_terms(self, u, v, coef):
+        qvs_set_phase_terms(self.h, u, v, coef)
+        return self
+
+    def evolve_ex(self, gammas, ts) -> float:
+        return qvs_evolve_ex(self.h, gammas, ts)
+
+    def gradient_ex(self, gammas, ts):
+        return qvs_gradient_ex(self.h, gammas, ts)
 
     def set_mixer(self, kind: int, desc: MixerDesc):
         qvs_set_mixer(self.h, kind, desc)

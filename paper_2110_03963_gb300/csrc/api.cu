@@ -7,6 +7,8 @@
 
 #include <new>
 
+#include <vector>
+
 #include "qvs_internal.h"
 
 namespace qvs {
@@ -306,6 +308,49 @@ extern "C" int qvs_evolve(qvs_t h, int p, const double* gammas, const double* ts
     case QVS_MIX_PARITY: return parity_evolve(h, p, gammas, ts);
   }
   return QVS_ESTATE;
+}
+
+extern "C" int qvs_set_phase_terms(qvs_t h, int n_terms, const int32_t* u, const int32_t* v, const double* coef) {
+  if (!h || h->n < 1 || n_terms < 0 || n_terms > 1024) return QVS_EINVAL;
+  if (n_terms > 0 && (!u || !v || !coef)) return QVS_EINVAL;
+  std::vector<ExTerm> t;
+  for (int j = 0; j < n_terms; ++j) {
+    if (u[j] < 0 || u[j] >= h->n || v[j] < -1 || v[j] >= h->n || v[j] == u[j] || !isfinite(coef[j]))
+      return QVS_EINVAL;
+    t.push_back({h->n - 1 - u[j], v[j] < 0 ? -1 : h->n - 1 - v[j], coef[j]});
+  }
+  h->ex.terms = t;
+  h->have_E = false;
+  return QVS_OK;
+}
+
+static bool ex_params_ok(qvs_t h, int p, const double* g, const double* t) {
+  const size_t J = h->ex.terms.size();
+  if (p < 1 || p > 4096 || !g || !t) return false;
+  for (size_t i = 0; i < (size_t)p * J; ++i)
+    if (!isfinite(g[i])) return false;
+  for (int k = 0; k < p; ++k)
+    if (!isfinite(t[k])) return false;
+  return true;
+}
+
+extern "C" int qvs_evolve_ex(qvs_t h, int p, const double* gammas, const double* ts) {
+  QVS_TRY(ready(h));
+  if (h->mixer != QVS_MIX_HYPERCUBE) return QVS_EUNSUPPORTED;
+  if (h->ex.terms.empty()) return QVS_ESTATE;
+  if (!ex_params_ok(h, p, gammas, ts)) return QVS_EINVAL;
+  h->have_E = false;
+  return hc_evolve_ex(h, p, gammas, ts);
+}
+
+extern "C" int qvs_gradient_ex(qvs_t h, int p, const double* gammas, const double* ts, double* E, double* dgamma,
+                               double* dt) {
+  QVS_TRY(ready(h));
+  if (h->mixer != QVS_MIX_HYPERCUBE) return QVS_EUNSUPPORTED;
+  if (h->ex.terms.empty()) return QVS_ESTATE;
+  if (!ex_params_ok(h, p, gammas, ts) || !E || !dgamma || !dt) return QVS_EINVAL;
+  h->have_E = false;
+  return hc_gradient_ex(h, p, gammas, ts, E, dgamma, dt);
 }
 
 extern "C" int qvs_expectation(qvs_t h, double* E) {

@@ -22,8 +22,14 @@ enum Shape : int {
   FV = 4,   // last forward pass for qvs_evolve: rotations, E, store psi
   R1 = 5,   // adjoint of F1
   R2 = 6,   // adjoint of F2
-  R0 = 7    // adjoint of F0 (gradient contributions only)
+  R0 = 7,   // adjoint of F0 (gradient contributions only)
+  R1X = 8,  // R1 / R0 of an ex-QAOA layer: also store g(x) for the per-term gradients (runtime
+  R0X = 9   // masks only)
 };
+__host__ __device__ constexpr int base_shape(int s) { return s == R1X ? R1 : (s == R0X ? R0 : s); }
+__host__ __device__ constexpr bool two_vector(int s) {
+  return base_shape(s) == FE || base_shape(s) == R1 || base_shape(s) == R2 || base_shape(s) == R0;
+}
 
 // Scalars of one pass. Rotations use the tangent form of the gauge (see hc_kernels.cuh): the
 // kernels never see cos t'; every real factor of the frame reaches them as a scale.
@@ -55,7 +61,10 @@ struct PassArgs {
   const int* qcta;      // per tile: [16] = {constant, linear coefficient of tile bits 0..11}
   const int* qthr;      // per thread: [8] = {pair sum of its own bits, cross sums of bits 5..8}
   int qpp[R];           // per register r: pair sum of register bits 5..8
-  T qscale;             // 2^-F
+  T qscale;             // 2^-F (quality) or 2^-32 (ex-QAOA phase angle in turns)
+  // ex-QAOA adjoint phase passes: g(x) = 2 Im(conj(lambda) phi)(x) stored at the physical index
+  // (the per-term gradients are its moments); NULL otherwise
+  T* gout;
 };
 
 // ---------------------------------------------------------------- per-pass scalars (host and device)
@@ -234,36 +243,40 @@ __device__ __forceinline__ void block_store3(T a, T b, T c, double* part, int ra
 // the register bits (per register, qpp). Flipped bits (qx != 0) read x = 1 - bit.
 template <class T>
 __device__ __forceinline__ void qgen2(T (&qv)[R], const PassArgs<T>& a, const int* s_q, int tid) {
+  // sums modulo 2^32 (exact for qualities, which stay below 2^30; ex-QAOA angles wrap by design)
   const uint32_t fl = a.qx ? 0xFFFu : 0u;
   const uint32_t xt = (uint32_t)tj<2>(0, tid) ^ fl;
   const int4 k0 = *reinterpret_cast<const int4*>(a.qthr + 8 * tid);
-  const int k4 = a.qthr[8 * tid + 4];
-  int qT = s_q[0] + k0.x;
+  const uint32_t k4 = (uint32_t)a.qthr[8 * tid + 4];
+  uint32_t qT = (uint32_t)s_q[0] + (uint32_t)k0.x;
 #pragma unroll
   for (int k = 0; k < TB; ++k)
     if (k < 5 || k > 8)
-      if ((xt >> k) & 1u) qT += s_q[1 + k];
-  int cc[RB] = {s_q[6] + k0.y, s_q[7] + k0.z, s_q[8] + k0.w, s_q[9] + k4};
+      if ((xt >> k) & 1u) qT += (uint32_t)s_q[1 + k];
+  uint32_t cc[RB] = {(uint32_t)s_q[6] + (uint32_t)k0.y, (uint32_t)s_q[7] + (uint32_t)k0.z,
+                     (uint32_t)s_q[8] + (uint32_t)k0.w, (uint32_t)s_q[9] + k4};
   if (fl) {
 #pragma unroll
     for (int i = 0; i < RB; ++i) {
       qT += cc[i];
-      cc[i] = -cc[i];
+      cc[i] = 0u - cc[i];
     }
   }
 #pragma unroll
   for (int r = 0; r < R; ++r) {
-    int v = qT + a.qpp[r];
+    uint32_t v = qT + (uint32_t)a.qpp[r];
 #pragma unroll
     for (int i = 0; i < RB; ++i)
       if ((r >> i) & 1) v += cc[i];
-    qv[r] = (T)v * a.qscale;
+    qv[r] = (T)(int32_t)v * a.qscale;
   }
 }
 
 template <class T, int SHAPE, int TH, bool ALT = false>
 __device__ __forceinline__ void run_pass(const PassArgs<T>& a, uint32_t bid, uint32_t nblk,
                                          unsigned char* smem_raw) {
+  constexpr int S = base_shape(SHAPE);
+  constexpr bool EXG = SHAPE != S;
   using C = typename Cx<T>::t;
   C* sm = reinterpret_cast<C*>(smem_raw);
   constexpr int TBF = TH == TH_NONE ? TH_NONE : TH;   // threshold of the "before" rotations
@@ -322,7 +335,7 @@ __device__ __forceinline__ void run_pass(const PassArgs<T>& a, uint32_t bid, uin
   };
 
   C v[R];
-  if constexpr (SHAPE == F0) {
+  if constexpr (S == F0) {
     const uint32_t tpop = __popc(base) + __popc(tj<2>(0, tid));
     if (a.gen_init) {
 #pragma unroll
@@ -346,7 +359,7 @@ __device__ __forceinline__ void run_pass(const PassArgs<T>& a, uint32_t bid, uin
     xchg_alt<1, 0, 1, ALT>(v, sm, tid);
     rot_layout<0, TAF>(v, a.mask_aft, a.ta);
     gstore<0>(v, a.psi_out, off0, a.tile);
-  } else if constexpr (SHAPE == F1) {
+  } else if constexpr (S == F1) {
     ld(I0{}, v, a.psi_in, off0);
     rot_layout<0, TBF>(v, a.mask_bef, a.tb);
     xchg_alt<0, 1, 0, ALT>(v, sm, tid);
@@ -361,7 +374,7 @@ __device__ __forceinline__ void run_pass(const PassArgs<T>& a, uint32_t bid, uin
     xchg_alt<1, 0, 1, ALT>(v, sm, tid);
     rot_layout<0, TAF>(v, a.mask_aft, a.ta);
     gstore<0>(v, a.psi_out, off0, a.tile);
-  } else if constexpr (SHAPE == F2) {
+  } else if constexpr (S == F2) {
     ld(I0{}, v, a.psi_in, off0);
     rot_layout<0, TBF>(v, a.mask_bef, a.tb);
     xchg_alt<0, 1, 0, ALT>(v, sm, tid);
@@ -369,21 +382,21 @@ __device__ __forceinline__ void run_pass(const PassArgs<T>& a, uint32_t bid, uin
     xchg_alt<1, 2, 1, ALT>(v, sm, tid);
     rot_layout<2, TBF>(v, a.mask_bef, a.tb);
     gstore<2>(v, a.psi_out, off2, a.tile);
-  } else if constexpr (SHAPE == FE || SHAPE == FV) {
+  } else if constexpr (S == FE || S == FV) {
     ld(I0{}, v, a.psi_in, off0);
     rot_layout<0, TBF>(v, a.mask_bef, a.tb);
-    if constexpr (SHAPE == FV) xchg_alt<0, 1, 0, ALT>(v, sm, tid);
+    if constexpr (S == FV) xchg_alt<0, 1, 0, ALT>(v, sm, tid);
     else xchg<0, 1>(v, sm, tid);   // FE's second half writes both buffers: keep the trailing barrier
     rot_layout<1, TBF>(v, a.mask_bef, a.tb);
     qget();
-    if constexpr (SHAPE == FV) xchg_alt<1, 2, 1, ALT>(v, sm, tid);
+    if constexpr (S == FV) xchg_alt<1, 2, 1, ALT>(v, sm, tid);
     else xchg<1, 2>(v, sm, tid);
     rot_layout<2, TBF>(v, a.mask_bef, a.tb);
     T e = T(0);
 #pragma unroll
     for (int r = 0; r < R; ++r) e += qv[r] * (v[r].x * v[r].x + v[r].y * v[r].y);
     e *= a.sc_E;
-    if constexpr (SHAPE == FV) {
+    if constexpr (S == FV) {
       const uint32_t tpop = __popc(base) + __popc(tj<2>(0, tid));
       gstore_plain<2>(v, a.psi_out, off2, a.tile, tpop, a.ox, a.out_fm, a.out_k);
       block_store3(e, T(0), T(0), a.part, a.row_E, -1, -1, tid, bid, nblk);
@@ -400,7 +413,7 @@ __device__ __forceinline__ void run_pass(const PassArgs<T>& a, uint32_t bid, uin
       gstore<0>(l, a.lam_out, off0, a.tile);
       block_store3(e, T(2) * acc, T(0), a.part, a.row_E, a.row_bef, -1, tid, bid, nblk);
     }
-  } else if constexpr (SHAPE == R1 || SHAPE == R0) {
+  } else if constexpr (S == R1 || S == R0) {
     C l[R];
     ld(I0{}, v, a.psi_in, off0);
     ld(I0{}, l, a.lam_in, off0);
@@ -414,7 +427,16 @@ __device__ __forceinline__ void run_pass(const PassArgs<T>& a, uint32_t bid, uin
 #pragma unroll
     for (int r = 0; r < R; ++r) acc_g += qv[r] * imdot_st(l[r], v[r]);
     acc_g *= a.sc_g;
-    if constexpr (SHAPE == R1) {
+    if constexpr (EXG) {
+      {
+        uint32_t o[RB];
+        reg_bit_offsets<2>(a.tile, o);
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+          a.gout[(off2 + reg_off(o, r)) ^ a.qx] = T(2) * a.sc_g * imdot_st(l[r], v[r]);
+      }
+    }
+    if constexpr (S == R1) {
       phase2x2(v, l, T(-1));
       sc = a.sc_b;
       unrot_layout_acc<2, TBF>(v, l, a.mask_bef, a.tb, a.c2b, sc, acc_b);
@@ -426,7 +448,7 @@ __device__ __forceinline__ void run_pass(const PassArgs<T>& a, uint32_t bid, uin
       if (a.psi_out) gstore<0>(v, a.psi_out, off0, a.tile);
     }
     block_store3(T(2) * acc_b, T(2) * acc_a, T(2) * acc_g, a.part, a.row_bef, a.row_aft, a.row_gam, tid, bid, nblk);
-  } else if constexpr (SHAPE == R2) {
+  } else if constexpr (S == R2) {
     C l[R];
     ld(I2{}, v, a.psi_in, off2);
     ld(I2{}, l, a.lam_in, off2);
@@ -443,7 +465,7 @@ __device__ __forceinline__ void run_pass(const PassArgs<T>& a, uint32_t bid, uin
 }
 
 template <class T, int SHAPE, int TH>
-__global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 1 : ((SHAPE == FE || SHAPE == R1 || SHAPE == R2 || SHAPE == R0) ? 2 : 4))
+__global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 1 : (two_vector(SHAPE) ? 2 : 4))
 pass_kernel(const __grid_constant__ PassArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   run_pass<T, SHAPE, TH>(a, blockIdx.x, gridDim.x, smem_raw);
@@ -451,7 +473,7 @@ pass_kernel(const __grid_constant__ PassArgs<T> a) {
 
 template <class T, int SHAPE, int TH>
 static int launch_one(const PassArgs<T>& a, uint32_t grid, cudaStream_t st) {
-  constexpr bool two = SHAPE == FE || SHAPE == R1 || SHAPE == R2 || SHAPE == R0;
+  constexpr bool two = two_vector(SHAPE);
   const size_t sm = (two ? 2 : 1) * (size_t)SM_SLOTS * sizeof(typename Cx<T>::t);
   static bool configured = false;   // per instantiation
   if (!configured) {
@@ -476,6 +498,11 @@ int launch_pass(int shape, const PassArgs<T>& a, uint32_t grid, cudaStream_t st)
     case R1: return launch_one<T, R1, TH>(a, grid, st);
     case R2: return launch_one<T, R2, TH>(a, grid, st);
     case R0: return launch_one<T, R0, TH>(a, grid, st);
+    case R1X:
+    case R0X:
+      if constexpr (TH == TH_RUNTIME)
+        return shape == R1X ? launch_one<T, R1X, TH>(a, grid, st) : launch_one<T, R0X, TH>(a, grid, st);
+      return QVS_EINVAL;
   }
   return QVS_EINVAL;
 }

@@ -236,9 +236,11 @@ static int make_plan(int n, int p, Plan& pl) {
 
 static const char* shape_name(int shape, bool dbl) {
   static const char* f[] = {"hc_pass_F0_c64", "hc_pass_F1_c64", "hc_pass_F2_c64", "hc_pass_FE_c64",
-                            "hc_pass_FV_c64", "hc_pass_R1_c64", "hc_pass_R2_c64", "hc_pass_R0_c64"};
+                            "hc_pass_FV_c64", "hc_pass_R1_c64", "hc_pass_R2_c64", "hc_pass_R0_c64",
+                            "hc_pass_R1X_c64", "hc_pass_R0X_c64"};
   static const char* d[] = {"hc_pass_F0_c128", "hc_pass_F1_c128", "hc_pass_F2_c128", "hc_pass_FE_c128",
-                            "hc_pass_FV_c128", "hc_pass_R1_c128", "hc_pass_R2_c128", "hc_pass_R0_c128"};
+                            "hc_pass_FV_c128", "hc_pass_R1_c128", "hc_pass_R2_c128", "hc_pass_R0_c128",
+                            "hc_pass_R1X_c128", "hc_pass_R0X_c128"};
   return dbl ? d[shape] : f[shape];
 }
 
@@ -253,6 +255,8 @@ static double shape_bytes(int shape, const void* psi_in, const void* psi_out, do
     case R1: return 3 * c + qb + (psi_out ? c : 0.0);
     case R2: return 3 * c + (psi_out ? c : 0.0);
     case R0: return 2 * c + qb;
+    case R1X: return 3 * c + qb + (psi_out ? c : 0.0) + qb;   // + the stored g
+    case R0X: return 2 * c + 2 * qb;
   }
   return 0.0;
 }
@@ -297,7 +301,8 @@ static int launch_shape(qvs_ctx* h, int shape, const PassArgs<T>& a, uint32_t gr
   cudaEvent_t ev;
   QVS_TRY(prof_begin(h, &ev));
   if constexpr (sizeof(T) == 4) {
-    QVS_TRY(launch_c64(pass_threshold(shape, a.mask_bef, a.mask_aft), shape, a, grid, h->stream));
+    const int th = shape >= R1X ? TH_RUNTIME : pass_threshold(shape, a.mask_bef, a.mask_aft);
+    QVS_TRY(launch_c64(th, shape, a, grid, h->stream));
   } else {
     QVS_TRY((launch_pass<T, TH_RUNTIME>(shape, a, grid, h->stream)));
   }
@@ -371,98 +376,224 @@ static int tile_index_bit(const Tile& t, int k) {
   return k < s ? k : k + t.hshift;
 }
 
-__global__ void qubo_rows_kernel(const QuboCoef* __restrict__ Q, Tile t, int flip, uint32_t ntiles,
-                                 int* __restrict__ rows) {
+// Rows of coefficient set blockIdx.y (sums mod 2^32: exact int32 qualities never wrap, ex-QAOA
+// angles are turns in 32-bit fixed point and wrap by design).
+__global__ void qubo_rows_kernel(const QuboCoef* __restrict__ Qs, Tile t, int flip, uint32_t ntiles,
+                                 int* __restrict__ rows0, size_t cstride) {
   const uint32_t bid = blockIdx.x * blockDim.x + threadIdx.x;
   if (bid >= ntiles) return;
+  const QuboCoef* Q = Qs + blockIdx.y;
   const uint32_t xb = tile_base(t, bid) ^ (flip ? all_bits(Q->n) : 0u);
   const int s = __popc(t.smask);
-  int qU = Q->c;
+  uint32_t qU = (uint32_t)Q->c;
   for (int i = 0; i < t.n_nt; ++i) {
     const int j = t.ntbit[i];
     if (!((xb >> j) & 1u)) continue;
-    qU += Q->h[j];
+    qU += (uint32_t)Q->h[j];
     for (int i2 = 0; i2 < i; ++i2) {
       const int j2 = t.ntbit[i2];
-      if ((xb >> j2) & 1u) qU += Q->J[j][j2];
+      if ((xb >> j2) & 1u) qU += (uint32_t)Q->J[j][j2];
     }
   }
-  int* row = rows + 16 * (size_t)bid;
-  row[0] = qU;
+  int* row = rows0 + cstride * blockIdx.y + 16 * (size_t)bid;
+  row[0] = (int)qU;
   for (int k = 0; k < TB; ++k) {
     const int pk = k < s ? k : k + t.hshift;
-    int L = Q->h[pk];
+    uint32_t L = (uint32_t)Q->h[pk];
     for (int i = 0; i < t.n_nt; ++i) {
       const int j = t.ntbit[i];
-      if ((xb >> j) & 1u) L += Q->J[pk][j];
+      if ((xb >> j) & 1u) L += (uint32_t)Q->J[pk][j];
     }
-    row[1 + k] = L;
+    row[1 + k] = (int)L;
   }
   row[13] = row[14] = row[15] = 0;
 }
 
 static size_t qubo_block_ints(uint32_t grid) { return 16 * (size_t)grid + 8 * (size_t)NT; }
 
-static int build_qubo_tables(qvs_ctx* h, const Plan& pl, uint32_t grid) {
-  QuboData& D = h->qubo;
-  const QuboCoef& Q = D.coef;
+// Tables of ncoef quadratic forms: block (c * g + tau) * 2 + f of tab holds the CTA rows and thread
+// rows of form c, tile type tau and frame f; pp[16 * block + r] its register pair sums.
+static int build_tables(qvs_ctx* h, const Plan& pl, uint32_t grid, const QuboCoef* coefs, int ncoef,
+                        DevBuf& dcoef, DevBuf& tab, std::vector<int32_t>& pp) {
   const size_t bi = qubo_block_ints(grid);
-  QVS_TRY(D.tab.ensure(sizeof(int) * bi * 2 * pl.g));
-  QVS_TRY(D.dcoef.ensure(sizeof(QuboCoef)));
-  QVS_CUDA_TRY(cudaMemcpyAsync(D.dcoef.ptr, &Q, sizeof(QuboCoef), cudaMemcpyHostToDevice, h->stream));
-  D.pp.assign(16 * 2 * (size_t)pl.g, 0);
-  std::vector<int> thr(8 * (size_t)NT * 2 * pl.g, 0);
+  const int nblk = ncoef * pl.g * 2;
+  QVS_TRY(tab.ensure(sizeof(int) * bi * nblk));
+  QVS_TRY(dcoef.ensure(sizeof(QuboCoef) * ncoef));
+  QVS_CUDA_TRY(cudaMemcpyAsync(dcoef.ptr, coefs, sizeof(QuboCoef) * ncoef, cudaMemcpyHostToDevice, h->stream));
+  pp.assign(16 * (size_t)nblk, 0);
+  std::vector<int> thr(8 * (size_t)NT * nblk, 0);
   for (int tau = 0; tau < pl.g; ++tau) {
     const Tile& t = pl.tile[tau];
     int pk[TB];
     for (int k = 0; k < TB; ++k) pk[k] = tile_index_bit(t, k);
     for (int f = 0; f < 2; ++f) {
-      const int blk = 2 * tau + f;
-      int* rows = D.tab.as<int>() + bi * blk;
-      qubo_rows_kernel<<<(grid + 127) / 128, 128, 0, h->stream>>>(D.dcoef.as<QuboCoef>(), t, f, grid, rows);
+      int* rows0 = tab.as<int>() + bi * (size_t)(tau * 2 + f);
+      dim3 gr((grid + 127) / 128, ncoef);
+      qubo_rows_kernel<<<gr, 128, 0, h->stream>>>(dcoef.as<QuboCoef>(), t, f, grid, rows0, bi * pl.g * 2);
       QVS_CUDA_TRY(cudaGetLastError());
       const uint32_t fl = f ? 0xFFFu : 0u;
-      for (int tid = 0; tid < NT; ++tid) {
-        const uint32_t xt = (uint32_t)tj<2>(0, tid) ^ fl;
-        int kt = 0, kc[RB] = {0, 0, 0, 0};
-        for (int k = 0; k < TB; ++k) {
-          if ((k >= 5 && k <= 8) || !((xt >> k) & 1u)) continue;
-          for (int l = 0; l < k; ++l)
-            if ((l < 5 || l > 8) && ((xt >> l) & 1u)) kt += Q.J[pk[k]][pk[l]];
-          for (int i = 0; i < RB; ++i) kc[i] += Q.J[pk[5 + i]][pk[k]];
+      for (int c = 0; c < ncoef; ++c) {
+        const QuboCoef& Q = coefs[c];
+        const int blk = (c * pl.g + tau) * 2 + f;
+        for (int tid = 0; tid < NT; ++tid) {
+          const uint32_t xt = (uint32_t)tj<2>(0, tid) ^ fl;
+          uint32_t kt = 0, kc[RB] = {0, 0, 0, 0};
+          for (int k = 0; k < TB; ++k) {
+            if ((k >= 5 && k <= 8) || !((xt >> k) & 1u)) continue;
+            for (int l = 0; l < k; ++l)
+              if ((l < 5 || l > 8) && ((xt >> l) & 1u)) kt += (uint32_t)Q.J[pk[k]][pk[l]];
+            for (int i = 0; i < RB; ++i) kc[i] += (uint32_t)Q.J[pk[5 + i]][pk[k]];
+          }
+          int* row = thr.data() + 8 * ((size_t)NT * blk + tid);
+          row[0] = (int)kt;
+          for (int i = 0; i < RB; ++i) row[1 + i] = (int)kc[i];
         }
-        int* row = thr.data() + 8 * ((size_t)NT * blk + tid);
-        row[0] = kt;
-        for (int i = 0; i < RB; ++i) row[1 + i] = kc[i];
-      }
-      for (int r = 0; r < R; ++r) {
-        const int x = r ^ (f ? R - 1 : 0);
-        int v = 0;
-        for (int i = 0; i < RB; ++i)
-          for (int i2 = 0; i2 < i; ++i2)
-            if (((x >> i) & 1) && ((x >> i2) & 1)) v += Q.J[pk[5 + i]][pk[5 + i2]];
-        D.pp[16 * (size_t)blk + r] = v;
+        for (int r = 0; r < R; ++r) {
+          const int x = r ^ (f ? R - 1 : 0);
+          uint32_t v = 0;
+          for (int i = 0; i < RB; ++i)
+            for (int i2 = 0; i2 < i; ++i2)
+              if (((x >> i) & 1) && ((x >> i2) & 1)) v += (uint32_t)Q.J[pk[5 + i]][pk[5 + i2]];
+          pp[16 * (size_t)blk + r] = (int32_t)v;
+        }
       }
     }
   }
-  for (int blk = 0; blk < 2 * pl.g; ++blk)
-    QVS_CUDA_TRY(cudaMemcpyAsync(D.tab.as<int>() + bi * blk + 16 * (size_t)grid, thr.data() + 8 * (size_t)NT * blk,
+  for (int blk = 0; blk < nblk; ++blk)
+    QVS_CUDA_TRY(cudaMemcpyAsync(tab.as<int>() + bi * blk + 16 * (size_t)grid, thr.data() + 8 * (size_t)NT * blk,
                                  sizeof(int) * 8 * NT, cudaMemcpyHostToDevice, h->stream));
   // the host staging vector goes out of scope: finish the copies first
   QVS_CUDA_TRY(cudaStreamSynchronize(h->stream));
-  D.tab_valid = true;
   return QVS_OK;
 }
 
-// point a pass that reads q at the tables of its tile type and frame
+static int build_qubo_tables(qvs_ctx* h, const Plan& pl, uint32_t grid) {
+  QVS_TRY(build_tables(h, pl, grid, &h->qubo.coef, 1, h->qubo.dcoef, h->qubo.tab, h->qubo.pp));
+  h->qubo.tab_valid = true;
+  return QVS_OK;
+}
+
+// point a pass at the tables of form c, its tile type and its frame
 template <class T>
-static void set_qubo_args(const qvs_ctx* h, int type, uint32_t grid, PassArgs<T>& a) {
-  const int blk = 2 * type + (a.qx ? 1 : 0);
-  const int* base = h->qubo.tab.as<int>() + qubo_block_ints(grid) * blk;
+static void set_table_args(const int* tab, const std::vector<int32_t>& pp, int c, int g, int type, uint32_t grid,
+                           T scale, PassArgs<T>& a) {
+  const int blk = (c * g + type) * 2 + (a.qx ? 1 : 0);
+  const int* base = tab + qubo_block_ints(grid) * blk;
   a.qcta = base;
   a.qthr = base + 16 * (size_t)grid;
-  for (int r = 0; r < R; ++r) a.qpp[r] = h->qubo.pp[16 * (size_t)blk + r];
-  a.qscale = (T)ldexp(1.0, -h->qubo.coef.F);
+  for (int r = 0; r < R; ++r) a.qpp[r] = pp[16 * (size_t)blk + r];
+  a.qscale = scale;
+}
+
+template <class T>
+static void set_qubo_args(const qvs_ctx* h, int g, int type, uint32_t grid, PassArgs<T>& a) {
+  set_table_args<T>(h->qubo.tab.as<int>(), h->qubo.pp, 0, g, type, grid, (T)ldexp(1.0, -h->qubo.coef.F), a);
+}
+
+// ex-QAOA state of one solve: per-layer phase-angle tables, the g buffer and the term list of the
+// moments kernel
+struct ExRun {
+  const int* tab;
+  const std::vector<int32_t>* pp;
+  float* g;
+  int nterms;
+  const int2* tbits;
+  const float* tc;
+  double* mpart;
+  uint32_t mgrid;
+};
+
+// the phase of an ex-QAOA layer: its angle (turns, 32-bit fixed point) from the layer's tables
+template <class T>
+static void set_ex_phase(const ExRun* ex, int g, int layer, int type, uint32_t grid, PassArgs<T>& a) {
+  set_table_args<T>(ex->tab, *ex->pp, layer, g, type, grid, (T)ldexp(1.0, -32), a);
+  if constexpr (sizeof(T) == 4) {
+    a.ph0 = 1.0f;   // phase_cs(q, 1, 0): exp(-i 2 pi q) with q in turns
+    a.ph1 = 0.0f;
+  } else {
+    a.ph0 = 6.283185307179586476925286766559;   // complex128: sincos(2 pi q)
+    a.ph1 = 0.0;
+  }
+}
+
+// ---------------------------------------------------------------- ex-QAOA per-term gradients
+//
+// After the adjoint phase pass of layer k has stored g(x) = 2 Im(conj(lambda) phi)(x), the
+// derivative by gamma_{k,j} is sum_x c_j s_j(x) g(x), with s_j = z_a z_b or z_a and z = 1 - 2x
+// (Sec. 2.3.2). On a tile of 4096 consecutive amplitudes (index bits 0..11) a Walsh-Hadamard
+// transform gives M[S] = sum_x prod_{k in S} z_k(x) g(x) for every subset S of the tile bits; term j
+// takes M[S_j] (its bits inside the tile) times its z over the tile-index bits. Each CTA walks a
+// fixed set of tiles, keeps its terms' sums in fp64 and writes them as partial rows; the rows are
+// summed over CTAs in a fixed order (deterministic).
+constexpr int MT_MAX = 1024;   // terms per solve
+__device__ __forceinline__ int mslot(int j) { return j + (j >> 4); }
+
+__device__ __forceinline__ void wht16(float (&v)[16]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int m = 0; m < 16; ++m)
+      if (!((m >> i) & 1)) {
+        const float x = v[m], y = v[m | (1 << i)];
+        v[m] = x + y;
+        v[m | (1 << i)] = x - y;
+      }
+}
+
+__global__ void __launch_bounds__(256) exq_moments_kernel(const float* __restrict__ g, int n, int nterms,
+                                                          const int2* __restrict__ tb, const float* __restrict__ tc,
+                                                          double* __restrict__ part) {
+  __shared__ float sm[4096 + 256];
+  const int t = threadIdx.x;
+  const uint32_t ntiles = 1u << (n - 12);
+  double acc[MT_MAX / 256];
+#pragma unroll
+  for (int i = 0; i < MT_MAX / 256; ++i) acc[i] = 0.0;
+  for (uint32_t T = blockIdx.x; T < ntiles; T += gridDim.x) {
+    float v[16];
+    const float* src = g + ((size_t)T << 12);
+#pragma unroll
+    for (int m = 0; m < 16; ++m) v[m] = __ldcs(src + t + 256 * m);   // register bits = tile bits 8..11
+    wht16(v);
+#pragma unroll
+    for (int m = 0; m < 16; ++m) sm[mslot(t + 256 * m)] = v[m];
+    __syncthreads();
+    const int pb = (t & 15) | ((t >> 4) << 8);                        // register bits = tile bits 4..7
+#pragma unroll
+    for (int m = 0; m < 16; ++m) v[m] = sm[mslot(pb | (m << 4))];
+    wht16(v);
+#pragma unroll
+    for (int m = 0; m < 16; ++m) sm[mslot(pb | (m << 4))] = v[m];
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < 16; ++m) v[m] = sm[mslot(m | (t << 4))];     // register bits = tile bits 0..3
+    wht16(v);
+#pragma unroll
+    for (int m = 0; m < 16; ++m) sm[mslot(m | (t << 4))] = v[m];
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < MT_MAX / 256; ++i) {
+      const int j = t + 256 * i;
+      if (j < nterms) {
+        const int2 b = tb[j];
+        int S = 0;
+        float sg = tc[j];
+        if (b.x < 12) S |= 1 << b.x;
+        else if ((T >> (b.x - 12)) & 1u) sg = -sg;
+        if (b.y >= 0) {
+          if (b.y < 12) S |= 1 << b.y;
+          else if ((T >> (b.y - 12)) & 1u) sg = -sg;
+        }
+        acc[i] += (double)(sg * sm[mslot(S)]);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < MT_MAX / 256; ++i) {
+    const int j = t + 256 * i;
+    if (j < nterms) part[(size_t)j * gridDim.x + blockIdx.x] = acc[i];
+  }
 }
 
 static bool shape_reads_q(int shape) { return shape != F2 && shape != R2; }
@@ -471,7 +602,7 @@ static bool shape_reads_q(int shape) { return shape != F2 && shape != R2; }
 
 template <class T>
 static int run_tiled(qvs_ctx* h, int p, const double* gammas, const double* ts, bool grad,
-                     double* E, double* dg, double* dt) {
+                     double* E, double* dg, double* dt, const ExRun* ex = nullptr, double* dG = nullptr) {
   using C = typename Cx<T>::t;
   Plan pl;
   QVS_TRY(make_plan(h->n, p, pl));
@@ -550,7 +681,8 @@ static int run_tiled(qvs_ctx* h, int p, const double* gammas, const double* ts, 
     int shape = pi.shape;
     if (j == F) shape = grad ? FE : FV;
     fwd_scalars<T>(a, shape, pi.lb, pi.la, pi.lg, G, n, p, gammas, ts, fr, lf);
-    if (qubo && shape_reads_q(shape)) set_qubo_args<T>(h, pi.type, grid, a);
+    if (qubo && shape_reads_q(shape)) set_qubo_args<T>(h, pl.g, pi.type, grid, a);
+    if (ex && pi.lg >= 0 && (shape == F0 || shape == F1)) set_ex_phase(ex, pl.g, pi.lg, pi.type, grid, a);
     if (j == F) {
       if (grad) {
         a.lam_out = h->lam.as<C>();
@@ -595,8 +727,22 @@ static int run_tiled(qvs_ctx* h, int p, const double* gammas, const double* ts, 
       // previous adjoint pass's uncompute
       Frame pf = (is_stored(j) || j == F - 1) ? fw[j] : pout;
       bwd_scalars<T>(a, shape, pi.lb, pi.la, pi.lg, G, n, gammas, ts, pf, lf);
-      if (qubo && shape_reads_q(shape)) set_qubo_args<T>(h, pi.type, grid, a);
+      if (qubo && shape_reads_q(shape)) set_qubo_args<T>(h, pl.g, pi.type, grid, a);
       pout = pf;
+      if (ex && pi.lg >= 0) {
+        set_ex_phase(ex, pl.g, pi.lg, pi.type, grid, a);
+        a.gout = reinterpret_cast<T*>(ex->g);
+        a.row_gam = -1;
+        QVS_TRY(launch_shape<T>(h, shape == R1 ? R1X : R0X, a, grid));
+        cudaEvent_t ev;
+        QVS_TRY(prof_begin(h, &ev));
+        exq_moments_kernel<<<ex->mgrid, 256, 0, h->stream>>>(
+            ex->g, n, ex->nterms, ex->tbits, ex->tc, ex->mpart + (size_t)pi.lg * ex->nterms * ex->mgrid);
+        QVS_CUDA_TRY(cudaGetLastError());
+        QVS_TRY(prof_end(h, "exq_moments", 4.0 * (double)h->dim, ev));
+        launches += 2;
+        continue;
+      }
       QVS_TRY(launch_shape<T>(h, shape, a, grid));
       ++launches;
     }
@@ -622,6 +768,20 @@ static int run_tiled(qvs_ctx* h, int p, const double* gammas, const double* ts, 
       dt[k] = h->host_res[1 + p + k];
     }
   }
+  if (ex && grad) {   // per-term sums over the moments kernel's CTAs
+    const int ns = p * ex->nterms;
+    ExData& X = h->ex;
+    std::vector<int> rm(3 * (size_t)ns, -1);
+    for (int s2 = 0; s2 < ns; ++s2) rm[3 * (size_t)s2] = s2;
+    QVS_TRY(X.mrowmap.ensure(sizeof(int) * rm.size()));
+    QVS_TRY(X.mres.ensure(sizeof(double) * ns));
+    QVS_CUDA_TRY(cudaMemcpyAsync(X.mrowmap.ptr, rm.data(), sizeof(int) * rm.size(), cudaMemcpyHostToDevice,
+                                 h->stream));
+    QVS_TRY(reduce_rows(h, ex->mpart, ex->mgrid, X.mrowmap.as<int>(), ns, X.mres.as<double>()));
+    QVS_CUDA_TRY(cudaMemcpyAsync(dG, X.mres.ptr, sizeof(double) * ns, cudaMemcpyDeviceToHost, h->stream));
+    QVS_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    h->launches += 1;
+  }
   return QVS_OK;
 }
 
@@ -637,6 +797,101 @@ static int hc_run(qvs_ctx* h, int p, const double* gammas, const double* ts, boo
                  : hc::run_tiled<float>(h, p, gammas, ts, grad, E, dg, dt);
   return small ? hc::run_small<double>(h, p, gammas, ts, grad, E, dg, dt)
                : hc::run_tiled<double>(h, p, gammas, ts, grad, E, dg, dt);
+}
+
+// ex-QAOA: per-layer phase-angle forms, their tables, the g buffer and the moments kernel's inputs
+static int ex_prepare(qvs_ctx* h, int p, const double* G, bool grad, hc::ExRun& run) {
+  using namespace hc;
+  ExData& X = h->ex;
+  const int n = h->n, J = (int)X.terms.size();
+  Plan pl;
+  QVS_TRY(make_plan(n, p, pl));
+  const uint32_t grid = 1u << (n - TB);
+  // angle of layer k in turns: sum_j gamma_kj c_j s_j / 2pi with s_j = z_a z_b = 1 - 2x_a - 2x_b + 4 x_a x_b
+  // (or z_a = 1 - 2 x_a), each coefficient reduced mod 1 turn into 32-bit fixed point
+  auto fx = [](double x) -> int32_t {
+    const double f = x - floor(x);
+    return (int32_t)(uint32_t)(int64_t)llround(f * 4294967296.0);
+  };
+  std::vector<QuboCoef> coefs(p);
+  std::vector<double> c1(p), h1((size_t)p * n), j1((size_t)p * n * n);
+  for (int k = 0; k < p; ++k) {
+    double c = 0.0;
+    std::vector<double> hh(n, 0.0), jj((size_t)n * n, 0.0);
+    for (int j = 0; j < J; ++j) {
+      const ExTerm& t = X.terms[j];
+      const double w = G[(size_t)k * J + j] * t.c / 6.283185307179586476925286766559;
+      c += w;
+      hh[t.a] -= 2.0 * w;
+      if (t.b >= 0) {
+        hh[t.b] -= 2.0 * w;
+        jj[(size_t)t.a * n + t.b] += 4.0 * w;
+        jj[(size_t)t.b * n + t.a] += 4.0 * w;
+      }
+    }
+    QuboCoef& Q = coefs[k];
+    Q.n = n;
+    Q.F = 32;
+    Q.c = fx(c);
+    for (int b = 0; b < n; ++b) Q.h[b] = fx(hh[b]);
+    for (int b = 0; b < n; ++b)
+      for (int b2 = 0; b2 < n; ++b2) Q.J[b][b2] = b == b2 ? 0 : fx(jj[(size_t)b * n + b2]);
+  }
+  QVS_TRY(build_tables(h, pl, grid, coefs.data(), p, X.coef, X.tab, X.pp));
+  run = ExRun{};
+  run.tab = X.tab.as<int>();
+  run.pp = &X.pp;
+  run.nterms = J;
+  if (grad) {
+    QVS_TRY(X.g.ensure(sizeof(float) * (size_t)h->dim));
+    std::vector<int2> tb(J);
+    std::vector<float> tc(J);
+    for (int j = 0; j < J; ++j) {
+      tb[j] = make_int2(X.terms[j].a, X.terms[j].b);
+      tc[j] = (float)X.terms[j].c;
+    }
+    QVS_TRY(X.mterms.ensure((sizeof(int2) + sizeof(float)) * (size_t)J));
+    QVS_CUDA_TRY(cudaMemcpyAsync(X.mterms.ptr, tb.data(), sizeof(int2) * J, cudaMemcpyHostToDevice, h->stream));
+    float* tcd = reinterpret_cast<float*>(X.mterms.as<int2>() + J);
+    QVS_CUDA_TRY(cudaMemcpyAsync(tcd, tc.data(), sizeof(float) * J, cudaMemcpyHostToDevice, h->stream));
+    run.g = X.g.as<float>();
+    run.tbits = X.mterms.as<int2>();
+    run.tc = tcd;
+    run.mgrid = std::min<uint32_t>((uint32_t)(h->dim >> 12), 512u);
+    QVS_TRY(X.mpart.ensure(sizeof(double) * (size_t)p * J * run.mgrid));
+    run.mpart = X.mpart.as<double>();
+    QVS_CUDA_TRY(cudaStreamSynchronize(h->stream));   // the host term arrays go out of scope
+  }
+  return QVS_OK;
+}
+
+static int ex_check(qvs_ctx* h) {
+  if (h->precision != QVS_C64 || h->n <= hc::TB || h->n > 32) return QVS_EUNSUPPORTED;
+  if (h->ex.terms.empty()) return QVS_ESTATE;
+  return QVS_OK;
+}
+
+int hc_evolve_ex(qvs_ctx* h, int p, const double* gammas, const double* ts) {
+  QVS_TRY(ex_check(h));
+  hc::ExRun run;
+  QVS_TRY(ex_prepare(h, p, gammas, false, run));
+  std::vector<double> zg(p, 0.0);
+  double E = 0.0;
+  QVS_TRY(hc::run_tiled<float>(h, p, zg.data(), ts, false, &E, nullptr, nullptr, &run, nullptr));
+  h->E = E;
+  h->have_E = true;
+  return QVS_OK;
+}
+
+int hc_gradient_ex(qvs_ctx* h, int p, const double* gammas, const double* ts, double* E, double* dG,
+                   double* dt) {
+  QVS_TRY(ex_check(h));
+  if ((int)h->ex.terms.size() > hc::MT_MAX) return QVS_EUNSUPPORTED;
+  hc::ExRun run;
+  QVS_TRY(ex_prepare(h, p, gammas, true, run));
+  std::vector<double> zg(p, 0.0), dg(p, 0.0);
+  h->have_E = false;
+  return hc::run_tiled<float>(h, p, zg.data(), ts, true, E, dg.data(), dt, &run, dG);
 }
 
 int hc_evolve(qvs_ctx* h, int p, const double* gammas, const double* ts) {

@@ -78,6 +78,22 @@ struct QuboData {
   std::vector<int32_t> pp;    // per tile type and frame: 16 register pair sums
 };
 
+// ex-QAOA phase terms (qvs_set_phase_terms): Sigma_j = c_j Z_a Z_b (b < 0: c_j Z_a) over INDEX bits.
+struct ExTerm {
+  int32_t a, b;
+  double c;
+};
+struct ExData {
+  std::vector<ExTerm> terms;  // empty: plain QAOA phase
+  DevBuf coef;                // per-layer QuboCoef of the phase angle in 2^-32 turns
+  DevBuf tab;                 // per layer, tile type and frame: CTA rows + thread rows
+  std::vector<int32_t> pp;    // per layer, tile type and frame: 16 register pair sums
+  DevBuf g;                   // float[dim]: 2 Im(conj(lambda) phi) at one phase point
+  DevBuf mterms;              // int2[nterms] index bits, float[nterms] coefficients
+  DevBuf mpart;               // double[p * nterms * grid] moment partial rows
+  DevBuf mrowmap, mres;       // identity row map and final per-term sums
+};
+
 // Circulant mixer data: eigenvalues in the order the FFT passes produce them.
 struct CircData {
   DevBuf lam;           // float2[dim]: eigenvalues (hi, lo) in row-spectral thread-major order
@@ -128,6 +144,7 @@ struct qvs_ctx {
   qvs::CircData circ;
   qvs::CsrData csr;
   qvs::QuboData qubo;
+  qvs::ExData ex;
 
   // QVS_OPT_PROFILE: per-kernel event timing
   struct KStat {
@@ -168,6 +185,10 @@ int ensure_q_vector(qvs_ctx* h);
 int hc_evolve(qvs_ctx* h, int p, const double* gammas, const double* ts);
 int hc_gradient(qvs_ctx* h, int p, const double* gammas, const double* ts, double* E, double* dg,
                 double* dt);
+// ex-QAOA on the tiled hypercube path: gammas / dG hold p * nterms values (layer-major)
+int hc_evolve_ex(qvs_ctx* h, int p, const double* gammas, const double* ts);
+int hc_gradient_ex(qvs_ctx* h, int p, const double* gammas, const double* ts, double* E, double* dG,
+                   double* dt);
 
 // circulant (QWOA) path: circulant.cu
 int circ_set_mixer(qvs_ctx* h, const qvs_mixer_desc* d);

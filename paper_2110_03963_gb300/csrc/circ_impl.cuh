@@ -41,6 +41,14 @@ __device__ __forceinline__ size_t priv_idx(uint32_t blk, int r, int tid) {
   return ((size_t)blk * R + r) * NT + tid;
 }
 
+// Compiler fence after every 8th register of a per-register loop: the loads of the next group are
+// not hoisted above it, so at most 8 registers' side-vector loads (stored psi, q) are in flight at
+// once instead of all 32 competing with the 64 state registers for the 128 a thread has.
+template <int r>
+__device__ __forceinline__ void group_fence() {
+  if constexpr ((r & 7) == 7) asm volatile("" ::: "memory");
+}
+
 // fractional turns of x * y for float-float x and y (|x y| well below 2^24)
 __device__ __forceinline__ float ff_turns(float xh, float xl, float yh, float yl) {
   const float p = xh * yh;
@@ -185,13 +193,14 @@ __global__ void __launch_bounds__(NT, 1) col_kernel(const __grid_constant__ Circ
           __stcs(a.out + gidx(jt | G::jreg(2, r)), x);
         });
       } else {
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
+        static_for<R>([&](auto ri) {
+          constexpr int r = decltype(ri)::value;
           const float q = qat(r);
           const float2 x = make_float2(v[r].x * invL, v[r].y * invL);
           e += q * (x.x * x.x + x.y * x.y);
           v[r] = make_float2(q * x.x, q * x.y);
-        }
+          group_fence<r>();
+        });
         tile_fwd<G>(v, sm, ts, tid);
         gtw(v, false);
         gstore0(v, a.out);
@@ -213,6 +222,7 @@ __global__ void __launch_bounds__(NT, 1) col_kernel(const __grid_constant__ Circ
         const float2 l = make_float2(v[r].x * invL, v[r].y * invL);
         g += q * (l.x * phi.y - l.y * phi.x);
         v[r] = make_float2(c * l.x - s * l.y, c * l.y + s * l.x);                   // P^dagger lambda'
+        group_fence<r>();
       });
       if constexpr (MODE == RCM) {
         tile_fwd<G>(v, sm, ts, tid);

@@ -53,8 +53,12 @@ __host__ __device__ constexpr int bitrev(int x, int d) {
 
 // Geometry of a tile DFT over tile bits [CB, 14) with digits D1 (low), D2, D3 (high); tile bits
 // below CB are spectator columns. Step layout k (0, 1, 2 for digits 1, 2, 3) holds digit k in
-// register bits 0..d_k-1 and the lowest other tile bits as spectators in the rest; thread bits are
-// the remaining tile bits in increasing order.
+// register bits 0..d_k-1 and spectators in the rest; thread bits are the remaining tile bits in
+// increasing order. Row tiles (CB = 0) take the lowest other tile bits as spectators. Column tiles
+// take the other digits' bits, highest first, then the highest column bits, so that the lowest
+// column bits (consecutive addresses) are lane bits: a warp's global load or store of one register
+// then covers whole 32-byte sectors, where the lowest-bit choice spread it over two to four times
+// as many partly used sectors.
 template <int CB, int D1, int D2, int D3>
 struct Geo {
   static_assert(CB + D1 + D2 + D3 == TB, "digits must cover the transform bits");
@@ -66,7 +70,10 @@ struct Geo {
   __host__ __device__ static constexpr int regbit(int k, int i) {
     if (i < dsize(k)) return dstart(k) + i;
     int need = i - dsize(k);
-    for (int b = 0; b < TB; ++b) {
+    for (int m = 0; m < TB; ++m) {
+      // candidate order: ascending for row tiles; descending for column tiles (the transform bits
+      // from the top, then the column bits from the top)
+      const int b = CB == 0 ? m : TB - 1 - m;
       if (b >= dstart(k) && b < dstart(k) + dsize(k)) continue;
       if (need == 0) return b;
       --need;

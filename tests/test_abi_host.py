@@ -102,3 +102,31 @@ def test_qubo_from_maxcut_matches_oracle_maxcut(qvs):
         qvs.qvs_qubo_from_maxcut(4, [0], [0])
     with pytest.raises(qvs.QvsError):
         qvs.qvs_qubo_from_maxcut(4, [0], [4])
+
+
+def test_new_entry_points_reject_bad_arguments_without_gpu(qvs):
+    """Argument checks of the quadratic-quality, ex-QAOA and parity-state entry points run before
+    any device work, so they are exercised here without a GPU."""
+    import ctypes
+    lib = qvs.load()
+    D = ctypes.POINTER(ctypes.c_double)
+    h = np.zeros(4)
+    J = np.zeros(16)
+    hp, Jp = h.ctypes.data_as(D), J.ctypes.data_as(D)
+    dummy = ctypes.c_void_p(1)   # never dereferenced: every call below fails its checks first
+    for n in (0, 33):
+        assert lib.qvs_quality_qubo(n, 0.0, hp, Jp, qvs.QVS_F32, dummy, None) == qvs.QVS_EINVAL
+    assert lib.qvs_quality_qubo(4, 0.0, hp, Jp, qvs.QVS_F32, None, None) == qvs.QVS_EINVAL
+    bad = np.array([0.0, np.inf, 0.0, 0.0])
+    assert lib.qvs_quality_qubo(4, 0.0, bad.ctypes.data_as(D), Jp, qvs.QVS_F32, dummy, None) == qvs.QVS_EINVAL
+    assert lib.qvs_set_quality_qubo(None, 4, 0.0, hp, Jp) == qvs.QVS_EINVAL
+    i32 = ctypes.POINTER(ctypes.c_int32)
+    u = np.zeros(1, dtype=np.int32)
+    assert lib.qvs_set_phase_terms(None, 1, u.ctypes.data_as(i32), u.ctypes.data_as(i32), hp) == qvs.QVS_EINVAL
+    g = np.zeros(4)
+    E = ctypes.c_double()
+    assert lib.qvs_evolve_ex(None, 1, g.ctypes.data_as(D), g.ctypes.data_as(D)) == qvs.QVS_EINVAL
+    assert lib.qvs_gradient_ex(None, 1, g.ctypes.data_as(D), g.ctypes.data_as(D), ctypes.byref(E),
+                               g.ctypes.data_as(D), g.ctypes.data_as(D)) == qvs.QVS_EINVAL
+    for n, A in ((13, 1), (12, 7), (12, -1), (0, 0)):
+        assert lib.qvs_state_parity(n, A, dummy, None) == qvs.QVS_EINVAL

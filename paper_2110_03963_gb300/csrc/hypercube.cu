@@ -814,7 +814,6 @@ static int ex_prepare(qvs_ctx* h, int p, const double* G, bool grad, hc::ExRun& 
     return (int32_t)(uint32_t)(int64_t)llround(f * 4294967296.0);
   };
   std::vector<QuboCoef> coefs(p);
-  std::vector<double> c1(p), h1((size_t)p * n), j1((size_t)p * n * n);
   for (int k = 0; k < p; ++k) {
     double c = 0.0;
     std::vector<double> hh(n, 0.0), jj((size_t)n * n, 0.0);

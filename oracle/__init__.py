@@ -572,6 +572,78 @@ def central_fd(prob: Problem, gammas, ts, h: float = 1e-3):
     return dg, dt
 
 
+# ============================================================== classical optimiser (Sec. 4)
+
+
+def bfgs_minimize(fg, x0, gtol: float = 1e-8, max_iter: int = 1000, c1: float = 1e-4):
+    """BFGS quasi-Newton minimisation, the paper's default classical optimiser (Sec. 4 uses
+    SciPy's BFGS through `minimize`), written out step by step:
+
+    * search direction d = -H g with H the inverse-Hessian estimate (H_0 = I);
+    * backtracking line search from step 1, halving until the Armijo condition
+      f(x + a d) <= f(x) + c1 a g.d holds;
+    * with s = x_new - x and y = g_new - g, the inverse update
+      H <- (I - rho s y^T) H (I - rho y s^T) + rho s s^T, rho = 1 / y.s, skipped when y.s <= 0
+      (the curvature condition fails) so that H stays positive definite;
+    * stop when max |g| <= gtol.
+
+    fg(x) returns (f, g). Returns (x, f, iterations, evaluations)."""
+    x = np.asarray(x0, dtype=np.float64).copy()
+    n = x.shape[0]
+    f, g = fg(x)
+    g = np.asarray(g, dtype=np.float64)
+    H = np.eye(n)
+    evals = 1
+    it = 0
+    while it < max_iter and np.max(np.abs(g)) > gtol:
+        d = -H @ g
+        slope = float(g @ d)
+        if slope >= 0.0:            # not a descent direction: restart from steepest descent
+            H = np.eye(n)
+            d = -g
+            slope = float(g @ d)
+        a = 1.0
+        while True:
+            xn = x + a * d
+            fn, gn = fg(xn)
+            evals += 1
+            if fn <= f + c1 * a * slope or a < 1e-20:
+                break
+            a *= 0.5
+        gn = np.asarray(gn, dtype=np.float64)
+        s_ = xn - x
+        y_ = gn - g
+        ys = float(y_ @ s_)
+        if ys > 0.0:
+            rho = 1.0 / ys
+            I = np.eye(n)
+            H = (I - rho * np.outer(s_, y_)) @ H @ (I - rho * np.outer(y_, s_)) + rho * np.outer(s_, s_)
+        x, f, g = xn, fn, gn
+        it += 1
+    return x, f, it, evals
+
+
+def optimise(prob: Problem, gammas0, ts0, gtol: float = 1e-8, max_iter: int = 1000):
+    """Minimise f(theta) = <theta|Q|theta> over theta = (gamma_1, t_1, ..., gamma_p, t_p) (the layer
+    order of Example 1) with `bfgs_minimize` and the adjoint gradient. Returns
+    (gammas, ts, f, iterations, evaluations)."""
+    p = len(gammas0)
+
+    def fg(th):
+        gs, ts = th[0::2], th[1::2]
+        f, dg, dt = gradient(prob, gs, ts)
+        out = np.empty(2 * p)
+        out[0::2] = dg
+        out[1::2] = dt
+        return f, out
+
+    th0 = np.empty(2 * p)
+    th0[0::2] = gammas0
+    th0[1::2] = ts0
+    th, f, it, ev = bfgs_minimize(fg, th0, gtol=gtol, max_iter=max_iter)
+    return th[0::2], th[1::2], f, it, ev
+
+
 # ============================================================== convenience builders
 
 

@@ -606,3 +606,52 @@ def test_exqaoa_gradient_vs_richardson_fd():
             tx[k] += hh
             return obj(G, tx)
         assert abs(rich(ft) - dt[k]) < 1e-8
+
+
+# ------------------------------------------------------------------ classical optimiser (Sec. 4: BFGS)
+
+def test_bfgs_quadratic_and_rosenbrock():
+    """A positive-definite quadratic reaches its closed-form minimiser A^-1 b; the Rosenbrock
+    function from (-1.2, 1) reaches (1, 1)."""
+    rng = wl.rng_for(200)
+    M = rng.standard_normal((6, 6))
+    A = M @ M.T + 6 * np.eye(6)
+    b = rng.standard_normal(6)
+    x, f, it, ev = orc.bfgs_minimize(lambda x: (0.5 * x @ A @ x - b @ x, A @ x - b), np.zeros(6), gtol=1e-12)
+    assert np.max(np.abs(x - np.linalg.solve(A, b))) < 1e-10
+    assert abs(f + 0.5 * b @ np.linalg.solve(A, b)) < 1e-12
+
+    def rosen(z):
+        a, c = z
+        return (1 - a) ** 2 + 100 * (c - a * a) ** 2, np.array([-2 * (1 - a) - 400 * a * (c - a * a), 200 * (c - a * a)])
+    x, f, it, ev = orc.bfgs_minimize(rosen, np.array([-1.2, 1.0]), gtol=1e-10)
+    assert np.max(np.abs(x - 1.0)) < 1e-8 and f < 1e-16
+
+
+def test_optimise_qaoa_matches_scipy_bfgs_and_closed_form():
+    """p=1 QAOA on a 3-regular 8-vertex graph: from the same start the written-out BFGS and SciPy's
+    BFGS (a library routine) reach the same optimum, which also equals the best value of the p=1
+    closed form on a fine (gamma, t) grid refined by the same optimiser."""
+    scipy_optimize = pytest.importorskip("scipy.optimize")
+    n = 8
+    G = wl.regular3_graph(n, wl.rng_for(201))
+    prob = orc.maxcut_problem(n, G.eu, G.ev)
+    g0, t0 = np.array([0.6]), np.array([0.4])
+    gs, ts, f, it, ev = orc.optimise(prob, g0, t0, gtol=1e-10)
+
+    def fg(th):
+        E, dg, dt = orc.gradient(prob, th[0::2], th[1::2])
+        return E, np.array([dg[0], dt[0]])
+    res = scipy_optimize.minimize(fg, np.array([0.6, 0.4]), jac=True, method="BFGS", options={"gtol": 1e-10})
+    # same optimal value; the points themselves may differ by the ansatz's symmetries
+    # (t -> t + pi, the gamma period of integer qualities), so they are not compared
+    assert abs(f - res.fun) < 1e-9
+    # the optimum is a stationary point of the p=1 closed form, with the same value there
+    assert abs(cf.p1_maxcut_expectation(n, G.eu, G.ev, None, gs[0], ts[0]) - f) < 1e-10
+    assert np.max(np.abs(cf.p1_maxcut_gradient(n, G.eu, G.ev, None, gs[0], ts[0]))) < 1e-5
+    # started from the best point of a (gamma, t) grid of the closed form, it ends at or below it
+    grid = np.linspace(0.0, math.pi, 41)
+    best = min((cf.p1_maxcut_expectation(n, G.eu, G.ev, None, gg, tt), gg, tt) for gg in grid for tt in grid)
+    gs2, ts2, f2, _, _ = orc.optimise(prob, np.array([best[1]]), np.array([best[2]]), gtol=1e-10)
+    assert f2 <= best[0] + 1e-12
+    assert abs(cf.p1_maxcut_expectation(n, G.eu, G.ev, None, gs2[0], ts2[0]) - f2) < 1e-10

@@ -172,6 +172,26 @@ int qvs_evolve_ex(qvs_t h, int p, const double* gammas, const double* ts);
 int qvs_gradient_ex(qvs_t h, int p, const double* gammas, const double* ts, double* E, double* dgamma,
                     double* dt);
 
+/* Objective-and-gradient callback of qvs_bfgs_minimize: writes f(x) and g = grad f(x) (n values)
+ * for the point x; returns QVS_OK or an error status, which stops the minimisation. */
+typedef int (*qvs_fg_fn)(const double* x, double* f, double* g, void* user);
+
+/* Sec. 4: BFGS minimisation (the paper's default optimiser), on the host: direction -H g with the
+ * inverse-Hessian estimate H (identity at the start and after a non-descent direction),
+ * backtracking line search from step 1 halving until f(x + a d) <= f(x) + 1e-4 a g.d, inverse
+ * update H <- (I - rho s y^T) H (I - rho y s^T) + rho s s^T (rho = 1/y.s, skipped when y.s <= 0),
+ * stop at max |g| <= gtol or after max_iter iterations. x (n host values) is the start and
+ * receives the result; f_out, iters_out, evals_out may be NULL. QVS_EINVAL for n outside
+ * 1..8192, NULL x or fg, negative max_iter or gtol; a callback error is returned as is. */
+int qvs_bfgs_minimize(int n, double* x, qvs_fg_fn fg, void* user, double gtol, int max_iter,
+                      double* f_out, int* iters_out, int* evals_out);
+
+/* Sec. 4: minimise f(theta) = <theta|Q|theta> over theta = (gamma_1, t_1, ..., gamma_p, t_p) with
+ * qvs_bfgs_minimize, each evaluation one qvs_gradient on the handle (device objective and adjoint
+ * gradient). gammas, ts (host, p values) hold the start and receive the result. */
+int qvs_optimise(qvs_t h, int p, double* gammas, double* ts, double gtol, int max_iter, double* f_out,
+                 int* iters_out, int* evals_out);
+
 /* Sec. 2.1: f = <theta|Q|theta> of the last qvs_evolve (fp64 reduction). */
 int qvs_expectation(qvs_t h, double* E);
 

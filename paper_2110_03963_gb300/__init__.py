@@ -35,7 +35,7 @@ EXPORTED = [
     "qvs_xy_ring_csr", "qvs_state_parity", "qvs_batch_create", "qvs_batch_set_quality", "qvs_batch_gradient",
     "qvs_batch_info", "qvs_batch_destroy", "qvs_gradient_small_noalloc", "qvs_strerror",
     "qvs_set_quality_qubo", "qvs_quality_qubo", "qvs_qubo_from_maxcut",
-    "qvs_set_phase_terms", "qvs_evolve_ex", "qvs_gradient_ex",
+    "qvs_set_phase_terms", "qvs_evolve_ex", "qvs_gradient_ex", "qvs_bfgs_minimize", "qvs_optimise",
 ]
 
 
@@ -64,6 +64,10 @@ class MixerDesc(ctypes.Structure):
 
 
 _lib = None
+
+# objective-and-gradient callback of qvs_bfgs_minimize: (x, f, g, user) -> status
+FG_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                         ctypes.POINTER(ctypes.c_double), ctypes.c_void_p)
 
 
 def load(path: str = LIB_PATH):
@@ -106,6 +110,8 @@ def load(path: str = LIB_PATH):
         "qvs_set_phase_terms": (I, [V, I, P(ctypes.c_int32), P(ctypes.c_int32), P(D)]),
         "qvs_evolve_ex": (I, [V, I, P(D), P(D)]),
         "qvs_gradient_ex": (I, [V, I, P(D), P(D), P(D), P(D), P(D)]),
+        "qvs_bfgs_minimize": (I, [I, P(D), FG_FN, V, D, I, P(D), P(I), P(I)]),
+        "qvs_optimise": (I, [V, I, P(D), P(D), D, I, P(D), P(I), P(I)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -329,6 +335,50 @@ def qvs_gradient_ex(h, gammas, ts):
     return E.value, dG, dt
 
 
+def qvs_bfgs_minimize(fg, x0, gtol: float = 1e-8, max_iter: int = 1000):
+    """BFGS on the host with a Python objective: fg(x) -> (f, g). Returns (x, f, iterations,
+    evaluations)."""
+    x = np.ascontiguousarray(x0, dtype=np.float64).copy()
+    n = x.shape[0]
+    err = []
+
+    def cb(xp, fp, gp, _user):
+        try:
+            xv = np.ctypeslib.as_array(xp, shape=(n,)).copy()
+            f, g = fg(xv)
+            fp[0] = float(f)
+            gv = np.asarray(g, dtype=np.float64)
+            for i in range(n):
+                gp[i] = float(gv[i])
+            return QVS_OK
+        except Exception as e:   # reported after the call; a non-zero status stops the loop
+            err.append(e)
+            return -1
+    cfn = FG_FN(cb)
+    f = ctypes.c_double()
+    it = ctypes.c_int()
+    ev = ctypes.c_int()
+    st = load().qvs_bfgs_minimize(n, _dptr(x), cfn, None, float(gtol), int(max_iter), ctypes.byref(f),
+                                  ctypes.byref(it), ctypes.byref(ev))
+    if err:
+        raise err[0]
+    _check(st, "qvs_bfgs_minimize")
+    return x, f.value, it.value, ev.value
+
+
+def qvs_optimise(h, gammas0, ts0, gtol: float = 1e-6, max_iter: int = 200):
+    """BFGS over theta = (gamma_1, t_1, ...) with the device gradient. Returns
+    (gammas, ts, f, iterations, evaluations)."""
+    g = np.ascontiguousarray(gammas0, dtype=np.float64).copy()
+    t = np.ascontiguousarray(ts0, dtype=np.float64).copy()
+    f = ctypes.c_double()
+    it = ctypes.c_int()
+    ev = ctypes.c_int()
+    _check(load().qvs_optimise(h, len(g), _dptr(g), _dptr(t), float(gtol), int(max_iter), ctypes.byref(f),
+                               ctypes.byref(it), ctypes.byref(ev)), "qvs_optimise")
+    return g, t, f.value, it.value, ev.value
+
+
 def qvs_quality_subset(n: int, w, out, dtype: int, stream=None):
     w = np.ascontiguousarray(w, dtype=np.float64)
     p, dev = _ptr_of(out)
@@ -539,6 +589,9 @@ class Simulator:
     def set_phase_terms(self, u, v, coef):
         qvs_set_phase_terms(self.h, u, v, coef)
         return self
+
+    def optimise(self, gammas0, ts0, gtol: float = 1e-6, max_iter: int = 200):
+        return qvs_optimise(self.h, gammas0, ts0, gtol, max_iter)
 
     def evolve_ex(self, gammas, ts) -> float:
         return qvs_evolve_ex(self.h, gammas, ts)

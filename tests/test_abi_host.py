@@ -130,3 +130,35 @@ def test_new_entry_points_reject_bad_arguments_without_gpu(qvs):
                                g.ctypes.data_as(D), g.ctypes.data_as(D)) == qvs.QVS_EINVAL
     for n, A in ((13, 1), (12, 7), (12, -1), (0, 0)):
         assert lib.qvs_state_parity(n, A, dummy, None) == qvs.QVS_EINVAL
+
+
+def test_bfgs_minimize_matches_oracle(qvs):
+    """The library's host BFGS (no GPU involved) against the oracle's written-out BFGS on the same
+    functions: a positive-definite quadratic and Rosenbrock."""
+    rng = np.random.default_rng(202)
+    M = rng.standard_normal((5, 5))
+    A = M @ M.T + 5 * np.eye(5)
+    b = rng.standard_normal(5)
+    quad = lambda x: (0.5 * x @ A @ x - b @ x, A @ x - b)
+    # gtol well above the fp64 resolution of the Armijo test (|f| ~ 0.1, so decreases below ~1e-17
+    # are invisible and a tighter gtol would only run into the iteration cap)
+    x, f, it, ev = qvs.qvs_bfgs_minimize(quad, np.zeros(5), gtol=1e-8)
+    xo, fo, ito, evo = orc.bfgs_minimize(quad, np.zeros(5), gtol=1e-8)
+    assert np.max(np.abs(A @ x - b)) <= 1e-8 and it < 200
+    assert np.max(np.abs(x - np.linalg.solve(A, b))) < 1e-8
+    assert (it, ev) == (ito, evo) and abs(f - fo) < 1e-14 and np.max(np.abs(x - xo)) < 1e-12
+
+    def rosen(z):
+        a, c = z
+        return (1 - a) ** 2 + 100 * (c - a * a) ** 2, np.array([-2 * (1 - a) - 400 * a * (c - a * a), 200 * (c - a * a)])
+    x, f, it, ev = qvs.qvs_bfgs_minimize(rosen, np.array([-1.2, 1.0]), gtol=1e-10)
+    xo, fo, ito, evo = orc.bfgs_minimize(rosen, np.array([-1.2, 1.0]), gtol=1e-10)
+    assert np.max(np.abs(x - 1.0)) < 1e-8
+    assert abs(it - ito) <= 2 and np.max(np.abs(x - xo)) < 1e-8
+
+
+def test_bfgs_minimize_argument_errors_and_callback_failure(qvs):
+    with pytest.raises(qvs.QvsError):
+        qvs.qvs_bfgs_minimize(lambda x: (0.0, x), np.zeros(0))
+    with pytest.raises(ZeroDivisionError):
+        qvs.qvs_bfgs_minimize(lambda x: (1.0 / 0.0, x), np.ones(2))

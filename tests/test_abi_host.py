@@ -162,3 +162,16 @@ def test_bfgs_minimize_argument_errors_and_callback_failure(qvs):
         qvs.qvs_bfgs_minimize(lambda x: (0.0, x), np.zeros(0))
     with pytest.raises(ZeroDivisionError):
         qvs.qvs_bfgs_minimize(lambda x: (1.0 / 0.0, x), np.ones(2))
+
+
+def test_optimise_rejects_bad_arguments_without_gpu(qvs):
+    import ctypes
+    lib = qvs.load()
+    D = ctypes.POINTER(ctypes.c_double)
+    g = np.zeros(2)
+    f = ctypes.c_double()
+    it = ctypes.c_int()
+    assert lib.qvs_optimise(None, 1, g.ctypes.data_as(D), g.ctypes.data_as(D), 1e-6, 10, ctypes.byref(f),
+                            ctypes.byref(it), ctypes.byref(it)) == qvs.QVS_EINVAL
+    with pytest.raises(qvs.QvsError):
+        qvs.qvs_bfgs_minimize(lambda x: (0.0, x), np.zeros(3), gtol=-1.0)

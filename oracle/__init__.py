@@ -575,19 +575,25 @@ def central_fd(prob: Problem, gammas, ts, h: float = 1e-3):
 # ============================================================== classical optimiser (Sec. 4)
 
 
+BFGS_MAX_HALVINGS = 30   # line-search step sizes 1, 1/2, ..., 2^-30
+
+
 def bfgs_minimize(fg, x0, gtol: float = 1e-8, max_iter: int = 1000, c1: float = 1e-4):
     """BFGS quasi-Newton minimisation, the paper's default classical optimiser (Sec. 4 uses
     SciPy's BFGS through `minimize`), written out step by step:
 
     * search direction d = -H g with H the inverse-Hessian estimate (H_0 = I);
     * backtracking line search from step 1, halving until the Armijo condition
-      f(x + a d) <= f(x) + c1 a g.d holds;
+      f(x + a d) <= f(x) + c1 a g.d holds, for at most BFGS_MAX_HALVINGS halvings;
     * with s = x_new - x and y = g_new - g, the inverse update
       H <- (I - rho s y^T) H (I - rho y s^T) + rho s s^T, rho = 1 / y.s, skipped when y.s <= 0
       (the curvature condition fails) so that H stays positive definite;
-    * stop when max |g| <= gtol.
+    * stop when max |g| <= gtol (stop = 0), after max_iter iterations (stop = 1), or when no step
+      of the line search decreases f enough (stop = 2: the objective's rounding hides any further
+      descent; x, f, g stay at the last accepted point, as SciPy's BFGS ends with its
+      precision-loss message).
 
-    fg(x) returns (f, g). Returns (x, f, iterations, evaluations)."""
+    fg(x) returns (f, g). Returns (x, f, iterations, evaluations, stop)."""
     x = np.asarray(x0, dtype=np.float64).copy()
     n = x.shape[0]
     f, g = fg(x)
@@ -595,7 +601,11 @@ def bfgs_minimize(fg, x0, gtol: float = 1e-8, max_iter: int = 1000, c1: float = 
     H = np.eye(n)
     evals = 1
     it = 0
-    while it < max_iter and np.max(np.abs(g)) > gtol:
+    stop = 1
+    while it < max_iter:
+        if np.max(np.abs(g)) <= gtol:
+            stop = 0
+            break
         d = -H @ g
         slope = float(g @ d)
         if slope >= 0.0:            # not a descent direction: restart from steepest descent
@@ -603,13 +613,18 @@ def bfgs_minimize(fg, x0, gtol: float = 1e-8, max_iter: int = 1000, c1: float = 
             d = -g
             slope = float(g @ d)
         a = 1.0
-        while True:
+        accepted = False
+        for _ in range(BFGS_MAX_HALVINGS + 1):
             xn = x + a * d
             fn, gn = fg(xn)
             evals += 1
-            if fn <= f + c1 * a * slope or a < 1e-20:
+            if fn <= f + c1 * a * slope:
+                accepted = True
                 break
             a *= 0.5
+        if not accepted:
+            stop = 2
+            break
         gn = np.asarray(gn, dtype=np.float64)
         s_ = xn - x
         y_ = gn - g
@@ -620,13 +635,16 @@ def bfgs_minimize(fg, x0, gtol: float = 1e-8, max_iter: int = 1000, c1: float = 
             H = (I - rho * np.outer(s_, y_)) @ H @ (I - rho * np.outer(y_, s_)) + rho * np.outer(s_, s_)
         x, f, g = xn, fn, gn
         it += 1
-    return x, f, it, evals
+    else:
+        if np.max(np.abs(g)) <= gtol:
+            stop = 0
+    return x, f, it, evals, stop
 
 
 def optimise(prob: Problem, gammas0, ts0, gtol: float = 1e-8, max_iter: int = 1000):
     """Minimise f(theta) = <theta|Q|theta> over theta = (gamma_1, t_1, ..., gamma_p, t_p) (the layer
     order of Example 1) with `bfgs_minimize` and the adjoint gradient. Returns
-    (gammas, ts, f, iterations, evaluations)."""
+    (gammas, ts, f, iterations, evaluations, stop)."""
     p = len(gammas0)
 
     def fg(th):
@@ -640,8 +658,8 @@ def optimise(prob: Problem, gammas0, ts0, gtol: float = 1e-8, max_iter: int = 10
     th0 = np.empty(2 * p)
     th0[0::2] = gammas0
     th0[1::2] = ts0
-    th, f, it, ev = bfgs_minimize(fg, th0, gtol=gtol, max_iter=max_iter)
-    return th[0::2], th[1::2], f, it, ev
+    th, f, it, ev, stop = bfgs_minimize(fg, th0, gtol=gtol, max_iter=max_iter)
+    return th[0::2], th[1::2], f, it, ev, stop
 
 
 # ============================================================== convenience builders

@@ -612,21 +612,45 @@ def test_exqaoa_gradient_vs_richardson_fd():
 
 def test_bfgs_quadratic_and_rosenbrock():
     """A positive-definite quadratic reaches its closed-form minimiser A^-1 b; the Rosenbrock
-    function from (-1.2, 1) reaches (1, 1)."""
+    function from (-1.2, 1) reaches (1, 1).
+
+    Bound on the quadratic: the loop stops with max|g| <= gtol, g = A (x - x*), and A = M M^T + 6 I
+    has lambda_min(A) >= 6, so max|x - x*| <= ||x - x*||_2 <= ||g||_2 / 6 <= sqrt(6) gtol / 6 =
+    gtol / sqrt(6). gtol = 1e-8 is about the smallest the Armijo test can resolve here: a step
+    near x* lowers f by about g^T A^-1 g / 2 ~ 1e-17 when max|g| ~ 1e-8, which is the fp64
+    spacing of |f| ~ 0.1; below that no step decreases f and the search ends with stop = 2."""
     rng = wl.rng_for(200)
     M = rng.standard_normal((6, 6))
     A = M @ M.T + 6 * np.eye(6)
     b = rng.standard_normal(6)
-    x, f, it, ev = orc.bfgs_minimize(lambda x: (0.5 * x @ A @ x - b @ x, A @ x - b), np.zeros(6), gtol=1e-8)
-    assert it < 200   # converged, not stopped by the iteration cap
-    assert np.max(np.abs(x - np.linalg.solve(A, b))) < 1e-8
+    gtol = 1e-8
+    x, f, it, ev, stop = orc.bfgs_minimize(lambda x: (0.5 * x @ A @ x - b @ x, A @ x - b), np.zeros(6), gtol=gtol)
+    assert stop == 0 and it < 200   # converged, not stopped by the iteration cap or the line search
+    assert np.max(np.abs(x - np.linalg.solve(A, b))) <= gtol / math.sqrt(6.0) * (1 + 1e-6)
     assert abs(f + 0.5 * b @ np.linalg.solve(A, b)) < 1e-12
 
     def rosen(z):
         a, c = z
         return (1 - a) ** 2 + 100 * (c - a * a) ** 2, np.array([-2 * (1 - a) - 400 * a * (c - a * a), 200 * (c - a * a)])
-    x, f, it, ev = orc.bfgs_minimize(rosen, np.array([-1.2, 1.0]), gtol=1e-10)
+    x, f, it, ev, stop = orc.bfgs_minimize(rosen, np.array([-1.2, 1.0]), gtol=1e-10)
     assert np.max(np.abs(x - 1.0)) < 1e-8 and f < 1e-16
+
+
+def test_bfgs_stops_on_precision_loss_at_the_best_point():
+    """When no line-search step can lower f (here f is rounded to multiples of 1e-6 while its
+    gradient stays exact), the search ends with stop = 2 at the last accepted point: it never moves
+    to a worse point, and the returned f is the objective there."""
+    D = np.array([1.0, 3.7])
+
+    def fq(z):
+        v = float(np.sum(D * (z - 1.0) ** 2))
+        return math.floor(v * 1e6) / 1e6, 2.0 * D * (z - 1.0)
+    x0 = np.array([3.0, -2.0])
+    x, f, it, ev, stop = orc.bfgs_minimize(fq, x0, gtol=1e-12, max_iter=500)
+    assert stop == 2
+    assert f == fq(x)[0] and f <= fq(x0)[0]
+    assert np.max(np.abs(x - 1.0)) < 2e-3            # inside the flat band around the minimiser
+    assert ev <= it + 1 + (it + 1) * 31               # at most 31 trial points per iteration
 
 
 def test_optimise_qaoa_matches_scipy_bfgs_and_closed_form():
@@ -638,7 +662,7 @@ def test_optimise_qaoa_matches_scipy_bfgs_and_closed_form():
     G = wl.regular3_graph(n, wl.rng_for(201))
     prob = orc.maxcut_problem(n, G.eu, G.ev)
     g0, t0 = np.array([0.6]), np.array([0.4])
-    gs, ts, f, it, ev = orc.optimise(prob, g0, t0, gtol=1e-10)
+    gs, ts, f, it, ev, _ = orc.optimise(prob, g0, t0, gtol=1e-10)
 
     def fg(th):
         E, dg, dt = orc.gradient(prob, th[0::2], th[1::2])
@@ -653,6 +677,6 @@ def test_optimise_qaoa_matches_scipy_bfgs_and_closed_form():
     # started from the best point of a (gamma, t) grid of the closed form, it ends at or below it
     grid = np.linspace(0.0, math.pi, 41)
     best = min((cf.p1_maxcut_expectation(n, G.eu, G.ev, None, gg, tt), gg, tt) for gg in grid for tt in grid)
-    gs2, ts2, f2, _, _ = orc.optimise(prob, np.array([best[1]]), np.array([best[2]]), gtol=1e-10)
+    gs2, ts2, f2, _, _, _ = orc.optimise(prob, np.array([best[1]]), np.array([best[2]]), gtol=1e-10)
     assert f2 <= best[0] + 1e-12
     assert abs(cf.p1_maxcut_expectation(n, G.eu, G.ev, None, gs2[0], ts2[0]) - f2) < 1e-10

@@ -14,7 +14,8 @@
  *     traps or prints. qvs_strerror() names a code. A CUDA failure is QVS_ECUDA and leaves the
  *     handle usable unless the CUDA context itself is lost.
  *   - A qvs_t handle owns every device buffer it allocates (state, adjoint vector, checkpoints,
- *     copies of q and of the mixer, reduction scratch); qvs_destroy frees them. Inputs are always
+ *     copies of q and of the mixer, reduction scratch), through the allocator hooks given to
+ *     qvs_create (default cudaMalloc); qvs_destroy frees them. Inputs are always
  *     copied: the caller may free or reuse its buffers as soon as a call returns.
  *   - "on_device" arguments: 0 = the pointer is host memory, 1 = device memory of the handle's
  *     device. Host inputs may be pageable or pinned.
@@ -53,6 +54,8 @@ enum {
 enum { QVS_C64 = 1, QVS_C128 = 2 };
 /* element type of quality vectors */
 enum { QVS_I32 = 1, QVS_F32 = 2, QVS_F64 = 3 };
+/* initial-state kinds of qvs_set_initial_state */
+enum { QVS_INIT_UNIFORM = 0, QVS_INIT_EXPLICIT = 1 };
 /* mixer kinds (paper Sec. 3: sparse, circulant, and the QAOA hypercube) */
 enum { QVS_MIX_HYPERCUBE = 1, QVS_MIX_CIRCULANT = 2, QVS_MIX_CSR = 3, QVS_MIX_PARITY = 4 };
 /* options for qvs_set_option */
@@ -101,11 +104,28 @@ typedef struct {
   double cheb_tol;
 } qvs_mixer_desc;
 
-/* Sec. 4 ("plan"): create a handle for states of dimension dim at the given precision on the
- * current CUDA device. stream: a cudaStream_t or NULL. On success *out is set. */
-int qvs_create(qvs_t* out, int64_t dim, int precision, void* stream);
+/* Sec. 5 (the plan/destroy life cycle of the Unitary table): create a handle for states of
+ * dimension dim (2 <= dim <= 2^34) at the given precision on the current CUDA device.
+ *   stream     a cudaStream_t or NULL (legacy default stream); every kernel and copy of the
+ *              handle is ordered on it.
+ *   alloc, dealloc, alloc_ctx
+ *              device-memory hooks, both NULL (cudaMalloc / cudaFree) or both set. Every device
+ *              buffer the handle owns is then obtained as alloc(bytes, alloc_ctx) and returned as
+ *              dealloc(ptr, alloc_ctx). alloc returns NULL when it cannot serve the request (the
+ *              call that needed the memory returns QVS_ENOMEM) and must return blocks aligned to
+ *              256 bytes (a misaligned block is handed back to dealloc and the call returns
+ *              QVS_EINVAL). dealloc may be called while earlier work on the handle's stream still
+ *              reads the block: the hooks must not reuse it before that work completes in stream
+ *              order (a stream-ordered pool allocating on the handle's stream, such as the PyTorch
+ *              caching allocator, satisfies this). The hooks are called on the thread of the
+ *              qvs_* call that needs the memory, never from a device callback.
+ * On success *out is set. QVS_EINVAL for NULL out, dim or precision out of range, or only one of
+ * alloc/dealloc given; QVS_ECUDA when no CUDA device is usable. */
+int qvs_create(qvs_t* out, int64_t dim, int precision, void* stream, void* (*alloc)(size_t, void*),
+               void (*dealloc)(void*, void*), void* alloc_ctx);
 
-/* Release every device buffer of the handle (NULL is accepted). */
+/* Sec. 5 (destroy): wait for the handle's stream, then return every device buffer of the handle to
+ * the allocator that made it (NULL is accepted). */
 int qvs_destroy(qvs_t h);
 
 /* Sec. 2.1: set the quality vector q (dim entries). I32 and F32 values are used as given
@@ -132,9 +152,15 @@ int qvs_set_quality_qubo(qvs_t h, int n_qubits, double c, const double* hlin, co
 /* Sec. 3: set the mixing operator (copied). */
 int qvs_set_mixer(qvs_t h, int kind, const qvs_mixer_desc* desc);
 
-/* Sec. 2.1 / Sec. 5: set |psi0> (dim complex values, interleaved re/im, in the handle's
- * precision). psi0 = NULL restores the default equal superposition 1/sqrt(dim). */
-int qvs_set_initial_state(qvs_t h, const void* psi0, int on_device);
+/* Sec. 2.1 / Sec. 5 (the Ansatz table's initial state): choose |psi0>.
+ *   kind = QVS_INIT_UNIFORM   the equal superposition 1/sqrt(dim) over the simulated space (the
+ *                             default; never stored: the first pass generates it); psi0 must be NULL.
+ *   kind = QVS_INIT_EXPLICIT  psi0 holds dim complex values (interleaved re/im, in the handle's
+ *                             precision), host or device memory per on_device; copied into the
+ *                             handle (the caller may free it on return).
+ * QVS_EINVAL for another kind, a NULL psi0 with QVS_INIT_EXPLICIT or a non-NULL one with
+ * QVS_INIT_UNIFORM. */
+int qvs_set_initial_state(qvs_t h, int kind, const void* psi0, int on_device);
 
 /* Set an option (QVS_OPT_*). */
 int qvs_set_option(qvs_t h, int option, int64_t value);
@@ -178,19 +204,22 @@ typedef int (*qvs_fg_fn)(const double* x, double* f, double* g, void* user);
 
 /* Sec. 4: BFGS minimisation (the paper's default optimiser), on the host: direction -H g with the
  * inverse-Hessian estimate H (identity at the start and after a non-descent direction),
- * backtracking line search from step 1 halving until f(x + a d) <= f(x) + 1e-4 a g.d, inverse
- * update H <- (I - rho s y^T) H (I - rho y s^T) + rho s s^T (rho = 1/y.s, skipped when y.s <= 0),
- * stop at max |g| <= gtol or after max_iter iterations. x (n host values) is the start and
- * receives the result; f_out, iters_out, evals_out may be NULL. QVS_EINVAL for n outside
- * 1..8192, NULL x or fg, negative max_iter or gtol; a callback error is returned as is. */
+ * backtracking line search from step 1 halving (at most 30 times) until
+ * f(x + a d) <= f(x) + 1e-4 a g.d, inverse update H <- (I - rho s y^T) H (I - rho y s^T) + rho s s^T
+ * (rho = 1/y.s, skipped when y.s <= 0). It stops when max |g| <= gtol (*stop_out = 0), after
+ * max_iter iterations (1), or when no step of the line search decreases f enough (2: the
+ * objective's rounding hides further descent; x and f stay at the last accepted point). x (n host
+ * values) is the start and receives the result; f_out, iters_out, evals_out, stop_out may be NULL.
+ * QVS_EINVAL for n outside 1..8192, NULL x or fg, negative max_iter or gtol; a callback error is
+ * returned as is. */
 int qvs_bfgs_minimize(int n, double* x, qvs_fg_fn fg, void* user, double gtol, int max_iter,
-                      double* f_out, int* iters_out, int* evals_out);
+                      double* f_out, int* iters_out, int* evals_out, int* stop_out);
 
 /* Sec. 4: minimise f(theta) = <theta|Q|theta> over theta = (gamma_1, t_1, ..., gamma_p, t_p) with
  * qvs_bfgs_minimize, each evaluation one qvs_gradient on the handle (device objective and adjoint
  * gradient). gammas, ts (host, p values) hold the start and receive the result. */
 int qvs_optimise(qvs_t h, int p, double* gammas, double* ts, double gtol, int max_iter, double* f_out,
-                 int* iters_out, int* evals_out);
+                 int* iters_out, int* evals_out, int* stop_out);
 
 /* Sec. 2.1: f = <theta|Q|theta> of the last qvs_evolve (fp64 reduction). */
 int qvs_expectation(qvs_t h, double* E);

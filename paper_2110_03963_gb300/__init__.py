@@ -24,6 +24,7 @@ QVS_OK, QVS_EINVAL, QVS_ENOMEM, QVS_ECUDA, QVS_ESTATE, QVS_ENUMERIC, QVS_ETIMEOU
     0, -1, -2, -3, -4, -5, -6, -7
 QVS_C64, QVS_C128 = 1, 2
 QVS_I32, QVS_F32, QVS_F64 = 1, 2, 3
+QVS_INIT_UNIFORM, QVS_INIT_EXPLICIT = 0, 1
 QVS_MIX_HYPERCUBE, QVS_MIX_CIRCULANT, QVS_MIX_CSR, QVS_MIX_PARITY = 1, 2, 3, 4
 QVS_OPT_CKPT_LAYERS = 1
 QVS_OPT_PROFILE = 2
@@ -65,6 +66,10 @@ class MixerDesc(ctypes.Structure):
 
 _lib = None
 
+# device-memory hooks of qvs_create: alloc(bytes, ctx) -> pointer or NULL; dealloc(pointer, ctx)
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+DEALLOC_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
 # objective-and-gradient callback of qvs_bfgs_minimize: (x, f, g, user) -> status
 FG_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                          ctypes.POINTER(ctypes.c_double), ctypes.c_void_p)
@@ -80,11 +85,11 @@ def load(path: str = LIB_PATH):
     lib = ctypes.CDLL(path)
     P, I, I64, D, V = ctypes.POINTER, ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
     sig = {
-        "qvs_create": (I, [P(V), I64, I, V]),
+        "qvs_create": (I, [P(V), I64, I, V, ALLOC_FN, DEALLOC_FN, V]),
         "qvs_destroy": (I, [V]),
         "qvs_set_quality": (I, [V, V, I, I]),
         "qvs_set_mixer": (I, [V, I, P(MixerDesc)]),
-        "qvs_set_initial_state": (I, [V, V, I]),
+        "qvs_set_initial_state": (I, [V, I, V, I]),
         "qvs_set_option": (I, [V, I, I64]),
         "qvs_evolve": (I, [V, I, P(D), P(D)]),
         "qvs_expectation": (I, [V, P(D)]),
@@ -110,8 +115,8 @@ def load(path: str = LIB_PATH):
         "qvs_set_phase_terms": (I, [V, I, P(ctypes.c_int32), P(ctypes.c_int32), P(D)]),
         "qvs_evolve_ex": (I, [V, I, P(D), P(D)]),
         "qvs_gradient_ex": (I, [V, I, P(D), P(D), P(D), P(D), P(D)]),
-        "qvs_bfgs_minimize": (I, [I, P(D), FG_FN, V, D, I, P(D), P(I), P(I)]),
-        "qvs_optimise": (I, [V, I, P(D), P(D), D, I, P(D), P(I), P(I)]),
+        "qvs_bfgs_minimize": (I, [I, P(D), FG_FN, V, D, I, P(D), P(I), P(I), P(I)]),
+        "qvs_optimise": (I, [V, I, P(D), P(D), D, I, P(D), P(I), P(I), P(I)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -161,9 +166,42 @@ def _stream_ptr(stream):
 # ---------------------------------------------------------------- thin wrappers, same names
 
 
-def qvs_create(dim: int, precision: int = QVS_C64, stream=None) -> ctypes.c_void_p:
+class TorchAllocator:
+    """Device-memory hooks for qvs_create that take every handle buffer from the PyTorch caching
+    allocator on the handle's stream (so library buffers share PyTorch's pool and its stream-ordered
+    reuse). Keep the object alive as long as the handle."""
+
+    def __init__(self, stream=None, device=None):
+        import torch
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        self.stream = _stream_ptr(stream).value or 0
+        self.live = 0
+        self.alloc_fn = ALLOC_FN(self._alloc)
+        self.dealloc_fn = DEALLOC_FN(self._dealloc)
+
+    def _alloc(self, nbytes, _ctx):
+        import torch
+        try:
+            ptr = torch.cuda.caching_allocator_alloc(int(nbytes), self.device, self.stream)
+        except Exception:          # out of memory (or any failure): the library returns QVS_ENOMEM
+            return None
+        self.live += 1
+        return ptr
+
+    def _dealloc(self, ptr, _ctx):
+        import torch
+        torch.cuda.caching_allocator_delete(ptr)
+        self.live -= 1
+
+
+def qvs_create(dim: int, precision: int = QVS_C64, stream=None, allocator=None) -> ctypes.c_void_p:
+    """allocator: None (the library's cudaMalloc) or an object with ``alloc_fn`` / ``dealloc_fn``
+    ctypes callbacks (ALLOC_FN / DEALLOC_FN), e.g. TorchAllocator; the caller keeps it alive."""
     h = ctypes.c_void_p()
-    _check(load().qvs_create(ctypes.byref(h), int(dim), int(precision), _stream_ptr(stream)), "qvs_create")
+    af = allocator.alloc_fn if allocator is not None else ALLOC_FN()
+    df = allocator.dealloc_fn if allocator is not None else DEALLOC_FN()
+    _check(load().qvs_create(ctypes.byref(h), int(dim), int(precision), _stream_ptr(stream), af, df, None),
+           "qvs_create")
     return h
 
 
@@ -185,20 +223,29 @@ def qvs_set_mixer(h, kind: int, desc: MixerDesc):
 
 
 def qvs_set_initial_state(h, psi0=None):
+    """psi0 None: the equal superposition (QVS_INIT_UNIFORM); else the explicit state (host array or
+    device tensor of dim complex values in the handle's precision)."""
     if psi0 is None:
-        _check(load().qvs_set_initial_state(h, None, 0), "qvs_set_initial_state")
+        _check(load().qvs_set_initial_state(h, QVS_INIT_UNIFORM, None, 0), "qvs_set_initial_state")
         return
     p, dev = _ptr_of(psi0)
-    _check(load().qvs_set_initial_state(h, p, dev), "qvs_set_initial_state")
+    _check(load().qvs_set_initial_state(h, QVS_INIT_EXPLICIT, p, dev), "qvs_set_initial_state")
 
 
 def qvs_set_option(h, option: int, value: int):
     _check(load().qvs_set_option(h, int(option), int(value)), "qvs_set_option")
 
 
+def _params(gammas, ts):
+    g = np.ascontiguousarray(gammas, dtype=np.float64).reshape(-1)
+    t = np.ascontiguousarray(ts, dtype=np.float64).reshape(-1)
+    if g.shape != t.shape:
+        raise QvsError(QVS_EINVAL, f"gammas ({g.shape[0]}) and ts ({t.shape[0]}) differ in length")
+    return g, t
+
+
 def qvs_evolve(h, gammas, ts):
-    g = np.ascontiguousarray(gammas, dtype=np.float64)
-    t = np.ascontiguousarray(ts, dtype=np.float64)
+    g, t = _params(gammas, ts)
     _check(load().qvs_evolve(h, len(g), _dptr(g), _dptr(t)), "qvs_evolve")
 
 
@@ -210,8 +257,7 @@ def qvs_expectation(h) -> float:
 
 def qvs_gradient(h, gammas, ts):
     """Returns (E, dgamma[p], dt[p])."""
-    g = np.ascontiguousarray(gammas, dtype=np.float64)
-    t = np.ascontiguousarray(ts, dtype=np.float64)
+    g, t = _params(gammas, ts)
     p = len(g)
     e = ctypes.c_double()
     dg = np.zeros(p)
@@ -337,7 +383,8 @@ def qvs_gradient_ex(h, gammas, ts):
 
 def qvs_bfgs_minimize(fg, x0, gtol: float = 1e-8, max_iter: int = 1000):
     """BFGS on the host with a Python objective: fg(x) -> (f, g). Returns (x, f, iterations,
-    evaluations)."""
+    evaluations, stop) with stop 0 = gradient below gtol, 1 = max_iter reached, 2 = line search
+    could not decrease f (precision loss)."""
     x = np.ascontiguousarray(x0, dtype=np.float64).copy()
     n = x.shape[0]
     err = []
@@ -358,25 +405,27 @@ def qvs_bfgs_minimize(fg, x0, gtol: float = 1e-8, max_iter: int = 1000):
     f = ctypes.c_double()
     it = ctypes.c_int()
     ev = ctypes.c_int()
+    stop = ctypes.c_int()
     st = load().qvs_bfgs_minimize(n, _dptr(x), cfn, None, float(gtol), int(max_iter), ctypes.byref(f),
-                                  ctypes.byref(it), ctypes.byref(ev))
+                                  ctypes.byref(it), ctypes.byref(ev), ctypes.byref(stop))
     if err:
         raise err[0]
     _check(st, "qvs_bfgs_minimize")
-    return x, f.value, it.value, ev.value
+    return x, f.value, it.value, ev.value, stop.value
 
 
 def qvs_optimise(h, gammas0, ts0, gtol: float = 1e-6, max_iter: int = 200):
     """BFGS over theta = (gamma_1, t_1, ...) with the device gradient. Returns
-    (gammas, ts, f, iterations, evaluations)."""
+    (gammas, ts, f, iterations, evaluations, stop)."""
     g = np.ascontiguousarray(gammas0, dtype=np.float64).copy()
     t = np.ascontiguousarray(ts0, dtype=np.float64).copy()
     f = ctypes.c_double()
     it = ctypes.c_int()
     ev = ctypes.c_int()
+    stop = ctypes.c_int()
     _check(load().qvs_optimise(h, len(g), _dptr(g), _dptr(t), float(gtol), int(max_iter), ctypes.byref(f),
-                               ctypes.byref(it), ctypes.byref(ev)), "qvs_optimise")
-    return g, t, f.value, it.value, ev.value
+                               ctypes.byref(it), ctypes.byref(ev), ctypes.byref(stop)), "qvs_optimise")
+    return g, t, f.value, it.value, ev.value, stop.value
 
 
 def qvs_quality_subset(n: int, w, out, dtype: int, stream=None):
@@ -424,13 +473,22 @@ def qvs_xy_ring_csr(n: int, k: int):
 
 def qvs_gradient_small_noalloc(n: int, precision: int, q_dev, gammas, ts, out_dev, stream=None):
     """Allocation-free small-state solve (n <= 12): writes E, dgamma[p], dt[p] into the device
-    tensor out_dev (1 + 2p float64) on the stream; see include/qvs.h for the limits."""
-    g = np.ascontiguousarray(gammas, dtype=np.float64)
-    t = np.ascontiguousarray(ts, dtype=np.float64)
-    qp, qdev = _ptr_of(q_dev)
-    op, odev = _ptr_of(out_dev)
-    assert qdev == 1 and odev == 1, "q and out must be device tensors"
-    _check(load().qvs_gradient_small_noalloc(int(n), int(precision), len(g), qp, _dptr(g), _dptr(t), op,
+    tensor out_dev (1 + 2p float64) on the stream; see include/qvs.h for the limits. The sizes and
+    dtypes of q_dev and out_dev are checked here, since the library receives bare pointers."""
+    import torch
+    g, t = _params(gammas, ts)
+    p = g.shape[0]
+    want = torch.float32 if precision == QVS_C64 else torch.float64
+    for name, x in (("q", q_dev), ("out", out_dev)):
+        if not (isinstance(x, torch.Tensor) and x.is_cuda and x.is_contiguous()):
+            raise QvsError(QVS_EINVAL, f"{name} must be a contiguous CUDA tensor")
+    if not 1 <= int(n) <= 30 or q_dev.dtype != want or q_dev.numel() != (1 << int(n)):
+        raise QvsError(QVS_EINVAL, f"q must hold 2^n {want} values")
+    if out_dev.dtype != torch.float64 or out_dev.numel() < 1 + 2 * p:
+        raise QvsError(QVS_EINVAL, "out must hold at least 1 + 2p float64 values")
+    qp, _ = _ptr_of(q_dev)
+    op, _ = _ptr_of(out_dev)
+    _check(load().qvs_gradient_small_noalloc(int(n), int(precision), p, qp, _dptr(g), _dptr(t), op,
                                              _stream_ptr(stream)), "qvs_gradient_small_noalloc")
     return out_dev
 
@@ -562,10 +620,16 @@ def csr_desc(rowptr, colind, values=None, implicit_value: float = 1.0, spec=(0.0
 class Simulator:
     """Owns one qvs handle: quality vector + mixer + optional initial state."""
 
-    def __init__(self, dim: int, precision: int = QVS_C64, stream=None):
+    def __init__(self, dim: int, precision: int = QVS_C64, stream=None, allocator="torch"):
+        """allocator: "torch" (default: device buffers from the PyTorch caching allocator on the
+        handle's stream), None (the library's cudaMalloc) or a hooks object (see qvs_create)."""
         self.dim = int(dim)
         self.precision = precision
-        self.h = qvs_create(dim, precision, stream)
+        self.h = None
+        if allocator == "torch":
+            allocator = TorchAllocator(stream)
+        self.allocator = allocator
+        self.h = qvs_create(dim, precision, stream, allocator)
 
     def close(self):
         if self.h is not None:
@@ -628,7 +692,10 @@ class Simulator:
 
 
 class QAOAObjective:
-    """torch.autograd.Function-style objective: E(gammas, ts) with the adjoint gradient."""
+    """The objective E(gammas, ts) = <theta|Q|theta> of a Simulator as a differentiable PyTorch
+    function: the forward pass runs the device solve (qvs_gradient: forward sweep, objective and
+    adjoint sweep), the backward pass returns grad_out * (dE/dgamma, dE/dt) from that same solve,
+    in the dtype and on the device of the inputs."""
 
     @staticmethod
     def function(sim: Simulator):
@@ -639,12 +706,13 @@ class QAOAObjective:
             def forward(ctx, gammas, ts):
                 E, dg, dt = sim.gradient(gammas.detach().cpu().double().numpy(),
                                          ts.detach().cpu().double().numpy())
-                ctx.save_for_backward(torch.from_numpy(dg), torch.from_numpy(dt))
-                return torch.tensor(E, dtype=torch.float64)
+                ctx.save_for_backward(torch.from_numpy(dg).to(gammas.device, gammas.dtype),
+                                      torch.from_numpy(dt).to(ts.device, ts.dtype))
+                return torch.tensor(E, dtype=torch.float64, device=gammas.device)
 
             @staticmethod
             def backward(ctx, grad_out):
                 dg, dt = ctx.saved_tensors
-                return grad_out * dg, grad_out * dt
+                return grad_out.to(dg.dtype) * dg, grad_out.to(dt.dtype) * dt
 
         return _Evolve.apply

@@ -13,6 +13,13 @@
 
 namespace qvs {
 
+static thread_local const Allocator* t_allocator = nullptr;
+
+const Allocator* current_allocator() { return t_allocator; }
+
+AllocScope::AllocScope(const Allocator* a) : prev(t_allocator) { t_allocator = a; }
+AllocScope::~AllocScope() { t_allocator = prev; }
+
 int ensure_host_res(qvs_ctx* h, int p) {
   if (h->host_res && h->host_res_cap >= p) return QVS_OK;
   if (h->host_res) cudaFreeHost(h->host_res);
@@ -108,17 +115,22 @@ static bool params_ok(int p, const double* g, const double* t) {
 
 using namespace qvs;
 
-extern "C" int qvs_create(qvs_t* out, int64_t dim, int precision, void* stream) {
+extern "C" int qvs_create(qvs_t* out, int64_t dim, int precision, void* stream,
+                          void* (*alloc)(size_t, void*), void (*dealloc)(void*, void*), void* alloc_ctx) {
   if (!out) return QVS_EINVAL;
   *out = nullptr;
   if (dim < 2 || dim > (int64_t(1) << 34)) return QVS_EINVAL;
   if (precision != QVS_C64 && precision != QVS_C128) return QVS_EINVAL;
+  if ((alloc == nullptr) != (dealloc == nullptr)) return QVS_EINVAL;
   qvs_ctx* h = new (std::nothrow) qvs_ctx();
   if (!h) return QVS_ENOMEM;
   h->dim = dim;
   h->n = log2_exact(dim);
   h->precision = precision;
   h->stream = (cudaStream_t)stream;
+  h->allocator.alloc = alloc;
+  h->allocator.dealloc = dealloc;
+  h->allocator.ctx = alloc_ctx;
   if (cudaGetDevice(&h->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
     (void)cudaGetLastError();
@@ -134,23 +146,11 @@ extern "C" int qvs_destroy(qvs_t h) {
   if (!h) return QVS_OK;
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
-  h->q.release();
-  h->psi0.release();
-  h->psi.release();
-  h->lam.release();
-  h->ckpt.release();
-  h->part.release();
-  h->res.release();
-  h->rowmap.release();
-  h->work.release();
-  h->circ.lam.release();
-  h->circ.tab.release();
-  h->circ.qT.release();
-  h->csr.rowptr.release();
-  h->csr.colind.release();
-  h->csr.values.release();
-  h->qubo.dcoef.release();
-  h->qubo.tab.release();
+  qvs::DevBuf* bufs[] = {&h->q, &h->psi0, &h->psi, &h->lam, &h->ckpt, &h->part, &h->res, &h->rowmap,
+                         &h->work, &h->circ.lam, &h->circ.tab, &h->circ.qT, &h->csr.rowptr,
+                         &h->csr.colind, &h->csr.values, &h->qubo.dcoef, &h->qubo.tab, &h->ex.coef,
+                         &h->ex.tab, &h->ex.g, &h->ex.mterms, &h->ex.mpart, &h->ex.mrowmap, &h->ex.mres};
+  for (qvs::DevBuf* b : bufs) b->release();
   if (h->host_res) cudaFreeHost(h->host_res);
   prof_release(h);
   delete h;
@@ -176,6 +176,7 @@ static int convert_on_device(qvs_ctx* h, Dst* d, const Src* s, int64_t n) {
 
 extern "C" int qvs_set_quality(qvs_t h, const void* q, int dtype, int on_device) {
   if (!h || !q) return QVS_EINVAL;
+  AllocScope scope(&h->allocator);
   if (dtype != QVS_I32 && dtype != QVS_F32 && dtype != QVS_F64) return QVS_EINVAL;
   const int64_t n = h->dim;
   const size_t in_elem = dtype == QVS_F64 ? 8 : 4;
@@ -214,6 +215,7 @@ extern "C" int qvs_set_quality(qvs_t h, const void* q, int dtype, int on_device)
 
 extern "C" int qvs_set_quality_qubo(qvs_t h, int n_qubits, double c, const double* hlin, const double* J) {
   if (!h || !hlin || !J) return QVS_EINVAL;
+  AllocScope scope(&h->allocator);
   if (h->n < 1 || n_qubits != h->n) return QVS_EINVAL;
   QVS_TRY(qubo_quantize(n_qubits, c, hlin, J, &h->qubo.coef));
   h->qubo.on = true;
@@ -238,6 +240,7 @@ int ensure_q_vector(qvs_ctx* h) {
 
 extern "C" int qvs_set_mixer(qvs_t h, int kind, const qvs_mixer_desc* d) {
   if (!h || !d) return QVS_EINVAL;
+  AllocScope scope(&h->allocator);
   h->have_mixer = false;
   h->have_E = false;
   if (kind == QVS_MIX_HYPERCUBE) {
@@ -258,13 +261,17 @@ extern "C" int qvs_set_mixer(qvs_t h, int kind, const qvs_mixer_desc* d) {
   return QVS_OK;
 }
 
-extern "C" int qvs_set_initial_state(qvs_t h, const void* psi0, int on_device) {
+extern "C" int qvs_set_initial_state(qvs_t h, int kind, const void* psi0, int on_device) {
   if (!h) return QVS_EINVAL;
-  h->have_E = false;
-  if (!psi0) {
+  if (kind == QVS_INIT_UNIFORM) {
+    if (psi0) return QVS_EINVAL;
+    h->have_E = false;
     h->have_psi0 = false;
     return QVS_OK;
   }
+  if (kind != QVS_INIT_EXPLICIT || !psi0) return QVS_EINVAL;
+  AllocScope scope(&h->allocator);
+  h->have_E = false;
   const size_t bytes = elem_bytes(h) * (size_t)h->dim;
   QVS_TRY(h->psi0.ensure(bytes));
   QVS_CUDA_TRY(cudaMemcpyAsync(h->psi0.ptr, psi0, bytes,
@@ -298,6 +305,7 @@ static int ready(qvs_t h) {
 
 extern "C" int qvs_evolve(qvs_t h, int p, const double* gammas, const double* ts) {
   QVS_TRY(ready(h));
+  AllocScope scope(&h->allocator);
   if (!params_ok(p, gammas, ts)) return QVS_EINVAL;
   h->have_E = false;
   if (h->mixer != QVS_MIX_HYPERCUBE) QVS_TRY(ensure_q_vector(h));
@@ -336,6 +344,7 @@ static bool ex_params_ok(qvs_t h, int p, const double* g, const double* t) {
 
 extern "C" int qvs_evolve_ex(qvs_t h, int p, const double* gammas, const double* ts) {
   QVS_TRY(ready(h));
+  AllocScope scope(&h->allocator);
   if (h->mixer != QVS_MIX_HYPERCUBE) return QVS_EUNSUPPORTED;
   if (h->ex.terms.empty()) return QVS_ESTATE;
   if (!ex_params_ok(h, p, gammas, ts)) return QVS_EINVAL;
@@ -346,6 +355,7 @@ extern "C" int qvs_evolve_ex(qvs_t h, int p, const double* gammas, const double*
 extern "C" int qvs_gradient_ex(qvs_t h, int p, const double* gammas, const double* ts, double* E, double* dgamma,
                                double* dt) {
   QVS_TRY(ready(h));
+  AllocScope scope(&h->allocator);
   if (h->mixer != QVS_MIX_HYPERCUBE) return QVS_EUNSUPPORTED;
   if (h->ex.terms.empty()) return QVS_ESTATE;
   if (!ex_params_ok(h, p, gammas, ts) || !E || !dgamma || !dt) return QVS_EINVAL;
@@ -363,6 +373,7 @@ extern "C" int qvs_expectation(qvs_t h, double* E) {
 extern "C" int qvs_gradient(qvs_t h, int p, const double* gammas, const double* ts, double* E,
                             double* dgamma, double* dt) {
   QVS_TRY(ready(h));
+  AllocScope scope(&h->allocator);
   if (!params_ok(p, gammas, ts) || !E || !dgamma || !dt) return QVS_EINVAL;
   h->have_E = false;
   if (h->mixer != QVS_MIX_HYPERCUBE) QVS_TRY(ensure_q_vector(h));

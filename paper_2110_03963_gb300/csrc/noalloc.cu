@@ -161,7 +161,7 @@ template <class T>
 static int launch(int n, int p, const void* q, const double* gammas, const double* ts, double* out,
                   void* scratch, cudaStream_t st) {
   using C = typename hc::Cx<T>::t;
-  static Args<T> a;   // built on the host, passed by value
+  Args<T> a;   // built on this thread's stack and copied into the launch
   memset(&a, 0, sizeof(a));
   a.n = n;
   a.p = p;

@@ -4,18 +4,22 @@
 //   * direction d = -H g, H the inverse-Hessian estimate (H_0 = I; reset to I when d is not a
 //     descent direction);
 //   * backtracking line search from step 1, halving until f(x + a d) <= f(x) + c1 a g.d
-//     (c1 = 1e-4);
+//     (c1 = 1e-4), at most kMaxHalvings times;
 //   * with s = x_new - x, y = g_new - g: H <- (I - rho s y^T) H (I - rho y s^T) + rho s s^T,
 //     rho = 1 / y.s, skipped when y.s <= 0;
-//   * stop when max |g| <= gtol or after max_iter iterations.
+//   * stop when max |g| <= gtol (stop 0), after max_iter iterations (stop 1), or when no step of
+//     the line search decreases f enough (stop 2: rounding of the objective hides any further
+//     descent; x, f and g stay at the last accepted point, as SciPy's BFGS ends on precision loss).
 #include <math.h>
 
 #include <vector>
 
 #include "qvs_internal.h"
 
+static const int kMaxHalvings = 30;
+
 extern "C" int qvs_bfgs_minimize(int n, double* x, qvs_fg_fn fg, void* user, double gtol, int max_iter,
-                                 double* f_out, int* iters_out, int* evals_out) {
+                                 double* f_out, int* iters_out, int* evals_out, int* stop_out) {
   if (n < 1 || n > 8192 || !x || !fg || max_iter < 0 || !(gtol >= 0.0)) return QVS_EINVAL;
   const size_t N = (size_t)n;
   std::vector<double> H(N * N, 0.0), g(N), gn(N), xn(N), d(N), s(N), y(N), Hy(N);
@@ -32,7 +36,12 @@ extern "C" int qvs_bfgs_minimize(int n, double* x, qvs_fg_fn fg, void* user, dou
     for (double e : v) m = fmax(m, fabs(e));
     return m;
   };
-  while (it < max_iter && gmax(g) > gtol) {
+  int stop = 1;
+  while (it < max_iter) {
+    if (gmax(g) <= gtol) {
+      stop = 0;
+      break;
+    }
     for (size_t i = 0; i < N; ++i) {
       double acc = 0.0;
       for (size_t j = 0; j < N; ++j) acc += H[i * N + j] * g[j];
@@ -49,12 +58,20 @@ extern "C" int qvs_bfgs_minimize(int n, double* x, qvs_fg_fn fg, void* user, dou
       }
     }
     double a = 1.0, fn = 0.0;
-    for (;;) {
+    bool accepted = false;
+    for (int halving = 0; halving <= kMaxHalvings; ++halving) {
       for (size_t i = 0; i < N; ++i) xn[i] = x[i] + a * d[i];
       QVS_TRY(fg(xn.data(), &fn, gn.data(), user));
       ++evals;
-      if (fn <= f + 1e-4 * a * slope || a < 1e-20) break;
+      if (fn <= f + 1e-4 * a * slope) {
+        accepted = true;
+        break;
+      }
       a *= 0.5;
+    }
+    if (!accepted) {
+      stop = 2;
+      break;
     }
     double ys = 0.0;
     for (size_t i = 0; i < N; ++i) {
@@ -85,9 +102,11 @@ extern "C" int qvs_bfgs_minimize(int n, double* x, qvs_fg_fn fg, void* user, dou
     f = fn;
     ++it;
   }
+  if (stop == 1 && gmax(g) <= gtol) stop = 0;
   if (f_out) *f_out = f;
   if (iters_out) *iters_out = it;
   if (evals_out) *evals_out = evals;
+  if (stop_out) *stop_out = stop;
   return QVS_OK;
 }
 
@@ -114,7 +133,7 @@ int qva_fg(const double* th, double* f, double* g, void* user) {
 }  // namespace
 
 extern "C" int qvs_optimise(qvs_t h, int p, double* gammas, double* ts, double gtol, int max_iter, double* f_out,
-                            int* iters_out, int* evals_out) {
+                            int* iters_out, int* evals_out, int* stop_out) {
   if (!h || p < 1 || p > 4096 || !gammas || !ts) return QVS_EINVAL;
   OptCtx c{h, p, std::vector<double>(p), std::vector<double>(p), std::vector<double>(p), std::vector<double>(p)};
   std::vector<double> th(2 * (size_t)p);
@@ -122,7 +141,7 @@ extern "C" int qvs_optimise(qvs_t h, int p, double* gammas, double* ts, double g
     th[2 * k] = gammas[k];
     th[2 * k + 1] = ts[k];
   }
-  QVS_TRY(qvs_bfgs_minimize(2 * p, th.data(), qva_fg, &c, gtol, max_iter, f_out, iters_out, evals_out));
+  QVS_TRY(qvs_bfgs_minimize(2 * p, th.data(), qva_fg, &c, gtol, max_iter, f_out, iters_out, evals_out, stop_out));
   for (int k = 0; k < p; ++k) {
     gammas[k] = th[2 * k];
     ts[k] = th[2 * k + 1];

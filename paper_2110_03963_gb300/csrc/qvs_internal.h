@@ -26,29 +26,69 @@
 
 namespace qvs {
 
-// Device buffer owned by a handle.
+// Device allocator of a handle: the alloc/dealloc hooks given to qvs_create (both NULL: the
+// CUDA runtime's cudaMalloc / cudaFree).
+struct Allocator {
+  void* (*alloc)(size_t, void*) = nullptr;
+  void (*dealloc)(void*, void*) = nullptr;
+  void* ctx = nullptr;
+};
+
+// The allocator DevBuf::ensure uses on the calling thread. Every public entry point that works on
+// a handle sets it to the handle's allocator for the duration of the call (AllocScope); outside
+// such a call it is NULL and buffers come from cudaMalloc (batched solves, generators).
+const Allocator* current_allocator();
+struct AllocScope {
+  explicit AllocScope(const Allocator* a);
+  ~AllocScope();
+  AllocScope(const AllocScope&) = delete;
+  AllocScope& operator=(const AllocScope&) = delete;
+  const Allocator* prev;
+};
+
+// Device buffer owned by a handle. It remembers the allocator that made its block, so release()
+// always returns the block to the same allocator.
 struct DevBuf {
   void* ptr = nullptr;
   size_t bytes = 0;
+  Allocator made_by;
   int ensure(size_t b) {
     if (b <= bytes && ptr) return QVS_OK;
-    if (ptr) cudaFree(ptr);
-    ptr = nullptr;
-    bytes = 0;
+    release();
     if (b == 0) return QVS_OK;
-    cudaError_t e = cudaMalloc(&ptr, b);
-    if (e != cudaSuccess) {
-      (void)cudaGetLastError();
-      ptr = nullptr;
-      return QVS_ENOMEM;
+    const Allocator* a = current_allocator();
+    if (a && a->alloc) {
+      void* p = a->alloc(b, a->ctx);
+      if (!p) return QVS_ENOMEM;
+      if (reinterpret_cast<uintptr_t>(p) & 255u) {   // the hook must return 256-byte aligned blocks
+        if (a->dealloc) a->dealloc(p, a->ctx);
+        return QVS_EINVAL;
+      }
+      ptr = p;
+      made_by = *a;
+    } else {
+      cudaError_t e = cudaMalloc(&ptr, b);
+      if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        ptr = nullptr;
+        return QVS_ENOMEM;
+      }
+      made_by = Allocator{};
     }
     bytes = b;
     return QVS_OK;
   }
   void release() {
-    if (ptr) cudaFree(ptr);
+    if (ptr) {
+      if (made_by.alloc) {
+        if (made_by.dealloc) made_by.dealloc(ptr, made_by.ctx);
+      } else {
+        cudaFree(ptr);
+      }
+    }
     ptr = nullptr;
     bytes = 0;
+    made_by = Allocator{};
   }
   template <class T> T* as() const { return static_cast<T*>(ptr); }
 };
@@ -116,6 +156,7 @@ struct CsrData {
 
 struct qvs_ctx {
   int64_t dim = 0;
+  qvs::Allocator allocator;   // qvs_create's hooks (default: cudaMalloc / cudaFree)
   int n = 0;                // log2(dim) when dim is a power of two, else -1
   int precision = QVS_C64;
   cudaStream_t stream = nullptr;

@@ -56,11 +56,27 @@ def test_create_rejects_bad_arguments_without_gpu(qvs):
     import ctypes
     lib = qvs.load()
     h = ctypes.c_void_p()
-    assert lib.qvs_create(ctypes.byref(h), 1, qvs.QVS_C64, None) == qvs.QVS_EINVAL
-    assert lib.qvs_create(ctypes.byref(h), 1024, 7, None) == qvs.QVS_EINVAL
-    assert lib.qvs_create(None, 1024, qvs.QVS_C64, None) == qvs.QVS_EINVAL
+    no_a, no_d = qvs.ALLOC_FN(), qvs.DEALLOC_FN()
+    assert lib.qvs_create(ctypes.byref(h), 1, qvs.QVS_C64, None, no_a, no_d, None) == qvs.QVS_EINVAL
+    assert lib.qvs_create(ctypes.byref(h), 1024, 7, None, no_a, no_d, None) == qvs.QVS_EINVAL
+    assert lib.qvs_create(None, 1024, qvs.QVS_C64, None, no_a, no_d, None) == qvs.QVS_EINVAL
     assert lib.qvs_destroy(None) == qvs.QVS_OK
     assert lib.qvs_evolve(None, 1, None, None) == qvs.QVS_EINVAL
+    assert lib.qvs_set_initial_state(None, qvs.QVS_INIT_UNIFORM, None, 0) == qvs.QVS_EINVAL
+
+
+def test_create_rejects_half_an_allocator_without_gpu(qvs):
+    """The device-memory hooks come as a pair: alloc without dealloc (or the reverse) is refused
+    before any CUDA call, and no hook is ever called for a refused handle."""
+    import ctypes
+    lib = qvs.load()
+    calls = []
+    a = qvs.ALLOC_FN(lambda nbytes, ctx: calls.append(nbytes) or None)
+    d = qvs.DEALLOC_FN(lambda ptr, ctx: calls.append(ptr))
+    h = ctypes.c_void_p()
+    assert lib.qvs_create(ctypes.byref(h), 1024, qvs.QVS_C64, None, a, qvs.DEALLOC_FN(), None) == qvs.QVS_EINVAL
+    assert lib.qvs_create(ctypes.byref(h), 1024, qvs.QVS_C64, None, qvs.ALLOC_FN(), d, None) == qvs.QVS_EINVAL
+    assert h.value is None and calls == []
 
 
 @pytest.mark.parametrize("n,k", [(6, 3), (8, 4), (9, 2), (12, 6)])
@@ -142,19 +158,36 @@ def test_bfgs_minimize_matches_oracle(qvs):
     quad = lambda x: (0.5 * x @ A @ x - b @ x, A @ x - b)
     # gtol well above the fp64 resolution of the Armijo test (|f| ~ 0.1, so decreases below ~1e-17
     # are invisible and a tighter gtol would only run into the iteration cap)
-    x, f, it, ev = qvs.qvs_bfgs_minimize(quad, np.zeros(5), gtol=1e-8)
-    xo, fo, ito, evo = orc.bfgs_minimize(quad, np.zeros(5), gtol=1e-8)
-    assert np.max(np.abs(A @ x - b)) <= 1e-8 and it < 200
+    x, f, it, ev, stop = qvs.qvs_bfgs_minimize(quad, np.zeros(5), gtol=1e-8)
+    xo, fo, ito, evo, stopo = orc.bfgs_minimize(quad, np.zeros(5), gtol=1e-8)
+    assert np.max(np.abs(A @ x - b)) <= 1e-8 and it < 200 and stop == stopo == 0
     assert np.max(np.abs(x - np.linalg.solve(A, b))) < 1e-8
     assert (it, ev) == (ito, evo) and abs(f - fo) < 1e-14 and np.max(np.abs(x - xo)) < 1e-12
 
     def rosen(z):
         a, c = z
         return (1 - a) ** 2 + 100 * (c - a * a) ** 2, np.array([-2 * (1 - a) - 400 * a * (c - a * a), 200 * (c - a * a)])
-    x, f, it, ev = qvs.qvs_bfgs_minimize(rosen, np.array([-1.2, 1.0]), gtol=1e-10)
-    xo, fo, ito, evo = orc.bfgs_minimize(rosen, np.array([-1.2, 1.0]), gtol=1e-10)
+    x, f, it, ev, stop = qvs.qvs_bfgs_minimize(rosen, np.array([-1.2, 1.0]), gtol=1e-10)
+    xo, fo, ito, evo, stopo = orc.bfgs_minimize(rosen, np.array([-1.2, 1.0]), gtol=1e-10)
     assert np.max(np.abs(x - 1.0)) < 1e-8
     assert abs(it - ito) <= 2 and np.max(np.abs(x - xo)) < 1e-8
+
+
+def test_bfgs_precision_loss_stop_matches_oracle(qvs):
+    """Both BFGS loops end with stop = 2 at the same last accepted point when no line-search step
+    can lower a rounded objective."""
+    import math
+
+    D = np.array([1.0, 3.7])
+
+    def fq(z):
+        v = float(np.sum(D * (z - 1.0) ** 2))
+        return math.floor(v * 1e6) / 1e6, 2.0 * D * (z - 1.0)
+    x0 = np.array([3.0, -2.0])
+    x, f, it, ev, stop = qvs.qvs_bfgs_minimize(fq, x0, gtol=1e-12, max_iter=500)
+    xo, fo, ito, evo, stopo = orc.bfgs_minimize(fq, x0, gtol=1e-12, max_iter=500)
+    assert stop == stopo == 2
+    assert (it, ev) == (ito, evo) and f == fo and np.array_equal(x, xo)
 
 
 def test_bfgs_minimize_argument_errors_and_callback_failure(qvs):
@@ -172,6 +205,6 @@ def test_optimise_rejects_bad_arguments_without_gpu(qvs):
     f = ctypes.c_double()
     it = ctypes.c_int()
     assert lib.qvs_optimise(None, 1, g.ctypes.data_as(D), g.ctypes.data_as(D), 1e-6, 10, ctypes.byref(f),
-                            ctypes.byref(it), ctypes.byref(it)) == qvs.QVS_EINVAL
+                            ctypes.byref(it), ctypes.byref(it), ctypes.byref(it)) == qvs.QVS_EINVAL
     with pytest.raises(qvs.QvsError):
         qvs.qvs_bfgs_minimize(lambda x: (0.0, x), np.zeros(3), gtol=-1.0)

@@ -1,0 +1,122 @@
+"""GPU parity at the benchmarked sizes against stored fp64 oracle values.
+
+The oracle needs minutes to hours per solve at these sizes, so `tests/golden/make_oracle_values.py`
+ran it once on the CPU and stored, per case, the objective, the adjoint gradient and 4096 sampled
+final-state amplitudes (see that script). Here the CUDA path solves the same seeded instances
+(the qualities are generated on the GPU, bit-identical to the oracle's fp32 rounding) and is
+compared element by element:
+
+* QWOA circulant at N = 2^24, 2^25, 2^26 (the benchmark geometry and depth, p = 6) and 2^27: each
+  N runs its own column-transform geometry, so each is checked against the oracle;
+* QAOAz XY-ring Chebyshev at C(20,10) and (when stored) at the benchmark's C(24,12), p = 4;
+* QAOA weighted max-cut at the benchmark size n = 28, p = 8: objective and state sample.
+
+Tolerances: |dE|/|E| <= 1e-5 and gradient error <= 1e-4 (max-norm relative, as everywhere), and
+per sampled amplitude |psi_i - psi_ref_i| <= 2e-4 times the rms of the sampled reference
+amplitudes: the complex64 state carries a relative error of about 1e-6 per layer stage (phase
+rounding ~5e-7 rad, ~6e-8 per butterfly stage, growing as a random walk over <= 2p transforms of
+<= 28 stages), so per-amplitude errors stay near 1e-5 of the amplitude scale, 20x inside the bound.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from tests.gpu_util import TOL_E, TOL_G, lib, rel_err_E, rel_err_grad
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+TOL_AMP = 2e-4
+
+
+@pytest.fixture(scope="module")
+def qvs():
+    return lib()
+
+
+def _golden(name):
+    path = os.path.join(GOLDEN, f"oracle_{name}.json")
+    if not os.path.exists(path):
+        pytest.skip(f"stored oracle values {name} not generated")
+    with open(path) as f:
+        return json.load(f)
+
+
+def _check_state(qvs, sim, dim, ref):
+    import torch
+    dev = torch.empty(dim, dtype=torch.complex64, device="cuda")
+    qvs.qvs_get_state(sim.h, dev)
+    idx = torch.tensor(ref["sample_index"], dtype=torch.int64, device="cuda")
+    got = dev[idx].cpu().numpy().astype(np.complex128)
+    del dev
+    want = np.array(ref["sample_re"]) + 1j * np.array(ref["sample_im"])
+    scale = float(np.sqrt(np.mean(np.abs(want) ** 2)))
+    err = float(np.max(np.abs(got - want)))
+    assert err <= TOL_AMP * scale, (err, scale)
+
+
+def _check_solve(qvs, sim, dim, ref):
+    E = sim.evolve(ref["gammas"], ref["ts"])
+    assert rel_err_E(E, ref["f"]) < TOL_E
+    _check_state(qvs, sim, dim, ref)
+    if "dgamma" in ref:
+        E2, dg, dt = sim.gradient(ref["gammas"], ref["ts"])
+        assert rel_err_E(E2, ref["f_gradient_pass"]) < TOL_E
+        assert rel_err_grad(dg, dt, np.array(ref["dgamma"]), np.array(ref["dt"])) < TOL_G
+
+
+@pytest.mark.parametrize("log2n,p", [(24, 3), (25, 2), (26, 6), (27, 2)])
+def test_qwoa_benchmark_geometries_vs_stored_oracle(qvs, log2n, p):
+    import torch
+    ref = _golden(f"qwoa_n{log2n}_p{p}")
+    inst = wl.qwoa(log2n, p)
+    assert np.array_equal(inst.gammas, np.array(ref["gammas"]))
+    q = torch.empty(1 << log2n, dtype=torch.float32, device="cuda")
+    qvs.qvs_quality_subset(log2n, inst.weights, q, qvs.QVS_F32)
+    sim = qvs.Simulator(1 << log2n, qvs.QVS_C64)
+    sim.set_quality(q).set_mixer(qvs.QVS_MIX_CIRCULANT, qvs.circulant_desc(inst.offsets))
+    _check_solve(qvs, sim, 1 << log2n, ref)
+    sim.close()
+    del q
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("n,p", [(20, 2), (24, 4)])
+def test_qaoaz_csr_vs_stored_oracle(qvs, n, p):
+    import torch
+    k = n // 2
+    ref = _golden(f"csr_n{n}_k{k}_p{p}")
+    inst = wl.qaoaz(n, k, p)
+    assert np.array_equal(inst.ts, np.array(ref["ts"]))
+    states, rowptr, colind = qvs.qvs_xy_ring_csr(n, k)
+    dim = states.shape[0]
+    q = torch.empty(dim, dtype=torch.float32, device="cuda")
+    qvs.qvs_quality_portfolio(n, torch.from_numpy(states).cuda(), inst.port.returns, inst.port.cov,
+                              inst.port.omega, q, qvs.QVS_F32)
+    sim = qvs.Simulator(dim, qvs.QVS_C64)
+    sim.set_quality(q).set_mixer(qvs.QVS_MIX_CSR, qvs.csr_desc(rowptr, colind, None, 2.0))
+    _check_solve(qvs, sim, dim, ref)
+    sim.close()
+
+
+def test_qaoa_n28_benchmark_objective_and_state_vs_stored_oracle(qvs):
+    import torch
+    ref = _golden("wmaxcut_n28_p8")
+    n = 28
+    inst = wl.wmaxcut(n, 8)
+    assert np.array_equal(inst.gammas, np.array(ref["gammas"]))
+    G = inst.graph
+    q = torch.empty(1 << n, dtype=torch.float32, device="cuda")
+    qvs.qvs_quality_maxcut(n, G.eu, G.ev, G.w, q, qvs.QVS_F32)
+    sim = qvs.Simulator(1 << n, qvs.QVS_C64)
+    sim.set_quality(q).set_mixer(qvs.QVS_MIX_HYPERCUBE, qvs.hypercube_desc(n))
+    _check_solve(qvs, sim, 1 << n, ref)
+    # the gradient solve's forward objective equals the stored objective as well
+    E2, _, _ = sim.gradient(ref["gammas"], ref["ts"])
+    assert rel_err_E(E2, ref["f"]) < TOL_E
+    sim.close()
+    del q
+    torch.cuda.empty_cache()

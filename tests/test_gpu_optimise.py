@@ -19,9 +19,9 @@ def test_optimise_qaoa_p1_matches_oracle():
     qvs.qvs_quality_maxcut(n, G.eu, G.ev, G.w, q, qvs.QVS_F32)
     sim = qvs.Simulator(1 << n, qvs.QVS_C64)
     sim.set_quality(q).set_mixer(qvs.QVS_MIX_HYPERCUBE, qvs.hypercube_desc(n))
-    gs, ts, f, it, ev = sim.optimise(np.array([0.6]), np.array([0.4]), gtol=1e-4, max_iter=100)
+    gs, ts, f, it, ev, stop = sim.optimise(np.array([0.6]), np.array([0.4]), gtol=1e-4, max_iter=100)
     prob = orc.maxcut_problem(n, G.eu, G.ev, G.w, q_dtype=np.float32)
-    go, to, fo, ito, evo = orc.optimise(prob, np.array([0.6]), np.array([0.4]), gtol=1e-8)
+    go, to, fo, ito, evo, _ = orc.optimise(prob, np.array([0.6]), np.array([0.4]), gtol=1e-8)
     assert rel_err_E(f, fo) < 1e-5
     # the returned parameters reproduce the returned objective, and the optimum was descended to
     assert rel_err_E(sim.evolve(gs, ts), f) < 1e-6

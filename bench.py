@@ -38,13 +38,15 @@ UNIT = "amp-layer/s"
 WORKLOAD = "QAOA weighted max-cut, n=28 (2^28 complex64 amplitudes), G(28,1/2) U[0,1] weights, p=8, objective + adjoint gradient"
 
 
-# DRAM traffic of the dominant kernel per amplitude, from one ncu capture of the same kernels
-# (profiles/hc_passes_qaoa25_dram.md: measured at n=25, averaged over the launch mix of the n=28,
-# p=8 solve). Reported only while the kernel sources hash to the value recorded in that file.
-TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "hc_passes_qaoa25_dram.md")
-TRAFFIC_BYTES_PER_AMP = {"hc_pass_R1_c64": 32.1}
+# DRAM traffic of the dominant kernel per amplitude: ncu dram__bytes_read.sum +
+# dram__bytes_write.sum of one capture at n = 25, averaged over the launch mix of the n = 28, p = 8
+# solve, with the sha256 of the kernel sources it was taken on. Reported only while the sources
+# still hash to that value (null otherwise: the capture no longer describes the built kernel).
+TRAFFIC = {"hc_pass_R1_c64": {"bytes_per_amp": 32.1,
+                              "sources_sha256": "27fca3d68b427e35bd779cd0e182c7cef1235a07516413850f8de70d1a541e29"}}
 TRAFFIC_SOURCES = ["hc_kernels.cuh", "hc_pass.cuh", "hypercube.cu", "hc_pass_th_a.cu", "hc_pass_th_b.cu",
                    "hc_pass_th_c.cu", "hc_pass_th_d.cu"]
+GOLDEN = os.path.join(ROOT, "tests", "golden")
 
 
 def kernel_sources_sha256() -> str:
@@ -59,14 +61,30 @@ def kernel_sources_sha256() -> str:
 def _traffic_per_launch(kernel: str, amplitudes: int):
     """ncu DRAM bytes per launch of `kernel` at the benchmark size, or None when the capture no
     longer describes the built kernels."""
-    try:
-        with open(TRAFFIC_PROFILE) as f:
-            text = f.read()
-    except OSError:
+    t = TRAFFIC.get(kernel)
+    if t is None or t["sources_sha256"] != kernel_sources_sha256():
         return None
-    if kernel not in TRAFFIC_BYTES_PER_AMP or ("sha256: " + kernel_sources_sha256()) not in text:
+    return t["bytes_per_amp"] * amplitudes
+
+
+def _stored_oracle(name: str):
+    """Stored fp64 oracle values of a benchmark instance (written by the oracle-only script beside
+    the test fixtures), or None."""
+    path = os.path.join(GOLDEN, f"oracle_{name}.json")
+    if not os.path.exists(path):
         return None
-    return TRAFFIC_BYTES_PER_AMP[kernel] * amplitudes
+    with open(path) as f:
+        return json.load(f)
+
+
+def _rel(a, b):
+    return abs(a - b) / max(abs(b), 1e-30)
+
+
+def _grad_err(dg, dt, rdg, rdt):
+    g = np.concatenate([np.asarray(dg), np.asarray(dt)])
+    r = np.concatenate([np.asarray(rdg), np.asarray(rdt)])
+    return float(np.max(np.abs(g - r)) / max(np.max(np.abs(r)), 1e-30))
 
 
 def _peaks():
@@ -183,25 +201,112 @@ def oracle_sample(seconds_target: float = 15.0):
     return rate, desc, n
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the baseline record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def _oracle_solve_worker(args):
+    """One oracle objective + adjoint-gradient solve (run in a spawned worker process)."""
+    n, instance = args
+    import oracle as orc
+    inst = wl.wmaxcut(n, P_LAYERS, instance=instance)
+    G = inst.graph
+    prob = orc.maxcut_problem(n, G.eu, G.ev, G.w, q_dtype=np.float32)
+    t0 = time.perf_counter()
+    orc.gradient(prob, inst.gammas, inst.ts)
+    return time.perf_counter() - t0
+
+
+class OracleCores:
+    """The oracle on every host core at once: a pool of spawned single-threaded workers (spawn, so
+    no worker inherits a CUDA context), each solving its own instance of the workload family.
+    Throughput = workers x 2^n x p amplitude-layers / wall time of the whole round."""
+
+    def __init__(self, cores=None):
+        import multiprocessing as mp
+        self.cores = int(cores or os.cpu_count() or 1)
+        for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[var] = "1"
+        self.pool = mp.get_context("spawn").Pool(self.cores)
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+    def pick_n(self, seconds_target: float) -> int:
+        """Largest n (16..22) whose parallel round is predicted to stay within the target, from
+        one timed n = 16 round (time doubles per qubit)."""
+        t16 = max(self.round(16)[0], 1e-3)
+        n = 16
+        while n < 22 and t16 * 2.0 ** (n + 1 - 16) <= seconds_target:
+            n += 1
+        return n
+
+    def round(self, n: int, base: int = 0):
+        t0 = time.perf_counter()
+        per = self.pool.map(_oracle_solve_worker, [(n, base + i) for i in range(self.cores)])
+        wall = time.perf_counter() - t0
+        rate = self.cores * (1 << n) * P_LAYERS / wall
+        return wall, rate, per
+
+
+def oracle_all_cores(seconds_target: float = 15.0):
+    pool = OracleCores()
+    try:
+        n = pool.pick_n(seconds_target)
+        wall, rate, per = pool.round(n, base=1000)
+    finally:
+        pool.close()
+    desc = (f"oracle (numpy fp64) on {pool.cores} worker processes, one single-threaded objective + adjoint "
+            f"gradient of weighted max-cut on G({n},1/2), p={P_LAYERS} each: {wall:.2f} s wall for "
+            f"{pool.cores} solves of 2^{n} amplitudes (per solve {min(per):.2f}-{max(per):.2f} s)")
+    return rate, desc, n, pool.cores
+
+
 def run_reference(args):
+    """The oracle (the reference arm: the paper ships no code) on all host cores; each step is one
+    round of per-core solves of the same workload family at a bounded size."""
     world, rank, _ = _dist()
     if rank != 0:
         return 0
-    vals = []
-    n_used = None
-    desc = ""
     t_all = time.perf_counter()
-    for i in range(args.warmup + args.steps):
-        rate, desc, n_used = oracle_sample(seconds_target=max(2.0, 60.0 / max(1, args.warmup + args.steps)))
-        if i >= args.warmup:
-            vals.append(rate)
+    pool = OracleCores()
+    try:
+        target = max(2.0, 120.0 / max(1, args.warmup + args.steps))
+        n_used = pool.pick_n(target)
+        vals, walls = [], []
+        for i in range(args.warmup + args.steps):
+            wall, rate, _ = pool.round(n_used, base=100 * i)
+            if i >= args.warmup:
+                vals.append(rate)
+                walls.append(wall)
+    finally:
+        pool.close()
     value = float(np.median(vals))
+    desc = (f"oracle (numpy fp64) on {pool.cores} worker processes, each step one single-threaded objective + "
+            f"adjoint gradient per worker of weighted max-cut on G({n_used},1/2), p={P_LAYERS}; host CPU: "
+            f"{cpu_model()}")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": (1 << n_used) * P_LAYERS / value * 1e3, "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": float(np.median(walls)) * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample_n_qubits": n_used},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "config": {"workload": WORKLOAD, "sample_n_qubits": n_used, "solves_per_step": pool.cores},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": pool.cores, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "wall_s": time.perf_counter() - t_all,
     }
@@ -240,10 +345,13 @@ def _kernel_summary(qvs, h, peak, nsteps):
 
 
 def run_extras(qvs, torch, stream, peak, steps, warmup, only=None, qwoa_n=26, qwoa_p=6, qaoaz_n=24, qaoaz_p=4,
-               batch_count=4096):
+               batch_count=4096, headline=None):
     """Objective + adjoint-gradient throughput of the QWOA circulant (N=2^26, p=6), QAOAz CSR
     (n=24, weight 12, p=4) and batched QAOA (4096 instances) workloads."""
     out = {}
+    if only in (None, "c128"):
+        out.update(_extra_config1(qvs, torch, stream, steps, warmup))
+        out.update(_extra_c128_n28(qvs, torch, stream, peak, steps, warmup, headline))
     if only is None:
         out.update(_extra_inpass(qvs, torch, stream, peak, steps, warmup))
         out.update(_extra_exqaoa(qvs, torch, stream, peak, steps, warmup))
@@ -257,6 +365,67 @@ def run_extras(qvs, torch, stream, peak, steps, warmup, only=None, qwoa_n=26, qw
     if only in (None, "batch"):
         out.update(_extra_batch(qvs, torch, stream, peak, steps, warmup, batch_count, plain=only is None))
     return out
+
+
+def _extra_config1(qvs, torch, stream, steps, warmup):
+    """QAOA max-cut, n = 10, random 3-regular graph, integer qualities, p = 2, complex128, forward
+    objective only: latency of one evolve + expectation call (host arrays in, E out)."""
+    inst = wl.maxcut10()
+    G = inst.graph
+    n, p = 10, 2
+    q = torch.empty(1 << n, dtype=torch.int32, device="cuda")
+    qvs.qvs_quality_maxcut(n, G.eu, G.ev, None, q, qvs.QVS_I32, stream)
+    sim = qvs.Simulator(1 << n, qvs.QVS_C128, stream)
+    sim.set_quality(q).set_mixer(qvs.QVS_MIX_HYPERCUBE, qvs.hypercube_desc(n))
+    reps = 2000
+    for _ in range(50):
+        E = sim.evolve(inst.gammas, inst.ts)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        E = sim.evolve(inst.gammas, inst.ts)
+    us = (time.perf_counter() - t0) / reps * 1e6
+    launches = sim.launches()
+    sim.close()
+    ref = _stored_oracle("maxcut3_n10_p2")
+    units = float(1 << n) * p
+    return {"qaoa_maxcut3_n10_p2_c128_forward": {
+        "value": units / (us * 1e-6), "unit": UNIT, "us_per_solve": us, "launches_per_solve": launches,
+        "timing": "host wall clock per qvs_evolve + qvs_expectation call (synchronous), mean of %d" % reps,
+        "objective": E, "rel_err_E_vs_oracle": _rel(E, ref["f"]) if ref else None}}
+
+
+def _extra_c128_n28(qvs, torch, stream, peak, steps, warmup, headline):
+    """The plain complex128 path on the benchmark instance (the fp64-accuracy GPU solve), timed
+    beside the complex64 line, and the complex64 result's errors against it and against the stored
+    fp64 oracle objective."""
+    n, p = N_QUBITS, P_LAYERS
+    inst = wl.wmaxcut(n, p)
+    G = inst.graph
+    q = torch.empty(1 << n, dtype=torch.float32, device="cuda")
+    qvs.qvs_quality_maxcut(n, G.eu, G.ev, G.w, q, qvs.QVS_F32, stream)
+    sim = qvs.Simulator(1 << n, qvs.QVS_C128, stream)
+    sim.set_quality(q).set_mixer(qvs.QVS_MIX_HYPERCUBE, qvs.hypercube_desc(n))
+    del q
+    gs, ts = np.asarray(inst.gammas), np.asarray(inst.ts)
+    ms = _time_steps(torch, stream, lambda: sim.gradient(gs, ts), max(3, steps // 3), max(1, warmup // 2))
+    E, dg, dt = sim.gradient(gs, ts)
+    sim.set_option(qvs.QVS_OPT_PROFILE, 1)
+    sim.gradient(gs, ts)
+    roof, ker = _kernel_summary(qvs, sim.h, peak, 1)
+    sim.close()
+    torch.cuda.empty_cache()
+    ref = _stored_oracle(f"wmaxcut_n{n}_p{p}")
+    units = float(1 << n) * p
+    entry = {"value": units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "dtype": "c128",
+             "objective": E, "roofline": roof, "kernels": ker,
+             "rel_err_E_vs_oracle": _rel(E, ref["f"]) if ref else None}
+    if headline is not None:
+        E64, dg64, dt64 = headline
+        entry["c64_headline_errors"] = {
+            "rel_err_E_vs_c128": _rel(E64, E), "max_rel_grad_err_vs_c128": _grad_err(dg64, dt64, dg, dt),
+            "rel_err_E_vs_oracle": _rel(E64, ref["f"]) if ref else None}
+    return {f"qaoa_wmaxcut_n{n}_p{p}_c128": entry}
 
 
 def _extra_inpass(qvs, torch, stream, peak, steps, warmup, n=N_QUBITS, p=P_LAYERS):
@@ -386,6 +555,54 @@ def _extra_qaoaz(qvs, torch, stream, peak, steps, warmup, n, p):
     return out
 
 
+def _batch_roofline(torch, info, ms, peak):
+    """HBM and FP32-FMA rooflines of one batched solve from the library's cost model."""
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    mhz = 2070.0
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+    fma_peak = props.multi_processor_count * 128 * mhz * 1e6    # FP32 lanes x clock
+    gbs = info["bytes_per_solve"] / (ms * 1e-3) / 1e9
+    fmas = info["fma_per_solve"] / (ms * 1e-3)
+    return {"hbm": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                    "bytes_per_solve": info["bytes_per_solve"]},
+            "alu": {"bound": "alu", "achieved": fmas / 1e12, "peak": fma_peak / 1e12, "unit": "TFMA/s",
+                    "frac": fmas / fma_peak, "fma_per_solve": info["fma_per_solve"],
+                    "peak_note": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {mhz:.0f} MHz"}}
+
+
+def _extra_shared(qvs, torch, stream, peak, steps, n=20, count=1024):
+    """Many parameter sets of ONE instance (weighted max-cut on G(20,1/2)), depths 2..8: one shared
+    2^n quality vector against per-set copies of it."""
+    inst = wl.wmaxcut(n, 8, instance=7)
+    G = inst.graph
+    q = torch.empty(1 << n, dtype=torch.float32, device="cuda")
+    qvs.qvs_quality_maxcut(n, G.eu, G.ev, G.w, q, qvs.QVS_F32, stream)
+    rng = wl.rng_for(250, count)
+    ps = rng.integers(2, 9, size=count)
+    th = [wl.thetas(int(p), wl.rng_for(251, k)) for k, p in enumerate(ps)]
+    gl, tl = [t[0] for t in th], [t[1] for t in th]
+    units = float(1 << n) * float(ps.sum())
+    res = {}
+    for mode in ("shared", "copies"):
+        b = qvs.Batch([n] * count, ps, stream)
+        if mode == "shared":
+            b.set_quality_shared(q)
+        else:
+            b.set_quality(q.repeat(count))
+        ms = _time_steps(torch, stream, lambda: b.gradient(gl, tl), max(3, steps // 2), 2)
+        res[mode] = {"value": units / (ms * 1e-3), "ms_per_step": ms,
+                     "roofline": _batch_roofline(torch, b.info(), ms, peak)}
+        b.close()
+        torch.cuda.empty_cache()
+    return {f"parameter_sets_{count}_of_one_wmaxcut_n{n}": {
+        "value": res["shared"]["value"], "unit": UNIT, "ms_per_step": res["shared"]["ms_per_step"],
+        "roofline": res["shared"]["roofline"], "per_set_quality_copies": res["copies"],
+        "note": f"{count} parameter sets, p uniform in 2..8, one persistent launch; q read by all sets"}}
+
+
 def _extra_batch(qvs, torch, stream, peak, steps, warmup, count, plain=True):
     out = {}
     # batched QAOA: n in 12..20, p in 2..8, 3-regular graphs
@@ -401,10 +618,26 @@ def _extra_batch(qvs, torch, stream, peak, steps, warmup, count, plain=True):
     gl, tl = [i.gammas for i in insts], [i.ts for i in insts]
     ms = _time_steps(torch, stream, lambda: b.gradient(gl, tl), max(3, steps // 2), 2)
     units = float(sum(s * int(p) for s, p in zip(sizes, spec.ps)))
+    info = b.info()
     entry = {"value": units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
-             "instances_per_s": len(insts) / (ms * 1e-3), "launches_per_step": 1, "autotune": b.info()}
+             "instances_per_s": len(insts) / (ms * 1e-3), "launches_per_step": 1, "autotune": info,
+             "roofline": _batch_roofline(torch, info, ms, peak)}
+    # the device optimiser: one BFGS per instance, all advanced together (gtol 1e-3, <= 30 iterations)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, _, f, it, ev, stop = b.optimise(gl, tl, gtol=1e-3, max_iter=30)
+    opt_s = time.perf_counter() - t0
+    E0, _, _ = b.gradient(gl, tl)
+    entry["optimise"] = {
+        "instances_per_s": len(insts) / opt_s, "s_per_batch": opt_s, "gtol": 1e-3, "max_iter": 30,
+        "evaluations_max": int(ev.max()), "evaluations_mean": float(ev.mean()),
+        "stop_counts": {str(k): int((stop == k).sum()) for k in (0, 1, 2)},
+        "mean_relative_decrease": float(np.mean((E0 - f) / np.abs(E0))),
+        "note": "wall time of qvs_batch_optimise: one batched objective + gradient launch and one BFGS step "
+                "kernel per iteration (CUDA graph), all instances at once"}
     b.close()
     out[f"batched_qaoa_{count}"] = entry
+    out.update(_extra_shared(qvs, torch, stream, peak, steps))
     if not plain:
         return out
     # the plain per-instance path over the same instances, timed once
@@ -414,7 +647,6 @@ def _extra_batch(qvs, torch, stream, peak, steps, warmup, count, plain=True):
         sim = qvs.Simulator(sizes[k], qvs.QVS_C64, stream)
         sim.set_quality(q[int(offs[k]):int(offs[k + 1])]).set_mixer(qvs.QVS_MIX_HYPERCUBE, qvs.hypercube_desc(inst.graph.n))
         sims.append(sim)
-    setup_s = time.perf_counter() - t0
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k, inst in enumerate(insts):
@@ -426,6 +658,27 @@ def _extra_batch(qvs, torch, stream, peak, steps, warmup, count, plain=True):
     entry["plain_per_instance"] = {"value": units / plain_s, "unit": UNIT, "s_per_batch": plain_s,
                                    "note": "looped single-instance qvs_gradient calls, complex64"}
     entry["speedup_vs_plain"] = plain_s / (ms * 1e-3)
+    # the plain complex128 path (fp64-accuracy state) over the same instances, one handle reused per size
+    sims = {}
+    for k, inst in enumerate(insts):
+        n = inst.graph.n
+        if n not in sims:
+            sims[n] = qvs.Simulator(sizes[k], qvs.QVS_C128, stream)
+            sims[n].set_mixer(qvs.QVS_MIX_HYPERCUBE, qvs.hypercube_desc(n))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k, inst in enumerate(insts):
+        sim = sims[inst.graph.n]
+        sim.set_quality(q[int(offs[k]):int(offs[k + 1])])
+        sim.gradient(inst.gammas, inst.ts)
+    torch.cuda.synchronize()
+    plain128_s = time.perf_counter() - t0
+    for sim in sims.values():
+        sim.close()
+    entry["plain_per_instance_c128"] = {"value": units / plain128_s, "unit": UNIT, "s_per_batch": plain128_s,
+                                        "note": "looped single-instance qvs_gradient calls, complex128 (quality "
+                                                "copied into the handle before each call)"}
+    entry["speedup_vs_plain_c128"] = plain128_s / (ms * 1e-3)
     return out
 
 
@@ -544,12 +797,16 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_extras and (n, p) == (N_QUBITS, P_LAYERS):
         sim.close()
         torch.cuda.empty_cache()
-        extras = run_extras(qvs, torch, stream, peak, args.steps, args.warmup)
+        extras = run_extras(qvs, torch, stream, peak, args.steps, args.warmup,
+                            headline=(results[-1][0], results[-1][1], results[-1][2]))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, desc, _ = oracle_sample(seconds_target=15.0)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+        rate_all, desc_all, _, cores = oracle_all_cores(seconds_target=15.0)
+        rate1, desc1, _ = oracle_sample(seconds_target=15.0)
+        cpu = {"value": rate_all, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc_all,
+               "cpu_model": cpu_model(),
+               "single_thread": {"value": rate1, "unit": UNIT, "cores": 1, "sample": desc1}}
 
     if rank == 0:
         E0 = results[-1][0]
@@ -603,12 +860,14 @@ def run_workload(args):
     import paper_2110_03963_gb300 as qvs
     stream = torch.cuda.current_stream()
     peak, _ = _peaks()
-    n = args.qubits if args.qubits != N_QUBITS else {"qwoa": 26, "qaoaz": 24, "parity": 24, "batch": 0}[args.workload]
-    p = args.layers if args.layers != P_LAYERS else {"qwoa": 6, "qaoaz": 4, "parity": 4, "batch": 0}[args.workload]
+    n = args.qubits if args.qubits != N_QUBITS else {"qwoa": 26, "qaoaz": 24, "parity": 24, "batch": 0,
+                                                     "c128": 28}[args.workload]
+    p = args.layers if args.layers != P_LAYERS else {"qwoa": 6, "qaoaz": 4, "parity": 4, "batch": 0,
+                                                     "c128": 8}[args.workload]
     res = run_extras(qvs, torch, stream, peak, args.steps, args.warmup, only=args.workload, qwoa_n=n, qwoa_p=p,
                      qaoaz_n=n, qaoaz_p=p, batch_count=args.count)
-    (name, entry), = res.items()
-    print(json.dumps({"workload": name, **entry}), flush=True)
+    for name, entry in res.items():
+        print(json.dumps({"workload": name, **entry}), flush=True)
     return 0
 
 
@@ -624,7 +883,7 @@ def main():
                          "cost as a quadratic form evaluated inside the phase passes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the QWOA, QAOAz and batched lines")
-    ap.add_argument("--workload", default="qaoa", choices=["qaoa", "qwoa", "qaoaz", "parity", "batch"],
+    ap.add_argument("--workload", default="qaoa", choices=["qaoa", "qwoa", "qaoaz", "parity", "batch", "c128"],
                     help="qaoa = the benchmark line; the others print one diagnostic line for that workload "
                          "(sizes from --qubits/--layers/--count)")
     ap.add_argument("--count", type=int, default=4096, help="instances for --workload batch")

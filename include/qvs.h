@@ -307,8 +307,49 @@ int qvs_batch_set_quality(qvs_batch_t b, const float* q, int on_device);
 /* gammas, ts: concatenated host arrays; E[count], dgamma and dt concatenated host outputs. */
 int qvs_batch_gradient(qvs_batch_t b, const double* gammas, const double* ts, double* E,
                        double* dgamma, double* dt);
-/* The autotuner's choice (CTAs per SM) and its two trial times in milliseconds. */
-int qvs_batch_info(qvs_batch_t b, int* ctas_per_sm, double* tuned_ms_1, double* tuned_ms_2);
+/* Many parameter sets of ONE instance, evaluated at once (the GPU analogue of the paper's Sec. 4
+ * parallel evaluation of gradient components): every instance of the batch reads the same 2^n fp32
+ * qualities q (host or device per on_device; copied). All instances must have the same n (QVS_EINVAL otherwise); their
+ * depths and parameters may differ. */
+int qvs_batch_set_quality_shared(qvs_batch_t b, const float* q, int on_device);
+
+/* Sec. 4 on the device: minimise every instance's objective f_i(theta_i) over theta_i =
+ * (gamma_1, t_1, ..., gamma_p, t_p) with its own BFGS, all at once. Each iteration evaluates the
+ * objective and adjoint gradient of every still-active instance at its trial point in one launch of
+ * the batched kernel, then one small kernel advances every instance's BFGS state: the same rules as
+ * qvs_bfgs_minimize (Armijo test with c1 = 1e-4, at most 30 halvings, the inverse update skipped
+ * when y.s <= 0, a reset to steepest descent on a non-descent direction), the inverse-Hessian
+ * estimate kept in fp64 on the device. Both steps and the read-back of the active count form one
+ * CUDA graph, replayed until no instance is active. gammas, ts: concatenated host arrays (as for
+ * qvs_batch_gradient) holding the start points, overwritten with the results. Per-instance host
+ * outputs (count entries each, NULL allowed): f_out the final objective, iters_out the accepted
+ * iterations, evals_out the evaluations, stop_out 0 = max|g| <= gtol, 1 = max_iter reached,
+ * 2 = no line-search step lowered f. Needs 2p <= 128 per instance (QVS_EUNSUPPORTED otherwise);
+ * QVS_ESTATE before the qualities are set; QVS_EINVAL for negative gtol, max_iter outside
+ * 0..100000 or non-finite start values. */
+int qvs_batch_optimise(qvs_batch_t b, double* gammas, double* ts, double gtol, int max_iter, double* f_out,
+                       int* iters_out, int* evals_out, int* stop_out);
+
+/* What a batch does per solve (qvs_batch_info):
+ *   ctas_per_sm      the autotuner's choice (0 before the first solve or optimisation);
+ *   trial_ms[2]      its timed launches at 1 and 2 CTAs per SM;
+ *   bytes_per_solve  compulsory global-memory bytes of one solve, summed over every pass of every
+ *                    instance (8 per complex64 vector element read or written, 4 per quality read;
+ *                    the HBM roofline's numerator whether or not a pass hits in L2);
+ *   fma_per_solve    fp32 fused multiply-adds of one solve (a model: 2 per amplitude, rotated bit
+ *                    and vector, 2 more per amplitude and bit for the adjoint accumulations, about
+ *                    8 per phase; the FP32-pipe roofline's numerator);
+ *   amp_layers       sum over instances of 2^n p (the throughput unit);
+ *   shared_quality   1 when every instance reads one shared quality vector. */
+typedef struct {
+  int ctas_per_sm;
+  int shared_quality;
+  double trial_ms[2];
+  double bytes_per_solve;
+  double fma_per_solve;
+  double amp_layers;
+} qvs_batch_info_t;
+int qvs_batch_info(qvs_batch_t b, qvs_batch_info_t* info);
 int qvs_batch_destroy(qvs_batch_t b);
 
 /* ----------------------------------------------------------------- allocation-free small solve

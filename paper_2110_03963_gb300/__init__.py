@@ -37,6 +37,7 @@ EXPORTED = [
     "qvs_batch_info", "qvs_batch_destroy", "qvs_gradient_small_noalloc", "qvs_strerror",
     "qvs_set_quality_qubo", "qvs_quality_qubo", "qvs_qubo_from_maxcut",
     "qvs_set_phase_terms", "qvs_evolve_ex", "qvs_gradient_ex", "qvs_bfgs_minimize", "qvs_optimise",
+    "qvs_batch_set_quality_shared", "qvs_batch_optimise",
 ]
 
 
@@ -61,6 +62,17 @@ class MixerDesc(ctypes.Structure):
         ("spec_lo", ctypes.c_double),
         ("spec_hi", ctypes.c_double),
         ("cheb_tol", ctypes.c_double),
+    ]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [
+        ("ctas_per_sm", ctypes.c_int),
+        ("shared_quality", ctypes.c_int),
+        ("trial_ms", ctypes.c_double * 2),
+        ("bytes_per_solve", ctypes.c_double),
+        ("fma_per_solve", ctypes.c_double),
+        ("amp_layers", ctypes.c_double),
     ]
 
 
@@ -105,8 +117,10 @@ def load(path: str = LIB_PATH):
         "qvs_gradient_small_noalloc": (I, [I, I, I, V, P(D), P(D), V, V]),
         "qvs_batch_create": (I, [P(V), I, P(ctypes.c_int32), P(ctypes.c_int32), V]),
         "qvs_batch_set_quality": (I, [V, V, I]),
+        "qvs_batch_set_quality_shared": (I, [V, V, I]),
+        "qvs_batch_optimise": (I, [V, P(D), P(D), D, I, P(D), P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int)]),
         "qvs_batch_gradient": (I, [V, P(D), P(D), P(D), P(D), P(D)]),
-        "qvs_batch_info": (I, [V, P(I), P(D), P(D)]),
+        "qvs_batch_info": (I, [V, P(BatchInfo)]),
         "qvs_batch_destroy": (I, [V]),
         "qvs_strerror": (ctypes.c_char_p, [I]),
         "qvs_set_quality_qubo": (I, [V, I, D, P(D), P(D)]),
@@ -508,6 +522,28 @@ def qvs_batch_set_quality(b, q):
     _check(load().qvs_batch_set_quality(b, p, dev), "qvs_batch_set_quality")
 
 
+def qvs_batch_set_quality_shared(b, q):
+    """One quality vector (2^n fp32 values) read by every instance of the batch (all of one n)."""
+    p, dev = _ptr_of(q)
+    _check(load().qvs_batch_set_quality_shared(b, p, dev), "qvs_batch_set_quality_shared")
+
+
+def qvs_batch_optimise(b, gammas, ts, count: int, gtol: float = 1e-6, max_iter: int = 200):
+    """Device BFGS of every instance at once. gammas, ts: concatenated start points. Returns
+    (gammas, ts, f[count], iterations[count], evaluations[count], stop[count])."""
+    g, t = _params(gammas, ts)
+    g, t = g.copy(), t.copy()
+    f = np.zeros(count)
+    it = np.zeros(count, dtype=np.int32)
+    ev = np.zeros(count, dtype=np.int32)
+    stop = np.zeros(count, dtype=np.int32)
+    IP = ctypes.POINTER(ctypes.c_int)
+    _check(load().qvs_batch_optimise(b, _dptr(g), _dptr(t), float(gtol), int(max_iter), _dptr(f),
+                                     it.ctypes.data_as(IP), ev.ctypes.data_as(IP), stop.ctypes.data_as(IP)),
+           "qvs_batch_optimise")
+    return g, t, f, it, ev, stop
+
+
 def qvs_batch_gradient(b, gammas, ts, count: int):
     """gammas, ts: concatenated per-instance parameters. Returns (E[count], dgamma, dt) concatenated."""
     g = np.ascontiguousarray(gammas, dtype=np.float64)
@@ -520,11 +556,11 @@ def qvs_batch_gradient(b, gammas, ts, count: int):
 
 
 def qvs_batch_info(b):
-    c = ctypes.c_int()
-    t1 = ctypes.c_double()
-    t2 = ctypes.c_double()
-    _check(load().qvs_batch_info(b, ctypes.byref(c), ctypes.byref(t1), ctypes.byref(t2)), "qvs_batch_info")
-    return {"ctas_per_sm": c.value, "trial_ms": [t1.value, t2.value]}
+    info = BatchInfo()
+    _check(load().qvs_batch_info(b, ctypes.byref(info)), "qvs_batch_info")
+    return {"ctas_per_sm": info.ctas_per_sm, "trial_ms": [info.trial_ms[0], info.trial_ms[1]],
+            "bytes_per_solve": info.bytes_per_solve, "fma_per_solve": info.fma_per_solve,
+            "amp_layers": info.amp_layers, "shared_quality": bool(info.shared_quality)}
 
 
 def qvs_batch_destroy(b):
@@ -561,6 +597,18 @@ class Batch:
         E, dg, dt = qvs_batch_gradient(self.h, np.concatenate(gammas_list), np.concatenate(ts_list), len(self.ns))
         cut = lambda v: [v[self.poff[i]:self.poff[i + 1]] for i in range(len(self.ns))]
         return E, cut(dg), cut(dt)
+
+    def set_quality_shared(self, q):
+        qvs_batch_set_quality_shared(self.h, q)
+        return self
+
+    def optimise(self, gammas_list, ts_list, gtol: float = 1e-6, max_iter: int = 200):
+        """Lists of per-instance start points -> (list of gammas, list of ts, f, iterations,
+        evaluations, stop), per instance."""
+        g, t, f, it, ev, stop = qvs_batch_optimise(self.h, np.concatenate(gammas_list), np.concatenate(ts_list),
+                                                   len(self.ns), gtol, max_iter)
+        cut = lambda v: [v[self.poff[i]:self.poff[i + 1]] for i in range(len(self.ns))]
+        return cut(g), cut(t), f, it, ev, stop
 
     def info(self):
         return qvs_batch_info(self.h)

@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "hc_pass.cuh"
+#include "hc_batch.h"
 
 namespace qvs {
 namespace hc {
@@ -944,6 +945,7 @@ struct BatchArgs {
   double* out_dg;            // concatenated like gammas
   double* out_dt;
   int* counter;
+  const int* active;         // per-instance flags (NULL: every instance); 0 = skip
   unsigned char* ws;         // workspace slots
   size_t slot_bytes;
   int64_t dim_max;
@@ -951,7 +953,7 @@ struct BatchArgs {
 };
 
 // pass j (1-based) of an instance's forward schedule (same rules as make_plan)
-__device__ __forceinline__ void bpass_info(const BInst& I, int j, int& type, int& shape, int& lb, int& la,
+__host__ __device__ __forceinline__ void bpass_info(const BInst& I, int j, int& type, int& shape, int& lb, int& la,
                                            int& lg) {
   const int p = I.p;
   if (I.g == 1) {
@@ -971,6 +973,43 @@ __device__ __forceinline__ void bpass_info(const BInst& I, int j, int& type, int
     else if (j % 2 == 0) { shape = F2; lb = (j - 2) / 2; la = -1; lg = -1; }
     else { shape = F1; lb = (j - 3) / 2; la = (j - 1) / 2; lg = (j - 1) / 2; }
   }
+}
+
+// Cost model of one instance's solve in the batched kernel, per amplitude summed over its passes:
+// compulsory global-memory bytes (8 per complex64 vector read or written, 4 per quality read) and
+// fp32 fused multiply-adds. The runtime-mask kernels rotate all 12 tile bits of a layer (masked
+// bits with tangent 0): 2 FMAs per amplitude, bit and vector, plus 2 per amplitude and bit for the
+// adjoint accumulation; a phase costs about 8 (argument reduction and the complex product).
+struct PassCost {
+  double bytes, fma;
+};
+static PassCost batch_instance_cost(const BInst& I) {
+  auto stored = [&](int j) { return j >= 1 && j <= I.F - 1 && j % I.ck_c == 0 && (j / I.ck_c) <= I.nck; };
+  double bytes = 0.0, fma = 0.0;
+  for (int j = 1; j <= I.F; ++j) {   // forward
+    int type, shape, lb, la, lg;
+    bpass_info(I, j, type, shape, lb, la, lg);
+    const double rot = 2.0 * TB * ((lb >= 0) + (la >= 0));
+    switch (shape) {
+      case F0: bytes += 12; fma += rot + 8; break;
+      case F1: bytes += 20; fma += rot + 8; break;
+      case F2: bytes += 16; fma += rot; break;
+      case FE: bytes += 20; fma += (lb >= 0 ? 8.0 * TB : 0.0) + 4; break;   // rotate, E, lambda, undo
+    }
+  }
+  for (int j = I.F - 1; j >= 1; --j) {   // adjoint
+    int type, shape, lb, la, lg;
+    bpass_info(I, j, type, shape, lb, la, lg);
+    const double unrot = 6.0 * TB * ((lb >= 0) + (la >= 0));
+    const double psi_w = (j - 1 >= 1 && !stored(j - 1)) ? 8.0 : 0.0;
+    switch (shape) {
+      case F0: bytes += 20; fma += unrot + 4; break;                  // R0
+      case F1: bytes += 28 + psi_w; fma += unrot + 16; break;         // R1
+      case F2: bytes += 24 + psi_w; fma += unrot; break;              // R2
+    }
+  }
+  const double dim = (double)((int64_t)1 << I.n);
+  return {bytes * dim, fma * dim};
 }
 
 __device__ __forceinline__ void run_shape(int shape, const PassArgs<float>& a, uint32_t t, uint32_t nt,
@@ -1004,6 +1043,7 @@ __global__ void __launch_bounds__(NT, 2) batch_kernel(const __grid_constant__ Ba
     __syncthreads();
     if (idx >= a.count) return;
     const int i = a.order[idx];
+    if (a.active && !a.active[i]) continue;   // uniform across the CTA: i comes from shared memory
     const BInst& I = a.inst[i];
     const int F = I.F;
     const int64_t dim = (int64_t)1 << I.n;
@@ -1092,32 +1132,12 @@ __global__ void __launch_bounds__(NT, 2) batch_kernel(const __grid_constant__ Ba
 }  // namespace hc
 }  // namespace qvs
 
-struct qvs_batch {
-  int count = 0;
-  int total_p = 0;
-  int64_t total_q = 0;
-  cudaStream_t stream = nullptr;
-  std::vector<int> n, p, th0;
-  std::vector<int64_t> qoff;
-  qvs::DevBuf inst, order, q, theta, out, counter, ws;
-  size_t slot_bytes = 0;
-  int64_t dim_max = 0;
-  int nck_max = 0;
-  int nslots = 0;
-  int sms = 0;
-  int ctas_per_sm = 0;       // chosen by the autotuner on the first solve (0 = not yet tuned)
-  double tuned_ms[3] = {0, 0, 0};
-  double* host_theta = nullptr;   // pinned: gammas then ts
-  double* host_out = nullptr;     // pinned: E, dg, dt
-  cudaGraphExec_t graph = nullptr;
-  bool have_q = false;
-};
-
 namespace qvs {
 namespace hc {
 
-static int batch_launch(qvs_batch_t b, int ctas_per_sm) {
+int batch_launch(qvs_batch_t b, int ctas_per_sm, const int* active) {
   BatchArgs a{};
+  a.active = active;
   a.count = b->count;
   a.inst = b->inst.as<BInst>();
   a.order = b->order.as<int>();
@@ -1136,6 +1156,40 @@ static int batch_launch(qvs_batch_t b, int ctas_per_sm) {
   QVS_CUDA_TRY(cudaMemsetAsync(b->counter.ptr, 0, sizeof(int), b->stream));
   batch_kernel<<<grid, NT, 2 * SM_SLOTS * sizeof(float2), b->stream>>>(a);
   QVS_CUDA_TRY(cudaGetLastError());
+  return QVS_OK;
+}
+
+int batch_autotune(qvs_batch_t b) {
+  if (b->ctas_per_sm > 0) return QVS_OK;
+  // one timed launch per candidate occupancy, keep the fastest
+  cudaEvent_t e0, e1;
+  QVS_CUDA_TRY(cudaEventCreate(&e0));
+  QVS_CUDA_TRY(cudaEventCreate(&e1));
+  double best = 1e30;
+  int choice = 1;
+  for (int c = 1; c <= 2; ++c) {
+    int st = QVS_OK;
+    if (cudaEventRecord(e0, b->stream) != cudaSuccess) st = QVS_ECUDA;
+    if (st == QVS_OK) st = batch_launch(b, c, nullptr);
+    if (st == QVS_OK && (cudaEventRecord(e1, b->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+      st = QVS_ECUDA;
+    float ms = 0.f;
+    if (st == QVS_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) st = QVS_ECUDA;
+    if (st != QVS_OK) {
+      (void)cudaGetLastError();
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return st;
+    }
+    b->tuned_ms[c] = ms;
+    if (ms < best) {
+      best = ms;
+      choice = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->ctas_per_sm = choice;
   return QVS_OK;
 }
 
@@ -1192,6 +1246,10 @@ extern "C" int qvs_batch_create(qvs_batch_t* out, int count, const int32_t* n_qu
     b->nck_max = std::max(b->nck_max, I.nck);
     max_rows_tiles = std::max(max_rows_tiles, (size_t)(3 * pl.F + 1) * I.ntiles);
     cost[i] = (double)((int64_t)1 << n) * (2 * pl.F - 1);
+    const PassCost pc = batch_instance_cost(I);
+    b->model_bytes += pc.bytes;
+    b->model_fma += pc.fma;
+    b->amp_layers += (double)((int64_t)1 << n) * p;
     qtot += (int64_t)1 << n;
     ptot += p;
   }
@@ -1213,7 +1271,6 @@ extern "C" int qvs_batch_create(qvs_batch_t* out, int count, const int32_t* n_qu
                   ~(size_t)255;
   int st = QVS_OK;
   if ((st = b->inst.ensure(sizeof(BInst) * count)) != QVS_OK || (st = b->order.ensure(sizeof(int) * count)) != QVS_OK ||
-      (st = b->q.ensure(sizeof(float) * (size_t)qtot)) != QVS_OK ||
       (st = b->theta.ensure(sizeof(double) * 2 * (size_t)ptot)) != QVS_OK ||
       (st = b->out.ensure(sizeof(double) * ((size_t)count + 2 * (size_t)ptot))) != QVS_OK ||
       (st = b->counter.ensure(sizeof(int))) != QVS_OK ||
@@ -1240,10 +1297,55 @@ extern "C" int qvs_batch_create(qvs_batch_t* out, int count, const int32_t* n_qu
   return QVS_OK;
 }
 
+// Captured graphs hold the quality pointer: drop them when the buffer moves.
+static int batch_ensure_q(qvs_batch_t b, size_t bytes) {
+  void* before = b->q.ptr;
+  QVS_TRY(b->q.ensure(bytes));
+  if (b->q.ptr != before) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->opt_graph) cudaGraphExecDestroy(b->opt_graph);
+    b->graph = nullptr;
+    b->opt_graph = nullptr;
+  }
+  return QVS_OK;
+}
+
+// Point every instance's quality offset at its own segment (shared = false) or at the one
+// shared vector (shared = true); the kernel reads the offsets from the device instance table.
+static int batch_set_qoffsets(qvs_batch_t b, bool shared) {
+  using namespace qvs::hc;
+  if (b->shared_q == shared && b->have_q) return QVS_OK;
+  std::vector<BInst> inst(b->count);
+  QVS_CUDA_TRY(cudaMemcpyAsync(inst.data(), b->inst.ptr, sizeof(BInst) * b->count, cudaMemcpyDeviceToHost,
+                               b->stream));
+  QVS_CUDA_TRY(cudaStreamSynchronize(b->stream));
+  for (int i = 0; i < b->count; ++i) inst[i].qoff = shared ? 0 : b->qoff[i];
+  QVS_CUDA_TRY(cudaMemcpyAsync(b->inst.ptr, inst.data(), sizeof(BInst) * b->count, cudaMemcpyHostToDevice,
+                               b->stream));
+  QVS_CUDA_TRY(cudaStreamSynchronize(b->stream));
+  b->shared_q = shared;
+  return QVS_OK;
+}
+
 extern "C" int qvs_batch_set_quality(qvs_batch_t b, const float* q, int on_device) {
   if (!b || !q) return QVS_EINVAL;
+  QVS_TRY(batch_ensure_q(b, sizeof(float) * (size_t)b->total_q));
   QVS_CUDA_TRY(cudaMemcpyAsync(b->q.ptr, q, sizeof(float) * (size_t)b->total_q,
                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, b->stream));
+  QVS_TRY(batch_set_qoffsets(b, false));
+  b->have_q = true;
+  return QVS_OK;
+}
+
+extern "C" int qvs_batch_set_quality_shared(qvs_batch_t b, const float* q, int on_device) {
+  if (!b || !q) return QVS_EINVAL;
+  for (int i = 1; i < b->count; ++i)
+    if (b->n[i] != b->n[0]) return QVS_EINVAL;
+  const size_t dim = (size_t)1 << b->n[0];
+  QVS_TRY(batch_ensure_q(b, sizeof(float) * dim));
+  QVS_CUDA_TRY(cudaMemcpyAsync(b->q.ptr, q, sizeof(float) * dim,
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, b->stream));
+  QVS_TRY(batch_set_qoffsets(b, true));
   b->have_q = true;
   return QVS_OK;
 }
@@ -1259,28 +1361,11 @@ extern "C" int qvs_batch_gradient(qvs_batch_t b, const double* gammas, const dou
   memcpy(b->host_theta, gammas, sizeof(double) * P);
   memcpy(b->host_theta + P, ts, sizeof(double) * P);
   if (b->ctas_per_sm == 0) {
-    // autotune: one timed run per candidate occupancy, keep the fastest
-    cudaEvent_t e0, e1;
-    QVS_CUDA_TRY(cudaEventCreate(&e0));
-    QVS_CUDA_TRY(cudaEventCreate(&e1));
-    double best = 1e30;
-    for (int c = 1; c <= 2; ++c) {
-      QVS_CUDA_TRY(cudaMemcpyAsync(b->theta.ptr, b->host_theta, sizeof(double) * 2 * P, cudaMemcpyHostToDevice,
-                                   b->stream));
-      QVS_CUDA_TRY(cudaEventRecord(e0, b->stream));
-      QVS_TRY(hc::batch_launch(b, c));
-      QVS_CUDA_TRY(cudaEventRecord(e1, b->stream));
-      QVS_CUDA_TRY(cudaEventSynchronize(e1));
-      float ms = 0.f;
-      QVS_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-      b->tuned_ms[c] = ms;
-      if (ms < best) {
-        best = ms;
-        b->ctas_per_sm = c;
-      }
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    QVS_CUDA_TRY(cudaMemcpyAsync(b->theta.ptr, b->host_theta, sizeof(double) * 2 * P, cudaMemcpyHostToDevice,
+                                 b->stream));
+    QVS_TRY(hc::batch_autotune(b));
+  }
+  if (!b->graph) {
     // capture the whole solve (parameters in, kernel, results out) as a CUDA graph
     cudaStream_t cs;
     QVS_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -1291,7 +1376,7 @@ extern "C" int qvs_batch_gradient(qvs_batch_t b, const double* gammas, const dou
     int st = QVS_OK;
     if (cudaMemcpyAsync(b->theta.ptr, b->host_theta, sizeof(double) * 2 * P, cudaMemcpyHostToDevice, cs) != cudaSuccess)
       st = QVS_ECUDA;
-    if (st == QVS_OK) st = hc::batch_launch(b, b->ctas_per_sm);
+    if (st == QVS_OK) st = hc::batch_launch(b, b->ctas_per_sm, nullptr);
     if (st == QVS_OK &&
         cudaMemcpyAsync(b->host_out, b->out.ptr, sizeof(double) * ((size_t)b->count + 2 * P), cudaMemcpyDeviceToHost,
                         cs) != cudaSuccess)
@@ -1313,11 +1398,16 @@ extern "C" int qvs_batch_gradient(qvs_batch_t b, const double* gammas, const dou
   return QVS_OK;
 }
 
-extern "C" int qvs_batch_info(qvs_batch_t b, int* ctas_per_sm, double* tuned_ms_1, double* tuned_ms_2) {
-  if (!b) return QVS_EINVAL;
-  if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm;
-  if (tuned_ms_1) *tuned_ms_1 = b->tuned_ms[1];
-  if (tuned_ms_2) *tuned_ms_2 = b->tuned_ms[2];
+extern "C" int qvs_batch_info(qvs_batch_t b, qvs_batch_info_t* info) {
+  if (!b || !info) return QVS_EINVAL;
+  memset(info, 0, sizeof(*info));
+  info->ctas_per_sm = b->ctas_per_sm;
+  info->trial_ms[0] = b->tuned_ms[1];
+  info->trial_ms[1] = b->tuned_ms[2];
+  info->bytes_per_solve = b->model_bytes;
+  info->fma_per_solve = b->model_fma;
+  info->amp_layers = b->amp_layers;
+  info->shared_quality = b->shared_q ? 1 : 0;
   return QVS_OK;
 }
 
@@ -1326,6 +1416,13 @@ extern "C" int qvs_batch_destroy(qvs_batch_t b) {
   if (b->stream) cudaStreamSynchronize(b->stream);
   else cudaDeviceSynchronize();
   if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->opt_graph) cudaGraphExecDestroy(b->opt_graph);
+  b->opt_state.release();
+  b->opt_vec.release();
+  b->opt_H.release();
+  b->opt_active.release();
+  b->opt_nactive.release();
+  if (b->host_nactive) cudaFreeHost(b->host_nactive);
   b->inst.release();
   b->order.release();
   b->q.release();

@@ -61,8 +61,19 @@ def _wmaxcut(n: int, p: int):
     return prob, inst.gammas, inst.ts, desc
 
 
+def _maxcut10():
+    inst = wl.maxcut10()
+    G = inst.graph
+    prob = orc.maxcut_problem(10, G.eu, G.ev)
+    desc = ("QAOA max-cut (Sec. 6.1 cost, integer uncut-edge counts), n=10, random 3-regular graph "
+            "workloads.maxcut10(), hypercube mixer (Sec. 2.3.1), p=2, complex128")
+    return prob, inst.gammas, inst.ts, desc
+
+
 # case name -> (case number, builder, with gradient)
 CASES = {
+    "maxcut3_n10_p2": (8, _maxcut10, True),
+    "batch_optimise_64": (9, None, None),
     "qwoa_n24_p3": (1, lambda: _qwoa(24, 3), True),
     "qwoa_n25_p2": (2, lambda: _qwoa(25, 2), True),
     "qwoa_n26_p6": (3, lambda: _qwoa(26, 6), True),
@@ -73,7 +84,43 @@ CASES = {
 }
 
 
+def optimise_instances(count: int = 64):
+    """(n, p, instance) of the sampled optimisation instances: 3-regular max-cut (the batched
+    workload's family) with n in 12..15 and p in 1..3, sizes the oracle optimises in seconds."""
+    rng = wl.rng_for(SAMPLE_SEED, 100)
+    ns = rng.integers(12, 16, size=count)
+    ps = rng.integers(1, 4, size=count)
+    return [(int(n), int(p), 5000 + i) for i, (n, p) in enumerate(zip(ns, ps))]
+
+
+def run_optimise_case(name: str = "batch_optimise_64") -> str:
+    """The oracle's BFGS (gtol 1e-8) from each instance's seeded start point (workloads.maxcut3)."""
+    t0 = time.time()
+    rows = []
+    for n, p, inst_id in optimise_instances():
+        inst = wl.maxcut3(n, p, instance=inst_id)
+        G = inst.graph
+        prob = orc.maxcut_problem(n, G.eu, G.ev)
+        gs, ts, f, it, ev, stop = orc.optimise(prob, inst.gammas, inst.ts, gtol=1e-8, max_iter=500)
+        rows.append({"n": n, "p": p, "instance": inst_id, "f0": orc.objective(prob, inst.gammas, inst.ts),
+                     "f": float(f), "gammas": [float(x) for x in gs], "ts": [float(x) for x in ts],
+                     "iterations": int(it), "evaluations": int(ev), "stop": int(stop)})
+    out = {"what": "BFGS (Sec. 4) of 64 QAOA max-cut instances on random 3-regular graphs "
+                   "(workloads.maxcut3(n, p, instance)), integer qualities, from the seeded start points, "
+                   "gtol 1e-8, max_iter 500",
+           "written_by": "tests/golden/make_oracle_values.py (calls only oracle/ on workloads/ inputs)",
+           "instances": rows, "oracle_seconds": round(time.time() - t0, 1)}
+    path = os.path.join(HERE, f"oracle_{name}.json")
+    lines = [f"{json.dumps(k)}: {json.dumps(v, separators=(',', ':'))}" for k, v in out.items() if k != "instances"]
+    body = ",\n".join(json.dumps(r, separators=(",", ":")) for r in rows)
+    with open(path, "w") as fh:
+        fh.write("{\n" + ",\n".join(lines) + ',\n"instances": [\n' + body + "\n]\n}\n")
+    return path
+
+
 def run_case(name: str) -> str:
+    if name == "batch_optimise_64":
+        return run_optimise_case(name)
     number, build, with_grad = CASES[name]
     t0 = time.time()
     prob, gammas, ts, desc = build()

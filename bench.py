@@ -720,6 +720,7 @@ def run_ours(args):
     sim.set_mixer(qvs.QVS_MIX_HYPERCUBE, qvs.hypercube_desc(n))
     if args.ckpt is not None:
         sim.set_option(qvs.QVS_OPT_CKPT_LAYERS, args.ckpt)
+    sim.set_option(qvs.QVS_OPT_STAGED, args.staged)
     gs, ts = np.asarray(inst.gammas), np.asarray(inst.ts)
 
     def barrier():
@@ -822,7 +823,8 @@ def run_ours(args):
                        "quality": ("quadratic form evaluated in the phase passes (fixed point 2^-%d)"
                                    % sim_qubo_F if qubo else "fp32 vector in HBM"),
                        "l2": "inputs larger than L2 (2 GiB state%s)" % ("" if qubo else ", 1 GiB q"),
-                       "ckpt_layers": args.ckpt if args.ckpt is not None else "ceil(sqrt(p))"},
+                       "ckpt_layers": args.ckpt if args.ckpt is not None else "ceil(sqrt(p))",
+                       "staged_passes": bool(args.staged)},
             "roofline": {"bound": "hbm", "kernel": top["name"], "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
                          "traffic": _traffic_per_launch(top["name"], dim) if (n, p) == (N_QUBITS, P_LAYERS)
@@ -881,6 +883,8 @@ def main():
     ap.add_argument("--quality", default="vector", choices=["vector", "qubo"],
                     help="vector: q generated once into HBM and read by the phase passes; qubo: the max-cut "
                          "cost as a quadratic form evaluated inside the phase passes")
+    ap.add_argument("--staged", type=int, default=1, choices=[0, 1],
+                    help="1: two-vector hypercube passes as TMA-staged persistent kernels; 0: one CTA per tile")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the QWOA, QAOAz and batched lines")
     ap.add_argument("--workload", default="qaoa", choices=["qaoa", "qwoa", "qaoaz", "parity", "batch", "c128"],

@@ -63,9 +63,15 @@ enum {
   QVS_OPT_CKPT_LAYERS = 1,  /* adjoint: store the forward state every this many layers and
                                uncompute in between; 0 = ceil(sqrt(p)) (default); 1 = store
                                every pass boundary (no uncompute)                             */
-  QVS_OPT_PROFILE = 2       /* 1: bracket every kernel launch with CUDA events on the handle's
+  QVS_OPT_PROFILE = 2,      /* 1: bracket every kernel launch with CUDA events on the handle's
                                stream and accumulate per-kernel statistics (qvs_kernel_stats);
                                0: off (default). Setting it resets the statistics.           */
+  QVS_OPT_STAGED = 3        /* hypercube mixer, complex64, n > 12: 1 (default) runs the two-vector
+                               passes (last forward pass and the adjoint passes) as persistent
+                               kernels whose next tile is copied into shared memory by the
+                               Tensor Memory Accelerator while the current one is processed;
+                               0 runs one CTA per tile. Results are identical. A staged pass whose
+                               copy wait expires makes the call return QVS_ETIMEOUT.          */
 };
 
 /*
@@ -329,6 +335,22 @@ int qvs_batch_set_quality_shared(qvs_batch_t b, const float* q, int on_device);
  * 0..100000 or non-finite start values. */
 int qvs_batch_optimise(qvs_batch_t b, double* gammas, double* ts, double gtol, int max_iter, double* f_out,
                        int* iters_out, int* evals_out, int* stop_out);
+
+/* Sec. 5 (the Ansatz's benchmark method with param_persist): a depth sweep D = d_min..d_max of
+ * `repeats` optimisations of ONE QAOA instance (hypercube mixer, n qubits with 12 <= n <= 28,
+ * equal-superposition start, 2^n fp32 qualities q in host or device memory per on_device). Each
+ * depth is one batch of `repeats` parameter sets sharing q, optimised together by
+ * qvs_batch_optimise(gtol, max_iter). Start points (the random draws are the caller's):
+ *   D = d_min: repeat r starts from init[r*2*d_min .. ]: gamma_1..gamma_dmin, then t_1..t_dmin;
+ *   D > d_min: every repeat starts from the best optimum (lowest f, first repeat on ties) of depth
+ *              D-1 for layers 1..D-1 and from its own new-layer values for layer D, taken in order
+ *              from the rest of init: repeats * (gamma_D, t_D) per depth.
+ * Outputs (host): f_out[(d_max - d_min + 1) * repeats] the optimised objectives, depth-major;
+ * best_theta: per depth D (in order) its best parameters, gamma_1..gamma_D then t_1..t_D
+ * (sum over D of 2D values). QVS_EINVAL for a NULL pointer or a size out of range (2 d_max <= 128). */
+int qvs_benchmark(int n, const float* q, int on_device, int d_min, int d_max, int repeats,
+                  const double* init, double gtol, int max_iter, double* f_out, double* best_theta,
+                  void* stream);
 
 /* What a batch does per solve (qvs_batch_info):
  *   ctas_per_sm      the autotuner's choice (0 before the first solve or optimisation);

@@ -662,6 +662,36 @@ def optimise(prob: Problem, gammas0, ts0, gtol: float = 1e-8, max_iter: int = 10
     return th[0::2], th[1::2], f, it, ev, stop
 
 
+def benchmark(prob: Problem, d_min: int, d_max: int, repeats: int, init, gtol: float = 1e-8,
+              max_iter: int = 1000):
+    """Sec. 5, the Ansatz's benchmark method with param_persist = True: for each depth
+    D = d_min..d_max, `repeats` optimisations (`optimise`). At D = d_min repeat r starts from
+    init[r * 2 d_min:] (gamma_1..gamma_D, then t_1..t_D); at every later depth each repeat starts
+    from the best optimum of depth D - 1 (lowest f, the first repeat on ties) for layers 1..D-1 and
+    from its own next two init values (gamma_D, t_D) for layer D.
+    Returns (f[depth][repeat], [(gammas, ts) of the best repeat at each depth])."""
+    init = np.asarray(init, dtype=np.float64).reshape(-1)
+    pos = 0
+    fs, best = [], []
+    for D in range(d_min, d_max + 1):
+        row = []
+        results = []
+        for r in range(repeats):
+            if D == d_min:
+                g0 = init[pos + r * 2 * D: pos + r * 2 * D + D]
+                t0 = init[pos + r * 2 * D + D: pos + (r + 1) * 2 * D]
+            else:
+                g0 = np.append(best[-1][0], init[pos + 2 * r])
+                t0 = np.append(best[-1][1], init[pos + 2 * r + 1])
+            gs, ts, f, _, _, _ = optimise(prob, g0, t0, gtol=gtol, max_iter=max_iter)
+            row.append(f)
+            results.append((np.asarray(gs), np.asarray(ts)))
+        pos += repeats * 2 * D if D == d_min else repeats * 2
+        fs.append(row)
+        best.append(results[int(np.argmin(row))])
+    return np.array(fs), best
+
+
 # ============================================================== convenience builders
 
 

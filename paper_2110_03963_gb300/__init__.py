@@ -28,6 +28,7 @@ QVS_INIT_UNIFORM, QVS_INIT_EXPLICIT = 0, 1
 QVS_MIX_HYPERCUBE, QVS_MIX_CIRCULANT, QVS_MIX_CSR, QVS_MIX_PARITY = 1, 2, 3, 4
 QVS_OPT_CKPT_LAYERS = 1
 QVS_OPT_PROFILE = 2
+QVS_OPT_STAGED = 3
 
 EXPORTED = [
     "qvs_create", "qvs_destroy", "qvs_set_quality", "qvs_set_mixer", "qvs_set_initial_state",
@@ -37,7 +38,7 @@ EXPORTED = [
     "qvs_batch_info", "qvs_batch_destroy", "qvs_gradient_small_noalloc", "qvs_strerror",
     "qvs_set_quality_qubo", "qvs_quality_qubo", "qvs_qubo_from_maxcut",
     "qvs_set_phase_terms", "qvs_evolve_ex", "qvs_gradient_ex", "qvs_bfgs_minimize", "qvs_optimise",
-    "qvs_batch_set_quality_shared", "qvs_batch_optimise",
+    "qvs_batch_set_quality_shared", "qvs_batch_optimise", "qvs_benchmark",
 ]
 
 
@@ -118,6 +119,7 @@ def load(path: str = LIB_PATH):
         "qvs_batch_create": (I, [P(V), I, P(ctypes.c_int32), P(ctypes.c_int32), V]),
         "qvs_batch_set_quality": (I, [V, V, I]),
         "qvs_batch_set_quality_shared": (I, [V, V, I]),
+        "qvs_benchmark": (I, [I, V, I, I, I, I, P(D), D, I, P(D), P(D), V]),
         "qvs_batch_optimise": (I, [V, P(D), P(D), D, I, P(D), P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int)]),
         "qvs_batch_gradient": (I, [V, P(D), P(D), P(D), P(D), P(D)]),
         "qvs_batch_info": (I, [V, P(BatchInfo)]),
@@ -542,6 +544,28 @@ def qvs_batch_optimise(b, gammas, ts, count: int, gtol: float = 1e-6, max_iter: 
                                      it.ctypes.data_as(IP), ev.ctypes.data_as(IP), stop.ctypes.data_as(IP)),
            "qvs_batch_optimise")
     return g, t, f, it, ev, stop
+
+
+def qvs_benchmark(n: int, q, d_min: int, d_max: int, repeats: int, init, gtol: float = 1e-6, max_iter: int = 200,
+                  stream=None):
+    """Depth sweep with persisted parameters (see include/qvs.h). init: the start values (repeats x
+    2 d_min for the first depth, then repeats x 2 per later depth). Returns (f[depth][repeat],
+    list of best (gammas, ts) per depth)."""
+    nd = d_max - d_min + 1
+    need = repeats * 2 * d_min + repeats * 2 * (nd - 1)
+    x0 = np.ascontiguousarray(init, dtype=np.float64).reshape(-1)
+    if x0.shape[0] != need:
+        raise QvsError(QVS_EINVAL, f"init needs {need} values")
+    f = np.zeros(nd * repeats)
+    best = np.zeros(sum(2 * D for D in range(d_min, d_max + 1)))
+    qp, dev = _ptr_of(q)
+    _check(load().qvs_benchmark(int(n), qp, dev, int(d_min), int(d_max), int(repeats), _dptr(x0), float(gtol),
+                                int(max_iter), _dptr(f), _dptr(best), _stream_ptr(stream)), "qvs_benchmark")
+    out, o = [], 0
+    for D in range(d_min, d_max + 1):
+        out.append((best[o:o + D].copy(), best[o + D:o + 2 * D].copy()))
+        o += 2 * D
+    return f.reshape(nd, repeats), out
 
 
 def qvs_batch_gradient(b, gammas, ts, count: int):

@@ -26,7 +26,8 @@ int ensure_host_res(qvs_ctx* h, int p) {
   h->host_res = nullptr;
   h->host_res_cap = 0;
   const int cap = p < 64 ? 64 : p;
-  QVS_CUDA_TRY(cudaMallocHost((void**)&h->host_res, sizeof(double) * (1 + 2 * (size_t)cap)));
+  // 1 + 2 cap result slots and one more for the device error flag
+  QVS_CUDA_TRY(cudaMallocHost((void**)&h->host_res, sizeof(double) * (2 + 2 * (size_t)cap)));
   h->host_res_cap = cap;
   return QVS_OK;
 }
@@ -149,7 +150,8 @@ extern "C" int qvs_destroy(qvs_t h) {
   qvs::DevBuf* bufs[] = {&h->q, &h->psi0, &h->psi, &h->lam, &h->ckpt, &h->part, &h->res, &h->rowmap,
                          &h->work, &h->circ.lam, &h->circ.tab, &h->circ.qT, &h->csr.rowptr,
                          &h->csr.colind, &h->csr.values, &h->qubo.dcoef, &h->qubo.tab, &h->ex.coef,
-                         &h->ex.tab, &h->ex.g, &h->ex.mterms, &h->ex.mpart, &h->ex.mrowmap, &h->ex.mres};
+                         &h->ex.tab, &h->ex.g, &h->ex.mterms, &h->ex.mpart, &h->ex.mrowmap, &h->ex.mres,
+                         &h->flags};
   for (qvs::DevBuf* b : bufs) b->release();
   if (h->host_res) cudaFreeHost(h->host_res);
   prof_release(h);
@@ -286,6 +288,11 @@ extern "C" int qvs_set_option(qvs_t h, int option, int64_t value) {
   if (option == QVS_OPT_CKPT_LAYERS) {
     if (value < 0 || value > 4096) return QVS_EINVAL;
     h->ckpt_layers = (int)value;
+    return QVS_OK;
+  }
+  if (option == QVS_OPT_STAGED) {
+    if (value != 0 && value != 1) return QVS_EINVAL;
+    h->staged = value == 1;
     return QVS_OK;
   }
   if (option == QVS_OPT_PROFILE) {

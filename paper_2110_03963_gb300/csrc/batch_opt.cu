@@ -320,3 +320,56 @@ extern "C" int qvs_batch_optimise(qvs_batch_t b, double* gammas, double* ts, dou
   }
   return QVS_OK;
 }
+
+// Sec. 5 (benchmark with param_persist): a depth sweep of repeated optimisations of one instance.
+// Each depth is one batch of `repeats` parameter sets sharing the instance's qualities, optimised
+// together; the best optimum of a depth seeds the first layers of every repeat at the next depth.
+extern "C" int qvs_benchmark(int n, const float* q, int on_device, int d_min, int d_max, int repeats,
+                             const double* init, double gtol, int max_iter, double* f_out, double* best_theta,
+                             void* stream) {
+  if (!q || !init || !f_out || !best_theta || n < 12 || n > 28 || repeats < 1 || repeats > 65536 ||
+      d_min < 1 || d_max < d_min || d_max > bopt::NT / 2 || max_iter < 0 || !(gtol >= 0.0))
+    return QVS_EINVAL;
+  std::vector<double> best_g, best_t;   // best optimum of the previous depth
+  const double* next = init;
+  double* fo = f_out;
+  double* bo = best_theta;
+  for (int D = d_min; D <= d_max; ++D) {
+    std::vector<int32_t> ns(repeats, n), ps(repeats, D);
+    std::vector<double> g((size_t)repeats * D), t((size_t)repeats * D);
+    for (int r = 0; r < repeats; ++r) {
+      if (D == d_min) {   // repeat r: gamma_1..gamma_D then t_1..t_D
+        for (int k = 0; k < D; ++k) {
+          g[(size_t)r * D + k] = next[(size_t)r * 2 * D + k];
+          t[(size_t)r * D + k] = next[(size_t)r * 2 * D + D + k];
+        }
+      } else {            // persisted layers, then the repeat's own new layer
+        for (int k = 0; k < D - 1; ++k) {
+          g[(size_t)r * D + k] = best_g[k];
+          t[(size_t)r * D + k] = best_t[k];
+        }
+        g[(size_t)r * D + D - 1] = next[2 * (size_t)r];
+        t[(size_t)r * D + D - 1] = next[2 * (size_t)r + 1];
+      }
+    }
+    next += D == d_min ? (size_t)repeats * 2 * D : (size_t)repeats * 2;
+    qvs_batch_t b = nullptr;
+    QVS_TRY(qvs_batch_create(&b, repeats, ns.data(), ps.data(), stream));
+    int st = qvs_batch_set_quality_shared(b, q, on_device);
+    if (st == QVS_OK) st = qvs_batch_optimise(b, g.data(), t.data(), gtol, max_iter, fo, nullptr, nullptr, nullptr);
+    qvs_batch_destroy(b);
+    if (st != QVS_OK) return st;
+    int rb = 0;
+    for (int r = 1; r < repeats; ++r)
+      if (fo[r] < fo[rb]) rb = r;
+    best_g.assign(g.begin() + (size_t)rb * D, g.begin() + (size_t)rb * D + D);
+    best_t.assign(t.begin() + (size_t)rb * D, t.begin() + (size_t)rb * D + D);
+    for (int k = 0; k < D; ++k) {
+      bo[k] = best_g[k];
+      bo[D + k] = best_t[k];
+    }
+    fo += repeats;
+    bo += 2 * D;
+  }
+  return QVS_OK;
+}

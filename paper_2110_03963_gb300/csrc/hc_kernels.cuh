@@ -24,15 +24,19 @@ constexpr int NT = TILE / R;     // threads per CTA (256)
 //   L0: register bits {0, 9, 10, 11}, thread bits {1..8}   (global float4 loads/stores)
 //   L1: register bits {1, 2, 3, 4},   thread bits {0, 5..11}
 //   L2: register bits {5, 6, 7, 8},   thread bits {0..4, 9..11} (lanes = 32 consecutive j)
+//   L3: register bits {4, 9, 10, 11}, thread bits {0..3, 5..8} (lanes = two runs of 16 j)
+// L0, L1, L2 cover all twelve tile bits; L3 and L2 cover bits 4..11, all that a pass rotating only
+// the tile bits >= 4 needs, with one transpose between them instead of two.
 template <int L>
 __host__ __device__ __forceinline__ constexpr int tj(int r, int tid) {
   return L == 0 ? ((r & 1) | (tid << 1) | ((r >> 1) << 9))
        : L == 1 ? ((tid & 1) | (r << 1) | ((tid >> 1) << 5))
-                : ((tid & 31) | (r << 5) | ((tid >> 5) << 9));
+       : L == 2 ? ((tid & 31) | (r << 5) | ((tid >> 5) << 9))
+                : ((tid & 15) | ((r & 1) << 4) | ((tid >> 4) << 5) | ((r >> 1) << 9));
 }
 // tile bit carried by register bit i in layout L
 __host__ __device__ __forceinline__ constexpr int regbit(int L, int i) {
-  return L == 0 ? (i == 0 ? 0 : 8 + i) : (L == 1 ? 1 + i : 5 + i);
+  return L == 0 ? (i == 0 ? 0 : 8 + i) : (L == 1 ? 1 + i : (L == 2 ? 5 + i : (i == 0 ? 4 : 8 + i)));
 }
 // shared-memory slot of tile index j: two padding slots after every 32 amplitudes. The map is
 // additive over disjoint index bits, so a register's slot is the thread's base slot plus a
@@ -298,6 +302,25 @@ __device__ __forceinline__ void sget(C (&v)[R], const C* sm, int tid) {
   } else {
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = b[spos(tj<L>(r, 0))];
+  }
+}
+
+// read layout L from a dense shared copy of the tile (slot = tile index, no padding): L0 reads
+// 16-byte pairs at 16 (tid + 256 k) and L2 reads 8 bytes at 8 (lane + 32 (r + 16 warp)), so a warp's
+// accesses are contiguous and conflict-free
+template <int L, class C>
+__device__ __forceinline__ void dget(C (&v)[R], const C* st, int tid) {
+  const C* b = st + tj<L>(0, tid);
+  if constexpr (L == 0 && sizeof(C) == 8) {
+#pragma unroll
+    for (int r = 0; r < R; r += 2) {
+      const float4 w = *reinterpret_cast<const float4*>(b + tj<0>(r, 0));
+      *reinterpret_cast<float2*>(&v[r]) = make_float2(w.x, w.y);
+      *reinterpret_cast<float2*>(&v[r + 1]) = make_float2(w.z, w.w);
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = b[tj<L>(r, 0)];
   }
 }
 

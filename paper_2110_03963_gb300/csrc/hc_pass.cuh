@@ -272,9 +272,18 @@ __device__ __forceinline__ void qgen2(T (&qv)[R], const PassArgs<T>& a, const in
   }
 }
 
-template <class T, int SHAPE, int TH, bool ALT = false>
+struct NoHook {
+  __device__ void operator()() const {}
+};
+
+// STG: the tile's input vectors were landed densely in shared memory (stg: psi at [0, TILE), lambda
+// at [TILE, 2 TILE), index = tile index) by the staged persistent kernel; the transposes then go
+// through the single buffer sm, one vector at a time. Once every thread has read the stage (a
+// barrier after the loads), consumed() runs, which lands the next tile there.
+template <class T, int SHAPE, int TH, bool ALT = false, bool STG = false, class Fn = NoHook>
 __device__ __forceinline__ void run_pass(const PassArgs<T>& a, uint32_t bid, uint32_t nblk,
-                                         unsigned char* smem_raw) {
+                                         unsigned char* smem_raw, const typename Cx<T>::t* stg = nullptr,
+                                         Fn consumed = Fn{}) {
   constexpr int S = base_shape(SHAPE);
   constexpr bool EXG = SHAPE != S;
   using C = typename Cx<T>::t;
@@ -283,14 +292,27 @@ __device__ __forceinline__ void run_pass(const PassArgs<T>& a, uint32_t bid, uin
   constexpr int TAF = TH == TH_NONE ? 0 : TH;         // threshold of the "after" rotations
   auto x2 = [&](auto lf, auto lt, C(&p)[R], C(&l)[R]) {
     constexpr int LF = decltype(lf)::value, LT = decltype(lt)::value;
-    xchg2<LF, LT>(p, l, sm, threadIdx.x);
+    if constexpr (STG) {
+      xchg<LF, LT>(p, sm, threadIdx.x);
+      xchg<LF, LT>(l, sm, threadIdx.x);
+    } else {
+      xchg2<LF, LT>(p, l, sm, threadIdx.x);
+    }
   };
   using I0 = std::integral_constant<int, 0>;
   using I1 = std::integral_constant<int, 1>;
   using I2 = std::integral_constant<int, 2>;
-  auto ld = [&](auto li, C(&v)[R], const C* g, uint32_t off) {
+  // which: 0 = psi, 1 = lambda (the staged copy's half)
+  auto ld = [&](auto li, C(&v)[R], int which, const C* g, uint32_t off) {
     constexpr int L = decltype(li)::value;
-    gload<L>(v, g, off, a.tile);
+    if constexpr (STG) dget<L>(v, stg + which * TILE, threadIdx.x);
+    else gload<L>(v, g, off, a.tile);
+  };
+  auto loaded = [&]() {
+    if constexpr (STG) {
+      __syncthreads();
+      consumed();
+    }
   };
   const int tid = threadIdx.x;
   const uint32_t base = tile_base(a.tile, bid);
@@ -312,6 +334,24 @@ __device__ __forceinline__ void run_pass(const PassArgs<T>& a, uint32_t bid, uin
     }
     qload<2>(qv, a.q, off2, a.tile, a.qx);
   };
+  // the vector's loads can be issued early; the in-pass quadratic form needs its table row, which
+  // the first barrier publishes
+  auto qget_early = [&]() {
+    if constexpr (!ALT) {
+      if (a.qcta) return;
+    }
+    qload<2>(qv, a.q, off2, a.tile, a.qx);
+  };
+  auto qget_late = [&]() {
+    if constexpr (!ALT) {
+      if (a.qcta) qgen2<T>(qv, a, s_q, tid);
+    }
+  };
+  // Passes whose rotated tile bits all lie in 4..11 (TH >= 4: every tile type but the contiguous
+  // one) go through layouts L3 and L2 only: one transpose per direction instead of two.
+  constexpr bool TWO = TH >= 4 && TH < TB;
+  const uint32_t off3 = base + toff(a.tile, tj<3>(0, tid));
+  using I3 = std::integral_constant<int, 3>;
 
   // v <- (rho exp(-+i gamma q)) v on the amplitudes of layout 2 (dir = +1 forward, -1 adjoint)
   auto phase2 = [&](C (&v)[R], T dir, T rho) {
@@ -359,8 +399,20 @@ __device__ __forceinline__ void run_pass(const PassArgs<T>& a, uint32_t bid, uin
     xchg_alt<1, 0, 1, ALT>(v, sm, tid);
     rot_layout<0, TAF>(v, a.mask_aft, a.ta);
     gstore<0>(v, a.psi_out, off0, a.tile);
+  } else if constexpr (S == F1 && TWO) {
+    ld(I3{}, v, 0, a.psi_in, off3);
+    rot_layout<3, TBF>(v, a.mask_bef, a.tb);
+    qget_early();
+    xchg_alt<3, 2, 0, ALT>(v, sm, tid);
+    qget_late();
+    rot_layout<2, TBF>(v, a.mask_bef, a.tb);
+    phase2(v, T(1), a.rho_p);
+    rot_layout<2, TAF>(v, a.mask_aft, a.ta);
+    xchg_alt<2, 3, 1, ALT>(v, sm, tid);
+    rot_layout<3, TAF>(v, a.mask_aft, a.ta);
+    gstore<3>(v, a.psi_out, off3, a.tile);
   } else if constexpr (S == F1) {
-    ld(I0{}, v, a.psi_in, off0);
+    ld(I0{}, v, 0, a.psi_in, off0);
     rot_layout<0, TBF>(v, a.mask_bef, a.tb);
     xchg_alt<0, 1, 0, ALT>(v, sm, tid);
     rot_layout<1, TBF>(v, a.mask_bef, a.tb);
@@ -374,8 +426,14 @@ __device__ __forceinline__ void run_pass(const PassArgs<T>& a, uint32_t bid, uin
     xchg_alt<1, 0, 1, ALT>(v, sm, tid);
     rot_layout<0, TAF>(v, a.mask_aft, a.ta);
     gstore<0>(v, a.psi_out, off0, a.tile);
+  } else if constexpr (S == F2 && TWO) {
+    ld(I3{}, v, 0, a.psi_in, off3);
+    rot_layout<3, TBF>(v, a.mask_bef, a.tb);
+    xchg_alt<3, 2, 0, ALT>(v, sm, tid);
+    rot_layout<2, TBF>(v, a.mask_bef, a.tb);
+    gstore<2>(v, a.psi_out, off2, a.tile);
   } else if constexpr (S == F2) {
-    ld(I0{}, v, a.psi_in, off0);
+    ld(I0{}, v, 0, a.psi_in, off0);
     rot_layout<0, TBF>(v, a.mask_bef, a.tb);
     xchg_alt<0, 1, 0, ALT>(v, sm, tid);
     rot_layout<1, TBF>(v, a.mask_bef, a.tb);
@@ -383,14 +441,25 @@ __device__ __forceinline__ void run_pass(const PassArgs<T>& a, uint32_t bid, uin
     rot_layout<2, TBF>(v, a.mask_bef, a.tb);
     gstore<2>(v, a.psi_out, off2, a.tile);
   } else if constexpr (S == FE || S == FV) {
-    ld(I0{}, v, a.psi_in, off0);
-    rot_layout<0, TBF>(v, a.mask_bef, a.tb);
-    if constexpr (S == FV) xchg_alt<0, 1, 0, ALT>(v, sm, tid);
-    else xchg<0, 1>(v, sm, tid);   // FE's second half writes both buffers: keep the trailing barrier
-    rot_layout<1, TBF>(v, a.mask_bef, a.tb);
-    qget();
-    if constexpr (S == FV) xchg_alt<1, 2, 1, ALT>(v, sm, tid);
-    else xchg<1, 2>(v, sm, tid);
+    if constexpr (TWO) {
+      ld(I3{}, v, 0, a.psi_in, off3);
+      loaded();
+      rot_layout<3, TBF>(v, a.mask_bef, a.tb);
+      qget_early();
+      if constexpr (S == FV) xchg_alt<3, 2, 0, ALT>(v, sm, tid);
+      else xchg<3, 2>(v, sm, tid);   // FE's second half writes both buffers: keep the trailing barrier
+      qget_late();
+    } else {
+      ld(I0{}, v, 0, a.psi_in, off0);
+      loaded();
+      rot_layout<0, TBF>(v, a.mask_bef, a.tb);
+      if constexpr (S == FV) xchg_alt<0, 1, 0, ALT>(v, sm, tid);
+      else xchg<0, 1>(v, sm, tid);   // FE's second half writes both buffers: keep the trailing barrier
+      rot_layout<1, TBF>(v, a.mask_bef, a.tb);
+      qget();
+      if constexpr (S == FV) xchg_alt<1, 2, 1, ALT>(v, sm, tid);
+      else xchg<1, 2>(v, sm, tid);
+    }
     rot_layout<2, TBF>(v, a.mask_bef, a.tb);
     T e = T(0);
 #pragma unroll
@@ -406,23 +475,40 @@ __device__ __forceinline__ void run_pass(const PassArgs<T>& a, uint32_t bid, uin
       for (int r = 0; r < R; ++r) { l[r].x = qv[r] * v[r].x; l[r].y = qv[r] * v[r].y; }
       T acc = T(0), sc = a.sc_b;
       unrot_layout_acc<2, TBF>(v, l, a.mask_bef, a.tb, a.c2b, sc, acc);
-      x2(I2{}, I1{}, v, l);
-      unrot_layout_acc<1, TBF>(v, l, a.mask_bef, a.tb, a.c2b, sc, acc);
-      x2(I1{}, I0{}, v, l);
-      unrot_layout_acc<0, TBF>(v, l, a.mask_bef, a.tb, a.c2b, sc, acc);
-      gstore<0>(l, a.lam_out, off0, a.tile);
+      if constexpr (TWO) {
+        x2(I2{}, I3{}, v, l);
+        unrot_layout_acc<3, TBF>(v, l, a.mask_bef, a.tb, a.c2b, sc, acc);
+        gstore<3>(l, a.lam_out, off3, a.tile);
+      } else {
+        x2(I2{}, I1{}, v, l);
+        unrot_layout_acc<1, TBF>(v, l, a.mask_bef, a.tb, a.c2b, sc, acc);
+        x2(I1{}, I0{}, v, l);
+        unrot_layout_acc<0, TBF>(v, l, a.mask_bef, a.tb, a.c2b, sc, acc);
+        gstore<0>(l, a.lam_out, off0, a.tile);
+      }
       block_store3(e, T(2) * acc, T(0), a.part, a.row_E, a.row_bef, -1, tid, bid, nblk);
     }
   } else if constexpr (S == R1 || S == R0) {
     C l[R];
-    ld(I0{}, v, a.psi_in, off0);
-    ld(I0{}, l, a.lam_in, off0);
     T acc_a = T(0), acc_b = T(0), acc_g = T(0), sc = a.sc_a;
-    unrot_layout_acc<0, TAF>(v, l, a.mask_aft, a.ta, a.c2a, sc, acc_a);
-    x2(I0{}, I1{}, v, l);
-    unrot_layout_acc<1, TAF>(v, l, a.mask_aft, a.ta, a.c2a, sc, acc_a);
-    qget();
-    x2(I1{}, I2{}, v, l);
+    if constexpr (TWO) {
+      ld(I3{}, v, 0, a.psi_in, off3);
+      ld(I3{}, l, 1, a.lam_in, off3);
+      loaded();
+      unrot_layout_acc<3, TAF>(v, l, a.mask_aft, a.ta, a.c2a, sc, acc_a);
+      qget_early();
+      x2(I3{}, I2{}, v, l);
+      qget_late();
+    } else {
+      ld(I0{}, v, 0, a.psi_in, off0);
+      ld(I0{}, l, 1, a.lam_in, off0);
+      loaded();
+      unrot_layout_acc<0, TAF>(v, l, a.mask_aft, a.ta, a.c2a, sc, acc_a);
+      x2(I0{}, I1{}, v, l);
+      unrot_layout_acc<1, TAF>(v, l, a.mask_aft, a.ta, a.c2a, sc, acc_a);
+      qget();
+      x2(I1{}, I2{}, v, l);
+    }
     unrot_layout_acc<2, TAF>(v, l, a.mask_aft, a.ta, a.c2a, sc, acc_a);
 #pragma unroll
     for (int r = 0; r < R; ++r) acc_g += qv[r] * imdot_st(l[r], v[r]);
@@ -440,6 +526,34 @@ __device__ __forceinline__ void run_pass(const PassArgs<T>& a, uint32_t bid, uin
       phase2x2(v, l, T(-1));
       sc = a.sc_b;
       unrot_layout_acc<2, TBF>(v, l, a.mask_bef, a.tb, a.c2b, sc, acc_b);
+      if constexpr (TWO) {
+        x2(I2{}, I3{}, v, l);
+        unrot_layout_acc<3, TBF>(v, l, a.mask_bef, a.tb, a.c2b, sc, acc_b);
+        gstore<3>(l, a.lam_out, off3, a.tile);
+        if (a.psi_out) gstore<3>(v, a.psi_out, off3, a.tile);
+      } else {
+        x2(I2{}, I1{}, v, l);
+        unrot_layout_acc<1, TBF>(v, l, a.mask_bef, a.tb, a.c2b, sc, acc_b);
+        x2(I1{}, I0{}, v, l);
+        unrot_layout_acc<0, TBF>(v, l, a.mask_bef, a.tb, a.c2b, sc, acc_b);
+        gstore<0>(l, a.lam_out, off0, a.tile);
+        if (a.psi_out) gstore<0>(v, a.psi_out, off0, a.tile);
+      }
+    }
+    block_store3(T(2) * acc_b, T(2) * acc_a, T(2) * acc_g, a.part, a.row_bef, a.row_aft, a.row_gam, tid, bid, nblk);
+  } else if constexpr (S == R2) {
+    C l[R];
+    ld(I2{}, v, 0, a.psi_in, off2);
+    ld(I2{}, l, 1, a.lam_in, off2);
+    loaded();
+    T acc_b = T(0), sc = a.sc_b;
+    unrot_layout_acc<2, TBF>(v, l, a.mask_bef, a.tb, a.c2b, sc, acc_b);
+    if constexpr (TWO) {
+      x2(I2{}, I3{}, v, l);
+      unrot_layout_acc<3, TBF>(v, l, a.mask_bef, a.tb, a.c2b, sc, acc_b);
+      gstore<3>(l, a.lam_out, off3, a.tile);
+      if (a.psi_out) gstore<3>(v, a.psi_out, off3, a.tile);
+    } else {
       x2(I2{}, I1{}, v, l);
       unrot_layout_acc<1, TBF>(v, l, a.mask_bef, a.tb, a.c2b, sc, acc_b);
       x2(I1{}, I0{}, v, l);
@@ -447,19 +561,6 @@ __device__ __forceinline__ void run_pass(const PassArgs<T>& a, uint32_t bid, uin
       gstore<0>(l, a.lam_out, off0, a.tile);
       if (a.psi_out) gstore<0>(v, a.psi_out, off0, a.tile);
     }
-    block_store3(T(2) * acc_b, T(2) * acc_a, T(2) * acc_g, a.part, a.row_bef, a.row_aft, a.row_gam, tid, bid, nblk);
-  } else if constexpr (S == R2) {
-    C l[R];
-    ld(I2{}, v, a.psi_in, off2);
-    ld(I2{}, l, a.lam_in, off2);
-    T acc_b = T(0), sc = a.sc_b;
-    unrot_layout_acc<2, TBF>(v, l, a.mask_bef, a.tb, a.c2b, sc, acc_b);
-    x2(I2{}, I1{}, v, l);
-    unrot_layout_acc<1, TBF>(v, l, a.mask_bef, a.tb, a.c2b, sc, acc_b);
-    x2(I1{}, I0{}, v, l);
-    unrot_layout_acc<0, TBF>(v, l, a.mask_bef, a.tb, a.c2b, sc, acc_b);
-    gstore<0>(l, a.lam_out, off0, a.tile);
-    if (a.psi_out) gstore<0>(v, a.psi_out, off0, a.tile);
     block_store3(T(2) * acc_b, T(0), T(0), a.part, a.row_bef, -1, -1, tid, bid, nblk);
   }
 }

@@ -24,7 +24,10 @@
 #include <type_traits>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "hc_pass.cuh"
+#include "hc_staged.cuh"
 #include "hc_batch.h"
 
 namespace qvs {
@@ -297,13 +300,90 @@ static int launch_c64(int th, int shape, const PassArgs<float>& a, uint32_t grid
   }
 }
 
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime (no link to libcuda)
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+    else
+      (void)cudaGetLastError();
+  }
+  return fn;
+}
+
+// The tile box of tile geometry t over a 2^n-element vector (elem bytes per element): the packed
+// 5-d view (low chunk bits up to 8 | chunk bits 8..s-1 | middle non-tile bits | high tile bits |
+// top non-tile bits); a tile is {d0, d1, 1, d3, 1} at (0, 0, mid, 0, top).
+static int encode_tile_map(CUtensorMap* map, const void* base, int elem, const Tile& t, int n, int* mid_bits,
+                           int* top_bits) {
+  auto enc = tensor_map_encoder();
+  if (!enc) return QVS_EUNSUPPORTED;
+  const int s = __builtin_popcount(t.smask), hfirst = s + t.hshift, nh = TB - s;
+  const int top = n - hfirst - nh;
+  const cuuint64_t d0 = s > 8 ? 256u : (1u << s), d1 = s > 8 ? (1u << (s - 8)) : 1u;
+  cuuint64_t dims[5] = {d0, d1, (cuuint64_t)1 << (hfirst - s), (cuuint64_t)1 << nh, (cuuint64_t)1 << top};
+  cuuint64_t strides[4] = {d0 * elem, ((cuuint64_t)1 << s) * elem, ((cuuint64_t)1 << hfirst) * elem,
+                           ((cuuint64_t)1 << (hfirst + nh)) * elem};
+  cuuint32_t box[5] = {(cuuint32_t)d0, (cuuint32_t)d1, 1u, (cuuint32_t)1u << nh, 1u};
+  cuuint32_t es[5] = {1u, 1u, 1u, 1u, 1u};
+  const CUresult r =
+      enc(map, elem == 8 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, const_cast<void*>(base),
+          dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return QVS_ECUDA;
+  *mid_bits = hfirst - s;
+  *top_bits = top;
+  return QVS_OK;
+}
+
+static int launch_staged_c64(int th, int shape, const PassArgs<float>& a, const StageMaps& m, uint32_t ntiles,
+                             uint32_t grid, cudaStream_t st) {
+  switch (th) {
+#define QVS_HC_CASE(K) \
+    case K: return launch_staged<K>(shape, a, m, ntiles, grid, st);
+    QVS_HC_C64_THRESHOLDS(QVS_HC_CASE)
+#undef QVS_HC_CASE
+    default: return launch_staged<TH_RUNTIME>(shape, a, m, ntiles, grid, st);
+  }
+}
+
+// Which complex64 passes run staged (persistent CTAs, TMA-fed): the last forward pass FE, whose
+// single input vector leaves room for the stage beside two transpose buffers' worth of work (n=28:
+// 1.41 -> 1.17 ms per launch). The adjoint passes measured no faster staged (R2 1.474 vs 1.479 ms,
+// R1 2.215 vs 2.259 ms: their two vectors go through one transpose buffer one after the other), so
+// they keep one CTA per tile. Also needed: the option on, the tensor-map encoder available, and the
+// tile's high field within one box dimension (at most 256 elements: chunks of >= 4 bits, n <= 28).
+static bool use_staged(const qvs_ctx* h, int shape, const Tile& t) {
+  return h->staged && shape == FE && __builtin_popcount(t.smask) >= TB - 8 && tensor_map_encoder();
+}
+
 template <class T>
 static int launch_shape(qvs_ctx* h, int shape, const PassArgs<T>& a, uint32_t grid) {
   cudaEvent_t ev;
   QVS_TRY(prof_begin(h, &ev));
   if constexpr (sizeof(T) == 4) {
     const int th = shape >= R1X ? TH_RUNTIME : pass_threshold(shape, a.mask_bef, a.mask_aft);
-    QVS_TRY(launch_c64(th, shape, a, grid, h->stream));
+    if (use_staged(h, shape, a.tile)) {
+      StageMaps m;
+      memset(&m, 0, sizeof(m));
+      m.two = shape != FE;
+      QVS_TRY(encode_tile_map(&m.psi, a.psi_in, 8, a.tile, h->n, &m.mid_bits, &m.top_bits));
+      if (m.two) QVS_TRY(encode_tile_map(&m.lam, a.lam_in, 8, a.tile, h->n, &m.mid_bits, &m.top_bits));
+      m.qpf = shape != R2 && !a.qcta && a.q;
+      if (m.qpf) QVS_TRY(encode_tile_map(&m.q, a.q, 4, a.tile, h->n, &m.mid_bits, &m.top_bits));
+      m.err = h->flags.as<int>();
+      const uint32_t ctas = std::min<uint32_t>(grid, 2u * (uint32_t)h->sms);
+      QVS_TRY(launch_staged_c64(th, shape, a, m, grid, ctas, h->stream));
+    } else {
+      QVS_TRY(launch_c64(th, shape, a, grid, h->stream));
+    }
   } else {
     QVS_TRY((launch_pass<T, TH_RUNTIME>(shape, a, grid, h->stream)));
   }
@@ -653,6 +733,8 @@ static int run_tiled(qvs_ctx* h, int p, const double* gammas, const double* ts, 
   }
   QVS_CUDA_TRY(cudaMemcpyAsync(h->rowmap.ptr, rowmap.data(), sizeof(int) * rowmap.size(),
                                cudaMemcpyHostToDevice, h->stream));
+  QVS_TRY(h->flags.ensure(16));
+  QVS_CUDA_TRY(cudaMemsetAsync(h->flags.ptr, 0, 16, h->stream));
 
   const T amp = (T)(1.0 / sqrt((double)h->dim));
   const int n = h->n;
@@ -760,8 +842,11 @@ static int run_tiled(qvs_ctx* h, int p, const double* gammas, const double* ts, 
   QVS_TRY(ensure_host_res(h, p));
   QVS_CUDA_TRY(cudaMemcpyAsync(h->host_res, h->res.ptr, sizeof(double) * nout,
                                cudaMemcpyDeviceToHost, h->stream));
+  int* host_flag = reinterpret_cast<int*>(h->host_res + 1 + 2 * (size_t)h->host_res_cap);
+  QVS_CUDA_TRY(cudaMemcpyAsync(host_flag, h->flags.ptr, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   QVS_CUDA_TRY(cudaStreamSynchronize(h->stream));
   QVS_TRY(prof_flush(h));
+  if (*host_flag != 0) return QVS_ETIMEOUT;   // a staged pass gave up waiting for its tile copies
   *E = h->host_res[0];
   if (grad) {
     for (int k = 0; k < p; ++k) {

@@ -173,6 +173,8 @@ struct qvs_ctx {
   qvs::DevBuf res;          // double[1 + 2p] final reductions
   qvs::DevBuf rowmap;       // int[...] reduction row map
   qvs::DevBuf work;         // mixer-specific scratch
+  qvs::DevBuf flags;        // int error flags written by bounded device waits
+  bool staged = true;       // QVS_OPT_STAGED
   double* host_res = nullptr;   // pinned, 1 + 2 * host_res_cap doubles
   int host_res_cap = 0;
 

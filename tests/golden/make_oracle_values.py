@@ -74,6 +74,7 @@ def _maxcut10():
 CASES = {
     "maxcut3_n10_p2": (8, _maxcut10, True),
     "batch_optimise_64": (9, None, None),
+    "benchmark_n12_d1_3": (10, None, None),
     "qwoa_n24_p3": (1, lambda: _qwoa(24, 3), True),
     "qwoa_n25_p2": (2, lambda: _qwoa(25, 2), True),
     "qwoa_n26_p6": (3, lambda: _qwoa(26, 6), True),
@@ -118,9 +119,40 @@ def run_optimise_case(name: str = "batch_optimise_64") -> str:
     return path
 
 
+def benchmark_inputs():
+    """Instance and start values of the depth-sweep case: 3-regular max-cut on 12 qubits, depths
+    1..3, 6 repeats; first-depth starts uniform on [0, pi], later new layers uniform on [0, pi]."""
+    inst = wl.maxcut3(12, 1, instance=7000)
+    rng = wl.rng_for(SAMPLE_SEED, 200)
+    repeats, d_min, d_max = 6, 1, 3
+    init = rng.uniform(0.0, np.pi, size=repeats * 2 * d_min + repeats * 2 * (d_max - d_min))
+    return inst.graph, d_min, d_max, repeats, init
+
+
+def run_benchmark_case(name: str = "benchmark_n12_d1_3") -> str:
+    t0 = time.time()
+    G, d_min, d_max, repeats, init = benchmark_inputs()
+    prob = orc.maxcut_problem(G.n, G.eu, G.ev)
+    f, best = orc.benchmark(prob, d_min, d_max, repeats, init, gtol=1e-8, max_iter=500)
+    out = {"what": "depth sweep with persisted parameters (Sec. 5 benchmark, param_persist): 3-regular max-cut "
+                   "workloads.maxcut3(12, 1, instance=7000).graph, integer qualities, D = 1..3, 6 repeats, "
+                   "oracle BFGS gtol 1e-8, start values from workloads.rng_for(301, 200)",
+           "written_by": "tests/golden/make_oracle_values.py (calls only oracle/ on workloads/ inputs)",
+           "init": [float(x) for x in init], "f": [[float(x) for x in row] for row in f],
+           "best": [[[float(x) for x in g], [float(x) for x in t]] for g, t in best],
+           "oracle_seconds": round(time.time() - t0, 1)}
+    path = os.path.join(HERE, f"oracle_{name}.json")
+    lines = [f"{json.dumps(k)}: {json.dumps(v, separators=(',', ':'))}" for k, v in out.items()]
+    with open(path, "w") as fh:
+        fh.write("{\n" + ",\n".join(lines) + "\n}\n")
+    return path
+
+
 def run_case(name: str) -> str:
     if name == "batch_optimise_64":
         return run_optimise_case(name)
+    if name == "benchmark_n12_d1_3":
+        return run_benchmark_case(name)
     number, build, with_grad = CASES[name]
     t0 = time.time()
     prob, gammas, ts, desc = build()

@@ -327,3 +327,29 @@ def test_full28_p8_gradient_vs_c128_central_fd(full28, qvs):
     rdt = np.array([fd(1, k) for k in range(8)])
     s128.close()
     assert rel_err_grad(dg, dt, rdg, rdt) < TOL_G
+
+
+@pytest.mark.parametrize("n,p", [(13, 3), (14, 2), (16, 4), (19, 3), (21, 2), (25, 2)])
+def test_staged_passes_bit_identical_to_per_tile(qvs, n, p):
+    """The TMA-staged persistent passes (QVS_OPT_STAGED = 1) read the same inputs from a shared
+    stage instead of global memory and do the same arithmetic, so objective and gradient equal the
+    one-CTA-per-tile kernels' bit for bit; covers chunk widths s = 11 (n = 13) down to s = 4 and
+    both frames (random t spans |tan t| > 1)."""
+    import torch
+    G = wl.gnp_graph(n, 0.5, wl.rng_for(260, n))
+    q = torch.empty(1 << n, dtype=torch.float32, device="cuda")
+    qvs.qvs_quality_maxcut(n, G.eu, G.ev, G.w, q, qvs.QVS_F32)
+    gs, ts = wl.thetas(p, wl.rng_for(261, n))
+    out = []
+    for staged in (0, 1):
+        sim = qvs.Simulator(1 << n, qvs.QVS_C64)
+        sim.set_quality(q).set_mixer(qvs.QVS_MIX_HYPERCUBE, qvs.hypercube_desc(n))
+        sim.set_option(qvs.QVS_OPT_STAGED, staged)
+        out.append(sim.gradient(gs, ts))
+        sim.close()
+    (E0, dg0, dt0), (E1, dg1, dt1) = out
+    assert E0 == E1 and np.array_equal(dg0, dg1) and np.array_equal(dt0, dt1)
+    prob = orc.maxcut_problem(n, G.eu, G.ev, G.w, q_dtype=np.float32)
+    if n <= 21:
+        f, rdg, rdt = orc.gradient(prob, gs, ts)
+        assert rel_err_E(E1, f) < TOL_E and rel_err_grad(dg1, dt1, rdg, rdt) < TOL_G

@@ -680,3 +680,30 @@ def test_optimise_qaoa_matches_scipy_bfgs_and_closed_form():
     gs2, ts2, f2, _, _, _ = orc.optimise(prob, np.array([best[1]]), np.array([best[2]]), gtol=1e-10)
     assert f2 <= best[0] + 1e-12
     assert abs(cf.p1_maxcut_expectation(n, G.eu, G.ev, None, gs2[0], ts2[0]) - f2) < 1e-10
+
+
+def test_benchmark_depth_sweep_with_persisted_parameters():
+    """Sec. 5 benchmark with param_persist: one depth and one repeat is exactly `optimise`; and when
+    every new layer starts at gamma = t = 0 (an identity layer), each repeat at depth D + 1 starts
+    at the best optimum of depth D, so the best objective never increases with depth."""
+    n = 8
+    G = wl.regular3_graph(n, wl.rng_for(203))
+    prob = orc.maxcut_problem(n, G.eu, G.ev)
+    g0, t0 = np.array([0.7]), np.array([0.3])
+    f, best = orc.benchmark(prob, 1, 1, 1, np.concatenate([g0, t0]), gtol=1e-9)
+    gs, ts, fo, _, _, _ = orc.optimise(prob, g0, t0, gtol=1e-9)
+    assert f.shape == (1, 1) and f[0, 0] == fo and np.array_equal(best[0][0], gs)
+    rng = wl.rng_for(204)
+    repeats = 3
+    init = np.concatenate([rng.uniform(0, np.pi, size=2 * repeats), np.zeros(2 * repeats * 2)])
+    f, best = orc.benchmark(prob, 1, 3, repeats, init, gtol=1e-9)
+    assert f.shape == (3, repeats)
+    for D in range(1, 3):
+        assert f[D].min() <= f[D - 1].min() + 1e-12
+        # the persisted start reproduces the previous depth's best objective exactly
+        g_start = np.append(best[D - 1][0], 0.0)
+        t_start = np.append(best[D - 1][1], 0.0)
+        assert abs(orc.objective(prob, g_start, t_start) - f[D - 1].min()) < 1e-12
+    for D, (g, t) in enumerate(best, start=1):
+        assert len(g) == len(t) == D
+        assert abs(orc.objective(prob, g, t) - f[D - 1].min()) < 1e-12

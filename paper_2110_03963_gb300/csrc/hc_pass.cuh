@@ -565,8 +565,17 @@ __device__ __forceinline__ void run_pass(const PassArgs<T>& a, uint32_t bid, uin
   }
 }
 
+// CTAs per SM the complex64 kernels are compiled for (register budget 65536 / (256 x CTAs)): the
+// single-vector passes 4 (64 registers); the last forward pass FE 3 (80 registers, no spills: at
+// n=28 1.41 -> 1.22 ms per launch); the adjoint passes 2 (128 registers: R2 at 3 spills and runs
+// 1.47 -> 1.72 ms, R1 and R0 spill more).
+template <class T, int SHAPE>
+__host__ __device__ constexpr int ctas_per_sm() {
+  return sizeof(T) == 8 ? 1 : (!two_vector(SHAPE) ? 4 : (SHAPE == FE ? 3 : 2));
+}
+
 template <class T, int SHAPE, int TH>
-__global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 1 : (two_vector(SHAPE) ? 2 : 4))
+__global__ void __launch_bounds__(NT, ctas_per_sm<T, SHAPE>())
 pass_kernel(const __grid_constant__ PassArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   run_pass<T, SHAPE, TH>(a, blockIdx.x, gridDim.x, smem_raw);

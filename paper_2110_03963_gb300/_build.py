@@ -17,8 +17,12 @@ LIB = os.path.join(PKG, "libqvs.so")
 ROOT = os.path.dirname(PKG)
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
-              "-I" + os.path.join(ROOT, "include")]
+# -ffp-contract=off: the host compiler rounds every product and sum separately on every machine
+# (gcc fuses multiply-adds on Arm by default, not on x86-64), so host-side fp64 arithmetic such as
+# the BFGS loop gives the same results on both and matches the device step kernel operation for
+# operation.
+NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+              "--expt-relaxed-constexpr", "-I" + os.path.join(ROOT, "include")]
 
 
 def nvcc() -> str:

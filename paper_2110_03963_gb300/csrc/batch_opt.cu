@@ -53,16 +53,6 @@ struct StepArgs {
   int max_iter;
 };
 
-__device__ __forceinline__ double block_sum(double v, double* red) {
-  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  double s = 0.0;
-  for (int w = 0; w < NT / 32; ++w) s += red[w];
-  return s;
-}
-
 __device__ __forceinline__ double block_max(double v, double* red) {
   for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
   __syncthreads();
@@ -73,6 +63,25 @@ __device__ __forceinline__ double block_max(double v, double* red) {
   return s;
 }
 
+// The step's fp64 arithmetic is the host BFGS's (qvs_bfgs_minimize) operation for operation:
+// products and sums rounded separately (no fused multiply-add), dot products summed in index order
+// by one thread. Given the same objective values the two loops then take the same decisions.
+__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
+
+// sum_k a[k] b[k] in index order, by thread 0, broadcast through shared memory
+__device__ __forceinline__ double ordered_dot(const double* a, const double* b, int m, double* bcast) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double acc = 0.0;
+    for (int k = 0; k < m; ++k) acc = dadd(acc, dmul(a[k], b[k]));
+    *bcast = acc;
+  }
+  __syncthreads();
+  return *bcast;
+}
+
 // theta component j of an instance: gamma_{j/2} (j even) or t_{j/2} (j odd)
 __device__ __forceinline__ double& theta_ref(const StepArgs& a, int th0, int j) {
   return (j & 1) ? a.ts[th0 + (j >> 1)] : a.gammas[th0 + (j >> 1)];
@@ -80,6 +89,8 @@ __device__ __forceinline__ double& theta_ref(const StepArgs& a, int th0, int j) 
 
 __global__ void __launch_bounds__(NT) bfgs_step_kernel(const __grid_constant__ StepArgs A) {
   __shared__ double red[NT / 32];
+  __shared__ double s_a[NT], s_b[NT], s_c[NT];
+  __shared__ double s_dot;
   const int i = blockIdx.x, j = threadIdx.x;
   State& S = A.st[i];
   if (S.stage == DONE) return;
@@ -113,26 +124,27 @@ __global__ void __launch_bounds__(NT) bfgs_step_kernel(const __grid_constant__ S
     }
   } else {   // TRIAL
     const double f0 = S.f, a = S.a, slope = S.slope;
-    if (fE <= f0 + kC1 * a * slope) {
+    if (fE <= dadd(f0, dmul(dmul(kC1, a), slope))) {
       // accept: s = x_t - x, y = g_t - g, inverse-Hessian update
-      const double s = own ? __dsub_rn(xt, x[j]) : 0.0;
-      const double y = own ? __dsub_rn(gt, g[j]) : 0.0;
-      const double ys = block_sum(y * s, red);
+      const double s = own ? dsub(xt, x[j]) : 0.0;
+      const double y = own ? dsub(gt, g[j]) : 0.0;
+      s_a[j] = y;
+      s_b[j] = s;
+      const double ys = ordered_dot(s_a, s_b, m, &s_dot);
       if (ys > 0.0) {
-        __shared__ double s_y[NT], s_s[NT], s_Hy[NT];
-        s_y[j] = y;
-        s_s[j] = s;
-        __syncthreads();
         double hy = 0.0;
         if (own)
-          for (int k = 0; k < m; ++k) hy += H[(size_t)j * m + k] * s_y[k];
-        s_Hy[j] = own ? hy : 0.0;
-        const double yHy = block_sum(own ? y * hy : 0.0, red);
+          for (int k = 0; k < m; ++k) hy = dadd(hy, dmul(H[(size_t)j * m + k], s_a[k]));
+        s_c[j] = hy;
+        const double yHy = ordered_dot(s_a, s_c, m, &s_dot);
         const double rho = 1.0 / ys;
-        const double cs = rho * rho * yHy + rho;
+        const double cs = dadd(dmul(dmul(rho, rho), yHy), rho);
         if (own)
-          for (int k = 0; k < m; ++k)
-            H[(size_t)j * m + k] += -rho * (s_s[j] * s_Hy[k] + s_Hy[j] * s_s[k]) + cs * s_s[j] * s_s[k];
+          for (int k = 0; k < m; ++k) {
+            const double t1 = dadd(dmul(s_b[j], s_c[k]), dmul(s_c[j], s_b[k]));
+            const double t2 = dadd(dmul(-rho, t1), dmul(dmul(cs, s_b[j]), s_b[k]));
+            H[(size_t)j * m + k] = dadd(H[(size_t)j * m + k], t2);
+          }
       }
       if (own) {
         x[j] = xt;
@@ -159,30 +171,29 @@ __global__ void __launch_bounds__(NT) bfgs_step_kernel(const __grid_constant__ S
           S.a = a * 0.5;
         }
         __syncthreads();
-        if (own) theta_ref(A, S.th0, j) = __dadd_rn(x[j], __dmul_rn(S.a, d[j]));
+        if (own) theta_ref(A, S.th0, j) = dadd(x[j], dmul(S.a, d[j]));
       }
     }
     if (j == 0) S.evals += 1;
   }
   __syncthreads();
   if (direction) {
-    __shared__ double s_g[NT];
-    s_g[j] = own ? g[j] : 0.0;
+    s_a[j] = own ? g[j] : 0.0;
     __syncthreads();
-    double dj = 0.0;
+    double acc = 0.0;
     if (own)
-      for (int k = 0; k < m; ++k) dj -= H[(size_t)j * m + k] * s_g[k];
-    double slope = block_sum(own ? s_g[j] * dj : 0.0, red);
+      for (int k = 0; k < m; ++k) acc = dadd(acc, dmul(H[(size_t)j * m + k], s_a[k]));
+    s_b[j] = -acc;
+    double slope = ordered_dot(s_a, s_b, m, &s_dot);
     if (slope >= 0.0) {   // not a descent direction: restart from steepest descent
-      if (own) {
+      if (own)
         for (int k = 0; k < m; ++k) H[(size_t)j * m + k] = (k == j) ? 1.0 : 0.0;
-        dj = -s_g[j];
-      }
-      slope = block_sum(own ? s_g[j] * dj : 0.0, red);
+      s_b[j] = -s_a[j];
+      slope = ordered_dot(s_a, s_b, m, &s_dot);
     }
     if (own) {
-      d[j] = dj;
-      theta_ref(A, S.th0, j) = __dadd_rn(x[j], dj);   // a = 1
+      d[j] = s_b[j];
+      theta_ref(A, S.th0, j) = dadd(x[j], dmul(1.0, s_b[j]));   // a = 1
     }
     if (j == 0) {
       S.slope = slope;

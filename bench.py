@@ -551,6 +551,19 @@ def _extra_qaoaz(qvs, torch, stream, peak, steps, warmup, n, p):
     out[f"qaoaz_csr_n{n}_k{n // 2}_p{p}"] = {"value": units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
                                              "launches_per_step": sim.launches(), "roofline": roof, "kernels": ker,
                                              "nnz": int(colind.shape[0])}
+    E_csr = sim.gradient(inst.gammas, inst.ts)[0]
+    sim.close()
+    # the same ring without the stored matrix: neighbour ranks generated from each row's state bits
+    sim = qvs.Simulator(dim, qvs.QVS_C64, stream)
+    sim.set_quality(q).set_mixer(qvs.QVS_MIX_XY_RING, qvs.xy_ring_desc(n, n // 2))
+    ms = _time_steps(torch, stream, lambda: sim.gradient(inst.gammas, inst.ts), max(2, steps // 2), 2)
+    sim.set_option(qvs.QVS_OPT_PROFILE, 1)
+    E_xy = sim.gradient(inst.gammas, inst.ts)[0]
+    roof, ker = _kernel_summary(qvs, sim.h, peak, 1)
+    out[f"qaoaz_xy_ring_matrix_free_n{n}_k{n // 2}_p{p}"] = {
+        "value": units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "launches_per_step": sim.launches(),
+        "roofline": roof, "kernels": ker, "rel_diff_E_vs_csr": abs(E_xy - E_csr) / abs(E_csr),
+        "note": "QVS_MIX_XY_RING: the config's XY ring applied without the CSR arrays"}
     sim.close()
     return out
 

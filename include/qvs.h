@@ -57,7 +57,7 @@ enum { QVS_I32 = 1, QVS_F32 = 2, QVS_F64 = 3 };
 /* initial-state kinds of qvs_set_initial_state */
 enum { QVS_INIT_UNIFORM = 0, QVS_INIT_EXPLICIT = 1 };
 /* mixer kinds (paper Sec. 3: sparse, circulant, and the QAOA hypercube) */
-enum { QVS_MIX_HYPERCUBE = 1, QVS_MIX_CIRCULANT = 2, QVS_MIX_CSR = 3, QVS_MIX_PARITY = 4 };
+enum { QVS_MIX_HYPERCUBE = 1, QVS_MIX_CIRCULANT = 2, QVS_MIX_CSR = 3, QVS_MIX_PARITY = 4, QVS_MIX_XY_RING = 5 };
 /* options for qvs_set_option */
 enum {
   QVS_OPT_CKPT_LAYERS = 1,  /* adjoint: store the forward state every this many layers and
@@ -94,6 +94,12 @@ enum {
  *     (1-indexed positions k) B_odd couples (k, k+1) for odd k, B_even (k, k+1) for even k plus
  *     the closing pair (N, 1) when N is even, B_last the closing pair when N is odd; each coupling
  *     is X X + Y Y; one t per layer. Reads n_qubits only.
+ * QVS_MIX_XY_RING (Sec. 2.4.1): the XY ring sum_a (X_a X_{a+1} + Y_a Y_{a+1}) (a+1 mod n) on the
+ *     basis states of n_qubits qubits with hamming_weight ones (2 <= n <= 31, 1 <= k < n), in
+ *     increasing integer order: the operator qvs_xy_ring_csr writes as CSR, applied without it (each
+ *     row's neighbours are ranked from its state bits on the device). dim must equal C(n, k);
+ *     complex64. spec_lo/spec_hi and cheb_tol as for QVS_MIX_CSR; the Gershgorin bound used to cap
+ *     the estimated interval is 2 min(n, 2 min(k, n - k)).
  */
 typedef struct {
   int n_qubits;
@@ -108,6 +114,7 @@ typedef struct {
   int csr_on_device;
   double spec_lo, spec_hi;
   double cheb_tol;
+  int hamming_weight;   /* QVS_MIX_XY_RING */
 } qvs_mixer_desc;
 
 /* Sec. 5 (the plan/destroy life cycle of the Unitary table): create a handle for states of

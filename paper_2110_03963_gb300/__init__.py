@@ -25,7 +25,7 @@ QVS_OK, QVS_EINVAL, QVS_ENOMEM, QVS_ECUDA, QVS_ESTATE, QVS_ENUMERIC, QVS_ETIMEOU
 QVS_C64, QVS_C128 = 1, 2
 QVS_I32, QVS_F32, QVS_F64 = 1, 2, 3
 QVS_INIT_UNIFORM, QVS_INIT_EXPLICIT = 0, 1
-QVS_MIX_HYPERCUBE, QVS_MIX_CIRCULANT, QVS_MIX_CSR, QVS_MIX_PARITY = 1, 2, 3, 4
+QVS_MIX_HYPERCUBE, QVS_MIX_CIRCULANT, QVS_MIX_CSR, QVS_MIX_PARITY, QVS_MIX_XY_RING = 1, 2, 3, 4, 5
 QVS_OPT_CKPT_LAYERS = 1
 QVS_OPT_PROFILE = 2
 QVS_OPT_STAGED = 3
@@ -63,6 +63,7 @@ class MixerDesc(ctypes.Structure):
         ("spec_lo", ctypes.c_double),
         ("spec_hi", ctypes.c_double),
         ("cheb_tol", ctypes.c_double),
+        ("hamming_weight", ctypes.c_int),
     ]
 
 
@@ -648,6 +649,16 @@ def qvs_strerror(status: int) -> str:
 def parity_desc(n: int) -> MixerDesc:
     d = MixerDesc()
     d.n_qubits = n
+    return d
+
+
+def xy_ring_desc(n: int, k: int, spec=(0.0, 0.0), tol: float = 0.0) -> MixerDesc:
+    """The XY ring on the Hamming-weight-k states of n qubits, applied without a stored matrix."""
+    d = MixerDesc()
+    d.n_qubits = n
+    d.hamming_weight = k
+    d.spec_lo, d.spec_hi = spec
+    d.cheb_tol = tol
     return d
 
 

@@ -253,6 +253,8 @@ extern "C" int qvs_set_mixer(qvs_t h, int kind, const qvs_mixer_desc* d) {
     QVS_TRY(circ_set_mixer(h, d));
   } else if (kind == QVS_MIX_CSR) {
     QVS_TRY(csr_set_mixer(h, d));
+  } else if (kind == QVS_MIX_XY_RING) {
+    QVS_TRY(xy_set_mixer(h, d));
   } else if (kind == QVS_MIX_PARITY) {
     QVS_TRY(parity_set_mixer(h, d));
   } else {
@@ -319,7 +321,8 @@ extern "C" int qvs_evolve(qvs_t h, int p, const double* gammas, const double* ts
   switch (h->mixer) {
     case QVS_MIX_HYPERCUBE: return hc_evolve(h, p, gammas, ts);
     case QVS_MIX_CIRCULANT: return circ_evolve(h, p, gammas, ts);
-    case QVS_MIX_CSR: return csr_evolve(h, p, gammas, ts);
+    case QVS_MIX_CSR:
+    case QVS_MIX_XY_RING: return csr_evolve(h, p, gammas, ts);
     case QVS_MIX_PARITY: return parity_evolve(h, p, gammas, ts);
   }
   return QVS_ESTATE;
@@ -387,7 +390,8 @@ extern "C" int qvs_gradient(qvs_t h, int p, const double* gammas, const double* 
   switch (h->mixer) {
     case QVS_MIX_HYPERCUBE: return hc_gradient(h, p, gammas, ts, E, dgamma, dt);
     case QVS_MIX_CIRCULANT: return circ_gradient(h, p, gammas, ts, E, dgamma, dt);
-    case QVS_MIX_CSR: return csr_gradient(h, p, gammas, ts, E, dgamma, dt);
+    case QVS_MIX_CSR:
+    case QVS_MIX_XY_RING: return csr_gradient(h, p, gammas, ts, E, dgamma, dt);
     case QVS_MIX_PARITY: return parity_gradient(h, p, gammas, ts, E, dgamma, dt);
   }
   return QVS_ESTATE;

@@ -39,14 +39,23 @@ struct StepArgs {
   float implicit_value;
   float inv_b, a_over_b;      // W~ = W / b - a / b
   float alpha, beta;          // T_next = alpha W~ T_cur - beta T_prev
-  float2 c;                   // coefficient of T_next added to y
+  float2 c, c_lo;             // coefficient of T_next added to y: the fp64 value as hi + lo floats
   const float2* tcur;
   const float2* tprev;        // may be NULL when beta == 0
   float2* tnext;
   float2* y;                  // y += c * T_next
   int y_init;                 // 1: y = c0 * tcur + c * tnext (first term folded in)
-  float2 c0;
+  float2 c0, c0_lo;
 };
+
+// c * t for an fp64 coefficient carried as the float pair c_hi + c_lo (c_hi = float(c), c_lo =
+// float(c - c_hi): the coefficient to about 2^-48 relative): both products in fp32, summed, so
+// only the product is rounded to single precision, not the coefficient
+__device__ __forceinline__ float2 cmul_ff(float2 chi, float2 clo, float2 t) {
+  const float2 h = make_float2(fmaf(chi.x, t.x, -chi.y * t.y), fmaf(chi.x, t.y, chi.y * t.x));
+  const float2 l = make_float2(fmaf(clo.x, t.x, -clo.y * t.y), fmaf(clo.x, t.y, clo.y * t.x));
+  return make_float2(h.x + l.x, h.y + l.y);
+}
 
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
@@ -97,11 +106,129 @@ __device__ __forceinline__ float2 row_spmv(const uint32_t* __restrict__ rowptr, 
   return acc;
 }
 
-__global__ void __launch_bounds__(NT) cheb_step_kernel(const __grid_constant__ StepArgs a) {
+// The sparse operator W, applied one row at a time.
+//
+// CsrOp: an explicit CSR matrix (row_spmv above).
+// XyRingOp: the XY ring sum_a (X_a X_{a+1} + Y_a Y_{a+1}) (a + 1 mod n) on the n-bit basis states of
+// Hamming weight k in increasing order (the matrix qvs_xy_ring_csr writes), generated from the row's
+// state bits instead of read: (XX + YY) maps |01> to 2 |10> on a pair of differing bits, and the
+// rank of a weight-k state with set bits c_1 < ... < c_k in increasing order is sum_i C(c_i, i).
+// Moving the set bit at position b (p of the set bits lie below it) to the free position b + 1
+// changes the rank by +C(b, p) (Pascal's rule); moving it from b + 1 down to a free b changes it by
+// -C(b, p). The ring's closing pair (bits 0 and n-1) moves the lowest set bit to the top or the
+// highest to the bottom, which renumbers every set bit; that rank is summed afresh.
+struct CsrOp {
+  const uint32_t* rowptr;
+  const int32_t* colind;
+  const float* values;
+  float iv;
+  __device__ __forceinline__ float2 apply(const float2* __restrict__ x, int64_t row, int lane, bool valid) const {
+    return row_spmv(rowptr, colind, values, iv, x, row, lane, valid);
+  }
+  __device__ __forceinline__ double apply_d(const double* __restrict__ x, int64_t r) const {
+    double acc = 0.0;
+    for (uint32_t j = rowptr[r]; j < rowptr[r + 1]; ++j) acc += (double)(values ? values[j] : iv) * x[colind[j]];
+    return acc;
+  }
+};
+
+constexpr int XY_BW = 33;   // binomial table row width: C(b, j) at binom[b * XY_BW + j], b, j <= 32
+
+struct XyRingOp {
+  const uint32_t* states;   // basis state of each row
+  const int32_t* binom;     // C(b, j), b <= n, j <= k
+  int n, k;
+  __device__ __forceinline__ int32_t C(int b, int j) const { return __ldg(binom + b * XY_BW + j); }
+  // visit(neighbour row) for every nonzero of the row (all values 2)
+  // rank of the neighbour across the closing pair (bit 0, bit n - 1), which must differ
+  __device__ __forceinline__ int64_t wrap_rank(uint32_t s) const {
+    int64_t r = 0;
+    uint32_t t = s;
+    int i = 1;
+    if (s & 1u) {   // the lowest set bit (at 0) moves to n - 1 and becomes the k-th
+      t &= t - 1u;
+      i = 2;
+      while (t) {
+        const int c = __ffs(t) - 1;
+        t &= t - 1u;
+        r += C(c, i - 1);
+        ++i;
+      }
+      r += C(n - 1, k);
+    } else {        // the highest set bit (at n - 1) moves to 0 and becomes the first
+      while (i < k) {
+        const int c = __ffs(t) - 1;
+        t &= t - 1u;
+        r += C(c, i + 1);
+        ++i;
+      }
+    }
+    return r;
+  }
+  template <class F>
+  __device__ __forceinline__ void neighbours(uint32_t s, int64_t row, F&& visit) const {
+    uint32_t d = (s ^ (s >> 1)) & ((1u << (n - 1)) - 1u);   // bit b: bits b and b + 1 differ
+    while (d) {
+      const int b = __ffs(d) - 1;
+      d &= d - 1u;
+      const int32_t step = C(b, __popc(s & ((1u << b) - 1u)));
+      visit(((s >> b) & 1u) ? row + step : row - step);
+    }
+    if ((s ^ (s >> (n - 1))) & 1u) visit(wrap_rank(s));
+  }
+  // the same neighbours in groups of 8 adjacent pairs: each group's ranks first, then its gathers,
+  // so up to 8 loads are in flight instead of one per dependent step
+  __device__ __forceinline__ float2 gather_sum(const float2* __restrict__ x, uint32_t s, int64_t row) const {
+    float2 acc = make_float2(0.f, 0.f);
+    const uint32_t d = (s ^ (s >> 1)) & ((1u << (n - 1)) - 1u);
+#pragma unroll
+    for (int g = 0; g < 32; g += 8) {
+      if ((d >> g) == 0u) break;
+      int64_t nb[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int b = g + u;
+        const bool on = (d >> b) & 1u;
+        const int32_t step = on ? C(b, __popc(s & ((1u << b) - 1u))) : 0;
+        nb[u] = on ? (((s >> b) & 1u) ? row + step : row - step) : -1;
+      }
+      float2 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = nb[u] >= 0 ? __ldg(x + nb[u]) : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        acc.x += v[u].x;
+        acc.y += v[u].y;
+      }
+    }
+    if ((s ^ (s >> (n - 1))) & 1u) {
+      const float2 v = __ldg(x + wrap_rank(s));
+      acc.x += v.x;
+      acc.y += v.y;
+    }
+    return acc;
+  }
+  __device__ __forceinline__ float2 apply(const float2* __restrict__ x, int64_t row, int, bool valid) const {
+    if (!valid) return make_float2(0.f, 0.f);
+    const float2 acc = gather_sum(x, __ldg(states + row), row);
+    return make_float2(2.f * acc.x, 2.f * acc.y);
+  }
+  __device__ __forceinline__ double apply_d(const double* __restrict__ x, int64_t r) const {
+    double acc = 0.0;
+    neighbours(states[r], r, [&](int64_t nb) { acc += x[nb]; });
+    return 2.0 * acc;
+  }
+};
+
+// The operator is a __grid_constant__ parameter: read in place, not copied into registers (a copied
+// CSR operator doubled the step's registers to 64 and halved the rows in flight that bound it).
+template <class Op>
+__global__ void __launch_bounds__(NT) cheb_step_kernel(const __grid_constant__ StepArgs a,
+                                                       const __grid_constant__ Op op) {
   const int lane = threadIdx.x & (LPR - 1);
   const int64_t row = (int64_t)blockIdx.x * ROWS_PER_CTA + (threadIdx.x / LPR);
   const bool valid = row < a.dim;
-  const float2 wx = row_spmv(a.rowptr, a.colind, a.values, a.implicit_value, a.tcur, row, lane, valid);
+  const float2 wx = op.apply(a.tcur, row, lane, valid);
   if (lane != 0 || !valid) return;
   const float2 tc = a.tcur[row];
   // W~ x = (W x) / b - (a / b) x
@@ -113,9 +240,9 @@ __global__ void __launch_bounds__(NT) cheb_step_kernel(const __grid_constant__ S
     t.y -= a.beta * tp.y;
   }
   a.tnext[row] = t;
-  const float2 ct = cmulf(a.c, t);
+  const float2 ct = cmul_ff(a.c, a.c_lo, t);
   if (a.y_init) {
-    const float2 c0 = cmulf(a.c0, tc);
+    const float2 c0 = cmul_ff(a.c0, a.c0_lo, tc);
     a.y[row] = make_float2(c0.x + ct.x, c0.y + ct.y);
   } else {
     const float2 yo = a.y[row];
@@ -123,10 +250,11 @@ __global__ void __launch_bounds__(NT) cheb_step_kernel(const __grid_constant__ S
   }
 }
 
-// y = c0 * x (a single-term series, bt == 0)
-__global__ void scale_kernel(int64_t dim, float2 c0, const float2* __restrict__ x, float2* __restrict__ y) {
+// y = c0 * x (a single-term series, bt == 0); c0 as an fp64 value split into hi + lo floats
+__global__ void scale_kernel(int64_t dim, float2 c0, float2 c0_lo, const float2* __restrict__ x,
+                             float2* __restrict__ y) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < dim; i += (int64_t)gridDim.x * blockDim.x)
-    y[i] = cmulf(c0, x[i]);
+    y[i] = cmul_ff(c0, c0_lo, x[i]);
 }
 
 // fractional turns of gamma q (gamma / 2pi as float-float, q exact in fp32)
@@ -189,9 +317,8 @@ __global__ void __launch_bounds__(NT) ew_kernel(const __grid_constant__ EwArgs a
 }
 
 // df/dt partial: 2 Im sum_row conj(lambda_row) (W psi)_row
-__global__ void __launch_bounds__(NT) dt_kernel(int64_t dim, const uint32_t* __restrict__ rowptr,
-                                                const int32_t* __restrict__ colind, const float* __restrict__ values,
-                                                float iv, const float2* __restrict__ psi,
+template <class Op>
+__global__ void __launch_bounds__(NT) dt_kernel(int64_t dim, const __grid_constant__ Op op, const float2* __restrict__ psi,
                                                 const float2* __restrict__ lam, double* part, int prow,
                                                 int nchunks) {
   const int lane = threadIdx.x & (LPR - 1);
@@ -200,7 +327,7 @@ __global__ void __launch_bounds__(NT) dt_kernel(int64_t dim, const uint32_t* __r
   for (int chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
     const int64_t row = (int64_t)chunk * ROWS_PER_CTA + (threadIdx.x / LPR);
     const bool valid = row < dim;
-    const float2 wx = row_spmv(rowptr, colind, values, iv, psi, row, lane, valid);
+    const float2 wx = op.apply(psi, row, lane, valid);
     if (lane == 0 && valid) {
       const float2 l = lam[row];
       acc += l.x * wx.y - l.y * wx.x;
@@ -232,14 +359,11 @@ __global__ void rowptr32_kernel(int64_t n1, const int64_t* __restrict__ in, uint
 // lies from them. The interval used is the extreme Ritz values widened by those residuals and by 1 %
 // of the width, capped by the Gershgorin interval (which always encloses the spectrum).
 
-__global__ void lz_spmv_kernel(int64_t dim, const uint32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
-                               const float* __restrict__ values, float iv, const double* __restrict__ x,
+template <class Op>
+__global__ void lz_spmv_kernel(int64_t dim, const __grid_constant__ Op op, const double* __restrict__ x,
                                double* __restrict__ y) {
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < dim; r += (int64_t)gridDim.x * blockDim.x) {
-    double acc = 0.0;
-    for (uint32_t j = rowptr[r]; j < rowptr[r + 1]; ++j) acc += (double)(values ? values[j] : iv) * x[colind[j]];
-    y[r] = acc;
-  }
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < dim; r += (int64_t)gridDim.x * blockDim.x)
+    y[r] = op.apply_d(x, r);
 }
 
 __device__ __forceinline__ void lz_block_add(double v, double* out) {
@@ -345,6 +469,20 @@ static double tri_last_component(const std::vector<double>& al, const std::vecto
   return fabs(x[k - 1]);
 }
 
+static CsrOp make_csr_op(const CsrData& C) {
+  return CsrOp{C.rowptr.as<uint32_t>(), C.colind.as<int32_t>(), C.has_values ? C.values.as<float>() : nullptr,
+               C.implicit_value};
+}
+static XyRingOp make_xy_op(const CsrData& C) {
+  return XyRingOp{C.states.as<uint32_t>(), C.binom.as<int32_t>(), C.xy_n, C.xy_k};
+}
+// f(op) with the handle's operator type
+template <class F>
+static int with_op(const CsrData& C, F&& f) {
+  if (C.xy) return f(make_xy_op(C));
+  return f(make_csr_op(C));
+}
+
 static int lanczos_interval(qvs_ctx* h, int iters, double gersh, double* lo, double* hi) {
   const int64_t dim = h->dim;
   CsrData& C = h->csr;
@@ -358,7 +496,6 @@ static int lanczos_interval(qvs_ctx* h, int iters, double gersh, double* lo, dou
   double* vp = v + dim;
   double* w = vp + dim;
   double* sc = w + dim;   // two accumulators
-  const float* vals = C.has_values ? C.values.as<float>() : nullptr;
   cudaStream_t st = h->stream;
   auto scalar = [&](double* out) -> int {
     QVS_CUDA_TRY(cudaMemcpyAsync(out, sc, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -378,8 +515,10 @@ static int lanczos_interval(qvs_ctx* h, int iters, double gersh, double* lo, dou
   double beta = 0.0;
   const int kmax = (int)std::min<int64_t>(iters, dim);
   for (int j = 0; j < kmax; ++j) {
-    lz_spmv_kernel<<<RED_GRID, NT, 0, st>>>(dim, C.rowptr.as<uint32_t>(), C.colind.as<int32_t>(), vals,
-                                            C.implicit_value, v, w);
+    QVS_TRY(with_op(C, [&](auto op) -> int {
+      lz_spmv_kernel<<<RED_GRID, NT, 0, st>>>(dim, op, v, w);
+      return QVS_OK;
+    }));
     QVS_CUDA_TRY(cudaMemsetAsync(sc, 0, sizeof(double), st));
     lz_dot_kernel<<<RED_GRID, NT, 0, st>>>(dim, v, w, sc);
     QVS_CUDA_TRY(cudaGetLastError());
@@ -415,6 +554,13 @@ static int lanczos_interval(qvs_ctx* h, int iters, double gersh, double* lo, dou
 }
 
 // ---------------------------------------------------------------- host side
+
+// an fp64 complex value as hi + lo float pairs (hi = nearest float, lo = nearest float of the rest)
+static void split_ff(double re, double im, float2* hi, float2* lo) {
+  const float hr = (float)re, hi_ = (float)im;
+  *hi = make_float2(hr, hi_);
+  *lo = make_float2((float)(re - (double)hr), (float)(im - (double)hi_));
+}
 
 // Chebyshev coefficients c_m = (2 - delta_m0) (-i)^m J_m(b t) e^{-i t a}, cut where the tail bound
 // sum_{m > K} 2 |J_m(b t)| < tol. Returns K + 1 coefficients, or an empty vector if none fits.
@@ -472,18 +618,19 @@ static int expmv(qvs_ctx* h, double t, const float2* x, float2* y, float2* s0, f
   const int K = (int)(c.size() / 2) - 1;
   const uint32_t grid = (uint32_t)((dim + ROWS_PER_CTA - 1) / ROWS_PER_CTA);
   const double nnz = (double)C.nnz;
-  const double step_bytes = nnz * 4.0 + (C.has_values ? nnz * 4.0 : 0.0) + (double)dim * (4.0 + 8 + 8 + 8 + 16);
+  // compulsory bytes per series term: the operator's index data (the CSR arrays, or one state word
+  // per row), T_cur's own row, T_prev, T_next and y (the neighbour gathers of T_cur hit in L2)
+  const double step_bytes = C.xy ? (double)dim * (4.0 + 8 + 8 + 8 + 16)
+                                 : nnz * 4.0 + (C.has_values ? nnz * 4.0 : 0.0) + (double)dim * (4.0 + 8 + 8 + 8 + 16);
   if (K == 0) {
     return launch_prof(h, "csr_scale", 16.0 * dim, launches, [&] {
-      scale_kernel<<<RED_GRID, NT, 0, h->stream>>>(dim, make_float2((float)c[0], (float)c[1]), x, y);
+      float2 c0, c0_lo;
+      split_ff(c[0], c[1], &c0, &c0_lo);
+      scale_kernel<<<RED_GRID, NT, 0, h->stream>>>(dim, c0, c0_lo, x, y);
     });
   }
   StepArgs s{};
   s.dim = dim;
-  s.rowptr = C.rowptr.as<uint32_t>();
-  s.colind = C.colind.as<int32_t>();
-  s.values = C.has_values ? C.values.as<float>() : nullptr;
-  s.implicit_value = C.implicit_value;
   s.inv_b = (float)(1.0 / b);
   s.a_over_b = (float)(a / b);
   // T_0 = x, T_1 = W~ x, y = c0 T_0 + c1 T_1
@@ -499,11 +646,14 @@ static int expmv(qvs_ctx* h, double t, const float2* x, float2* y, float2* s0, f
     s.tprev = m == 1 ? nullptr : tprev;
     s.tnext = tnext;
     s.y = y;
-    s.c = make_float2((float)c[2 * m], (float)c[2 * m + 1]);
+    split_ff(c[2 * m], c[2 * m + 1], &s.c, &s.c_lo);
     s.y_init = m == 1 ? 1 : 0;
-    s.c0 = make_float2((float)c[0], (float)c[1]);
-    QVS_TRY(launch_prof(h, "csr_cheb_step", step_bytes, launches, [&] {
-      cheb_step_kernel<<<grid, NT, 0, h->stream>>>(s);
+    split_ff(c[0], c[1], &s.c0, &s.c0_lo);
+    QVS_TRY(launch_prof(h, C.xy ? "xy_cheb_step" : "csr_cheb_step", step_bytes, launches, [&] {
+      with_op(C, [&](auto op) -> int {
+        cheb_step_kernel<<<grid, NT, 0, h->stream>>>(s, op);
+        return QVS_OK;
+      });
     }));
     tprev = tcur;
     tcur = tnext;
@@ -590,10 +740,11 @@ static int run(qvs_ctx* h, int p, const double* gammas, const double* ts, bool g
     const int nchunks = (int)((dim + ROWS_PER_CTA - 1) / ROWS_PER_CTA);
     for (int k = p - 1; k >= 0; --k) {
       const float2* psik = psiK + (size_t)k * dim;
-      QVS_TRY(launch_prof(h, "csr_dt", (double)C.nnz * 4.0 + (double)dim * 20.0, launches, [&] {
-        dt_kernel<<<RED_GRID, NT, 0, h->stream>>>(dim, C.rowptr.as<uint32_t>(), C.colind.as<int32_t>(),
-                                                  C.has_values ? C.values.as<float>() : nullptr, C.implicit_value,
-                                                  psik, lam, h->part.as<double>(), 1 + p + k, nchunks);
+      QVS_TRY(launch_prof(h, "csr_dt", (C.xy ? 4.0 * dim : (double)C.nnz * 4.0) + (double)dim * 20.0, launches, [&] {
+        with_op(C, [&](auto op) -> int {
+          dt_kernel<<<RED_GRID, NT, 0, h->stream>>>(dim, op, psik, lam, h->part.as<double>(), 1 + p + k, nchunks);
+          return QVS_OK;
+        });
       }));
       QVS_TRY(expmv(h, -ts[k], lam, lam2, s0, s1, s2, launches));
       std::swap(lam, lam2);
@@ -635,6 +786,7 @@ int csr_set_mixer(qvs_ctx* h, const qvs_mixer_desc* d) {
   if (!d->rowptr || !d->colind || d->nnz < 0 || d->nnz >= (int64_t(1) << 32)) return QVS_EINVAL;
   if (!(d->cheb_tol >= 0.0) || !isfinite(d->spec_lo) || !isfinite(d->spec_hi)) return QVS_EINVAL;
   CsrData& C = h->csr;
+  C.xy = false;
   const int64_t nnz = d->nnz;
   const auto kind = d->csr_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   if (!d->csr_on_device) {
@@ -685,6 +837,56 @@ int csr_set_mixer(qvs_ctx* h, const qvs_mixer_desc* d) {
     C.spec_hi = d->spec_hi;
   }
   QVS_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return QVS_OK;
+}
+
+int xy_set_mixer(qvs_ctx* h, const qvs_mixer_desc* d) {
+  using namespace cs;
+  if (h->precision != QVS_C64) return QVS_EUNSUPPORTED;
+  const int n = d->n_qubits, k = d->hamming_weight;
+  if (n < 2 || n > 31 || k < 1 || k >= n) return QVS_EINVAL;
+  if (!(d->cheb_tol >= 0.0) || !isfinite(d->spec_lo) || !isfinite(d->spec_hi)) return QVS_EINVAL;
+  std::vector<int32_t> binom((size_t)XY_BW * XY_BW, 0);
+  for (int b = 0; b < XY_BW; ++b) {
+    binom[(size_t)b * XY_BW] = 1;
+    for (int j = 1; j <= b && j < XY_BW; ++j) {
+      const int64_t v = (int64_t)binom[(size_t)(b - 1) * XY_BW + j - 1] + (j < b ? binom[(size_t)(b - 1) * XY_BW + j] : 0);
+      binom[(size_t)b * XY_BW + j] = v > INT32_MAX ? INT32_MAX : (int32_t)v;   // only C(b, j), b <= 31 used
+    }
+  }
+  if ((int64_t)binom[(size_t)n * XY_BW + k] != h->dim) return QVS_EINVAL;
+  // the weight-k states in increasing order (next state with the same popcount: Gosper's rule)
+  std::vector<uint32_t> st((size_t)h->dim);
+  uint32_t x = (1u << k) - 1u;
+  for (int64_t r = 0; r < h->dim; ++r) {
+    st[(size_t)r] = x;
+    const uint32_t c = x & (0u - x), rr = x + c;
+    x = (((rr ^ x) >> 2) / c) | rr;
+  }
+  CsrData& C = h->csr;
+  QVS_TRY(C.states.ensure(sizeof(uint32_t) * st.size()));
+  QVS_TRY(C.binom.ensure(sizeof(int32_t) * binom.size()));
+  QVS_CUDA_TRY(cudaMemcpyAsync(C.states.ptr, st.data(), sizeof(uint32_t) * st.size(), cudaMemcpyHostToDevice,
+                               h->stream));
+  QVS_CUDA_TRY(cudaMemcpyAsync(C.binom.ptr, binom.data(), sizeof(int32_t) * binom.size(), cudaMemcpyHostToDevice,
+                               h->stream));
+  C.xy = true;
+  C.xy_n = n;
+  C.xy_k = k;
+  C.nnz = 0;
+  C.tol = d->cheb_tol > 0 ? d->cheb_tol : 1e-7;
+  if (d->spec_lo == 0.0 && d->spec_hi == 0.0) {
+    // Gershgorin: a row has at most min(n, 2 min(k, n - k)) differing ring pairs, each entry 2
+    const double G = 2.0 * std::min(n, 2 * std::min(k, n - k)) * (1.0 + 1e-12);
+    C.gersh = G;
+    QVS_TRY(lanczos_interval(h, 64, G, &C.spec_lo, &C.spec_hi));
+  } else {
+    if (!(d->spec_hi > d->spec_lo)) return QVS_EINVAL;
+    C.spec_lo = d->spec_lo;
+    C.spec_hi = d->spec_hi;
+  }
+  QVS_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  st.clear();
   return QVS_OK;
 }
 

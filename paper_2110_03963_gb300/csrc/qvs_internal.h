@@ -150,6 +150,11 @@ struct CsrData {
   float implicit_value = 0.f;
   double spec_lo = 0, spec_hi = 0, tol = 1e-7;
   double gersh = 0;         // Gershgorin radius (0 when the caller gave the interval)
+  // matrix-free XY ring on the Hamming-weight-k states of n qubits (QVS_MIX_XY_RING)
+  bool xy = false;
+  int xy_n = 0, xy_k = 0;
+  DevBuf states;            // uint32 basis state per row, increasing
+  DevBuf binom;             // int32 binomial table
 };
 
 }  // namespace qvs
@@ -247,6 +252,7 @@ int parity_gradient(qvs_ctx* h, int p, const double* gammas, const double* ts, d
 
 // CSR Chebyshev path: csr_cheb.cu
 int csr_set_mixer(qvs_ctx* h, const qvs_mixer_desc* d);
+int xy_set_mixer(qvs_ctx* h, const qvs_mixer_desc* d);
 int csr_evolve(qvs_ctx* h, int p, const double* gammas, const double* ts);
 int csr_gradient(qvs_ctx* h, int p, const double* gammas, const double* ts, double* E, double* dg,
                  double* dt);

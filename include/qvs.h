@@ -367,7 +367,8 @@ int qvs_benchmark(int n, const float* q, int on_device, int d_min, int d_max, in
  *                    the HBM roofline's numerator whether or not a pass hits in L2);
  *   fma_per_solve    fp32 fused multiply-adds of one solve (a model: 2 per amplitude, rotated bit
  *                    and vector, 2 more per amplitude and bit for the adjoint accumulations, about
- *                    8 per phase; the FP32-pipe roofline's numerator);
+ *                    8 per phase; passes on the contiguous tile type rotate all 12 tile bits, the
+ *                    others the 8 bits 4..11; the FP32-pipe roofline's numerator);
  *   amp_layers       sum over instances of 2^n p (the throughput unit);
  *   shared_quality   1 when every instance reads one shared quality vector. */
 typedef struct {

@@ -13,6 +13,7 @@ namespace hc {
 
 constexpr int TH_NONE = TB;   // no "before" rotations, all tile bits "after" (single-tile schedules)
 constexpr int TH_RUNTIME = -1;
+constexpr int TH_RUNTIME_HI = -2;   // runtime masks within tile bits 4..11: the two-layout form
 
 enum Shape : int {
   F0 = 0,   // first pass: psi0 (generated or loaded), phase, rotations ("after")
@@ -349,7 +350,7 @@ __device__ __forceinline__ void run_pass(const PassArgs<T>& a, uint32_t bid, uin
   };
   // Passes whose rotated tile bits all lie in 4..11 (TH >= 4: every tile type but the contiguous
   // one) go through layouts L3 and L2 only: one transpose per direction instead of two.
-  constexpr bool TWO = TH >= 4 && TH < TB;
+  constexpr bool TWO = (TH >= 4 && TH < TB) || TH == TH_RUNTIME_HI;
   const uint32_t off3 = base + toff(a.tile, tj<3>(0, tid));
   using I3 = std::integral_constant<int, 3>;
 

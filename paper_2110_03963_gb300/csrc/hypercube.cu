@@ -1062,30 +1062,32 @@ __host__ __device__ __forceinline__ void bpass_info(const BInst& I, int j, int& 
 
 // Cost model of one instance's solve in the batched kernel, per amplitude summed over its passes:
 // compulsory global-memory bytes (8 per complex64 vector read or written, 4 per quality read) and
-// fp32 fused multiply-adds. The runtime-mask kernels rotate all 12 tile bits of a layer (masked
-// bits with tangent 0): 2 FMAs per amplitude, bit and vector, plus 2 per amplitude and bit for the
-// adjoint accumulation; a phase costs about 8 (argument reduction and the complex product).
+// fp32 fused multiply-adds. A pass on the contiguous tile type rotates all 12 tile bits of a layer
+// (the runtime masks give the others tangent 0); the two-layout form of the high types rotates the
+// 8 bits 4..11. Each rotated bit costs 2 FMAs per amplitude and vector, plus 2 per amplitude for
+// the adjoint accumulation; a phase costs about 8 (argument reduction and the complex product).
 struct PassCost {
   double bytes, fma;
 };
 static PassCost batch_instance_cost(const BInst& I) {
   auto stored = [&](int j) { return j >= 1 && j <= I.F - 1 && j % I.ck_c == 0 && (j / I.ck_c) <= I.nck; };
   double bytes = 0.0, fma = 0.0;
+  auto bits = [&](int type) { return (I.gmask[type] & 0xFu) ? (double)TB : 8.0; };
   for (int j = 1; j <= I.F; ++j) {   // forward
     int type, shape, lb, la, lg;
     bpass_info(I, j, type, shape, lb, la, lg);
-    const double rot = 2.0 * TB * ((lb >= 0) + (la >= 0));
+    const double rot = 2.0 * bits(type) * ((lb >= 0) + (la >= 0));
     switch (shape) {
       case F0: bytes += 12; fma += rot + 8; break;
       case F1: bytes += 20; fma += rot + 8; break;
       case F2: bytes += 16; fma += rot; break;
-      case FE: bytes += 20; fma += (lb >= 0 ? 8.0 * TB : 0.0) + 4; break;   // rotate, E, lambda, undo
+      case FE: bytes += 20; fma += (lb >= 0 ? 8.0 * bits(type) : 0.0) + 4; break;   // rotate, E, lambda, undo
     }
   }
   for (int j = I.F - 1; j >= 1; --j) {   // adjoint
     int type, shape, lb, la, lg;
     bpass_info(I, j, type, shape, lb, la, lg);
-    const double unrot = 6.0 * TB * ((lb >= 0) + (la >= 0));
+    const double unrot = 6.0 * bits(type) * ((lb >= 0) + (la >= 0));
     const double psi_w = (j - 1 >= 1 && !stored(j - 1)) ? 8.0 : 0.0;
     switch (shape) {
       case F0: bytes += 20; fma += unrot + 4; break;                  // R0
@@ -1097,17 +1099,25 @@ static PassCost batch_instance_cost(const BInst& I) {
   return {bytes * dim, fma * dim};
 }
 
+template <int TH>
+__device__ __forceinline__ void run_shape_th(int shape, const PassArgs<float>& a, uint32_t t, uint32_t nt,
+                                             unsigned char* sm) {
+  switch (shape) {
+    case F0: run_pass<float, F0, TH, true>(a, t, nt, sm); break;
+    case F1: run_pass<float, F1, TH, true>(a, t, nt, sm); break;
+    case F2: run_pass<float, F2, TH, true>(a, t, nt, sm); break;
+    case FE: run_pass<float, FE, TH, true>(a, t, nt, sm); break;
+    case R1: run_pass<float, R1, TH, true>(a, t, nt, sm); break;
+    case R2: run_pass<float, R2, TH, true>(a, t, nt, sm); break;
+    case R0: run_pass<float, R0, TH, true>(a, t, nt, sm); break;
+  }
+}
+// a pass whose masks leave tile bits 0..3 alone (every high tile type of n <= 20) takes the
+// two-layout form: one transpose per direction, and no tangent-0 rotations of the low bits
 __device__ __forceinline__ void run_shape(int shape, const PassArgs<float>& a, uint32_t t, uint32_t nt,
                                           unsigned char* sm) {
-  switch (shape) {
-    case F0: run_pass<float, F0, TH_RUNTIME, true>(a, t, nt, sm); break;
-    case F1: run_pass<float, F1, TH_RUNTIME, true>(a, t, nt, sm); break;
-    case F2: run_pass<float, F2, TH_RUNTIME, true>(a, t, nt, sm); break;
-    case FE: run_pass<float, FE, TH_RUNTIME, true>(a, t, nt, sm); break;
-    case R1: run_pass<float, R1, TH_RUNTIME, true>(a, t, nt, sm); break;
-    case R2: run_pass<float, R2, TH_RUNTIME, true>(a, t, nt, sm); break;
-    case R0: run_pass<float, R0, TH_RUNTIME, true>(a, t, nt, sm); break;
-  }
+  if ((a.mask_bef | a.mask_aft) & 0xFu) run_shape_th<TH_RUNTIME>(shape, a, t, nt, sm);
+  else run_shape_th<TH_RUNTIME_HI>(shape, a, t, nt, sm);
 }
 
 __global__ void __launch_bounds__(NT, 2) batch_kernel(const __grid_constant__ BatchArgs a) {

@@ -346,6 +346,10 @@ def _kernel_summary(qvs, h, peak, nsteps):
 
 def run_extras(qvs, torch, stream, peak, steps, warmup, only=None, qwoa_n=26, qwoa_p=6, qaoaz_n=24, qaoaz_p=4,
                batch_count=4096, headline=None):
+    # the batched lines tune their schedule afresh (a schedule cache in the user's home directory
+    # from an earlier run on another GPU or build would otherwise be reused)
+    import tempfile
+    os.environ.setdefault("QVS_TUNE_CACHE", os.path.join(tempfile.mkdtemp(prefix="qvs_tune_"), "batch_tune.json"))
     """Objective + adjoint-gradient throughput of the QWOA circulant (N=2^26, p=6), QAOAz CSR
     (n=24, weight 12, p=4) and batched QAOA (4096 instances) workloads."""
     out = {}

@@ -359,9 +359,15 @@ int qvs_benchmark(int n, const float* q, int on_device, int d_min, int d_max, in
                   const double* init, double gtol, int max_iter, double* f_out, double* best_theta,
                   void* stream);
 
+/* Pin the batch's schedule instead of tuning it: ctas_per_sm 1 or 2 (0: let the autotuner choose
+ * on the next solve) and ckpt_policy 0 (forward states stored every ceil(sqrt(p)) layers,
+ * uncomputed in between) or 1 (every pass boundary stored). QVS_EINVAL for other values,
+ * QVS_ENOMEM when the policy's workspace cannot be allocated. */
+int qvs_batch_set_schedule(qvs_batch_t b, int ctas_per_sm, int ckpt_policy);
+
 /* What a batch does per solve (qvs_batch_info):
  *   ctas_per_sm      the autotuner's choice (0 before the first solve or optimisation);
- *   trial_ms[2]      its timed launches at 1 and 2 CTAs per SM;
+ *   trial_ms[2]      its timed launches at 1 and 2 CTAs per SM under checkpoint policy 0;
  *   bytes_per_solve  compulsory global-memory bytes of one solve, summed over every pass of every
  *                    instance (8 per complex64 vector element read or written, 4 per quality read;
  *                    the HBM roofline's numerator whether or not a pass hits in L2);
@@ -370,7 +376,15 @@ int qvs_benchmark(int n, const float* q, int on_device, int d_min, int d_max, in
  *                    8 per phase; passes on the contiguous tile type rotate all 12 tile bits, the
  *                    others the 8 bits 4..11; the FP32-pipe roofline's numerator);
  *   amp_layers       sum over instances of 2^n p (the throughput unit);
- *   shared_quality   1 when every instance reads one shared quality vector. */
+ *   shared_quality   1 when every instance reads one shared quality vector;
+ *   ckpt_policy      the autotuner's checkpoint policy: 0 = store the forward state every
+ *                    ceil(sqrt(p)) layers and uncompute in between, 1 = store every pass boundary
+ *                    (no uncompute, larger workspace);
+ *   from_cache       1 when the choice came from the schedule cache (no trial launches): a JSON
+ *                    file, QVS_TUNE_CACHE or else $HOME/.cache/qvs/batch_tune.json, keyed by GPU
+ *                    name, SM count, instance count and the (n, p) multiset;
+ *   trial_ms_all[4]  the timed candidates: policy 0 at 1 and 2 CTAs/SM, then policy 1 (0 = not
+ *                    timed). */
 typedef struct {
   int ctas_per_sm;
   int shared_quality;
@@ -378,6 +392,9 @@ typedef struct {
   double bytes_per_solve;
   double fma_per_solve;
   double amp_layers;
+  int ckpt_policy;
+  int from_cache;
+  double trial_ms_all[4];
 } qvs_batch_info_t;
 int qvs_batch_info(qvs_batch_t b, qvs_batch_info_t* info);
 int qvs_batch_destroy(qvs_batch_t b);

@@ -38,7 +38,7 @@ EXPORTED = [
     "qvs_batch_info", "qvs_batch_destroy", "qvs_gradient_small_noalloc", "qvs_strerror",
     "qvs_set_quality_qubo", "qvs_quality_qubo", "qvs_qubo_from_maxcut",
     "qvs_set_phase_terms", "qvs_evolve_ex", "qvs_gradient_ex", "qvs_bfgs_minimize", "qvs_optimise",
-    "qvs_batch_set_quality_shared", "qvs_batch_optimise", "qvs_benchmark",
+    "qvs_batch_set_quality_shared", "qvs_batch_optimise", "qvs_benchmark", "qvs_batch_set_schedule",
 ]
 
 
@@ -75,6 +75,9 @@ class BatchInfo(ctypes.Structure):
         ("bytes_per_solve", ctypes.c_double),
         ("fma_per_solve", ctypes.c_double),
         ("amp_layers", ctypes.c_double),
+        ("ckpt_policy", ctypes.c_int),
+        ("from_cache", ctypes.c_int),
+        ("trial_ms_all", ctypes.c_double * 4),
     ]
 
 
@@ -124,6 +127,7 @@ def load(path: str = LIB_PATH):
         "qvs_batch_optimise": (I, [V, P(D), P(D), D, I, P(D), P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int)]),
         "qvs_batch_gradient": (I, [V, P(D), P(D), P(D), P(D), P(D)]),
         "qvs_batch_info": (I, [V, P(BatchInfo)]),
+        "qvs_batch_set_schedule": (I, [V, I, I]),
         "qvs_batch_destroy": (I, [V]),
         "qvs_strerror": (ctypes.c_char_p, [I]),
         "qvs_set_quality_qubo": (I, [V, I, D, P(D), P(D)]),
@@ -585,7 +589,13 @@ def qvs_batch_info(b):
     _check(load().qvs_batch_info(b, ctypes.byref(info)), "qvs_batch_info")
     return {"ctas_per_sm": info.ctas_per_sm, "trial_ms": [info.trial_ms[0], info.trial_ms[1]],
             "bytes_per_solve": info.bytes_per_solve, "fma_per_solve": info.fma_per_solve,
-            "amp_layers": info.amp_layers, "shared_quality": bool(info.shared_quality)}
+            "amp_layers": info.amp_layers, "shared_quality": bool(info.shared_quality),
+            "ckpt_policy": info.ckpt_policy, "from_cache": bool(info.from_cache),
+            "trial_ms_all": [info.trial_ms_all[k] for k in range(4)]}
+
+
+def qvs_batch_set_schedule(b, ctas_per_sm: int, ckpt_policy: int):
+    _check(load().qvs_batch_set_schedule(b, int(ctas_per_sm), int(ckpt_policy)), "qvs_batch_set_schedule")
 
 
 def qvs_batch_destroy(b):
@@ -634,6 +644,10 @@ class Batch:
                                                    len(self.ns), gtol, max_iter)
         cut = lambda v: [v[self.poff[i]:self.poff[i + 1]] for i in range(len(self.ns))]
         return cut(g), cut(t), f, it, ev, stop
+
+    def set_schedule(self, ctas_per_sm: int, ckpt_policy: int):
+        qvs_batch_set_schedule(self.h, ctas_per_sm, ckpt_policy)
+        return self
 
     def info(self):
         return qvs_batch_info(self.h)

@@ -19,6 +19,10 @@
 
 #include <string.h>
 
+#include <stdio.h>
+#include <stdlib.h>
+#include <sys/stat.h>
+
 #include <algorithm>
 #include <new>
 #include <type_traits>
@@ -1254,37 +1258,165 @@ int batch_launch(qvs_batch_t b, int ctas_per_sm, const int* active) {
   return QVS_OK;
 }
 
+// Switch the batch to checkpoint policy pol: its instance table, slot size and workspace. The
+// captured graphs name the old workspace and slot size, so they are dropped.
+int batch_configure(qvs_batch_t b, int pol) {
+  const size_t ws_bytes = b->slot_bytes_pol[pol] * (size_t)b->nslots;
+  QVS_TRY(b->ws.ensure(ws_bytes));
+  QVS_CUDA_TRY(cudaMemcpyAsync(b->inst.ptr, b->host_inst[pol].data(), b->host_inst[pol].size(), cudaMemcpyHostToDevice,
+                               b->stream));
+  QVS_CUDA_TRY(cudaStreamSynchronize(b->stream));
+  b->ckpt_policy = pol;
+  b->slot_bytes = b->slot_bytes_pol[pol];
+  b->nck_max = b->nck_max_pol[pol];
+  b->model_bytes = b->model_bytes_pol[pol];
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->opt_graph) cudaGraphExecDestroy(b->opt_graph);
+  b->graph = nullptr;
+  b->opt_graph = nullptr;
+  return QVS_OK;
+}
+
+// ---- persistent cache of tuned schedules
+//
+// A JSON file (QVS_TUNE_CACHE, else $HOME/.cache/qvs/batch_tune.json) with one entry per line:
+//   {"key": "<gpu>|<sms>|<count>|<hash of the (n, p) multiset>", "ctas_per_sm": c, "ckpt_policy": k, "ms": t}
+// Unreadable or unwritable files are ignored (the batch is then tuned every time).
+static std::string tune_cache_path() {
+  if (const char* e = getenv("QVS_TUNE_CACHE")) return e;
+  const char* home = getenv("HOME");
+  if (!home) return "";
+  const std::string dir = std::string(home) + "/.cache/qvs";
+  mkdir((std::string(home) + "/.cache").c_str(), 0755);
+  mkdir(dir.c_str(), 0755);
+  return dir + "/batch_tune.json";
+}
+
+static std::string tune_key(qvs_batch_t b) {
+  std::vector<uint32_t> np(b->count);
+  for (int i = 0; i < b->count; ++i) np[i] = ((uint32_t)b->n[i] << 8) | (uint32_t)b->p[i];
+  std::sort(np.begin(), np.end());
+  uint64_t h = 1469598103934665603ull;   // FNV-1a over the sorted (n, p) pairs
+  for (uint32_t v : np)
+    for (int k = 0; k < 4; ++k) {
+      h ^= (v >> (8 * k)) & 0xFFu;
+      h *= 1099511628211ull;
+    }
+  std::string name = b->gpu_name;
+  for (char& c : name)
+    if (c == '"' || c == '|' || c == '\\') c = '_';
+  char buf[256];
+  snprintf(buf, sizeof(buf), "%s|%d|%d|%016llx", name.c_str(), b->sms, b->count, (unsigned long long)h);
+  return buf;
+}
+
+static std::vector<std::string> tune_cache_lines(const std::string& path) {
+  std::vector<std::string> out;
+  if (path.empty()) return out;
+  FILE* f = fopen(path.c_str(), "r");
+  if (!f) return out;
+  char line[1024];
+  while (fgets(line, sizeof(line), f)) {
+    std::string l(line);
+    if (l.find("{\"key\": \"") != std::string::npos) {
+      while (!l.empty() && (l.back() == '\n' || l.back() == ',' || l.back() == ' ')) l.pop_back();
+      out.push_back(l);
+    }
+  }
+  fclose(f);
+  return out;
+}
+
+static bool tune_cache_lookup(const std::string& key, int* ctas, int* pol) {
+  const std::string needle = "{\"key\": \"" + key + "\",";
+  for (const std::string& l : tune_cache_lines(tune_cache_path())) {
+    if (l.compare(0, needle.size(), needle) != 0) continue;
+    int c = 0, k = -1;
+    if (sscanf(l.c_str() + needle.size(), " \"ctas_per_sm\": %d, \"ckpt_policy\": %d", &c, &k) == 2 && c >= 1 &&
+        c <= 2 && (k == 0 || k == 1)) {
+      *ctas = c;
+      *pol = k;
+      return true;
+    }
+  }
+  return false;
+}
+
+static void tune_cache_store(const std::string& key, int ctas, int pol, double ms) {
+  const std::string path = tune_cache_path();
+  if (path.empty()) return;
+  std::vector<std::string> lines = tune_cache_lines(path);
+  const std::string needle = "{\"key\": \"" + key + "\",";
+  lines.erase(std::remove_if(lines.begin(), lines.end(),
+                             [&](const std::string& l) { return l.compare(0, needle.size(), needle) == 0; }),
+              lines.end());
+  char buf[512];
+  snprintf(buf, sizeof(buf), "{\"key\": \"%s\", \"ctas_per_sm\": %d, \"ckpt_policy\": %d, \"ms\": %.3f}", key.c_str(),
+           ctas, pol, ms);
+  lines.push_back(buf);
+  const std::string tmp = path + ".tmp";
+  FILE* f = fopen(tmp.c_str(), "w");
+  if (!f) return;
+  fputs("{\"batch_schedules\": [\n", f);
+  for (size_t i = 0; i < lines.size(); ++i) fprintf(f, "%s%s\n", lines[i].c_str(), i + 1 < lines.size() ? "," : "");
+  fputs("]}\n", f);
+  const bool ok = fclose(f) == 0;
+  if (ok) rename(tmp.c_str(), path.c_str());
+  else remove(tmp.c_str());
+}
+
+// Choose the schedule on the first solve: a cached choice for the same GPU and instance mix, else
+// one timed launch per candidate (CTAs per SM 1 or 2, checkpoint policy 0 or 1; a policy whose
+// workspace cannot be allocated is skipped), keeping the fastest. Needs b->theta set.
 int batch_autotune(qvs_batch_t b) {
   if (b->ctas_per_sm > 0) return QVS_OK;
-  // one timed launch per candidate occupancy, keep the fastest
+  const std::string key = tune_key(b);
+  int cc = 0, cp = 0;
+  if (tune_cache_lookup(key, &cc, &cp) && batch_configure(b, cp) == QVS_OK) {
+    b->ctas_per_sm = cc;
+    b->from_cache = true;
+    return QVS_OK;
+  }
+  (void)cudaGetLastError();
   cudaEvent_t e0, e1;
   QVS_CUDA_TRY(cudaEventCreate(&e0));
   QVS_CUDA_TRY(cudaEventCreate(&e1));
   double best = 1e30;
-  int choice = 1;
-  for (int c = 1; c <= 2; ++c) {
-    int st = QVS_OK;
-    if (cudaEventRecord(e0, b->stream) != cudaSuccess) st = QVS_ECUDA;
-    if (st == QVS_OK) st = batch_launch(b, c, nullptr);
-    if (st == QVS_OK && (cudaEventRecord(e1, b->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
-      st = QVS_ECUDA;
-    float ms = 0.f;
-    if (st == QVS_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) st = QVS_ECUDA;
-    if (st != QVS_OK) {
+  int choice = 1, choice_pol = 0;
+  for (int pol = 0; pol < 2; ++pol) {
+    if (batch_configure(b, pol) != QVS_OK) {   // e.g. the larger workspace does not fit
       (void)cudaGetLastError();
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
-      return st;
+      continue;
     }
-    b->tuned_ms[c] = ms;
-    if (ms < best) {
-      best = ms;
-      choice = c;
+    for (int c = 1; c <= 2; ++c) {
+      int st = QVS_OK;
+      if (cudaEventRecord(e0, b->stream) != cudaSuccess) st = QVS_ECUDA;
+      if (st == QVS_OK) st = batch_launch(b, c, nullptr);
+      if (st == QVS_OK && (cudaEventRecord(e1, b->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+        st = QVS_ECUDA;
+      float ms = 0.f;
+      if (st == QVS_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) st = QVS_ECUDA;
+      if (st != QVS_OK) {
+        (void)cudaGetLastError();
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return st;
+      }
+      b->trial_ms4[2 * pol + c - 1] = ms;
+      if (pol == 0) b->tuned_ms[c] = ms;
+      if (ms < best) {
+        best = ms;
+        choice = c;
+        choice_pol = pol;
+      }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (best >= 1e30) return QVS_ENOMEM;
+  QVS_TRY(batch_configure(b, choice_pol));
   b->ctas_per_sm = choice;
+  tune_cache_store(key, choice, choice_pol, best);
   return QVS_OK;
 }
 
@@ -1301,7 +1433,7 @@ extern "C" int qvs_batch_create(qvs_batch_t* out, int count, const int32_t* n_qu
   if (!b) return QVS_ENOMEM;
   b->count = count;
   b->stream = (cudaStream_t)stream;
-  std::vector<BInst> inst(count);
+  std::vector<BInst> inst(count), inst_all(count);   // checkpoint policies 0 and 1
   std::vector<double> cost(count);
   int64_t qtot = 0;
   int ptot = 0;
@@ -1337,12 +1469,18 @@ extern "C" int qvs_batch_create(qvs_batch_t* out, int count, const int32_t* n_qu
     b->p.push_back(p);
     b->th0.push_back(ptot);
     b->qoff.push_back(qtot);
+    BInst& A = inst_all[i];
+    A = I;
+    A.ck_c = 1;
+    A.nck = pl.F - 1;
     b->dim_max = std::max<int64_t>(b->dim_max, (int64_t)1 << n);
-    b->nck_max = std::max(b->nck_max, I.nck);
+    b->nck_max_pol[0] = std::max(b->nck_max_pol[0], I.nck);
+    b->nck_max_pol[1] = std::max(b->nck_max_pol[1], A.nck);
     max_rows_tiles = std::max(max_rows_tiles, (size_t)(3 * pl.F + 1) * I.ntiles);
     cost[i] = (double)((int64_t)1 << n) * (2 * pl.F - 1);
     const PassCost pc = batch_instance_cost(I);
-    b->model_bytes += pc.bytes;
+    b->model_bytes_pol[0] += pc.bytes;
+    b->model_bytes_pol[1] += batch_instance_cost(A).bytes;
     b->model_fma += pc.fma;
     b->amp_layers += (double)((int64_t)1 << n) * p;
     qtot += (int64_t)1 << n;
@@ -1361,9 +1499,20 @@ extern "C" int qvs_batch_create(qvs_batch_t* out, int count, const int32_t* n_qu
     return QVS_ECUDA;
   }
   b->sms = prop.multiProcessorCount;
+  b->gpu_name = prop.name;
   b->nslots = 2 * b->sms;
-  b->slot_bytes = (sizeof(float2) * (size_t)b->dim_max * (2 + b->nck_max) + sizeof(double) * max_rows_tiles + 255) &
-                  ~(size_t)255;
+  for (int pol = 0; pol < 2; ++pol) {
+    b->slot_bytes_pol[pol] =
+        (sizeof(float2) * (size_t)b->dim_max * (2 + b->nck_max_pol[pol]) + sizeof(double) * max_rows_tiles + 255) &
+        ~(size_t)255;
+    const std::vector<BInst>& src = pol ? inst_all : inst;
+    b->host_inst[pol].assign(reinterpret_cast<const unsigned char*>(src.data()),
+                             reinterpret_cast<const unsigned char*>(src.data() + count));
+  }
+  b->ckpt_policy = 0;
+  b->slot_bytes = b->slot_bytes_pol[0];
+  b->nck_max = b->nck_max_pol[0];
+  b->model_bytes = b->model_bytes_pol[0];
   int st = QVS_OK;
   if ((st = b->inst.ensure(sizeof(BInst) * count)) != QVS_OK || (st = b->order.ensure(sizeof(int) * count)) != QVS_OK ||
       (st = b->theta.ensure(sizeof(double) * 2 * (size_t)ptot)) != QVS_OK ||
@@ -1410,13 +1559,12 @@ static int batch_ensure_q(qvs_batch_t b, size_t bytes) {
 static int batch_set_qoffsets(qvs_batch_t b, bool shared) {
   using namespace qvs::hc;
   if (b->shared_q == shared && b->have_q) return QVS_OK;
-  std::vector<BInst> inst(b->count);
-  QVS_CUDA_TRY(cudaMemcpyAsync(inst.data(), b->inst.ptr, sizeof(BInst) * b->count, cudaMemcpyDeviceToHost,
-                               b->stream));
-  QVS_CUDA_TRY(cudaStreamSynchronize(b->stream));
-  for (int i = 0; i < b->count; ++i) inst[i].qoff = shared ? 0 : b->qoff[i];
-  QVS_CUDA_TRY(cudaMemcpyAsync(b->inst.ptr, inst.data(), sizeof(BInst) * b->count, cudaMemcpyHostToDevice,
-                               b->stream));
+  for (int pol = 0; pol < 2; ++pol) {
+    BInst* inst = reinterpret_cast<BInst*>(b->host_inst[pol].data());
+    for (int i = 0; i < b->count; ++i) inst[i].qoff = shared ? 0 : b->qoff[i];
+  }
+  QVS_CUDA_TRY(cudaMemcpyAsync(b->inst.ptr, b->host_inst[b->ckpt_policy].data(), sizeof(BInst) * b->count,
+                               cudaMemcpyHostToDevice, b->stream));
   QVS_CUDA_TRY(cudaStreamSynchronize(b->stream));
   b->shared_q = shared;
   return QVS_OK;
@@ -1493,12 +1641,23 @@ extern "C" int qvs_batch_gradient(qvs_batch_t b, const double* gammas, const dou
   return QVS_OK;
 }
 
+extern "C" int qvs_batch_set_schedule(qvs_batch_t b, int ctas_per_sm, int ckpt_policy) {
+  if (!b || ctas_per_sm < 0 || ctas_per_sm > 2 || (ckpt_policy != 0 && ckpt_policy != 1)) return QVS_EINVAL;
+  QVS_TRY(qvs::hc::batch_configure(b, ckpt_policy));
+  b->ctas_per_sm = ctas_per_sm;   // 0: the autotuner chooses again on the next solve
+  b->from_cache = false;
+  return QVS_OK;
+}
+
 extern "C" int qvs_batch_info(qvs_batch_t b, qvs_batch_info_t* info) {
   if (!b || !info) return QVS_EINVAL;
   memset(info, 0, sizeof(*info));
   info->ctas_per_sm = b->ctas_per_sm;
   info->trial_ms[0] = b->tuned_ms[1];
   info->trial_ms[1] = b->tuned_ms[2];
+  info->ckpt_policy = b->ckpt_policy;
+  info->from_cache = b->from_cache ? 1 : 0;
+  for (int k = 0; k < 4; ++k) info->trial_ms_all[k] = b->trial_ms4[k];
   info->bytes_per_solve = b->model_bytes;
   info->fma_per_solve = b->model_fma;
   info->amp_layers = b->amp_layers;

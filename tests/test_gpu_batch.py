@@ -87,3 +87,55 @@ def test_batch_4096_sampled_vs_oracle(qvs):
         assert rel_err_grad(dg[k], dt[k], dgs, dts) < TOL_G, k
         sim.close()
     b.close()
+
+
+@pytest.mark.parametrize("ctas,policy", [(1, 0), (2, 0), (1, 1), (2, 1)])
+def test_batch_every_schedule_vs_oracle(qvs, ctas, policy):
+    """Every schedule the autotuner can pick (1 or 2 CTAs per SM; forward states stored every
+    ceil(sqrt(p)) layers with uncompute between, or at every pass boundary) gives the oracle's
+    objective and gradient."""
+    ns = [12, 14, 16, 13, 18, 12, 15]
+    ps = [3, 5, 2, 8, 4, 1, 6]
+    b, insts, _ = _build_batch(qvs, ns, ps, seed=3)
+    b.set_schedule(ctas, policy)
+    E, dg, dt = b.gradient([i.gammas for i in insts], [i.ts for i in insts])
+    info = b.info()
+    assert info["ctas_per_sm"] == ctas and info["ckpt_policy"] == policy and not info["from_cache"]
+    for k, inst in enumerate(insts):
+        prob = orc.maxcut_problem(inst.graph.n, inst.graph.eu, inst.graph.ev)
+        f, rdg, rdt = orc.gradient(prob, inst.gammas, inst.ts)
+        assert rel_err_E(E[k], f) < TOL_E, k
+        assert rel_err_grad(dg[k], dt[k], rdg, rdt) < TOL_G, k
+    b.close()
+
+
+def test_batch_autotuner_and_schedule_cache(qvs, tmp_path, monkeypatch):
+    """The first batch of a mix times the candidates and records its choice in the cache file; a
+    second batch of the same (n, p) mix takes the choice from the cache without timing; a batch of
+    another mix is tuned afresh."""
+    import json
+    cache = tmp_path / "tune.json"
+    monkeypatch.setenv("QVS_TUNE_CACHE", str(cache))
+    ns, ps = [13, 16, 12, 15], [2, 3, 4, 2]
+    b1, insts, _ = _build_batch(qvs, ns, ps, seed=4)
+    b1.gradient([i.gammas for i in insts], [i.ts for i in insts])
+    i1 = b1.info()
+    assert not i1["from_cache"] and i1["ctas_per_sm"] in (1, 2) and i1["ckpt_policy"] in (0, 1)
+    assert sum(t > 0 for t in i1["trial_ms_all"]) >= 2
+    entries = json.loads(cache.read_text())["batch_schedules"]
+    assert len(entries) == 1
+    assert entries[0]["ctas_per_sm"] == i1["ctas_per_sm"] and entries[0]["ckpt_policy"] == i1["ckpt_policy"]
+    # the same multiset of (n, p) in another order
+    b2, insts2, _ = _build_batch(qvs, ns[::-1], ps[::-1], seed=5)
+    E2, _, _ = b2.gradient([i.gammas for i in insts2], [i.ts for i in insts2])
+    i2 = b2.info()
+    assert i2["from_cache"] and (i2["ctas_per_sm"], i2["ckpt_policy"]) == (i1["ctas_per_sm"], i1["ckpt_policy"])
+    assert i2["trial_ms_all"] == [0.0, 0.0, 0.0, 0.0]
+    prob = orc.maxcut_problem(insts2[0].graph.n, insts2[0].graph.eu, insts2[0].graph.ev)
+    assert rel_err_E(E2[0], orc.objective(prob, insts2[0].gammas, insts2[0].ts)) < TOL_E
+    b3, insts3, _ = _build_batch(qvs, [12, 12], [1, 2], seed=6)
+    b3.gradient([i.gammas for i in insts3], [i.ts for i in insts3])
+    assert not b3.info()["from_cache"]
+    assert len(json.loads(cache.read_text())["batch_schedules"]) == 2
+    for b in (b1, b2, b3):
+        b.close()

@@ -36,17 +36,25 @@ struct CircArgs {
   int row_a, row_b;
 };
 
-// thread-major private index of register r of thread tid in tile blk
-__device__ __forceinline__ size_t priv_idx(uint32_t blk, int r, int tid) {
-  return ((size_t)blk * R + r) * NT + tid;
+// Thread-major private arrays (q in column-pass order, the stored vectors, the eigenvalue table):
+// only these kernels read them, so they are interleaved by register pairs: registers 2m and 2m+1 of
+// a thread sit side by side (one float4 of a complex array, one float2 of q), so one access serves
+// two registers and a warp's access still covers consecutive bytes.
+__device__ __forceinline__ size_t pair_idx(uint32_t blk, int m, int tid) {   // units of the pair
+  return ((size_t)blk * (R / 2) + m) * NT + tid;
+}
+template <int C>
+__device__ __forceinline__ float2 half4(const float4& x) {
+  if constexpr (C == 0) return make_float2(x.x, x.y);
+  else return make_float2(x.z, x.w);
 }
 
 // Compiler fence after every 8th register of a per-register loop: the loads of the next group are
 // not hoisted above it, so at most 8 registers' side-vector loads (stored psi, q) are in flight at
 // once instead of all 32 competing with the 64 state registers for the 128 a thread has.
-template <int r>
+template <int r, int GROUP = 8>
 __device__ __forceinline__ void group_fence() {
-  if constexpr ((r & 7) == 7) asm volatile("" ::: "memory");
+  if constexpr ((r & (GROUP - 1)) == GROUP - 1) asm volatile("" ::: "memory");
 }
 
 // fractional turns of x * y for float-float x and y (|x y| well below 2^24)
@@ -83,7 +91,10 @@ __device__ __forceinline__ void block_store2(float a, float b, double scale, dou
 // copy the twiddle sub-tables into shared memory (after the exchange buffer)
 __device__ __forceinline__ const float2* load_twsub(float2* sm, const float2* __restrict__ g) {
   float2* ts = sm + SM_SLOTS;
-  for (int i = threadIdx.x; i < TW_SLOTS; i += blockDim.x) ts[i] = __ldg(g + i);
+  static_assert(SM_SLOTS % 2 == 0 && TW_SLOTS % 2 == 0, "paired copy");
+  const float4* g4 = reinterpret_cast<const float4*>(g);
+  float4* t4 = reinterpret_cast<float4*>(ts);
+  for (int i = threadIdx.x; i < TW_SLOTS / 2; i += blockDim.x) t4[i] = __ldg(g4 + i);
   __syncthreads();
   return ts;
 }
@@ -143,8 +154,15 @@ __global__ void __launch_bounds__(NT, 1) col_kernel(const __grid_constant__ Circ
   };
   // The side vectors never alias the stored-vector outputs: restrict-qualified copies let their
   // loads be issued ahead of the stores instead of one latency at a time.
-  const float* __restrict__ qT = a.qT;
-  auto qat = [&](int r) { return __ldcs(qT + priv_idx(blk, r, tid_fresh())); };
+  const float2* __restrict__ qT2 = reinterpret_cast<const float2*>(a.qT);
+  // q of register r: one 8-byte load per pair of registers (r a compile-time index, loops unrolled;
+  // 16-byte quads made the adjoint pass spill)
+  float2 q2;
+  auto qat = [&](auto ri) {
+    constexpr int r = decltype(ri)::value;
+    if constexpr ((r & 1) == 0) q2 = __ldcs(qT2 + pair_idx(blk, r >> 1, tid_fresh()));
+    return (r & 1) ? q2.y : q2.x;
+  };
   const float invL = 1.0f / (float)G::L;
 
   float2 v[R];
@@ -154,7 +172,7 @@ __global__ void __launch_bounds__(NT, 1) col_kernel(const __grid_constant__ Circ
       constexpr int r = decltype(ri)::value;
       float2 x = a.psi0 ? __ldg(a.psi0 + gidx(jt | G::jreg(2, r))) : make_float2(a.init_amp, 0.0f);
       float c, s;
-      phase_cs(r, qat(r), a.ph_hi, a.ph_lo, c, s);
+      phase_cs(r, qat(ri), a.ph_hi, a.ph_lo, c, s);
       v[r] = make_float2(c * x.x + s * x.y, c * x.y - s * x.x);
     });
     tile_fwd<G>(v, sm, ts, tid);
@@ -171,18 +189,19 @@ __global__ void __launch_bounds__(NT, 1) col_kernel(const __grid_constant__ Circ
     if constexpr (MODE == CM) {
 #pragma unroll
       for (int r = 0; r < R; ++r) v[r] = make_float2(v[r].x * invL, v[r].y * invL);
-      float2* __restrict__ po = a.priv_out;
+      float4* __restrict__ po = reinterpret_cast<float4*>(a.priv_out);
       if (po) {   // stored for the adjoint
 #pragma unroll
-        for (int r = 0; r < R; ++r) __stcs(po + priv_idx(blk, r, tid), v[r]);
+        for (int m = 0; m < R / 2; ++m)
+          __stcs(po + pair_idx(blk, m, tid), make_float4(v[2 * m].x, v[2 * m].y, v[2 * m + 1].x, v[2 * m + 1].y));
       }
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
+      static_for<R>([&](auto ri) {
+        constexpr int r = decltype(ri)::value;
         const float2 x = v[r];
         float c, s;
-        phase_cs(r, qat(r), a.ph_hi, a.ph_lo, c, s);
+        phase_cs(r, qat(ri), a.ph_hi, a.ph_lo, c, s);
         v[r] = make_float2(c * x.x + s * x.y, c * x.y - s * x.x);
-      }
+      });
       tile_fwd<G>(v, sm, ts, tid);
       gtw(v, false);
       gstore0(v, a.out);
@@ -193,34 +212,43 @@ __global__ void __launch_bounds__(NT, 1) col_kernel(const __grid_constant__ Circ
         static_for<R>([&](auto ri) {
           constexpr int r = decltype(ri)::value;
           const float2 x = make_float2(v[r].x * invL, v[r].y * invL);
-          e += qat(r) * (x.x * x.x + x.y * x.y);
+          e += qat(ri) * (x.x * x.x + x.y * x.y);
           __stcs(a.out + gidx(jt | G::jreg(2, r)), x);
         });
       } else {
         static_for<R>([&](auto ri) {
           constexpr int r = decltype(ri)::value;
-          const float q = qat(r);
+          const float q = qat(ri);
           const float2 x = make_float2(v[r].x * invL, v[r].y * invL);
           e += q * (x.x * x.x + x.y * x.y);
           v[r] = make_float2(q * x.x, q * x.y);
           group_fence<r>();
         });
-        __syncthreads();
+        // the objective is reduced before the forward transform (its barrier also separates the
+        // two in the schedule), so neither the sum nor its row and output pointers stay live
+        // across the transform
+        block_store2(e, 0.0f, 1.0, a.part, a.row_a, -1);
         tile_fwd<G>(v, sm, ts, tid);
         gtw(v, false);
         gstore0(v, a.out);
+        return;
       }
       block_store2(e, 0.0f, 1.0, a.part, a.row_a, -1);
     } else {   // RCM, RCF: v = lambda' after the adjoint mixer; gamma gradient, then phase^dagger
-      const float2* __restrict__ pin = a.priv_in;
+      const float4* __restrict__ pin = reinterpret_cast<const float4*>(a.priv_in);
       float g = 0.0f;
       const int jt = G::template jthr<2>(tid);
+      float4 ps4;
       static_for<R>([&](auto ri) {
         constexpr int r = decltype(ri)::value;
         float2 ps;
-        if constexpr (MODE == RCM) ps = __ldcs(pin + priv_idx(blk, r, tid));
-        else ps = a.psi0 ? __ldg(a.psi0 + gidx(jt | G::jreg(2, r))) : make_float2(a.init_amp, 0.0f);
-        const float q = qat(r);
+        if constexpr (MODE == RCM) {
+          if constexpr ((r & 1) == 0) ps4 = __ldcs(pin + pair_idx(blk, r >> 1, tid));
+          ps = half4<r & 1>(ps4);
+        } else {
+          ps = a.psi0 ? __ldg(a.psi0 + gidx(jt | G::jreg(2, r))) : make_float2(a.init_amp, 0.0f);
+        }
+        const float q = qat(ri);
         float c, s;
         phase_cs(r, q, a.ph2_hi, a.ph2_lo, c, s);
         const float2 phi = make_float2(c * ps.x + s * ps.y, c * ps.y - s * ps.x);   // P psi
@@ -229,13 +257,13 @@ __global__ void __launch_bounds__(NT, 1) col_kernel(const __grid_constant__ Circ
         v[r] = make_float2(c * l.x - s * l.y, c * l.y + s * l.x);                   // P^dagger lambda'
         group_fence<r>();
       });
+      // gamma-gradient row reduced before the forward transform (see the last pass above)
+      block_store2(g, 0.0f, 2.0, a.part, a.row_a, -1);
       if constexpr (MODE == RCM) {
-        __syncthreads();
         tile_fwd<G>(v, sm, ts, tid);
         gtw(v, false);
         gstore0(v, a.out);
       }
-      block_store2(g, 0.0f, 2.0, a.part, a.row_a, -1);
     }
   }
 }
@@ -262,27 +290,31 @@ __global__ void __launch_bounds__(NT, 1) row_kernel(const __grid_constant__ Circ
   }
   tile_fwd<G>(v, sm, ts, tid);
   // restrict-qualified: the table and stored-vector loads are issued ahead of the stores
-  const float2* __restrict__ lamT = a.lamT;
-  const float2* __restrict__ pin = a.priv_in;
-  float2* __restrict__ po = a.priv_out;
+  const float4* __restrict__ lamT = reinterpret_cast<const float4*>(a.lamT);
+  const float4* __restrict__ pin = reinterpret_cast<const float4*>(a.priv_in);
+  float4* __restrict__ po = reinterpret_cast<float4*>(a.priv_out);
   float acc = 0.0f;
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const float2 lam = __ldcs(lamT + priv_idx(blk, r, tid));
+  float4 lam4, x4;
+  static_for<R>([&](auto ri) {
+    constexpr int r = decltype(ri)::value;
+    if constexpr ((r & 1) == 0) lam4 = __ldcs(lamT + pair_idx(blk, r >> 1, tid));
+    const float2 lam = half4<r & 1>(lam4);
     float s, c;
     __sincosf(6.28318530717958647692f * ff_turns(lam.x, lam.y, a.ev_hi, a.ev_lo), &s, &c);
     if constexpr (MODE == RF) {
       v[r] = make_float2(c * v[r].x + s * v[r].y, c * v[r].y - s * v[r].x);   // exp(-i t lambda)
     } else {
-      const float2 x = __ldcs(pin + priv_idx(blk, r, tid));
+      if constexpr ((r & 1) == 0) x4 = __ldcs(pin + pair_idx(blk, r >> 1, tid));
+      const float2 x = half4<r & 1>(x4);
       acc += lam.x * (v[r].x * x.y - v[r].y * x.x);
       v[r] = make_float2(c * v[r].x - s * v[r].y, c * v[r].y + s * v[r].x);   // exp(+i t lambda)
     }
-  }
+  });
   if constexpr (MODE == RF) {
     if (po) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) __stcs(po + priv_idx(blk, r, tid), v[r]);
+      for (int m = 0; m < R / 2; ++m)
+        __stcs(po + pair_idx(blk, m, tid), make_float4(v[2 * m].x, v[2 * m].y, v[2 * m + 1].x, v[2 * m + 1].y));
     }
   }
   tile_inv<G>(v, sm, ts, tid);
@@ -323,7 +355,7 @@ __global__ void __launch_bounds__(NT) lam_kernel(int n, int nofs, const int64_t*
       else lam += 2.0 * w[i] * cospi(2.0 * (double)((s * k) & (N - 1)) / (double)N);
     }
     const float hi = (float)lam;
-    lamT[priv_idx(blk, r, tid)] = make_float2(hi, (float)(lam - (double)hi));
+    lamT[pair_idx(blk, r >> 1, tid) * 2 + (r & 1)] = make_float2(hi, (float)(lam - (double)hi));
   }
 }
 
@@ -337,7 +369,7 @@ __global__ void __launch_bounds__(NT) qperm_kernel(const float* __restrict__ q, 
     constexpr int r = decltype(ri)::value;
     const int j = jt | GC::jreg(2, r);
     const uint32_t g = (uint32_t)(j & ((1 << CB) - 1)) | (blk << CB) | ((uint32_t)(j >> CB) << TB);
-    qT[priv_idx(blk, r, tid)] = q[g];
+    qT[pair_idx(blk, r >> 1, tid) * 2 + (r & 1)] = q[g];
   });
 }
 

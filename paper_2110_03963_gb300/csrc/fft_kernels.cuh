@@ -221,14 +221,24 @@ __device__ __forceinline__ void xchg(float2 (&v)[R], float2* sm, int tid) {
   __syncthreads();
 }
 
-// Shared-memory twiddle sub-tables (built once per CTA from a 256-entry global table computed in
-// fp64 and rounded once): e^{-2 pi i e / 2^14} = A14[e >> 7] * B14[e & 127]. The four-step twiddle
-// of the N-point transform is computed directly (one hardware sine/cosine of the exactly reduced
-// turn, in the column pass).
-constexpr int TW_A14 = 0, TW_B14 = 128, TW_SLOTS = 256;
+// Shared-memory twiddle table (built once per CTA from a global table computed in fp64 and rounded
+// once): W12[k] = e^{-2 pi i k / 2^12} and U4[k] = e^{-2 pi i k / 2^14} (k < 4). An inter-digit
+// twiddle e^{-2 pi i e / 2^14} whose exponent e is a multiple of 4 (every twiddle of a transform of at
+// most 12 bits, and the digit-2 twiddles of the 13- and 14-bit ones) is one table read; any other
+// is W12[e >> 2] * U4[e & 3]. The four-step twiddle of the N-point transform is computed directly
+// (one hardware sine/cosine of the exactly reduced turn, in the column pass).
+constexpr int TW_W12 = 0, TW_U4 = 4096, TW_SLOTS = 4104;
 
+// W12 is stored swizzled, entry k at slot k ^ ((k >> 4) & 15): the digit twiddles of a warp read
+// entries whose indices are multiples of 8 or 16 apart, which without the swizzle would share one
+// or two of the 32 banks.
+__host__ __device__ __forceinline__ constexpr int tw_slot(int k) { return k ^ ((k >> 4) & 15); }
+
+// SH: low bits of e known to be zero
+template <int SH>
 __device__ __forceinline__ float2 tw14(const float2* __restrict__ ts, int e) {
-  return cmul(ts[TW_A14 + (e >> 7)], ts[TW_B14 + (e & 127)]);
+  if constexpr (SH >= 2) return ts[TW_W12 + tw_slot(e >> 2)];
+  else return cmul(ts[TW_W12 + tw_slot(e >> 2)], ts[TW_U4 + (e & 3)]);
 }
 
 // Twiddle between digit 3 and digit 2 (in step layout 2): omega_L^((j1 + 2^D1 j2) * k3), and
@@ -244,7 +254,7 @@ __device__ __forceinline__ void twiddle32(float2 (&v)[R], const float2* ts, int 
     if constexpr (k3 != 0) {
       const int jlow = ((jt | G::jreg(2, r)) >> G::dstart(0)) & ((1 << (D1 + D2)) - 1);
       const int e = (jlow * k3) & (G::L - 1);
-      const float2 w = tw14(ts, e << (TB - G::B));
+      const float2 w = tw14<TB - G::B>(ts, e << (TB - G::B));
       v[r] = CONJ ? cmulc(v[r], w) : cmul(v[r], w);
     }
   });
@@ -259,7 +269,7 @@ __device__ __forceinline__ void twiddle21(float2 (&v)[R], const float2* ts, int 
     if constexpr (k2 != 0) {
       const int j1 = ((jt | G::jreg(1, r)) >> G::dstart(0)) & ((1 << D1) - 1);
       const int e = ((j1 * k2) << D3) & (G::L - 1);
-      const float2 w = tw14(ts, e << (TB - G::B));
+      const float2 w = tw14<D3 + TB - G::B>(ts, e << (TB - G::B));
       v[r] = CONJ ? cmulc(v[r], w) : cmul(v[r], w);
     }
   });

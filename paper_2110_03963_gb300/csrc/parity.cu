@@ -14,6 +14,12 @@
 // phase of layer k is applied as the tile is loaded in the first pass of the layer. n = 24 needs
 // three passes per layer.
 //
+// Chained sweeps. Consecutive gates of a pass are applied two at a time: each thread takes the
+// amplitudes spanned by the two gates' bits (16 for gates on four distinct bits, 8 when they share
+// one), loads those either gate moves, applies the first gate and then the second in registers, and
+// writes them back. Against one sweep per gate this moves 12 amplitudes instead of 16 through shared
+// memory per 16 and halves the barriers; a pass with an odd gate count ends with a one-gate sweep.
+//
 // Gradient. Every pass output of the forward sweep is stored. The reverse sweep runs the passes
 // backwards on (psi, lambda): psi is re-read from the pass's stored output and both vectors are
 // staged in shared memory; each gate is undone on both after its term
@@ -24,6 +30,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <utility>
 #include <vector>
 
 #include "qvs_internal.h"
@@ -49,6 +56,25 @@ __host__ __device__ __forceinline__ constexpr uint32_t swz(uint32_t j) {
 }
 constexpr int SLOTS = TILE;
 
+// combination c of a two-gate sweep on four distinct bits moves unless both gates see 00 or 11
+__host__ __device__ constexpr bool moved4(int c) {
+  return ((c & 3) == 1 || (c & 3) == 2) || ((c >> 2) == 1 || (c >> 2) == 2);
+}
+
+template <class F, int... I>
+__device__ __forceinline__ void static_for_impl(F&& f, std::integer_sequence<int, I...>) {
+  (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+  static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
+
+// kinds of a sweep: one gate (pairs); two gates on four distinct tile bits (combination bits 0, 1
+// = the first gate's, 2, 3 = the second's); two gates sharing one bit (combination bit 1 = the shared
+// bit, 0 = the first gate's other bit, 2 = the second's)
+enum SweepKind : uint8_t { SW_ONE = 0, SW_DISJOINT = 1, SW_SHARED = 2 };
+
 struct PassDesc {
   uint8_t pos[TB];       // index bit of tile bit i (pos[i] = i for i < CHUNK)
   uint8_t ga[MAXG];      // gate g couples tile bits ga[g] and gb[g]
@@ -56,6 +82,11 @@ struct PassDesc {
   uint16_t goff[MAXG][4];  // slot offsets of gate g: pair groups k = 1..3 (t + 256 k), and the pair mask
   uint8_t ntbit[MAXNT];  // non-tile index bits (the CTA index scatters into them)
   int ngates, nnt;
+  int nsweeps;
+  uint8_t skind[MAXG];       // SweepKind of sweep s
+  uint8_t sgate[MAXG];       // its first gate (the second, if any, is sgate + 1)
+  uint8_t sbits[MAXG][4];    // the tile bits it spans, ascending (3 or 4 of them)
+  uint16_t soff[MAXG][16];   // slot offset of combination c of its bits (in the kind's bit order)
 };
 
 struct Args {
@@ -103,6 +134,17 @@ __device__ __forceinline__ uint32_t pair_slot(uint32_t t, int a, int b) {
   uint32_t x = ((t >> p1) << (p1 + 1)) | (t & ((1u << p1) - 1u));
   x = ((x >> p2) << (p2 + 1)) | (x & ((1u << p2) - 1u));
   return swz(x | (1u << b));
+}
+
+// slot of the group base: g's bits spread over the tile bits other than the NB ascending bits b[]
+template <int NB>
+__device__ __forceinline__ uint32_t group_slot(uint32_t g, const uint8_t* b) {
+#pragma unroll
+  for (int i = 0; i < NB; ++i) {
+    const int p = b[i];
+    g = ((g >> p) << (p + 1)) | (g & ((1u << p) - 1u));
+  }
+  return swz(g);
 }
 
 // paired-float arithmetic: one instruction for both components
@@ -179,14 +221,63 @@ __global__ void __launch_bounds__(NT) fwd_kernel(const __grid_constant__ Args a)
   }
   __syncthreads();
   const float2 cc = make_float2(a.c, a.c), sn = make_float2(a.s, -a.s);
-  for (int gi = 0; gi < a.d.ngates; ++gi) {
-    const uint32_t s0 = pair_slot(t, a.d.ga[gi], a.d.gb[gi]), sm_ab = a.d.goff[gi][3];
+  // c x - i s y = (c x.re + s y.im, c x.im - s y.re) and c y - i s x on a pair (x, y)
+  auto givens = [&](float2& x, float2& y) {
+    const float2 x0 = x;
+    x = fma2(cc, x, mul2(sn, swp(y)));
+    y = fma2(cc, y, mul2(sn, swp(x0)));
+  };
+  for (int sw = 0; sw < a.d.nsweeps; ++sw) {
+    const int kind = a.d.skind[sw];
+    const uint16_t* off = a.d.soff[sw];
+    if (kind == SW_DISJOINT) {   // one group of 16 per thread; 12 of them move
+      const uint32_t sb = group_slot<4>(t, a.d.sbits[sw]);
+      float2 v[16];
+      static_for<16>([&](auto ci) {
+        constexpr int c = decltype(ci)::value;
+        if constexpr (moved4(c)) v[c] = sm[sb ^ off[c]];
+      });
+      static_for<4>([&](auto ci) {   // first gate: combination bits 0, 1
+        constexpr int h = decltype(ci)::value << 2;
+        givens(v[h | 1], v[h | 2]);
+      });
+      static_for<4>([&](auto ci) {   // second gate: combination bits 2, 3
+        constexpr int l = decltype(ci)::value;
+        givens(v[l | 4], v[l | 8]);
+      });
+      static_for<16>([&](auto ci) {
+        constexpr int c = decltype(ci)::value;
+        if constexpr (moved4(c)) sm[sb ^ off[c]] = v[c];
+      });
+    } else if (kind == SW_SHARED) {   // two groups of 8 per thread; 6 of each move
 #pragma unroll
-    for (int k = 0; k < TILE / 4 / NT; ++k) {
-      const uint32_t lo = k ? (s0 ^ a.d.goff[gi][k - 1]) : s0, hi = lo ^ sm_ab;
-      const float2 x = sm[lo], y = sm[hi];
-      sm[lo] = fma2(cc, x, mul2(sn, swp(y)));   // c x - i s y = (c x.re + s y.im, c x.im - s y.re)
-      sm[hi] = fma2(cc, y, mul2(sn, swp(x)));   // c y - i s x
+      for (int hg = 0; hg < 2; ++hg) {
+        const uint32_t sb = group_slot<3>(t + NT * hg, a.d.sbits[sw]);
+        float2 v[8];
+        static_for<8>([&](auto ci) {
+          constexpr int c = decltype(ci)::value;
+          if constexpr (c != 0 && c != 7) v[c] = sm[sb ^ off[c]];
+        });
+        givens(v[1], v[2]);   // first gate: combination bits 0, 1 (bit 2 = 0)
+        givens(v[5], v[6]);   //                                  (bit 2 = 1)
+        givens(v[2], v[4]);   // second gate: combination bits 1, 2 (bit 0 = 0)
+        givens(v[3], v[5]);   //                                   (bit 0 = 1)
+        static_for<8>([&](auto ci) {
+          constexpr int c = decltype(ci)::value;
+          if constexpr (c != 0 && c != 7) sm[sb ^ off[c]] = v[c];
+        });
+      }
+    } else {
+      const int gi = a.d.sgate[sw];
+      const uint32_t s0 = pair_slot(t, a.d.ga[gi], a.d.gb[gi]), sm_ab = a.d.goff[gi][3];
+#pragma unroll
+      for (int k = 0; k < TILE / 4 / NT; ++k) {
+        const uint32_t lo = k ? (s0 ^ a.d.goff[gi][k - 1]) : s0, hi = lo ^ sm_ab;
+        float2 x = sm[lo], y = sm[hi];
+        givens(x, y);
+        sm[lo] = x;
+        sm[hi] = y;
+      }
     }
     __syncthreads();
   }
@@ -216,20 +307,82 @@ __global__ void __launch_bounds__(NT) rev_kernel(const __grid_constant__ Args a)
   // componentwise products (re*im, im*re) whose difference is taken once at the end
   float2 at = make_float2(0.f, 0.f);
   const float2 cc = make_float2(a.c, a.c), sn = make_float2(-a.s, a.s);
-  for (int gi = a.d.ngates - 1; gi >= 0; --gi) {
-    const uint32_t s0 = pair_slot(t, a.d.ga[gi], a.d.gb[gi]), sm_ab = a.d.goff[gi][3];
+  // on a pair at the gate's output: accumulate the gradient term, then undo the gate on both
+  // vectors: (a, b) -> (c a + i s b, c b + i s a) = (c a.re - s b.im, c a.im + s b.re)
+  auto undo = [&](float2& x, float2& y, float2& u, float2& v) {
+    at = fma2(u, swp(y), at);
+    at = fma2(v, swp(x), at);
+    const float2 x0 = x, u0 = u;
+    x = fma2(cc, x, mul2(sn, swp(y)));
+    y = fma2(cc, y, mul2(sn, swp(x0)));
+    u = fma2(cc, u, mul2(sn, swp(v)));
+    v = fma2(cc, v, mul2(sn, swp(u0)));
+  };
+  for (int sw = a.d.nsweeps - 1; sw >= 0; --sw) {
+    const int kind = a.d.skind[sw];
+    const uint16_t* off = a.d.soff[sw];
+    if (kind == SW_DISJOINT) {
+      const uint32_t sb = group_slot<4>(t, a.d.sbits[sw]);
+      float2 x[16], l[16];
+      static_for<16>([&](auto ci) {
+        constexpr int c = decltype(ci)::value;
+        if constexpr (moved4(c)) {
+          x[c] = sp[sb ^ off[c]];
+          l[c] = sl[sb ^ off[c]];
+        }
+      });
+      static_for<4>([&](auto ci) {   // second gate first
+        constexpr int lo = decltype(ci)::value;
+        undo(x[lo | 4], x[lo | 8], l[lo | 4], l[lo | 8]);
+      });
+      static_for<4>([&](auto ci) {
+        constexpr int h = decltype(ci)::value << 2;
+        undo(x[h | 1], x[h | 2], l[h | 1], l[h | 2]);
+      });
+      static_for<16>([&](auto ci) {
+        constexpr int c = decltype(ci)::value;
+        if constexpr (moved4(c)) {
+          sp[sb ^ off[c]] = x[c];
+          sl[sb ^ off[c]] = l[c];
+        }
+      });
+    } else if (kind == SW_SHARED) {
 #pragma unroll
-    for (int k = 0; k < TILE / 4 / NT; ++k) {
-      const uint32_t lo = k ? (s0 ^ a.d.goff[gi][k - 1]) : s0, hi = lo ^ sm_ab;
-      const float2 x = sp[lo], y = sp[hi];
-      const float2 u = sl[lo], v = sl[hi];
-      at = fma2(u, swp(y), at);
-      at = fma2(v, swp(x), at);
-      // undo: (a, b) -> (c a + i s b, c b + i s a) = (c a.re - s b.im, c a.im + s b.re)
-      sp[lo] = fma2(cc, x, mul2(sn, swp(y)));
-      sp[hi] = fma2(cc, y, mul2(sn, swp(x)));
-      sl[lo] = fma2(cc, u, mul2(sn, swp(v)));
-      sl[hi] = fma2(cc, v, mul2(sn, swp(u)));
+      for (int hg = 0; hg < 2; ++hg) {
+        const uint32_t sb = group_slot<3>(t + NT * hg, a.d.sbits[sw]);
+        float2 x[8], l[8];
+        static_for<8>([&](auto ci) {
+          constexpr int c = decltype(ci)::value;
+          if constexpr (c != 0 && c != 7) {
+            x[c] = sp[sb ^ off[c]];
+            l[c] = sl[sb ^ off[c]];
+          }
+        });
+        undo(x[2], x[4], l[2], l[4]);   // second gate first: combination bits 1, 2
+        undo(x[3], x[5], l[3], l[5]);
+        undo(x[1], x[2], l[1], l[2]);   // first gate: combination bits 0, 1
+        undo(x[5], x[6], l[5], l[6]);
+        static_for<8>([&](auto ci) {
+          constexpr int c = decltype(ci)::value;
+          if constexpr (c != 0 && c != 7) {
+            sp[sb ^ off[c]] = x[c];
+            sl[sb ^ off[c]] = l[c];
+          }
+        });
+      }
+    } else {
+      const int gi = a.d.sgate[sw];
+      const uint32_t s0 = pair_slot(t, a.d.ga[gi], a.d.gb[gi]), sm_ab = a.d.goff[gi][3];
+#pragma unroll
+      for (int k = 0; k < TILE / 4 / NT; ++k) {
+        const uint32_t lo = k ? (s0 ^ a.d.goff[gi][k - 1]) : s0, hi = lo ^ sm_ab;
+        float2 x = sp[lo], y = sp[hi], u = sl[lo], v = sl[hi];
+        undo(x, y, u, v);
+        sp[lo] = x;
+        sp[hi] = y;
+        sl[lo] = u;
+        sl[hi] = v;
+      }
     }
     __syncthreads();
   }
@@ -355,6 +508,46 @@ static int plan_layer(int n, std::vector<Pass>& out) {
       done[sel[i]] = 1;
     }
     left -= (int)sel.size();
+    // sweeps: consecutive gates two at a time (the order within the pass is kept)
+    P.d.nsweeps = 0;
+    auto combo_offsets = [&](int s, const int* cb, int nb) {
+      for (int c = 0; c < (1 << nb); ++c) {
+        uint32_t x = 0;
+        for (int i = 0; i < nb; ++i)
+          if ((c >> i) & 1) x |= 1u << cb[i];
+        P.d.soff[s][c] = (uint16_t)swz(x);
+      }
+      int sorted[4];
+      for (int i = 0; i < nb; ++i) sorted[i] = cb[i];
+      std::sort(sorted, sorted + nb);
+      for (int i = 0; i < 4; ++i) P.d.sbits[s][i] = (uint8_t)(i < nb ? sorted[i] : 0);
+    };
+    for (int g = 0; g < P.d.ngates;) {
+      const int s = P.d.nsweeps++;
+      P.d.sgate[s] = (uint8_t)g;
+      if (g + 1 < P.d.ngates) {
+        const int a1 = P.d.ga[g], b1 = P.d.gb[g], a2 = P.d.ga[g + 1], b2 = P.d.gb[g + 1];
+        const int shared = (a1 == a2) + (a1 == b2) + (b1 == a2) + (b1 == b2);
+        if (shared == 0) {
+          const int cb[4] = {a1, b1, a2, b2};
+          P.d.skind[s] = SW_DISJOINT;
+          combo_offsets(s, cb, 4);
+          g += 2;
+          continue;
+        }
+        if (shared == 1) {
+          const int sh = (a1 == a2 || a1 == b2) ? a1 : b1;
+          const int o1 = sh == a1 ? b1 : a1, o2 = sh == a2 ? b2 : a2;
+          const int cb[3] = {o1, sh, o2};
+          P.d.skind[s] = SW_SHARED;
+          combo_offsets(s, cb, 3);
+          g += 2;
+          continue;
+        }
+      }
+      P.d.skind[s] = SW_ONE;   // last gate of an odd count, or a gate repeated on the same pair
+      g += 1;
+    }
     P.d.nnt = 0;
     for (int b = 0; b < n; ++b)
       if (!in_tile(b)) P.d.ntbit[P.d.nnt++] = (uint8_t)b;

@@ -46,13 +46,17 @@ constexpr int CHUNK = 4;         // lowest index bits, always in the tile
 constexpr int MAXG = 40;         // gates per pass
 constexpr int MAXNT = 32;        // non-tile bits
 
-// Shared slot of tile index j: tile bits 4 and 5 are XORed into the low four bits (the 8-byte
-// bank class of a half-warp access). A gate's 16 lanes of a half-warp then fall on 16 distinct
-// classes for every gate pair the schedules produce at n = 12..28, and for the staging accesses
-// (lanes = tile bits 0..4); n = 30 has one gate with a two-way conflict. The map is linear over
-// XOR, so slot(j1 ^ j2) = slot(j1) ^ slot(j2) and no padding slots are needed.
+// Shared slot of tile index j: tile bits 4, 5, 6 and 7 XOR the classes 11, 12, 2 and 13 into the low
+// four bits (the 8-byte bank class of a half-warp access). A sweep's 16 lanes of a half-warp take
+// the first four tile bits its gates leave free, so they fall on 16 distinct classes whenever those
+// bits' classes are independent: for the one- and two-gate sweeps of every schedule at n = 12..30
+// that costs 1.02 times the conflict-free count of shared-memory wavefronts (1.27 with bits 4 and 5
+// alone). Staging lanes (tile bits 0..3) are always conflict-free. The map is linear over XOR, so
+// slot(j1 ^ j2) = slot(j1) ^ slot(j2), leaves bits 8..11 alone (slot(t + 256 m) = slot(t) + 256 m)
+// and needs no padding slots.
 __host__ __device__ __forceinline__ constexpr uint32_t swz(uint32_t j) {
-  return j ^ (((j >> 4) & 1u) ? 11u : 0u) ^ (((j >> 5) & 1u) ? 12u : 0u);
+  return j ^ (((j >> 4) & 1u) ? 11u : 0u) ^ (((j >> 5) & 1u) ? 12u : 0u) ^ (((j >> 6) & 1u) ? 2u : 0u) ^
+         (((j >> 7) & 1u) ? 13u : 0u);
 }
 constexpr int SLOTS = TILE;
 

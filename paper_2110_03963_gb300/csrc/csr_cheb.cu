@@ -116,7 +116,8 @@ __device__ __forceinline__ float2 row_spmv(const uint32_t* __restrict__ rowptr, 
 // Moving the set bit at position b (p of the set bits lie below it) to the free position b + 1
 // changes the rank by +C(b, p) (Pascal's rule); moving it from b + 1 down to a free b changes it by
 // -C(b, p). The ring's closing pair (bits 0 and n-1) moves the lowest set bit to the top or the
-// highest to the bottom, which renumbers every set bit; that rank is summed afresh.
+// highest to the bottom, which renumbers every set bit; that neighbour's rank is summed afresh once,
+// when the mixer is set.
 struct CsrOp {
   const uint32_t* rowptr;
   const int32_t* colind;
@@ -135,87 +136,58 @@ struct CsrOp {
 constexpr int XY_BW = 33;   // binomial table row width: C(b, j) at binom[b * XY_BW + j], b, j <= 32
 
 struct XyRingOp {
-  const uint32_t* states;   // basis state of each row
+  const uint2* rows;        // per row: basis state, row of the closing-pair neighbour (-1: none)
   const int32_t* binom;     // C(b, j), b <= n, j <= k
   int n, k;
-  __device__ __forceinline__ int32_t C(int b, int j) const { return __ldg(binom + b * XY_BW + j); }
-  // visit(neighbour row) for every nonzero of the row (all values 2)
-  // rank of the neighbour across the closing pair (bit 0, bit n - 1), which must differ
-  __device__ __forceinline__ int64_t wrap_rank(uint32_t s) const {
-    int64_t r = 0;
-    uint32_t t = s;
-    int i = 1;
-    if (s & 1u) {   // the lowest set bit (at 0) moves to n - 1 and becomes the k-th
-      t &= t - 1u;
-      i = 2;
-      while (t) {
-        const int c = __ffs(t) - 1;
-        t &= t - 1u;
-        r += C(c, i - 1);
-        ++i;
-      }
-      r += C(n - 1, k);
-    } else {        // the highest set bit (at n - 1) moves to 0 and becomes the first
-      while (i < k) {
-        const int c = __ffs(t) - 1;
-        t &= t - 1u;
-        r += C(c, i + 1);
-        ++i;
-      }
-    }
-    return r;
-  }
+  // Row indices and rank steps are 32-bit: the largest space allowed, C(31, 15), is below 2^31.
+  // The closing pair (bits 0 and n-1) moves the lowest set bit to the top or the highest to the
+  // bottom, which renumbers every set bit; that neighbour's row is computed once, on the host, when
+  // the mixer is set, and read with the state.
   template <class F>
-  __device__ __forceinline__ void neighbours(uint32_t s, int64_t row, F&& visit) const {
+  __device__ __forceinline__ void neighbours(uint2 rw, int32_t row, F&& visit) const {
+    const uint32_t s = rw.x;
     uint32_t d = (s ^ (s >> 1)) & ((1u << (n - 1)) - 1u);   // bit b: bits b and b + 1 differ
     while (d) {
       const int b = __ffs(d) - 1;
       d &= d - 1u;
-      const int32_t step = C(b, __popc(s & ((1u << b) - 1u)));
+      const int32_t step = __ldg(binom + (b * XY_BW + __popc(s & ((1u << b) - 1u))));
       visit(((s >> b) & 1u) ? row + step : row - step);
     }
-    if ((s ^ (s >> (n - 1))) & 1u) visit(wrap_rank(s));
+    if ((int32_t)rw.y >= 0) visit((int32_t)rw.y);
   }
   // the same neighbours in groups of 8 adjacent pairs: each group's ranks first, then its gathers,
   // so up to 8 loads are in flight instead of one per dependent step
-  __device__ __forceinline__ float2 gather_sum(const float2* __restrict__ x, uint32_t s, int64_t row) const {
+  __device__ __forceinline__ float2 gather_sum(const float2* __restrict__ x, uint2 rw, int32_t row) const {
+    const uint32_t s = rw.x;
     float2 acc = make_float2(0.f, 0.f);
     const uint32_t d = (s ^ (s >> 1)) & ((1u << (n - 1)) - 1u);
 #pragma unroll
     for (int g = 0; g < 32; g += 8) {
       if ((d >> g) == 0u) break;
-      int64_t nb[8];
+      int32_t nb[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int b = g + u;
-        const bool on = (d >> b) & 1u;
-        const int32_t step = on ? C(b, __popc(s & ((1u << b) - 1u))) : 0;
-        nb[u] = on ? (((s >> b) & 1u) ? row + step : row - step) : -1;
+        const int32_t step = ((d >> b) & 1u) ? __ldg(binom + (b * XY_BW + __popc(s & ((1u << b) - 1u)))) : 0;
+        nb[u] = ((s >> b) & 1u) ? row + step : row - step;
       }
       float2 v[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = nb[u] >= 0 ? __ldg(x + nb[u]) : make_float2(0.f, 0.f);
+      for (int u = 0; u < 8; ++u) v[u] = ((d >> (g + u)) & 1u) ? __ldg(x + nb[u]) : make_float2(0.f, 0.f);
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        acc.x += v[u].x;
-        acc.y += v[u].y;
-      }
+      for (int u = 0; u < 8; ++u) acc = __fadd2_rn(acc, v[u]);
     }
-    if ((s ^ (s >> (n - 1))) & 1u) {
-      const float2 v = __ldg(x + wrap_rank(s));
-      acc.x += v.x;
-      acc.y += v.y;
-    }
+    if ((int32_t)rw.y >= 0) acc = __fadd2_rn(acc, __ldg(x + (int32_t)rw.y));
     return acc;
   }
   __device__ __forceinline__ float2 apply(const float2* __restrict__ x, int64_t row, int, bool valid) const {
     if (!valid) return make_float2(0.f, 0.f);
-    const float2 acc = gather_sum(x, __ldg(states + row), row);
+    const float2 acc = gather_sum(x, __ldg(rows + row), (int32_t)row);
     return make_float2(2.f * acc.x, 2.f * acc.y);
   }
   __device__ __forceinline__ double apply_d(const double* __restrict__ x, int64_t r) const {
     double acc = 0.0;
-    neighbours(states[r], r, [&](int64_t nb) { acc += x[nb]; });
+    neighbours(rows[r], (int32_t)r, [&](int32_t nb) { acc += x[nb]; });
     return 2.0 * acc;
   }
 };
@@ -474,7 +446,7 @@ static CsrOp make_csr_op(const CsrData& C) {
                C.implicit_value};
 }
 static XyRingOp make_xy_op(const CsrData& C) {
-  return XyRingOp{C.states.as<uint32_t>(), C.binom.as<int32_t>(), C.xy_n, C.xy_k};
+  return XyRingOp{C.states.as<uint2>(), C.binom.as<int32_t>(), C.xy_n, C.xy_k};
 }
 // f(op) with the handle's operator type
 template <class F>
@@ -855,18 +827,31 @@ int xy_set_mixer(qvs_ctx* h, const qvs_mixer_desc* d) {
     }
   }
   if ((int64_t)binom[(size_t)n * XY_BW + k] != h->dim) return QVS_EINVAL;
-  // the weight-k states in increasing order (next state with the same popcount: Gosper's rule)
-  std::vector<uint32_t> st((size_t)h->dim);
+  // the weight-k states in increasing order (next state with the same popcount: Gosper's rule),
+  // each with the row of its closing-pair neighbour: the rank sum_i C(c_i, i) of the state with bits
+  // 0 and n-1 exchanged (set bits c_1 < ... < c_k), or -1 when the two bits agree
+  auto rank = [&](uint32_t s) {
+    int64_t r = 0;
+    for (int i = 1; s; ++i) {
+      const int c = __builtin_ctz(s);
+      s &= s - 1u;
+      r += binom[(size_t)c * XY_BW + i];
+    }
+    return r;
+  };
+  const uint32_t ends = 1u | (1u << (n - 1));
+  std::vector<uint2> st((size_t)h->dim);
   uint32_t x = (1u << k) - 1u;
   for (int64_t r = 0; r < h->dim; ++r) {
-    st[(size_t)r] = x;
+    const bool differ = ((x & ends) != 0u) && ((x & ends) != ends);
+    st[(size_t)r] = make_uint2(x, differ ? (uint32_t)rank(x ^ ends) : 0xffffffffu);
     const uint32_t c = x & (0u - x), rr = x + c;
     x = (((rr ^ x) >> 2) / c) | rr;
   }
   CsrData& C = h->csr;
-  QVS_TRY(C.states.ensure(sizeof(uint32_t) * st.size()));
+  QVS_TRY(C.states.ensure(sizeof(uint2) * st.size()));
   QVS_TRY(C.binom.ensure(sizeof(int32_t) * binom.size()));
-  QVS_CUDA_TRY(cudaMemcpyAsync(C.states.ptr, st.data(), sizeof(uint32_t) * st.size(), cudaMemcpyHostToDevice,
+  QVS_CUDA_TRY(cudaMemcpyAsync(C.states.ptr, st.data(), sizeof(uint2) * st.size(), cudaMemcpyHostToDevice,
                                h->stream));
   QVS_CUDA_TRY(cudaMemcpyAsync(C.binom.ptr, binom.data(), sizeof(int32_t) * binom.size(), cudaMemcpyHostToDevice,
                                h->stream));

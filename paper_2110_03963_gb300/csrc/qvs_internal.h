@@ -153,7 +153,8 @@ struct CsrData {
   // matrix-free XY ring on the Hamming-weight-k states of n qubits (QVS_MIX_XY_RING)
   bool xy = false;
   int xy_n = 0, xy_k = 0;
-  DevBuf states;            // uint32 basis state per row, increasing
+  DevBuf states;            // uint2 per row: its basis state (rows in increasing state order) and the
+                            // row of its closing-pair neighbour (-1: bits 0 and n-1 agree)
   DevBuf binom;             // int32 binomial table
 };
 

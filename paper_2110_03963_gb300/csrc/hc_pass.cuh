@@ -586,12 +586,8 @@ template <class T, int SHAPE, int TH>
 static int launch_one(const PassArgs<T>& a, uint32_t grid, cudaStream_t st) {
   constexpr bool two = two_vector(SHAPE);
   const size_t sm = (two ? 2 : 1) * (size_t)SM_SLOTS * sizeof(typename Cx<T>::t);
-  static bool configured = false;   // per instantiation
-  if (!configured) {
-    QVS_CUDA_TRY(cudaFuncSetAttribute(pass_kernel<T, SHAPE, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)sm));
-    configured = true;
-  }
+  static std::atomic<uint64_t> configured{0};   // per instantiation: devices already set
+  QVS_TRY(smem_limit_once(reinterpret_cast<const void*>(pass_kernel<T, SHAPE, TH>), configured, (int)sm));
   pass_kernel<T, SHAPE, TH><<<grid, NT, sm, st>>>(a);
   QVS_CUDA_TRY(cudaGetLastError());
   return QVS_OK;

@@ -164,16 +164,13 @@ int launch_staged(int shape, const PassArgs<float>& a, const StageMaps& m, uint3
                   cudaStream_t st) {
   const size_t sm =
       kStageAlign + (size_t)(m.two ? 2 : 1) * TILE * sizeof(float2) + (size_t)SM_SLOTS * sizeof(float2);
-  auto go = [&](auto kern, bool& configured) -> int {
-    if (!configured) {
-      QVS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      configured = true;
-    }
+  auto go = [&](auto kern, std::atomic<uint64_t>& configured) -> int {
+    QVS_TRY(smem_limit_once(reinterpret_cast<const void*>(kern), configured, (int)sm));
     kern<<<grid, NT, sm, st>>>(a, m, ntiles);
     QVS_CUDA_TRY(cudaGetLastError());
     return QVS_OK;
   };
-  static bool c_fe = false, c_r1 = false, c_r2 = false, c_r0 = false;   // per instantiation
+  static std::atomic<uint64_t> c_fe{0}, c_r1{0}, c_r2{0}, c_r0{0};   // per instantiation: devices set
   switch (shape) {
     case FE: return go(staged_kernel<FE, TH>, c_fe);
     case R1: return go(staged_kernel<R1, TH>, c_r1);

@@ -172,7 +172,7 @@ extern "C" int qvs_quality_maxcut(int n, int n_edges, const int32_t* eu, const i
   if (n_edges > 0 && (!eu || !ev)) return QVS_EINVAL;
   if (out_dtype != QVS_I32 && out_dtype != QVS_F32 && out_dtype != QVS_F64) return QVS_EINVAL;
   if (out_dtype == QVS_I32 && w) return QVS_EINVAL;
-  static MaxcutArgs a;   // large; built on the host then passed by value
+  MaxcutArgs a;   // built on the host (one per call) and passed by value
   memset(&a, 0, sizeof(a));
   a.n = n;
   a.m = n_edges;
@@ -215,7 +215,7 @@ extern "C" int qvs_quality_portfolio(int n_qubits, int64_t dim, const int64_t* s
   if (n_qubits < 2 || (n_qubits & 1) || n_qubits / 2 > kMaxAssets || n_qubits > 62) return QVS_EINVAL;
   if (dim < 1 || !states || !returns || !cov || !q_out || !isfinite(omega)) return QVS_EINVAL;
   if (out_dtype != QVS_F32 && out_dtype != QVS_F64) return QVS_EINVAL;
-  static PortArgs a;
+  PortArgs a;   // built on the host (one per call) and passed by value
   memset(&a, 0, sizeof(a));
   a.nq = n_qubits;
   a.M = n_qubits / 2;

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -25,6 +26,19 @@
   } while (0)
 
 namespace qvs {
+
+// Raise a kernel's dynamic shared-memory limit to `bytes` on the current device, once per device:
+// the attribute belongs to the device, so a process that drives several GPUs sets it on each.
+// `done` holds one bit per device index (devices >= 64 set it on every call).
+inline int smem_limit_once(const void* fn, std::atomic<uint64_t>& done, int bytes) {
+  int dev = 0;
+  QVS_CUDA_TRY(cudaGetDevice(&dev));
+  const uint64_t bit = dev < 64 ? (uint64_t(1) << dev) : 0;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return QVS_OK;
+  QVS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  done.fetch_or(bit, std::memory_order_acq_rel);
+  return QVS_OK;
+}
 
 // Device allocator of a handle: the alloc/dealloc hooks given to qvs_create (both NULL: the
 // CUDA runtime's cudaMalloc / cudaFree).

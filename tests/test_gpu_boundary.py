@@ -2,6 +2,7 @@
 of qvs_set_initial_state and the differentiable objective (torch.autograd) against the fp64 oracle.
 The failing allocator is a host-side fake (its alloc returns NULL); no device fault is involved."""
 import ctypes
+import gc
 
 import numpy as np
 import pytest
@@ -117,6 +118,7 @@ def test_default_simulator_uses_the_torch_caching_allocator(qvs):
     import torch
     n = 18
     _, q = _maxcut(qvs, n, 224)
+    gc.collect()   # transient tensors of the set-up must not count in the baseline
     torch.cuda.synchronize()
     before = torch.cuda.memory_allocated()
     sim = qvs.Simulator(1 << n, qvs.QVS_C64)
@@ -127,7 +129,8 @@ def test_default_simulator_uses_the_torch_caching_allocator(qvs):
     assert sim.allocator.live > 0
     sim.close()
     assert sim.allocator.live == 0
-    assert torch.cuda.memory_allocated() == before
+    gc.collect()
+    assert torch.cuda.memory_allocated() <= before   # every block the handle took is back
 
 
 def test_initial_state_kinds(qvs):

@@ -181,6 +181,9 @@ static Tile make_tile(int n, int s, int hfirst, int nh) {
   return t;
 }
 
+// tile type of pass j (1-based) when a layer takes three types (see make_plan)
+__host__ __device__ __forceinline__ int three_type(int j) { return (j & 1) ? 1 + ((j - 1) / 2) % 2 : 0; }
+
 static int make_plan(int n, int p, Plan& pl) {
   pl = Plan{};
   pl.n = n;
@@ -227,11 +230,16 @@ static int make_plan(int n, int p, Plan& pl) {
       else q = {q.type, FE, p - 1, -1, -1};
     }
   } else {
+    // Passes alternate: odd j carries a phase (F0, F1, FE) and rotates one high tile type on both
+    // of its sides, even j (F2) rotates the rest of a layer. Odd passes alternate types 1 and 2 and
+    // every even pass takes type 0, so each layer rotates types {1, 0, 2} or {2, 0, 1}: the
+    // arithmetic-heavy phase passes always use a high type (two register layouts), and the
+    // contiguous type 0 (three layouts, one more transpose per direction) only the F2 / R2 passes.
     pl.F = 2 * p + 1;
     pl.pass.assign(pl.F + 1, PassInfo{});
     for (int j = 1; j <= pl.F; ++j) {
       PassInfo& q = pl.pass[j];
-      q.type = (j - 1) % 3;
+      q.type = three_type(j);
       if (j == 1) q = {q.type, F0, -1, 0, 0};
       else if (j == pl.F) q = {q.type, FE, p - 1, -1, -1};
       else if (j % 2 == 0) q = {q.type, F2, (j - 2) / 2, -1, -1};
@@ -1053,7 +1061,7 @@ __host__ __device__ __forceinline__ void bpass_info(const BInst& I, int j, int& 
     else if (j <= p) { shape = F1; lb = j - 2; la = j - 1; lg = j - 1; }
     else { shape = FE; lb = p - 1; la = -1; lg = -1; }
   } else {
-    type = (j - 1) % 3;
+    type = three_type(j);
     if (j == 1) { shape = F0; lb = -1; la = 0; lg = 0; }
     else if (j == I.F) { shape = FE; lb = p - 1; la = -1; lg = -1; }
     else if (j % 2 == 0) { shape = F2; lb = (j - 2) / 2; la = -1; lg = -1; }

@@ -376,7 +376,29 @@ __device__ __forceinline__ void run_pass(const PassArgs<T>& a, uint32_t bid, uin
   };
 
   C v[R];
-  if constexpr (S == F0) {
+  if constexpr (S == F0 && TWO) {   // the high tile types: one transpose (L2 -> L3)
+    const uint32_t tpop = __popc(base) + __popc(tj<2>(0, tid));
+    if (a.gen_init) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {   // W_j = amp (-i)^|j|
+        C w;
+        w.x = a.init_amp;
+        w.y = T(0);
+        v[r] = mul_ipow(w, (0u - (tpop + (uint32_t)cpop(tj<2>(r, 0)))) & 3u);
+      }
+    } else {
+      gload_plain<2>(v, a.psi_in, off2, a.tile, tpop);
+    }
+    if constexpr (!ALT) {
+      if (a.qcta) __syncthreads();
+    }
+    qget();
+    phase2(v, T(1), a.rho_p);
+    rot_layout<2, TAF>(v, a.mask_aft, a.ta);
+    xchg_alt<2, 3, 0, ALT>(v, sm, tid);
+    rot_layout<3, TAF>(v, a.mask_aft, a.ta);
+    gstore<3>(v, a.psi_out, off3, a.tile);
+  } else if constexpr (S == F0) {
     const uint32_t tpop = __popc(base) + __popc(tj<2>(0, tid));
     if (a.gen_init) {
 #pragma unroll

@@ -2,6 +2,8 @@
 // circ_n*.cu translation units (compiled in parallel).
 #pragma once
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <math.h>
 
 
@@ -34,7 +36,35 @@ struct CircArgs {
   float init_amp;
   double* part;                // partial rows [row * gridDim.x + blockIdx.x]
   int row_a, row_b;
+  int tma_store;               // 1: the layout-0 result leaves through one tensor store (out_map)
+  CUtensorMap out_map;         // 4-d view of `out` matching the shared-memory box (see box_word)
 };
+
+// ---------------------------------------------------------------- tensor-store epilogue
+//
+// The column tile of Geo<2, 4, 4, 4> (4 adjacent columns x 4096 rows of a 2^26 state) is stored in
+// one bulk tensor copy from shared memory instead of 32 per-thread stores per thread, whose burst
+// at the end of every tile kept the LSU queue full (lg-throttle the top stall). The box is
+// {4 columns, 4 (row bits 4-5), 16 (row bits 0-3), 64 (row bits 6-11)}: in shared memory a tile
+// index lands at box_word, and a half-warp of layout 0 (lanes = tile bits 0, 1, 6, 7) writes 16
+// consecutive 8-byte words, one per bank pair. The copy reads the transpose buffer, free after the
+// last transpose; the CTA waits only until the copy has read it.
+template <class G>
+struct TmaTile {
+  static constexpr bool ok = false;
+};
+template <>
+struct TmaTile<Geo<2, 4, 4, 4>> {
+  static constexpr bool ok = true;
+};
+__host__ __device__ constexpr int box_word(int j) {
+  return (j & 3) | (((j >> 6) & 3) << 2) | (((j >> 2) & 15) << 4) | ((j >> 8) << 8);
+}
+constexpr int kBoxAlign = 1024;   // the dynamic shared region is realigned to this (tensor copies: 128 B)
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
 
 // Thread-major private arrays (q in column-pass order, the stored vectors, the eigenvalue table):
 // only these kernels read them, so they are interleaved by register pairs: registers 2m and 2m+1 of
@@ -102,7 +132,9 @@ __device__ __forceinline__ const float2* load_twsub(float2* sm, const float2* __
 template <class G, int MODE>
 __global__ void __launch_bounds__(NT, 1) col_kernel(const __grid_constant__ CircArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* sm = reinterpret_cast<float2*>(smem_raw);
+  // the region is over-allocated by kBoxAlign bytes; the buffers start at the first aligned address
+  const uint32_t pad = (kBoxAlign - (smem_addr(smem_raw) & (kBoxAlign - 1u))) & (kBoxAlign - 1u);
+  float2* sm = reinterpret_cast<float2*>(smem_raw + pad);
   const float2* ts = load_twsub(sm, a.twsub);
   constexpr int CB = G::dstart(0);
   const int tid = threadIdx.x;
@@ -143,6 +175,29 @@ __global__ void __launch_bounds__(NT, 1) col_kernel(const __grid_constant__ Circ
   };
   auto gstore0 = [&](const float2(&v)[R], float2* dst) {
     const int jt = G::template jthr<0>(tid_fresh());
+    if constexpr (TmaTile<G>::ok) {
+      // a.tma_store is uniform; the alignment test never fails (the region is realigned above)
+      if (a.tma_store && (smem_addr(sm) & 127u) == 0u) {
+        const int bw = box_word(jt);
+        static_for<R>([&](auto ri) {
+          constexpr int r = decltype(ri)::value;
+          constexpr int o = box_word(G::jreg(0, r));
+          sm[bw + o] = v[r];
+        });
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // visible to the copy engine
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          asm volatile(
+              "cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%1, %2, %2, %2}], [%3];" ::"l"(
+                  reinterpret_cast<uint64_t>(&a.out_map)),
+              "r"((int)(4u * blk)), "r"(0), "r"(smem_addr(sm))
+              : "memory");
+          asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+          asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+        }
+        return;
+      }
+    }
     static_for<R>([&](auto ri) {
       constexpr int r = decltype(ri)::value;
       __stcs(dst + gidx(jt | G::jreg(0, r)), v[r]);
@@ -390,7 +445,7 @@ struct Driver {
     const int64_t dim = h->dim;
     const uint32_t grid = (uint32_t)(dim >> TB);
     const size_t vb = sizeof(float2) * (size_t)dim;
-    const size_t smem = sizeof(float2) * (SM_SLOTS + TW_SLOTS);
+    const size_t smem = sizeof(float2) * (SM_SLOTS + TW_SLOTS) + kBoxAlign;
     // q in column-pass order (rebuilt when q or the mixer changed)
     if (!h->circ.qT_valid) {
       QVS_TRY(h->circ.qT.ensure(sizeof(float) * (size_t)dim));
@@ -437,8 +492,37 @@ struct Driver {
     auto ph = [&](CircArgs& a, int k) { turns_split(gammas[k], &a.ph_hi, &a.ph_lo); };
     auto ev = [&](CircArgs& a, int k) { turns_split(ts[k], &a.ev_hi, &a.ev_lo); };
     const double colb = 16.0 + 4.0, rowb = 16.0 + 8.0;   // bytes per amplitude (state r+w, q / lambda)
+    // tensor maps of the two state buffers for the tensor-store epilogue (box_word's order: columns,
+    // row bits 4-5, row bits 0-3, row bits 6-11); per-thread stores when the driver has no encoder
+    // or rejects the view
+    CUtensorMap map_w, map_l;
+    bool tma_w = false, tma_l = false;
+    if constexpr (TmaTile<GC>::ok) {
+      auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(hc::tensor_map_encode_fn());
+      auto encode = [&](CUtensorMap* m, void* ptr) -> bool {
+        if (!enc || !ptr) return false;
+        const cuuint64_t C = (cuuint64_t)dim >> GC::B;   // columns: the index bits below the transform
+        cuuint64_t dims[4] = {C, 4, 16, 64};
+        cuuint64_t strides[3] = {16 * C * 8, C * 8, 64 * C * 8};
+        cuuint32_t box[4] = {4, 4, 16, 64};
+        cuuint32_t es[4] = {1, 1, 1, 1};
+        return enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, ptr, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+      };
+      tma_w = h->staged && encode(&map_w, W);
+      tma_l = h->staged && encode(&map_l, Lb);
+    }
     int64_t launches = 0;
-    auto launch_col = [&](int mode, const CircArgs& a, double bytes) -> int {
+    auto launch_col = [&](int mode, const CircArgs& a0, double bytes) -> int {
+      CircArgs a = a0;
+      if (a.out == W && tma_w) {
+        a.tma_store = 1;
+        a.out_map = map_w;
+      } else if (a.out == Lb && a.out && tma_l) {
+        a.tma_store = 1;
+        a.out_map = map_l;
+      }
       cudaEvent_t e0;
       QVS_TRY(prof_begin(h, &e0));
       switch (mode) {

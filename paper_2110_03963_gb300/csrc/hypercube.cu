@@ -327,6 +327,9 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
+// the same lookup for the other mixer paths (NULL when the driver lacks the entry point)
+void* tensor_map_encode_fn() { return reinterpret_cast<void*>(tensor_map_encoder()); }
+
 // The tile box of tile geometry t over a 2^n-element vector (elem bytes per element): the packed
 // 5-d view (low chunk bits up to 8 | chunk bits 8..s-1 | middle non-tile bits | high tile bits |
 // top non-tile bits); a tile is {d0, d1, 1, d3, 1} at (0, 0, mid, 0, top).

@@ -268,6 +268,9 @@ int parity_gradient(qvs_ctx* h, int p, const double* gammas, const double* ts, d
 // CSR Chebyshev path: csr_cheb.cu
 int csr_set_mixer(qvs_ctx* h, const qvs_mixer_desc* d);
 int xy_set_mixer(qvs_ctx* h, const qvs_mixer_desc* d);
+namespace hc {
+void* tensor_map_encode_fn();   // cuTensorMapEncodeTiled from the driver, or NULL
+}
 int csr_evolve(qvs_ctx* h, int p, const double* gammas, const double* ts);
 int csr_gradient(qvs_ctx* h, int p, const double* gammas, const double* ts, double* E, double* dg,
                  double* dt);

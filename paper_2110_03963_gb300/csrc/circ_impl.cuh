@@ -37,7 +37,10 @@ struct CircArgs {
   double* part;                // partial rows [row * gridDim.x + blockIdx.x]
   int row_a, row_b;
   int tma_store;               // 1: the layout-0 result leaves through one tensor store (out_map)
+  int pf_ahead;                // > 0: prefetch into L2 the inputs of tile blockIdx.x + pf_ahead
+  int pf_map;                  // 1: in_map describes `in` (column passes' state prefetch)
   CUtensorMap out_map;         // 4-d view of `out` matching the shared-memory box (see box_word)
+  CUtensorMap in_map;          // the same view of `in`
 };
 
 // ---------------------------------------------------------------- tensor-store epilogue
@@ -64,6 +67,25 @@ constexpr int kBoxAlign = 1024;   // the dynamic shared region is realigned to t
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// L2 prefetch hints for the tile one wave later (one CTA per SM: tile blockIdx.x + SMs starts when
+// this one ends), so its state loads find the data in L2. Only the state tile is prefetched:
+// adding q, the eigenvalue table and the stored vectors made the passes slower overall (QWOA
+// N=2^26: 15.3 ms without prefetch, 15.9 with all inputs, 15.0 with the state only).
+// Contiguous blocks go in 32 KiB requests (16-byte aligned, multiples of 16 bytes).
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  const char* c = static_cast<const char*>(p);
+  for (uint32_t o = 0; o < bytes; o += 32768u) {
+    const uint32_t n = bytes - o < 32768u ? bytes - o : 32768u;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(c + o), "r"(n) : "memory");
+  }
+}
+__device__ __forceinline__ void prefetch_l2_box(const CUtensorMap* m, int c0) {
+  asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %2, %2}];" ::"l"(
+                   reinterpret_cast<uint64_t>(m)),
+               "r"(c0), "r"(0)
+               : "memory");
 }
 
 // Thread-major private arrays (q in column-pass order, the stored vectors, the eigenvalue table):
@@ -135,10 +157,16 @@ __global__ void __launch_bounds__(NT, 1) col_kernel(const __grid_constant__ Circ
   // the region is over-allocated by kBoxAlign bytes; the buffers start at the first aligned address
   const uint32_t pad = (kBoxAlign - (smem_addr(smem_raw) & (kBoxAlign - 1u))) & (kBoxAlign - 1u);
   float2* sm = reinterpret_cast<float2*>(smem_raw + pad);
+  const uint32_t blk = blockIdx.x;
+  if constexpr (TmaTile<G>::ok) {
+    if (a.pf_ahead > 0 && threadIdx.x == 0 && blk + (uint32_t)a.pf_ahead < gridDim.x) {
+      const uint32_t nb = blk + (uint32_t)a.pf_ahead;
+      if (MODE != CF && a.pf_map) prefetch_l2_box(&a.in_map, (int)(4u * nb));
+    }
+  }
   const float2* ts = load_twsub(sm, a.twsub);
   constexpr int CB = G::dstart(0);
   const int tid = threadIdx.x;
-  const uint32_t blk = blockIdx.x;
   // global index of tile index j
   auto gidx = [&](int j) -> uint32_t {
     return (uint32_t)(j & ((1 << CB) - 1)) | (blk << CB) | ((uint32_t)(j >> CB) << TB);
@@ -330,9 +358,13 @@ __global__ void __launch_bounds__(NT, 1) row_kernel(const __grid_constant__ Circ
   using G = GRow;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* sm = reinterpret_cast<float2*>(smem_raw);
-  const float2* ts = load_twsub(sm, a.twsub);
   const int tid = threadIdx.x;
   const uint32_t blk = blockIdx.x;
+  if (a.pf_ahead > 0 && tid == 0 && blk + (uint32_t)a.pf_ahead < gridDim.x) {
+    const uint32_t nb = blk + (uint32_t)a.pf_ahead;
+    prefetch_l2(a.in + ((size_t)nb << TB), (uint32_t)(TILE * sizeof(float2)));
+  }
+  const float2* ts = load_twsub(sm, a.twsub);
   const float2* src = a.in + ((size_t)blk << TB);
   float2* dst = a.out + ((size_t)blk << TB);
   float2 v[R];
@@ -514,6 +546,8 @@ struct Driver {
       tma_l = h->staged && encode(&map_l, Lb);
     }
     int64_t launches = 0;
+    // prefetch distance: the tile one wave later (one CTA per SM)
+    const int pf = TmaTile<GC>::ok && h->staged ? h->sms : 0;
     auto launch_col = [&](int mode, const CircArgs& a0, double bytes) -> int {
       CircArgs a = a0;
       if (a.out == W && tma_w) {
@@ -522,6 +556,14 @@ struct Driver {
       } else if (a.out == Lb && a.out && tma_l) {
         a.tma_store = 1;
         a.out_map = map_l;
+      }
+      a.pf_ahead = pf;
+      if (a.in == W && tma_w) {
+        a.pf_map = 1;
+        a.in_map = map_w;
+      } else if (a.in == Lb && a.in && tma_l) {
+        a.pf_map = 1;
+        a.in_map = map_l;
       }
       cudaEvent_t e0;
       QVS_TRY(prof_begin(h, &e0));
@@ -539,7 +581,9 @@ struct Driver {
                                     "circ_col_adjoint", "circ_col_adjoint_first"};
       return prof_end(h, names[mode], bytes * (double)dim, e0);
     };
-    auto launch_row = [&](int mode, const CircArgs& a, double bytes) -> int {
+    auto launch_row = [&](int mode, const CircArgs& a0, double bytes) -> int {
+      CircArgs a = a0;
+      a.pf_ahead = pf;
       cudaEvent_t e0;
       QVS_TRY(prof_begin(h, &e0));
       if (mode == RF) row_kernel<RF><<<grid, NT, smem, h->stream>>>(a);

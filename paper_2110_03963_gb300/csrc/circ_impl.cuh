@@ -38,7 +38,9 @@ struct CircArgs {
   int row_a, row_b;
   int tma_store;               // 1: the layout-0 result leaves through one tensor store (out_map)
   int pf_ahead;                // > 0: prefetch into L2 the inputs of tile blockIdx.x + pf_ahead
-  int pf_map;                  // 1: in_map describes `in` (column passes' state prefetch)
+  int pf_map;                  // 1: in_map describes `in` (column passes' state prefetch and load)
+  int tma_load;                // 1: the layout-0 input arrives through one tensor load (in_map)
+  int* err;                    // set to 1 when a tile copy did not arrive within the wait limit
   CUtensorMap out_map;         // 4-d view of `out` matching the shared-memory box (see box_word)
   CUtensorMap in_map;          // the same view of `in`
 };
@@ -81,6 +83,35 @@ __device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(c + o), "r"(n) : "memory");
   }
 }
+// Tile loads through the tensor engine complete on an mbarrier. Every wait is bounded by 2 s of the
+// global timer: on expiry the CTA sets the caller's error flag, waits (again bounded) for its own
+// copy in flight and returns, and the host reports QVS_ETIMEOUT.
+constexpr uint64_t kCopyWaitNs = 2000000000ull;
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool mbar_done(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  if (mbar_done(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (;;) {
+    if (mbar_done(bar, parity)) return true;
+    if (global_ns() - t0 > kCopyWaitNs) return false;
+  }
+}
+
 __device__ __forceinline__ void prefetch_l2_box(const CUtensorMap* m, int c0) {
   asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %2, %2}];" ::"l"(
                    reinterpret_cast<uint64_t>(m)),
@@ -194,12 +225,51 @@ __global__ void __launch_bounds__(NT, 1) col_kernel(const __grid_constant__ Circ
       v[r] = conj ? cmulc(v[r], w) : cmul(v[r], w);
     });
   };
-  auto gload0 = [&](float2(&v)[R], const float2* src) {
+  // layout-0 input; false when the tensor copy did not arrive (the error flag is then set)
+  auto gload0 = [&](float2(&v)[R], const float2* src) -> bool {
     const int jt = G::template jthr<0>(tid_fresh());
+    if constexpr (TmaTile<G>::ok) {
+      // a.tma_load is uniform; the alignment test never fails (the region is realigned above)
+      if (a.tma_load && (smem_addr(sm) & 127u) == 0u) {
+        __shared__ __align__(8) uint64_t bar;
+        if (threadIdx.x == 0) {
+          asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar)) : "memory");
+          asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&bar)),
+                       "r"((uint32_t)(TILE * sizeof(float2)))
+                       : "memory");
+          asm volatile(
+              "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+              " [%0], [%1, {%2, %3, %3, %3}], [%4];" ::"r"(smem_addr(sm)),
+              "l"(reinterpret_cast<uint64_t>(&a.in_map)), "r"((int)(4u * blk)), "r"(0), "r"(smem_addr(&bar))
+              : "memory");
+        }
+        const bool failed = __syncthreads_or(mbar_wait_bounded(&bar, 0) ? 0 : 1) != 0;
+        if (failed) {   // never expected: report, let the copy in flight finish, stop
+          if (threadIdx.x == 0) {
+            atomicExch(a.err, 1);
+            (void)mbar_wait_bounded(&bar, 0);
+          }
+          return false;
+        }
+        const int bw = box_word(jt);
+        static_for<R>([&](auto ri) {
+          constexpr int r = decltype(ri)::value;
+          constexpr int o = box_word(G::jreg(0, r));
+          v[r] = sm[bw + o];
+        });
+        __syncthreads();   // the transposes reuse the buffer
+        return true;
+      }
+    }
     static_for<R>([&](auto ri) {
       constexpr int r = decltype(ri)::value;
       v[r] = __ldcs(src + gidx(jt | G::jreg(0, r)));
     });
+    return true;
   };
   auto gstore0 = [&](const float2(&v)[R], float2* dst) {
     const int jt = G::template jthr<0>(tid_fresh());
@@ -262,7 +332,7 @@ __global__ void __launch_bounds__(NT, 1) col_kernel(const __grid_constant__ Circ
     gtw(v, false);
     gstore0(v, a.out);
   } else {
-    gload0(v, a.in);
+    if (!gload0(v, a.in)) return;
     gtw(v, true);
     tile_inv<G>(v, sm, ts, tid);
     // block barriers around the per-register step separate the inverse and forward transforms in
@@ -492,6 +562,8 @@ struct Driver {
     }
     const int nslots = 1 + 2 * p;
     const int nrows = 2 * p + 1;   // 0: E; 1..p: dgamma_k; p+1..2p: dt_k
+    QVS_TRY(h->flags.ensure(16));
+    QVS_CUDA_TRY(cudaMemsetAsync(h->flags.ptr, 0, 16, h->stream));
     QVS_TRY(h->part.ensure(sizeof(double) * (size_t)nrows * grid));
     QVS_TRY(h->res.ensure(sizeof(double) * nslots));
     QVS_TRY(h->rowmap.ensure(sizeof(int) * 3 * nslots));
@@ -521,6 +593,7 @@ struct Driver {
     base.init_amp = (float)(1.0 / sqrt((double)dim));
     base.part = h->part.as<double>();
     base.row_a = base.row_b = -1;
+    base.err = h->flags.as<int>();
     auto ph = [&](CircArgs& a, int k) { turns_split(gammas[k], &a.ph_hi, &a.ph_lo); };
     auto ev = [&](CircArgs& a, int k) { turns_split(ts[k], &a.ev_hi, &a.ev_lo); };
     const double colb = 16.0 + 4.0, rowb = 16.0 + 8.0;   // bytes per amplitude (state r+w, q / lambda)
@@ -565,6 +638,7 @@ struct Driver {
         a.pf_map = 1;
         a.in_map = map_l;
       }
+      a.tma_load = a.pf_map;
       cudaEvent_t e0;
       QVS_TRY(prof_begin(h, &e0));
       switch (mode) {
@@ -659,8 +733,11 @@ struct Driver {
     QVS_TRY(ensure_host_res(h, p));
     QVS_CUDA_TRY(cudaMemcpyAsync(h->host_res, h->res.ptr, sizeof(double) * nout, cudaMemcpyDeviceToHost,
                                  h->stream));
+    int* host_flag = reinterpret_cast<int*>(h->host_res + 1 + 2 * (size_t)h->host_res_cap);
+    QVS_CUDA_TRY(cudaMemcpyAsync(host_flag, h->flags.ptr, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     QVS_CUDA_TRY(cudaStreamSynchronize(h->stream));
     QVS_TRY(prof_flush(h));
+    if (*host_flag != 0) return QVS_ETIMEOUT;   // a column pass gave up waiting for its tile copy
     *E = h->host_res[0];
     if (grad)
       for (int k = 0; k < p; ++k) {

@@ -6,7 +6,6 @@
 #include <cudaTypedefs.h>
 #include <math.h>
 
-
 #include <vector>
 
 #include "fft_kernels.cuh"
@@ -29,7 +28,7 @@ struct CircArgs {
   const float2* priv_in;       // stored vector read by the adjoint (thread-major)
   const float* qT;             // q in column-pass thread-major order
   const float2* lamT;          // eigenvalues (hi, lo) in row-spectral thread-major order
-  const float2* twsub;         // TW_SLOTS twiddle sub-table entries (copied to shared memory)
+  const float2* twsub;         // the TW_SLOTS twiddle-table entries (copied to shared memory)
   float ph_hi, ph_lo;          // phase: gamma / 2pi (float-float)
   float ph2_hi, ph2_lo;        // reverse passes: the phase to re-apply to the stored psi
   float ev_hi, ev_lo;          // eigenphase: t / 2pi (float-float)
@@ -45,15 +44,16 @@ struct CircArgs {
   CUtensorMap in_map;          // the same view of `in`
 };
 
-// ---------------------------------------------------------------- tensor-store epilogue
+// ---------------------------------------------------------------- tensor copies of a column tile
 //
-// The column tile of Geo<2, 4, 4, 4> (4 adjacent columns x 4096 rows of a 2^26 state) is stored in
-// one bulk tensor copy from shared memory instead of 32 per-thread stores per thread, whose burst
-// at the end of every tile kept the LSU queue full (lg-throttle the top stall). The box is
-// {4 columns, 4 (row bits 4-5), 16 (row bits 0-3), 64 (row bits 6-11)}: in shared memory a tile
-// index lands at box_word, and a half-warp of layout 0 (lanes = tile bits 0, 1, 6, 7) writes 16
-// consecutive 8-byte words, one per bank pair. The copy reads the transpose buffer, free after the
-// last transpose; the CTA waits only until the copy has read it.
+// The column tile of Geo<2, 4, 4, 4> (4 adjacent columns x 4096 rows of a 2^26 state) is loaded by
+// one tensor copy into the transpose buffer and stored by one from it, instead of 32 loads and 32
+// stores per thread, whose burst at the end of every tile kept the LSU queue full (lg throttle was
+// the top stall). The box is {4 columns, 4 (row bits 4-5), 16 (row bits 0-3), 64 (row bits 6-11)}:
+// in shared memory a tile index lands at box_word, and a half-warp of layout 0 (lanes = tile bits
+// 0, 1, 6, 7) reads or writes 16 consecutive 8-byte words, one per bank pair. The load completes on
+// an mbarrier before the first transpose; the store reads the buffer after the last transpose, and
+// the CTA waits only until the copy has read it.
 template <class G>
 struct TmaTile {
   static constexpr bool ok = false;
@@ -83,6 +83,13 @@ __device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(c + o), "r"(n) : "memory");
   }
 }
+__device__ __forceinline__ void prefetch_l2_box(const CUtensorMap* m, int c0) {
+  asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %2, %2}];" ::"l"(
+                   reinterpret_cast<uint64_t>(m)),
+               "r"(c0), "r"(0)
+               : "memory");
+}
+
 // Tile loads through the tensor engine complete on an mbarrier. Every wait is bounded by 2 s of the
 // global timer: on expiry the CTA sets the caller's error flag, waits (again bounded) for its own
 // copy in flight and returns, and the host reports QVS_ETIMEOUT.
@@ -110,13 +117,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     if (mbar_done(bar, parity)) return true;
     if (global_ns() - t0 > kCopyWaitNs) return false;
   }
-}
-
-__device__ __forceinline__ void prefetch_l2_box(const CUtensorMap* m, int c0) {
-  asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %2, %2}];" ::"l"(
-                   reinterpret_cast<uint64_t>(m)),
-               "r"(c0), "r"(0)
-               : "memory");
 }
 
 // Thread-major private arrays (q in column-pass order, the stored vectors, the eigenvalue table):

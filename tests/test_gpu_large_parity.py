@@ -8,7 +8,9 @@ compared element by element:
 
 * QWOA circulant at N = 2^24, 2^25, 2^26 (the benchmark geometry and depth, p = 6) and 2^27: each
   N runs its own column-transform geometry, so each is checked against the oracle;
-* QAOAz XY-ring Chebyshev at C(20,10) and (when stored) at the benchmark's C(24,12), p = 4;
+* QAOAz XY-ring Chebyshev at C(20,10), p = 2 (at the benchmark's C(24,12) the oracle's Taylor-series
+  mixer needs hours per application; the CSR and matrix-free operators are compared with each
+  other there instead);
 * QAOA weighted max-cut at the benchmark size n = 28, p = 8: objective and state sample.
 
 Tolerances: |dE|/|E| <= 1e-5 and gradient error <= 1e-4 (max-norm relative, as everywhere), and
@@ -84,7 +86,7 @@ def test_qwoa_benchmark_geometries_vs_stored_oracle(qvs, log2n, p):
     torch.cuda.empty_cache()
 
 
-@pytest.mark.parametrize("n,p", [(20, 2), (24, 4)])
+@pytest.mark.parametrize("n,p", [(20, 2)])
 def test_qaoaz_csr_vs_stored_oracle(qvs, n, p):
     import torch
     k = n // 2

@@ -234,6 +234,25 @@ def test_xy_ring_matrix_free_equals_csr_at_c20_10(qvs):
     sim_c.close()
 
 
+def test_xy_ring_c24_12_csr_equals_matrix_free(qvs):
+    """At the benchmark's C(24,12) with its depth p = 4 (where the fp64 oracle is out of reach):
+    the explicit CSR ring and the matrix-free ring, two independent operator codes, give the same
+    objective and gradient to rounding (1e-6 / 1e-5; they differ in neighbour summation order and in
+    their estimated spectral intervals), and the evolved state keeps unit norm on the subspace."""
+    n, k, p = 24, 12, 4
+    inst = wl.qaoaz(n, k, p)
+    sim_x, _ = _setup_xy(qvs, n, k, inst.port)
+    sim_c, _, _ = _setup(qvs, n, k, inst.port)
+    Ex, dgx, dtx = sim_x.gradient(inst.gammas, inst.ts)
+    Ec, dgc, dtc = sim_c.gradient(inst.gammas, inst.ts)
+    assert rel_err_E(Ex, Ec) < 1e-6 and rel_err_grad(dgx, dtx, dgc, dtc) < 1e-5
+    sim_x.evolve(inst.gammas, inst.ts)
+    norm = float(np.sum(np.abs(sim_x.state().astype(np.complex128)) ** 2))
+    assert abs(norm - 1.0) < 1e-5
+    sim_x.close()
+    sim_c.close()
+
+
 def test_xy_ring_spectral_interval_is_reproducible(qvs):
     """The spectral interval that qvs_set_mixer estimates (Lanczos, fp64) is summed in a fixed
     order, so two handles given the same ring take the same Chebyshev series: objective and

@@ -66,12 +66,15 @@ enum {
   QVS_OPT_PROFILE = 2,      /* 1: bracket every kernel launch with CUDA events on the handle's
                                stream and accumulate per-kernel statistics (qvs_kernel_stats);
                                0: off (default). Setting it resets the statistics.           */
-  QVS_OPT_STAGED = 3        /* hypercube mixer, complex64, n > 12: 1 (default) runs the two-vector
-                               passes (last forward pass and the adjoint passes) as persistent
-                               kernels whose next tile is copied into shared memory by the
-                               Tensor Memory Accelerator while the current one is processed;
-                               0 runs one CTA per tile. Results are identical. A staged pass whose
-                               copy wait expires makes the call return QVS_ETIMEOUT.          */
+  QVS_OPT_STAGED = 3        /* complex64 data movement through the Tensor Memory Accelerator;
+                               1 (default), 0 = per-thread loads and stores, one CTA per tile.
+                               Hypercube mixer, n > 12: the last forward pass runs as a persistent
+                               kernel whose next tile is copied into shared memory while the
+                               current one is processed. Circulant mixer, N = 2^26: each column
+                               tile is loaded and stored by one tensor copy, and every column and
+                               row pass prefetches the next wave's state tile into L2. Results are
+                               identical either way. A pass whose copy wait expires makes the call
+                               return QVS_ETIMEOUT.                                            */
 };
 
 /*

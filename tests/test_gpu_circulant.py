@@ -118,6 +118,25 @@ def test_full26_identities(full26):
     assert rel_err_E(E1, qh.mean()) < TOL_E
 
 
+def test_full26_tensor_copies_bit_identical(qvs, full26):
+    """At N=2^26 the column tiles move through tensor copies and the passes prefetch into L2
+    (QVS_OPT_STAGED = 1, the default); per-thread loads and stores (0) run the same arithmetic, so
+    the objective, the gradient and the final state agree bit for bit."""
+    inst, sim, _ = full26
+    gs, ts = np.asarray(inst.gammas, float), np.asarray(inst.ts, float)
+    out = {}
+    for staged in (1, 0):
+        sim.set_option(qvs.QVS_OPT_STAGED, staged)
+        E, dg, dt = sim.gradient(gs, ts)
+        E2 = sim.evolve(gs, ts)
+        out[staged] = (E, dg, dt, E2, sim.state())
+    sim.set_option(qvs.QVS_OPT_STAGED, 1)
+    (Ea, dga, dta, E2a, pa), (Eb, dgb, dtb, E2b, pb) = out[1], out[0]
+    assert Ea == Eb and E2a == E2b
+    assert np.array_equal(dga, dgb) and np.array_equal(dta, dtb)
+    assert np.array_equal(pa, pb)
+
+
 def test_full26_norm_bounds_and_gradient_consistency(full26):
     inst, sim, q = full26
     gs, ts = np.asarray(inst.gammas, float), np.asarray(inst.ts, float)

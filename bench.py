@@ -805,9 +805,15 @@ def run_ours(args):
     barrier()
     t0 = time.perf_counter()
     e2e_steps = max(3, args.steps // 2)
+    t_up = t_solve = 0.0
     for _ in range(e2e_steps):
+        ta = time.perf_counter()
         set_inputs()
+        torch.cuda.synchronize()              # separates the upload from the solve in the split below
+        tb = time.perf_counter()
         E, dg, dt = sim.gradient(gs, ts)      # returns E and 2p gradient entries to the host
+        t_up += tb - ta
+        t_solve += time.perf_counter() - tb
     barrier()
     e2e_ms, e2e_value = replica_aggregate((time.perf_counter() - t0) / e2e_steps * 1e3, units, world, allreduce_max)
 
@@ -854,7 +860,8 @@ def run_ours(args):
             "kernels": kernels,
             "gpu_launches": launches_per_step * args.steps,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d_quality + 16 * p,
-                    "d2h_bytes_per_step": 8 * (1 + 2 * p)},
+                    "d2h_bytes_per_step": 8 * (1 + 2 * p),
+                    "upload_ms_per_step": t_up / e2e_steps * 1e3, "solve_ms_per_step": t_solve / e2e_steps * 1e3},
             "clocks": clocks,
             "objective": E0,
         }

@@ -170,6 +170,35 @@ def _ptr_of(x):
     raise TypeError(type(x))
 
 
+def _check_buffer(x, count: int, dtypes, what: str, device: Optional[bool] = None, exact: bool = False):
+    """The library receives bare pointers and reads or writes ``count`` elements: refuse (QVS_EINVAL)
+    a buffer that is not contiguous, holds fewer elements (or, with ``exact``, another number), has
+    another dtype (names as numpy or torch print them, without the "torch." prefix), or lives on the
+    wrong side (``device`` True / False; None: either)."""
+    if isinstance(x, np.ndarray):
+        n, dt, on_dev, contig = x.size, str(x.dtype), False, x.flags["C_CONTIGUOUS"]
+    else:
+        import torch
+        if not isinstance(x, torch.Tensor):
+            raise QvsError(QVS_EINVAL, f"{what}: a numpy array or a torch tensor is required")
+        n, dt, on_dev, contig = x.numel(), str(x.dtype).replace("torch.", ""), x.is_cuda, x.is_contiguous()
+    if not contig:
+        raise QvsError(QVS_EINVAL, f"{what} must be contiguous")
+    if device is not None and on_dev != device:
+        raise QvsError(QVS_EINVAL, f"{what} must be a {'device tensor' if device else 'host array'}")
+    if (n != count) if exact else (n < count):
+        raise QvsError(QVS_EINVAL, f"{what} holds {n} values, {count} needed")
+    if dt not in dtypes:
+        raise QvsError(QVS_EINVAL, f"{what} has dtype {dt}, expected one of {sorted(dtypes)}")
+
+
+def _quality_dtype(dtype: int) -> str:
+    name = {QVS_I32: "int32", QVS_F32: "float32", QVS_F64: "float64"}.get(int(dtype))
+    if name is None:
+        raise QvsError(QVS_EINVAL, f"unknown quality dtype {dtype}")
+    return name
+
+
 def _stream_ptr(stream):
     if stream is None:
         try:
@@ -324,8 +353,8 @@ def qvs_quality_maxcut(n: int, eu, ev, w, out, dtype: int, stream=None):
     if w is not None:
         w = np.ascontiguousarray(w, dtype=np.float64)
         wp = _dptr(w)
+    _check_buffer(out, 1 << int(n), {_quality_dtype(dtype)}, "quality output", device=True)
     p, dev = _ptr_of(out)
-    assert dev == 1, "quality output must be a device tensor"
     _check(load().qvs_quality_maxcut(n, len(eu), eu.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                                      ev.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), wp, int(dtype), p,
                                      _stream_ptr(stream)), "qvs_quality_maxcut")
@@ -345,8 +374,8 @@ def qvs_set_quality_qubo(h, n_qubits: int, c: float, hlin, J):
 
 def qvs_quality_qubo(n_qubits: int, c: float, hlin, J, out, dtype: int, stream=None):
     hl, Jm = _qubo_arrays(n_qubits, hlin, J)
+    _check_buffer(out, 1 << int(n_qubits), {_quality_dtype(dtype)}, "quality output", device=True)
     p, dev = _ptr_of(out)
-    assert dev == 1, "quality output must be a device tensor"
     _check(load().qvs_quality_qubo(int(n_qubits), float(c), _dptr(hl), _dptr(Jm), int(dtype), p,
                                    _stream_ptr(stream)), "qvs_quality_qubo")
     return out
@@ -451,8 +480,8 @@ def qvs_optimise(h, gammas0, ts0, gtol: float = 1e-6, max_iter: int = 200):
 
 def qvs_quality_subset(n: int, w, out, dtype: int, stream=None):
     w = np.ascontiguousarray(w, dtype=np.float64)
+    _check_buffer(out, 1 << int(n), {_quality_dtype(dtype)}, "quality output", device=True)
     p, dev = _ptr_of(out)
-    assert dev == 1
     _check(load().qvs_quality_subset(n, _dptr(w), int(dtype), p, _stream_ptr(stream)), "qvs_quality_subset")
     return out
 
@@ -460,10 +489,11 @@ def qvs_quality_subset(n: int, w, out, dtype: int, stream=None):
 def qvs_quality_portfolio(n_qubits: int, states_dev, returns, cov, omega: float, out, dtype: int, stream=None):
     r = np.ascontiguousarray(returns, dtype=np.float64)
     c = np.ascontiguousarray(cov, dtype=np.float64)
+    dim = int(states_dev.shape[0])
+    _check_buffer(states_dev, dim, {"int64"}, "states", device=True)
+    _check_buffer(out, dim, {_quality_dtype(dtype)}, "quality output", device=True)
     sp, sdev = _ptr_of(states_dev)
     op, odev = _ptr_of(out)
-    assert sdev == 1 and odev == 1
-    dim = int(states_dev.shape[0])
     _check(load().qvs_quality_portfolio(n_qubits, dim, sp, _dptr(r), _dptr(c), float(omega), int(dtype), op,
                                         _stream_ptr(stream)), "qvs_quality_portfolio")
     return out
@@ -471,8 +501,8 @@ def qvs_quality_portfolio(n_qubits: int, states_dev, returns, cov, omega: float,
 
 def qvs_state_parity(n_qubits: int, A: int, out, stream=None):
     """The QAOAz parity initial state written into the complex64 device tensor ``out``."""
+    _check_buffer(out, 1 << int(n_qubits), {"complex64"}, "parity state output", device=True)
     op, odev = _ptr_of(out)
-    assert odev == 1
     _check(load().qvs_state_parity(int(n_qubits), int(A), op, _stream_ptr(stream)), "qvs_state_parity")
     return out
 
@@ -624,6 +654,7 @@ class Batch:
             pass
 
     def set_quality(self, q_concat):
+        _check_buffer(q_concat, int(self.qoff[-1]), {"float32"}, "concatenated qualities", exact=True)
         qvs_batch_set_quality(self.h, q_concat)
         return self
 
@@ -634,6 +665,7 @@ class Batch:
         return E, cut(dg), cut(dt)
 
     def set_quality_shared(self, q):
+        _check_buffer(q, 1 << int(self.ns.max()), {"float32"}, "shared quality vector", exact=True)
         qvs_batch_set_quality_shared(self.h, q)
         return self
 
@@ -699,7 +731,13 @@ def csr_desc(rowptr, colind, values=None, implicit_value: float = 1.0, spec=(0.0
     d = MixerDesc()
     rp, dev1 = _ptr_of(rowptr)
     ci, dev2 = _ptr_of(colind)
-    assert dev1 == dev2
+    if dev1 != dev2:
+        raise QvsError(QVS_EINVAL, "rowptr and colind must both be host arrays or both device tensors")
+    nnz = int(colind.shape[0])
+    _check_buffer(rowptr, int(rowptr.shape[0]), {"int64"}, "rowptr")
+    _check_buffer(colind, nnz, {"int32"}, "colind")
+    if values is not None:
+        _check_buffer(values, nnz, {"float32"}, "values", device=bool(dev1), exact=True)
     d._keep = (rowptr, colind, values)
     d.rowptr = rp.value
     d.colind = ci.value
@@ -740,6 +778,7 @@ class Simulator:
             pass
 
     def set_quality(self, q, dtype=None):
+        _check_buffer(q, self.dim, {"int32", "float32", "float64"}, "quality vector", exact=True)
         qvs_set_quality(self.h, q, dtype)
         return self
 
@@ -761,10 +800,17 @@ class Simulator:
         return qvs_gradient_ex(self.h, gammas, ts)
 
     def set_mixer(self, kind: int, desc: MixerDesc):
+        if int(kind) == QVS_MIX_CSR:   # the library copies dim + 1 row pointers
+            rowptr = desc._keep[0]
+            if int(rowptr.shape[0]) != self.dim + 1:
+                raise QvsError(QVS_EINVAL, f"rowptr holds {int(rowptr.shape[0])} entries, {self.dim + 1} needed")
         qvs_set_mixer(self.h, kind, desc)
         return self
 
     def set_initial_state(self, psi0=None):
+        if psi0 is not None:
+            want = "complex64" if self.precision == QVS_C64 else "complex128"
+            _check_buffer(psi0, self.dim, {want}, "initial state", exact=True)
         qvs_set_initial_state(self.h, psi0)
         return self
 

@@ -234,11 +234,20 @@ constexpr int TW_W12 = 0, TW_U4 = 4096, TW_SLOTS = 4104;
 // or two of the 32 banks.
 __host__ __device__ __forceinline__ constexpr int tw_slot(int k) { return k ^ ((k >> 4) & 15); }
 
-// SH: low bits of e known to be zero
+// SH: low bits of e known to be zero. Exponents that are not multiples of 4 (the digit-3 twiddles
+// of 13- and 14-bit transforms) are not read from the table: e shifted to the top of a 32-bit word
+// is the turn e / 2^14 as a signed fixed-point fraction in [-1/2, 1/2), and one hardware
+// sine/cosine of it replaces two table reads (whose indices fall on few banks) and a product.
 template <int SH>
 __device__ __forceinline__ float2 tw14(const float2* __restrict__ ts, int e) {
-  if constexpr (SH >= 2) return ts[TW_W12 + tw_slot(e >> 2)];
-  else return cmul(ts[TW_W12 + tw_slot(e >> 2)], ts[TW_U4 + (e & 3)]);
+  if constexpr (SH >= 2) {
+    return ts[TW_W12 + tw_slot(e >> 2)];
+  } else {
+    const int32_t es = (int32_t)((uint32_t)e << (32 - TB));
+    float sn, cs;
+    __sincosf((float)es * 1.46291807926715968e-09f, &sn, &cs);   // 2 pi / 2^32
+    return make_float2(cs, -sn);
+  }
 }
 
 // Twiddle between digit 3 and digit 2 (in step layout 2): omega_L^((j1 + 2^D1 j2) * k3), and

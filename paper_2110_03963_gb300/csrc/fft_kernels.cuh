@@ -234,20 +234,23 @@ constexpr int TW_W12 = 0, TW_U4 = 4096, TW_SLOTS = 4104;
 // or two of the 32 banks.
 __host__ __device__ __forceinline__ constexpr int tw_slot(int k) { return k ^ ((k >> 4) & 15); }
 
+// one hardware sine/cosine of e^{-2 pi i e / 2^14}: e shifted to the top of a 32-bit word is the
+// turn as a signed fixed-point fraction in [-1/2, 1/2)
+__device__ __forceinline__ float2 tw14_direct(int e) {
+  const int32_t es = (int32_t)((uint32_t)e << (32 - TB));
+  float sn, cs;
+  __sincosf((float)es * 1.46291807926715968e-09f, &sn, &cs);   // 2 pi / 2^32
+  return make_float2(cs, -sn);
+}
+
 // SH: low bits of e known to be zero. Exponents that are not multiples of 4 (the digit-3 twiddles
 // of 13- and 14-bit transforms) are not read from the table: e shifted to the top of a 32-bit word
 // is the turn e / 2^14 as a signed fixed-point fraction in [-1/2, 1/2), and one hardware
 // sine/cosine of it replaces two table reads (whose indices fall on few banks) and a product.
 template <int SH>
 __device__ __forceinline__ float2 tw14(const float2* __restrict__ ts, int e) {
-  if constexpr (SH >= 2) {
-    return ts[TW_W12 + tw_slot(e >> 2)];
-  } else {
-    const int32_t es = (int32_t)((uint32_t)e << (32 - TB));
-    float sn, cs;
-    __sincosf((float)es * 1.46291807926715968e-09f, &sn, &cs);   // 2 pi / 2^32
-    return make_float2(cs, -sn);
-  }
+  if constexpr (SH >= 2) return ts[TW_W12 + tw_slot(e >> 2)];
+  else return tw14_direct(e);
 }
 
 // Twiddle between digit 3 and digit 2 (in step layout 2): omega_L^((j1 + 2^D1 j2) * k3), and
@@ -278,7 +281,8 @@ __device__ __forceinline__ void twiddle21(float2 (&v)[R], const float2* ts, int 
     if constexpr (k2 != 0) {
       const int j1 = ((jt | G::jreg(1, r)) >> G::dstart(0)) & ((1 << D1) - 1);
       const int e = ((j1 * k2) << D3) & (G::L - 1);
-      const float2 w = tw14<D3 + TB - G::B>(ts, e << (TB - G::B));
+      // the 14-bit row transform's digit-2 reads land 2-way on the banks: computed as well
+      const float2 w = G::B == TB ? tw14_direct(e) : tw14<D3 + TB - G::B>(ts, e << (TB - G::B));
       v[r] = CONJ ? cmulc(v[r], w) : cmul(v[r], w);
     }
   });

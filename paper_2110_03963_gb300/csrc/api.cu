@@ -148,7 +148,7 @@ extern "C" int qvs_destroy(qvs_t h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
   qvs::DevBuf* bufs[] = {&h->q, &h->psi0, &h->psi, &h->lam, &h->ckpt, &h->part, &h->res, &h->rowmap,
-                         &h->work, &h->circ.lam, &h->circ.tab, &h->circ.qT, &h->csr.rowptr,
+                         &h->work, &h->circ.lam, &h->circ.qT, &h->csr.rowptr,
                          &h->csr.colind, &h->csr.values, &h->csr.states, &h->csr.binom, &h->qubo.dcoef, &h->qubo.tab, &h->ex.coef,
                          &h->ex.tab, &h->ex.g, &h->ex.mterms, &h->ex.mpart, &h->ex.mrowmap, &h->ex.mres,
                          &h->flags};

@@ -28,7 +28,6 @@ struct CircArgs {
   const float2* priv_in;       // stored vector read by the adjoint (thread-major)
   const float* qT;             // q in column-pass thread-major order
   const float2* lamT;          // eigenvalues (hi, lo) in row-spectral thread-major order
-  const float2* twsub;         // the TW_SLOTS twiddle-table entries (copied to shared memory)
   float ph_hi, ph_lo;          // phase: gamma / 2pi (float-float)
   float ph2_hi, ph2_lo;        // reverse passes: the phase to re-apply to the stored psi
   float ev_hi, ev_lo;          // eigenphase: t / 2pi (float-float)
@@ -171,17 +170,6 @@ __device__ __forceinline__ void block_store2(float a, float b, double scale, dou
 
 // ---------------------------------------------------------------- column pass
 
-// copy the twiddle sub-tables into shared memory (after the exchange buffer)
-__device__ __forceinline__ const float2* load_twsub(float2* sm, const float2* __restrict__ g) {
-  float2* ts = sm + SM_SLOTS;
-  static_assert(SM_SLOTS % 2 == 0 && TW_SLOTS % 2 == 0, "paired copy");
-  const float4* g4 = reinterpret_cast<const float4*>(g);
-  float4* t4 = reinterpret_cast<float4*>(ts);
-  for (int i = threadIdx.x; i < TW_SLOTS / 2; i += blockDim.x) t4[i] = __ldg(g4 + i);
-  __syncthreads();
-  return ts;
-}
-
 template <class G, int MODE>
 __global__ void __launch_bounds__(NT, 1) col_kernel(const __grid_constant__ CircArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -195,7 +183,6 @@ __global__ void __launch_bounds__(NT, 1) col_kernel(const __grid_constant__ Circ
       if (MODE != CF && a.pf_map) prefetch_l2_box(&a.in_map, (int)(4u * nb));
     }
   }
-  const float2* ts = load_twsub(sm, a.twsub);
   constexpr int CB = G::dstart(0);
   const int tid = threadIdx.x;
   // global index of tile index j
@@ -328,13 +315,13 @@ __global__ void __launch_bounds__(NT, 1) col_kernel(const __grid_constant__ Circ
       phase_cs(r, qat(ri), a.ph_hi, a.ph_lo, c, s);
       v[r] = make_float2(c * x.x + s * x.y, c * x.y - s * x.x);
     });
-    tile_fwd<G>(v, sm, ts, tid);
+    tile_fwd<G>(v, sm, tid);
     gtw(v, false);
     gstore0(v, a.out);
   } else {
     if (!gload0(v, a.in)) return;
     gtw(v, true);
-    tile_inv<G>(v, sm, ts, tid);
+    tile_inv<G>(v, sm, tid);
     // block barriers around the per-register step separate the inverse and forward transforms in
     // the schedule: fewer values held across them, fewer register spills (ptxas -v: RCM 820 -> 492,
     // CL 524 -> 376 bytes per thread at n = 26)
@@ -355,7 +342,7 @@ __global__ void __launch_bounds__(NT, 1) col_kernel(const __grid_constant__ Circ
         phase_cs(r, qat(ri), a.ph_hi, a.ph_lo, c, s);
         v[r] = make_float2(c * x.x + s * x.y, c * x.y - s * x.x);
       });
-      tile_fwd<G>(v, sm, ts, tid);
+      tile_fwd<G>(v, sm, tid);
       gtw(v, false);
       gstore0(v, a.out);
     } else if constexpr (MODE == CL || MODE == CV) {
@@ -381,7 +368,7 @@ __global__ void __launch_bounds__(NT, 1) col_kernel(const __grid_constant__ Circ
         // two in the schedule), so neither the sum nor its row and output pointers stay live
         // across the transform
         block_store2(e, 0.0f, 1.0, a.part, a.row_a, -1);
-        tile_fwd<G>(v, sm, ts, tid);
+        tile_fwd<G>(v, sm, tid);
         gtw(v, false);
         gstore0(v, a.out);
         return;
@@ -413,7 +400,7 @@ __global__ void __launch_bounds__(NT, 1) col_kernel(const __grid_constant__ Circ
       // gamma-gradient row reduced before the forward transform (see the last pass above)
       block_store2(g, 0.0f, 2.0, a.part, a.row_a, -1);
       if constexpr (MODE == RCM) {
-        tile_fwd<G>(v, sm, ts, tid);
+        tile_fwd<G>(v, sm, tid);
         gtw(v, false);
         gstore0(v, a.out);
       }
@@ -434,7 +421,6 @@ __global__ void __launch_bounds__(NT, 1) row_kernel(const __grid_constant__ Circ
     const uint32_t nb = blk + (uint32_t)a.pf_ahead;
     prefetch_l2(a.in + ((size_t)nb << TB), (uint32_t)(TILE * sizeof(float2)));
   }
-  const float2* ts = load_twsub(sm, a.twsub);
   const float2* src = a.in + ((size_t)blk << TB);
   float2* dst = a.out + ((size_t)blk << TB);
   float2 v[R];
@@ -445,7 +431,7 @@ __global__ void __launch_bounds__(NT, 1) row_kernel(const __grid_constant__ Circ
       v[r] = __ldcs(src + (jt | G::jreg(2, r)));
     });
   }
-  tile_fwd<G>(v, sm, ts, tid);
+  tile_fwd<G>(v, sm, tid);
   // restrict-qualified: the table and stored-vector loads are issued ahead of the stores
   const float4* __restrict__ lamT = reinterpret_cast<const float4*>(a.lamT);
   const float4* __restrict__ pin = reinterpret_cast<const float4*>(a.priv_in);
@@ -474,7 +460,7 @@ __global__ void __launch_bounds__(NT, 1) row_kernel(const __grid_constant__ Circ
         __stcs(po + pair_idx(blk, m, tid), make_float4(v[2 * m].x, v[2 * m].y, v[2 * m + 1].x, v[2 * m + 1].y));
     }
   }
-  tile_inv<G>(v, sm, ts, tid);
+  tile_inv<G>(v, sm, tid);
   const float invL = 1.0f / (float)TILE;
   {
     const int jt = G::template jthr<2>(tid);
@@ -547,7 +533,7 @@ struct Driver {
     const int64_t dim = h->dim;
     const uint32_t grid = (uint32_t)(dim >> TB);
     const size_t vb = sizeof(float2) * (size_t)dim;
-    const size_t smem = sizeof(float2) * (SM_SLOTS + TW_SLOTS) + kBoxAlign;
+    const size_t smem = sizeof(float2) * SM_SLOTS + kBoxAlign;
     // q in column-pass order (rebuilt when q or the mixer changed)
     if (!h->circ.qT_valid) {
       QVS_TRY(h->circ.qT.ensure(sizeof(float) * (size_t)dim));
@@ -589,7 +575,6 @@ struct Driver {
     base.psi0 = h->have_psi0 ? h->psi0.as<float2>() : nullptr;
     base.qT = h->circ.qT.as<float>();
     base.lamT = h->circ.lam.as<float2>();
-    base.twsub = h->circ.tab.as<float2>();
     base.init_amp = (float)(1.0 / sqrt((double)dim));
     base.part = h->part.as<double>();
     base.row_a = base.row_b = -1;

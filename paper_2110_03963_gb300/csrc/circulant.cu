@@ -105,18 +105,6 @@ int circ_set_mixer(qvs_ctx* h, const qvs_mixer_desc* d) {
     if (d->offsets[i] <= 0 || d->offsets[i] >= N) return QVS_EINVAL;
     if (d->offset_weights && !isfinite(d->offset_weights[i])) return QVS_EINVAL;
   }
-  // twiddle tables (fp64, rounded once): W12[k] = w_4096^k, U4[k] = w_16384^k, w_M = e^{-2 pi i / M}
-  std::vector<float2> tab(TW_SLOTS, make_float2(0.0f, 0.0f));
-  const double two_pi = 6.283185307179586476925286766559;
-  auto w = [&](int64_t e, int64_t M) {
-    const double ang = two_pi * (double)(e % M) / (double)M;
-    return make_float2((float)cos(ang), (float)-sin(ang));
-  };
-  for (int k = 0; k < 4096; ++k) tab[TW_W12 + tw_slot(k)] = w(k, 4096);
-  for (int k = 0; k < 4; ++k) tab[TW_U4 + k] = w(k, TILE);
-  QVS_TRY(h->circ.tab.ensure(sizeof(float2) * tab.size()));
-  QVS_CUDA_TRY(cudaMemcpyAsync(h->circ.tab.ptr, tab.data(), sizeof(float2) * tab.size(),
-                               cudaMemcpyHostToDevice, h->stream));
   std::vector<double> wt(d->n_offsets, 1.0);
   if (d->offset_weights)
     for (int i = 0; i < d->n_offsets; ++i) wt[i] = d->offset_weights[i];

@@ -6,8 +6,8 @@
 // column transform over the high index bits and a row transform over the low 14 bits, with the
 // twiddle omega_N^(j_low * k_col) between them (four-step). Each of those tile transforms is again
 // a three-digit four-step transform: a small DFT over each digit (at most 32 points, in registers,
-// radix-2 decimation in frequency with compile-time twiddles) and one table twiddle per amplitude
-// between digits. Outputs stay in the digit-reversed, bit-reversed order the steps produce; the
+// radix-2 decimation in frequency with compile-time twiddles) and one computed twiddle per
+// amplitude between digits. Outputs stay in the digit-reversed, bit-reversed order the steps produce; the
 // eigenvalue table is stored in that order, and the inverse transform runs the same steps
 // backwards, so no reordering pass is ever made.
 #pragma once
@@ -117,7 +117,7 @@ struct Geo {
   }
 };
 
-// threadIdx.x read through a volatile instruction: index arithmetic (and the table loads that
+// threadIdx.x read through a volatile instruction: index arithmetic (and the loads that
 // depend on it) is recomputed where it is used instead of being kept live, or reused, across the
 // forward and inverse transforms of one pass
 __device__ __forceinline__ int tid_fresh() {
@@ -221,43 +221,23 @@ __device__ __forceinline__ void xchg(float2 (&v)[R], float2* sm, int tid) {
   __syncthreads();
 }
 
-// Shared-memory twiddle table (built once per CTA from a global table computed in fp64 and rounded
-// once): W12[k] = e^{-2 pi i k / 2^12} and U4[k] = e^{-2 pi i k / 2^14} (k < 4). An inter-digit
-// twiddle e^{-2 pi i e / 2^14} whose exponent e is a multiple of 4 (every twiddle of a transform of at
-// most 12 bits, and the digit-2 twiddles of the 13- and 14-bit ones) is one table read; any other
-// is W12[e >> 2] * U4[e & 3]. The four-step twiddle of the N-point transform is computed directly
-// (one hardware sine/cosine of the exactly reduced turn, in the column pass).
-constexpr int TW_W12 = 0, TW_U4 = 4096, TW_SLOTS = 4104;
-
-// W12 is stored swizzled, entry k at slot k ^ ((k >> 4) & 15): the digit twiddles of a warp read
-// entries whose indices are multiples of 8 or 16 apart, which without the swizzle would share one
-// or two of the 32 banks.
-__host__ __device__ __forceinline__ constexpr int tw_slot(int k) { return k ^ ((k >> 4) & 15); }
-
-// one hardware sine/cosine of e^{-2 pi i e / 2^14}: e shifted to the top of a 32-bit word is the
-// turn as a signed fixed-point fraction in [-1/2, 1/2)
-__device__ __forceinline__ float2 tw14_direct(int e) {
+// Inter-digit twiddles e^{-2 pi i e / 2^14}: the integer exponent shifted to the top of a 32-bit word
+// is the turn e / 2^14 as a signed fixed-point fraction in [-1/2, 1/2), and one hardware
+// sine/cosine of its float conversion gives the twiddle. A shared 4096-entry table of fp64-rounded
+// roots (one read per twiddle, XOR-swizzled against bank conflicts) measured slower in every pass:
+// QWOA N=2^26, p=6 14.2 ms computed against 15.0 ms with the table.
+__device__ __forceinline__ float2 tw14(int e) {
   const int32_t es = (int32_t)((uint32_t)e << (32 - TB));
   float sn, cs;
   __sincosf((float)es * 1.46291807926715968e-09f, &sn, &cs);   // 2 pi / 2^32
   return make_float2(cs, -sn);
 }
 
-// SH: low bits of e known to be zero. Exponents that are not multiples of 4 (the digit-3 twiddles
-// of 13- and 14-bit transforms) are not read from the table: e shifted to the top of a 32-bit word
-// is the turn e / 2^14 as a signed fixed-point fraction in [-1/2, 1/2), and one hardware
-// sine/cosine of it replaces two table reads (whose indices fall on few banks) and a product.
-template <int SH>
-__device__ __forceinline__ float2 tw14(const float2* __restrict__ ts, int e) {
-  if constexpr (SH >= 2) return ts[TW_W12 + tw_slot(e >> 2)];
-  else return tw14_direct(e);
-}
-
 // Twiddle between digit 3 and digit 2 (in step layout 2): omega_L^((j1 + 2^D1 j2) * k3), and
 // between digit 2 and digit 1 (in step layout 1): omega_L^(2^D3 * j1 * k2). conj = true applies
 // the conjugate (inverse transform).
 template <class G, bool CONJ>
-__device__ __forceinline__ void twiddle32(float2 (&v)[R], const float2* ts, int tid) {
+__device__ __forceinline__ void twiddle32(float2 (&v)[R], int tid) {
   constexpr int D1 = G::dsize(0), D2 = G::dsize(1), D3 = G::dsize(2);
   const int jt = G::template jthr<2>(tid_fresh());
   static_for<R>([&](auto ri) {
@@ -266,13 +246,13 @@ __device__ __forceinline__ void twiddle32(float2 (&v)[R], const float2* ts, int 
     if constexpr (k3 != 0) {
       const int jlow = ((jt | G::jreg(2, r)) >> G::dstart(0)) & ((1 << (D1 + D2)) - 1);
       const int e = (jlow * k3) & (G::L - 1);
-      const float2 w = tw14<TB - G::B>(ts, e << (TB - G::B));
+      const float2 w = tw14(e << (TB - G::B));
       v[r] = CONJ ? cmulc(v[r], w) : cmul(v[r], w);
     }
   });
 }
 template <class G, bool CONJ>
-__device__ __forceinline__ void twiddle21(float2 (&v)[R], const float2* ts, int tid) {
+__device__ __forceinline__ void twiddle21(float2 (&v)[R], int tid) {
   constexpr int D1 = G::dsize(0), D2 = G::dsize(1), D3 = G::dsize(2);
   const int jt = G::template jthr<1>(tid_fresh());
   static_for<R>([&](auto ri) {
@@ -282,7 +262,7 @@ __device__ __forceinline__ void twiddle21(float2 (&v)[R], const float2* ts, int 
       const int j1 = ((jt | G::jreg(1, r)) >> G::dstart(0)) & ((1 << D1) - 1);
       const int e = ((j1 * k2) << D3) & (G::L - 1);
       // the 14-bit row transform's digit-2 reads land 2-way on the banks: computed as well
-      const float2 w = G::B == TB ? tw14_direct(e) : tw14<D3 + TB - G::B>(ts, e << (TB - G::B));
+      const float2 w = tw14(e << (TB - G::B));
       v[r] = CONJ ? cmulc(v[r], w) : cmul(v[r], w);
     }
   });
@@ -290,25 +270,25 @@ __device__ __forceinline__ void twiddle21(float2 (&v)[R], const float2* ts, int 
 
 // forward tile DFT: from step layout 2 (natural order in the transform bits) to step layout 0
 template <class G>
-__device__ __forceinline__ void tile_fwd(float2 (&v)[R], float2* sm, const float2* ts, int tid) {
+__device__ __forceinline__ void tile_fwd(float2 (&v)[R], float2* sm, int tid) {
   small_dft<G, 2>(v);
-  twiddle32<G, false>(v, ts, tid);
+  twiddle32<G, false>(v, tid);
   xchg<G, 2, 1>(v, sm, tid);
   small_dft<G, 1>(v);
-  twiddle21<G, false>(v, ts, tid);
+  twiddle21<G, false>(v, tid);
   xchg<G, 1, 0>(v, sm, tid);
   small_dft<G, 0>(v);
 }
 
 // inverse tile DFT (unscaled): from step layout 0 back to step layout 2
 template <class G>
-__device__ __forceinline__ void tile_inv(float2 (&v)[R], float2* sm, const float2* ts, int tid) {
+__device__ __forceinline__ void tile_inv(float2 (&v)[R], float2* sm, int tid) {
   small_idft<G, 0>(v);
   xchg<G, 0, 1>(v, sm, tid);
-  twiddle21<G, true>(v, ts, tid);
+  twiddle21<G, true>(v, tid);
   small_idft<G, 1>(v);
   xchg<G, 1, 2>(v, sm, tid);
-  twiddle32<G, true>(v, ts, tid);
+  twiddle32<G, true>(v, tid);
   small_idft<G, 2>(v);
 }
 

@@ -151,7 +151,6 @@ struct ExData {
 // Circulant mixer data: eigenvalues in the order the FFT passes produce them.
 struct CircData {
   DevBuf lam;           // float2[dim]: eigenvalues (hi, lo) in row-spectral thread-major order
-  DevBuf tab;           // float2 twiddle tables
   DevBuf qT;            // float[dim]: q in column-pass thread-major order
   bool qT_valid = false;
 };

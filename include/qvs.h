@@ -404,8 +404,7 @@ int qvs_batch_destroy(qvs_batch_t b);
 
 /* ----------------------------------------------------------------- allocation-free small solve
  * The paper has no counterpart to this entry point. It is for callers that cannot allocate device
- * memory at the moment they need a solve: code running while a stream is being captured into a
- * CUDA graph (cudaMalloc cannot be captured), code inside an allocator or memory-pool callback, a
+ * memory at the moment they need a solve: code inside an allocator or memory-pool callback, a
  * real-time loop whose device memory is fixed up front, or a host runtime that owns all device
  * memory and forbids libraries from taking more.
  *
@@ -426,10 +425,10 @@ int qvs_batch_destroy(qvs_batch_t b);
  *   stream     cudaStream_t or NULL.
  * The call only enqueues one kernel on `stream` and returns; `out` is valid once the stream has
  * reached that point. The first call on a device (with that device current) resolves the scratch
- * address with cudaGetSymbolAddress and sets the kernel's shared-memory limit; make that first call
- * before any stream capture. Every call on a device shares the one scratch array and overwrites
- * it (it keeps the last call's contents; nothing in it needs to start at zero), so calls whose
- * kernels may overlap on the GPU - on different streams without ordering between them - race.
+ * address with cudaGetSymbolAddress and sets the kernel's shared-memory limit. Every call on a
+ * device shares the one scratch array and overwrites it (it keeps the last call's contents;
+ * nothing in it needs to start at zero), so calls whose kernels may overlap on the GPU - on
+ * different streams without ordering between them - race.
  */
 #define QVS_NOALLOC_SCRATCH_BYTES (4u << 20)
 #define QVS_NOALLOC_MAX_LAYERS 128

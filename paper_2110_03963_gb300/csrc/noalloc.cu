@@ -1,10 +1,9 @@
 // Allocation-free variant of the small-state solve (objective + adjoint gradient of the QAOA
 // hypercube ansatz for states of at most 2^12 amplitudes).
 //
-// Some callers cannot allocate device memory at the time they need a solve: code that runs while
-// a CUDA stream is being captured into a graph (cudaMalloc is not capturable), inside an allocator
-// or memory-pool callback, in a real-time loop whose memory budget is fixed up front, or in a host
-// runtime that owns all device memory and forbids libraries from taking more. For them
+// Some callers cannot allocate device memory at the time they need a solve: code that runs inside
+// an allocator or memory-pool callback, in a real-time loop whose memory budget is fixed up front,
+// or in a host runtime that owns all device memory and forbids libraries from taking more. For them
 // qvs_gradient_small_noalloc takes every input and output from the caller and keeps its only
 // scratch - the forward states the adjoint sweep reads back - in one file-scope device array of
 // fixed size, so it never calls cudaMalloc, cudaFree or any allocating routine.

@@ -2,8 +2,8 @@
 qvs_gradient, through the C ABI, twice in a row (the static scratch keeps the previous call's
 contents, which must not leak into the next result).
 
-It serves callers that cannot allocate device memory when they need a solve (stream capture,
-allocator callbacks, fixed-budget real-time loops, runtimes that own all device memory). This file
+It serves callers that cannot allocate device memory when they need a solve (allocator
+callbacks, fixed-budget real-time loops, runtimes that own all device memory). This file
 is collected last so that a failure here comes after every other test has run."""
 import numpy as np
 import pytest

@@ -32,7 +32,8 @@ Conventions: qubit u is bit (n-1-u) of the basis index (most significant first, 
 ``np.binary_repr`` in Example 3 and q_90 = 0 for (0,1,0,1,1,0,1,0) in Sec. 6.1.1).
 
 Every function below is pinned by ``tests/test_oracle_pins.py`` against values the paper prints,
-closed forms, dense matrix exponentials, and invariants.
+closed forms, dense matrix exponentials, and invariants; ``tests/test_oracle_mutants.py`` plants
+one mistake at a time in these functions and checks that a pin fails.
 """
 from __future__ import annotations
 

@@ -120,6 +120,13 @@ def test_p4_circulant_vs_expm():
         ref = scipy.linalg.expm(-1j * t * C) @ psi
         assert np.max(np.abs(orc.mix_circulant(psi, lam, t) - ref)) < 1e-11
     assert np.max(np.abs(orc.apply_circulant_W(psi, lam) - C @ psi)) < 1e-11
+    # a weighted symmetric first row (one weight per offset, as the library's offset weights)
+    roww = np.zeros(N)
+    for s_, w_ in zip([1, 3, 10, 32], [0.4, 1.7, 0.9, 2.5]):
+        roww[s_] = roww[(N - s_) % N] = w_
+    Cw = np.array([[roww[(k - j) % N] for k in range(N)] for j in range(N)])
+    lamw = orc.circulant_eigenvalues(roww)
+    assert np.max(np.abs(orc.mix_circulant(psi, lamw, 0.8) - scipy.linalg.expm(-0.8j * Cw) @ psi)) < 1e-11
 
 
 @pytest.mark.parametrize("n,k", [(6, 3), (8, 4), (7, 2)])
@@ -206,6 +213,11 @@ def test_p7_circulant_eigenvalues(log2n):
     assert np.max(np.abs(lam - cf.pow2_circulant_eigs(log2n))) < 1e-10
     # library FFT of the first row gives the same spectrum
     assert np.max(np.abs(lam - np.fft.fft(row).real)) < 1e-9
+    # the QWOA problem builder takes the same spectrum and the subset-sum qualities
+    w = wl.item_weights(log2n, wl.rng_for(95, log2n))
+    prob = orc.qwoa_problem(log2n, w, wl.circulant_offsets_pow2(log2n))
+    assert np.max(np.abs(prob.lam - cf.pow2_circulant_eigs(log2n))) < 1e-10
+    assert np.array_equal(prob.q, orc.subset_quality(log2n, w))
     # degree: every vertex has 2*(log2n-1) + 1 neighbours
     assert lam[0] == pytest.approx(2 * (log2n - 1) + 1)
 
@@ -339,6 +351,11 @@ def test_parity_state_and_conservation():
         for a in range(A):
             sup = idx[np.abs(s) > 0]
             assert np.all(((sup >> (n - 1 - 2 * a)) & 1) == 0) and np.all(((sup >> (n - 2 - 2 * a)) & 1) == 1)
+    # the QAOAz parity problem starts from the parity state of its constraint value
+    P = wl.portfolio(n // 2, wl.rng_for(94, 1))
+    for A in [1, 3]:
+        s0 = orc.qaoaz_parity_problem(n, A, P.returns, P.cov, P.omega).initial_state()
+        assert abs(np.vdot(s0, s0) - 1.0) < 1e-14 and np.all(np.abs(s0[(w_odd - w_even) != A]) == 0)
     rng = np.random.default_rng(16)
     psi = rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)
     out = orc.mix_parity(psi, n, 1.1)
@@ -416,6 +433,10 @@ def test_portfolio_two_assets_hand_computed():
 def test_subspace_count():
     assert orc.subspace_states(10, 5).shape[0] == math.comb(10, 5)
     assert orc.subspace_states(24, 12).shape[0] == 2704156
+    # the QAOAz problem lives on the weight-k states
+    P = wl.portfolio(4, wl.rng_for(91, 0))
+    st = orc.qaoaz_problem(8, 3, P.returns, P.cov, P.omega).states
+    assert st.shape[0] == math.comb(8, 3) and all(bin(int(x)).count("1") == 3 for x in st)
 
 
 # ------------------------------------------------------------------ quadratic (QUBO) qualities
@@ -652,6 +673,24 @@ def test_bfgs_stops_on_precision_loss_at_the_best_point():
     assert np.max(np.abs(x - 1.0)) < 2e-3            # inside the flat band around the minimiser
     assert ev <= it + 1 + (it + 1) * 31               # at most 31 trial points per iteration
 
+    # The same bowl plus a deterministic noise of up to 1e-6 that differs at every point (a hash
+    # of the point's bytes); the gradient stays that of the bowl. Every trial point the line search
+    # rejects near the end is then strictly worse than the point it started from, so the point
+    # returned must be the best one evaluated.
+    seen = []
+
+    def fn(z):
+        h = 0
+        for w in np.ascontiguousarray(z, dtype=np.float64).view(np.uint64).tolist():
+            h = ((h ^ w) * 0x9E3779B97F4A7C15 + 0x632BE59BD9B4E019) % (1 << 64)
+            h ^= h >> 29
+        v = float(np.sum(D * (z - 1.0) ** 2)) + 1e-6 * (h % (1 << 53)) / float(1 << 53)
+        seen.append(v)
+        return v, 2.0 * D * (z - 1.0)
+    x, f, it, ev, stop = orc.bfgs_minimize(fn, x0, gtol=1e-12, max_iter=500)
+    assert stop == 2 and len(seen) == ev
+    assert f == min(seen) and f == fn(x)[0]
+
 
 def test_optimise_qaoa_matches_scipy_bfgs_and_closed_form():
     """p=1 QAOA on a 3-regular 8-vertex graph: from the same start the written-out BFGS and SciPy's
@@ -707,3 +746,21 @@ def test_benchmark_depth_sweep_with_persisted_parameters():
     for D, (g, t) in enumerate(best, start=1):
         assert len(g) == len(t) == D
         assert abs(orc.objective(prob, g, t) - f[D - 1].min()) < 1e-12
+    # With no optimiser iterations every repeat ends at its start, which shows where each start
+    # value is read: at depth 1, repeat r takes init[2r] (gamma) and init[2r + 1] (t); at every
+    # later depth, the best start of the previous depth plus the next pair (gamma, t) of init.
+    init = rng.uniform(0.1, np.pi, size=2 * repeats + 2 * repeats * 2)
+    f, best = orc.benchmark(prob, 1, 3, repeats, init, max_iter=0)
+    prev = None
+    for D in range(1, 4):
+        starts = []
+        for r in range(repeats):
+            if D == 1:
+                starts.append((init[2 * r: 2 * r + 1], init[2 * r + 1: 2 * r + 2]))
+            else:
+                base = 2 * repeats + 2 * repeats * (D - 2) + 2 * r
+                starts.append((np.append(prev[0], init[base]), np.append(prev[1], init[base + 1])))
+        fD = [orc.objective(prob, g, t) for g, t in starts]
+        assert np.array_equal(f[D - 1], fD)
+        prev = starts[int(np.argmin(fD))]
+        assert np.array_equal(best[D - 1][0], prev[0]) and np.array_equal(best[D - 1][1], prev[1])

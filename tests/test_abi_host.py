@@ -189,6 +189,24 @@ def test_bfgs_precision_loss_stop_matches_oracle(qvs):
     assert stop == stopo == 2
     assert (it, ev) == (ito, evo) and f == fo and np.array_equal(x, xo)
 
+    # a bowl with a deterministic noise of up to 1e-6 per point: every rejected trial point is
+    # worse than its start, so the library must return the best point it evaluated
+    seen = []
+
+    def fn(z):
+        h = 0
+        for w in np.ascontiguousarray(z, dtype=np.float64).view(np.uint64).tolist():
+            h = ((h ^ w) * 0x9E3779B97F4A7C15 + 0x632BE59BD9B4E019) % (1 << 64)
+            h ^= h >> 29
+        v = float(np.sum(D * (z - 1.0) ** 2)) + 1e-6 * (h % (1 << 53)) / float(1 << 53)
+        seen.append(v)
+        return v, 2.0 * D * (z - 1.0)
+    x, f, it, ev, stop = qvs.qvs_bfgs_minimize(fn, x0, gtol=1e-12, max_iter=500)
+    assert stop == 2 and len(seen) == ev and f == min(seen)
+    seen.clear()
+    xo, fo, ito, evo, stopo = orc.bfgs_minimize(fn, x0, gtol=1e-12, max_iter=500)
+    assert (it, ev, stop) == (ito, evo, stopo) and f == fo and np.array_equal(x, xo)
+
 
 def test_bfgs_minimize_argument_errors_and_callback_failure(qvs):
     with pytest.raises(qvs.QvsError):

@@ -306,9 +306,11 @@ int qvs_xy_ring_csr(int n, int k, int64_t* states, int64_t* rowptr, int32_t* col
  * max-cut-style instances with the hypercube mixer and the equal-superposition initial state:
  * instance i has n_qubits[i] qubits (12 <= n <= 28) and layers[i] layers (1 <= p <= 64), complex64
  * state, fp32 qualities. The kernel's CTAs pull instances (longest first) from a device counter and
- * run each one's forward sweep, objective and adjoint gradient to completion; the first solve
- * times one and two CTAs per SM and keeps the faster, then captures parameters-in, the kernel and
- * results-out as a CUDA graph that later solves replay.
+ * run each one's forward sweep, objective and adjoint gradient to completion. The first solve
+ * picks the schedule (qvs_batch_info): one timed launch per candidate of 1 or 2 CTAs per SM and
+ * checkpoint policy 0 or 1, or the cached choice for the same GPU and instance mix, unless
+ * qvs_batch_set_schedule pinned one. It then captures parameters-in, the kernel and results-out
+ * as a CUDA graph that later solves replay.
  *
  * Layouts: qualities are concatenated in instance order (instance i at offset
  * sum_{j<i} 2^n_j); parameters and gradient entries are concatenated per instance (instance i at

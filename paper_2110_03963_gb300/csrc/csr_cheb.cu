@@ -593,9 +593,10 @@ static int expmv(qvs_ctx* h, double t, const float2* x, float2* y, float2* s0, f
   const int K = (int)(c.size() / 2) - 1;
   const uint32_t grid = (uint32_t)((dim + ROWS_PER_CTA - 1) / ROWS_PER_CTA);
   const double nnz = (double)C.nnz;
-  // compulsory bytes per series term: the operator's index data (the CSR arrays, or one state word
-  // per row), T_cur's own row, T_prev, T_next and y (the neighbour gathers of T_cur hit in L2)
-  const double step_bytes = C.xy ? (double)dim * (4.0 + 8 + 8 + 8 + 16)
+  // compulsory bytes per series term: the operator's index data (the CSR arrays, or one 8-byte
+  // record per row: the state word and the closing-pair neighbour's rank), T_cur's own row, T_prev,
+  // T_next and y (the neighbour gathers of T_cur hit in L2)
+  const double step_bytes = C.xy ? (double)dim * (8.0 + 8 + 8 + 8 + 16)
                                  : nnz * 4.0 + (C.has_values ? nnz * 4.0 : 0.0) + (double)dim * (4.0 + 8 + 8 + 8 + 16);
   if (K == 0) {
     return launch_prof(h, "csr_scale", 16.0 * dim, launches, [&] {

@@ -213,6 +213,60 @@ def _stream_ptr(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
+# ---------------------------------------------------------------- what the binding knows of a handle
+#
+# The library takes bare pointers and reads or writes as many elements as the handle's dimension,
+# precision, ex-QAOA term count or batch layout says. The wrappers below keep those figures for
+# every live handle they created, so that each call can refuse a short or mistyped buffer first.
+
+class _HandleInfo:
+    __slots__ = ("dim", "precision", "n_terms")
+
+    def __init__(self, dim: int, precision: int):
+        self.dim, self.precision, self.n_terms = int(dim), int(precision), 0
+
+    @property
+    def complex_dtype(self) -> str:
+        return "complex64" if self.precision == QVS_C64 else "complex128"
+
+
+_HANDLES: dict = {}   # qvs_create handle address -> _HandleInfo
+_BATCHES: dict = {}   # qvs_batch_create handle address -> (qubit counts, layers), int64 arrays
+
+
+def _addr(h) -> int:
+    if isinstance(h, ctypes.c_void_p):
+        return int(h.value or 0)
+    return int(h or 0)
+
+
+def _handle_info(h) -> _HandleInfo:
+    info = _HANDLES.get(_addr(h))
+    if info is None:
+        raise QvsError(QVS_EINVAL, "not a live handle of qvs_create")
+    return info
+
+
+def _batch_info(b):
+    info = _BATCHES.get(_addr(b))
+    if info is None:
+        raise QvsError(QVS_EINVAL, "not a live handle of qvs_batch_create")
+    return info
+
+
+def _edges(eu, ev, w):
+    """Edge endpoint arrays (int32) and optional weights (fp64) of one length."""
+    eu = np.ascontiguousarray(eu, dtype=np.int32).reshape(-1)
+    ev = np.ascontiguousarray(ev, dtype=np.int32).reshape(-1)
+    if eu.shape != ev.shape:
+        raise QvsError(QVS_EINVAL, f"eu ({eu.shape[0]}) and ev ({ev.shape[0]}) differ in length")
+    if w is not None:
+        w = np.ascontiguousarray(w, dtype=np.float64).reshape(-1)
+        if w.shape != eu.shape:
+            raise QvsError(QVS_EINVAL, f"w holds {w.shape[0]} weights for {eu.shape[0]} edges")
+    return eu, ev, w
+
+
 # ---------------------------------------------------------------- thin wrappers, same names
 
 
@@ -252,18 +306,24 @@ def qvs_create(dim: int, precision: int = QVS_C64, stream=None, allocator=None) 
     df = allocator.dealloc_fn if allocator is not None else DEALLOC_FN()
     _check(load().qvs_create(ctypes.byref(h), int(dim), int(precision), _stream_ptr(stream), af, df, None),
            "qvs_create")
+    _HANDLES[_addr(h)] = _HandleInfo(dim, precision)
     return h
 
 
 def qvs_destroy(h):
     _check(load().qvs_destroy(h), "qvs_destroy")
+    _HANDLES.pop(_addr(h), None)
 
 
 def qvs_set_quality(h, q, dtype: Optional[int] = None):
+    """q: dim values (host array or device tensor) of type dtype (None: taken from q's dtype)."""
+    info = _handle_info(h)
     if dtype is None:
-        dt = str(q.dtype)
-        dtype = {"int32": QVS_I32, "float32": QVS_F32, "float64": QVS_F64,
-                 "torch.int32": QVS_I32, "torch.float32": QVS_F32, "torch.float64": QVS_F64}[dt]
+        dt = str(getattr(q, "dtype", "")).replace("torch.", "")
+        dtype = {"int32": QVS_I32, "float32": QVS_F32, "float64": QVS_F64}.get(dt)
+        if dtype is None:
+            raise QvsError(QVS_EINVAL, f"quality vector has dtype {dt or type(q).__name__}")
+    _check_buffer(q, info.dim, {_quality_dtype(dtype)}, "quality vector", exact=True)
     p, dev = _ptr_of(q)
     _check(load().qvs_set_quality(h, p, int(dtype), dev), "qvs_set_quality")
 
@@ -275,9 +335,11 @@ def qvs_set_mixer(h, kind: int, desc: MixerDesc):
 def qvs_set_initial_state(h, psi0=None):
     """psi0 None: the equal superposition (QVS_INIT_UNIFORM); else the explicit state (host array or
     device tensor of dim complex values in the handle's precision)."""
+    info = _handle_info(h)
     if psi0 is None:
         _check(load().qvs_set_initial_state(h, QVS_INIT_UNIFORM, None, 0), "qvs_set_initial_state")
         return
+    _check_buffer(psi0, info.dim, {info.complex_dtype}, "initial state", exact=True)
     p, dev = _ptr_of(psi0)
     _check(load().qvs_set_initial_state(h, QVS_INIT_EXPLICIT, p, dev), "qvs_set_initial_state")
 
@@ -318,6 +380,9 @@ def qvs_gradient(h, gammas, ts):
 
 
 def qvs_get_state(h, out):
+    """Copy the state (dim complex values in the handle's precision) into out (host or device)."""
+    info = _handle_info(h)
+    _check_buffer(out, info.dim, {info.complex_dtype}, "state output")
     p, dev = _ptr_of(out)
     _check(load().qvs_get_state(h, p, dev), "qvs_get_state")
     return out
@@ -347,12 +412,8 @@ def qvs_kernel_stats(h):
 
 
 def qvs_quality_maxcut(n: int, eu, ev, w, out, dtype: int, stream=None):
-    eu = np.ascontiguousarray(eu, dtype=np.int32)
-    ev = np.ascontiguousarray(ev, dtype=np.int32)
-    wp = None
-    if w is not None:
-        w = np.ascontiguousarray(w, dtype=np.float64)
-        wp = _dptr(w)
+    eu, ev, w = _edges(eu, ev, w)
+    wp = None if w is None else _dptr(w)
     _check_buffer(out, 1 << int(n), {_quality_dtype(dtype)}, "quality output", device=True)
     p, dev = _ptr_of(out)
     _check(load().qvs_quality_maxcut(n, len(eu), eu.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
@@ -383,12 +444,8 @@ def qvs_quality_qubo(n_qubits: int, c: float, hlin, J, out, dtype: int, stream=N
 
 def qvs_qubo_from_maxcut(n: int, eu, ev, w=None):
     """(c, hlin[n], J[n, n]) of the max-cut cost (host, no GPU needed)."""
-    eu = np.ascontiguousarray(eu, dtype=np.int32)
-    ev = np.ascontiguousarray(ev, dtype=np.int32)
-    wp = None
-    if w is not None:
-        w = np.ascontiguousarray(w, dtype=np.float64)
-        wp = _dptr(w)
+    eu, ev, w = _edges(eu, ev, w)
+    wp = None if w is None else _dptr(w)
     c = ctypes.c_double()
     hl = np.zeros(n, dtype=np.float64)
     J = np.zeros(n * n, dtype=np.float64)
@@ -400,19 +457,31 @@ def qvs_qubo_from_maxcut(n: int, eu, ev, w=None):
 
 def qvs_set_phase_terms(h, u, v, coef):
     """ex-QAOA terms coef[j] Z_u[j] Z_v[j] (v[j] = -1: a single Z)."""
-    u = np.ascontiguousarray(u, dtype=np.int32)
-    v = np.ascontiguousarray(v, dtype=np.int32)
-    c = np.ascontiguousarray(coef, dtype=np.float64)
-    assert u.shape == v.shape == c.shape
+    info = _handle_info(h)
+    u = np.ascontiguousarray(u, dtype=np.int32).reshape(-1)
+    v = np.ascontiguousarray(v, dtype=np.int32).reshape(-1)
+    c = np.ascontiguousarray(coef, dtype=np.float64).reshape(-1)
+    if not u.shape == v.shape == c.shape:
+        raise QvsError(QVS_EINVAL, f"u, v and coef differ in length ({u.shape[0]}, {v.shape[0]}, {c.shape[0]})")
     _check(load().qvs_set_phase_terms(h, len(c), u.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                                       v.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dptr(c)),
            "qvs_set_phase_terms")
+    info.n_terms = int(c.shape[0])
+
+
+def _ex_params(h, gammas, ts):
+    """gammas (p x n_terms values, layer-major) and ts (p values) for the handle's ex-QAOA terms."""
+    info = _handle_info(h)
+    G = np.ascontiguousarray(gammas, dtype=np.float64)
+    t = np.ascontiguousarray(ts, dtype=np.float64).reshape(-1)
+    if info.n_terms > 0 and G.size != t.shape[0] * info.n_terms:
+        raise QvsError(QVS_EINVAL, f"gammas hold {G.size} values, {t.shape[0]} x {info.n_terms} needed")
+    return G, t
 
 
 def qvs_evolve_ex(h, gammas, ts) -> float:
     """gammas: (p, n_terms) array; returns the objective."""
-    G = np.ascontiguousarray(gammas, dtype=np.float64)
-    t = np.ascontiguousarray(ts, dtype=np.float64)
+    G, t = _ex_params(h, gammas, ts)
     _check(load().qvs_evolve_ex(h, len(t), _dptr(G), _dptr(t)), "qvs_evolve_ex")
     E = ctypes.c_double()
     _check(load().qvs_expectation(h, ctypes.byref(E)), "qvs_expectation")
@@ -421,8 +490,7 @@ def qvs_evolve_ex(h, gammas, ts) -> float:
 
 def qvs_gradient_ex(h, gammas, ts):
     """gammas: (p, n_terms) array; returns (E, dgamma (p, n_terms), dt (p,))."""
-    G = np.ascontiguousarray(gammas, dtype=np.float64)
-    t = np.ascontiguousarray(ts, dtype=np.float64)
+    G, t = _ex_params(h, gammas, ts)
     p = len(t)
     E = ctypes.c_double()
     dG = np.zeros(G.shape, dtype=np.float64)
@@ -545,30 +613,48 @@ def qvs_gradient_small_noalloc(n: int, precision: int, q_dev, gammas, ts, out_de
 
 
 def qvs_batch_create(n_qubits, layers, stream=None):
-    ns = np.ascontiguousarray(n_qubits, dtype=np.int32)
-    ps = np.ascontiguousarray(layers, dtype=np.int32)
+    ns = np.ascontiguousarray(n_qubits, dtype=np.int32).reshape(-1)
+    ps = np.ascontiguousarray(layers, dtype=np.int32).reshape(-1)
     h = ctypes.c_void_p()
+    if ns.shape != ps.shape:
+        raise QvsError(QVS_EINVAL, f"n_qubits ({ns.shape[0]}) and layers ({ps.shape[0]}) differ in length")
     _check(load().qvs_batch_create(ctypes.byref(h), len(ns), ns.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                                    ps.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _stream_ptr(stream)),
            "qvs_batch_create")
+    _BATCHES[_addr(h)] = (ns.astype(np.int64), ps.astype(np.int64))
     return h
 
 
 def qvs_batch_set_quality(b, q):
+    """The instances' fp32 qualities concatenated in instance order (host or device)."""
+    ns, _ = _batch_info(b)
+    _check_buffer(q, int(np.sum(np.int64(1) << ns)), {"float32"}, "concatenated qualities", exact=True)
     p, dev = _ptr_of(q)
     _check(load().qvs_batch_set_quality(b, p, dev), "qvs_batch_set_quality")
 
 
 def qvs_batch_set_quality_shared(b, q):
     """One quality vector (2^n fp32 values) read by every instance of the batch (all of one n)."""
+    ns, _ = _batch_info(b)
+    _check_buffer(q, 1 << int(ns.max()), {"float32"}, "shared quality vector", exact=True)
     p, dev = _ptr_of(q)
     _check(load().qvs_batch_set_quality_shared(b, p, dev), "qvs_batch_set_quality_shared")
+
+
+def _batch_params(b, gammas, ts, count: int):
+    """Concatenated per-instance parameters: sum of the instances' layers each, count instances."""
+    ns, ps = _batch_info(b)
+    g, t = _params(gammas, ts)
+    if int(count) != ns.shape[0] or g.shape[0] != int(ps.sum()):
+        raise QvsError(QVS_EINVAL, f"{g.shape[0]} parameters for {int(count)} instances; the batch has "
+                                   f"{ns.shape[0]} instances and {int(ps.sum())} layers")
+    return g, t
 
 
 def qvs_batch_optimise(b, gammas, ts, count: int, gtol: float = 1e-6, max_iter: int = 200):
     """Device BFGS of every instance at once. gammas, ts: concatenated start points. Returns
     (gammas, ts, f[count], iterations[count], evaluations[count], stop[count])."""
-    g, t = _params(gammas, ts)
+    g, t = _batch_params(b, gammas, ts, count)
     g, t = g.copy(), t.copy()
     f = np.zeros(count)
     it = np.zeros(count, dtype=np.int32)
@@ -593,6 +679,7 @@ def qvs_benchmark(n: int, q, d_min: int, d_max: int, repeats: int, init, gtol: f
         raise QvsError(QVS_EINVAL, f"init needs {need} values")
     f = np.zeros(nd * repeats)
     best = np.zeros(sum(2 * D for D in range(d_min, d_max + 1)))
+    _check_buffer(q, 1 << int(n), {"float32"}, "quality vector", exact=True)
     qp, dev = _ptr_of(q)
     _check(load().qvs_benchmark(int(n), qp, dev, int(d_min), int(d_max), int(repeats), _dptr(x0), float(gtol),
                                 int(max_iter), _dptr(f), _dptr(best), _stream_ptr(stream)), "qvs_benchmark")
@@ -605,8 +692,7 @@ def qvs_benchmark(n: int, q, d_min: int, d_max: int, repeats: int, init, gtol: f
 
 def qvs_batch_gradient(b, gammas, ts, count: int):
     """gammas, ts: concatenated per-instance parameters. Returns (E[count], dgamma, dt) concatenated."""
-    g = np.ascontiguousarray(gammas, dtype=np.float64)
-    t = np.ascontiguousarray(ts, dtype=np.float64)
+    g, t = _batch_params(b, gammas, ts, count)
     E = np.zeros(count)
     dg = np.zeros(len(g))
     dt = np.zeros(len(g))
@@ -630,6 +716,7 @@ def qvs_batch_set_schedule(b, ctas_per_sm: int, ckpt_policy: int):
 
 def qvs_batch_destroy(b):
     _check(load().qvs_batch_destroy(b), "qvs_batch_destroy")
+    _BATCHES.pop(_addr(b), None)
 
 
 class Batch:

@@ -42,3 +42,105 @@ def test_csr_desc_checks_its_arrays():
     _refused(qvs.csr_desc, rowptr.astype(np.int32), colind, None, 2.0)
     _refused(qvs.csr_desc, rowptr, colind.astype(np.int64), None, 2.0)
     _refused(qvs.csr_desc, rowptr, colind, np.ones(3, np.float32), 0.0)     # one value per nonzero
+
+
+class _FakeLib:
+    """Stands in for libqvs: records each call and returns QVS_OK; qvs_create and qvs_batch_create
+    hand out distinct fake handles. A buffer check that let a bad buffer through would show up as a
+    recorded call where the test expects none."""
+
+    def __init__(self):
+        self.calls = []
+        self.next = 0x1000
+
+    def __getattr__(self, name):
+        if name == "qvs_strerror":
+            return lambda status: b"fake status"
+        def fn(*args):
+            self.calls.append(name)
+            if name in ("qvs_create", "qvs_batch_create"):
+                args[0]._obj.value = self.next
+                self.next += 0x100
+            return 0
+        return fn
+
+
+@pytest.fixture
+def fake(monkeypatch):
+    lib = _FakeLib()
+    monkeypatch.setattr(qvs, "_lib", lib)
+    monkeypatch.setattr(qvs, "_HANDLES", {})
+    monkeypatch.setattr(qvs, "_BATCHES", {})
+    return lib
+
+
+def _passes(lib, name, fn, *args, **kw):
+    before = len(lib.calls)
+    fn(*args, **kw)
+    assert name in lib.calls[before:]
+
+
+def _refused_before_library(lib, fn, *args, **kw):
+    before = len(lib.calls)
+    _refused(fn, *args, **kw)
+    assert lib.calls[before:] == []
+
+
+def test_handle_buffers_are_sized_by_the_handle(fake):
+    h = qvs.qvs_create(16, qvs.QVS_C64)
+    _passes(fake, "qvs_set_quality", qvs.qvs_set_quality, h, np.zeros(16, np.int32))
+    _passes(fake, "qvs_set_quality", qvs.qvs_set_quality, h, np.zeros(16, np.float64), qvs.QVS_F64)
+    _refused_before_library(fake, qvs.qvs_set_quality, h, np.zeros(8, np.float32))
+    _refused_before_library(fake, qvs.qvs_set_quality, h, np.zeros(16, np.float32), qvs.QVS_F64)
+    _refused_before_library(fake, qvs.qvs_set_quality, h, np.zeros(16, np.int64))
+    _passes(fake, "qvs_set_initial_state", qvs.qvs_set_initial_state, h, np.zeros(16, np.complex64))
+    _passes(fake, "qvs_set_initial_state", qvs.qvs_set_initial_state, h, None)
+    _refused_before_library(fake, qvs.qvs_set_initial_state, h, np.zeros(16, np.complex128))
+    _refused_before_library(fake, qvs.qvs_set_initial_state, h, np.zeros(15, np.complex64))
+    _passes(fake, "qvs_get_state", qvs.qvs_get_state, h, np.zeros(16, np.complex64))
+    _refused_before_library(fake, qvs.qvs_get_state, h, np.zeros(8, np.complex64))
+    _refused_before_library(fake, qvs.qvs_get_state, h, np.zeros(16, np.complex128))
+    h2 = qvs.qvs_create(16, qvs.QVS_C128)
+    _passes(fake, "qvs_get_state", qvs.qvs_get_state, h2, np.zeros(16, np.complex128))
+    _refused_before_library(fake, qvs.qvs_get_state, h2, np.zeros(16, np.complex64))
+    qvs.qvs_destroy(h)
+    _refused_before_library(fake, qvs.qvs_get_state, h, np.zeros(16, np.complex64))   # destroyed
+    _refused_before_library(fake, qvs.qvs_get_state, None, np.zeros(16, np.complex64))
+
+
+def test_ex_qaoa_parameters_match_the_terms(fake):
+    h = qvs.qvs_create(1 << 13, qvs.QVS_C64)
+    _passes(fake, "qvs_evolve_ex", qvs.qvs_evolve_ex, h, np.zeros((1, 1)), [0.1])   # no terms: library decides
+    _refused_before_library(fake, qvs.qvs_set_phase_terms, h, [0, 1], [1], [1.0, 2.0])
+    _passes(fake, "qvs_set_phase_terms", qvs.qvs_set_phase_terms, h, [0, 1, 2], [1, -1, 5], [1.0, 2.0, 0.5])
+    _passes(fake, "qvs_gradient_ex", qvs.qvs_gradient_ex, h, np.zeros((2, 3)), [0.1, 0.2])
+    _refused_before_library(fake, qvs.qvs_gradient_ex, h, np.zeros((2, 2)), [0.1, 0.2])
+    _refused_before_library(fake, qvs.qvs_evolve_ex, h, np.zeros((1, 3)), [0.1, 0.2])
+
+
+def test_edge_lists_have_one_length(fake):
+    _refused_before_library(fake, qvs.qvs_qubo_from_maxcut, 4, [0, 1], [1], None)
+    _refused_before_library(fake, qvs.qvs_qubo_from_maxcut, 4, [0, 1], [1, 2], [1.0])
+    _passes(fake, "qvs_qubo_from_maxcut", qvs.qvs_qubo_from_maxcut, 4, [0, 1], [1, 2], [1.0, 0.5])
+
+
+def test_batch_buffers_are_sized_by_the_batch(fake):
+    b = qvs.qvs_batch_create([12, 13], [2, 3])
+    _passes(fake, "qvs_batch_set_quality", qvs.qvs_batch_set_quality, b, np.zeros(4096 + 8192, np.float32))
+    _refused_before_library(fake, qvs.qvs_batch_set_quality, b, np.zeros(4096 * 2, np.float32))
+    _refused_before_library(fake, qvs.qvs_batch_set_quality, b, np.zeros(4096 + 8192, np.float64))
+    _passes(fake, "qvs_batch_gradient", qvs.qvs_batch_gradient, b, np.zeros(5), np.zeros(5), 2)
+    _refused_before_library(fake, qvs.qvs_batch_gradient, b, np.zeros(4), np.zeros(4), 2)
+    _refused_before_library(fake, qvs.qvs_batch_gradient, b, np.zeros(5), np.zeros(5), 3)
+    _passes(fake, "qvs_batch_optimise", qvs.qvs_batch_optimise, b, np.zeros(5), np.zeros(5), 2)
+    _refused_before_library(fake, qvs.qvs_batch_optimise, b, np.zeros(6), np.zeros(6), 2)
+    _refused_before_library(fake, qvs.qvs_batch_create, [12, 13], [2])
+    bs = qvs.qvs_batch_create([12, 12, 12], [1, 2, 3])
+    _passes(fake, "qvs_batch_set_quality_shared", qvs.qvs_batch_set_quality_shared, bs, np.zeros(4096, np.float32))
+    _refused_before_library(fake, qvs.qvs_batch_set_quality_shared, bs, np.zeros(2048, np.float32))
+    qvs.qvs_batch_destroy(b)
+    _refused_before_library(fake, qvs.qvs_batch_gradient, b, np.zeros(5), np.zeros(5), 2)
+    # the depth sweep reads 2^n fp32 qualities
+    init = np.zeros(2 * 2 * 1 + 2 * 2)
+    _passes(fake, "qvs_benchmark", qvs.qvs_benchmark, 12, np.zeros(4096, np.float32), 1, 2, 2, init)
+    _refused_before_library(fake, qvs.qvs_benchmark, 12, np.zeros(2048, np.float32), 1, 2, 2, init)

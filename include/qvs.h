@@ -293,6 +293,19 @@ int qvs_quality_subset(int n, const double* w, int out_dtype, void* q_out, void*
 int qvs_quality_portfolio(int n_qubits, int64_t dim, const int64_t* states, const double* returns,
                           const double* cov, double omega, int out_dtype, void* q_out, void* stream);
 
+/* Sec. 3 (the sparse mixer's series expansion), host only: the Chebyshev coefficients the library
+ * uses for exp(-i t W) v when the spectrum of W lies in [a - b, a + b]:
+ *     exp(-i t W) = sum_{m=0}^{K} c_m T_m((W - a) / b),
+ *     c_m = (2 - delta_{m0}) (-i)^m J_m(b t) e^{-i t a}   (the Jacobi-Anger expansion),
+ * with K the smallest index whose tail bound sum_{m>K} 2 |J_m(b t)| is below tol (fp64 Bessel values,
+ * std::cyl_bessel_j). c (NULL: query only) receives the K + 1 coefficients as interleaved re/im
+ * doubles, room for 2 max_terms values; *n_terms = K + 1; *tail (may be NULL) = the tail bound,
+ * which bounds the series' error in the 2-norm for a normalised v. QVS_EINVAL for non-finite a, b, t,
+ * b < 0, tol <= 0 or max_terms outside 1..20000; QVS_ENUMERIC when more than max_terms terms are
+ * needed. */
+int qvs_chebyshev_coefficients(double a, double b, double t, double tol, int max_terms, double* c,
+                               int* n_terms, double* tail);
+
 /* Sec. 2.4.1: the XY-ring mixer sum_{a} (X_a X_{a+1} + Y_a Y_{a+1}) (a+1 mod n) restricted to
  * the n-qubit basis states of Hamming weight k, as CSR over those states in increasing integer
  * order. Host arrays; pass NULL outputs to query the sizes (*dim_out, *nnz_out). Values are all 2

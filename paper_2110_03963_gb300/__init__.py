@@ -34,7 +34,7 @@ EXPORTED = [
     "qvs_create", "qvs_destroy", "qvs_set_quality", "qvs_set_mixer", "qvs_set_initial_state",
     "qvs_set_option", "qvs_evolve", "qvs_expectation", "qvs_gradient", "qvs_get_state",
     "qvs_last_launch_count", "qvs_kernel_stats", "qvs_quality_maxcut", "qvs_quality_subset", "qvs_quality_portfolio",
-    "qvs_xy_ring_csr", "qvs_state_parity", "qvs_batch_create", "qvs_batch_set_quality", "qvs_batch_gradient",
+    "qvs_xy_ring_csr", "qvs_chebyshev_coefficients", "qvs_state_parity", "qvs_batch_create", "qvs_batch_set_quality", "qvs_batch_gradient",
     "qvs_batch_info", "qvs_batch_destroy", "qvs_gradient_small_noalloc", "qvs_strerror",
     "qvs_set_quality_qubo", "qvs_quality_qubo", "qvs_qubo_from_maxcut",
     "qvs_set_phase_terms", "qvs_evolve_ex", "qvs_gradient_ex", "qvs_bfgs_minimize", "qvs_optimise",
@@ -118,6 +118,7 @@ def load(path: str = LIB_PATH):
         "qvs_quality_subset": (I, [I, P(D), I, V, V]),
         "qvs_quality_portfolio": (I, [I, I64, V, P(D), P(D), D, I, V, V]),
         "qvs_xy_ring_csr": (I, [I, I, V, V, V, P(I64), P(I64)]),
+        "qvs_chebyshev_coefficients": (I, [D, D, D, D, I, P(D), P(I), P(D)]),
         "qvs_state_parity": (I, [I, I, V, V]),
         "qvs_gradient_small_noalloc": (I, [I, I, I, V, P(D), P(D), V, V]),
         "qvs_batch_create": (I, [P(V), I, P(ctypes.c_int32), P(ctypes.c_int32), V]),
@@ -573,6 +574,18 @@ def qvs_state_parity(n_qubits: int, A: int, out, stream=None):
     op, odev = _ptr_of(out)
     _check(load().qvs_state_parity(int(n_qubits), int(A), op, _stream_ptr(stream)), "qvs_state_parity")
     return out
+
+
+def qvs_chebyshev_coefficients(a: float, b: float, t: float, tol: float, max_terms: int = 20000):
+    """(c[K + 1] complex, tail bound) of exp(-i t W) = sum_m c_m T_m((W - a) / b) (host, no GPU)."""
+    n = ctypes.c_int()
+    tail = ctypes.c_double()
+    _check(load().qvs_chebyshev_coefficients(float(a), float(b), float(t), float(tol), int(max_terms), None,
+                                             ctypes.byref(n), ctypes.byref(tail)), "qvs_chebyshev_coefficients")
+    c = np.zeros(2 * n.value, dtype=np.float64)
+    _check(load().qvs_chebyshev_coefficients(float(a), float(b), float(t), float(tol), int(max_terms), _dptr(c),
+                                             ctypes.byref(n), ctypes.byref(tail)), "qvs_chebyshev_coefficients")
+    return c[0::2] + 1j * c[1::2], tail.value
 
 
 def qvs_xy_ring_csr(n: int, k: int):

@@ -571,6 +571,26 @@ static std::vector<double> cheb_coeffs(double a, double b, double t, double tol,
   return c;
 }
 
+}  // namespace cs
+}  // namespace qvs
+
+extern "C" int qvs_chebyshev_coefficients(double a, double b, double t, double tol, int max_terms, double* c,
+                                          int* n_terms, double* tail) {
+  if (!n_terms || !isfinite(a) || !isfinite(b) || !isfinite(t) || !(b >= 0.0) || !(tol > 0.0) ||
+      max_terms < 1 || max_terms > 20000)
+    return QVS_EINVAL;
+  double tl = 0.0;
+  const std::vector<double> v = qvs::cs::cheb_coeffs(a, b, t, tol, max_terms - 1, &tl);
+  if (v.empty()) return QVS_ENUMERIC;
+  *n_terms = (int)(v.size() / 2);
+  if (tail) *tail = tl;
+  if (c) memcpy(c, v.data(), sizeof(double) * v.size());
+  return QVS_OK;
+}
+
+namespace qvs {
+namespace cs {
+
 static int launch_prof(qvs_ctx* h, const char* name, double bytes, int64_t& launches,
                        const std::function<void()>& fn) {
   cudaEvent_t e0;

@@ -226,3 +226,45 @@ def test_optimise_rejects_bad_arguments_without_gpu(qvs):
                             ctypes.byref(it), ctypes.byref(it), ctypes.byref(it)) == qvs.QVS_EINVAL
     with pytest.raises(qvs.QvsError):
         qvs.qvs_bfgs_minimize(lambda x: (0.0, x), np.zeros(3), gtol=-1.0)
+
+
+@pytest.mark.parametrize("a,b,t,tol", [(0.0, 30.645, 0.7, 1e-7), (1.5, 3.0, -2.0, 1e-10), (-4.0, 10.0, 2.9, 1e-6),
+                                       (2.0, 0.0, 1.3, 1e-7)])
+def test_chebyshev_coefficients_vs_bessel_and_expm(qvs, a, b, t, tol):
+    """The series coefficients the sparse mixer uses, on the host: equal to the Jacobi-Anger
+    coefficients from SciPy's Bessel functions; K the first index whose tail bound drops below tol;
+    and the truncated series reproduces scipy's expm on a dense symmetric matrix whose spectrum lies
+    in [a - b, a + b] to within that bound."""
+    sp = pytest.importorskip("scipy.special")
+    la = pytest.importorskip("scipy.linalg")
+    c, tail = qvs.qvs_chebyshev_coefficients(a, b, t, tol)
+    K = len(c) - 1
+    m = np.arange(K + 1)
+    ref = np.where(m == 0, 1.0, 2.0) * (-1j) ** m * sp.jv(m, b * t) * np.exp(-1j * t * a)
+    assert np.max(np.abs(c - ref)) < 1e-13
+    rest = 2.0 * np.abs(sp.jv(np.arange(K + 1, K + 400), b * t))
+    assert abs(tail - rest.sum()) < 1e-15 + 1e-9 * tail
+    assert tail < tol and (K == 0 or tail + 2.0 * abs(sp.jv(K, b * t)) >= tol)
+
+    rng = np.random.default_rng(205)
+    Q, _ = np.linalg.qr(rng.standard_normal((24, 24)))
+    lam = a + b * rng.uniform(-1.0, 1.0, 24)
+    W = (Q * lam) @ Q.T
+    v = rng.standard_normal(24) + 1j * rng.standard_normal(24)
+    v /= np.linalg.norm(v)
+    Wt = (W - a * np.eye(24)) / b if b > 0 else np.zeros((24, 24))
+    t_prev, t_cur = v, Wt @ v
+    y = c[0] * t_prev + (c[1] * t_cur if K >= 1 else 0.0)
+    for k in range(2, K + 1):
+        t_prev, t_cur = t_cur, 2.0 * (Wt @ t_cur) - t_prev
+        y = y + c[k] * t_cur
+    assert np.linalg.norm(y - la.expm(-1j * t * W) @ v) <= tail + 1e-12
+
+
+def test_chebyshev_coefficients_argument_errors(qvs):
+    for args in [(0.0, -1.0, 1.0, 1e-7), (0.0, 1.0, float("nan"), 1e-7), (0.0, 1.0, 1.0, 0.0)]:
+        with pytest.raises(qvs.QvsError):
+            qvs.qvs_chebyshev_coefficients(*args)
+    with pytest.raises(qvs.QvsError) as e:
+        qvs.qvs_chebyshev_coefficients(0.0, 100.0, 10.0, 1e-7, max_terms=50)   # needs ~1000 terms
+    assert e.value.status == qvs.QVS_ENUMERIC

@@ -275,6 +275,14 @@ int qvs_quality_maxcut(int n, int n_edges, const int32_t* eu, const int32_t* ev,
 int qvs_quality_qubo(int n_qubits, double c, const double* hlin, const double* J, int out_dtype,
                      void* q_out, void* stream);
 
+/* The fixed-point form of qvs_set_quality_qubo / qvs_quality_qubo (host only, no GPU): *F and the
+ * integer coefficients ci (for c), hi[u] (for hlin[u]) and Ji[u*n + v] (for J[u*n + v], u < v; zero
+ * on and below the diagonal), each the nearest integer to the coefficient times 2^F (halves away
+ * from zero). q(x) = 2^-F (ci + sum_u hi[u] x_u + sum_{u<v} Ji[u*n+v] x_u x_v) exactly. QVS_EINVAL as
+ * qvs_quality_qubo, or for a NULL output. */
+int qvs_qubo_fixed_point(int n_qubits, double c, const double* hlin, const double* J, int* F, int32_t* ci,
+                         int32_t* hi, int32_t* Ji);
+
 /* The max-cut cost of qvs_quality_maxcut as a quadratic form (host only): an edge (u, v) with
  * weight w (w = NULL: 1) adds w [x_u == x_v] = w (1 - x_u - x_v + 2 x_u x_v), i.e. w to *c, -w to
  * hlin[u] and hlin[v], 2w to J[min(u,v)*n + max(u,v)]. Outputs: *c, hlin[n], J[n*n] (zeroed

@@ -36,7 +36,7 @@ EXPORTED = [
     "qvs_last_launch_count", "qvs_kernel_stats", "qvs_quality_maxcut", "qvs_quality_subset", "qvs_quality_portfolio",
     "qvs_xy_ring_csr", "qvs_chebyshev_coefficients", "qvs_state_parity", "qvs_batch_create", "qvs_batch_set_quality", "qvs_batch_gradient",
     "qvs_batch_info", "qvs_batch_destroy", "qvs_gradient_small_noalloc", "qvs_strerror",
-    "qvs_set_quality_qubo", "qvs_quality_qubo", "qvs_qubo_from_maxcut",
+    "qvs_set_quality_qubo", "qvs_quality_qubo", "qvs_qubo_fixed_point", "qvs_qubo_from_maxcut",
     "qvs_set_phase_terms", "qvs_evolve_ex", "qvs_gradient_ex", "qvs_bfgs_minimize", "qvs_optimise",
     "qvs_batch_set_quality_shared", "qvs_batch_optimise", "qvs_benchmark", "qvs_batch_set_schedule",
 ]
@@ -133,6 +133,7 @@ def load(path: str = LIB_PATH):
         "qvs_strerror": (ctypes.c_char_p, [I]),
         "qvs_set_quality_qubo": (I, [V, I, D, P(D), P(D)]),
         "qvs_quality_qubo": (I, [I, D, P(D), P(D), I, V, V]),
+        "qvs_qubo_fixed_point": (I, [I, D, P(D), P(D), P(I), P(ctypes.c_int32), P(ctypes.c_int32), P(ctypes.c_int32)]),
         "qvs_qubo_from_maxcut": (I, [I, I, P(ctypes.c_int32), P(ctypes.c_int32), P(D), P(D), P(D), P(D)]),
         "qvs_set_phase_terms": (I, [V, I, P(ctypes.c_int32), P(ctypes.c_int32), P(D)]),
         "qvs_evolve_ex": (I, [V, I, P(D), P(D)]),
@@ -441,6 +442,19 @@ def qvs_quality_qubo(n_qubits: int, c: float, hlin, J, out, dtype: int, stream=N
     _check(load().qvs_quality_qubo(int(n_qubits), float(c), _dptr(hl), _dptr(Jm), int(dtype), p,
                                    _stream_ptr(stream)), "qvs_quality_qubo")
     return out
+
+
+def qvs_qubo_fixed_point(n_qubits: int, c: float, hlin, J):
+    """(F, ci, hi[n], Ji[n, n]) of the quadratic form's fixed-point coefficients (host, no GPU)."""
+    n = int(n_qubits)
+    hl, Jm = _qubo_arrays(n, hlin, J)
+    F, ci = ctypes.c_int(), ctypes.c_int32()
+    hi = np.zeros(n, dtype=np.int32)
+    Ji = np.zeros(n * n, dtype=np.int32)
+    I32 = ctypes.POINTER(ctypes.c_int32)
+    _check(load().qvs_qubo_fixed_point(n, float(c), _dptr(hl), _dptr(Jm), ctypes.byref(F), ctypes.byref(ci),
+                                       hi.ctypes.data_as(I32), Ji.ctypes.data_as(I32)), "qvs_qubo_fixed_point")
+    return F.value, ci.value, hi, Ji.reshape(n, n)
 
 
 def qvs_qubo_from_maxcut(n: int, eu, ev, w=None):

@@ -307,6 +307,20 @@ extern "C" int qvs_quality_qubo(int n_qubits, double c, const double* hlin, cons
   return qvs::qubo_generate(Q, out_dtype, q_out, (cudaStream_t)stream);
 }
 
+extern "C" int qvs_qubo_fixed_point(int n_qubits, double c, const double* hlin, const double* J, int* F,
+                                    int32_t* ci, int32_t* hi, int32_t* Ji) {
+  if (!F || !ci || !hi || !Ji) return QVS_EINVAL;
+  qvs::QuboCoef Q;
+  QVS_TRY(qvs::qubo_quantize(n_qubits, c, hlin, J, &Q));
+  const int n = n_qubits;
+  *F = Q.F;
+  *ci = Q.c;
+  for (int u = 0; u < n; ++u) hi[u] = Q.h[n - 1 - u];
+  for (int u = 0; u < n; ++u)
+    for (int v = 0; v < n; ++v) Ji[u * n + v] = v > u ? Q.J[n - 1 - u][n - 1 - v] : 0;
+  return QVS_OK;
+}
+
 extern "C" int qvs_qubo_from_maxcut(int n, int n_edges, const int32_t* eu, const int32_t* ev, const double* w,
                                     double* c, double* hlin, double* J) {
   if (n < 1 || n > 32 || n_edges < 0 || !c || !hlin || !J) return QVS_EINVAL;

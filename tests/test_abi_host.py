@@ -268,3 +268,31 @@ def test_chebyshev_coefficients_argument_errors(qvs):
     with pytest.raises(qvs.QvsError) as e:
         qvs.qvs_chebyshev_coefficients(0.0, 100.0, 10.0, 1e-7, max_terms=50)   # needs ~1000 terms
     assert e.value.status == qvs.QVS_ENUMERIC
+
+
+def test_qubo_fixed_point_equals_oracle(qvs):
+    """The library's host quantiser of quadratic qualities against the oracle's fixed-point rule,
+    integer for integer: random forms over six decades of scale, dyadic coefficients with exact
+    halves, an all-zero form (F at its upper clamp) and one whose sum S forces F below zero."""
+    rng = np.random.default_rng(206)
+    cases = []
+    for n, scale in ((1, 1.0), (5, 1e-4), (9, 1.0), (16, 1e2), (24, 3e3), (32, 0.5)):
+        cases.append((n, scale * rng.standard_normal(), scale * rng.standard_normal(n),
+                      np.triu(scale * rng.standard_normal((n, n)), 1) + np.tril(rng.standard_normal((n, n)))))
+    # S ~ 3.75 gives F = 28; odd multiples of 2^-29 then sit exactly half-way between grid points
+    halves = np.zeros((4, 4))
+    halves[0, 1], halves[1, 3] = 3 * 2.0 ** -29, -5 * 2.0 ** -29
+    cases.append((4, 0.75, [2.0 ** -29, -(2.0 ** -29), 3.0, 0.0], halves))
+    cases.append((3, 0.0, np.zeros(3), np.zeros((3, 3))))
+    cases.append((6, 5e9, 1e9 * np.ones(6), np.zeros((6, 6))))
+    for n, c, h, J in cases:
+        F, ci, hi, Ji = qvs.qvs_qubo_fixed_point(n, c, h, J)
+        Fo, cio, hio, Jio = orc.qubo_fixed_point(n, c, h, J)
+        assert (F, ci) == (Fo, cio), (n, F, Fo)
+        assert hi.tolist() == hio and Ji.tolist() == Jio, n
+    F, ci, hi, Ji = qvs.qvs_qubo_fixed_point(4, 0.75, [2.0 ** -29, -(2.0 ** -29), 3.0, 0.0], halves)
+    assert F == 28 and hi[:2].tolist() == [1, -1] and (Ji[0, 1], Ji[1, 3]) == (2, -3)   # away from zero
+    assert qvs.qvs_qubo_fixed_point(3, 0.0, np.zeros(3), np.zeros((3, 3)))[0] == 40
+    assert qvs.qvs_qubo_fixed_point(6, 5e9, 1e9 * np.ones(6), np.zeros((6, 6)))[0] < 0
+    with pytest.raises(qvs.QvsError):
+        qvs.qvs_qubo_fixed_point(3, float("inf"), np.zeros(3), np.zeros((3, 3)))

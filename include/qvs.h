@@ -301,6 +301,23 @@ int qvs_quality_subset(int n, const double* w, int out_dtype, void* q_out, void*
 int qvs_quality_portfolio(int n_qubits, int64_t dim, const int64_t* states, const double* returns,
                           const double* cov, double omega, int out_dtype, void* q_out, void* stream);
 
+/* Sec. 2.4.1 (the parity-ring mixer's factors as passes), host only: how QVS_MIX_PARITY splits one
+ * layer's Givens gates (B_odd, B_even, B_last of both rings, in the printed order) into shared-memory
+ * passes. Each pass stages a tile of QVS_PARITY_TILE_BITS index bits (index bit b = qubit n-1-b) and
+ * applies its gates in order, two at a time where they chain ("sweeps"). Call with ngates = NULL to
+ * get *n_passes only; otherwise every array has room for max_passes passes:
+ *   ngates[i], nsweeps[i]              gates and sweeps of pass i;
+ *   tile_bits[i*TILE_BITS + j]         the tile's index bits (the 4 lowest index bits first);
+ *   gate_bits[2*(i*MAX_GATES + g) + e] the two index bits of gate g (-1 past ngates[i]);
+ *   sweep_kind[i*MAX_GATES + s]        0 = one gate, 1 = two gates on four distinct bits, 2 = two
+ *                                      gates sharing one bit (-1 past nsweeps[i]);
+ *   sweep_first[i*MAX_GATES + s]       the sweep's first gate (the second, if any, follows it).
+ * 12 <= n_qubits <= 30. QVS_EINVAL for other sizes, a NULL array or too small max_passes. */
+#define QVS_PARITY_TILE_BITS 12
+#define QVS_PARITY_MAX_GATES 40
+int qvs_parity_plan(int n_qubits, int max_passes, int* n_passes, int32_t* ngates, int32_t* tile_bits,
+                    int32_t* gate_bits, int32_t* nsweeps, int32_t* sweep_kind, int32_t* sweep_first);
+
 /* Sec. 3 (the sparse mixer's series expansion), host only: the Chebyshev coefficients the library
  * uses for exp(-i t W) v when the spectrum of W lies in [a - b, a + b]:
  *     exp(-i t W) = sum_{m=0}^{K} c_m T_m((W - a) / b),

@@ -34,7 +34,7 @@ EXPORTED = [
     "qvs_create", "qvs_destroy", "qvs_set_quality", "qvs_set_mixer", "qvs_set_initial_state",
     "qvs_set_option", "qvs_evolve", "qvs_expectation", "qvs_gradient", "qvs_get_state",
     "qvs_last_launch_count", "qvs_kernel_stats", "qvs_quality_maxcut", "qvs_quality_subset", "qvs_quality_portfolio",
-    "qvs_xy_ring_csr", "qvs_chebyshev_coefficients", "qvs_state_parity", "qvs_batch_create", "qvs_batch_set_quality", "qvs_batch_gradient",
+    "qvs_xy_ring_csr", "qvs_chebyshev_coefficients", "qvs_parity_plan", "qvs_state_parity", "qvs_batch_create", "qvs_batch_set_quality", "qvs_batch_gradient",
     "qvs_batch_info", "qvs_batch_destroy", "qvs_gradient_small_noalloc", "qvs_strerror",
     "qvs_set_quality_qubo", "qvs_quality_qubo", "qvs_qubo_fixed_point", "qvs_qubo_from_maxcut",
     "qvs_set_phase_terms", "qvs_evolve_ex", "qvs_gradient_ex", "qvs_bfgs_minimize", "qvs_optimise",
@@ -119,6 +119,7 @@ def load(path: str = LIB_PATH):
         "qvs_quality_portfolio": (I, [I, I64, V, P(D), P(D), D, I, V, V]),
         "qvs_xy_ring_csr": (I, [I, I, V, V, V, P(I64), P(I64)]),
         "qvs_chebyshev_coefficients": (I, [D, D, D, D, I, P(D), P(I), P(D)]),
+        "qvs_parity_plan": (I, [I, I, P(I)] + [P(ctypes.c_int32)] * 6),
         "qvs_state_parity": (I, [I, I, V, V]),
         "qvs_gradient_small_noalloc": (I, [I, I, I, V, P(D), P(D), V, V]),
         "qvs_batch_create": (I, [P(V), I, P(ctypes.c_int32), P(ctypes.c_int32), V]),
@@ -600,6 +601,31 @@ def qvs_chebyshev_coefficients(a: float, b: float, t: float, tol: float, max_ter
     _check(load().qvs_chebyshev_coefficients(float(a), float(b), float(t), float(tol), int(max_terms), _dptr(c),
                                              ctypes.byref(n), ctypes.byref(tail)), "qvs_chebyshev_coefficients")
     return c[0::2] + 1j * c[1::2], tail.value
+
+
+PARITY_TILE_BITS, PARITY_MAX_GATES = 12, 40
+
+
+def qvs_parity_plan(n_qubits: int):
+    """The parity-ring mixer's passes for one layer (host, no GPU): a list of dicts with the tile's
+    index bits, the gates as index-bit pairs in order, and the sweeps as (kind, first gate)."""
+    n = int(n_qubits)
+    npass = ctypes.c_int()
+    _check(load().qvs_parity_plan(n, 0, ctypes.byref(npass), None, None, None, None, None, None), "qvs_parity_plan")
+    m = npass.value
+    T, G = PARITY_TILE_BITS, PARITY_MAX_GATES
+    ng, ns = np.zeros(m, np.int32), np.zeros(m, np.int32)
+    tb, gb = np.zeros(m * T, np.int32), np.zeros(m * G * 2, np.int32)
+    sk, sf = np.zeros(m * G, np.int32), np.zeros(m * G, np.int32)
+    I32 = ctypes.POINTER(ctypes.c_int32)
+    _check(load().qvs_parity_plan(n, m, ctypes.byref(npass), *(a.ctypes.data_as(I32) for a in (ng, tb, gb, ns, sk, sf))),
+           "qvs_parity_plan")
+    out = []
+    for i in range(m):
+        g = gb[i * G * 2:(i + 1) * G * 2].reshape(G, 2)[:ng[i]]
+        out.append({"tile": tb[i * T:(i + 1) * T].tolist(), "gates": [tuple(x) for x in g.tolist()],
+                    "sweeps": list(zip(sk[i * G:i * G + ns[i]].tolist(), sf[i * G:i * G + ns[i]].tolist()))})
+    return out
 
 
 def qvs_xy_ring_csr(n: int, k: int):

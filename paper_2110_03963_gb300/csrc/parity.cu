@@ -714,3 +714,32 @@ extern "C" int qvs_state_parity(int n_qubits, int A, void* dst, void* stream) {
   QVS_CUDA_TRY(cudaGetLastError());
   return QVS_OK;
 }
+
+static_assert(qvs::pr::TB == QVS_PARITY_TILE_BITS && qvs::pr::MAXG == QVS_PARITY_MAX_GATES,
+              "the plan layout of qvs_parity_plan");
+
+extern "C" int qvs_parity_plan(int n_qubits, int max_passes, int* n_passes, int32_t* ngates, int32_t* tile_bits,
+                               int32_t* gate_bits, int32_t* nsweeps, int32_t* sweep_kind, int32_t* sweep_first) {
+  using namespace qvs::pr;
+  if (!n_passes || n_qubits < TB || n_qubits > 30 || max_passes < 0) return QVS_EINVAL;
+  std::vector<Pass> layer;
+  QVS_TRY(plan_layer(n_qubits, layer));
+  *n_passes = (int)layer.size();
+  if (!ngates) return QVS_OK;   // size query
+  if ((int)layer.size() > max_passes || !tile_bits || !gate_bits || !nsweeps || !sweep_kind || !sweep_first)
+    return QVS_EINVAL;
+  for (size_t i = 0; i < layer.size(); ++i) {
+    const PassDesc& d = layer[i].d;
+    ngates[i] = d.ngates;
+    nsweeps[i] = d.nsweeps;
+    for (int b = 0; b < TB; ++b) tile_bits[i * TB + b] = d.pos[b];
+    for (int g = 0; g < MAXG; ++g) {
+      const size_t k = i * MAXG + g;
+      gate_bits[2 * k] = g < d.ngates ? d.pos[d.ga[g]] : -1;
+      gate_bits[2 * k + 1] = g < d.ngates ? d.pos[d.gb[g]] : -1;
+      sweep_kind[k] = g < d.nsweeps ? d.skind[g] : -1;
+      sweep_first[k] = g < d.nsweeps ? d.sgate[g] : -1;
+    }
+  }
+  return QVS_OK;
+}

@@ -296,3 +296,54 @@ def test_qubo_fixed_point_equals_oracle(qvs):
     assert qvs.qvs_qubo_fixed_point(6, 5e9, 1e9 * np.ones(6), np.zeros((6, 6)))[0] < 0
     with pytest.raises(qvs.QvsError):
         qvs.qvs_qubo_fixed_point(3, float("inf"), np.zeros(3), np.zeros((3, 3)))
+
+
+@pytest.mark.parametrize("n", [12, 13, 16, 21, 24, 25, 26, 27, 28, 29, 30])
+def test_parity_plan_reproduces_the_printed_product(qvs, n):
+    """The library's packing of one parity-mixer layer into shared-memory passes (host only), against
+    the oracle's factors (B_odd, B_even, B_last of both rings in the printed order): the same gates,
+    and every two gates that share a qubit in the printed relative order, so the product is the same
+    unitary (gates on disjoint qubits commute). Each pass's gates lie in its 12-bit tile, which holds
+    the 4 lowest index bits first; the sweeps cover the gates in order, two at a time when the kind
+    says so, with the kind matching how the two gates share bits."""
+    plan = qvs.qvs_parity_plan(n)
+    printed = [frozenset(pq) for r in orc.parity_ring_rounds(n) for pq in r]
+    assert len(set(printed)) == len(printed)
+    got = [frozenset((n - 1 - a, n - 1 - b)) for P in plan for (a, b) in P["gates"]]
+    assert sorted(map(sorted, got)) == sorted(map(sorted, printed))
+    pos = {g: i for i, g in enumerate(got)}
+    for i, g in enumerate(printed):
+        for h in printed[i + 1:]:
+            if g & h:
+                assert pos[g] < pos[h], (sorted(g), sorted(h))
+    for P in plan:
+        tile, gates = P["tile"], P["gates"]
+        assert len(set(tile)) == 12 and tile[:4] == [0, 1, 2, 3] and max(tile) < n
+        assert all(a in tile and b in tile and a != b for a, b in gates)
+        covered = []
+        for kind, first in P["sweeps"]:
+            assert first == len(covered)
+            if kind == 0:
+                covered.append(first)
+                nxt = first + 1
+                assert nxt == len(gates) or set(gates[first]) == set(gates[nxt])
+            else:
+                shared = len(set(gates[first]) & set(gates[first + 1]))
+                assert (kind, shared) in ((1, 0), (2, 1))
+                covered += [first, first + 1]
+        assert covered == list(range(len(gates)))
+    if n == 24:
+        assert len(plan) == 3
+    if n in (26, 27, 28):
+        assert len(plan) == 4
+
+
+def test_parity_plan_argument_errors(qvs):
+    import ctypes
+    lib = qvs.load()
+    npass = ctypes.c_int()
+    for n in (11, 31):
+        assert lib.qvs_parity_plan(n, 0, ctypes.byref(npass), None, None, None, None, None, None) == qvs.QVS_EINVAL
+    assert lib.qvs_parity_plan(24, 0, None, None, None, None, None, None, None) == qvs.QVS_EINVAL
+    buf = (ctypes.c_int32 * 1024)()
+    assert lib.qvs_parity_plan(24, 2, ctypes.byref(npass), buf, buf, buf, buf, buf, buf) == qvs.QVS_EINVAL

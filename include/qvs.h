@@ -301,6 +301,19 @@ int qvs_quality_subset(int n, const double* w, int out_dtype, void* q_out, void*
 int qvs_quality_portfolio(int n_qubits, int64_t dim, const int64_t* states, const double* returns,
                           const double* cov, double omega, int out_dtype, void* q_out, void* stream);
 
+/* Sec. 2.3.1 (the hypercube mixer as commuting single-bit rotations), host only: the forward pass
+ * schedule QVS_MIX_HYPERCUBE runs for n_qubits (12..32) and p layers. Pass j (0-based, in order)
+ * applies, on tiles of 2^12 amplitudes: the rotations of layer layer_before[j] on the index bits
+ * rot_bits[j] (bit b set = index bit b), then the phase of layer layer_phase[j], then the rotations
+ * of layer layer_after[j] on the same bits (-1: that part is absent). shape[j]: 0 = first pass (the
+ * initial state is generated or loaded), 1 = rotations, phase, rotations, 2 = rotations only,
+ * 3 = last pass (rotations, objective, adjoint seed). type[j] is the tile type (0 = the 12 lowest
+ * index bits). The adjoint sweep runs the same passes backwards. Call with shape = NULL to get
+ * *n_passes only; otherwise every array has room for max_passes entries. QVS_EINVAL for sizes out
+ * of range, a NULL array or too small max_passes. */
+int qvs_hypercube_plan(int n_qubits, int p, int max_passes, int* n_passes, int32_t* shape, int32_t* type,
+                       uint32_t* rot_bits, int32_t* layer_before, int32_t* layer_after, int32_t* layer_phase);
+
 /* Sec. 2.4.1 (the parity-ring mixer's factors as passes), host only: how QVS_MIX_PARITY splits one
  * layer's Givens gates (B_odd, B_even, B_last of both rings, in the printed order) into shared-memory
  * passes. Each pass stages a tile of QVS_PARITY_TILE_BITS index bits (index bit b = qubit n-1-b) and

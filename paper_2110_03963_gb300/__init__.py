@@ -34,7 +34,7 @@ EXPORTED = [
     "qvs_create", "qvs_destroy", "qvs_set_quality", "qvs_set_mixer", "qvs_set_initial_state",
     "qvs_set_option", "qvs_evolve", "qvs_expectation", "qvs_gradient", "qvs_get_state",
     "qvs_last_launch_count", "qvs_kernel_stats", "qvs_quality_maxcut", "qvs_quality_subset", "qvs_quality_portfolio",
-    "qvs_xy_ring_csr", "qvs_chebyshev_coefficients", "qvs_parity_plan", "qvs_state_parity", "qvs_batch_create", "qvs_batch_set_quality", "qvs_batch_gradient",
+    "qvs_xy_ring_csr", "qvs_chebyshev_coefficients", "qvs_parity_plan", "qvs_hypercube_plan", "qvs_state_parity", "qvs_batch_create", "qvs_batch_set_quality", "qvs_batch_gradient",
     "qvs_batch_info", "qvs_batch_destroy", "qvs_gradient_small_noalloc", "qvs_strerror",
     "qvs_set_quality_qubo", "qvs_quality_qubo", "qvs_qubo_fixed_point", "qvs_qubo_from_maxcut",
     "qvs_set_phase_terms", "qvs_evolve_ex", "qvs_gradient_ex", "qvs_bfgs_minimize", "qvs_optimise",
@@ -120,6 +120,8 @@ def load(path: str = LIB_PATH):
         "qvs_xy_ring_csr": (I, [I, I, V, V, V, P(I64), P(I64)]),
         "qvs_chebyshev_coefficients": (I, [D, D, D, D, I, P(D), P(I), P(D)]),
         "qvs_parity_plan": (I, [I, I, P(I)] + [P(ctypes.c_int32)] * 6),
+        "qvs_hypercube_plan": (I, [I, I, I, P(I), P(ctypes.c_int32), P(ctypes.c_int32), P(ctypes.c_uint32),
+                                   P(ctypes.c_int32), P(ctypes.c_int32), P(ctypes.c_int32)]),
         "qvs_state_parity": (I, [I, I, V, V]),
         "qvs_gradient_small_noalloc": (I, [I, I, I, V, P(D), P(D), V, V]),
         "qvs_batch_create": (I, [P(V), I, P(ctypes.c_int32), P(ctypes.c_int32), V]),
@@ -601,6 +603,23 @@ def qvs_chebyshev_coefficients(a: float, b: float, t: float, tol: float, max_ter
     _check(load().qvs_chebyshev_coefficients(float(a), float(b), float(t), float(tol), int(max_terms), _dptr(c),
                                              ctypes.byref(n), ctypes.byref(tail)), "qvs_chebyshev_coefficients")
     return c[0::2] + 1j * c[1::2], tail.value
+
+
+def qvs_hypercube_plan(n_qubits: int, p: int):
+    """The hypercube mixer's forward pass schedule (host, no GPU): a list of dicts per pass with its
+    shape, tile type, rotated index bits (a mask) and the layers of its rotations and phase."""
+    m = ctypes.c_int()
+    _check(load().qvs_hypercube_plan(int(n_qubits), int(p), 0, ctypes.byref(m), None, None, None, None, None, None),
+           "qvs_hypercube_plan")
+    F = m.value
+    shape, typ, lb, la, lg = (np.zeros(F, np.int32) for _ in range(5))
+    bits = np.zeros(F, np.uint32)
+    I32, U32 = ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_uint32)
+    _check(load().qvs_hypercube_plan(int(n_qubits), int(p), F, ctypes.byref(m), shape.ctypes.data_as(I32),
+                                     typ.ctypes.data_as(I32), bits.ctypes.data_as(U32), lb.ctypes.data_as(I32),
+                                     la.ctypes.data_as(I32), lg.ctypes.data_as(I32)), "qvs_hypercube_plan")
+    return [{"shape": int(shape[j]), "type": int(typ[j]), "bits": int(bits[j]), "before": int(lb[j]),
+             "after": int(la[j]), "phase": int(lg[j])} for j in range(F)]
 
 
 PARITY_TILE_BITS, PARITY_MAX_GATES = 12, 40

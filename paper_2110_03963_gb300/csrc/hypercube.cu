@@ -1698,3 +1698,30 @@ extern "C" int qvs_batch_destroy(qvs_batch_t b) {
   (void)cudaGetLastError();
   return QVS_OK;
 }
+
+extern "C" int qvs_hypercube_plan(int n_qubits, int p, int max_passes, int* n_passes, int32_t* shape, int32_t* type,
+                                  uint32_t* rot_bits, int32_t* layer_before, int32_t* layer_after,
+                                  int32_t* layer_phase) {
+  using namespace qvs::hc;
+  if (!n_passes || n_qubits < TB || n_qubits > 32 || p < 1 || p > 4096 || max_passes < 0) return QVS_EINVAL;
+  Plan pl;
+  QVS_TRY(make_plan(n_qubits, p, pl));
+  *n_passes = pl.F;
+  if (!shape) return QVS_OK;   // size query
+  if (pl.F > max_passes || !type || !rot_bits || !layer_before || !layer_after || !layer_phase) return QVS_EINVAL;
+  for (int j = 1; j <= pl.F; ++j) {
+    const PassInfo& q = pl.pass[j];
+    const Tile& t = pl.tile[q.type];
+    const int s = __builtin_popcount(t.smask);
+    uint32_t bits = 0;   // tile bit i is index bit i below s and index bit i + hshift above
+    for (int i = 0; i < TB; ++i)
+      if ((pl.gmask[q.type] >> i) & 1u) bits |= 1u << (i < s ? i : i + t.hshift);
+    shape[j - 1] = q.shape;
+    type[j - 1] = q.type;
+    rot_bits[j - 1] = bits;
+    layer_before[j - 1] = q.lb;
+    layer_after[j - 1] = q.la;
+    layer_phase[j - 1] = q.lg;
+  }
+  return QVS_OK;
+}

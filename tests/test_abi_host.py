@@ -347,3 +347,54 @@ def test_parity_plan_argument_errors(qvs):
     assert lib.qvs_parity_plan(24, 0, None, None, None, None, None, None, None) == qvs.QVS_EINVAL
     buf = (ctypes.c_int32 * 1024)()
     assert lib.qvs_parity_plan(24, 2, ctypes.byref(npass), buf, buf, buf, buf, buf, buf) == qvs.QVS_EINVAL
+
+
+@pytest.mark.parametrize("n", list(range(12, 33)))
+def test_hypercube_plan_composes_the_ansatz(qvs, n):
+    """The hypercube pass schedule (host only) composes exactly prod_k exp(-i t_k W) exp(-i g_k Q):
+    rotations of different bits commute and the phase is diagonal, so it suffices that each layer's
+    phase comes after every rotation of the previous layer, in layer order, and that every index bit
+    is rotated exactly once per layer, after that layer's phase. Also: the first pass generates the
+    initial state and carries phase 0, the last computes the objective and carries no phase, and
+    with three tile types every pass with a phase runs on a high tile type (not the 12 lowest bits)."""
+    full = (1 << n) - 1
+    for p in (1, 2, 3, 5, 8):
+        plan = qvs.qvs_hypercube_plan(n, p)
+        three = any(P["type"] == 2 for P in plan)
+        rotated = [0] * p
+        phases = []
+
+        def rotate(k, bits):
+            assert 0 <= k < p and phases and phases[-1] == k   # after phase k, before phase k + 1
+            assert rotated[k] & bits == 0, (n, p, k)
+            rotated[k] |= bits
+
+        for j, P in enumerate(plan):
+            assert P["bits"] != 0 and P["bits"] & ~full == 0
+            if P["type"] == 0:
+                assert P["bits"] == 0xFFF
+            if P["before"] >= 0:
+                rotate(P["before"], P["bits"])
+            if P["phase"] >= 0:
+                k = P["phase"]
+                assert k == len(phases) and (k == 0 or rotated[k - 1] == full), (n, p, j)
+                phases.append(k)
+                assert P["after"] == k
+            if P["after"] >= 0:
+                rotate(P["after"], P["bits"])
+            assert (P["shape"] == 0) == (j == 0) and (P["shape"] == 3) == (j == len(plan) - 1)
+            assert (P["phase"] >= 0) == (P["shape"] in (0, 1))
+            if three and P["shape"] in (0, 1, 3):
+                assert P["type"] != 0, (n, p, j)
+        assert phases == list(range(p)) and rotated == [full] * p
+
+
+def test_hypercube_plan_argument_errors(qvs):
+    import ctypes
+    lib = qvs.load()
+    m = ctypes.c_int()
+    for n, p in ((11, 2), (33, 2), (20, 0)):
+        assert lib.qvs_hypercube_plan(n, p, 0, ctypes.byref(m), *([None] * 6)) == qvs.QVS_EINVAL
+    buf32 = (ctypes.c_int32 * 8)()
+    bufu = (ctypes.c_uint32 * 8)()
+    assert lib.qvs_hypercube_plan(28, 8, 8, ctypes.byref(m), buf32, buf32, bufu, buf32, buf32, buf32) == qvs.QVS_EINVAL

@@ -283,7 +283,7 @@ extern "C" int qvs_batch_optimise(qvs_batch_t b, double* gammas, double* ts, dou
   {
     cudaStream_t cs;
     QVS_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    cudaGraph_t g;
+    cudaGraph_t g = nullptr;
     const cudaStream_t keep = b->stream;
     b->stream = cs;
     int stc = QVS_OK;
@@ -300,11 +300,11 @@ extern "C" int qvs_batch_optimise(qvs_batch_t b, double* gammas, double* ts, dou
     const cudaError_t ce = cudaStreamEndCapture(cs, &g);
     b->stream = keep;
     cudaStreamDestroy(cs);
-    if (stc != QVS_OK) {
+    if (stc != QVS_OK || ce != cudaSuccess) {   // a failed capture leaves no graph behind
+      if (ce == cudaSuccess && g) cudaGraphDestroy(g);
       (void)cudaGetLastError();
-      return stc;
+      return stc != QVS_OK ? stc : QVS_ECUDA;
     }
-    QVS_CUDA_TRY(ce);
     const cudaError_t ie = cudaGraphInstantiate(&b->opt_graph, g, 0);
     cudaGraphDestroy(g);
     QVS_CUDA_TRY(ie);

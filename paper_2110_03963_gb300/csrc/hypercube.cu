@@ -1620,10 +1620,14 @@ extern "C" int qvs_batch_gradient(qvs_batch_t b, const double* gammas, const dou
     // capture the whole solve (parameters in, kernel, results out) as a CUDA graph
     cudaStream_t cs;
     QVS_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    cudaGraph_t g;
+    cudaGraph_t g = nullptr;
     const cudaStream_t keep = b->stream;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaStreamDestroy(cs);
+      (void)cudaGetLastError();
+      return QVS_ECUDA;
+    }
     b->stream = cs;
-    QVS_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     int st = QVS_OK;
     if (cudaMemcpyAsync(b->theta.ptr, b->host_theta, sizeof(double) * 2 * P, cudaMemcpyHostToDevice, cs) != cudaSuccess)
       st = QVS_ECUDA;
@@ -1635,8 +1639,11 @@ extern "C" int qvs_batch_gradient(qvs_batch_t b, const double* gammas, const dou
     const cudaError_t ce = cudaStreamEndCapture(cs, &g);
     b->stream = keep;
     cudaStreamDestroy(cs);
-    if (st != QVS_OK) return st;
-    QVS_CUDA_TRY(ce);
+    if (st != QVS_OK || ce != cudaSuccess) {   // a failed capture leaves no graph behind
+      if (ce == cudaSuccess && g) cudaGraphDestroy(g);
+      (void)cudaGetLastError();
+      return st != QVS_OK ? st : QVS_ECUDA;
+    }
     const cudaError_t ie = cudaGraphInstantiate(&b->graph, g, 0);
     cudaGraphDestroy(g);
     QVS_CUDA_TRY(ie);

@@ -60,9 +60,12 @@ enum { QVS_INIT_UNIFORM = 0, QVS_INIT_EXPLICIT = 1 };
 enum { QVS_MIX_HYPERCUBE = 1, QVS_MIX_CIRCULANT = 2, QVS_MIX_CSR = 3, QVS_MIX_PARITY = 4, QVS_MIX_XY_RING = 5 };
 /* options for qvs_set_option */
 enum {
-  QVS_OPT_CKPT_LAYERS = 1,  /* adjoint: store the forward state every this many layers and
-                               uncompute in between; 0 = ceil(sqrt(p)) (default); 1 = store
-                               every pass boundary (no uncompute)                             */
+  QVS_OPT_CKPT_LAYERS = 1,  /* hypercube adjoint: store the forward state every this many
+                               layers and uncompute in between; 0 = ceil(sqrt(p)) (default).
+                               1 stores every layer boundary: up to 20 qubits a layer is one
+                               pass, so nothing is uncomputed; from 21 qubits a layer is two
+                               passes and the rotation-only pass of each layer is still
+                               uncomputed.                                                    */
   QVS_OPT_PROFILE = 2,      /* 1: bracket every kernel launch with CUDA events on the handle's
                                stream and accumulate per-kernel statistics (qvs_kernel_stats);
                                0: off (default). Setting it resets the statistics.           */

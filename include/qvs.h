@@ -71,13 +71,15 @@ enum {
                                0: off (default). Setting it resets the statistics.           */
   QVS_OPT_STAGED = 3        /* complex64 data movement through the Tensor Memory Accelerator;
                                1 (default), 0 = per-thread loads and stores, one CTA per tile.
-                               Hypercube mixer, n > 12: the last forward pass runs as a persistent
+                               Hypercube mixer, complex64, n > 12: the last forward pass of
+                               qvs_gradient (fused with the adjoint seed) runs as a persistent
                                kernel whose next tile is copied into shared memory while the
-                               current one is processed. Circulant mixer, N = 2^26: each column
-                               tile is loaded and stored by one tensor copy, and every column and
-                               row pass prefetches the next wave's state tile into L2. Results are
-                               identical either way. A pass whose copy wait expires makes the call
-                               return QVS_ETIMEOUT.                                            */
+                               current one is processed, when that pass's tile keeps at least 4
+                               contiguous low index bits (every n <= 28). Circulant mixer,
+                               N = 2^26: each column tile is loaded and stored by one tensor
+                               copy, and every column and row pass prefetches the next wave's
+                               state tile into L2. Results are identical either way. A pass
+                               whose copy wait expires makes the call return QVS_ETIMEOUT.    */
 };
 
 /*

@@ -240,7 +240,7 @@ int ensure_q_vector(qvs_ctx* h) {
 }
 }  // namespace qvs
 
-extern "C" int qvs_set_mixer(qvs_t h, int kind, const qvs_mixer_desc* d) {
+static int qvs_set_mixer_impl(qvs_t h, int kind, const qvs_mixer_desc* d) {
   if (!h || !d) return QVS_EINVAL;
   AllocScope scope(&h->allocator);
   h->have_mixer = false;
@@ -263,6 +263,10 @@ extern "C" int qvs_set_mixer(qvs_t h, int kind, const qvs_mixer_desc* d) {
   h->mixer = kind;
   h->have_mixer = true;
   return QVS_OK;
+}
+
+extern "C" int qvs_set_mixer(qvs_t h, int kind, const qvs_mixer_desc* d) {
+  return qvs::guarded([&] { return qvs_set_mixer_impl(h, kind, d); });
 }
 
 extern "C" int qvs_set_initial_state(qvs_t h, int kind, const void* psi0, int on_device) {

@@ -220,8 +220,8 @@ __global__ void __launch_bounds__(NT) bfgs_step_kernel(const __grid_constant__ S
 
 using namespace qvs;
 
-extern "C" int qvs_batch_optimise(qvs_batch_t b, double* gammas, double* ts, double gtol, int max_iter,
-                                  double* f_out, int* iters_out, int* evals_out, int* stop_out) {
+static int qvs_batch_optimise_impl(qvs_batch_t b, double* gammas, double* ts, double gtol, int max_iter,
+                                   double* f_out, int* iters_out, int* evals_out, int* stop_out) {
   using bopt::State;
   if (!b || !gammas || !ts || max_iter < 0 || max_iter > 100000 || !(gtol >= 0.0)) return QVS_EINVAL;
   if (!b->have_q) return QVS_ESTATE;
@@ -332,12 +332,19 @@ extern "C" int qvs_batch_optimise(qvs_batch_t b, double* gammas, double* ts, dou
   return QVS_OK;
 }
 
+extern "C" int qvs_batch_optimise(qvs_batch_t b, double* gammas, double* ts, double gtol, int max_iter,
+                                  double* f_out, int* iters_out, int* evals_out, int* stop_out) {
+  return qvs::guarded([&] {
+    return qvs_batch_optimise_impl(b, gammas, ts, gtol, max_iter, f_out, iters_out, evals_out, stop_out);
+  });
+}
+
 // Sec. 5 (benchmark with param_persist): a depth sweep of repeated optimisations of one instance.
 // Each depth is one batch of `repeats` parameter sets sharing the instance's qualities, optimised
 // together; the best optimum of a depth seeds the first layers of every repeat at the next depth.
-extern "C" int qvs_benchmark(int n, const float* q, int on_device, int d_min, int d_max, int repeats,
-                             const double* init, double gtol, int max_iter, double* f_out, double* best_theta,
-                             void* stream) {
+static int qvs_benchmark_impl(int n, const float* q, int on_device, int d_min, int d_max, int repeats,
+                              const double* init, double gtol, int max_iter, double* f_out, double* best_theta,
+                              void* stream) {
   if (!q || !init || !f_out || !best_theta || n < 12 || n > 28 || repeats < 1 || repeats > 65536 ||
       d_min < 1 || d_max < d_min || d_max > bopt::NT / 2 || max_iter < 0 || !(gtol >= 0.0))
     return QVS_EINVAL;
@@ -383,4 +390,12 @@ extern "C" int qvs_benchmark(int n, const float* q, int on_device, int d_min, in
     bo += 2 * D;
   }
   return QVS_OK;
+}
+
+extern "C" int qvs_benchmark(int n, const float* q, int on_device, int d_min, int d_max, int repeats,
+                             const double* init, double gtol, int max_iter, double* f_out, double* best_theta,
+                             void* stream) {
+  return qvs::guarded([&] {
+    return qvs_benchmark_impl(n, q, on_device, d_min, d_max, repeats, init, gtol, max_iter, f_out, best_theta, stream);
+  });
 }

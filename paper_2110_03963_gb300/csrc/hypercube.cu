@@ -1431,8 +1431,8 @@ int batch_autotune(qvs_batch_t b) {
 }  // namespace hc
 }  // namespace qvs
 
-extern "C" int qvs_batch_create(qvs_batch_t* out, int count, const int32_t* n_qubits, const int32_t* layers,
-                                void* stream) {
+static int qvs_batch_create_impl(qvs_batch_t* out, int count, const int32_t* n_qubits, const int32_t* layers,
+                                 void* stream) {
   using namespace qvs;
   using namespace qvs::hc;
   if (!out || count < 1 || count > (1 << 20) || !n_qubits || !layers) return QVS_EINVAL;
@@ -1547,6 +1547,11 @@ extern "C" int qvs_batch_create(qvs_batch_t* out, int count, const int32_t* n_qu
   }
   *out = b;
   return QVS_OK;
+}
+
+extern "C" int qvs_batch_create(qvs_batch_t* out, int count, const int32_t* n_qubits, const int32_t* layers,
+                                void* stream) {
+  return qvs::guarded([&] { return qvs_batch_create_impl(out, count, n_qubits, layers, stream); });
 }
 
 // Captured graphs hold the quality pointer: drop them when the buffer moves.

@@ -18,8 +18,8 @@
 
 static const int kMaxHalvings = 30;
 
-extern "C" int qvs_bfgs_minimize(int n, double* x, qvs_fg_fn fg, void* user, double gtol, int max_iter,
-                                 double* f_out, int* iters_out, int* evals_out, int* stop_out) {
+static int qvs_bfgs_minimize_impl(int n, double* x, qvs_fg_fn fg, void* user, double gtol, int max_iter,
+                                  double* f_out, int* iters_out, int* evals_out, int* stop_out) {
   if (n < 1 || n > 8192 || !x || !fg || max_iter < 0 || !(gtol >= 0.0)) return QVS_EINVAL;
   const size_t N = (size_t)n;
   std::vector<double> H(N * N, 0.0), g(N), gn(N), xn(N), d(N), s(N), y(N), Hy(N);
@@ -110,6 +110,13 @@ extern "C" int qvs_bfgs_minimize(int n, double* x, qvs_fg_fn fg, void* user, dou
   return QVS_OK;
 }
 
+extern "C" int qvs_bfgs_minimize(int n, double* x, qvs_fg_fn fg, void* user, double gtol, int max_iter,
+                                 double* f_out, int* iters_out, int* evals_out, int* stop_out) {
+  return qvs::guarded([&] {
+    return qvs_bfgs_minimize_impl(n, x, fg, user, gtol, max_iter, f_out, iters_out, evals_out, stop_out);
+  });
+}
+
 namespace {
 struct OptCtx {
   qvs_t h;
@@ -132,8 +139,8 @@ int qva_fg(const double* th, double* f, double* g, void* user) {
 }
 }  // namespace
 
-extern "C" int qvs_optimise(qvs_t h, int p, double* gammas, double* ts, double gtol, int max_iter, double* f_out,
-                            int* iters_out, int* evals_out, int* stop_out) {
+static int qvs_optimise_impl(qvs_t h, int p, double* gammas, double* ts, double gtol, int max_iter, double* f_out,
+                             int* iters_out, int* evals_out, int* stop_out) {
   if (!h || p < 1 || p > 4096 || !gammas || !ts) return QVS_EINVAL;
   OptCtx c{h, p, std::vector<double>(p), std::vector<double>(p), std::vector<double>(p), std::vector<double>(p)};
   std::vector<double> th(2 * (size_t)p);
@@ -147,4 +154,11 @@ extern "C" int qvs_optimise(qvs_t h, int p, double* gammas, double* ts, double g
     ts[k] = th[2 * k + 1];
   }
   return QVS_OK;
+}
+
+extern "C" int qvs_optimise(qvs_t h, int p, double* gammas, double* ts, double gtol, int max_iter, double* f_out,
+                            int* iters_out, int* evals_out, int* stop_out) {
+  return qvs::guarded([&] {
+    return qvs_optimise_impl(h, p, gammas, ts, gtol, max_iter, f_out, iters_out, evals_out, stop_out);
+  });
 }

@@ -233,8 +233,8 @@ extern "C" int qvs_quality_portfolio(int n_qubits, int64_t dim, const int64_t* s
 
 // ------------------------------------------------------------------ XY-ring CSR (host)
 
-extern "C" int qvs_xy_ring_csr(int n, int k, int64_t* states, int64_t* rowptr, int32_t* colind,
-                               int64_t* dim_out, int64_t* nnz_out) {
+static int qvs_xy_ring_csr_impl(int n, int k, int64_t* states, int64_t* rowptr, int32_t* colind,
+                                int64_t* dim_out, int64_t* nnz_out) {
   if (n < 3 || n > 40 || k < 0 || k > n) return QVS_EINVAL;
   // binomial table for the combinatorial number system rank of a weight-k state
   std::vector<std::vector<int64_t>> C(n + 1, std::vector<int64_t>(n + 2, 0));
@@ -297,6 +297,11 @@ extern "C" int qvs_xy_ring_csr(int n, int k, int64_t* states, int64_t* rowptr, i
     rowptr[r + 1] = pos;
   }
   return QVS_OK;
+}
+
+extern "C" int qvs_xy_ring_csr(int n, int k, int64_t* states, int64_t* rowptr, int32_t* colind,
+                               int64_t* dim_out, int64_t* nnz_out) {
+  return qvs::guarded([&] { return qvs_xy_ring_csr_impl(n, k, states, rowptr, colind, dim_out, nnz_out); });
 }
 
 extern "C" int qvs_quality_qubo(int n_qubits, double c, const double* hlin, const double* J, int out_dtype,

@@ -5,6 +5,8 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <new>
+#include <stdexcept>
 #include <string>
 #include <vector>
 
@@ -26,6 +28,21 @@
   } while (0)
 
 namespace qvs {
+
+// Run f() (an entry point's body) so that no C++ exception crosses the C ABI: a host allocation
+// that fails (std::bad_alloc, or a size past std::vector's limit) becomes QVS_ENOMEM.
+template <class F>
+int guarded(F&& f) {
+  try {
+    return f();
+  } catch (const std::bad_alloc&) {
+    return QVS_ENOMEM;
+  } catch (const std::length_error&) {
+    return QVS_ENOMEM;
+  } catch (...) {
+    return QVS_EINVAL;
+  }
+}
 
 // Raise a kernel's dynamic shared-memory limit to `bytes` on the current device, once per device:
 // the attribute belongs to the device, so a process that drives several GPUs sets it on each.

@@ -398,3 +398,25 @@ def test_hypercube_plan_argument_errors(qvs):
     buf32 = (ctypes.c_int32 * 8)()
     bufu = (ctypes.c_uint32 * 8)()
     assert lib.qvs_hypercube_plan(28, 8, 8, ctypes.byref(m), buf32, buf32, bufu, buf32, buf32, buf32) == qvs.QVS_EINVAL
+
+
+def test_host_allocation_failure_returns_enomem():
+    """No C++ exception crosses the C ABI: in a child process whose address space is capped at
+    3 GiB, the XY-ring CSR builder asked for C(33,16) states (a 9.4 GB state list) returns
+    QVS_ENOMEM instead of aborting the process."""
+    import subprocess
+    import sys
+    import textwrap
+    pytest.importorskip("resource")
+    code = textwrap.dedent("""
+        import ctypes, resource
+        resource.setrlimit(resource.RLIMIT_AS, (3 << 30, 3 << 30))
+        import paper_2110_03963_gb300 as q
+        lib = q.load()
+        dim, nnz = ctypes.c_int64(), ctypes.c_int64()
+        print(lib.qvs_xy_ring_csr(33, 16, None, None, None, ctypes.byref(dim), ctypes.byref(nnz)))
+    """)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=root, timeout=120)
+    assert r.returncode == 0, r.stderr[-500:]
+    assert int(r.stdout.strip().splitlines()[-1]) == -2   # QVS_ENOMEM

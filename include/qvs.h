@@ -271,6 +271,8 @@ int qvs_kernel_stats(qvs_t h, int slot, char* name, int name_len, int64_t* launc
  * Sec. 6.1, max-cut: q_i = sum over edges e=(u,v) with x_u(i) == x_v(i) of w_e (w = NULL: 1),
  *   dim = 2^n; edge endpoints are qubit indices (host arrays). The sum runs over the edges in
  *   the given order in fp64 and is rounded once to out_dtype (QVS_I32 needs w == NULL).
+ *   1 <= n <= 40, 0 <= n_edges <= 1024 (no edges: q = 0); QVS_EINVAL otherwise, for an endpoint
+ *   outside 0..n-1, a self-loop or a non-finite weight.
  */
 int qvs_quality_maxcut(int n, int n_edges, const int32_t* eu, const int32_t* ev, const double* w,
                        int out_dtype, void* q_out, void* stream);
@@ -296,7 +298,8 @@ int qvs_qubo_from_maxcut(int n, int n_edges, const int32_t* eu, const int32_t* e
                          double* c, double* hlin, double* J);
 
 /* QWOA subset sums: q_i = sum_b w_b x_b(i) over items b = 0..n-1 (qubit b selects item b),
- * fp64 in item order, rounded once to out_dtype (F32 or F64). w: host array of n weights. */
+ * fp64 in item order, rounded once to out_dtype (F32 or F64). w: host array of n weights,
+ * 1 <= n <= 40. */
 int qvs_quality_subset(int n, const double* w, int out_dtype, void* q_out, void* stream);
 
 /* Sec. 6.2, portfolio cost on a list of basis states (device array states[dim], n_qubits

@@ -339,6 +339,24 @@ int qvs_hypercube_plan(int n_qubits, int p, int max_passes, int* n_passes, int32
 int qvs_parity_plan(int n_qubits, int max_passes, int* n_passes, int32_t* ngates, int32_t* tile_bits,
                     int32_t* gate_bits, int32_t* nsweeps, int32_t* sweep_kind, int32_t* sweep_first);
 
+/* Host only: the register layouts of the tiled kernels, for checks of their index maps without a
+ * GPU. For thread t and register r of step layout `layout`, index[t * regs + r] is the tile index
+ * that register holds; slot[j] is the shared-memory slot of tile index j (8-byte words) and
+ * global[j] its offset in the state vector for the first tile. Families:
+ *   QVS_LAYOUT_HYPERCUBE        log2n 0; layouts 0..3 of the 2^12-amplitude hypercube tiles (the
+ *                               contiguous tile type: global[j] = j);
+ *   QVS_LAYOUT_CIRCULANT_COLUMN log2n 17..27; layouts 0..2 (one per transform digit) of that
+ *                               size's column pass over 2^14-amplitude tiles;
+ *   QVS_LAYOUT_CIRCULANT_ROW    log2n 0; layouts 0..2 of the row pass (contiguous tiles);
+ *   QVS_LAYOUT_CIRCULANT_BOX    log2n 26, layout 0: slot[j] is the word of the tensor-copy box.
+ * index has room for threads * regs values, slot and global for the tile's amplitudes (4096 or
+ * 16384); *threads, *regs and *column_bits (the tile bits that are consecutive index bits)
+ * describe the layout. QVS_EINVAL for another family, size or layout, or a NULL pointer. */
+enum { QVS_LAYOUT_HYPERCUBE = 1, QVS_LAYOUT_CIRCULANT_COLUMN = 2, QVS_LAYOUT_CIRCULANT_ROW = 3,
+       QVS_LAYOUT_CIRCULANT_BOX = 4 };
+int qvs_tile_layout(int family, int log2n, int layout, int32_t* index, int32_t* slot, int32_t* global,
+                    int* threads, int* regs, int* column_bits);
+
 /* Sec. 3 (the sparse mixer's series expansion), host only: the Chebyshev coefficients the library
  * uses for exp(-i t W) v when the spectrum of W lies in [a - b, a + b]:
  *     exp(-i t W) = sum_{m=0}^{K} c_m T_m((W - a) / b),

@@ -34,7 +34,7 @@ EXPORTED = [
     "qvs_create", "qvs_destroy", "qvs_set_quality", "qvs_set_mixer", "qvs_set_initial_state",
     "qvs_set_option", "qvs_evolve", "qvs_expectation", "qvs_gradient", "qvs_get_state",
     "qvs_last_launch_count", "qvs_kernel_stats", "qvs_quality_maxcut", "qvs_quality_subset", "qvs_quality_portfolio",
-    "qvs_xy_ring_csr", "qvs_chebyshev_coefficients", "qvs_parity_plan", "qvs_hypercube_plan", "qvs_state_parity", "qvs_batch_create", "qvs_batch_set_quality", "qvs_batch_gradient",
+    "qvs_xy_ring_csr", "qvs_chebyshev_coefficients", "qvs_parity_plan", "qvs_hypercube_plan", "qvs_tile_layout", "qvs_state_parity", "qvs_batch_create", "qvs_batch_set_quality", "qvs_batch_gradient",
     "qvs_batch_info", "qvs_batch_destroy", "qvs_gradient_small_noalloc", "qvs_strerror",
     "qvs_set_quality_qubo", "qvs_quality_qubo", "qvs_qubo_fixed_point", "qvs_qubo_from_maxcut",
     "qvs_set_phase_terms", "qvs_evolve_ex", "qvs_gradient_ex", "qvs_bfgs_minimize", "qvs_optimise",
@@ -120,6 +120,7 @@ def load(path: str = LIB_PATH):
         "qvs_xy_ring_csr": (I, [I, I, V, V, V, P(I64), P(I64)]),
         "qvs_chebyshev_coefficients": (I, [D, D, D, D, I, P(D), P(I), P(D)]),
         "qvs_parity_plan": (I, [I, I, P(I)] + [P(ctypes.c_int32)] * 6),
+        "qvs_tile_layout": (I, [I, I, I, P(ctypes.c_int32), P(ctypes.c_int32), P(ctypes.c_int32), P(I), P(I), P(I)]),
         "qvs_hypercube_plan": (I, [I, I, I, P(I), P(ctypes.c_int32), P(ctypes.c_int32), P(ctypes.c_uint32),
                                    P(ctypes.c_int32), P(ctypes.c_int32), P(ctypes.c_int32)]),
         "qvs_state_parity": (I, [I, I, V, V]),
@@ -620,6 +621,25 @@ def qvs_hypercube_plan(n_qubits: int, p: int):
                                      la.ctypes.data_as(I32), lg.ctypes.data_as(I32)), "qvs_hypercube_plan")
     return [{"shape": int(shape[j]), "type": int(typ[j]), "bits": int(bits[j]), "before": int(lb[j]),
              "after": int(la[j]), "phase": int(lg[j])} for j in range(F)]
+
+
+QVS_LAYOUT_HYPERCUBE, QVS_LAYOUT_CIRCULANT_COLUMN, QVS_LAYOUT_CIRCULANT_ROW, QVS_LAYOUT_CIRCULANT_BOX = 1, 2, 3, 4
+
+
+def qvs_tile_layout(family: int, log2n: int, layout: int):
+    """A tiled kernel's register layout (host, no GPU): (index[threads, regs], slot[tile], global[tile],
+    column_bits) -- the tile index of each thread register, the shared-memory slot and the
+    state-vector offset (first tile) of each tile index."""
+    I32 = ctypes.POINTER(ctypes.c_int32)
+    index = np.zeros(512 * 32, np.int32)
+    slot = np.zeros(1 << 14, np.int32)
+    glob = np.zeros(1 << 14, np.int32)
+    th, rg, cb = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().qvs_tile_layout(int(family), int(log2n), int(layout), index.ctypes.data_as(I32),
+                                  slot.ctypes.data_as(I32), glob.ctypes.data_as(I32), ctypes.byref(th),
+                                  ctypes.byref(rg), ctypes.byref(cb)), "qvs_tile_layout")
+    tile = th.value * rg.value
+    return index[:tile].reshape(th.value, rg.value), slot[:tile], glob[:tile], cb.value
 
 
 PARITY_TILE_BITS, PARITY_MAX_GATES = 12, 40

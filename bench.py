@@ -220,6 +220,42 @@ def cpu_model() -> str:
     return "unknown"
 
 
+def _host_numa(ptr: int, nbytes: int, gpu_index: int):
+    """Where a host buffer's pages live relative to the GPU: {"buffer_pages": {"N0": pages, ...},
+    "gpu_node": node}, the pages summed over the mappings (/proc/self/maps, numa_maps) that overlap
+    the buffer, the node from the GPU's PCI device in sysfs; None for a part that cannot be read (a
+    diagnostic of the upload rate only)."""
+    out = {"buffer_pages": None, "gpu_node": None}
+    try:
+        starts = set()
+        with open("/proc/self/maps") as f:
+            for ln in f:
+                lo, hi = (int(x, 16) for x in ln.split()[0].split("-"))
+                if lo < ptr + nbytes and hi > ptr:
+                    starts.add(lo)
+        pages = {}
+        with open("/proc/self/numa_maps") as f:
+            for ln in f:
+                parts = ln.split()
+                if parts and int(parts[0], 16) in starts:
+                    for x in parts[2:]:
+                        k, _, v = x.partition("=")
+                        if k.startswith("N") and k[1:].isdigit():
+                            pages[k] = pages.get(k, 0) + int(v)
+        out["buffer_pages"] = pages or None
+    except (OSError, ValueError):
+        pass
+    try:
+        bus = subprocess.run(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=pci.bus_id", "--format=csv,noheader"],
+                             capture_output=True, text=True, timeout=20).stdout.strip().lower()
+        dom, rest = bus.split(":", 1)
+        with open(f"/sys/bus/pci/devices/{dom[-4:]}:{rest}/numa_node") as f:
+            out["gpu_node"] = int(f.read().strip())
+    except (OSError, ValueError, subprocess.SubprocessError):
+        pass
+    return out
+
+
 def _oracle_solve_worker(args):
     """One oracle objective + adjoint-gradient solve (run in a spawned worker process)."""
     n, instance = args
@@ -786,6 +822,7 @@ def run_ours(args):
     step_bytes = sum(s["bytes"] for s in stats) / max(2, min(args.steps, 5))
 
     # ---- end to end through the C ABI with host buffers
+    numa = None
     if qubo:
         def set_inputs():                     # H2D of the step's quadratic form (host arrays)
             sim.set_quality_qubo(n, qc, qh, qJ)
@@ -793,6 +830,7 @@ def run_ours(args):
     else:
         q_host = torch.empty(dim, dtype=torch.float32, pin_memory=True)
         q_host.copy_(q.cpu())
+        numa = _host_numa(q_host.data_ptr(), 4 * dim, dev)
         del q
         torch.cuda.empty_cache()
 
@@ -861,7 +899,8 @@ def run_ours(args):
             "gpu_launches": launches_per_step * args.steps,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d_quality + 16 * p,
                     "d2h_bytes_per_step": 8 * (1 + 2 * p),
-                    "upload_ms_per_step": t_up / e2e_steps * 1e3, "solve_ms_per_step": t_solve / e2e_steps * 1e3},
+                    "upload_ms_per_step": t_up / e2e_steps * 1e3, "solve_ms_per_step": t_solve / e2e_steps * 1e3,
+                    "host_numa": numa},
             "clocks": clocks,
             "objective": E0,
         }

@@ -243,7 +243,7 @@ def _host_numa(ptr: int, nbytes: int, gpu_index: int):
                         if k.startswith("N") and k[1:].isdigit():
                             pages[k] = pages.get(k, 0) + int(v)
         out["buffer_pages"] = pages or None
-    except (OSError, ValueError):
+    except Exception:   # a diagnostic: never let it stop the bench
         pass
     try:
         bus = subprocess.run(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=pci.bus_id", "--format=csv,noheader"],
@@ -251,7 +251,7 @@ def _host_numa(ptr: int, nbytes: int, gpu_index: int):
         dom, rest = bus.split(":", 1)
         with open(f"/sys/bus/pci/devices/{dom[-4:]}:{rest}/numa_node") as f:
             out["gpu_node"] = int(f.read().strip())
-    except (OSError, ValueError, subprocess.SubprocessError):
+    except Exception:
         pass
     return out
 

@@ -107,6 +107,7 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.lines = []
+        self.first = 0
 
     def start(self):
         try:
@@ -122,6 +123,18 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def wait_first(self, timeout: float = 3.0):
+        """Wait (at most `timeout` s) for the first sample, so that nvidia-smi's start-up lies
+        before the timed region."""
+        t_end = time.time() + timeout
+        while self.proc is not None and not self.lines and time.time() < t_end:
+            time.sleep(0.02)
+
+    def mark(self):
+        """The timed region starts: the summary uses the samples from here on (all of them when
+        none arrives before stop)."""
+        self.first = len(self.lines)
+
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
@@ -133,7 +146,7 @@ class ClockSampler:
             self.proc.kill()
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in (self.lines[self.first:] if len(self.lines) > self.first else self.lines):
             parts = [x.strip() for x in ln.split(",")]
             if len(parts) < 8:
                 continue
@@ -781,13 +794,16 @@ def run_ours(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    # ---- device-resident timing
+    # ---- device-resident timing (the clock sampler starts before the warm-up, so that its
+    # start-up does not fall into the timed steps)
+    sampler = ClockSampler(dev)
+    sampler.start()
+    sampler.wait_first()
     for _ in range(args.warmup):
         sim.gradient(gs, ts)
     launches_per_step = sim.launches()
-    sampler = ClockSampler(dev)
     barrier()
-    sampler.start()
+    sampler.mark()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)

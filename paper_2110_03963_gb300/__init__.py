@@ -4,7 +4,9 @@ algorithms (QAOA, QWOA, QAOAz; Matwiejew & Wang, arXiv 2110.03963).
 The binding only marshals arguments: every step of the evolution, objective and gradient runs in
 the CUDA kernels of ``libqvs.so`` (built in-tree by ``_build.py``). PyTorch supplies device memory
 for inputs/outputs given as tensors and the CUDA stream. Loading fails loudly if the library is
-missing; there is no CPU fallback.
+missing; there is no CPU fallback. Before each call, every buffer passed as a bare pointer is
+checked against the element count, dtype and side (host or device) the library will use, taken
+from what the binding recorded when it created the handle or batch.
 
 Function names match the C ABI in ``include/qvs.h``.
 """

@@ -420,3 +420,55 @@ def test_host_allocation_failure_returns_enomem():
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=root, timeout=120)
     assert r.returncode == 0, r.stderr[-500:]
     assert int(r.stdout.strip().splitlines()[-1]) == -2   # QVS_ENOMEM
+
+
+def _prototypes():
+    """{name: [parameter declarations]} of every function include/qvs.h declares."""
+    src = open(os.path.join(ROOT, "include", "qvs.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for m in re.finditer(r"\b(qvs_\w+)\s*\(", src):
+        name, i, depth = m.group(1), m.end(), 1
+        j = i
+        while depth:
+            depth += {"(": 1, ")": -1}.get(src[j], 0)
+            j += 1
+        if src[j:].lstrip().startswith(";"):
+            params, cur, depth = [], "", 0
+            for ch in src[i:j - 1]:
+                depth += {"(": 1, ")": -1}.get(ch, 0)
+                if ch == "," and depth == 0:
+                    params.append(cur.strip())
+                    cur = ""
+                else:
+                    cur += ch
+            params.append(cur.strip())
+            out[name] = [p for p in params if p and p != "void"]
+    return out
+
+
+def test_binding_signatures_match_the_header(qvs):
+    """Every ctypes signature the binding sets has the header's parameter count, and each argument
+    the header's kind: fp64 by value, 32- or 64-bit integer by value, or a pointer (handles,
+    arrays, callbacks)."""
+    import ctypes
+    lib = qvs.load()
+    protos = _prototypes()
+    assert set(protos) == set(qvs.EXPORTED)
+    pointer_like = (ctypes.c_void_p, ctypes.c_char_p)
+    for name, params in protos.items():
+        argtypes = getattr(lib, name).argtypes
+        assert argtypes is not None and len(argtypes) == len(params), (name, params, argtypes)
+        for decl, t in zip(params, argtypes):
+            if "*" in decl or "(" in decl or decl.split()[0] in ("qvs_t", "qvs_batch_t", "qvs_fg_fn"):
+                ok = (t in pointer_like or issubclass(t, ctypes._Pointer) or issubclass(t, ctypes._CFuncPtr))
+            elif decl.split()[0] == "double":
+                ok = t is ctypes.c_double
+            elif decl.split()[0] == "int64_t":
+                ok = ctypes.sizeof(t) == 8 and issubclass(t, ctypes._SimpleCData) and t not in (ctypes.c_double,)
+            elif decl.split()[0] in ("int", "int32_t"):
+                ok = t in (ctypes.c_int, ctypes.c_int32)
+            else:
+                ok = False
+            assert ok, (name, decl, t)
+    assert lib.qvs_strerror.restype is ctypes.c_char_p

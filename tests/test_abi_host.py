@@ -462,6 +462,17 @@ def test_binding_signatures_match_the_header(qvs):
         for decl, t in zip(params, argtypes):
             if "*" in decl or "(" in decl or decl.split()[0] in ("qvs_t", "qvs_batch_t", "qvs_fg_fn"):
                 ok = (t in pointer_like or issubclass(t, ctypes._Pointer) or issubclass(t, ctypes._CFuncPtr))
+                # a typed pointer points to the header's element type
+                base = decl.replace("const", "").split("*")[0].split()
+                if ok and issubclass(t, ctypes._Pointer) and "(" not in decl and base:
+                    want = {"double": ctypes.c_double, "float": ctypes.c_float, "int": ctypes.c_int,
+                            "int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64, "uint32_t": ctypes.c_uint32,
+                            "qvs_t": ctypes.c_void_p, "qvs_batch_t": ctypes.c_void_p,
+                            "qvs_mixer_desc": qvs.MixerDesc, "qvs_batch_info_t": qvs.BatchInfo}.get(base[0])
+                    ok = want is not None and ctypes.sizeof(t._type_) == ctypes.sizeof(want) and (
+                        t._type_ is want or (issubclass(want, ctypes._SimpleCData) and
+                                             issubclass(t._type_, ctypes._SimpleCData) and
+                                             t._type_._type_ == want._type_))
             elif decl.split()[0] == "double":
                 ok = t is ctypes.c_double
             elif decl.split()[0] == "int64_t":

@@ -483,3 +483,34 @@ def test_binding_signatures_match_the_header(qvs):
                 ok = False
             assert ok, (name, decl, t)
     assert lib.qvs_strerror.restype is ctypes.c_char_p
+
+
+def test_binding_structs_match_the_header(qvs, tmp_path):
+    """The binding's ctypes mirrors of qvs_mixer_desc and qvs_batch_info_t have the C structs'
+    size and field offsets, as a C compiler lays them out from include/qvs.h."""
+    import ctypes
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"qvs_mixer_desc": qvs.MixerDesc, "qvs_batch_info_t": qvs.BatchInfo}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', f'#include "{os.path.join(ROOT, "include", "qvs.h")}"',
+             "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-o", str(exe), str(src)], check=True, capture_output=True, timeout=60)
+    got = {}
+    for ln in subprocess.run([str(exe)], check=True, capture_output=True, text=True, timeout=30).stdout.splitlines():
+        cname, field, value = ln.split()
+        got[(cname, field)] = int(value)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)

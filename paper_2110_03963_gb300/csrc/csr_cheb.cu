@@ -375,7 +375,8 @@ __global__ void __launch_bounds__(NT) lz_update_kernel(int64_t dim, double alpha
   lz_block_add(acc, out);
 }
 
-__global__ void lz_scale_kernel(int64_t dim, double s, const double* __restrict__ x, double* __restrict__ y) {
+// y = s x, also in place (y may be x, so neither pointer is restrict-qualified)
+__global__ void lz_scale_kernel(int64_t dim, double s, const double* x, double* y) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < dim; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = s * x[i];
 }

@@ -43,7 +43,7 @@ WORKLOAD = "QAOA weighted max-cut, n=28 (2^28 complex64 amplitudes), G(28,1/2) U
 # solve, with the sha256 of the kernel sources it was taken on. Reported only while the sources
 # still hash to that value (null otherwise: the capture no longer describes the built kernel).
 TRAFFIC = {"hc_pass_R1_c64": {"bytes_per_amp": 32.0,
-                              "sources_sha256": "1bb4b7f157300b6731697e95e1a4bab094fc27fecb9e2f48853408245072563d"}}
+                              "sources_sha256": "7c1a236ef3537adea55cb14b82f65ae2f027be52b49a9734c8997ab13b9cd97a"}}
 TRAFFIC_SOURCES = ["hc_kernels.cuh", "hc_pass.cuh", "hc_staged.cuh", "hypercube.cu", "hc_pass_th_a.cu",
                    "hc_pass_th_b.cu", "hc_pass_th_c.cu", "hc_pass_th_d.cu"]
 GOLDEN = os.path.join(ROOT, "tests", "golden")

@@ -22,6 +22,7 @@
 #include <stdio.h>
 #include <stdlib.h>
 #include <sys/stat.h>
+#include <unistd.h>
 
 #include <algorithm>
 #include <new>
@@ -1362,7 +1363,7 @@ static void tune_cache_store(const std::string& key, int ctas, int pol, double m
   snprintf(buf, sizeof(buf), "{\"key\": \"%s\", \"ctas_per_sm\": %d, \"ckpt_policy\": %d, \"ms\": %.3f}", key.c_str(),
            ctas, pol, ms);
   lines.push_back(buf);
-  const std::string tmp = path + ".tmp";
+  const std::string tmp = path + ".tmp." + std::to_string((long long)getpid());   // one per process
   FILE* f = fopen(tmp.c_str(), "w");
   if (!f) return;
   fputs("{\"batch_schedules\": [\n", f);

@@ -896,13 +896,17 @@ def hypercube_desc(n: int) -> MixerDesc:
 
 
 def circulant_desc(offsets, weights=None) -> MixerDesc:
+    """Connection offsets and (optionally) one weight per offset; the library reads n_offsets of
+    each, so the two arrays must have one length."""
     d = MixerDesc()
-    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    off = np.ascontiguousarray(offsets, dtype=np.int64).reshape(-1)
     d.n_offsets = len(off)
     d._off = off   # keep alive
     d.offsets = off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
     if weights is not None:
-        w = np.ascontiguousarray(weights, dtype=np.float64)
+        w = np.ascontiguousarray(weights, dtype=np.float64).reshape(-1)
+        if w.shape != off.shape:
+            raise QvsError(QVS_EINVAL, f"{w.shape[0]} weights for {off.shape[0]} offsets")
         d._w = w
         d.offset_weights = w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     return d

@@ -144,3 +144,17 @@ def test_batch_buffers_are_sized_by_the_batch(fake):
     init = np.zeros(2 * 2 * 1 + 2 * 2)
     _passes(fake, "qvs_benchmark", qvs.qvs_benchmark, 12, np.zeros(4096, np.float32), 1, 2, 2, init)
     _refused_before_library(fake, qvs.qvs_benchmark, 12, np.zeros(2048, np.float32), 1, 2, 2, init)
+
+
+def test_mixer_descriptions():
+    d = qvs.circulant_desc([1, 2, 4], [0.5, 1.0, 2.0])
+    assert d.n_offsets == 3 and [d.offsets[i] for i in range(3)] == [1, 2, 4]
+    assert [d.offset_weights[i] for i in range(3)] == [0.5, 1.0, 2.0]
+    assert not qvs.circulant_desc([1, 2]).offset_weights          # NULL: every weight 1
+    _refused(qvs.circulant_desc, [1, 2, 4], [0.5, 1.0])            # one weight per offset
+    d = qvs.xy_ring_desc(24, 12, (-31.0, 31.0), 1e-8)
+    assert (d.n_qubits, d.hamming_weight, d.spec_lo, d.spec_hi, d.cheb_tol) == (24, 12, -31.0, 31.0, 1e-8)
+    assert qvs.hypercube_desc(28).n_qubits == 28 and qvs.parity_desc(26).n_qubits == 26
+    rowptr, colind = np.array([0, 1, 2], np.int64), np.array([1, 0], np.int32)
+    d = qvs.csr_desc(rowptr, colind, np.full(2, 2.0, np.float32), 0.0, (-2.0, 2.0))
+    assert (d.nnz, d.csr_on_device, d.spec_lo, d.spec_hi) == (2, 0, -2.0, 2.0) and d.values

@@ -568,7 +568,9 @@ def qvs_optimise(h, gammas0, ts0, gtol: float = 1e-6, max_iter: int = 200):
 
 
 def qvs_quality_subset(n: int, w, out, dtype: int, stream=None):
-    w = np.ascontiguousarray(w, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64).reshape(-1)
+    if w.shape[0] != int(n):
+        raise QvsError(QVS_EINVAL, f"{w.shape[0]} item weights for {int(n)} qubits")
     _check_buffer(out, 1 << int(n), {_quality_dtype(dtype)}, "quality output", device=True)
     p, dev = _ptr_of(out)
     _check(load().qvs_quality_subset(n, _dptr(w), int(dtype), p, _stream_ptr(stream)), "qvs_quality_subset")
@@ -576,8 +578,11 @@ def qvs_quality_subset(n: int, w, out, dtype: int, stream=None):
 
 
 def qvs_quality_portfolio(n_qubits: int, states_dev, returns, cov, omega: float, out, dtype: int, stream=None):
-    r = np.ascontiguousarray(returns, dtype=np.float64)
+    r = np.ascontiguousarray(returns, dtype=np.float64).reshape(-1)
     c = np.ascontiguousarray(cov, dtype=np.float64)
+    M = int(n_qubits) // 2           # the library reads M returns and the M x M covariance, row-major
+    if r.shape[0] != M or c.size != M * M:
+        raise QvsError(QVS_EINVAL, f"{M} assets need {M} returns and an {M} x {M} covariance")
     dim = int(states_dev.shape[0])
     _check_buffer(states_dev, dim, {"int64"}, "states", device=True)
     _check_buffer(out, dim, {_quality_dtype(dtype)}, "quality output", device=True)

@@ -158,3 +158,16 @@ def test_mixer_descriptions():
     rowptr, colind = np.array([0, 1, 2], np.int64), np.array([1, 0], np.int32)
     d = qvs.csr_desc(rowptr, colind, np.full(2, 2.0, np.float32), 0.0, (-2.0, 2.0))
     assert (d.nnz, d.csr_on_device, d.spec_lo, d.spec_hi) == (2, 0, -2.0, 2.0) and d.values
+
+
+def test_generator_inputs_have_the_sizes_the_library_reads(fake):
+    def refused_for(what, fn, *args):
+        before = len(fake.calls)
+        with pytest.raises(qvs.QvsError) as e:
+            fn(*args)
+        assert e.value.status == qvs.QVS_EINVAL and what in str(e.value) and fake.calls[before:] == []
+    refused_for("item weights", qvs.qvs_quality_subset, 4, np.ones(3), np.zeros(16, np.float32), qvs.QVS_F32)
+    states = np.arange(16, dtype=np.int64)
+    out = np.zeros(16, np.float32)
+    refused_for("assets", qvs.qvs_quality_portfolio, 4, states, [1.0], np.eye(2), 0.5, out, qvs.QVS_F32)
+    refused_for("assets", qvs.qvs_quality_portfolio, 4, states, [1.0, 2.0], np.eye(3), 0.5, out, qvs.QVS_F32)

@@ -431,8 +431,11 @@ def qvs_quality_maxcut(n: int, eu, ev, w, out, dtype: int, stream=None):
 
 
 def _qubo_arrays(n, hlin, J):
-    hl = np.ascontiguousarray(hlin, dtype=np.float64).reshape(n)
-    Jm = np.ascontiguousarray(J, dtype=np.float64).reshape(n * n)
+    hl = np.ascontiguousarray(hlin, dtype=np.float64).reshape(-1)
+    Jm = np.ascontiguousarray(J, dtype=np.float64).reshape(-1)
+    if hl.shape[0] != int(n) or Jm.shape[0] != int(n) * int(n):
+        raise QvsError(QVS_EINVAL, f"a quadratic form on {int(n)} qubits needs {int(n)} linear and "
+                                   f"{int(n)} x {int(n)} pair coefficients")
     return hl, Jm
 
 
@@ -844,9 +847,16 @@ class Batch:
         qvs_batch_set_quality(self.h, q_concat)
         return self
 
+    def _per_instance(self, gammas_list, ts_list):
+        """Per-instance parameter arrays, one of each instance's depth, concatenated."""
+        if len(gammas_list) != len(self.ns) or len(ts_list) != len(self.ns) or any(
+                len(g) != p or len(t) != p for g, t, p in zip(gammas_list, ts_list, self.ps.tolist())):
+            raise QvsError(QVS_EINVAL, "one gamma and one t array per instance, of that instance's depth")
+        return np.concatenate(gammas_list), np.concatenate(ts_list)
+
     def gradient(self, gammas_list, ts_list):
         """Lists of per-instance parameter arrays -> (E array, list of dgamma, list of dt)."""
-        E, dg, dt = qvs_batch_gradient(self.h, np.concatenate(gammas_list), np.concatenate(ts_list), len(self.ns))
+        E, dg, dt = qvs_batch_gradient(self.h, *self._per_instance(gammas_list, ts_list), len(self.ns))
         cut = lambda v: [v[self.poff[i]:self.poff[i + 1]] for i in range(len(self.ns))]
         return E, cut(dg), cut(dt)
 
@@ -858,8 +868,8 @@ class Batch:
     def optimise(self, gammas_list, ts_list, gtol: float = 1e-6, max_iter: int = 200):
         """Lists of per-instance start points -> (list of gammas, list of ts, f, iterations,
         evaluations, stop), per instance."""
-        g, t, f, it, ev, stop = qvs_batch_optimise(self.h, np.concatenate(gammas_list), np.concatenate(ts_list),
-                                                   len(self.ns), gtol, max_iter)
+        g, t, f, it, ev, stop = qvs_batch_optimise(self.h, *self._per_instance(gammas_list, ts_list), len(self.ns),
+                                                   gtol, max_iter)
         cut = lambda v: [v[self.poff[i]:self.poff[i + 1]] for i in range(len(self.ns))]
         return cut(g), cut(t), f, it, ev, stop
 

@@ -171,3 +171,15 @@ def test_generator_inputs_have_the_sizes_the_library_reads(fake):
     out = np.zeros(16, np.float32)
     refused_for("assets", qvs.qvs_quality_portfolio, 4, states, [1.0], np.eye(2), 0.5, out, qvs.QVS_F32)
     refused_for("assets", qvs.qvs_quality_portfolio, 4, states, [1.0, 2.0], np.eye(3), 0.5, out, qvs.QVS_F32)
+
+
+def test_batch_parameters_per_instance(fake):
+    b = qvs.Batch([12, 13], [2, 3])
+    good_g, good_t = [np.zeros(2), np.zeros(3)], [np.zeros(2), np.zeros(3)]
+    _passes(fake, "qvs_batch_gradient", b.gradient, good_g, good_t)
+    # the right total (5) split 3 + 2 across the instances is refused, as is a missing instance
+    _refused_before_library(fake, b.gradient, [np.zeros(3), np.zeros(2)], [np.zeros(3), np.zeros(2)])
+    _refused_before_library(fake, b.optimise, [np.zeros(2)], [np.zeros(2)])
+    _refused_before_library(fake, qvs.qvs_quality_qubo, 3, 0.0, np.zeros(3), np.zeros((2, 2)),
+                            np.zeros(8, np.float32), qvs.QVS_F32)
+    b.close()   # while the stand-in is in place: the fake handle must never reach the real library

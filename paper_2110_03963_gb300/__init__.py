@@ -849,8 +849,9 @@ class Batch:
 
     def _per_instance(self, gammas_list, ts_list):
         """Per-instance parameter arrays, one of each instance's depth, concatenated."""
-        if len(gammas_list) != len(self.ns) or len(ts_list) != len(self.ns) or any(
-                len(g) != p or len(t) != p for g, t, p in zip(gammas_list, ts_list, self.ps.tolist())):
+        lg = np.fromiter(map(len, gammas_list), dtype=np.int64, count=len(gammas_list))
+        lt = np.fromiter(map(len, ts_list), dtype=np.int64, count=len(ts_list))
+        if lg.shape != self.ps.shape or lt.shape != self.ps.shape or np.any(lg != self.ps) or np.any(lt != self.ps):
             raise QvsError(QVS_EINVAL, "one gamma and one t array per instance, of that instance's depth")
         return np.concatenate(gammas_list), np.concatenate(ts_list)
 

@@ -79,7 +79,7 @@ def test_create_rejects_half_an_allocator_without_gpu(qvs):
     assert h.value is None and calls == []
 
 
-@pytest.mark.parametrize("n,k", [(6, 3), (8, 4), (9, 2), (12, 6)])
+@pytest.mark.parametrize("n,k", [(6, 3), (8, 4), (9, 2), (12, 6), (7, 1), (7, 6), (5, 0), (5, 5), (3, 1)])
 def test_xy_ring_csr_matches_oracle_operator(qvs, n, k):
     states, rowptr, colind = qvs.qvs_xy_ring_csr(n, k)
     ref_states = orc.subspace_states(n, k)

@@ -514,3 +514,17 @@ def test_binding_structs_match_the_header(qvs, tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for fname, _ in py._fields_:
             assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+
+
+def test_host_entry_points_degenerate_inputs(qvs):
+    """No edges: the quadratic form is zero. No iterations: BFGS returns its start, as the oracle's.
+    t = 0: the series is the single coefficient 1."""
+    c, h, J = qvs.qvs_qubo_from_maxcut(5, [], [])
+    assert c == 0.0 and not h.any() and not J.any()
+    quad = lambda x: (float(x @ x), 2.0 * x)
+    x0 = np.array([1.0, -2.0])
+    x, f, it, ev, stop = qvs.qvs_bfgs_minimize(quad, x0, gtol=1e-8, max_iter=0)
+    xo, fo, ito, evo, stopo = orc.bfgs_minimize(quad, x0, gtol=1e-8, max_iter=0)
+    assert np.array_equal(x, x0) and (f, it, ev, stop) == (fo, ito, evo, stopo) == (5.0, 0, 1, 1)
+    c, tail = qvs.qvs_chebyshev_coefficients(1.5, 10.0, 0.0, 1e-7)
+    assert len(c) == 1 and c[0] == 1.0 and tail == 0.0
